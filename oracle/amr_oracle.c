@@ -1,0 +1,884 @@
+/*
+ * amr_oracle.c -- plain, unfused FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg load
+ * this.  It shares no code with the CUDA path.  Every function follows the
+ * paper's definitions in the paper's order:
+ *   Sec. 4  conservation law, U, F^x/F^y/F^z, ideal-gas EOS, MOL operator
+ *           L(U), PLM reconstruction with generalised minmod, HLL flux;
+ *   Sec. 5.1 the three-line form of TVD-RK2 (U1, U2, average);
+ *   Sec. 3  Berger-Colella recursion: grids as separate IBVPs, subcycling;
+ *   Sec. 7.1 GLM-MHD variables and fluxes.
+ * Where the paper is silent or garbled the reading taken is stated at the
+ * function (PLM half slope, true two-wave HLL, induction-flux ordering,
+ * Dedner 2x2 normal-field solve, CFL, ghost refill per stage, conservative
+ * minmod prolongation, pairwise restriction, flux registers).
+ *
+ * Deliberately slow: per-cell loops, no blocking, no fusion.  Compile with
+ * -O2 -ffp-contract=off so no multiply-add is contracted.
+ */
+#include "amr_oracle.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define GH 2          /* ghost cells per side: PLM needs two cells on each side (Sec. 4 stencil) */
+#define MAXV 9
+
+static char g_err[512];
+const char* orc_error(void) { return g_err; }
+
+/* ------------------------------------------------------------------------ */
+/* Point functions                                                          */
+/* ------------------------------------------------------------------------ */
+
+static double sgn(double a) { return a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); }
+
+/* Sec. 4 minmod(a,b,c) = 1/4 (sign a + sign b) |sign a + sign c| min(|a|,|b|,|c|), sign(0) = 0. */
+double orc_minmod3(double a, double b, double c) {
+  double m = fabs(a);
+  if (fabs(b) < m) m = fabs(b);
+  if (fabs(c) < m) m = fabs(c);
+  return 0.25 * (sgn(a) + sgn(b)) * fabs(sgn(a) + sgn(c)) * m;
+}
+
+/* Two-argument minmod used by the prolongation limiter (paper-silent reading). */
+double orc_minmod2(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+/* Sec. 4 PLM, face i-1/2 from u4 = (u_{i-2}, u_{i-1}, u_i, u_{i+1}).
+ * The printed formula adds the full limited difference to the cell value; the
+ * reading taken (plm_literal = 0) adds half of it, i.e. extrapolates from the
+ * cell centre to the face with the limited slope. */
+void orc_plm_face(const orc_config* cfg, const double* u, double* ul, double* ur) {
+  const double th = cfg->theta;
+  const double h = cfg->plm_literal ? 1.0 : 0.5;
+  *ul = u[1] + h * orc_minmod3((u[1] - u[0]) * th, (u[2] - u[1]) * th, (u[2] - u[0]) / 2.0);
+  *ur = u[2] + h * orc_minmod3((u[2] - u[3]) * th, (u[1] - u[2]) * th, (u[1] - u[3]) / 2.0);
+}
+
+/* Reconstructed variables R = (rho, vx, vy, vz, e, Bx, By, Bz, psi), e the
+ * specific internal energy (the listing of Sec. 5.1 loads Rho, Eint, Vx, Vy, Vz). */
+static void cons_to_rec(const orc_config* c, const double* u, double* r) {
+  double rho = u[0];
+  double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+  double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+  double mag = 0.0;
+  if (c->nvar == 9) mag = 0.5 * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+  r[0] = rho; r[1] = vx; r[2] = vy; r[3] = vz;
+  r[4] = (u[4] - kin - mag) / rho;
+  if (c->nvar == 9) { r[5] = u[5]; r[6] = u[6]; r[7] = u[7]; r[8] = u[8]; }
+}
+
+/* Sec. 4: U = (rho, rho v, rho E) with E = v^2/2 + e; Sec. 7.1 adds B^2/2, B, psi. */
+static void rec_to_cons(const orc_config* c, const double* r, double* u) {
+  double rho = r[0];
+  double v2 = r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+  u[0] = rho; u[1] = rho * r[1]; u[2] = rho * r[2]; u[3] = rho * r[3];
+  u[4] = rho * (v2 / 2.0 + r[4]);
+  if (c->nvar == 9) {
+    u[4] += (r[5] * r[5] + r[6] * r[6] + r[7] * r[7]) / 2.0;
+    u[5] = r[5]; u[6] = r[6]; u[7] = r[7]; u[8] = r[8];
+  }
+}
+
+static double pressure(const orc_config* c, const double* r) { return (c->gamma - 1.0) * r[0] * r[4]; } /* p = (gamma-1) rho e */
+
+/* Signal speed along dir: sound speed (Sec. 4) or fast magnetosonic speed (MHD). */
+static double signal_speed(const orc_config* c, const double* r, int dir) {
+  double p = pressure(c, r);
+  double a2 = c->gamma * p / r[0];
+  if (c->nvar != 9) return sqrt(a2);
+  double b2 = (r[5] * r[5] + r[6] * r[6] + r[7] * r[7]) / r[0];
+  double bd2 = r[5 + dir] * r[5 + dir] / r[0];
+  double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * bd2;
+  if (disc < 0.0) disc = 0.0;
+  return sqrt(0.5 * (s + sqrt(disc)));
+}
+
+/* Physical flux F^dir of reconstructed state r (Sec. 4 F^x,F^y,F^z; Sec. 7.1 GLM-MHD).
+ * Induction entries use F^d_{B_k} = v_d B_k - v_k B_d (k != d), F^d_{B_d} = psi,
+ * F^d_psi = c_h^2 B_d; F^x as printed already has this form, the printed F^y and
+ * F^z have two of their B entries interchanged. */
+static void rec_flux(const orc_config* c, const double* r, int d, double ch, double* f) {
+  double rho = r[0];
+  const double* v = r + 1;
+  double p = pressure(c, r);
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double h = r[4] + p / rho;                       /* h = e + p/rho */
+  f[0] = rho * v[d];
+  for (int k = 0; k < 3; ++k) f[1 + k] = rho * v[k] * v[d] + (k == d ? p : 0.0);
+  f[4] = rho * (v2 / 2.0 + h) * v[d];
+  if (c->nvar == 9) {
+    const double* B = r + 5;
+    double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    double Bv = B[0] * v[0] + B[1] * v[1] + B[2] * v[2];
+    for (int k = 0; k < 3; ++k) f[1 + k] += (k == d ? B2 / 2.0 : 0.0) - B[k] * B[d];
+    f[4] += B2 * v[d] - B[d] * Bv;
+    for (int k = 0; k < 3; ++k) f[5 + k] = (k == d) ? r[8] : v[d] * B[k] - v[k] * B[d];
+    f[8] = ch * ch * B[d];
+  }
+}
+
+void orc_prim_to_cons(const orc_config* c, const double* w, double* u) {
+  double r[MAXV];
+  r[0] = w[0]; r[1] = w[1]; r[2] = w[2]; r[3] = w[3];
+  r[4] = w[4] / ((c->gamma - 1.0) * w[0]);          /* e = p / ((gamma-1) rho) */
+  if (c->nvar == 9) for (int k = 5; k < 9; ++k) r[k] = w[k];
+  rec_to_cons(c, r, u);
+}
+
+void orc_cons_to_prim(const orc_config* c, const double* u, double* w) {
+  double r[MAXV];
+  cons_to_rec(c, u, r);
+  for (int k = 0; k < c->nvar; ++k) w[k] = r[k];
+  w[4] = pressure(c, r);
+}
+
+/* Interface flux from reconstructed left/right states.
+ * HLL (default): the two-wave solver of Harten, Lax & van Leer with the
+ *   Sec. 4 signal speeds lambda^{+-} = v_d +- c, S_L = min(0, lambda^-_l, lambda^-_r),
+ *   S_R = max(0, lambda^+_l, lambda^+_r).
+ * LLF: the flux as printed in Sec. 4, 0.5 (F_l + F_r - lambda_0 (U_r - U_l)) with
+ *   lambda_0 = max(0, lambda^+_l, lambda^+_r, -lambda^-_l, -lambda^-_r); the jump
+ *   is taken in the conserved variables.
+ * MHD: the (B_d, psi) pair is solved exactly (Dedner et al. 2002 upwind 2x2
+ *   system), and B_d of both states is replaced by the resolved value before
+ *   the remaining seven variables go through HLL/LLF. */
+static void riemann_rec(const orc_config* c, const double* rl_in, const double* rr_in, int d, double ch,
+                        double* F) {
+  const int nv = c->nvar;
+  double rl[MAXV], rr[MAXV];
+  for (int k = 0; k < nv; ++k) { rl[k] = rl_in[k]; rr[k] = rr_in[k]; }
+  double Bm = 0.0, psim = 0.0;
+  if (nv == 9) {
+    double Bl = rl[5 + d], Br = rr[5 + d];
+    Bm = 0.5 * (Bl + Br) - (rr[8] - rl[8]) / (2.0 * ch);
+    psim = 0.5 * (rl[8] + rr[8]) - 0.5 * ch * (Br - Bl);
+    rl[5 + d] = Bm; rr[5 + d] = Bm;
+  }
+  double Ul[MAXV], Ur[MAXV], Fl[MAXV], Fr[MAXV];
+  rec_to_cons(c, rl, Ul);
+  rec_to_cons(c, rr, Ur);
+  rec_flux(c, rl, d, ch, Fl);
+  rec_flux(c, rr, d, ch, Fr);
+  double cl = signal_speed(c, rl, d), cr = signal_speed(c, rr, d);
+  double lpl = rl[1 + d] + cl, lml = rl[1 + d] - cl;
+  double lpr = rr[1 + d] + cr, lmr = rr[1 + d] - cr;
+  if (c->riemann == ORC_LLF) {
+    double a = 0.0;
+    if (lpl > a) a = lpl;
+    if (lpr > a) a = lpr;
+    if (-lml > a) a = -lml;
+    if (-lmr > a) a = -lmr;
+    for (int k = 0; k < nv; ++k) F[k] = 0.5 * (Fl[k] + Fr[k] - a * (Ur[k] - Ul[k]));
+  } else {
+    double SL = 0.0, SR = 0.0;
+    if (lml < SL) SL = lml;
+    if (lmr < SL) SL = lmr;
+    if (lpl > SR) SR = lpl;
+    if (lpr > SR) SR = lpr;
+    if (SR - SL == 0.0) {
+      for (int k = 0; k < nv; ++k) F[k] = 0.5 * (Fl[k] + Fr[k]);
+    } else {
+      for (int k = 0; k < nv; ++k) F[k] = (SR * Fl[k] - SL * Fr[k] + SL * SR * (Ur[k] - Ul[k])) / (SR - SL);
+    }
+  }
+  if (nv == 9) {
+    F[5 + d] = psim;
+    F[8] = ch * ch * Bm;
+  }
+}
+
+void orc_riemann(const orc_config* c, const double* wl, const double* wr, int dir, double ch, double* f) {
+  double ul[MAXV], ur[MAXV], rl[MAXV], rr[MAXV];
+  orc_prim_to_cons(c, wl, ul);
+  orc_prim_to_cons(c, wr, ur);
+  cons_to_rec(c, ul, rl);
+  cons_to_rec(c, ur, rr);
+  riemann_rec(c, rl, rr, dir, ch, f);
+}
+
+void orc_phys_flux(const orc_config* c, const double* w, int dir, double ch, double* f) {
+  double u[MAXV], r[MAXV];
+  orc_prim_to_cons(c, w, u);
+  cons_to_rec(c, u, r);
+  rec_flux(c, r, dir, ch, f);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchy                                                                */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int level, lo[3], n[3], m[3];
+  size_t ncell_g;          /* m0*m1*m2 */
+  double* U;               /* [V][m2][m1][m0] with ghosts */
+  double* U1;              /* stage-1 state, same shape */
+  double* Uold;            /* interior copy at the start of the level's step */
+  double* F[3];            /* face fluxes, [V][n2'][n1'][n0'] with n_d' = n_d + 1 */
+  unsigned char* covered;  /* interior cells covered by level+1 (NULL if none) */
+  int* sib; int nsib;      /* same-level candidates for ghost copies */
+  int* par; int npar;      /* parent-level candidates for prolongation */
+} opatch;
+
+/* One coarse-fine face: fine patch side of a level-l patch against an
+ * uncovered level-(l-1) cell C. */
+typedef struct {
+  int fpatch, d, side;     /* fine patch, normal dir, side of the fine patch (0 lo, 1 hi) */
+  int fface[3];            /* local face index in the fine patch of the (0,0) sub-face */
+  int cpatch, cidx[3];     /* coarse patch holding C and C's local interior index */
+  int cface;               /* local face index along d of the face in C's patch */
+  int cside;               /* +1: face is C's high face, -1: C's low face */
+  double Rc[MAXV], Rf[MAXV];
+} oreg;
+
+struct orc_sim {
+  orc_config cfg;
+  int V, np, nlev;
+  opatch* P;
+  int* lev_first; int* lev_count;   /* patches sorted by level */
+  double dx0[3];
+  oreg** reg; int* nreg;            /* per level l >= 1 */
+  double ch_used;
+  int err;
+};
+
+static size_t gidx(const opatch* p, int i, int j, int k) { /* ghost-extended local index */
+  return ((size_t)(k + GH) * p->m[1] + (size_t)(j + GH)) * p->m[0] + (size_t)(i + GH);
+}
+static size_t fidx(const opatch* p, int d, int i, int j, int k) {
+  int n0 = p->n[0] + (d == 0), n1 = p->n[1] + (d == 1);
+  return ((size_t)k * n1 + j) * n0 + i;
+}
+static size_t fsize(const opatch* p, int d) {
+  return (size_t)(p->n[0] + (d == 0)) * (p->n[1] + (d == 1)) * (p->n[2] + (d == 2));
+}
+
+static int level_n(const orc_sim* s, int l, int d) { return s->cfg.base_n[d] << l; }
+
+static int periodic(const orc_sim* s, int d) { return s->cfg.bc[2 * d] == ORC_BC_PERIODIC; }
+
+/* does [alo,ahi) intersect [blo,bhi) under the periodic images of axis d */
+static int axis_touch(const orc_sim* s, int l, int d, int alo, int ahi, int blo, int bhi) {
+  int N = level_n(s, l, d);
+  for (int sh = -1; sh <= 1; ++sh) {
+    if (sh != 0 && !periodic(s, d)) continue;
+    int lo = blo + sh * N, hi = bhi + sh * N;
+    if (alo < hi && lo < ahi) return 1;
+  }
+  return 0;
+}
+
+static int contains(const opatch* q, const int* g) {
+  for (int d = 0; d < 3; ++d)
+    if (g[d] < q->lo[d] || g[d] >= q->lo[d] + q->n[d]) return 0;
+  return 1;
+}
+
+static void free_sim(orc_sim* s) {
+  if (!s) return;
+  if (s->P) {
+    for (int i = 0; i < s->np; ++i) {
+      opatch* p = &s->P[i];
+      free(p->U); free(p->U1); free(p->Uold); free(p->covered); free(p->sib); free(p->par);
+      for (int d = 0; d < 3; ++d) free(p->F[d]);
+    }
+  }
+  if (s->reg) for (int l = 0; l < s->nlev; ++l) free(s->reg[l]);
+  free(s->reg); free(s->nreg); free(s->P); free(s->lev_first); free(s->lev_count);
+  free(s);
+}
+
+void orc_destroy(orc_sim* s) { free_sim(s); }
+
+static int find_in(const orc_sim* s, const int* cand, int ncand, const int* g) {
+  for (int c = 0; c < ncand; ++c)
+    if (contains(&s->P[cand[c]], g)) return cand[c];
+  return -1;
+}
+
+/* Build the coarse-fine register faces of level l (Berger-Colella refluxing). */
+static int build_registers(orc_sim* s, int l) {
+  int cap = 64, n = 0;
+  oreg* R = (oreg*)malloc(sizeof(oreg) * cap);
+  /* entries grouped by (d, side) so that reflux touches any coarse cell at most once per group */
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+      for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi) {
+        opatch* p = &s->P[pi];
+        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        int xf = side ? p->lo[d] + p->n[d] : p->lo[d];        /* fine face plane (level l) */
+        int Xc = xf / 2;                                      /* coarse face plane */
+        int Cd = side ? Xc : Xc - 1;                          /* coarse cell outside the patch */
+        int Nc = level_n(s, l - 1, d);
+        if (Cd < 0 || Cd >= Nc) {
+          if (!periodic(s, d)) continue;                      /* physical boundary: no register */
+          Cd = (Cd + Nc) % Nc;
+        }
+        for (int b = p->lo[t2] / 2; b < (p->lo[t2] + p->n[t2]) / 2; ++b)
+          for (int a = p->lo[t1] / 2; a < (p->lo[t1] + p->n[t1]) / 2; ++a) {
+            int C[3];
+            C[d] = Cd; C[t1] = a; C[t2] = b;
+            /* covered by a level-l patch?  (children of C lie in one patch: even alignment) */
+            int child[3] = {2 * C[0], 2 * C[1], 2 * C[2]};
+            int cov = 0;
+            for (int qi = s->lev_first[l]; qi < s->lev_first[l] + s->lev_count[l] && !cov; ++qi)
+              if (contains(&s->P[qi], child)) cov = 1;
+            if (cov) continue;
+            int cq = -1;
+            for (int qi = s->lev_first[l - 1]; qi < s->lev_first[l - 1] + s->lev_count[l - 1]; ++qi)
+              if (contains(&s->P[qi], C)) { cq = qi; break; }
+            if (cq < 0) {
+              snprintf(g_err, sizeof g_err, "level %d patch %d: coarse cell outside level %d", l, pi, l - 1);
+              free(R);
+              return -1;
+            }
+            if (n == cap) { cap *= 2; R = (oreg*)realloc(R, sizeof(oreg) * cap); }
+            oreg* e = &R[n++];
+            memset(e, 0, sizeof *e);
+            e->fpatch = pi; e->d = d; e->side = side;
+            e->fface[d] = side ? p->n[d] : 0;
+            e->fface[t1] = 2 * a - p->lo[t1];
+            e->fface[t2] = 2 * b - p->lo[t2];
+            e->cpatch = cq;
+            for (int k = 0; k < 3; ++k) e->cidx[k] = C[k] - s->P[cq].lo[k];
+            e->cside = side ? -1 : +1;
+            e->cface = side ? e->cidx[d] : e->cidx[d] + 1;
+          }
+      }
+  s->reg[l] = R;
+  s->nreg[l] = n;
+  return 0;
+}
+
+orc_sim* orc_create(const orc_config* cfg, int npatch, const orc_patch* patches) {
+  g_err[0] = 0;
+  if (!cfg || npatch <= 0 || !patches || (cfg->nvar != 5 && cfg->nvar != 9)) {
+    snprintf(g_err, sizeof g_err, "bad arguments");
+    return NULL;
+  }
+  orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+  s->cfg = *cfg;
+  s->V = cfg->nvar;
+  s->np = npatch;
+  int maxl = 0;
+  for (int i = 0; i < npatch; ++i) if (patches[i].level > maxl) maxl = patches[i].level;
+  s->nlev = maxl + 1;
+  s->lev_first = (int*)calloc(s->nlev, sizeof(int));
+  s->lev_count = (int*)calloc(s->nlev, sizeof(int));
+  s->P = (opatch*)calloc(npatch, sizeof(opatch));
+  /* keep the caller's patch order (ids are positions); require it sorted by level */
+  for (int i = 0; i < npatch; ++i) {
+    if (i > 0 && patches[i].level < patches[i - 1].level) {
+      snprintf(g_err, sizeof g_err, "patches must be sorted by level");
+      free_sim(s);
+      return NULL;
+    }
+    s->lev_count[patches[i].level]++;
+  }
+  for (int l = 1; l < s->nlev; ++l) s->lev_first[l] = s->lev_first[l - 1] + s->lev_count[l - 1];
+  for (int d = 0; d < 3; ++d) s->dx0[d] = (cfg->domain_hi[d] - cfg->domain_lo[d]) / cfg->base_n[d];
+  for (int i = 0; i < npatch; ++i) {
+    opatch* p = &s->P[i];
+    p->level = patches[i].level;
+    for (int d = 0; d < 3; ++d) { p->lo[d] = patches[i].lo[d]; p->n[d] = patches[i].n[d]; p->m[d] = p->n[d] + 2 * GH; }
+    p->ncell_g = (size_t)p->m[0] * p->m[1] * p->m[2];
+    size_t sz = p->ncell_g * s->V;
+    p->U = (double*)malloc(sz * sizeof(double));
+    p->U1 = (double*)malloc(sz * sizeof(double));
+    for (size_t k = 0; k < sz; ++k) { p->U[k] = NAN; p->U1[k] = NAN; }   /* unused ghosts stay NaN */
+    p->Uold = (double*)calloc((size_t)p->n[0] * p->n[1] * p->n[2] * s->V, sizeof(double));
+    for (int d = 0; d < 3; ++d) p->F[d] = (double*)calloc(fsize(p, d) * s->V, sizeof(double));
+  }
+  /* candidate lists */
+  for (int i = 0; i < npatch; ++i) {
+    opatch* p = &s->P[i];
+    int l = p->level;
+    p->sib = (int*)malloc(sizeof(int) * s->lev_count[l]);
+    for (int q = s->lev_first[l]; q < s->lev_first[l] + s->lev_count[l]; ++q) {
+      opatch* o = &s->P[q];
+      int ok = 1;
+      for (int d = 0; d < 3 && ok; ++d)
+        ok = axis_touch(s, l, d, p->lo[d] - GH, p->lo[d] + p->n[d] + GH, o->lo[d], o->lo[d] + o->n[d]);
+      if (ok) p->sib[p->nsib++] = q;
+    }
+    if (l > 0) {
+      p->par = (int*)malloc(sizeof(int) * s->lev_count[l - 1]);
+      for (int q = s->lev_first[l - 1]; q < s->lev_first[l - 1] + s->lev_count[l - 1]; ++q) {
+        opatch* o = &s->P[q];
+        int ok = 1;
+        for (int d = 0; d < 3 && ok; ++d)
+          ok = axis_touch(s, l - 1, d, p->lo[d] / 2 - 3, (p->lo[d] + p->n[d]) / 2 + 3, o->lo[d], o->lo[d] + o->n[d]);
+        if (ok) p->par[p->npar++] = q;
+      }
+    }
+  }
+  /* covered masks */
+  for (int l = 0; l + 1 < s->nlev; ++l)
+    for (int i = s->lev_first[l]; i < s->lev_first[l] + s->lev_count[l]; ++i) {
+      opatch* p = &s->P[i];
+      size_t nc = (size_t)p->n[0] * p->n[1] * p->n[2];
+      p->covered = (unsigned char*)calloc(nc, 1);
+      for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+          for (int ii = 0; ii < p->n[0]; ++ii) {
+            int child[3] = {2 * (p->lo[0] + ii), 2 * (p->lo[1] + j), 2 * (p->lo[2] + k)};
+            for (int q = s->lev_first[l + 1]; q < s->lev_first[l + 1] + s->lev_count[l + 1]; ++q)
+              if (contains(&s->P[q], child)) { p->covered[((size_t)k * p->n[1] + j) * p->n[0] + ii] = 1; break; }
+          }
+    }
+  s->reg = (oreg**)calloc(s->nlev, sizeof(oreg*));
+  s->nreg = (int*)calloc(s->nlev, sizeof(int));
+  for (int l = 1; l < s->nlev; ++l)
+    if (build_registers(s, l) != 0) { free_sim(s); return NULL; }
+  s->ch_used = cfg->ch;
+  return s;
+}
+
+int orc_set_cons(orc_sim* s, int pi, const double* u) {
+  if (pi < 0 || pi >= s->np) return -1;
+  opatch* p = &s->P[pi];
+  size_t nc = (size_t)p->n[0] * p->n[1] * p->n[2];
+  for (int v = 0; v < s->V; ++v)
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i)
+          p->U[v * p->ncell_g + gidx(p, i, j, k)] = u[v * nc + ((size_t)k * p->n[1] + j) * p->n[0] + i];
+  return 0;
+}
+
+int orc_set_prim(orc_sim* s, int pi, const double* w) {
+  if (pi < 0 || pi >= s->np) return -1;
+  opatch* p = &s->P[pi];
+  size_t nc = (size_t)p->n[0] * p->n[1] * p->n[2];
+  double* u = (double*)malloc(nc * s->V * sizeof(double));
+  double wc[MAXV], uc[MAXV];
+  for (size_t c = 0; c < nc; ++c) {
+    for (int v = 0; v < s->V; ++v) wc[v] = w[v * nc + c];
+    orc_prim_to_cons(&s->cfg, wc, uc);
+    for (int v = 0; v < s->V; ++v) u[v * nc + c] = uc[v];
+  }
+  orc_set_cons(s, pi, u);
+  free(u);
+  return 0;
+}
+
+int orc_get_cons(const orc_sim* s, int pi, double* u) {
+  if (pi < 0 || pi >= s->np) return -1;
+  const opatch* p = &s->P[pi];
+  size_t nc = (size_t)p->n[0] * p->n[1] * p->n[2];
+  for (int v = 0; v < s->V; ++v)
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i)
+          u[v * nc + ((size_t)k * p->n[1] + j) * p->n[0] + i] = p->U[v * p->ncell_g + gidx(p, i, j, k)];
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ghost zones (Sec. 3: each grid is an IBVP; Sec. 5.2 ghost cells)          */
+/* ------------------------------------------------------------------------ */
+
+/* Conserved state of coarse cell C on level lc at time fraction alpha of the
+ * coarse step: (1 - alpha) U_old + alpha U_new (linear in time).  Cells outside
+ * the domain map through the boundary condition (periodic wrap, outflow clamp). */
+static int coarse_value(orc_sim* s, const opatch* fine, int lc, const int* Cin, double alpha, double* out) {
+  int C[3];
+  for (int d = 0; d < 3; ++d) {
+    int N = level_n(s, lc, d);
+    C[d] = Cin[d];
+    if (C[d] < 0 || C[d] >= N) {
+      if (periodic(s, d)) C[d] = ((C[d] % N) + N) % N;
+      else C[d] = C[d] < 0 ? 0 : N - 1;
+    }
+  }
+  int q = find_in(s, fine->par, fine->npar, C);
+  if (q < 0) return -1;
+  const opatch* o = &s->P[q];
+  size_t nc = (size_t)o->n[0] * o->n[1] * o->n[2];
+  size_t ii = ((size_t)(C[2] - o->lo[2]) * o->n[1] + (C[1] - o->lo[1])) * o->n[0] + (C[0] - o->lo[0]);
+  size_t gi = gidx(o, C[0] - o->lo[0], C[1] - o->lo[1], C[2] - o->lo[2]);
+  for (int v = 0; v < s->V; ++v)
+    out[v] = (1.0 - alpha) * o->Uold[v * nc + ii] + alpha * o->U[v * o->ncell_g + gi];
+  return 0;
+}
+
+/* Coarse-to-fine prolongation (paper-silent reading): child = parent +
+ * sum_d (+-1/4) minmod(U_{C+1} - U_C, U_C - U_{C-1}) in the conserved variables.
+ * The children of a coarse cell average to the parent value. */
+static int prolong(orc_sim* s, const opatch* fine, const int* g, double alpha, double* out) {
+  int lc = fine->level - 1;
+  int C[3] = {g[0] >> 1, g[1] >> 1, g[2] >> 1};
+  double Uc[MAXV], Up[MAXV], Um[MAXV], sl[3][MAXV];
+  if (coarse_value(s, fine, lc, C, alpha, Uc)) return -1;
+  for (int d = 0; d < 3; ++d) {
+    int Cp[3] = {C[0], C[1], C[2]}, Cm[3] = {C[0], C[1], C[2]};
+    Cp[d] += 1; Cm[d] -= 1;
+    if (coarse_value(s, fine, lc, Cp, alpha, Up)) return -1;
+    if (coarse_value(s, fine, lc, Cm, alpha, Um)) return -1;
+    for (int v = 0; v < s->V; ++v) sl[d][v] = orc_minmod2(Up[v] - Uc[v], Uc[v] - Um[v]);
+  }
+  for (int v = 0; v < s->V; ++v) {
+    double val = Uc[v];
+    for (int d = 0; d < 3; ++d) {
+      double sg = (g[d] & 1) ? 1.0 : -1.0;
+      val = val + sg * 0.25 * sl[d][v];
+    }
+    out[v] = val;
+  }
+  return 0;
+}
+
+/* Fill the face ghost cells (only the cells a directional stencil uses) of
+ * patch pi in the state array `which` (0: U, 1: U1).  Order of precedence:
+ * physical outflow boundary, same-level (or periodic-image) sibling, parent. */
+static int fill_ghosts_patch(orc_sim* s, int pi, int which, double alpha) {
+  opatch* p = &s->P[pi];
+  const int V = s->V, l = p->level;
+  double* X = which ? p->U1 : p->U;
+  for (int dd = 0; dd < 3; ++dd) {
+    int a = (dd + 1) % 3, b = (dd + 2) % 3;
+    for (int side = 0; side < 2; ++side)
+      for (int gg = 0; gg < GH; ++gg)
+        for (int jb = 0; jb < p->n[b]; ++jb)
+          for (int ja = 0; ja < p->n[a]; ++ja) {
+            int loc[3];
+            loc[dd] = side ? p->n[dd] + gg : -1 - gg;
+            loc[a] = ja; loc[b] = jb;
+            int g[3] = {p->lo[0] + loc[0], p->lo[1] + loc[1], p->lo[2] + loc[2]};
+            size_t dst = gidx(p, loc[0], loc[1], loc[2]);
+            int N = level_n(s, l, dd);
+            if (g[dd] < 0 || g[dd] >= N) {
+              if (!periodic(s, dd)) {              /* outflow: zero-gradient copy */
+                int src[3] = {loc[0], loc[1], loc[2]};
+                src[dd] = side ? p->n[dd] - 1 : 0;
+                size_t si = gidx(p, src[0], src[1], src[2]);
+                for (int v = 0; v < V; ++v) X[v * p->ncell_g + dst] = X[v * p->ncell_g + si];
+                continue;
+              }
+              g[dd] = ((g[dd] % N) + N) % N;
+            }
+            int q = find_in(s, p->sib, p->nsib, g);
+            if (q >= 0) {
+              opatch* o = &s->P[q];
+              double* Y = which ? o->U1 : o->U;
+              size_t si = gidx(o, g[0] - o->lo[0], g[1] - o->lo[1], g[2] - o->lo[2]);
+              for (int v = 0; v < V; ++v) X[v * p->ncell_g + dst] = Y[v * o->ncell_g + si];
+              continue;
+            }
+            if (l == 0) {
+              snprintf(g_err, sizeof g_err, "level-0 ghost cell not covered (patch %d)", pi);
+              return -1;
+            }
+            double val[MAXV];
+            if (prolong(s, p, g, alpha, val)) {
+              snprintf(g_err, sizeof g_err, "prolongation source missing (patch %d)", pi);
+              return -1;
+            }
+            for (int v = 0; v < V; ++v) X[v * p->ncell_g + dst] = val[v];
+          }
+  }
+  return 0;
+}
+
+static int fill_ghosts_level(orc_sim* s, int l, int which, double alpha) {
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+  for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi)
+    bad |= (fill_ghosts_patch(s, pi, which, alpha) != 0);
+  return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MOL operator L(U) and one Euler stage (Sec. 4 MOL, Sec. 5.1 routine)      */
+/* ------------------------------------------------------------------------ */
+
+/* Face fluxes of patch p from state X (with filled ghosts): for every face
+ * along every direction reconstruct left/right states from the four cells
+ * along that direction, then apply the interface flux. */
+static void patch_fluxes(orc_sim* s, opatch* p, const double* X, double ch) {
+  const int V = s->V;
+  double r4[4][MAXV], col[4], rl[MAXV], rr[MAXV], Ftmp[MAXV], uc[MAXV];
+  for (int d = 0; d < 3; ++d) {
+    int nf0 = p->n[0] + (d == 0), nf1 = p->n[1] + (d == 1), nf2 = p->n[2] + (d == 2);
+    for (int k = 0; k < nf2; ++k)
+      for (int j = 0; j < nf1; ++j)
+        for (int i = 0; i < nf0; ++i) {
+          for (int c = 0; c < 4; ++c) {            /* cells f-2, f-1, f, f+1 along d */
+            int q[3] = {i, j, k};
+            q[d] += c - 2;
+            size_t gi = gidx(p, q[0], q[1], q[2]);
+            for (int v = 0; v < V; ++v) uc[v] = X[v * p->ncell_g + gi];
+            cons_to_rec(&s->cfg, uc, r4[c]);
+          }
+          for (int v = 0; v < V; ++v) {
+            for (int c = 0; c < 4; ++c) col[c] = r4[c][v];
+            orc_plm_face(&s->cfg, col, &rl[v], &rr[v]);
+          }
+          riemann_rec(&s->cfg, rl, rr, d, ch, Ftmp);
+          size_t fi = fidx(p, d, i, j, k);
+          size_t fs = fsize(p, d);
+          for (int v = 0; v < V; ++v) p->F[d][v * fs + fi] = Ftmp[v];
+        }
+  }
+}
+
+/* out = in + dt L(in), L(U) = -sum_d (F_{+1/2} - F_{-1/2}) / dx_d  (Sec. 4 MOL). */
+static void patch_update(orc_sim* s, opatch* p, const double* in, double* out, double dt, const double* dx) {
+  const int V = s->V;
+  size_t fs0 = fsize(p, 0), fs1 = fsize(p, 1), fs2 = fsize(p, 2);
+  for (int v = 0; v < V; ++v)
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i) {
+          double Lx = (p->F[0][v * fs0 + fidx(p, 0, i + 1, j, k)] - p->F[0][v * fs0 + fidx(p, 0, i, j, k)]) / dx[0];
+          double Ly = (p->F[1][v * fs1 + fidx(p, 1, i, j + 1, k)] - p->F[1][v * fs1 + fidx(p, 1, i, j, k)]) / dx[1];
+          double Lz = (p->F[2][v * fs2 + fidx(p, 2, i, j, k + 1)] - p->F[2][v * fs2 + fidx(p, 2, i, j, k)]) / dx[2];
+          double L = -(Lx + Ly + Lz);
+          size_t gi = v * p->ncell_g + gidx(p, i, j, k);
+          out[gi] = in[gi] + dt * L;
+        }
+}
+
+/* Register accumulation after a stage of level l (Berger-Colella refluxing):
+ * coarse side of level l+1 registers and fine side of level l registers.  The
+ * effective RK2 flux over a step is 1/2 (F(U^n) + F(U^1)). */
+static void accumulate_registers(orc_sim* s, int l, double dt) {
+  const int V = s->V;
+  if (l + 1 < s->nlev) {
+    for (int e = 0; e < s->nreg[l + 1]; ++e) {
+      oreg* r = &s->reg[l + 1][e];
+      opatch* c = &s->P[r->cpatch];
+      int f[3] = {r->cidx[0], r->cidx[1], r->cidx[2]};
+      f[r->d] = r->cface;
+      size_t fs = fsize(c, r->d), fi = fidx(c, r->d, f[0], f[1], f[2]);
+      for (int v = 0; v < V; ++v) r->Rc[v] += 0.5 * dt * c->F[r->d][v * fs + fi];
+    }
+  }
+  if (l > 0) {
+    for (int e = 0; e < s->nreg[l]; ++e) {
+      oreg* r = &s->reg[l][e];
+      opatch* p = &s->P[r->fpatch];
+      int t1 = (r->d + 1) % 3, t2 = (r->d + 2) % 3;
+      size_t fs = fsize(p, r->d);
+      for (int v = 0; v < V; ++v) {
+        double q[2][2];
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) {
+            int f[3] = {r->fface[0], r->fface[1], r->fface[2]};
+            f[t1] += a; f[t2] += b;
+            q[b][a] = p->F[r->d][v * fs + fidx(p, r->d, f[0], f[1], f[2])];
+          }
+        double sum = (q[0][0] + q[0][1]) + (q[1][0] + q[1][1]);
+        r->Rf[v] += 0.5 * dt * (0.25 * sum);
+      }
+    }
+  }
+}
+
+/* Restriction: coarse covered cell = 1/8 of the pairwise sum of its children
+ * (x pairs, then y, then z). */
+static void restrict_level(orc_sim* s, int lf) {
+  const int V = s->V;
+  int lc = lf - 1;
+#pragma omp parallel for schedule(dynamic)
+  for (int ci = s->lev_first[lc]; ci < s->lev_first[lc] + s->lev_count[lc]; ++ci) {
+    opatch* c = &s->P[ci];
+    for (int k = 0; k < c->n[2]; ++k)
+      for (int j = 0; j < c->n[1]; ++j)
+        for (int i = 0; i < c->n[0]; ++i) {
+          if (!c->covered[((size_t)k * c->n[1] + j) * c->n[0] + i]) continue;
+          int ch0[3] = {2 * (c->lo[0] + i), 2 * (c->lo[1] + j), 2 * (c->lo[2] + k)};
+          int q = -1;
+          for (int f = s->lev_first[lf]; f < s->lev_first[lf] + s->lev_count[lf]; ++f)
+            if (contains(&s->P[f], ch0)) { q = f; break; }
+          opatch* fp = &s->P[q];
+          int b0 = ch0[0] - fp->lo[0], b1 = ch0[1] - fp->lo[1], b2 = ch0[2] - fp->lo[2];
+          for (int v = 0; v < V; ++v) {
+            const double* Y = fp->U + v * fp->ncell_g;
+            double zs[2];
+            for (int dz = 0; dz < 2; ++dz) {
+              double ys[2];
+              for (int dy = 0; dy < 2; ++dy)
+                ys[dy] = Y[gidx(fp, b0, b1 + dy, b2 + dz)] + Y[gidx(fp, b0 + 1, b1 + dy, b2 + dz)];
+              zs[dz] = ys[0] + ys[1];
+            }
+            c->U[v * c->ncell_g + gidx(c, i, j, k)] = 0.125 * (zs[0] + zs[1]);
+          }
+        }
+  }
+}
+
+static void reflux_level(orc_sim* s, int lf) {
+  const int V = s->V;
+  for (int e = 0; e < s->nreg[lf]; ++e) {
+    oreg* r = &s->reg[lf][e];
+    opatch* c = &s->P[r->cpatch];
+    double dxc = s->dx0[r->d] / (double)(1 << (lf - 1));
+    size_t gi = gidx(c, r->cidx[0], r->cidx[1], r->cidx[2]);
+    for (int v = 0; v < V; ++v) {
+      double delta = r->Rf[v] - r->Rc[v];
+      c->U[v * c->ncell_g + gi] = c->U[v * c->ncell_g + gi] - r->cside * delta / dxc;
+    }
+  }
+}
+
+static void save_old_level(orc_sim* s, int l);
+
+/* Advance level l by dt from time fraction base of its parent's step
+ * (alpha0 = 0 for the first substep, 0.5 for the second). */
+static int advance_level(orc_sim* s, int l, double dt, double alpha0) {
+  const int V = s->V;
+  double dx[3];
+  for (int d = 0; d < 3; ++d) dx[d] = s->dx0[d] / (double)(1 << l);
+  int has_children = (l + 1 < s->nlev);
+  if (has_children) {
+    save_old_level(s, l);
+    for (int e = 0; e < s->nreg[l + 1]; ++e)
+      for (int v = 0; v < V; ++v) { s->reg[l + 1][e].Rc[v] = 0.0; s->reg[l + 1][e].Rf[v] = 0.0; }
+  }
+  double ch = s->ch_used;
+  /* stage 1: U1 = U^n + dt L(U^n), ghosts at the start of the step */
+  if (fill_ghosts_level(s, l, 0, alpha0)) return -1;
+#pragma omp parallel for schedule(dynamic)
+  for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi) {
+    opatch* p = &s->P[pi];
+    patch_fluxes(s, p, p->U, ch);
+    patch_update(s, p, p->U, p->U1, dt, dx);
+  }
+  accumulate_registers(s, l, dt);
+  /* stage 2: U2 = U1 + dt L(U1), ghosts at the end of the step; U^{n+1} = U^n/2 + U2/2 */
+  if (fill_ghosts_level(s, l, 1, alpha0 + 0.5)) return -1;
+#pragma omp parallel for schedule(dynamic)
+  for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi) {
+    opatch* p = &s->P[pi];
+    patch_fluxes(s, p, p->U1, ch);
+    size_t sz = p->ncell_g * V;
+    double* U2 = (double*)malloc(sz * sizeof(double));
+    memcpy(U2, p->U1, sz * sizeof(double));
+    patch_update(s, p, p->U1, U2, dt, dx);
+    for (int v = 0; v < V; ++v)
+      for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+          for (int i = 0; i < p->n[0]; ++i) {
+            size_t gi = v * p->ncell_g + gidx(p, i, j, k);
+            p->U[gi] = 0.5 * p->U[gi] + 0.5 * U2[gi];
+          }
+    free(U2);
+  }
+  accumulate_registers(s, l, dt);
+  if (has_children) {
+    if (advance_level(s, l + 1, 0.5 * dt, 0.0)) return -1;
+    if (advance_level(s, l + 1, 0.5 * dt, 0.5)) return -1;
+    restrict_level(s, l + 1);
+    reflux_level(s, l + 1);
+  }
+  return 0;
+}
+
+/* Per-cell CFL rate sum_d (|v_d| + c_d) / dx0_d.  A level-l cell has dx_l =
+ * dx0 / 2^l and dt_l = dt0 / 2^l, so every level shares the same Courant
+ * number when dt0 = cfl / max over all cells of this rate. */
+static void cell_rates(orc_sim* s, double* rate_max, double* speed_max) {
+  double rm = 0.0, sm = 0.0;
+  for (int pi = 0; pi < s->np; ++pi) {
+    opatch* p = &s->P[pi];
+    double u[MAXV], r[MAXV];
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i) {
+          size_t gi = gidx(p, i, j, k);
+          for (int v = 0; v < s->V; ++v) u[v] = p->U[v * p->ncell_g + gi];
+          cons_to_rec(&s->cfg, u, r);
+          double rate = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            double sp = fabs(r[1 + d]) + signal_speed(&s->cfg, r, d);
+            rate += sp / s->dx0[d];
+            if (sp > sm) sm = sp;
+          }
+          if (rate > rm) rm = rate;
+        }
+  }
+  *rate_max = rm;
+  *speed_max = sm;
+}
+
+double orc_cfl_dt(orc_sim* s) {
+  double rm, sm;
+  cell_rates(s, &rm, &sm);
+  return s->cfg.cfl / rm;
+}
+
+int orc_step(orc_sim* s, double dt, double* dt_used) {
+  double rm, sm;
+  cell_rates(s, &rm, &sm);
+  if (dt <= 0.0) dt = s->cfg.cfl / rm;
+  if (s->V == 9) s->ch_used = (s->cfg.ch > 0.0) ? s->cfg.ch : sm;
+  if (dt_used) *dt_used = dt;
+  if (s->cfg.nthreads > 0) {
+#ifdef _OPENMP
+    omp_set_num_threads(s->cfg.nthreads);
+#endif
+  }
+  return advance_level(s, 0, dt, 0.0);
+}
+
+double orc_last_ch(const orc_sim* s) { return s->ch_used; }
+
+static void save_old_level(orc_sim* s, int l) {
+  for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi) {
+    opatch* p = &s->P[pi];
+    size_t nc = (size_t)p->n[0] * p->n[1] * p->n[2];
+    for (int v = 0; v < s->V; ++v)
+      for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+          for (int i = 0; i < p->n[0]; ++i)
+            p->Uold[v * nc + ((size_t)k * p->n[1] + j) * p->n[0] + i] = p->U[v * p->ncell_g + gidx(p, i, j, k)];
+  }
+}
+
+int orc_save_old(orc_sim* s, int level) {
+  if (level < 0 || level >= s->nlev) return -1;
+  save_old_level(s, level);
+  return 0;
+}
+
+int orc_fill_ghosts(orc_sim* s, int level, int which, double alpha) {
+  if (level < 0 || level >= s->nlev) return -1;
+  return fill_ghosts_level(s, level, which, alpha);
+}
+
+int orc_get_ghosted(const orc_sim* s, int pi, int which, double* out) {
+  if (pi < 0 || pi >= s->np) return -1;
+  const opatch* p = &s->P[pi];
+  memcpy(out, which ? p->U1 : p->U, p->ncell_g * s->V * sizeof(double));
+  return 0;
+}
+
+void orc_totals(const orc_sim* s, double* out) {
+  for (int v = 0; v < s->V; ++v) out[v] = 0.0;
+  for (int pi = 0; pi < s->np; ++pi) {
+    const opatch* p = &s->P[pi];
+    double vol = 1.0;
+    for (int d = 0; d < 3; ++d) vol *= s->dx0[d] / (double)(1 << p->level);
+    for (int v = 0; v < s->V; ++v) {
+      double acc = 0.0;
+      for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+          for (int i = 0; i < p->n[0]; ++i) {
+            if (p->covered && p->covered[((size_t)k * p->n[1] + j) * p->n[0] + i]) continue;
+            acc += p->U[v * p->ncell_g + gidx(p, i, j, k)];
+          }
+      out[v] += acc * vol;
+    }
+  }
+}

@@ -1,0 +1,92 @@
+/*
+ * amr_oracle.h -- plain FP64 CPU oracle for the per-patch finite-volume update
+ * of block-structured AMR compressible Euler / GLM-MHD
+ * (Wang, Abel & Kaehler, "Adaptive Mesh Fluid Simulations on GPU").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code
+ * with the CUDA path: its own geometry, ghost fill, reconstruction, Riemann
+ * solver, time integrator, refluxing and restriction are written here from the
+ * paper (Sec. 3, Sec. 4 Eqs. for U, F, EOS, MOL, RK2, PLM, minmod, HLL;
+ * Sec. 5.1 three-line RK2 form; Sec. 7.1 GLM-MHD).
+ *
+ * Conventions of every state array that crosses this interface:
+ *   interior cells only, FP64, layout [var][z][y][x] (x fastest).
+ * Hydro variables (nvar = 5):  U = (rho, rho vx, rho vy, rho vz, rho E),
+ *                              W = (rho, vx, vy, vz, p)
+ * GLM-MHD (nvar = 9):          U = (rho, rho v, rho E + B^2/2, Bx, By, Bz, psi),
+ *                              W = (rho, vx, vy, vz, p, Bx, By, Bz, psi)
+ */
+#ifndef AMR_ORACLE_H
+#define AMR_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_HLL = 0, ORC_LLF = 1 };
+enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1 };
+
+typedef struct {
+  int nvar;           /* 5 (Euler) or 9 (GLM-MHD) */
+  int riemann;        /* ORC_HLL (two-wave HLL) or ORC_LLF (the printed Sec. 4 flux) */
+  int plm_literal;    /* 1: add the full limited slope at faces (printed PLM), 0: half slope */
+  double gamma;
+  double theta;       /* generalised-minmod parameter, 0 <= theta <= 2 */
+  double cfl;
+  int base_n[3];      /* level-0 cells per axis */
+  double domain_lo[3], domain_hi[3];
+  int bc[6];          /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
+  int max_level;
+  double ch;          /* GLM cleaning speed; <= 0: max signal speed at the start of each coarse step */
+  int nthreads;       /* OpenMP threads over patches; <= 0: library default */
+} orc_config;
+
+typedef struct { int level; int lo[3]; int n[3]; } orc_patch;
+
+typedef struct orc_sim orc_sim;
+
+/* Create a simulation; returns NULL on invalid input (message in orc_error()). */
+orc_sim* orc_create(const orc_config* cfg, int npatch, const orc_patch* patches);
+const char* orc_error(void);
+void orc_destroy(orc_sim* s);
+
+/* Set one patch from primitive W or conserved U (interior, [nvar][z][y][x]). */
+int orc_set_prim(orc_sim* s, int patch, const double* w);
+int orc_set_cons(orc_sim* s, int patch, const double* u);
+int orc_get_cons(const orc_sim* s, int patch, double* u);
+
+/* CFL step size of the current state (max over all cells of all levels). */
+double orc_cfl_dt(orc_sim* s);
+/* One coarse step of size dt (dt <= 0: CFL step).  Returns 0 or -1. */
+int orc_step(orc_sim* s, double dt, double* dt_used);
+/* Sum of U * cell volume over leaf (uncovered) cells, nvar values. */
+void orc_totals(const orc_sim* s, double* out);
+/* Cleaning speed used by the last step (MHD). */
+double orc_last_ch(const orc_sim* s);
+
+/* ---- test hooks: fill the face ghosts of one level (state 0: U, 1: U1) at
+ * parent-time fraction alpha, and read a patch's full ghosted array
+ * [nvar][n2+4][n1+4][n0+4] (edge/corner ghosts are never filled: NaN) ---- */
+int orc_fill_ghosts(orc_sim* s, int level, int which, double alpha);
+int orc_get_ghosted(const orc_sim* s, int patch, int which, double* out);
+/* Save the current state of a level as the "old" time level used by
+ * prolongation (done automatically at the start of every coarse-level step). */
+int orc_save_old(orc_sim* s, int level);
+
+/* ---- point functions, exposed for unit pins ---- */
+double orc_minmod3(double a, double b, double c);
+double orc_minmod2(double a, double b);
+/* PLM left/right states at face i-1/2 from four cell values u[0..3] = u_{i-2..i+1}. */
+void orc_plm_face(const orc_config* cfg, const double* u4, double* ul, double* ur);
+/* Physical flux of primitive state w along dir (0,1,2); ch used for MHD psi/B_d entries. */
+void orc_phys_flux(const orc_config* cfg, const double* w, int dir, double ch, double* f);
+void orc_prim_to_cons(const orc_config* cfg, const double* w, double* u);
+void orc_cons_to_prim(const orc_config* cfg, const double* u, double* w);
+/* Interface flux from primitive left/right states along dir. */
+void orc_riemann(const orc_config* cfg, const double* wl, const double* wr, int dir, double ch, double* f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,230 @@
+"""Pins of the oracle's AMR machinery (ghost fill, prolongation, time
+interpolation, restriction, refluxing, subcycling) and of its GLM-MHD solver.
+No GPU needed."""
+import math
+
+import numpy as np
+import pytest
+
+import amr_inputs as ai
+import oracle as orc
+import riemann_exact as rex
+
+P, O = ai.PERIODIC, ai.OUTFLOW
+
+
+def two_level(base=16, fine_lo=8, fine_hi=24, tile=8):
+    patches = ai.uniform_patches((base,) * 3, (tile,) * 3)
+    for z in range(fine_lo, fine_hi, tile):
+        for y in range(fine_lo, fine_hi, tile):
+            for x in range(fine_lo, fine_hi, tile):
+                patches.append(ai.Patch(1, (x, y, z), (tile,) * 3))
+    return patches
+
+
+def three_level_seeded(seed=11):
+    """base 32^3 tiled by seeded 8..16 patches; L1 = centred 32^3 cube, L2 = centred 32^3 cube."""
+    return ai.nested_cubes(32, (32, 32), seed, pmin=8, pmax=16)
+
+
+def _linear_field(problem, coef=(0.05, 0.1, -0.05)):
+    for p, w in zip(problem.patches, problem.prim):
+        z, y, x = ai._centres(p, problem.base_n, problem.domain_lo, problem.domain_hi)
+        w[0] = np.broadcast_to(1.0 + coef[0] * x + coef[1] * y + coef[2] * z, w.shape[1:])
+    return problem
+
+
+@pytest.mark.parametrize("bc", [P, O])
+def test_uniform_state_preserved_bitwise_on_amr(bc):
+    pb = ai.uniform(two_level(), (16,) * 3, bc=(bc,) * 6)
+    o = orc.Oracle(pb)
+    u0 = o.all_cons()
+    for _ in range(2):
+        o.step(0.01)
+    for a, b in zip(u0, o.all_cons()):
+        assert np.array_equal(a, b)
+
+
+def test_prolongation_of_linear_data_is_exact():
+    """Every face ghost of the fine level (sibling copies and prolonged cells alike)
+    equals the linear field at its centre when the parent data are linear."""
+    pb = _linear_field(ai.uniform(two_level(), (16,) * 3, bc=(O,) * 6, state=(1, 0.3, -0.2, 0.1, 1.0)))
+    o = orc.Oracle(pb)
+    o.save_old(0)
+    o.fill_ghosts(1, 0, 0.0)
+    for i, p in enumerate(pb.patches):
+        if p.level != 1:
+            continue
+        g = o.ghosted(i)
+        dx = 1.0 / 32
+        xs = (np.arange(-2, p.n[0] + 2) + p.lo[0] + 0.5) * dx
+        ys = (np.arange(-2, p.n[1] + 2) + p.lo[1] + 0.5) * dx
+        zs = (np.arange(-2, p.n[2] + 2) + p.lo[2] + 0.5) * dx
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        rho = 1.0 + 0.05 * X + 0.1 * Y - 0.05 * Z
+        face = np.isfinite(g[0])
+        assert face.sum() == p.ncell + 2 * 2 * (p.n[0] * p.n[1] + p.n[1] * p.n[2] + p.n[0] * p.n[2])
+        np.testing.assert_allclose(g[0][face], rho[face], rtol=0, atol=2e-15)
+        np.testing.assert_allclose(g[1][face], 0.3 * rho[face], rtol=0, atol=2e-15)
+
+
+def test_prolongation_interpolates_linearly_in_time():
+    A = (1.0, 0.1, 0.2, -0.3, 0.8)
+    B = (1.5, -0.2, 0.0, 0.1, 1.4)
+    pa = ai.uniform(two_level(), (16,) * 3, bc=(P,) * 6, state=A)
+    pbb = ai.uniform(two_level(), (16,) * 3, bc=(P,) * 6, state=B)
+    o = orc.Oracle(pa)
+    o.save_old(0)                                   # old level-0 state = A
+    lib = orc.lib()
+    for i, p in enumerate(pbb.patches):             # new level-0 state = B
+        if p.level == 0:
+            u = np.ascontiguousarray(np.stack([orc.prim_to_cons(pbb.prim[i][:, 0, 0, 0])[v] *
+                                               np.ones(pbb.prim[i].shape[1:]) for v in range(5)]))
+            lib.orc_set_cons(o._h, i, orc._dp(u))
+    uA, uB = orc.prim_to_cons(A), orc.prim_to_cons(B)
+    for alpha in (0.0, 0.5, 1.0):
+        o.fill_ghosts(1, 0, alpha)
+        want = (1 - alpha) * uA + alpha * uB
+        # a ghost cell of patch (8,8,8) at x = 7 (outside the fine box, in no sibling)
+        idx = next(i for i, p in enumerate(pbb.patches) if p.level == 1 and p.lo == (8, 8, 8))
+        g = o.ghosted(idx)
+        np.testing.assert_array_equal(g[:, 2 + 3, 2 + 3, 1], want)
+
+
+@pytest.mark.parametrize("nvar", [5, 9])
+def test_periodic_amr_conservation_to_roundoff(nvar):
+    """Refluxing + restriction keep every conserved total at round-off on a periodic
+    three-level hierarchy with subcycling."""
+    pb = ai.random_smooth(three_level_seeded(), (32,) * 3, nvar=nvar, seed=5, amp=0.2)
+    o = orc.Oracle(pb, nthreads=8)
+    t0 = o.totals()
+    for _ in range(2):
+        o.step()
+    t1 = o.totals()
+    scale = max(np.abs(t0).max(), 1.0)
+    assert np.all(np.abs(t1 - t0) <= 2e-14 * scale), (t1 - t0)
+
+
+def test_restriction_sets_covered_cells_to_child_average():
+    pb = ai.random_smooth(two_level(), (16,) * 3, seed=9, amp=0.2)
+    o = orc.Oracle(pb)
+    o.step()
+    cons = o.all_cons()
+    for ci, c in enumerate(pb.patches):
+        if c.level != 0:
+            continue
+        for fi, f in enumerate(pb.patches):
+            if f.level != 1:
+                continue
+            lo = [max(c.lo[d], f.lo[d] // 2) for d in range(3)]
+            hi = [min(c.lo[d] + c.n[d], (f.lo[d] + f.n[d]) // 2) for d in range(3)]
+            if any(lo[d] >= hi[d] for d in range(3)):
+                continue
+            cz = cons[ci][:, lo[2] - c.lo[2]:hi[2] - c.lo[2], lo[1] - c.lo[1]:hi[1] - c.lo[1],
+                          lo[0] - c.lo[0]:hi[0] - c.lo[0]]
+            fz = cons[fi][:, 2 * lo[2] - f.lo[2]:2 * hi[2] - f.lo[2], 2 * lo[1] - f.lo[1]:2 * hi[1] - f.lo[1],
+                          2 * lo[0] - f.lo[0]:2 * hi[0] - f.lo[0]]
+            avg = fz.reshape(5, cz.shape[1], 2, cz.shape[2], 2, cz.shape[3], 2).mean(axis=(2, 4, 6))
+            np.testing.assert_allclose(cz, avg, rtol=1e-14, atol=1e-15)
+
+
+def test_amr_sod_error_matches_uniform_fine_grid():
+    """A fine level over the region the waves occupy gives the fine-grid accuracy."""
+    t_end = 0.1
+
+    def l1(o, pb):
+        err = 0.0
+        nb = pb.base_n[0]
+        covered = np.zeros(nb, bool)
+        for p in pb.patches:
+            if p.level == 1:
+                covered[p.lo[0] // 2:(p.lo[0] + p.n[0]) // 2] = True
+        for i, p in enumerate(pb.patches):
+            n = nb << p.level
+            x = (np.arange(p.n[0]) + p.lo[0]) / n
+            er, _, _ = rex.cell_average(x, x + 1 / n, t_end, 0.5, (1, 0, 1, 0.125, 0, 0.1))
+            rho = o.cons(i)[0, 0, 0]
+            keep = np.ones(p.n[0], bool) if p.level == 1 else ~covered[p.lo[0]:p.lo[0] + p.n[0]]
+            err += np.abs(rho - er)[keep].sum() / n
+        return err
+
+    def run(patches, base):
+        pb = ai.sod(n=base[0], ny=1)
+        pb.base_n = base
+        pb.patches = patches
+        pb.prim = ai._fill(patches, base, 5, lambda p, w, x, y, z: (
+            w.__setitem__(0, np.broadcast_to(np.where(x < 0.5, 1.0, 0.125), w.shape[1:])),
+            w.__setitem__(4, np.broadcast_to(np.where(x < 0.5, 1.0, 0.1), w.shape[1:]))))
+        pb.max_level = max(p.level for p in patches)
+        o = orc.Oracle(pb)
+        o.run_to(t_end)
+        return o, pb
+
+    amr = [ai.Patch(0, (0, 0, 0), (64, 2, 2)), ai.Patch(1, (32, 0, 0), (64, 4, 4))]
+    o, pb = run(amr, (64, 2, 2))
+    e_amr = l1(o, pb)
+    o64, pb64 = run([ai.Patch(0, (0, 0, 0), (64, 2, 2))], (64, 2, 2))
+    e64 = l1(o64, pb64)
+    o128, pb128 = run([ai.Patch(0, (0, 0, 0), (128, 2, 2))], (128, 2, 2))
+    e128 = l1(o128, pb128)
+    assert e_amr < 0.8 * e64, (e_amr, e64, e128)
+    assert e_amr < 1.3 * e128, (e_amr, e64, e128)
+
+
+# ---------------------------------------------------------------------------
+# GLM-MHD (Sec. 7)
+# ---------------------------------------------------------------------------
+
+def test_brio_wu_keeps_normal_field_and_psi_exact():
+    pb = ai.brio_wu(n=200)
+    o = orc.Oracle(pb)
+    o.run_to(0.1)
+    u = o.cons(0)
+    assert np.all(u[5] == 0.75)
+    assert np.all(u[8] == 0.0)
+    assert np.all(u[0] > 0.1) and np.all(u[0] < 1.0 + 1e-12)
+    w = o.prim(0)
+    assert np.all(w[4] > 0)
+    # the left and right states far from the waves are untouched
+    assert u[0, 0, 0, 0] == 1.0 and u[0, 0, 0, -1] == 0.125
+
+
+def test_mhd_with_zero_field_reproduces_hydro_run():
+    patches = ai.uniform_patches((16, 16, 16), (8, 8, 8))
+    p5 = ai.random_smooth(patches, (16,) * 3, nvar=5, seed=21)
+    p9 = ai.random_smooth(patches, (16,) * 3, nvar=5, seed=21)
+    p9.nvar = 9
+    p9.prim = [np.concatenate([w, np.zeros((4,) + w.shape[1:])]) for w in p5.prim]
+    o5, o9 = orc.Oracle(p5), orc.Oracle(p9)
+    for _ in range(3):
+        dt = o5.step()
+        o9.step(dt)
+    for a, b in zip(o5.all_cons(), o9.all_cons()):
+        np.testing.assert_allclose(b[:5], a, rtol=1e-13, atol=1e-14)
+        assert np.all(b[5:] == 0.0)
+
+
+def test_cp_alfven_wave_second_order():
+    errs = []
+    for n in (32, 64, 128):
+        pb = ai.cp_alfven(n=n)
+        o = orc.Oracle(pb)
+        o.run_to(1.0)            # one full period: the exact solution is the initial state
+        u = o.cons(0)
+        errs.append(np.abs(u[6, 0, 0] - pb.prim[0][6, 0, 0]).mean() +
+                    np.abs(u[7, 0, 0] - pb.prim[0][7, 0, 0]).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 1.7, (errs, orders)
+
+
+def test_mhd_periodic_conservation_and_cleaning_speed():
+    patches = ai.uniform_patches((16, 16, 16), (8, 8, 8))
+    pb = ai.orszag_tang(N=16, tile=8)
+    o = orc.Oracle(pb)
+    t0 = o.totals()
+    for _ in range(3):
+        o.step()
+    t1 = o.totals()
+    assert np.all(np.abs(t1 - t0) <= 1e-14 * np.abs(t0).max() + 1e-15), (t1 - t0)
+    # cleaning speed = the largest signal speed |v_d| + c_f,d at the step start (> sound + flow)
+    assert o.last_ch() > 1.0
