@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the AMR finite-volume update on GB300.
+
+Workload: 3D Euler, Kelvin-Helmholtz shear layer in a periodic 256^3 box tiled
+by 512 patches of 32^3 (rho 2 / 1, vx +-0.5, p 2.5, seeded v_y noise), gamma
+1.4, PLM (theta 1.5) + HLL + TVD-RK2, CFL 0.4 recomputed on the GPU every step.
+
+One "step" = one full RK2 coarse step of every cell (16.8M cell-updates).
+Headline `value`: batched FP32 path (one launch per kernel, CUDA-graph replay)
+in cell-updates/s, device-timed with CUDA events on the solver's stream.
+Also measured in the same run: the plain per-patch FP64 path and the batched
+FP64 path (same metric), the per-class kernel times (CUDA events around every
+launch) that give the stage kernel's HBM roofline fraction, the end-to-end
+rate through the C ABI with host buffers, and the FP64 CPU oracle on the host
+cores (`cpu_baseline`).
+
+`--impl reference` times the oracle alone (the reference arm of this
+benchmark), each step being one RK2 step of a 128^3 periodic sub-box of the
+same workload.  Under torchrun every rank advances its own replica on its own
+GPU (weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-updates/s and % HBM roofline, batched FP32 vs plain FP64, 1 GB300"
+UNIT = "cell-updates/s"
+N = 256
+TILE = 32
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[3 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        return out
+
+
+def make_solver(pb, precision, batched, graph, stream):
+    from paper_0910_5547_gb300 import Solver
+    return Solver.from_problem(pb, precision=precision, batched=batched, use_graph=graph,
+                               stream=stream.cuda_stream)
+
+
+def timed_steps(torch, s, stream, steps, dt=0.0):
+    """Device time of `steps` coarse steps with CUDA events on the solver's stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        s.step(dt, sync=False)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_baseline(steps=2):
+    """The FP64 oracle as it stands, all host cores, on a bounded sample: `steps`
+    RK2 steps of the full 256^3 / 32^3-patch workload."""
+    import amr_inputs as ai
+    import oracle as orc
+    cores = len(os.sched_getaffinity(0))
+    pb = ai.kelvin_helmholtz(N=N, tile=TILE)
+    o = orc.Oracle(pb, nthreads=cores)
+    t = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    dt = time.perf_counter() - t
+    return {"value": N ** 3 * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} RK2 steps (CFL dt) of the full 256^3 periodic workload, 512 patches of 32^3, "
+                      f"FP64, OpenMP over patches; {dt:.1f} s wall"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import amr_inputs as ai
+    import oracle as orc
+    oracle_cores = len(os.sched_getaffinity(0))
+    n = 128
+    pb = ai.kelvin_helmholtz(N=n, tile=TILE)
+    o = orc.Oracle(pb, nthreads=oracle_cores)
+    for _ in range(args.warmup):
+        o.step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    wall = time.perf_counter() - t
+    value = n ** 3 * args.steps / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "kelvin_helmholtz_periodic_32^3_patches", "sample_box": f"{n}^3",
+                   "full_box": f"{N}^3", "dt": "CFL 0.4 every step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_cores, "kind": "oracle",
+                         "sample": f"each step = one RK2 step of a {n}^3 periodic sub-box of the 256^3 "
+                                   f"Kelvin-Helmholtz workload (same 32^3 patches), FP64 oracle, OpenMP"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    from paper_0910_5547_gb300 import build as B
+    from paper_0910_5547_gb300 import native as NV
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        dist.barrier()
+
+    import amr_inputs as ai
+    pb = ai.kelvin_helmholtz(N=N, tile=TILE)
+    cells = N ** 3
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: batched FP32, graph replay, CFL every step ----
+    s = make_solver(pb, "fp32", True, True, stream)
+    for _ in range(args.warmup):
+        s.step(0.0, sync=False)
+    torch.cuda.synchronize()
+    s.check()
+    n0 = s.launches()
+    barrier()
+    with ClockSampler(local) as clk:
+        elapsed = timed_steps(torch, s, stream, args.steps)
+    barrier()
+    launches = s.launches() - n0
+    s.check()
+    elapsed = max_over_ranks(elapsed)
+    value = ws * cells * args.steps / elapsed
+
+    # ---- per-kernel event timing (eager launches, same solver) ----
+    ksteps = max(3, min(args.steps, 20))
+    NV.amr_set_timing(s.h, True)
+    for _ in range(ksteps):
+        s.step(0.0, sync=False)
+    tm = NV.amr_get_timing(s.h)
+    NV.amr_set_timing(s.h, False)
+    V, W = 5, 4
+    t1, c1 = tm["stage1"]
+    t2, c2 = tm["stage2"]
+    stage_bytes = (2 + 3) * V * W * cells            # stage 1: read U, write U1; stage 2: read U1, U, write U
+    achieved = stage_bytes / ((t1 + t2) / ksteps / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    step_kernel_ms = {k: round(v[0] / ksteps, 4) for k, v in tm.items() if v[1]}
+    s.close()
+
+    # ---- batched FP64 and plain per-patch FP64 ----
+    def rate(precision, batched, graph, steps):
+        so = make_solver(pb, precision, batched, graph, stream)
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        t = timed_steps(torch, so, stream, steps)
+        so.check()
+        so.close()
+        return cells * steps / t
+
+    k64 = max(3, args.steps // 10)
+    fp64_batched = rate("fp64", True, True, k64)
+    fp64_plain = rate("fp64", False, False, k64)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    s = make_solver(pb, "fp32", True, True, stream)
+    nstate = NV.amr_state_size(s.h)
+    h_in = torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy()
+    h_out = torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy()
+    h_in[:] = s.state_all()
+    ke = max(3, min(args.steps, 10))
+    NV.amr_set_state(s.h, h_in, NV.AMR_STATE_CONSERVED)
+    s.step(0.0, sync=False)
+    NV.amr_get_state_all(s.h, h_out)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(ke):
+        NV.amr_set_state(s.h, h_in, NV.AMR_STATE_CONSERVED)
+        s.step(0.0, sync=False)
+        NV.amr_get_state_all(s.h, h_out)
+    e2e_t = max_over_ranks(time.perf_counter() - t)
+    s.close()
+    e2e = {"value": ws * cells * ke / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nstate * 8,
+           "d2h_bytes_per_step": nstate * 8, "steps": ke,
+           "note": "per step: packed FP64 conserved state host->device (pinned), one RK2 step, state device->host"}
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline(args.cpu_steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "kelvin_helmholtz_256^3_periodic_512_patches_32^3", "cells": cells,
+                   "patches": len(pb.patches), "path": "batched FP32, CUDA graph per coarse step",
+                   "dt": "CFL 0.4 recomputed on the GPU every step",
+                   "l2": "working set (U + U1, 0.75 GB FP32) exceeds the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "fp64_batched": {"value": fp64_batched, "unit": UNIT, "steps": k64},
+        "fp64_plain": {"value": fp64_plain, "unit": UNIT, "steps": k64,
+                       "path": "one stage-kernel and one ghost-copy launch per patch, no graph"},
+        "batched_fp32_over_plain_fp64": value / ws / fp64_plain,
+        "roofline": {"bound": "hbm", "kernel": "stage_kernel (stage 1 + stage 2)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_cell_update": (2 + 3) * V * W,
+                     "timed_steps": ksteps},
+        "step_kernel_ms": step_kernel_ms,
+        "cell_update_roofline_frac": value / ws * 100 / (peak * 1e9),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * amr.h -- C ABI of the GB300 (sm_103a) block-structured AMR finite-volume
+ * update: compressible Euler and GLM-MHD on a hierarchy of patches.
+ *
+ * What one coarse step computes (Wang, Abel & Kaehler, "Adaptive Mesh Fluid
+ * Simulations on GPU"):
+ *   - Sec. 4, conservation law U_t + div F = 0 with U = (rho, rho v, rho E),
+ *     the fluxes F^x, F^y, F^z, the ideal-gas EOS p = (gamma-1) rho e;
+ *   - Sec. 4, the method of lines L(U) = -sum_d (F_{+1/2} - F_{-1/2}) / dx_d;
+ *   - Sec. 4, PLM reconstruction of (rho, e, vx, vy, vz) with the generalised
+ *     minmod limiter (theta) and half the limited slope added at each face;
+ *   - Sec. 4, the HLL interface flux (AMR_HLL: two-wave HLL with the signal
+ *     speeds v_d +- c; AMR_LLF: the flux formula as printed, with lambda_0);
+ *   - Sec. 5.1, TVD-RK2 as two identical Euler stages and an average:
+ *     U1 = U + dt L(U), U2 = U1 + dt L(U1), U^{n+1} = U/2 + U2/2;
+ *   - Sec. 3, Berger-Colella recursion: every patch is an initial-boundary
+ *     value problem, level l advances with dt / 2^l (subcycling), ghost zones
+ *     come from same-level siblings, physical boundaries, or the parent level
+ *     (conservative minmod prolongation, linear in time); after the two
+ *     substeps of a level its parent receives the restriction (mean of the 8
+ *     children) and the flux-register correction (refluxing) on coarse cells
+ *     next to the fine patches;
+ *   - Sec. 7.1, the GLM-MHD system (nvar = 9): U = (rho, rho v, rho E + B^2/2,
+ *     B, psi), with the Dedner upwind solve for the (B_d, psi) pair.
+ *
+ * Every entry point returns an amr_status and never throws.  A handle is used
+ * by one host thread at a time.  All device work is ordered on the handle's
+ * CUDA stream (amr_config.cuda_stream, or a stream the library creates).
+ */
+#ifndef AMR_GB300_H
+#define AMR_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amr_handle amr_handle; /* opaque; created by amr_create, freed by amr_destroy */
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_ERR_ARG = -1,          /* invalid argument, size, config, or non-finite input */
+  AMR_ERR_NESTING = -2,      /* patch set violates alignment, overlap, coverage or nesting */
+  AMR_ERR_CUDA = -3,         /* a CUDA runtime call failed (message in amr_last_error) */
+  AMR_ERR_NONPHYSICAL = -4,  /* non-positive density/pressure or NaN produced or supplied */
+  AMR_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
+  AMR_ERR_STATE = -6         /* call out of order (e.g. amr_step before amr_set_patches) */
+} amr_status;
+
+enum { AMR_FP64 = 0, AMR_FP32 = 1 };                 /* bulk precision of state and arithmetic */
+enum { AMR_HLL = 0, AMR_LLF = 1 };                    /* interface flux */
+enum { AMR_BC_OUTFLOW = 0, AMR_BC_PERIODIC = 1 };     /* per domain face */
+enum { AMR_STATE_CONSERVED = 0, AMR_STATE_PRIMITIVE = 1 };
+
+typedef struct {
+  int nvar;              /* 5 (Euler) or 9 (GLM-MHD) */
+  int precision;         /* AMR_FP64 or AMR_FP32; flux registers and totals are FP64 always */
+  int riemann;           /* AMR_HLL or AMR_LLF */
+  double gamma;          /* adiabatic index, > 1 */
+  double theta;          /* generalised minmod parameter, 0 <= theta <= 2 */
+  double cfl;            /* Courant number for the CFL step (0, 1] */
+  int base_n[3];         /* level-0 cells per axis, 1 .. 4096 */
+  double domain_lo[3];   /* physical box */
+  double domain_hi[3];
+  int bc[6];             /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi; periodic faces come in pairs */
+  int max_level;         /* deepest level allowed, 0 .. 12 */
+  int ref_ratio;         /* must be 2 (0 means 2) */
+  double ch;             /* GLM cleaning speed; <= 0: max signal speed at each coarse step start */
+  int batched;           /* 1: one launch per kernel per level; 0: one launch per patch ("plain") */
+  int use_graph;         /* 1: capture a coarse step as a CUDA graph and replay it */
+  void* cuda_stream;     /* cudaStream_t to run on; NULL: the library creates its own */
+} amr_config;
+
+/* One patch: `n` interior cells per axis starting at `lo` in the index space of
+ * its level (level l has base_n * 2^l cells per axis).  Patches of level >= 1
+ * have even lo and even n.  Sizes 2 .. 1024 per axis. */
+typedef struct {
+  int level;
+  int lo[3];
+  int n[3];
+} amr_patch;
+
+/* Fill *cfg with defaults: Euler, FP64, HLL, gamma 1.4, theta 1.5, cfl 0.4,
+ * 32^3 unit box, outflow, batched launches with graphs.  Host only. */
+void amr_default_config(amr_config* cfg);
+
+/* Create a handle (selects device 0 or the current device; no patches yet).
+ * *out receives the handle, or NULL on failure.  AMR_ERR_ARG on a bad config,
+ * AMR_ERR_CUDA if no usable GPU. */
+amr_status amr_create(const amr_config* cfg, amr_handle** out);
+
+/* Host-only check of a patch set against cfg: sizes, alignment, ordering by
+ * level, no same-level overlap, level 0 tiles the domain, proper nesting (each
+ * patch footprint grown by two parent cells is covered by the parent level,
+ * except beyond outflow faces).  No GPU is touched.  On failure returns
+ * AMR_ERR_ARG or AMR_ERR_NESTING and writes a message to msg (may be NULL). */
+amr_status amr_validate_patches(const amr_config* cfg, int npatch, const amr_patch* patches,
+                                char* msg, int msg_len);
+
+/* Install a patch set (validated as above) and its initial state.  state is a
+ * HOST array of npatch pointers; state[i] holds patch i's interior cells, FP64,
+ * layout [nvar][n2][n1][n0] (x fastest); state_kind selects conserved U or
+ * primitive W = (rho, vx, vy, vz, p [, Bx, By, Bz, psi]).  The library copies
+ * the data; the caller keeps ownership.  Allocates all device memory and
+ * rebuilds the per-level launch tables (and the step graph).
+ * AMR_ERR_NONPHYSICAL if a density or pressure is <= 0 or a value is not finite. */
+amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches,
+                           const double* const* state, int state_kind);
+
+/* Replace the state of the installed patches from ONE packed host buffer: all
+ * patches in patch order, each [nvar][n2][n1][n0] FP64 (amr_state_size doubles).
+ * Pinned host memory gives asynchronous copies.  Stream-ordered; no sync. */
+amr_status amr_set_state(amr_handle* h, const double* packed, int state_kind);
+
+/* Number of doubles in the packed state (sum over patches of nvar * cells). */
+long long amr_state_size(const amr_handle* h);
+
+/* Advance one coarse step.  dt > 0: use it; dt <= 0: CFL step from the current
+ * state, dt0 = cfl / max over all cells of sum_d (|v_d| + c_d) / dx0_d (level
+ * l uses dt0 / 2^l).  If dt_used is not NULL the call synchronises and stores
+ * the step taken and reports device-detected non-physical states; with
+ * dt_used == NULL the step is only enqueued. */
+amr_status amr_step(amr_handle* h, double dt, double* dt_used);
+
+/* CFL step of the current state (synchronises). */
+amr_status amr_cfl_dt(amr_handle* h, double* dt);
+
+/* Copy patch `patch`'s interior conserved state, FP64 [nvar][n2][n1][n0], to
+ * the caller's host buffer.  Synchronises. */
+amr_status amr_get_state(amr_handle* h, int patch, double* out);
+
+/* Copy all patches' conserved state into one packed host buffer (layout as in
+ * amr_set_state).  Synchronises. */
+amr_status amr_get_state_all(amr_handle* h, double* packed);
+
+/* out[nvar]: sum over leaf cells (not covered by a finer patch) of U * cell
+ * volume, accumulated in FP64 in a fixed order.  Synchronises. */
+amr_status amr_conserved_totals(amr_handle* h, double* out);
+
+/* Query: device-detected non-physical state since the last call (clears it).
+ * Synchronises.  Returns AMR_OK or AMR_ERR_NONPHYSICAL. */
+amr_status amr_check(amr_handle* h);
+
+/* Kernel classes reported by amr_get_timing. */
+enum {
+  AMR_T_STAGE1 = 0,   /* fused stage kernel, stage 1 */
+  AMR_T_STAGE2 = 1,   /* fused stage kernel, stage 2 (+ RK2 average) */
+  AMR_T_GHOST = 2,    /* sibling / periodic / outflow ghost copies */
+  AMR_T_PARENT = 3,   /* parent-tile gather + prolongation */
+  AMR_T_REG = 4,      /* flux-register accumulation */
+  AMR_T_SYNC = 5,     /* restriction + reflux + old-state copy */
+  AMR_T_SPEED = 6,    /* CFL / signal-speed reduction */
+  AMR_T_NCLASS = 7
+};
+
+/* on != 0: subsequent amr_step calls run eagerly (no graph) with a CUDA event
+ * pair around every launch on the handle's stream; amr_get_timing then
+ * synchronises and returns, per class, the summed milliseconds (ms[c]) and
+ * launch counts (count[c]) since timing was switched on, and resets them. */
+amr_status amr_set_timing(amr_handle* h, int on);
+amr_status amr_get_timing(amr_handle* h, double* ms, long long* count, int nclass);
+
+/* Number of kernels the library launched so far (graph replays count every
+ * kernel node) -- used to report launches in a timed region. */
+long long amr_kernel_launches(const amr_handle* h);
+
+/* Message describing the last failure on this handle ("" if none). */
+const char* amr_last_error(const amr_handle* h);
+
+/* Message of the last failure of amr_create / amr_validate_patches on this thread. */
+const char* amr_global_error(void);
+
+/* Free every device and host resource of the handle (NULL is a no-op). */
+void amr_destroy(amr_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMR_GB300_H */

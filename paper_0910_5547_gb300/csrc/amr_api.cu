@@ -1,0 +1,682 @@
+// amr_api.cu -- the C ABI of include/amr.h: handle lifecycle, device memory,
+// table upload, and the host recursion of one coarse step (Sec. 3,
+// Berger-Colella subcycling; Sec. 5.1 two Euler stages plus the average,
+// fused on the GPU).  A coarse step is enqueued as a fixed launch sequence
+// whose dt is read from device memory, so it can be captured once as a CUDA
+// graph and replayed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/amr.h"
+#include "hierarchy.h"
+#include "kernels.cuh"
+#include "ops.h"
+
+using namespace amr;
+
+namespace {
+
+thread_local std::string g_global_err;
+
+__global__ void begin_speed_kernel(StepParams* params) {
+  params->rate_bits = 0ull;
+  params->speed_bits = 0ull;
+}
+
+// dt0 = cfl / max rate (CFL mode); GLM cleaning speed = fixed value or max signal speed.
+__global__ void finalize_speed_kernel(StepParams* params, double cfl, double ch_fixed, int set_dt) {
+  const double rate = __longlong_as_double((long long)params->rate_bits);
+  const double speed = __longlong_as_double((long long)params->speed_bits);
+  if (set_dt) params->dt0 = cfl / rate;
+  params->ch = ch_fixed > 0.0 ? ch_fixed : speed;
+}
+
+__global__ void set_dt_kernel(StepParams* params, double dt) { params->dt0 = dt; }
+
+struct DevLevel {
+  int nitems = 0, nghost = 0, nprolong = 0, ngather = 0, nrestrict = 0, nreg = 0, nuniq = 0;
+  const StageItem* items = nullptr;
+  const CopySeg* ghost = nullptr;
+  const ProlongBox* prolong = nullptr;
+  const CopySeg* gather = nullptr;
+  const RestrictSeg* restrict_segs = nullptr;
+  const RegFace* regs = nullptr;
+  const int* reflux_first = nullptr;
+  double* R = nullptr;  // registers: [2][nvar][nreg]
+  int64_t arena_begin = 0, arena_end = 0;  // element range of the level's patches
+};
+
+}  // namespace
+
+struct amr_handle {
+  amr_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  OpsBase* ops = nullptr;
+  std::string err;
+  Plan plan;
+  bool ready = false;
+  // device memory
+  void* U = nullptr;
+  void* U1 = nullptr;
+  void* Uold = nullptr;
+  void* tile = nullptr;
+  double* packed = nullptr;
+  double* partial = nullptr;
+  double* totals = nullptr;
+  double* regs = nullptr;
+  unsigned char* tables = nullptr;
+  StepParams* params = nullptr;
+  const PatchDesc* d_desc = nullptr;
+  const ChunkDesc* d_chunks = nullptr;
+  const CoverBox* d_cover = nullptr;
+  const int* d_cover_first = nullptr;
+  const int64_t* d_packed_off = nullptr;
+  const double* d_level_vol = nullptr;
+  int nchunk = 0;
+  std::vector<ChunkDesc> chunks;
+  std::vector<DevLevel> dl;
+  double dx0[3] = {1, 1, 1};
+  // graphs: [0] fixed dt, [1] CFL dt
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_launches[2] = {0, 0};
+  long long launches = 0;
+  long long counting = 0;   // launches counted while enqueueing
+  // optional per-class event timing (eager steps only)
+  bool timing = false;
+  int cur_class = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pairs[AMR_T_NCLASS];  // (start, stop) indices into ev_pool
+  size_t ev_used = 0;
+  double t_ms[AMR_T_NCLASS] = {0};
+  long long t_cnt[AMR_T_NCLASS] = {0};
+};
+
+namespace {
+
+amr_status fail(amr_handle* h, amr_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail(h, AMR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+cudaEvent_t next_event(amr_handle* h, int* idx) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  *idx = (int)h->ev_used;
+  return h->ev_pool[h->ev_used++];
+}
+
+// Launch wrapper: counts the launch and, when timing is on, brackets it with
+// an event pair on the handle's stream.
+#define LK(call)                                                   \
+  do {                                                             \
+    int i0_ = -1, i1_ = -1;                                        \
+    if (h->timing) cudaEventRecord(next_event(h, &i0_), h->stream); \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return e_;                              \
+    if (h->timing) {                                               \
+      cudaEventRecord(next_event(h, &i1_), h->stream);             \
+      h->ev_pairs[h->cur_class].push_back({i0_, i1_});             \
+    }                                                              \
+    h->counting += 1;                                              \
+  } while (0)
+
+void free_device(amr_handle* h) {
+  for (int g = 0; g < 2; ++g) {
+    if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+    h->graph[g] = nullptr;
+  }
+  void* ptrs[] = {h->U, h->U1, h->Uold, h->tile, h->packed, h->partial, h->totals, h->regs, h->tables};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->U = h->U1 = h->Uold = h->tile = nullptr;
+  h->packed = h->partial = h->totals = h->regs = nullptr;
+  h->tables = nullptr;
+  h->dl.clear();
+  h->ready = false;
+}
+
+OpsBase* make_ops(const amr_config& c) {
+  PhysParams p{c.gamma, c.theta, c.ch, c.riemann == AMR_LLF ? 1 : 0};
+  if (c.nvar == 5) return c.precision == AMR_FP32 ? make_ops_f32_euler(p) : make_ops_f64_euler(p);
+  return c.precision == AMR_FP32 ? make_ops_f32_mhd(p) : make_ops_f64_mhd(p);
+}
+
+double level_dx(const amr_handle* h, int l, int d) { return h->dx0[d] / (double)(1 << l); }
+
+// ---- one coarse step -------------------------------------------------------
+
+cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha) {
+  const DevLevel& L = h->dl[l];
+  const LevelPlan& LP = h->plan.levels[l];
+  if (l > 0) {
+    h->cur_class = AMR_T_PARENT;
+    LK(h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->Uold, alpha));
+    LK(h->ops->prolong(h->stream, L.prolong, L.nprolong, h->d_desc, h->tile, arr));
+  }
+  h->cur_class = AMR_T_GHOST;
+  if (h->cfg.batched || L.nghost == 0) {
+    LK(h->ops->ghost_copy(h->stream, L.ghost, L.nghost, h->d_desc, arr));
+  } else {
+    for (int p = 0; p < LP.count; ++p) {
+      int a = LP.ghost_first[p], b = LP.ghost_first[p + 1];
+      if (b > a) LK(h->ops->ghost_copy(h->stream, L.ghost + a, b - a, h->d_desc, arr));
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
+  const DevLevel& L = h->dl[l];
+  const LevelPlan& LP = h->plan.levels[l];
+  double dx[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
+  h->cur_class = s == 1 ? AMR_T_STAGE1 : AMR_T_STAGE2;
+  if (h->cfg.batched) {
+    LK(h->ops->stage(s, h->stream, h->d_desc, L.items, L.nitems, in, out, h->params, l, dx, 0));
+  } else {
+    for (int p = 0; p < LP.count; ++p) {
+      int a = LP.item_first[p], b = LP.item_first[p + 1];
+      if (b > a) LK(h->ops->stage(s, h->stream, h->d_desc, L.items + a, b - a, in, out, h->params, l, dx, 0));
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t advance(amr_handle* h, int l, double alpha0) {
+  const int nlev = (int)h->dl.size();
+  const bool kids = l + 1 < nlev;
+  DevLevel& L = h->dl[l];
+  const size_t es = h->ops->elem_size();
+  if (kids) {
+    cudaError_t e = cudaMemcpyAsync((char*)h->Uold + L.arena_begin * es, (char*)h->U + L.arena_begin * es,
+                                    (L.arena_end - L.arena_begin) * es, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e;
+  if ((e = fill_ghosts(h, l, h->U, alpha0)) != cudaSuccess) return e;
+  if ((e = stage(h, l, 1, h->U, h->U1)) != cudaSuccess) return e;
+  h->cur_class = AMR_T_REG;
+  if (kids) {
+    DevLevel& K = h->dl[l + 1];
+    if (K.nreg) LK(h->ops->reg_coarse(h->stream, K.regs, K.nreg, h->d_desc, h->U, K.R, h->params, l, 1));
+  }
+  if (l > 0 && L.nreg) LK(h->ops->reg_fine(h->stream, L.regs, L.nreg, h->d_desc, h->U, L.R, h->params, l));
+  if ((e = fill_ghosts(h, l, h->U1, alpha0 + 0.5)) != cudaSuccess) return e;
+  if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;
+  h->cur_class = AMR_T_REG;
+  if (kids) {
+    DevLevel& K = h->dl[l + 1];
+    if (K.nreg) LK(h->ops->reg_coarse(h->stream, K.regs, K.nreg, h->d_desc, h->U1, K.R, h->params, l, 2));
+  }
+  if (l > 0 && L.nreg) LK(h->ops->reg_fine(h->stream, L.regs, L.nreg, h->d_desc, h->U1, L.R, h->params, l));
+  if (kids) {
+    if ((e = advance(h, l + 1, 0.0)) != cudaSuccess) return e;
+    if ((e = advance(h, l + 1, 0.5)) != cudaSuccess) return e;
+    DevLevel& K = h->dl[l + 1];
+    h->cur_class = AMR_T_SYNC;
+    LK(h->ops->restrict_(h->stream, K.restrict_segs, K.nrestrict, h->d_desc, h->U));
+    double dxc[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
+    if (K.nuniq) LK(h->ops->reflux(h->stream, K.regs, K.reflux_first, K.nuniq, K.nreg, h->d_desc, K.R, h->U, dxc));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_begin_speed(amr_handle* h) {
+  begin_speed_kernel<<<1, 1, 0, h->stream>>>(h->params);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_speed(amr_handle* h, int set_dt) {
+  finalize_speed_kernel<<<1, 1, 0, h->stream>>>(h->params, h->cfg.cfl, h->cfg.nvar == 9 ? h->cfg.ch : 1.0, set_dt);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_speed(amr_handle* h, int set_dt) {
+  h->cur_class = AMR_T_SPEED;
+  LK(launch_begin_speed(h));
+  LK(h->ops->speed(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, h->params, h->dx0));
+  LK(launch_finalize_speed(h, set_dt));
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_step(amr_handle* h, bool cfl) {
+  cudaError_t e;
+  if (cfl || h->cfg.nvar == 9) {
+    if ((e = enqueue_speed(h, cfl ? 1 : 0)) != cudaSuccess) return e;
+  }
+  return advance(h, 0, 0.0);
+}
+
+amr_status run_step(amr_handle* h, bool cfl) {
+  const int g = cfl ? 1 : 0;
+  if (h->cfg.use_graph && !h->timing) {
+    if (!h->graph[g]) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      h->counting = 0;
+      cudaError_t e = enqueue_step(h, cfl);
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+      if (e != cudaSuccess) return fail(h, AMR_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+      CK(e2);
+      CK(cudaGraphInstantiate(&h->graph[g], graph, 0));
+      cudaGraphDestroy(graph);
+      h->graph_launches[g] = h->counting;
+    }
+    CK(cudaGraphLaunch(h->graph[g], h->stream));
+    h->launches += h->graph_launches[g];
+  } else {
+    h->counting = 0;
+    CK(enqueue_step(h, cfl));
+    h->launches += h->counting;
+  }
+  return AMR_OK;
+}
+
+amr_status read_bad(amr_handle* h) {
+  unsigned int bad = 0;
+  CK(cudaMemcpyAsync(&bad, &h->params->bad, sizeof bad, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (bad) {
+    CK(cudaMemsetAsync(&h->params->bad, 0, sizeof(unsigned int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return fail(h, AMR_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) detected on the device");
+  }
+  return AMR_OK;
+}
+
+template <typename X>
+size_t put(std::vector<unsigned char>& buf, const std::vector<X>& v) {
+  size_t off = (buf.size() + 255) / 256 * 256;
+  buf.resize(off + v.size() * sizeof(X) + 1);
+  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(X));
+  return off;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void amr_default_config(amr_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof *c);
+  c->nvar = 5;
+  c->precision = AMR_FP64;
+  c->riemann = AMR_HLL;
+  c->gamma = 1.4;
+  c->theta = 1.5;
+  c->cfl = 0.4;
+  for (int d = 0; d < 3; ++d) {
+    c->base_n[d] = 32;
+    c->domain_lo[d] = 0.0;
+    c->domain_hi[d] = 1.0;
+  }
+  for (int f = 0; f < 6; ++f) c->bc[f] = AMR_BC_OUTFLOW;
+  c->max_level = 0;
+  c->ref_ratio = 2;
+  c->ch = 0.0;
+  c->batched = 1;
+  c->use_graph = 1;
+  c->cuda_stream = nullptr;
+}
+
+const char* amr_global_error(void) { return g_global_err.c_str(); }
+
+amr_status amr_create(const amr_config* cfg, amr_handle** out) {
+  if (!out) { g_global_err = "out is NULL"; return AMR_ERR_ARG; }
+  *out = nullptr;
+  if (!cfg) { g_global_err = "cfg is NULL"; return AMR_ERR_ARG; }
+  std::string msg;
+  amr_status st = validate_config(*cfg, msg);
+  if (st != AMR_OK) { g_global_err = msg; return st; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    g_global_err = "no CUDA device";
+    return AMR_ERR_CUDA;
+  }
+  amr_handle* h = new amr_handle();
+  h->cfg = *cfg;
+  for (int d = 0; d < 3; ++d) h->dx0[d] = (cfg->domain_hi[d] - cfg->domain_lo[d]) / cfg->base_n[d];
+  if (cfg->cuda_stream) {
+    h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      g_global_err = "cudaStreamCreate failed";
+      delete h;
+      return AMR_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  h->ops = make_ops(*cfg);
+  void* p = nullptr;
+  if (cudaMalloc(&p, sizeof(StepParams)) != cudaSuccess) {
+    g_global_err = "cudaMalloc of step parameters failed";
+    amr_destroy(h);
+    return AMR_ERR_CUDA;
+  }
+  h->params = static_cast<StepParams*>(p);
+  cudaMemsetAsync(h->params, 0, sizeof(StepParams), h->stream);
+  if (cudaGetLastError() != cudaSuccess) {
+    g_global_err = "CUDA error at create";
+    amr_destroy(h);
+    return AMR_ERR_CUDA;
+  }
+  *out = h;
+  return AMR_OK;
+}
+
+amr_status amr_validate_patches(const amr_config* cfg, int npatch, const amr_patch* patches, char* msg,
+                                int msg_len) {
+  std::string m;
+  amr_status st;
+  if (!cfg || npatch <= 0 || !patches) {
+    m = "null config, no patches or null patch array";
+    st = AMR_ERR_ARG;
+  } else {
+    std::vector<HPatch> P(npatch);
+    for (int i = 0; i < npatch; ++i) {
+      P[i].level = patches[i].level;
+      for (int d = 0; d < 3; ++d) { P[i].lo[d] = patches[i].lo[d]; P[i].n[d] = patches[i].n[d]; }
+    }
+    st = validate_patches(*cfg, P, m);
+  }
+  g_global_err = m;
+  if (msg && msg_len > 0) {
+    std::strncpy(msg, m.c_str(), (size_t)msg_len - 1);
+    msg[msg_len - 1] = 0;
+  }
+  return st;
+}
+
+amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, const double* const* state,
+                           int state_kind) {
+  if (!h) return AMR_ERR_ARG;
+  if (npatch <= 0 || !patches || !state) return fail(h, AMR_ERR_ARG, "null patches or state");
+  if (state_kind != AMR_STATE_CONSERVED && state_kind != AMR_STATE_PRIMITIVE)
+    return fail(h, AMR_ERR_ARG, "state_kind must be AMR_STATE_CONSERVED or AMR_STATE_PRIMITIVE");
+  for (int i = 0; i < npatch; ++i)
+    if (!state[i]) return fail(h, AMR_ERR_ARG, "null state pointer");
+  std::vector<HPatch> P(npatch);
+  for (int i = 0; i < npatch; ++i) {
+    P[i].level = patches[i].level;
+    for (int d = 0; d < 3; ++d) { P[i].lo[d] = patches[i].lo[d]; P[i].n[d] = patches[i].n[d]; }
+  }
+  Plan plan;
+  std::string msg;
+  amr_status st = build_plan(h->cfg, P, plan, msg);
+  if (st != AMR_OK) return fail(h, st, msg);
+  CK(cudaStreamSynchronize(h->stream));
+  free_device(h);
+  h->plan = std::move(plan);
+  Plan& pl = h->plan;
+  const int nv = pl.nvar;
+  const size_t es = h->ops->elem_size();
+  const int nlev = (int)pl.levels.size();
+
+  // chunks of <= 16384 interior cells
+  h->chunks.clear();
+  for (int i = 0; i < npatch; ++i) {
+    int nc = P[i].n[0] * P[i].n[1] * P[i].n[2];
+    for (int b = 0; b < nc; b += 16384) h->chunks.push_back({i, b, std::min(16384, nc - b)});
+  }
+  h->nchunk = (int)h->chunks.size();
+
+  // registers
+  std::vector<size_t> reg_off(nlev, 0);
+  size_t nregd = 0;
+  for (int l = 1; l < nlev; ++l) {
+    reg_off[l] = nregd;
+    nregd += 2 * (size_t)nv * pl.levels[l].regs.size();
+  }
+
+  // one table buffer
+  std::vector<unsigned char> buf;
+  size_t o_desc = put(buf, pl.desc);
+  size_t o_chunks = put(buf, h->chunks);
+  size_t o_cover = put(buf, pl.cover);
+  size_t o_cover_first = put(buf, pl.cover_first);
+  size_t o_packed_off = put(buf, pl.packed_off);
+  std::vector<double> lvol(nlev);
+  for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
+  size_t o_lvol = put(buf, lvol);
+  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; };
+  std::vector<Offs> lo(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = pl.levels[l];
+    lo[l].items = put(buf, L.items);
+    lo[l].ghost = put(buf, L.ghost);
+    lo[l].prolong = put(buf, L.prolong);
+    lo[l].gather = put(buf, L.gather);
+    lo[l].restr = put(buf, L.restrict_segs);
+    lo[l].regs = put(buf, L.regs);
+    lo[l].rf = put(buf, L.reflux_first);
+  }
+  void* p = nullptr;
+  CK(cudaMalloc(&p, buf.size()));
+  h->tables = static_cast<unsigned char*>(p);
+  CK(cudaMemcpyAsync(h->tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  h->d_desc = reinterpret_cast<const PatchDesc*>(h->tables + o_desc);
+  h->d_chunks = reinterpret_cast<const ChunkDesc*>(h->tables + o_chunks);
+  h->d_cover = reinterpret_cast<const CoverBox*>(h->tables + o_cover);
+  h->d_cover_first = reinterpret_cast<const int*>(h->tables + o_cover_first);
+  h->d_packed_off = reinterpret_cast<const int64_t*>(h->tables + o_packed_off);
+  h->d_level_vol = reinterpret_cast<const double*>(h->tables + o_lvol);
+
+  CK(cudaMalloc(&h->U, pl.arena_elems * es));
+  CK(cudaMalloc(&h->U1, pl.arena_elems * es));
+  CK(cudaMemsetAsync(h->U, 0, pl.arena_elems * es, h->stream));
+  CK(cudaMemsetAsync(h->U1, 0, pl.arena_elems * es, h->stream));
+  if (nlev > 1) {
+    CK(cudaMalloc(&h->Uold, pl.arena_elems * es));
+    CK(cudaMemsetAsync(h->Uold, 0, pl.arena_elems * es, h->stream));
+    CK(cudaMalloc(&h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
+  }
+  CK(cudaMalloc(&p, pl.packed_elems * sizeof(double)));
+  h->packed = static_cast<double*>(p);
+  CK(cudaMalloc(&p, (size_t)h->nchunk * nv * sizeof(double)));
+  h->partial = static_cast<double*>(p);
+  CK(cudaMalloc(&p, 16 * sizeof(double)));
+  h->totals = static_cast<double*>(p);
+  if (nregd) {
+    CK(cudaMalloc(&p, nregd * sizeof(double)));
+    h->regs = static_cast<double*>(p);
+    CK(cudaMemsetAsync(h->regs, 0, nregd * sizeof(double), h->stream));
+  }
+
+  h->dl.assign(nlev, DevLevel());
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = pl.levels[l];
+    DevLevel& D = h->dl[l];
+    D.nitems = (int)L.items.size();
+    D.nghost = (int)L.ghost.size();
+    D.nprolong = (int)L.prolong.size();
+    D.ngather = (int)L.gather.size();
+    D.nrestrict = (int)L.restrict_segs.size();
+    D.nreg = (int)L.regs.size();
+    D.nuniq = L.reflux_first.empty() ? 0 : (int)L.reflux_first.size() - 1;
+    D.items = reinterpret_cast<const StageItem*>(h->tables + lo[l].items);
+    D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
+    D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
+    D.gather = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather);
+    D.restrict_segs = reinterpret_cast<const RestrictSeg*>(h->tables + lo[l].restr);
+    D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
+    D.reflux_first = reinterpret_cast<const int*>(h->tables + lo[l].rf);
+    D.R = h->regs ? h->regs + reg_off[l] : nullptr;
+    const PatchDesc& a = pl.desc[L.first];
+    const PatchDesc& b = pl.desc[L.first + L.count - 1];
+    D.arena_begin = a.off;
+    D.arena_end = b.off + b.vstride * nv;
+  }
+
+  // initial state: pack on the host, one copy, convert on the device
+  std::vector<double> host(pl.packed_elems);
+  for (int i = 0; i < npatch; ++i) {
+    size_t n = (size_t)P[i].n[0] * P[i].n[1] * P[i].n[2] * nv;
+    std::memcpy(host.data() + pl.packed_off[i], state[i], n * sizeof(double));
+  }
+  CK(cudaMemcpyAsync(h->packed, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(&h->params->bad, 0, sizeof(unsigned int), h->stream));
+  CK(h->ops->pack_in(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->packed, h->U,
+                     state_kind == AMR_STATE_PRIMITIVE, h->params));
+  h->launches += 1;
+  CK(cudaStreamSynchronize(h->stream));
+  h->ready = true;
+  return read_bad(h);
+}
+
+long long amr_state_size(const amr_handle* h) { return (h && h->ready) ? h->plan.packed_elems : 0; }
+
+amr_status amr_set_state(amr_handle* h, const double* packed, int state_kind) {
+  if (!h) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  if (!packed) return fail(h, AMR_ERR_ARG, "null state buffer");
+  if (state_kind != AMR_STATE_CONSERVED && state_kind != AMR_STATE_PRIMITIVE)
+    return fail(h, AMR_ERR_ARG, "bad state_kind");
+  CK(cudaMemcpyAsync(h->packed, packed, h->plan.packed_elems * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(h->ops->pack_in(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->packed, h->U,
+                     state_kind == AMR_STATE_PRIMITIVE, h->params));
+  h->launches += 1;
+  return AMR_OK;
+}
+
+amr_status amr_step(amr_handle* h, double dt, double* dt_used) {
+  if (!h) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  if (!std::isfinite(dt)) return fail(h, AMR_ERR_ARG, "dt must be finite");
+  const bool cfl = !(dt > 0.0);
+  if (!cfl) {
+    set_dt_kernel<<<1, 1, 0, h->stream>>>(h->params, dt);
+    CK(cudaGetLastError());
+    h->launches += 1;
+  }
+  amr_status st = run_step(h, cfl);
+  if (st != AMR_OK) return st;
+  if (dt_used) {
+    CK(cudaMemcpyAsync(dt_used, &h->params->dt0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_bad(h);
+  }
+  return AMR_OK;
+}
+
+amr_status amr_cfl_dt(amr_handle* h, double* dt) {
+  if (!h || !dt) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  h->counting = 0;
+  CK(enqueue_speed(h, 1));
+  h->launches += h->counting;
+  CK(cudaMemcpyAsync(dt, &h->params->dt0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_get_state_all(amr_handle* h, double* packed) {
+  if (!h || !packed) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  CK(h->ops->pack_out(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, h->packed));
+  h->launches += 1;
+  CK(cudaMemcpyAsync(packed, h->packed, h->plan.packed_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_get_state(amr_handle* h, int patch, double* out) {
+  if (!h || !out) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  if (patch < 0 || patch >= (int)h->plan.patches.size()) return fail(h, AMR_ERR_ARG, "patch index out of range");
+  CK(h->ops->pack_out(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, h->packed));
+  h->launches += 1;
+  const HPatch& P = h->plan.patches[patch];
+  size_t n = (size_t)P.n[0] * P.n[1] * P.n[2] * h->plan.nvar;
+  CK(cudaMemcpyAsync(out, h->packed + h->plan.packed_off[patch], n * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_conserved_totals(amr_handle* h, double* out) {
+  if (!h || !out) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  CK(h->ops->totals(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, h->d_cover, h->d_cover_first,
+                    h->d_level_vol, h->partial, h->totals));
+  h->launches += 2;
+  CK(cudaMemcpyAsync(out, h->totals, h->plan.nvar * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_check(amr_handle* h) {
+  if (!h) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  return read_bad(h);
+}
+
+amr_status amr_set_timing(amr_handle* h, int on) {
+  if (!h) return AMR_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  h->timing = on != 0;
+  h->ev_used = 0;
+  for (int c = 0; c < AMR_T_NCLASS; ++c) {
+    h->ev_pairs[c].clear();
+    h->t_ms[c] = 0.0;
+    h->t_cnt[c] = 0;
+  }
+  return AMR_OK;
+}
+
+amr_status amr_get_timing(amr_handle* h, double* ms, long long* count, int nclass) {
+  if (!h || !ms || !count || nclass < 1) return AMR_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < AMR_T_NCLASS; ++c) {
+    for (auto& pr : h->ev_pairs[c]) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, h->ev_pool[pr.first], h->ev_pool[pr.second]));
+      h->t_ms[c] += t;
+      h->t_cnt[c] += 1;
+    }
+    h->ev_pairs[c].clear();
+  }
+  h->ev_used = 0;
+  for (int c = 0; c < nclass && c < AMR_T_NCLASS; ++c) {
+    ms[c] = h->t_ms[c];
+    count[c] = h->t_cnt[c];
+    h->t_ms[c] = 0.0;
+    h->t_cnt[c] = 0;
+  }
+  return AMR_OK;
+}
+
+long long amr_kernel_launches(const amr_handle* h) { return h ? h->launches : 0; }
+
+const char* amr_last_error(const amr_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void amr_destroy(amr_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_device(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->params) cudaFree(h->params);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h->ops;
+  delete h;
+}
+
+}  // extern "C"

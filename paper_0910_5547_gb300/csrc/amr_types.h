@@ -1,0 +1,103 @@
+// amr_types.h -- plain structs shared by the host planner (hierarchy.cpp) and
+// the sm_103a kernels.  Everything here is POD so tables can be copied to the
+// device with one cudaMemcpyAsync each.
+#pragma once
+#include <cstdint>
+
+#ifndef AMR_HD
+#ifdef __CUDACC__
+#define AMR_HD __host__ __device__
+#else
+#define AMR_HD
+#endif
+#endif
+
+namespace amr {
+
+constexpr int kGhost = 2;      // two ghost cells: the PLM face stencil reaches two cells out (Sec. 4)
+constexpr int kMaxVar = 9;
+constexpr int kStageThreads = 256;  // threads of one stage-kernel CTA (one per x-y column)
+constexpr int kMaxTileX = 32;
+constexpr int kPlaneMax = 432;    // max (wx + 4) * (wy + 4) of a stage tile
+
+// Device view of one patch.  Arrays U, U1 and Uold share the same layout and
+// offsets: var v, ghosted local cell (i, j, k) with -2 <= i < n0 + 2 sits at
+//   off + v * vstride + ((k + 2) * m1 + (j + 2)) * pitch + (i + 2)
+struct PatchDesc {
+  int64_t off;       // element offset of the patch in the state arena
+  int64_t vstride;   // elements between variables
+  int n[3];          // interior cells
+  int pitch;         // elements per x row (>= n0 + 4)
+  int m1;            // rows per z plane (n1 + 4)
+  int level;
+  int lo[3];         // level index of interior cell (0,0,0)
+  int tile_off;      // parent-tile offset (elements) for level >= 1, else -1
+  int tn[3];         // parent tile extent (n/2 + 4), level >= 1
+};
+
+AMR_HD inline int64_t cell_index(const PatchDesc& p, int i, int j, int k) {
+  return ((int64_t)(k + kGhost) * p.m1 + (j + kGhost)) * p.pitch + (i + kGhost);
+}
+
+// One CTA of the fused stage kernel: a wx * wy column block of one patch,
+// marching through z in [z0, z0 + wz).
+struct StageItem {
+  int patch;
+  int16_t x0, y0, z0, wx, wy, wz;
+  int16_t pad;
+};
+
+// Box copy used by ghost fill and parent-tile gather.  dst cell (a, b, c) of
+// the box maps to src local coordinate per axis: mode 0 -> a + sh, mode 1 -> sh.
+struct CopySeg {
+  int dst_patch;     // patch (ghost fill) or fine patch owning the tile (gather)
+  int src_patch;
+  int16_t dlo[3];    // dst box start in dst-local coordinates (ghosted / tile)
+  int16_t dn[3];     // dst box extent
+  int16_t sh[3];     // src mapping parameter per axis
+  uint8_t mode[3];   // 0 translate, 1 constant
+  uint8_t pad;
+};
+
+// Box of fine ghost cells filled by prolongation from the parent tile.
+struct ProlongBox {
+  int patch;
+  int16_t lo[3];     // fine local coordinates (may be negative: ghost region)
+  int16_t n[3];
+};
+
+// Restriction of a fine patch into (part of) one coarse patch.
+struct RestrictSeg {
+  int fine, coarse;
+  int16_t clo[3];    // coarse-local box start
+  int16_t cn[3];     // box extent
+};
+
+// One coarse-fine face: fine patch `fpatch` face plane on side `side` along
+// axis `d`, against the uncovered coarse cell C of patch `cpatch`.
+struct RegFace {
+  int fpatch, cpatch;
+  int16_t fface[3];  // fine local face index of the (0,0) sub-face (face i sits at the low side of cell i)
+  int16_t cidx[3];   // coarse local cell index of C
+  int8_t d, side;    // axis, side of the fine patch (0 lo, 1 hi)
+  int8_t cside;      // +1: face is C's high face, -1: C's low face
+  int8_t pad;
+};
+
+// Box of a coarse patch covered by a finer level (excluded from totals).
+struct CoverBox {
+  int16_t lo[3], n[3];
+};
+
+// Step parameters read by the kernels from device memory, so a captured step
+// graph stays valid for any dt.
+struct StepParams {
+  double dt0;          // coarse-level dt
+  double ch;           // GLM cleaning speed in use
+  unsigned long long rate_bits;   // max CFL rate (double bits, atomicMax)
+  unsigned long long speed_bits;  // max signal speed (double bits, atomicMax)
+  unsigned int bad;    // non-physical state detected
+  unsigned int pad;
+};
+
+}  // namespace amr

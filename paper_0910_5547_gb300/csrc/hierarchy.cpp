@@ -1,0 +1,520 @@
+// hierarchy.cpp -- host planner for the AMR patch hierarchy (Sec. 3:
+// Berger-Colella block-structured refinement, each grid an IBVP).  Builds the
+// launch tables of every kernel from the patch list.  No CUDA calls.
+#include "hierarchy.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <tuple>
+
+namespace amr {
+
+namespace {
+
+int level_n(const amr_config& c, int l, int d) { return c.base_n[d] << l; }
+bool periodic(const amr_config& c, int d) { return c.bc[2 * d] == AMR_BC_PERIODIC; }
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+std::string fmt(const char* f, int a = 0, int b = 0, int c = 0, int d = 0) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, f, a, b, c, d);
+  return buf;
+}
+
+bool boxes_overlap(const HPatch& a, const HPatch& b) {
+  for (int d = 0; d < 3; ++d)
+    if (a.lo[d] + a.n[d] <= b.lo[d] || b.lo[d] + b.n[d] <= a.lo[d]) return false;
+  return true;
+}
+
+// Intervals [lo, hi) of axis d at level l after periodic wrap / clipping at outflow faces.
+std::vector<std::pair<int, int>> wrap_interval(const amr_config& c, int l, int d, int lo, int hi) {
+  int N = level_n(c, l, d);
+  std::vector<std::pair<int, int>> out;
+  if (!periodic(c, d)) {
+    lo = std::max(lo, 0);
+    hi = std::min(hi, N);
+    if (lo < hi) out.push_back({lo, hi});
+    return out;
+  }
+  if (hi - lo >= N) {
+    out.push_back({0, N});
+    return out;
+  }
+  int a = ((lo % N) + N) % N;
+  int len = hi - lo;
+  if (a + len <= N) {
+    out.push_back({a, a + len});
+  } else {
+    out.push_back({a, N});
+    out.push_back({0, a + len - N});
+  }
+  return out;
+}
+
+// Decompose the cells with mask == 0 of an A x B grid into rectangles
+// (row runs merged across consecutive rows with identical extent).
+struct Rect { int a0, na, b0, nb; };
+std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) {
+  std::vector<Rect> done;
+  std::map<std::pair<int, int>, int> open;  // (a0, na) -> index into done
+  for (int b = 0; b < B; ++b) {
+    std::map<std::pair<int, int>, int> next;
+    int a = 0;
+    while (a < A) {
+      if (m[(size_t)b * A + a]) { ++a; continue; }
+      int s = a;
+      while (a < A && !m[(size_t)b * A + a]) ++a;
+      auto key = std::make_pair(s, a - s);
+      auto it = open.find(key);
+      if (it != open.end()) {
+        done[it->second].nb += 1;
+        next[key] = it->second;
+      } else {
+        done.push_back({s, a - s, b, 1});
+        next[key] = (int)done.size() - 1;
+      }
+    }
+    open.swap(next);
+  }
+  return done;
+}
+
+}  // namespace
+
+amr_status validate_config(const amr_config& c, std::string& msg) {
+  if (c.nvar != 5 && c.nvar != 9) { msg = "nvar must be 5 (Euler) or 9 (GLM-MHD)"; return AMR_ERR_ARG; }
+  if (c.precision != AMR_FP64 && c.precision != AMR_FP32) { msg = "precision must be AMR_FP64 or AMR_FP32"; return AMR_ERR_ARG; }
+  if (c.riemann != AMR_HLL && c.riemann != AMR_LLF) { msg = "riemann must be AMR_HLL or AMR_LLF"; return AMR_ERR_ARG; }
+  if (!(c.gamma > 1.0) || !std::isfinite(c.gamma)) { msg = "gamma must be > 1"; return AMR_ERR_ARG; }
+  if (!(c.theta >= 0.0 && c.theta <= 2.0)) { msg = "theta must lie in [0, 2]"; return AMR_ERR_ARG; }
+  if (!(c.cfl > 0.0 && c.cfl <= 1.0)) { msg = "cfl must lie in (0, 1]"; return AMR_ERR_ARG; }
+  if (c.max_level < 0 || c.max_level > 12) { msg = "max_level must lie in [0, 12]"; return AMR_ERR_ARG; }
+  if (c.ref_ratio != 0 && c.ref_ratio != 2) { msg = "only refinement ratio 2 is supported"; return AMR_ERR_ARG; }
+  for (int d = 0; d < 3; ++d) {
+    if (c.base_n[d] < 1 || c.base_n[d] > 4096) { msg = "base_n must lie in [1, 4096]"; return AMR_ERR_ARG; }
+    if ((int64_t)c.base_n[d] << c.max_level > (1 << 24)) { msg = "base_n * 2^max_level too large"; return AMR_ERR_ARG; }
+    if (!(c.domain_hi[d] > c.domain_lo[d]) || !std::isfinite(c.domain_hi[d] - c.domain_lo[d])) {
+      msg = "domain_hi must exceed domain_lo"; return AMR_ERR_ARG;
+    }
+    for (int s = 0; s < 2; ++s)
+      if (c.bc[2 * d + s] != AMR_BC_OUTFLOW && c.bc[2 * d + s] != AMR_BC_PERIODIC) { msg = "bad boundary code"; return AMR_ERR_ARG; }
+    if ((c.bc[2 * d] == AMR_BC_PERIODIC) != (c.bc[2 * d + 1] == AMR_BC_PERIODIC)) {
+      msg = "periodic boundaries must be set on both faces of an axis"; return AMR_ERR_ARG;
+    }
+  }
+  if (c.batched != 0 && c.batched != 1) { msg = "batched must be 0 or 1"; return AMR_ERR_ARG; }
+  if (c.nvar == 9 && c.ch > 0.0 && !std::isfinite(c.ch)) { msg = "ch must be finite"; return AMR_ERR_ARG; }
+  return AMR_OK;
+}
+
+amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, std::string& msg) {
+  amr_status st = validate_config(c, msg);
+  if (st != AMR_OK) return st;
+  if (P.empty()) { msg = "no patches"; return AMR_ERR_ARG; }
+  int maxl = 0;
+  for (size_t i = 0; i < P.size(); ++i) {
+    const HPatch& p = P[i];
+    if (p.level < 0 || p.level > c.max_level) { msg = fmt("patch %d: level %d outside [0, max_level]", (int)i, p.level); return AMR_ERR_ARG; }
+    if (i > 0 && p.level < P[i - 1].level) { msg = fmt("patch %d: patches must be sorted by level", (int)i); return AMR_ERR_ARG; }
+    maxl = std::max(maxl, p.level);
+    for (int d = 0; d < 3; ++d) {
+      if (p.n[d] < 2 || p.n[d] > 1024) { msg = fmt("patch %d: size %d outside [2, 1024] on axis %d", (int)i, p.n[d], d); return AMR_ERR_ARG; }
+      if (p.lo[d] < 0 || p.lo[d] + p.n[d] > level_n(c, p.level, d)) {
+        msg = fmt("patch %d: outside the level-%d domain on axis %d", (int)i, p.level, d); return AMR_ERR_NESTING;
+      }
+      if (p.level > 0 && ((p.lo[d] & 1) || (p.n[d] & 1))) {
+        msg = fmt("patch %d: refined patches need even lo and n (axis %d)", (int)i, d); return AMR_ERR_NESTING;
+      }
+    }
+  }
+  std::vector<int> first(maxl + 2, 0);
+  for (const HPatch& p : P) first[p.level + 1]++;
+  for (int l = 0; l <= maxl; ++l) {
+    if (first[l + 1] == 0) { msg = fmt("level %d has no patches", l); return AMR_ERR_NESTING; }
+    first[l + 1] += first[l];
+  }
+  // no same-level overlap
+  for (int l = 0; l <= maxl; ++l) {
+    std::vector<int> idx;
+    for (int i = first[l]; i < first[l + 1]; ++i) idx.push_back(i);
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return P[a].lo[0] < P[b].lo[0]; });
+    for (size_t a = 0; a < idx.size(); ++a)
+      for (size_t b = a + 1; b < idx.size(); ++b) {
+        if (P[idx[b]].lo[0] >= P[idx[a]].lo[0] + P[idx[a]].n[0]) break;
+        if (boxes_overlap(P[idx[a]], P[idx[b]])) {
+          msg = fmt("patches %d and %d overlap on level %d", idx[a], idx[b], l); return AMR_ERR_NESTING;
+        }
+      }
+  }
+  // level 0 tiles the domain
+  int64_t vol0 = 0;
+  for (int i = first[0]; i < first[1]; ++i) vol0 += (int64_t)P[i].n[0] * P[i].n[1] * P[i].n[2];
+  if (vol0 != (int64_t)c.base_n[0] * c.base_n[1] * c.base_n[2]) {
+    msg = "level-0 patches must tile the whole domain"; return AMR_ERR_NESTING;
+  }
+  // proper nesting: footprint grown by two parent cells is covered by the parent level
+  for (int l = 1; l <= maxl; ++l)
+    for (int i = first[l]; i < first[l + 1]; ++i) {
+      const HPatch& p = P[i];
+      std::vector<std::pair<int, int>> iv[3];
+      int64_t need = 1;
+      for (int d = 0; d < 3; ++d) {
+        iv[d] = wrap_interval(c, l - 1, d, p.lo[d] / 2 - 2, (p.lo[d] + p.n[d]) / 2 + 2);
+        int64_t len = 0;
+        for (auto& q : iv[d]) len += q.second - q.first;
+        need *= len;
+      }
+      int64_t got = 0;
+      for (int q = first[l - 1]; q < first[l]; ++q) {
+        const HPatch& o = P[q];
+        int64_t v = 1;
+        for (int d = 0; d < 3 && v; ++d) {
+          int64_t len = 0;
+          for (auto& r : iv[d]) {
+            int a = std::max(r.first, o.lo[d]), b = std::min(r.second, o.lo[d] + o.n[d]);
+            if (a < b) len += b - a;
+          }
+          v *= len;
+        }
+        got += v;
+      }
+      if (got != need) {
+        msg = fmt("patch %d (level %d) is not properly nested: its footprint grown by 2 parent cells "
+                  "is not covered by level %d", i, l, l - 1);
+        return AMR_ERR_NESTING;
+      }
+    }
+  return AMR_OK;
+}
+
+amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan, std::string& msg) {
+  amr_status st = validate_patches(cfg, P, msg);
+  if (st != AMR_OK) return st;
+  plan = Plan();
+  plan.cfg = cfg;
+  plan.nvar = cfg.nvar;
+  plan.patches = P;
+  const int np = (int)P.size();
+  int nlev = P.back().level + 1;
+  plan.levels.resize(nlev);
+  for (int i = 0; i < np; ++i) {
+    LevelPlan& L = plan.levels[P[i].level];
+    if (L.count == 0) L.first = i;
+    L.count++;
+    L.cells += (int64_t)P[i].n[0] * P[i].n[1] * P[i].n[2];
+  }
+
+  // ---- device descriptors and arena layout ----
+  plan.desc.resize(np);
+  int64_t off = 0, toff = 0, poff = 0;
+  plan.packed_off.resize(np);
+  for (int i = 0; i < np; ++i) {
+    PatchDesc& d = plan.desc[i];
+    const HPatch& p = P[i];
+    for (int a = 0; a < 3; ++a) { d.n[a] = p.n[a]; d.lo[a] = p.lo[a]; }
+    d.level = p.level;
+    d.pitch = (int)round_up(p.n[0] + 2 * kGhost, 4);
+    d.m1 = p.n[1] + 2 * kGhost;
+    d.vstride = round_up((int64_t)d.pitch * d.m1 * (p.n[2] + 2 * kGhost), 32);
+    d.off = off;
+    off += d.vstride * plan.nvar;
+    if (p.level > 0) {
+      d.tile_off = (int)toff;
+      for (int a = 0; a < 3; ++a) d.tn[a] = p.n[a] / 2 + 4;
+      toff += (int64_t)d.tn[0] * d.tn[1] * d.tn[2] * plan.nvar;
+    } else {
+      d.tile_off = -1;
+      d.tn[0] = d.tn[1] = d.tn[2] = 0;
+    }
+    plan.packed_off[i] = poff;
+    poff += (int64_t)p.n[0] * p.n[1] * p.n[2] * plan.nvar;
+  }
+  if (toff > INT32_MAX) { msg = "parent tiles exceed 2^31 elements"; return AMR_ERR_ARG; }
+  plan.arena_elems = off;
+  plan.tile_elems = toff;
+  plan.packed_elems = poff;
+
+  // ---- stage work items: x tiles <= 32 wide, y tiles filling 256 columns, z chunks ----
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = plan.levels[l];
+    L.item_first.push_back(0);
+    for (int i = L.first; i < L.first + L.count; ++i) {
+      const HPatch& p = P[i];
+      auto split = [](int n, int parts, std::vector<std::pair<int, int>>& out) {
+        out.clear();
+        int base = n / parts, rem = n % parts, s = 0;
+        for (int k = 0; k < parts; ++k) {
+          int w = base + (k < rem ? 1 : 0);
+          out.push_back({s, w});
+          s += w;
+        }
+      };
+      std::vector<std::pair<int, int>> xs, ys, zs;
+      split(p.n[0], (p.n[0] + kMaxTileX - 1) / kMaxTileX, xs);
+      int zparts = p.n[2] <= 48 ? 1 : (p.n[2] + 31) / 32;
+      split(p.n[2], zparts, zs);
+      for (auto& z : zs)
+        for (auto& x : xs) {
+          int wymax = std::min(kStageThreads / x.second, kPlaneMax / (x.second + 4) - 4);
+          split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);
+          for (auto& y : ys) {
+            StageItem it{};
+            it.patch = i;
+            it.x0 = (int16_t)x.first; it.wx = (int16_t)x.second;
+            it.y0 = (int16_t)y.first; it.wy = (int16_t)y.second;
+            it.z0 = (int16_t)z.first; it.wz = (int16_t)z.second;
+            L.items.push_back(it);
+          }
+        }
+      L.item_first.push_back((int)L.items.size());
+    }
+  }
+
+  // ---- ghost fill: sibling copies (incl. periodic images), outflow, prolongation boxes ----
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = plan.levels[l];
+    L.ghost_first.push_back(0);
+    L.prolong_first.push_back(0);
+    for (int i = L.first; i < L.first + L.count; ++i) {
+      const HPatch& p = P[i];
+      for (int d = 0; d < 3; ++d) {
+        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        int Nl = level_n(cfg, l, d);
+        for (int side = 0; side < 2; ++side)
+          for (int gg = 0; gg < kGhost; ++gg) {
+            int loc = side ? p.n[d] + gg : -1 - gg;
+            int G = p.lo[d] + loc;
+            if (G < 0 || G >= Nl) {
+              if (!periodic(cfg, d)) {  // outflow: zero-gradient copy of the boundary cell
+                CopySeg s{};
+                s.dst_patch = i; s.src_patch = i;
+                s.dlo[d] = (int16_t)loc; s.dn[d] = 1; s.mode[d] = 1;
+                s.sh[d] = (int16_t)(side ? p.n[d] - 1 : 0);
+                s.dlo[t1] = 0; s.dn[t1] = (int16_t)p.n[t1]; s.mode[t1] = 0; s.sh[t1] = 0;
+                s.dlo[t2] = 0; s.dn[t2] = (int16_t)p.n[t2]; s.mode[t2] = 0; s.sh[t2] = 0;
+                L.ghost.push_back(s);
+                continue;
+              }
+              G = ((G % Nl) + Nl) % Nl;
+            }
+            int A = p.n[t1], B = p.n[t2];
+            std::vector<unsigned char> mask((size_t)A * B, 0);
+            for (int q = L.first; q < L.first + L.count; ++q) {
+              const HPatch& o = P[q];
+              if (G < o.lo[d] || G >= o.lo[d] + o.n[d]) continue;
+              int a0 = std::max(p.lo[t1], o.lo[t1]), a1 = std::min(p.lo[t1] + p.n[t1], o.lo[t1] + o.n[t1]);
+              int b0 = std::max(p.lo[t2], o.lo[t2]), b1 = std::min(p.lo[t2] + p.n[t2], o.lo[t2] + o.n[t2]);
+              if (a0 >= a1 || b0 >= b1) continue;
+              CopySeg s{};
+              s.dst_patch = i; s.src_patch = q;
+              s.dlo[d] = (int16_t)loc; s.dn[d] = 1; s.mode[d] = 0;
+              s.sh[d] = (int16_t)((G - o.lo[d]) - loc);
+              s.dlo[t1] = (int16_t)(a0 - p.lo[t1]); s.dn[t1] = (int16_t)(a1 - a0); s.sh[t1] = (int16_t)(p.lo[t1] - o.lo[t1]);
+              s.dlo[t2] = (int16_t)(b0 - p.lo[t2]); s.dn[t2] = (int16_t)(b1 - b0); s.sh[t2] = (int16_t)(p.lo[t2] - o.lo[t2]);
+              L.ghost.push_back(s);
+              for (int b = b0; b < b1; ++b)
+                for (int a = a0; a < a1; ++a) mask[(size_t)(b - p.lo[t2]) * A + (a - p.lo[t1])] = 1;
+            }
+            std::vector<Rect> rects = mask_rects(mask, A, B);
+            if (!rects.empty() && l == 0) {
+              msg = fmt("level-0 patch %d has uncovered ghost cells", i);
+              return AMR_ERR_NESTING;
+            }
+            for (const Rect& r : rects) {
+              ProlongBox pb{};
+              pb.patch = i;
+              pb.lo[d] = (int16_t)loc; pb.n[d] = 1;
+              pb.lo[t1] = (int16_t)r.a0; pb.n[t1] = (int16_t)r.na;
+              pb.lo[t2] = (int16_t)r.b0; pb.n[t2] = (int16_t)r.nb;
+              L.prolong.push_back(pb);
+            }
+          }
+      }
+      L.ghost_first.push_back((int)L.ghost.size());
+      L.prolong_first.push_back((int)L.prolong.size());
+    }
+  }
+
+  // ---- parent-tile gathers (level >= 1): tile = footprint grown by 2 parent cells ----
+  for (int l = 1; l < nlev; ++l) {
+    LevelPlan& L = plan.levels[l];
+    const LevelPlan& C = plan.levels[l - 1];
+    L.gather_first.push_back(0);
+    for (int i = L.first; i < L.first + L.count; ++i) {
+      const HPatch& p = P[i];
+      struct Piece { int a, len, mode, src; };
+      std::vector<Piece> pieces[3];
+      for (int d = 0; d < 3; ++d) {
+        int Nc = level_n(cfg, l - 1, d);
+        int T0 = p.lo[d] / 2 - 2, tn = p.n[d] / 2 + 4;
+        int t = 0;
+        while (t < tn) {
+          int Cg = T0 + t;
+          int kind = Cg < 0 ? 0 : (Cg < Nc ? 1 : 2);
+          int e = t;
+          while (e < tn) {
+            int Cc = T0 + e;
+            int k2 = Cc < 0 ? 0 : (Cc < Nc ? 1 : 2);
+            if (k2 != kind) break;
+            ++e;
+          }
+          Piece pc{t, e - t, 0, 0};
+          if (kind == 1) { pc.mode = 0; pc.src = Cg; }
+          else if (periodic(cfg, d)) { pc.mode = 0; pc.src = kind == 0 ? Cg + Nc : Cg - Nc; }
+          else { pc.mode = 1; pc.src = kind == 0 ? 0 : Nc - 1; }
+          pieces[d].push_back(pc);
+          t = e;
+        }
+      }
+      int64_t covered = 0;
+      for (auto& p0 : pieces[0])
+        for (auto& p1 : pieces[1])
+          for (auto& p2 : pieces[2]) {
+            const Piece* pp[3] = {&p0, &p1, &p2};
+            for (int q = C.first; q < C.first + C.count; ++q) {
+              const HPatch& o = P[q];
+              CopySeg s{};
+              s.dst_patch = i; s.src_patch = q;
+              bool ok = true;
+              int64_t vol = 1;
+              for (int d = 0; d < 3 && ok; ++d) {
+                const Piece& pc = *pp[d];
+                if (pc.mode == 1) {
+                  if (pc.src < o.lo[d] || pc.src >= o.lo[d] + o.n[d]) { ok = false; break; }
+                  s.dlo[d] = (int16_t)pc.a; s.dn[d] = (int16_t)pc.len; s.mode[d] = 1;
+                  s.sh[d] = (int16_t)(pc.src - o.lo[d]);
+                  vol *= pc.len;
+                } else {
+                  int a = std::max(pc.src, o.lo[d]), b = std::min(pc.src + pc.len, o.lo[d] + o.n[d]);
+                  if (a >= b) { ok = false; break; }
+                  int dst0 = pc.a + (a - pc.src);
+                  s.dlo[d] = (int16_t)dst0; s.dn[d] = (int16_t)(b - a); s.mode[d] = 0;
+                  s.sh[d] = (int16_t)((a - o.lo[d]) - dst0);
+                  vol *= (b - a);
+                }
+              }
+              if (!ok) continue;
+              covered += vol;
+              L.gather.push_back(s);
+            }
+          }
+      const PatchDesc& d = plan.desc[i];
+      if (covered != (int64_t)d.tn[0] * d.tn[1] * d.tn[2]) {
+        msg = fmt("patch %d: parent tile not covered by level %d", i, l - 1);
+        return AMR_ERR_NESTING;
+      }
+      L.gather_first.push_back((int)L.gather.size());
+    }
+  }
+
+  // ---- restriction segments and coverage boxes ----
+  plan.cover_first.assign(np + 1, 0);
+  std::vector<std::vector<CoverBox>> cov(np);
+  for (int l = 1; l < nlev; ++l) {
+    LevelPlan& L = plan.levels[l];
+    const LevelPlan& C = plan.levels[l - 1];
+    for (int i = L.first; i < L.first + L.count; ++i) {
+      const HPatch& f = P[i];
+      for (int q = C.first; q < C.first + C.count; ++q) {
+        const HPatch& o = P[q];
+        int lo[3], hi[3];
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = std::max(f.lo[d] / 2, o.lo[d]);
+          hi[d] = std::min((f.lo[d] + f.n[d]) / 2, o.lo[d] + o.n[d]);
+          if (lo[d] >= hi[d]) ok = false;
+        }
+        if (!ok) continue;
+        RestrictSeg r{};
+        r.fine = i; r.coarse = q;
+        CoverBox cb{};
+        for (int d = 0; d < 3; ++d) {
+          r.clo[d] = (int16_t)(lo[d] - o.lo[d]); r.cn[d] = (int16_t)(hi[d] - lo[d]);
+          cb.lo[d] = r.clo[d]; cb.n[d] = r.cn[d];
+        }
+        L.restrict_segs.push_back(r);
+        cov[q].push_back(cb);
+      }
+    }
+  }
+  for (int i = 0; i < np; ++i) {
+    plan.cover_first[i + 1] = plan.cover_first[i] + (int)cov[i].size();
+    for (auto& b : cov[i]) plan.cover.push_back(b);
+  }
+
+  // ---- flux registers (level >= 1): fine patch faces against uncovered parent cells ----
+  for (int l = 1; l < nlev; ++l) {
+    LevelPlan& L = plan.levels[l];
+    const LevelPlan& C = plan.levels[l - 1];
+    std::vector<RegFace> regs;
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side)
+        for (int i = L.first; i < L.first + L.count; ++i) {
+          const HPatch& p = P[i];
+          int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          int xf = side ? p.lo[d] + p.n[d] : p.lo[d];
+          int Cd = side ? xf / 2 : xf / 2 - 1;
+          int Nc = level_n(cfg, l - 1, d);
+          if (Cd < 0 || Cd >= Nc) {
+            if (!periodic(cfg, d)) continue;
+            Cd = ((Cd % Nc) + Nc) % Nc;
+          }
+          int a0 = p.lo[t1] / 2, A = p.n[t1] / 2, b0 = p.lo[t2] / 2, B = p.n[t2] / 2;
+          // covered by a level-l patch?
+          std::vector<unsigned char> cov2((size_t)A * B, 0);
+          for (int q = L.first; q < L.first + L.count; ++q) {
+            const HPatch& o = P[q];
+            if (2 * Cd < o.lo[d] || 2 * Cd >= o.lo[d] + o.n[d]) continue;
+            int x0 = std::max(a0, o.lo[t1] / 2), x1 = std::min(a0 + A, (o.lo[t1] + o.n[t1]) / 2);
+            int y0 = std::max(b0, o.lo[t2] / 2), y1 = std::min(b0 + B, (o.lo[t2] + o.n[t2]) / 2);
+            for (int y = y0; y < y1; ++y)
+              for (int x = x0; x < x1; ++x) cov2[(size_t)(y - b0) * A + (x - a0)] = 1;
+          }
+          std::vector<int> owner((size_t)A * B, -1);
+          for (int q = C.first; q < C.first + C.count; ++q) {
+            const HPatch& o = P[q];
+            if (Cd < o.lo[d] || Cd >= o.lo[d] + o.n[d]) continue;
+            int x0 = std::max(a0, o.lo[t1]), x1 = std::min(a0 + A, o.lo[t1] + o.n[t1]);
+            int y0 = std::max(b0, o.lo[t2]), y1 = std::min(b0 + B, o.lo[t2] + o.n[t2]);
+            for (int y = y0; y < y1; ++y)
+              for (int x = x0; x < x1; ++x) owner[(size_t)(y - b0) * A + (x - a0)] = q;
+          }
+          for (int b = 0; b < B; ++b)
+            for (int a = 0; a < A; ++a) {
+              if (cov2[(size_t)b * A + a]) continue;
+              int q = owner[(size_t)b * A + a];
+              if (q < 0) { msg = fmt("patch %d: coarse neighbour cell outside level %d", i, l - 1); return AMR_ERR_NESTING; }
+              const HPatch& o = P[q];
+              RegFace r{};
+              r.fpatch = i; r.cpatch = q;
+              r.d = (int8_t)d; r.side = (int8_t)side; r.cside = (int8_t)(side ? -1 : 1);
+              int Cc[3];
+              Cc[d] = Cd; Cc[t1] = a0 + a; Cc[t2] = b0 + b;
+              for (int k = 0; k < 3; ++k) r.cidx[k] = (int16_t)(Cc[k] - o.lo[k]);
+              r.fface[d] = (int16_t)(side ? p.n[d] : 0);
+              r.fface[t1] = (int16_t)(2 * (a0 + a) - p.lo[t1]);
+              r.fface[t2] = (int16_t)(2 * (b0 + b) - p.lo[t2]);
+              regs.push_back(r);
+            }
+        }
+    // group by coarse cell, keeping the (d, side) order inside a cell
+    std::stable_sort(regs.begin(), regs.end(), [](const RegFace& a, const RegFace& b) {
+      return std::make_tuple(a.cpatch, a.cidx[2], a.cidx[1], a.cidx[0]) <
+             std::make_tuple(b.cpatch, b.cidx[2], b.cidx[1], b.cidx[0]);
+    });
+    L.regs = regs;
+    L.reflux_first.clear();
+    for (size_t e = 0; e < regs.size(); ++e) {
+      if (e == 0 || regs[e].cpatch != regs[e - 1].cpatch || regs[e].cidx[0] != regs[e - 1].cidx[0] ||
+          regs[e].cidx[1] != regs[e - 1].cidx[1] || regs[e].cidx[2] != regs[e - 1].cidx[2])
+        L.reflux_first.push_back((int)e);
+    }
+    L.reflux_first.push_back((int)regs.size());
+  }
+  return AMR_OK;
+}
+
+}  // namespace amr

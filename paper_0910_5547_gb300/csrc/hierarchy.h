@@ -1,0 +1,60 @@
+// hierarchy.h -- host-side planning of one patch hierarchy: validation and
+// every launch table the kernels consume (stage work items, ghost copies,
+// prolongation boxes, parent-tile gathers, restriction, flux registers,
+// coverage).  Pure C++, no CUDA calls: usable on a host without a GPU.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/amr.h"
+#include "amr_types.h"
+
+namespace amr {
+
+struct HPatch {
+  int level;
+  int lo[3];
+  int n[3];
+};
+
+struct LevelPlan {
+  int first = 0, count = 0;                  // patch range [first, first + count)
+  std::vector<StageItem> items;              // stage work items, grouped by patch
+  std::vector<int> item_first;               // per patch of the level: first item (size count + 1)
+  std::vector<CopySeg> ghost;                // sibling copies + outflow boundary, grouped by dst patch
+  std::vector<int> ghost_first;              // per patch (size count + 1)
+  std::vector<ProlongBox> prolong;           // fine ghosts from the parent tile (level >= 1)
+  std::vector<int> prolong_first;
+  std::vector<CopySeg> gather;               // parent-tile gathers (level >= 1), grouped by fine patch
+  std::vector<int> gather_first;
+  std::vector<RestrictSeg> restrict_segs;    // this level -> parent (level >= 1)
+  std::vector<RegFace> regs;                 // coarse-fine faces of this level (level >= 1), sorted by coarse cell
+  std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell
+  int64_t cells = 0;
+};
+
+struct Plan {
+  amr_config cfg{};
+  int nvar = 5;
+  std::vector<HPatch> patches;
+  std::vector<PatchDesc> desc;
+  std::vector<LevelPlan> levels;
+  std::vector<CoverBox> cover;               // covered boxes, grouped by patch
+  std::vector<int> cover_first;              // size npatch + 1
+  int64_t arena_elems = 0;                   // elements of one state array (U, U1, Uold)
+  int64_t tile_elems = 0;                    // elements of the parent-tile buffer
+  int64_t packed_elems = 0;                  // doubles of the packed interior state
+  std::vector<int64_t> packed_off;           // per patch offset (doubles) in the packed state
+};
+
+// Validation only (no allocation of plan tables).  Returns AMR_OK or an error
+// status with a message.
+amr_status validate_config(const amr_config& cfg, std::string& msg);
+amr_status validate_patches(const amr_config& cfg, const std::vector<HPatch>& P, std::string& msg);
+
+// Validate and build every table.  `align` = element alignment of patch
+// offsets (e.g. 64 for 256-byte alignment of FP32 arrays).
+amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan,
+                      std::string& msg);
+
+}  // namespace amr

@@ -1,0 +1,55 @@
+// ops.h -- type-erased launchers of the kernels of one (precision, physics)
+// instantiation.  The host orchestration (amr_api.cu) talks to the kernels only
+// through this interface; each ops_*.cu translation unit instantiates one.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "amr_types.h"
+
+namespace amr {
+
+struct ChunkDesc;
+
+struct PhysParams {  // host copy of the physics constants
+  double gamma, theta, ch_fixed;
+  int llf;
+};
+
+struct OpsBase {
+  virtual ~OpsBase() {}
+  virtual size_t elem_size() const = 0;
+  // fused RK2 stage over items [0, nitems) of `items` (device pointer)
+  virtual cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
+                            const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3], int grid) = 0;
+  virtual cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) = 0;
+  virtual cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,
+                             const void* U, const void* Uold, double alpha) = 0;
+  virtual cudaError_t prolong(cudaStream_t s, const ProlongBox* boxes, int nbox, const PatchDesc* desc,
+                              const void* tile, void* arena) = 0;
+  virtual cudaError_t restrict_(cudaStream_t s, const RestrictSeg* segs, int nseg, const PatchDesc* desc, void* U) = 0;
+  virtual cudaError_t reg_coarse(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc,
+                                 const void* Uin, double* R, StepParams* prm, int level, int stage) = 0;
+  virtual cudaError_t reg_fine(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc,
+                               const void* Uin, double* R, StepParams* prm, int level) = 0;
+  virtual cudaError_t reflux(cudaStream_t s, const RegFace* regs, const int* first, int nuniq, int nreg,
+                             const PatchDesc* desc, const double* R, void* U, const double dxc[3]) = 0;
+  virtual cudaError_t speed(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                            const void* U, StepParams* prm, const double dx0[3]) = 0;
+  virtual cudaError_t totals(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                             const void* U, const CoverBox* cover, const int* cover_first, const double* level_vol,
+                             double* partial, double* out) = 0;
+  virtual cudaError_t pack_in(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                              const int64_t* packed_off, const double* src, void* U, int prim, StepParams* prm) = 0;
+  virtual cudaError_t pack_out(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                               const int64_t* packed_off, const void* U, double* dst) = 0;
+};
+
+// factories, one per translation unit
+OpsBase* make_ops_f64_euler(const PhysParams&);
+OpsBase* make_ops_f32_euler(const PhysParams&);
+OpsBase* make_ops_f64_mhd(const PhysParams&);
+OpsBase* make_ops_f32_mhd(const PhysParams&);
+
+}  // namespace amr

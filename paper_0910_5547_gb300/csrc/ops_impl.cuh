@@ -1,0 +1,140 @@
+// ops_impl.cuh -- Ops<T, NV>: launch configuration of every kernel for one
+// (precision, physics) pair.  Included by the four ops_*.cu units only.
+#pragma once
+#include "kernels.cuh"
+#include "ops.h"
+
+namespace amr {
+
+template <typename T, int NV>
+struct Ops final : OpsBase {
+  Phys<T> ph{};
+  double gamma = 1.4;
+  int max_stage_ctas = 0;
+
+  explicit Ops(const PhysParams& p) {
+    gamma = p.gamma;
+    ph.gamma = (T)p.gamma;
+    ph.gm1 = (T)(p.gamma - 1.0);
+    ph.ggm1 = (T)(p.gamma * (p.gamma - 1.0));
+    ph.theta = (T)p.theta;
+    ph.llf = p.llf;
+    ph.ch = ph.ch2 = ph.half_inv_ch = T(0);
+    cudaFuncSetAttribute(stage_kernel<T, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV>());
+    cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV>());
+  }
+
+  size_t elem_size() const override { return sizeof(T); }
+
+  cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
+                    const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3], int grid) override {
+    if (nitems <= 0) return cudaSuccess;
+    StageArgs<T> a;
+    a.desc = desc;
+    a.items = items;
+    a.nitems = nitems;
+    a.Uin = static_cast<const T*>(Uin);
+    a.Uout = static_cast<T*>(Uout);
+    a.params = prm;
+    a.dt_scale = 1.0 / (double)(1 << level);
+    a.idx = (T)(1.0 / dx[0]);
+    a.idy = (T)(1.0 / dx[1]);
+    a.idz = (T)(1.0 / dx[2]);
+    a.ph = ph;
+    const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
+    const size_t sm = stage_smem_bytes<T, NV>();
+    if (stage == 1) stage_kernel<T, NV, 1><<<g, kStageThreads, sm, s>>>(a);
+    else stage_kernel<T, NV, 2><<<g, kStageThreads, sm, s>>>(a);
+    return cudaGetLastError();
+  }
+
+  static int grid_for(int n) { return n < 65535 ? n : 65535; }
+
+  cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) override {
+    if (nseg <= 0) return cudaSuccess;
+    copy_kernel<T, NV, false><<<grid_for(nseg), 128, 0, s>>>(segs, nseg, desc, static_cast<T*>(arena),
+                                                             static_cast<const T*>(arena), nullptr, T(0));
+    return cudaGetLastError();
+  }
+
+  cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,
+                     const void* U, const void* Uold, double alpha) override {
+    if (nseg <= 0) return cudaSuccess;
+    copy_kernel<T, NV, true><<<grid_for(nseg), 128, 0, s>>>(segs, nseg, desc, static_cast<T*>(tile),
+                                                            static_cast<const T*>(U), static_cast<const T*>(Uold),
+                                                            (T)alpha);
+    return cudaGetLastError();
+  }
+
+  cudaError_t prolong(cudaStream_t s, const ProlongBox* boxes, int nbox, const PatchDesc* desc, const void* tile,
+                      void* arena) override {
+    if (nbox <= 0) return cudaSuccess;
+    prolong_kernel<T, NV><<<grid_for(nbox), 128, 0, s>>>(boxes, nbox, desc, static_cast<const T*>(tile),
+                                                         static_cast<T*>(arena));
+    return cudaGetLastError();
+  }
+
+  cudaError_t restrict_(cudaStream_t s, const RestrictSeg* segs, int nseg, const PatchDesc* desc, void* U) override {
+    if (nseg <= 0) return cudaSuccess;
+    restrict_kernel<T, NV><<<grid_for(nseg), 128, 0, s>>>(segs, nseg, desc, static_cast<T*>(U));
+    return cudaGetLastError();
+  }
+
+  cudaError_t reg_coarse(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc, const void* Uin,
+                         double* R, StepParams* prm, int level, int stage) override {
+    if (nreg <= 0) return cudaSuccess;
+    reg_coarse_kernel<T, NV><<<grid_for((nreg + 127) / 128), 128, 0, s>>>(
+        regs, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level), ph, stage);
+    return cudaGetLastError();
+  }
+
+  cudaError_t reg_fine(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc, const void* Uin,
+                       double* R, StepParams* prm, int level) override {
+    if (nreg <= 0) return cudaSuccess;
+    reg_fine_kernel<T, NV><<<grid_for((nreg + 127) / 128), 128, 0, s>>>(
+        regs, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level), ph);
+    return cudaGetLastError();
+  }
+
+  cudaError_t reflux(cudaStream_t s, const RegFace* regs, const int* first, int nuniq, int nreg, const PatchDesc* desc,
+                     const double* R, void* U, const double dxc[3]) override {
+    if (nuniq <= 0) return cudaSuccess;
+    reflux_kernel<T, NV><<<grid_for((nuniq + 127) / 128), 128, 0, s>>>(regs, first, nuniq, nreg, desc, R,
+                                                                        static_cast<T*>(U), dxc[0], dxc[1], dxc[2]);
+    return cudaGetLastError();
+  }
+
+  cudaError_t speed(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const void* U,
+                    StepParams* prm, const double dx0[3]) override {
+    speed_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, static_cast<const T*>(U), prm,
+                                                         1.0 / dx0[0], 1.0 / dx0[1], 1.0 / dx0[2], ph);
+    return cudaGetLastError();
+  }
+
+  cudaError_t totals(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const void* U,
+                     const CoverBox* cover, const int* cover_first, const double* level_vol, double* partial,
+                     double* out) override {
+    totals_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, static_cast<const T*>(U), cover,
+                                                          cover_first, level_vol, partial);
+    totals_final_kernel<NV><<<1, 32, 0, s>>>(partial, nchunk, out);
+    return cudaGetLastError();
+  }
+
+  cudaError_t pack_in(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                      const int64_t* packed_off, const double* src, void* U, int prim, StepParams* prm) override {
+    pack_in_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, packed_off, src,
+                                                           static_cast<T*>(U), prim, gamma, prm);
+    return cudaGetLastError();
+  }
+
+  cudaError_t pack_out(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                       const int64_t* packed_off, const void* U, double* dst) override {
+    pack_out_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, packed_off,
+                                                            static_cast<const T*>(U), dst);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace amr

@@ -1,0 +1,168 @@
+// physics.cuh -- per-cell and per-face device arithmetic of the method:
+// primitive recovery, generalised-minmod PLM (Sec. 4), physical fluxes of the
+// Euler (Sec. 4) and GLM-MHD (Sec. 7.1) systems, and the HLL / LLF interface
+// flux.  Reconstructed variables W = (rho, vx, vy, vz, e [, Bx, By, Bz, psi]),
+// e the specific internal energy, p = (gamma - 1) rho e.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "amr_types.h"
+
+namespace amr {
+
+template <typename T>
+struct Phys {
+  T gamma;     // adiabatic index
+  T gm1;       // gamma - 1
+  T ggm1;      // gamma * (gamma - 1): c_s^2 = gamma p / rho = ggm1 * e
+  T theta;     // generalised minmod parameter
+  T ch;        // GLM cleaning speed (MHD)
+  T ch2;       // ch^2
+  T half_inv_ch;  // 1 / (2 ch)
+  int llf;     // 1: the printed Sec. 4 flux with lambda_0; 0: two-wave HLL
+};
+
+template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
+template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double dabs(double x) { return fabs(x); }
+__device__ __forceinline__ float drcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double drcp(double x) { return 1.0 / x; }
+
+// Half of the limited slope of cell i from (w_{i-1}, w_i, w_{i+1}):
+// 1/2 minmod(theta (w_i - w_{i-1}), theta (w_{i+1} - w_i), (w_{i+1} - w_{i-1}) / 2),
+// where minmod keeps the smallest magnitude if all three share a sign, else 0.
+template <typename T>
+__device__ __forceinline__ T half_slope(T wm, T w0, T wp, T theta) {
+  T a = w0 - wm, b = wp - w0;
+  T c = (wp - wm) * T(0.5);
+  T m = dmin(dmin(dabs(a * theta), dabs(b * theta)), dabs(c));
+  T s = (a * b > T(0)) ? (a > T(0) ? m : -m) : T(0);
+  return T(0.5) * s;
+}
+
+// Conserved -> reconstructed variables; returns false for rho <= 0, e <= 0 or NaN.
+template <typename T, int NV>
+__device__ __forceinline__ bool cons_to_prim(const T* u, T* w) {
+  T rho = u[0];
+  T r = drcp(rho);
+  T vx = u[1] * r, vy = u[2] * r, vz = u[3] * r;
+  T E = u[4];
+  if (NV == 9) E = E - T(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+  T e = E * r - T(0.5) * (vx * vx + vy * vy + vz * vz);
+  w[0] = rho; w[1] = vx; w[2] = vy; w[3] = vz; w[4] = e;
+  if (NV == 9) { w[5] = u[5]; w[6] = u[6]; w[7] = u[7]; w[8] = u[8]; }
+  return (rho > T(0)) && (e > T(0));
+}
+
+// Conserved vector, physical flux along D, normal velocity and signal speed of
+// a reconstructed state (Sec. 4 U, F^x/F^y/F^z; Sec. 7.1 for NV == 9 with the
+// induction entries F^d_{B_k} = v_d B_k - v_k B_d).  For MHD the caller has
+// already replaced B_D by the resolved normal field; F[5+D] and F[8] are left
+// for the caller (Dedner pair).
+template <typename T, int NV, int D>
+__device__ __forceinline__ void state_flux(const T* w, const Phys<T>& ph, T* U, T* F, T& c) {
+  const T rho = w[0], vx = w[1], vy = w[2], vz = w[3], e = w[4];
+  const T vn = w[1 + D];
+  const T p = ph.gm1 * rho * e;
+  const T v2 = vx * vx + vy * vy + vz * vz;
+  U[0] = rho;
+  U[1] = rho * vx; U[2] = rho * vy; U[3] = rho * vz;
+  U[4] = rho * (T(0.5) * v2 + e);
+  if (NV == 5) {
+    c = dsqrt(ph.ggm1 * e);
+    F[0] = U[1 + D];
+    F[1] = U[1] * vn; F[2] = U[2] * vn; F[3] = U[3] * vn;
+    F[1 + D] += p;
+    F[4] = (U[4] + p) * vn;
+  } else {
+    const T Bx = w[5], By = w[6], Bz = w[7];
+    const T Bn = w[5 + D];
+    const T B2 = Bx * Bx + By * By + Bz * Bz;
+    const T pt = p + T(0.5) * B2;
+    U[4] += T(0.5) * B2;
+    U[5] = Bx; U[6] = By; U[7] = Bz; U[8] = w[8];
+    // fast magnetosonic speed along D
+    const T r = drcp(rho);
+    const T a2 = ph.ggm1 * e;
+    const T b2 = B2 * r;
+    const T bn2 = Bn * Bn * r;
+    const T s = a2 + b2;
+    const T disc = dmax(s * s - T(4) * a2 * bn2, T(0));
+    c = dsqrt(T(0.5) * (s + dsqrt(disc)));
+    const T Bv = Bx * vx + By * vy + Bz * vz;
+    F[0] = U[1 + D];
+    F[1] = U[1] * vn - Bx * Bn; F[2] = U[2] * vn - By * Bn; F[3] = U[3] * vn - Bz * Bn;
+    F[1 + D] += pt;
+    F[4] = (U[4] + pt) * vn - Bn * Bv;
+    F[5] = vn * Bx - vx * Bn; F[6] = vn * By - vy * Bn; F[7] = vn * Bz - vz * Bn;
+    F[8] = T(0);
+  }
+}
+
+// Interface flux along D from reconstructed left/right states (copied: the MHD
+// branch overwrites the normal field with the Dedner-resolved value).
+template <typename T, int NV, int D>
+__device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
+  T Bm = T(0), psim = T(0);
+  if (NV == 9) {
+    const T Bl = wl[5 + D], Br = wr[5 + D];
+    Bm = T(0.5) * (Bl + Br) - (wr[8] - wl[8]) * ph.half_inv_ch;
+    psim = T(0.5) * (wl[8] + wr[8]) - T(0.5) * ph.ch * (Br - Bl);
+    wl[5 + D] = Bm;
+    wr[5 + D] = Bm;
+  }
+  T Ul[NV], Ur[NV], Fl[NV], Fr[NV], cl, cr;
+  state_flux<T, NV, D>(wl, ph, Ul, Fl, cl);
+  state_flux<T, NV, D>(wr, ph, Ur, Fr, cr);
+  const T vl = wl[1 + D], vr = wr[1 + D];
+  if (ph.llf) {
+    const T a = dmax(dmax(dmax(T(0), vl + cl), vr + cr), dmax(cl - vl, cr - vr));
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (Fl[k] + Fr[k] - a * (Ur[k] - Ul[k]));
+  } else {
+    const T SL = dmin(dmin(T(0), vl - cl), vr - cr);
+    const T SR = dmax(dmax(T(0), vl + cl), vr + cr);
+    const T den = SR - SL;
+    if (den > T(0)) {
+      const T inv = drcp(den);
+      const T slsr = SL * SR;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) F[k] = (SR * Fl[k] - SL * Fr[k] + slsr * (Ur[k] - Ul[k])) * inv;
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (Fl[k] + Fr[k]);
+    }
+  }
+  if (NV == 9) {
+    F[5 + D] = psim;
+    F[8] = ph.ch2 * Bm;
+  }
+}
+
+// Interface flux along D at the face between cells (c1 - e_D) and c1 of an
+// array holding conserved variables, stencil c1-2 .. c1+1 (used by the flux
+// register kernels: same arithmetic as the stage kernel's faces).
+template <typename T, int NV, int D>
+__device__ __forceinline__ void face_flux_from_array(const T* base, int64_t vstride, int64_t c1, int64_t step,
+                                                     const Phys<T>& ph, T* F) {
+  T w[4][NV];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    T u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = base[v * vstride + c1 + (q - 2) * step];
+    cons_to_prim<T, NV>(u, w[q]);
+  }
+  T wl[NV], wr[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    wl[v] = w[1][v] + half_slope(w[0][v], w[1][v], w[2][v], ph.theta);
+    wr[v] = w[2][v] - half_slope(w[1][v], w[2][v], w[3][v], ph.theta);
+  }
+  riemann<T, NV, D>(wl, wr, ph, F);
+}
+
+}  // namespace amr

@@ -1,0 +1,249 @@
+"""ctypes binding of the C ABI in include/amr.h (argument marshalling only).
+
+Every function has the name of the C entry point it wraps.  Non-OK statuses
+raise ``AmrError`` (carrying ``.status`` and the library's message).  The
+shared library must have been built (``paper_0910_5547_gb300.build.build()``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+AMR_OK = 0
+AMR_ERR_ARG = -1
+AMR_ERR_NESTING = -2
+AMR_ERR_CUDA = -3
+AMR_ERR_NONPHYSICAL = -4
+AMR_ERR_TIMEOUT = -5
+AMR_ERR_STATE = -6
+AMR_FP64, AMR_FP32 = 0, 1
+AMR_HLL, AMR_LLF = 0, 1
+AMR_BC_OUTFLOW, AMR_BC_PERIODIC = 0, 1
+AMR_STATE_CONSERVED, AMR_STATE_PRIMITIVE = 0, 1
+
+STATUS_NAMES = {0: "AMR_OK", -1: "AMR_ERR_ARG", -2: "AMR_ERR_NESTING", -3: "AMR_ERR_CUDA",
+                -4: "AMR_ERR_NONPHYSICAL", -5: "AMR_ERR_TIMEOUT", -6: "AMR_ERR_STATE"}
+
+# every entry point declared in include/amr.h
+EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_patches", "amr_set_state",
+           "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
+           "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
+           "amr_destroy", "amr_set_timing", "amr_get_timing"]
+TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
+
+
+class AmrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+        self.msg = msg
+
+
+class amr_config(ctypes.Structure):
+    _fields_ = [
+        ("nvar", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("riemann", ctypes.c_int),
+        ("gamma", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("base_n", ctypes.c_int * 3),
+        ("domain_lo", ctypes.c_double * 3),
+        ("domain_hi", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 6),
+        ("max_level", ctypes.c_int),
+        ("ref_ratio", ctypes.c_int),
+        ("ch", ctypes.c_double),
+        ("batched", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class amr_patch(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("lo", ctypes.c_int * 3), ("n", ctypes.c_int * 3)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libamr_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"native library {path} is missing: run paper_0910_5547_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.amr_default_config.argtypes = [ctypes.POINTER(amr_config)]
+    L.amr_default_config.restype = None
+    L.amr_create.argtypes = [ctypes.POINTER(amr_config), ctypes.POINTER(H)]
+    L.amr_validate_patches.argtypes = [ctypes.POINTER(amr_config), ctypes.c_int, ctypes.POINTER(amr_patch),
+                                       ctypes.c_char_p, ctypes.c_int]
+    L.amr_set_patches.argtypes = [H, ctypes.c_int, ctypes.POINTER(amr_patch), ctypes.POINTER(dp), ctypes.c_int]
+    L.amr_set_state.argtypes = [H, dp, ctypes.c_int]
+    L.amr_state_size.argtypes = [H]
+    L.amr_state_size.restype = ctypes.c_longlong
+    L.amr_step.argtypes = [H, ctypes.c_double, dp]
+    L.amr_cfl_dt.argtypes = [H, dp]
+    L.amr_get_state.argtypes = [H, ctypes.c_int, dp]
+    L.amr_get_state_all.argtypes = [H, dp]
+    L.amr_conserved_totals.argtypes = [H, dp]
+    L.amr_check.argtypes = [H]
+    L.amr_kernel_launches.argtypes = [H]
+    L.amr_kernel_launches.restype = ctypes.c_longlong
+    L.amr_last_error.argtypes = [H]
+    L.amr_last_error.restype = ctypes.c_char_p
+    L.amr_global_error.argtypes = []
+    L.amr_global_error.restype = ctypes.c_char_p
+    L.amr_destroy.argtypes = [H]
+    L.amr_destroy.restype = None
+    L.amr_set_timing.argtypes = [H, ctypes.c_int]
+    L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    for name in ("amr_create", "amr_validate_patches", "amr_set_patches", "amr_set_state", "amr_step",
+                 "amr_cfl_dt", "amr_get_state", "amr_get_state_all", "amr_conserved_totals", "amr_check",
+                 "amr_set_timing", "amr_get_timing"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(h, st: int):
+    if st != AMR_OK:
+        L = load()
+        msg = (L.amr_last_error(h) if h else L.amr_global_error()) or b""
+        raise AmrError(st, msg.decode())
+
+
+def amr_default_config(**overrides) -> amr_config:
+    c = amr_config()
+    load().amr_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        if isinstance(getattr(c, k), ctypes.Array):
+            getattr(c, k)[:] = list(v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def make_patches(patches: Sequence) -> ctypes.Array:
+    arr = (amr_patch * len(patches))()
+    for i, p in enumerate(patches):
+        arr[i].level = int(p.level)
+        arr[i].lo[:] = [int(x) for x in p.lo]
+        arr[i].n[:] = [int(x) for x in p.n]
+    return arr
+
+
+def amr_create(cfg: amr_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(None, load().amr_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def amr_validate_patches(cfg: amr_config, patches: Sequence):
+    """Returns (status, message); host only, needs no GPU."""
+    arr = make_patches(patches)
+    buf = ctypes.create_string_buffer(512)
+    st = load().amr_validate_patches(ctypes.byref(cfg), len(patches), arr, buf, 512)
+    return st, buf.value.decode()
+
+
+def amr_set_patches(h, patches: Sequence, states: Sequence[np.ndarray], kind: int = AMR_STATE_PRIMITIVE):
+    arr = make_patches(patches)
+    keep = [np.ascontiguousarray(s, dtype=np.float64) for s in states]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * len(keep))(*[_dp(a) for a in keep])
+    _check(h, load().amr_set_patches(h, len(patches), arr, ptrs, kind))
+
+
+def amr_set_state(h, packed: np.ndarray, kind: int = AMR_STATE_CONSERVED):
+    assert packed.dtype == np.float64 and packed.flags.c_contiguous
+    _check(h, load().amr_set_state(h, _dp(packed), kind))
+
+
+def amr_state_size(h) -> int:
+    return int(load().amr_state_size(h))
+
+
+def amr_step(h, dt: float = 0.0, sync: bool = True) -> float:
+    """One coarse step; returns the dt taken when sync (else nan)."""
+    if sync:
+        used = ctypes.c_double(0.0)
+        _check(h, load().amr_step(h, dt, ctypes.byref(used)))
+        return used.value
+    _check(h, load().amr_step(h, dt, None))
+    return float("nan")
+
+
+def amr_cfl_dt(h) -> float:
+    dt = ctypes.c_double(0.0)
+    _check(h, load().amr_cfl_dt(h, ctypes.byref(dt)))
+    return dt.value
+
+
+def amr_get_state(h, patch: int, shape) -> np.ndarray:
+    out = np.empty(shape, dtype=np.float64)
+    _check(h, load().amr_get_state(h, patch, _dp(out)))
+    return out
+
+
+def amr_get_state_all(h, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty(amr_state_size(h), dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(h, load().amr_get_state_all(h, _dp(out)))
+    return out
+
+
+def amr_conserved_totals(h, nvar: int) -> np.ndarray:
+    out = np.zeros(nvar, dtype=np.float64)
+    _check(h, load().amr_conserved_totals(h, _dp(out)))
+    return out
+
+
+def amr_check(h):
+    _check(h, load().amr_check(h))
+
+
+def amr_kernel_launches(h) -> int:
+    return int(load().amr_kernel_launches(h))
+
+
+def amr_last_error(h) -> str:
+    return (load().amr_last_error(h) or b"").decode()
+
+
+def amr_set_timing(h, on: bool):
+    _check(h, load().amr_set_timing(h, int(on)))
+
+
+def amr_get_timing(h) -> dict:
+    """{class: (total_ms, launches)} since timing was switched on (then reset)."""
+    n = len(TIMING_CLASSES)
+    ms = np.zeros(n)
+    cnt = (ctypes.c_longlong * n)()
+    _check(h, load().amr_get_timing(h, _dp(ms), cnt, n))
+    return {c: (float(ms[i]), int(cnt[i])) for i, c in enumerate(TIMING_CLASSES)}
+
+
+def amr_destroy(h):
+    if h:
+        load().amr_destroy(h)

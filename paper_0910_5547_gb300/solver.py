@@ -1,0 +1,97 @@
+"""Convenience wrapper around the C ABI: one ``Solver`` owns one amr_handle.
+
+Argument marshalling only -- every step of the method runs in the native
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+from typing import List, Sequence
+
+import numpy as np
+
+from . import native as N
+
+
+class Solver:
+    """A patch hierarchy resident on the GPU.
+
+    ``patches`` are objects with ``level``, ``lo`` and ``n``; ``state`` is a list
+    of float64 arrays (nvar, nz, ny, nx), primitive (default) or conserved.
+    """
+
+    def __init__(self, patches: Sequence, state: Sequence[np.ndarray], *, nvar=5, precision="fp64",
+                 gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(0,) * 6, max_level=None,
+                 riemann="hll", ch=0.0, batched=True, use_graph=True, domain_lo=(0.0, 0.0, 0.0),
+                 domain_hi=(1.0, 1.0, 1.0), kind=N.AMR_STATE_PRIMITIVE, stream=None):
+        self.patches = list(patches)
+        self.nvar = nvar
+        if max_level is None:
+            max_level = max(p.level for p in self.patches)
+        self.cfg = N.amr_default_config(
+            nvar=nvar, precision=N.AMR_FP32 if precision == "fp32" else N.AMR_FP64,
+            riemann=N.AMR_LLF if riemann == "llf" else N.AMR_HLL, gamma=gamma, theta=theta, cfl=cfl,
+            base_n=base_n, bc=bc, max_level=max_level, ch=ch, batched=int(batched), use_graph=int(use_graph),
+            domain_lo=domain_lo, domain_hi=domain_hi, cuda_stream=stream)
+        self.h = N.amr_create(self.cfg)
+        N.amr_set_patches(self.h, self.patches, state, kind)
+        self.offsets = np.cumsum([0] + [nvar * p.n[0] * p.n[1] * p.n[2] for p in self.patches])
+
+    @classmethod
+    def from_problem(cls, pb, **kw):
+        kw.setdefault("nvar", pb.nvar)
+        kw.setdefault("gamma", pb.gamma)
+        kw.setdefault("base_n", pb.base_n)
+        kw.setdefault("bc", pb.bc)
+        kw.setdefault("max_level", pb.max_level)
+        kw.setdefault("domain_lo", pb.domain_lo)
+        kw.setdefault("domain_hi", pb.domain_hi)
+        return cls(pb.patches, pb.prim, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.amr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, dt: float = 0.0, sync: bool = True) -> float:
+        return N.amr_step(self.h, dt, sync)
+
+    def cfl_dt(self) -> float:
+        return N.amr_cfl_dt(self.h)
+
+    def run_to(self, t_end: float, max_steps: int = 100000) -> int:
+        t, k = 0.0, 0
+        while t < t_end * (1 - 1e-14) and k < max_steps:
+            dt = min(self.cfl_dt(), t_end - t)
+            self.step(dt)
+            t += dt
+            k += 1
+        return k
+
+    def state_all(self) -> np.ndarray:
+        return N.amr_get_state_all(self.h)
+
+    def cons(self, i: int) -> np.ndarray:
+        p = self.patches[i]
+        return N.amr_get_state(self.h, i, (self.nvar, p.n[2], p.n[1], p.n[0]))
+
+    def all_cons(self) -> List[np.ndarray]:
+        flat = self.state_all()
+        out = []
+        for i, p in enumerate(self.patches):
+            out.append(flat[self.offsets[i]:self.offsets[i + 1]].reshape(self.nvar, p.n[2], p.n[1], p.n[0]))
+        return out
+
+    def set_state(self, packed: np.ndarray, kind=N.AMR_STATE_CONSERVED):
+        N.amr_set_state(self.h, packed, kind)
+
+    def totals(self) -> np.ndarray:
+        return N.amr_conserved_totals(self.h, self.nvar)
+
+    def check(self):
+        N.amr_check(self.h)
+
+    def launches(self) -> int:
+        return N.amr_kernel_launches(self.h)
