@@ -1,9 +1,13 @@
 """Error metrics used by the GPU parity tests.
 
 Per conserved variable v, over all cells of all patches weighted by cell
-volume:  L1 rel = sum |U - U_ref| dV / sum |U_ref| dV, where a variable whose
-reference norm is below 1e-12 of the density norm is normalised by the density
-norm instead;  max rel = max |U - U_ref| / max |U_ref| (same fallback).
+volume:  L1 rel = sum |U - U_ref| dV / S_v,  max rel = max |U - U_ref| / M_v.
+S_v (M_v) is the L1 norm (max) of the variable itself for rho and rho E; for a
+component of a vector (momentum, magnetic field) it is the norm of the whole
+vector (sum over its three components), so that a component that is nearly
+zero in a given problem (e.g. z-momentum of a flow without z-motion) is
+measured against the vector it belongs to, independent of the axes; psi is
+measured against the magnetic-field norm.
 """
 import numpy as np
 
@@ -26,10 +30,16 @@ def errors(got, ref, patches):
         den += np.abs(r).reshape(nv, -1).sum(axis=1) * vol
         mx = np.maximum(mx, d.max(axis=1))
         ref_mx = np.maximum(ref_mx, np.abs(r).reshape(nv, -1).max(axis=1))
-    small = den < 1e-12 * den[0]
-    den[small] = den[0]
-    ref_mx[ref_mx < 1e-12 * ref_mx[0]] = ref_mx[0]
-    return num / den, mx / ref_mx
+    S = den.copy()
+    M = ref_mx.copy()
+    S[1:4] = den[1:4].sum()
+    M[1:4] = ref_mx[1:4].max()
+    if nv == 9:
+        S[5:9] = den[5:8].sum()
+        M[5:9] = ref_mx[5:8].max()
+    S[S < 1e-12 * S[0]] = S[0]
+    M[M < 1e-12 * M[0]] = M[0]
+    return num / S, mx / M
 
 
 def assert_parity(got, ref, patches, precision, label=""):
