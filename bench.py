@@ -186,12 +186,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--only", default="", help="comma list of phases to run: fp32,fp64,e2e (default: all)")
+    ap.add_argument("--only", default="",
+                    help="comma list of phases: fp32,tiled,fp64,plain,e2e (default: all)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -215,7 +216,9 @@ def main():
         dist.barrier()
 
     import amr_inputs as ai
-    pb = ai.kelvin_helmholtz(N=N, tile=TILE)
+    phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e"}
+    single = ai.kelvin_helmholtz(N=N, tile=None)          # one 256^3 patch
+    tiled = ai.kelvin_helmholtz(N=N, tile=TILE) if phases & {"tiled", "plain"} else None
     cells = N ** 3
     stream = torch.cuda.Stream()
 
@@ -230,8 +233,17 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # ---- headline: batched FP32, graph replay, CFL every step ----
-    s = make_solver(pb, "fp32", True, True, stream)
+    def rate(pb, precision, batched, graph, steps):
+        so = make_solver(pb, precision, batched, graph, stream)
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        t = timed_steps(torch, so, stream, steps)
+        so.check()
+        so.close()
+        return ws * cells * steps / max_over_ranks(t)
+
+    # ---- headline: single-patch batched FP32, graph replay, CFL every step ----
+    s = make_solver(single, "fp32", True, True, stream)
     for _ in range(args.warmup):
         s.step(0.0, sync=False)
     torch.cuda.synchronize()
@@ -246,7 +258,7 @@ def main():
     elapsed = max_over_ranks(elapsed)
     value = ws * cells * args.steps / elapsed
 
-    # ---- per-kernel event timing (eager launches, same solver) ----
+    # ---- per-kernel event timing (eager launches, same solver and state) ----
     ksteps = max(3, min(args.steps, 20))
     NV.amr_set_timing(s.h, True)
     for _ in range(ksteps):
@@ -262,46 +274,44 @@ def main():
     step_kernel_ms = {k: round(v[0] / ksteps, 4) for k, v in tm.items() if v[1]}
     s.close()
 
-    # ---- batched FP64 and plain per-patch FP64 ----
-    def rate(precision, batched, graph, steps):
-        so = make_solver(pb, precision, batched, graph, stream)
-        for _ in range(2):
-            so.step(0.0, sync=False)
-        t = timed_steps(torch, so, stream, steps)
-        so.check()
-        so.close()
-        return cells * steps / t
-
-    phases = set(args.only.split(",")) if args.only else {"fp32", "fp64", "e2e"}
+    extra = {}
     k64 = max(3, args.steps // 10)
-    fp64_batched = rate("fp64", True, True, k64) if "fp64" in phases else None
-    fp64_plain = rate("fp64", False, False, k64) if "fp64" in phases else None
+    if "tiled" in phases:
+        extra["fp32_tiled_512"] = {"value": rate(tiled, "fp32", True, True, args.steps), "unit": UNIT,
+                                   "workload": "same box as 512 patches of 32^3, batched launches + graph"}
+    if "fp64" in phases:
+        extra["fp64_batched"] = {"value": rate(single, "fp64", True, True, k64), "unit": UNIT, "steps": k64,
+                                 "workload": "single 256^3 patch, batched + graph"}
+    if "plain" in phases:
+        extra["fp64_plain"] = {"value": rate(tiled, "fp64", False, False, k64), "unit": UNIT, "steps": k64,
+                               "workload": "512 patches of 32^3, one stage-kernel and ghost-copy launch per patch, "
+                                           "no graph"}
+        if "fp32_tiled_512" in extra:
+            extra["batched_fp32_over_plain_fp64"] = extra["fp32_tiled_512"]["value"] / extra["fp64_plain"]["value"]
 
-    # ---- end to end through the C ABI with pinned host buffers ----
-    if "e2e" not in phases:
-        if rank == 0:
-            print(json.dumps({"value": value, "roofline_achieved_gbs": achieved, "step_kernel_ms": step_kernel_ms}))
-        return
-    s = make_solver(pb, "fp32", True, True, stream)
-    nstate = NV.amr_state_size(s.h)
-    h_in = torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy()
-    h_out = torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy()
-    h_in[:] = s.state_all()
-    ke = max(3, min(args.steps, 10))
-    NV.amr_set_state(s.h, h_in, NV.AMR_STATE_CONSERVED)
-    s.step(0.0, sync=False)
-    NV.amr_get_state_all(s.h, h_out)
-    barrier()
-    t = time.perf_counter()
-    for _ in range(ke):
+    e2e = None
+    if "e2e" in phases:
+        s = make_solver(single, "fp32", True, True, stream)
+        nstate = NV.amr_state_size(s.h)
+        h_in = torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy()
+        h_out = torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy()
+        h_in[:] = s.state_all()
+        ke = max(3, min(args.steps, 10))
         NV.amr_set_state(s.h, h_in, NV.AMR_STATE_CONSERVED)
         s.step(0.0, sync=False)
         NV.amr_get_state_all(s.h, h_out)
-    e2e_t = max_over_ranks(time.perf_counter() - t)
-    s.close()
-    e2e = {"value": ws * cells * ke / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nstate * 8,
-           "d2h_bytes_per_step": nstate * 8, "steps": ke,
-           "note": "per step: packed FP64 conserved state host->device (pinned), one RK2 step, state device->host"}
+        barrier()
+        t = time.perf_counter()
+        for _ in range(ke):
+            NV.amr_set_state(s.h, h_in, NV.AMR_STATE_CONSERVED)
+            s.step(0.0, sync=False)
+            NV.amr_get_state_all(s.h, h_out)
+        e2e_t = max_over_ranks(time.perf_counter() - t)
+        s.close()
+        e2e = {"value": ws * cells * ke / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nstate * 8,
+               "d2h_bytes_per_step": nstate * 8, "steps": ke,
+               "note": "per step: packed FP64 conserved state host->device (pinned), one RK2 step (CFL), "
+                       "state device->host"}
 
     if rank != 0:
         return
@@ -310,22 +320,19 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "kelvin_helmholtz_256^3_periodic_512_patches_32^3", "cells": cells,
-                   "patches": len(pb.patches), "path": "batched FP32, CUDA graph per coarse step",
+        "config": {"workload": "kelvin_helmholtz_256^3_periodic", "cells": cells, "patches": 1,
+                   "path": "batched FP32, CUDA graph per coarse step",
                    "dt": "CFL 0.4 recomputed on the GPU every step",
-                   "l2": "working set (U + U1, 0.75 GB FP32) exceeds the 129 MB L2; no flush",
+                   "l2": "working set (U + U1, 0.7 GB FP32) exceeds the 129 MB L2; no flush",
                    "parallelism": f"replicas x{ws}"},
-        "fp64_batched": {"value": fp64_batched, "unit": UNIT, "steps": k64},
-        "fp64_plain": {"value": fp64_plain, "unit": UNIT, "steps": k64,
-                       "path": "one stage-kernel and one ghost-copy launch per patch, no graph"},
-        "batched_fp32_over_plain_fp64": value / ws / fp64_plain if fp64_plain else None,
+        **extra,
         "roofline": {"bound": "hbm", "kernel": "stage_kernel (stage 1 + stage 2)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_cell_update": (2 + 3) * V * W,
                      "timed_steps": ksteps},
         "step_kernel_ms": step_kernel_ms,
-        "cell_update_roofline_frac": value / ws * 100 / (peak * 1e9),
+        "cell_update_roofline_frac": value / ws * (2 + 3) * V * W / (peak * 1e9),
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -29,11 +29,23 @@ __global__ void begin_speed_kernel(StepParams* params) {
 }
 
 // dt0 = cfl / max rate (CFL mode); GLM cleaning speed = fixed value or max signal speed.
-__global__ void finalize_speed_kernel(StepParams* params, double cfl, double ch_fixed, int set_dt) {
-  const double rate = __longlong_as_double((long long)params->rate_bits);
-  const double speed = __longlong_as_double((long long)params->speed_bits);
-  if (set_dt) params->dt0 = cfl / rate;
-  params->ch = ch_fixed > 0.0 ? ch_fixed : speed;
+// The maxima come from the standalone reduction (from_next = 0) or from the
+// previous stage 2 of a single-level grid (from_next = 1); the stage-2
+// accumulators are cleared for the step about to run.
+__global__ void finalize_speed_kernel(StepParams* params, double cfl, double ch_fixed, int set_dt, int from_next,
+                                      int use_rates, int clear_next) {
+  if (use_rates) {
+    const unsigned long long rb = from_next ? params->next_rate_bits : params->rate_bits;
+    const unsigned long long sb = from_next ? params->next_speed_bits : params->speed_bits;
+    const double rate = __longlong_as_double((long long)rb);
+    const double speed = __longlong_as_double((long long)sb);
+    if (set_dt) params->dt0 = cfl / rate;
+    params->ch = ch_fixed > 0.0 ? ch_fixed : speed;
+  }
+  if (clear_next) {
+    params->next_rate_bits = 0ull;
+    params->next_speed_bits = 0ull;
+  }
 }
 
 __global__ void set_dt_kernel(StepParams* params, double dt) { params->dt0 = dt; }
@@ -82,9 +94,10 @@ struct amr_handle {
   std::vector<ChunkDesc> chunks;
   std::vector<DevLevel> dl;
   double dx0[3] = {1, 1, 1};
-  // graphs: [0] fixed dt, [1] CFL dt
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  long long graph_launches[2] = {0, 0};
+  // graphs: index = cfl + 2 * standalone-reduction
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long graph_launches[4] = {0, 0, 0, 0};
+  bool rates_valid = false;   // stage 2 of the last step left next-step maxima (single level)
   long long launches = 0;
   long long counting = 0;   // launches counted while enqueueing
   // optional per-class event timing (eager steps only)
@@ -137,10 +150,11 @@ cudaEvent_t next_event(amr_handle* h, int* idx) {
   } while (0)
 
 void free_device(amr_handle* h) {
-  for (int g = 0; g < 2; ++g) {
+  for (int g = 0; g < 4; ++g) {
     if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
     h->graph[g] = nullptr;
   }
+  h->rates_valid = false;
   void* ptrs[] = {h->U, h->U1, h->Uold, h->tile, h->packed, h->partial, h->totals, h->regs, h->tables};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -186,12 +200,14 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
   const LevelPlan& LP = h->plan.levels[l];
   double dx[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
   h->cur_class = s == 1 ? AMR_T_STAGE1 : AMR_T_STAGE2;
+  const int fuse = (s == 2 && h->dl.size() == 1) ? 1 : 0;
   if (h->cfg.batched) {
-    LK(h->ops->stage(s, h->stream, h->d_desc, L.items, L.nitems, in, out, h->params, l, dx, 0));
+    LK(h->ops->stage(s, h->stream, h->d_desc, L.items, L.nitems, in, out, h->params, l, dx, h->dx0, fuse, 0));
   } else {
     for (int p = 0; p < LP.count; ++p) {
       int a = LP.item_first[p], b = LP.item_first[p + 1];
-      if (b > a) LK(h->ops->stage(s, h->stream, h->d_desc, L.items + a, b - a, in, out, h->params, l, dx, 0));
+      if (b > a)
+        LK(h->ops->stage(s, h->stream, h->d_desc, L.items + a, b - a, in, out, h->params, l, dx, h->dx0, fuse, 0));
     }
   }
   return cudaSuccess;
@@ -241,35 +257,51 @@ cudaError_t launch_begin_speed(amr_handle* h) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_speed(amr_handle* h, int set_dt) {
-  finalize_speed_kernel<<<1, 1, 0, h->stream>>>(h->params, h->cfg.cfl, h->cfg.nvar == 9 ? h->cfg.ch : 1.0, set_dt);
+cudaError_t launch_finalize_speed(amr_handle* h, int set_dt, int from_next, int use_rates, int clear_next) {
+  finalize_speed_kernel<<<1, 1, 0, h->stream>>>(h->params, h->cfg.cfl, h->cfg.nvar == 9 ? h->cfg.ch : 1.0, set_dt,
+                                                from_next, use_rates, clear_next);
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_speed(amr_handle* h, int set_dt) {
+// Standalone reduction over the state; clear_next = 1 when a step follows.
+cudaError_t enqueue_speed(amr_handle* h, int set_dt, int clear_next) {
   h->cur_class = AMR_T_SPEED;
   LK(launch_begin_speed(h));
   LK(h->ops->speed(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, h->params, h->dx0));
-  LK(launch_finalize_speed(h, set_dt));
+  LK(launch_finalize_speed(h, set_dt, 0, 1, clear_next));
   return cudaSuccess;
 }
 
-cudaError_t enqueue_step(amr_handle* h, bool cfl) {
-  cudaError_t e;
-  if (cfl || h->cfg.nvar == 9) {
-    if ((e = enqueue_speed(h, cfl ? 1 : 0)) != cudaSuccess) return e;
+bool fused_rates(const amr_handle* h) { return h->dl.size() == 1; }
+
+// Which step variant runs: 1 bit "CFL dt", 2 bit "standalone reduction over the state".
+int step_variant(const amr_handle* h, bool cfl) {
+  const bool need = cfl || h->cfg.nvar == 9;
+  const bool standalone = need && !(fused_rates(h) && h->rates_valid);
+  return (cfl ? 1 : 0) + (standalone ? 2 : 0);
+}
+
+cudaError_t enqueue_step(amr_handle* h, int variant) {
+  const bool cfl = variant & 1, standalone = variant & 2;
+  const bool need = cfl || h->cfg.nvar == 9;
+  if (standalone) {
+    cudaError_t e = enqueue_speed(h, cfl ? 1 : 0, 1);
+    if (e != cudaSuccess) return e;
+  } else if (fused_rates(h)) {
+    h->cur_class = AMR_T_SPEED;
+    LK(launch_finalize_speed(h, cfl ? 1 : 0, 1, need ? 1 : 0, 1));
   }
   return advance(h, 0, 0.0);
 }
 
 amr_status run_step(amr_handle* h, bool cfl) {
-  const int g = cfl ? 1 : 0;
+  const int g = step_variant(h, cfl);
   if (h->cfg.use_graph && !h->timing) {
     if (!h->graph[g]) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       h->counting = 0;
-      cudaError_t e = enqueue_step(h, cfl);
+      cudaError_t e = enqueue_step(h, g);
       cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
       if (e != cudaSuccess) return fail(h, AMR_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
       CK(e2);
@@ -281,9 +313,10 @@ amr_status run_step(amr_handle* h, bool cfl) {
     h->launches += h->graph_launches[g];
   } else {
     h->counting = 0;
-    CK(enqueue_step(h, cfl));
+    CK(enqueue_step(h, g));
     h->launches += h->counting;
   }
+  if (fused_rates(h)) h->rates_valid = true;
   return AMR_OK;
 }
 
@@ -555,6 +588,7 @@ amr_status amr_set_state(amr_handle* h, const double* packed, int state_kind) {
   CK(h->ops->pack_in(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->packed, h->U,
                      state_kind == AMR_STATE_PRIMITIVE, h->params));
   h->launches += 1;
+  h->rates_valid = false;
   return AMR_OK;
 }
 
@@ -581,7 +615,14 @@ amr_status amr_cfl_dt(amr_handle* h, double* dt) {
   if (!h || !dt) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
   h->counting = 0;
-  CK(enqueue_speed(h, 1));
+  h->cur_class = AMR_T_SPEED;
+  if (fused_rates(h) && h->rates_valid) {
+    // maxima of the current state were left by the last stage 2: no pass over the state
+    CK(launch_finalize_speed(h, 1, 1, 1, 0));
+    h->counting += 1;
+  } else {
+    CK(enqueue_speed(h, 1, 0));
+  }
   h->launches += h->counting;
   CK(cudaMemcpyAsync(dt, &h->params->dt0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

@@ -98,6 +98,10 @@ struct StepParams {
   unsigned long long speed_bits;  // max signal speed (double bits, atomicMax)
   unsigned int bad;    // non-physical state detected
   unsigned int pad;
+  // maxima of the state written by the last stage 2 (single-level grids): the
+  // next step's CFL rate and signal speed without another pass over the state
+  unsigned long long next_rate_bits;
+  unsigned long long next_speed_bits;
 };
 
 }  // namespace amr

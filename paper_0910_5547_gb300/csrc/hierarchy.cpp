@@ -82,6 +82,74 @@ std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) 
   return done;
 }
 
+// Split boxes with more than `maxc` cells along their longest axis so that
+// one CTA per box keeps the GPU busy for large patches.
+constexpr int kMaxBoxCells = 4096;
+
+void split_copy(std::vector<CopySeg>& v, size_t from) {
+  std::vector<CopySeg> out(v.begin(), v.begin() + from);
+  for (size_t i = from; i < v.size(); ++i) {
+    std::vector<CopySeg> work{v[i]};
+    while (!work.empty()) {
+      CopySeg s = work.back();
+      work.pop_back();
+      int vol = s.dn[0] * s.dn[1] * s.dn[2];
+      if (vol <= kMaxBoxCells) { out.push_back(s); continue; }
+      int k = 0;
+      for (int a = 1; a < 3; ++a) if (s.dn[a] > s.dn[k]) k = a;
+      CopySeg a = s, b = s;
+      a.dn[k] = (int16_t)(s.dn[k] / 2);
+      b.dn[k] = (int16_t)(s.dn[k] - a.dn[k]);
+      b.dlo[k] = (int16_t)(s.dlo[k] + a.dn[k]);
+      work.push_back(b);
+      work.push_back(a);
+    }
+  }
+  v.swap(out);
+}
+
+void split_prolong(std::vector<ProlongBox>& v, size_t from) {
+  std::vector<ProlongBox> out(v.begin(), v.begin() + from);
+  for (size_t i = from; i < v.size(); ++i) {
+    std::vector<ProlongBox> work{v[i]};
+    while (!work.empty()) {
+      ProlongBox s = work.back();
+      work.pop_back();
+      if (s.n[0] * s.n[1] * s.n[2] <= kMaxBoxCells) { out.push_back(s); continue; }
+      int k = 0;
+      for (int a = 1; a < 3; ++a) if (s.n[a] > s.n[k]) k = a;
+      ProlongBox a = s, b = s;
+      a.n[k] = (int16_t)(s.n[k] / 2);
+      b.n[k] = (int16_t)(s.n[k] - a.n[k]);
+      b.lo[k] = (int16_t)(s.lo[k] + a.n[k]);
+      work.push_back(b);
+      work.push_back(a);
+    }
+  }
+  v.swap(out);
+}
+
+void split_restrict(std::vector<RestrictSeg>& v) {
+  std::vector<RestrictSeg> out;
+  for (size_t i = 0; i < v.size(); ++i) {
+    std::vector<RestrictSeg> work{v[i]};
+    while (!work.empty()) {
+      RestrictSeg s = work.back();
+      work.pop_back();
+      if (s.cn[0] * s.cn[1] * s.cn[2] <= kMaxBoxCells / 2) { out.push_back(s); continue; }
+      int k = 0;
+      for (int a = 1; a < 3; ++a) if (s.cn[a] > s.cn[k]) k = a;
+      RestrictSeg a = s, b = s;
+      a.cn[k] = (int16_t)(s.cn[k] / 2);
+      b.cn[k] = (int16_t)(s.cn[k] - a.cn[k]);
+      b.clo[k] = (int16_t)(s.clo[k] + a.cn[k]);
+      work.push_back(b);
+      work.push_back(a);
+    }
+  }
+  v.swap(out);
+}
+
 }  // namespace
 
 amr_status validate_config(const amr_config& c, std::string& msg) {
@@ -124,6 +192,9 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
       if (p.n[d] < 2 || p.n[d] > 1024) { msg = fmt("patch %d: size %d outside [2, 1024] on axis %d", (int)i, p.n[d], d); return AMR_ERR_ARG; }
       if (p.lo[d] < 0 || p.lo[d] + p.n[d] > level_n(c, p.level, d)) {
         msg = fmt("patch %d: outside the level-%d domain on axis %d", (int)i, p.level, d); return AMR_ERR_NESTING;
+      }
+      if ((int64_t)(p.n[0] + 4) * (p.n[1] + 4) * (p.n[2] + 4) * c.nvar > (int64_t)1 << 30) {
+        msg = fmt("patch %d: ghosted size times nvar exceeds 2^30 cells", (int)i); return AMR_ERR_ARG;
       }
       if (p.level > 0 && ((p.lo[d] & 1) || (p.n[d] & 1))) {
         msg = fmt("patch %d: refined patches need even lo and n (axis %d)", (int)i, d); return AMR_ERR_NESTING;
@@ -258,7 +329,9 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
       split(p.n[2], zparts, zs);
       for (auto& z : zs)
         for (auto& x : xs) {
-          int wymax = std::min(kStageThreads / x.second, kPlaneMax / (x.second + 4) - 4);
+          // one halo cell per thread: 4 (wx + wy) <= 256
+          int wymax = std::min(std::min(kStageThreads / x.second, kPlaneMax / (x.second + 4) - 4),
+                               kStageThreads / 4 - x.second);
           split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);
           for (auto& y : ys) {
             StageItem it{};
@@ -333,6 +406,41 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             }
           }
       }
+      // merge the two ghost layers of a face into one two-deep segment where
+      // both layers copy from the same source with the same mapping
+      {
+        const int g0 = L.ghost_first.back();
+        std::vector<CopySeg> segs(L.ghost.begin() + g0, L.ghost.end());
+        std::vector<char> used(segs.size(), 0);
+        std::vector<CopySeg> merged;
+        for (size_t a = 0; a < segs.size(); ++a) {
+          if (used[a]) continue;
+          CopySeg m = segs[a];
+          for (size_t b = a + 1; b < segs.size(); ++b) {
+            if (used[b]) continue;
+            const CopySeg& o = segs[b];
+            int d = -1;
+            for (int k = 0; k < 3; ++k)
+              if (m.dn[k] == 1 && o.dn[k] == 1 && (o.dlo[k] == m.dlo[k] - 1 || o.dlo[k] == m.dlo[k] + 1)) d = k;
+            if (d < 0 || o.src_patch != m.src_patch) continue;
+            bool same = true;
+            for (int k = 0; k < 3 && same; ++k) {
+              same = o.mode[k] == m.mode[k] && o.sh[k] == m.sh[k];
+              if (k != d) same = same && o.dlo[k] == m.dlo[k] && o.dn[k] == m.dn[k];
+            }
+            if (!same) continue;
+            m.dlo[d] = std::min(m.dlo[d], o.dlo[d]);
+            m.dn[d] = 2;
+            used[b] = 1;
+            break;
+          }
+          merged.push_back(m);
+        }
+        L.ghost.resize(g0);
+        L.ghost.insert(L.ghost.end(), merged.begin(), merged.end());
+        split_copy(L.ghost, g0);
+      }
+      split_prolong(L.prolong, L.prolong_first.back());
       L.ghost_first.push_back((int)L.ghost.size());
       L.prolong_first.push_back((int)L.prolong.size());
     }
@@ -401,6 +509,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
               L.gather.push_back(s);
             }
           }
+      split_copy(L.gather, L.gather_first.back());
       const PatchDesc& d = plan.desc[i];
       if (covered != (int64_t)d.tn[0] * d.tn[1] * d.tn[2]) {
         msg = fmt("patch %d: parent tile not covered by level %d", i, l - 1);
@@ -440,6 +549,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
       }
     }
   }
+  for (int l = 1; l < nlev; ++l) split_restrict(plan.levels[l].restrict_segs);
   for (int i = 0; i < np; ++i) {
     plan.cover_first[i + 1] = plan.cover_first[i] + (int)cov[i].size();
     for (auto& b : cov[i]) plan.cover.push_back(b);

@@ -27,14 +27,18 @@
 
 namespace amr {
 
-// Shared-memory plane of a stage CTA: (wy + 4) x (wx + 4) cells; the planner
-// keeps wx * wy <= 256, wx <= 32 and (wx + 4)(wy + 4) <= kPlaneMax.
-// Face count wy (wx + 1) + (wy + 1) wx = 2 wx wy + wx + wy <= 512 + 70.
+// Shared memory of a stage CTA, per variable: the primitive plane with its
+// face halo, (wy + 4) x (wx + 4) <= kPlaneMax cells; four face-state arrays
+// (left/right states of x faces, (wx + 2) wy <= kStateMax, and of y faces,
+// (wy + 2) wx <= kStateMax); and the x/y face fluxes, wy (wx + 1) + (wy + 1) wx
+// = 2 wx wy + wx + wy <= kFaceMax.  The planner keeps wx * wy <= 256, wx <= 32,
+// 4 (wx + wy) <= 256 and (wx + 4)(wy + 4) <= kPlaneMax.
 constexpr int kFaceMax = 2 * kStageThreads + 88;
+constexpr int kStateMax = kStageThreads + 128;
 
 template <typename T, int NV>
 constexpr size_t stage_smem_bytes() {
-  return sizeof(T) * NV * (2 * kPlaneMax + kFaceMax);
+  return sizeof(T) * NV * (kPlaneMax + 4 * kStateMax + kFaceMax);
 }
 
 struct ChunkDesc {  // a contiguous range of interior cells of one patch
@@ -53,8 +57,16 @@ struct StageArgs {
   StepParams* params;
   double dt_scale;   // 2^-level
   T idx, idy, idz;   // 1 / dx of the level
+  double idx0, idy0, idz0;  // 1 / dx of level 0 (CFL rate)
+  int fuse_rate;     // stage 2: accumulate the CFL rate of the new state
   Phys<T> ph;
 };
+
+template <typename T, int NV>
+__device__ __forceinline__ void load_cons(const T* base, int vstride, int c, T* u) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) u[v] = base[v * vstride + c];
+}
 
 template <typename T, int NV>
 __device__ __forceinline__ void load_cons(const T* base, int64_t vstride, int64_t c, T* u) {
@@ -73,17 +85,59 @@ __device__ __forceinline__ Phys<T> phys_with_ch(Phys<T> ph, const StepParams* pr
   return ph;
 }
 
+// CFL rate sum_d (|v_d| + c_d) / dx0_d and max signal speed of a conserved state.
+template <typename T, int NV>
+__device__ __forceinline__ void cell_rate(const T* u, const Phys<T>& ph, T idx0, T idy0, T idz0, T& rate,
+                                          T& speed) {
+  T w[NV];
+  cons_to_prim<T, NV>(u, w);
+  T c0, c1, c2;
+  if (NV == 5) {
+    c0 = c1 = c2 = dsqrt(ph.ggm1 * w[4]);
+  } else {
+    const T r = drcp(w[0]);
+    const T a2 = ph.ggm1 * w[4];
+    const T b2 = (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]) * r;
+    const T s = a2 + b2;
+    const T s2 = s * s;
+    const T f = T(4) * a2 * r;
+    c0 = dsqrt(T(0.5) * (s + dsqrt(dmax(s2 - f * w[5] * w[5], T(0)))));
+    c1 = dsqrt(T(0.5) * (s + dsqrt(dmax(s2 - f * w[6] * w[6], T(0)))));
+    c2 = dsqrt(T(0.5) * (s + dsqrt(dmax(s2 - f * w[7] * w[7], T(0)))));
+  }
+  const T s0 = dabs(w[1]) + c0, s1 = dabs(w[2]) + c1, s2 = dabs(w[3]) + c2;
+  rate = s0 * idx0 + s1 * idy0 + s2 * idz0;
+  speed = dmax(s0, dmax(s1, s2));
+}
+
+__device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Fused RK2 stage over work items (patch, wx x wy column block, z range).
+// Each thread owns one column and marches in z: primitives of planes k, k+1,
+// the z slope of plane k and the z-face flux F_{k-1/2} live in registers and
+// the next plane's global loads are issued one iteration ahead.  Per plane,
+// three shared-memory phases: (1) primitives of plane k with a two-cell face
+// halo; (2) every cell's x and y limited slopes, computed once, as face
+// states w +- s; (3) every x and y face flux, solved once.  The update then
+// differences the fluxes of the cell's six faces.
 template <typename T, int NV, int STAGE>
-__global__ void __launch_bounds__(kStageThreads) stage_kernel(StageArgs<T> a) {
+__global__ void __launch_bounds__(kStageThreads, (sizeof(T) == 4 && NV == 5) ? 2 : 1) stage_kernel(StageArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Wb0 = reinterpret_cast<T*>(smem_raw);
-  T* Wb1 = Wb0 + NV * kPlaneMax;
-  T* FX = Wb1 + NV * kPlaneMax;
+  T* W = reinterpret_cast<T*>(smem_raw);
+  T* XL = W + NV * kPlaneMax;
+  T* XR = XL + NV * kStateMax;
+  T* YL = XR + NV * kStateMax;
+  T* YR = YL + NV * kStateMax;
+  T* FX = YR + NV * kStateMax;
 
   const Phys<T> ph = phys_with_ch<T, NV>(a.ph, a.params);
   const T dt = (T)(a.params->dt0 * a.dt_scale);
   const int t = threadIdx.x;
   bool bad = false;
+  T rate_max = T(0), speed_max = T(0);
 
   for (int itn = blockIdx.x; itn < a.nitems; itn += gridDim.x) {
     const StageItem it = a.items[itn];
@@ -92,166 +146,232 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageArgs<T> a) {
     const int sw = wx + 4;
     const int ncol = wx * wy;
     const int nfx = wy * (wx + 1);
+    const int nfy = wx * (wy + 1);
     T* FY = FX + NV * nfx;
     const bool active = t < ncol;
     const int tx = active ? t % wx : 0, ty = active ? t / wx : 0;
-    const int gi = it.x0 + tx, gj = it.y0 + ty;
     const T* Ub = a.Uin + P.off;
-    const int64_t plane = (int64_t)P.pitch * P.m1;
-    const int64_t col = cell_index(P, gi, gj, 0);   // (k = 0) of own column
+    T* Ob = a.Uout + P.off;
+    const int vs = (int)P.vstride;
+    const int plane = P.pitch * P.m1;
+    const int col = ((it.z0 + kGhost) * P.m1 + (it.y0 + ty + kGhost)) * P.pitch + (it.x0 + tx + kGhost);
     const int me = (ty + 2) * sw + (tx + 2);
+    const int xs = ty * (wx + 2) + (tx + 1);     // x-state slot of the own cell
+    const int ys = (ty + 1) * wx + tx;           // y-state slot of the own cell
+    // this thread's halo cell (one per thread, 4 (wx + wy) <= blockDim)
+    const int nhalo = 4 * (wx + wy);
+    const bool has_halo = t < nhalo;
+    int hoff = 0, hpos = 0;
+    if (has_halo) {
+      int hx, hy;
+      if (t < 4 * wy) {
+        const int r = t >> 2, c = t & 3;
+        hy = r;
+        hx = c < 2 ? c - 2 : wx + (c - 2);
+      } else {
+        const int h2 = t - 4 * wy;
+        const int r = h2 / wx, c = h2 - r * wx;
+        hx = c;
+        hy = r < 2 ? r - 2 : wy + (r - 2);
+      }
+      hoff = ((it.z0 + kGhost) * P.m1 + (it.y0 + hy + kGhost)) * P.pitch + (it.x0 + hx + kGhost);
+      hpos = (hy + 2) * sw + (hx + 2);
+    }
+    // this thread's boundary slope (the halo cell next to the block edge), if any
+    const int eb = (int)blockDim.x - 1 - t;
+    int bkind = -1, bpos = 0, bslot = 0, bstep = 0;
+    if (eb < 2 * (wx + wy)) {
+      if (eb < wy) { bkind = 0; bpos = (eb + 2) * sw + 1; bslot = eb * (wx + 2); bstep = 1; }            // XL, x = -1
+      else if (eb < 2 * wy) {
+        const int r = eb - wy;
+        bkind = 1; bpos = (r + 2) * sw + wx + 2; bslot = r * (wx + 2) + wx + 1; bstep = 1;                // XR, x = wx
+      } else if (eb < 2 * wy + wx) {
+        const int c = eb - 2 * wy;
+        bkind = 2; bpos = 1 * sw + c + 2; bslot = c; bstep = sw;                                          // YL, y = -1
+      } else {
+        const int c = eb - 2 * wy - wx;
+        bkind = 3; bpos = (wy + 2) * sw + c + 2; bslot = (wy + 1) * wx + c; bstep = sw;                   // YR, y = wy
+      }
+    }
 
-    T wA[NV], wB[NV], sA[NV], Fm[NV];
-    if (active) {  // prologue: planes z0-2 .. z0+1
-      T u[NV], w0[NV], w1[NV];
-      const int k0 = it.z0;
-      load_cons<T, NV>(Ub, P.vstride, col + (int64_t)(k0 - 2) * plane, u);
-      cons_to_prim<T, NV>(u, w0);
-      load_cons<T, NV>(Ub, P.vstride, col + (int64_t)(k0 - 1) * plane, u);
-      cons_to_prim<T, NV>(u, w1);
-      load_cons<T, NV>(Ub, P.vstride, col + (int64_t)k0 * plane, u);
-      bad |= !cons_to_prim<T, NV>(u, wA);
-      load_cons<T, NV>(Ub, P.vstride, col + (int64_t)(k0 + 1) * plane, u);
-      bad |= !cons_to_prim<T, NV>(u, wB) && wz > 1;
+    T uD[NV], wA[NV], wB[NV], sA[NV], Fm[NV], hN[NV], unN[NV];
+    if (active) {  // prologue: planes z0-2 .. z0+2
+      T u0[NV], u1[NV], w0[NV], w1[NV];
+      load_cons<T, NV>(Ub, vs, col - 2 * plane, u0);
+      load_cons<T, NV>(Ub, vs, col - plane, u1);
+      load_cons<T, NV>(Ub, vs, col, uD);
+      cons_to_prim<T, NV>(u0, w0);
+      cons_to_prim<T, NV>(u1, w1);
+      bad |= !cons_to_prim<T, NV>(uD, wA);
+      load_cons<T, NV>(Ub, vs, col + plane, uD);
+      bad |= !cons_to_prim<T, NV>(uD, wB) && wz > 1;
+      load_cons<T, NV>(Ub, vs, col + 2 * plane, uD);
+      if (STAGE == 2) load_cons<T, NV>(Ob, vs, col, unN);
       T wl[NV], wr[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T s_m1 = half_slope(w0[v], w1[v], wA[v], ph.theta);
+        const T s_m1 = half_slope(w0[v], w1[v], wA[v], ph.theta);
         sA[v] = half_slope(w1[v], wA[v], wB[v], ph.theta);
         wl[v] = w1[v] + s_m1;
         wr[v] = wA[v] - sA[v];
       }
       riemann<T, NV, 2>(wl, wr, ph, Fm);
     }
+    if (has_halo) load_cons<T, NV>(Ub, vs, hoff, hN);
 
-    const int nhalo = 4 * (wx + wy);
     for (int kk = 0; kk < wz; ++kk) {
-      const int k = it.z0 + kk;
-      T* W = (kk & 1) ? Wb1 : Wb0;
-      T Fp[NV];
+      const int kn = kk + 1 < wz ? kk + 1 : kk;   // next plane (clamped: the last prefetch is unused)
+      T Fp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
+      // ---- phase 1: z face k+1/2, primitives of plane k into shared memory ----
       if (active) {
-        T u[NV], wC[NV], sB[NV], wl[NV], wr[NV];
-        load_cons<T, NV>(Ub, P.vstride, col + (int64_t)(k + 2) * plane, u);
-        bool ok = cons_to_prim<T, NV>(u, wC);
+        // stage input of the own cell, plane k (read two planes ago: a cache hit), issued
+        // here so that it is in flight across the three shared-memory phases
+        load_cons<T, NV>(Ub, vs, col + kk * plane, uin);
+        T wC[NV], sB[NV], wl[NV], wr[NV];
+        const bool ok = cons_to_prim<T, NV>(uD, wC);        // plane k+2
         if (kk + 2 < wz) bad |= !ok;
+        load_cons<T, NV>(Ub, vs, col + (kn + 2) * plane, uD);  // prefetch plane k+3
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           sB[v] = half_slope(wA[v], wB[v], wC[v], ph.theta);
           wl[v] = wA[v] + sA[v];
           wr[v] = wB[v] - sB[v];
           W[v * kPlaneMax + me] = wA[v];
+          own[v] = wA[v];
+          un[v] = unN[v];
         }
+        if (STAGE == 2) load_cons<T, NV>(Ob, vs, col + kn * plane, unN);
         riemann<T, NV, 2>(wl, wr, ph, Fp);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { sA[v] = sB[v]; }
-        // shift happens after the update (wA is needed there only through W)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) { wA[v] = wB[v]; wB[v] = wC[v]; }
+        for (int v = 0; v < NV; ++v) { sA[v] = sB[v]; wA[v] = wB[v]; wB[v] = wC[v]; }
       }
-      // face halo of plane k: x-halo (4 cells per row) and y-halo (4 rows per column)
-      for (int h = t; h < nhalo; h += blockDim.x) {
-        int hx, hy;
-        if (h < 4 * wy) {
-          int r = h >> 2, c = h & 3;
-          hy = r;
-          hx = c < 2 ? c - 2 : wx + (c - 2);
-        } else {
-          int h2 = h - 4 * wy;
-          int r = h2 / wx, c = h2 - r * wx;
-          hx = c;
-          hy = r < 2 ? r - 2 : wy + (r - 2);
-        }
-        T u[NV], w[NV];
-        load_cons<T, NV>(Ub, P.vstride, cell_index(P, it.x0 + hx, it.y0 + hy, k), u);
-        cons_to_prim<T, NV>(u, w);
-        const int pos = (hy + 2) * sw + (hx + 2);
+      if (has_halo) {
+        T w[NV];
+        cons_to_prim<T, NV>(hN, w);
+        load_cons<T, NV>(Ub, vs, hoff + kn * plane, hN);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) W[v * kPlaneMax + pos] = w[v];
+        for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
       }
       __syncthreads();
-      // x and y faces at the low side of every column, then the high edge faces
+      // ---- phase 2: x and y limited slopes once per cell -> face states ----
       if (active) {
-        T wl[NV], wr[NV], F[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const T* Wv = W + v * kPlaneMax + me;
-          wl[v] = Wv[-1] + half_slope(Wv[-2], Wv[-1], Wv[0], ph.theta);
-          wr[v] = Wv[0] - half_slope(Wv[-1], Wv[0], Wv[1], ph.theta);
+          const T w0 = own[v];
+          const T sx = half_slope(Wv[-1], w0, Wv[1], ph.theta);
+          const T sy = half_slope(Wv[-sw], w0, Wv[sw], ph.theta);
+          XL[v * kStateMax + xs] = w0 + sx;
+          XR[v * kStateMax + xs] = w0 - sx;
+          YL[v * kStateMax + ys] = w0 + sy;
+          YR[v * kStateMax + ys] = w0 - sy;
+        }
+      }
+      if (bkind >= 0) {
+        T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
+        const T sgn = (bkind == 0 || bkind == 2) ? T(1) : T(-1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* Wv = W + v * kPlaneMax + bpos;
+          const T w0 = Wv[0];
+          dst[v * kStateMax + bslot] = w0 + sgn * half_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
+        }
+      }
+      __syncthreads();
+      // ---- phase 3: every x and y face flux once ----
+      if (active) {
+        T wl[NV], wr[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          wl[v] = XL[v * kStateMax + xs - 1];
+          wr[v] = XR[v * kStateMax + xs];
+        }
+        riemann<T, NV, 0>(wl, wr, ph, Fx0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          wl[v] = YL[v * kStateMax + ys - wx];
+          wr[v] = YR[v * kStateMax + ys];
+        }
+        riemann<T, NV, 1>(wl, wr, ph, Fy0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          FX[v * nfx + ty * (wx + 1) + tx] = Fx0[v];
+          FY[v * nfy + ty * wx + tx] = Fy0[v];
+        }
+      }
+      if (eb < wy) {  // x face at the right edge of row eb
+        T wl[NV], wr[NV], F[NV];
+        const int sl = eb * (wx + 2) + wx;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          wl[v] = XL[v * kStateMax + sl];
+          wr[v] = XR[v * kStateMax + sl + 1];
         }
         riemann<T, NV, 0>(wl, wr, ph, F);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FX[v * nfx + ty * (wx + 1) + tx] = F[v];
+        for (int v = 0; v < NV; ++v) FX[v * nfx + eb * (wx + 1) + wx] = F[v];
+      } else if (eb < wy + wx) {  // y face at the top edge of column eb - wy
+        const int c = eb - wy;
+        T wl[NV], wr[NV], F[NV];
+        const int sl = wy * wx + c;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlaneMax + me;
-          wl[v] = Wv[-sw] + half_slope(Wv[-2 * sw], Wv[-sw], Wv[0], ph.theta);
-          wr[v] = Wv[0] - half_slope(Wv[-sw], Wv[0], Wv[sw], ph.theta);
+          wl[v] = YL[v * kStateMax + sl];
+          wr[v] = YR[v * kStateMax + sl + wx];
         }
         riemann<T, NV, 1>(wl, wr, ph, F);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FY[v * (wx * (wy + 1)) + ty * wx + tx] = F[v];
-      }
-      {
-        const int e = (int)blockDim.x - 1 - t;
-        if (e < wy) {  // x face at the right edge of row e
-          T wl[NV], wr[NV], F[NV];
-          const int pos = (e + 2) * sw + (wx + 2);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const T* Wv = W + v * kPlaneMax + pos;
-            wl[v] = Wv[-1] + half_slope(Wv[-2], Wv[-1], Wv[0], ph.theta);
-            wr[v] = Wv[0] - half_slope(Wv[-1], Wv[0], Wv[1], ph.theta);
-          }
-          riemann<T, NV, 0>(wl, wr, ph, F);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) FX[v * nfx + e * (wx + 1) + wx] = F[v];
-        } else if (e < wy + wx) {  // y face at the top edge of column e - wy
-          const int c = e - wy;
-          T wl[NV], wr[NV], F[NV];
-          const int pos = (wy + 2) * sw + (c + 2);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const T* Wv = W + v * kPlaneMax + pos;
-            wl[v] = Wv[-sw] + half_slope(Wv[-2 * sw], Wv[-sw], Wv[0], ph.theta);
-            wr[v] = Wv[0] - half_slope(Wv[-sw], Wv[0], Wv[sw], ph.theta);
-          }
-          riemann<T, NV, 1>(wl, wr, ph, F);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) FY[v * (wx * (wy + 1)) + wy * wx + c] = F[v];
-        }
+        for (int v = 0; v < NV; ++v) FY[v * nfy + wy * wx + c] = F[v];
       }
       __syncthreads();
+      // ---- update: U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2 ----
       if (active) {
-        const int64_t c = col + (int64_t)k * plane;
-        const int nfy = wx * (wy + 1);
-        T* Ob = a.Uout + P.off;
+        const int c = col + kk * plane;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T Lx = (FX[v * nfx + ty * (wx + 1) + tx + 1] - FX[v * nfx + ty * (wx + 1) + tx]) * a.idx;
-          const T Ly = (FY[v * nfy + (ty + 1) * wx + tx] - FY[v * nfy + ty * wx + tx]) * a.idy;
+          const T Lx = (FX[v * nfx + ty * (wx + 1) + tx + 1] - Fx0[v]) * a.idx;
+          const T Ly = (FY[v * nfy + (ty + 1) * wx + tx] - Fy0[v]) * a.idy;
           const T Lz = (Fp[v] - Fm[v]) * a.idz;
           const T L = -(Lx + Ly + Lz);
-          const T uin = Ub[v * P.vstride + c];
           if (STAGE == 1) {
-            Ob[v * P.vstride + c] = uin + dt * L;
+            Ob[v * vs + c] = uin[v] + dt * L;
           } else {
-            const T un = Ob[v * P.vstride + c];
-            const T u2 = uin + dt * L;
-            Ob[v * P.vstride + c] = T(0.5) * un + T(0.5) * u2;
+            const T u2 = uin[v] + dt * L;
+            un[v] = T(0.5) * un[v] + T(0.5) * u2;
+            Ob[v * vs + c] = un[v];
           }
           Fm[v] = Fp[v];
+        }
+        if (STAGE == 2 && a.fuse_rate) {
+          T r, sp;
+          cell_rate<T, NV>(un, ph, (T)a.idx0, (T)a.idy0, (T)a.idz0, r, sp);
+          rate_max = dmax(rate_max, r);
+          speed_max = dmax(speed_max, sp);
         }
       }
     }
     __syncthreads();  // the next item reuses the shared buffers
   }
   if (bad) atomicOr(&a.params->bad, 1u);
+  if (STAGE == 2 && a.fuse_rate) {
+    double r = (double)rate_max, sp = (double)speed_max;
+    for (int o = 16; o > 0; o >>= 1) {
+      r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+      sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
+    }
+    if ((t & 31) == 0) {
+      atomic_max_pos_double(&a.params->next_rate_bits, r);
+      atomic_max_pos_double(&a.params->next_speed_bits, sp);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // ghost fill and parent-tile gather
 // ---------------------------------------------------------------------------
 
+// One CTA per box: dst cell (a, b, c) = dlo + (i, j, k) takes the src cell whose
+// local coordinate per axis is (dst + sh) (translate) or sh (constant).
 template <typename T, int NV, bool GATHER>
 __global__ void copy_kernel(const CopySeg* segs, int nseg, const PatchDesc* desc, T* dst_arena,
                             const T* src_arena, const T* src_old, T alpha) {
@@ -261,23 +381,31 @@ __global__ void copy_kernel(const CopySeg* segs, int nseg, const PatchDesc* desc
     const PatchDesc S = desc[g.src_patch];
     const int n0 = g.dn[0], n1 = g.dn[1], n2 = g.dn[2];
     const int total = n0 * n1 * n2;
+    const int svs = (int)S.vstride;
+    const int sp = S.pitch, sm1 = S.m1;
+    const T* Sb = src_arena + S.off;
+    const T* Ob = GATHER ? src_old + S.off : nullptr;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      const int a = e % n0, b = (e / n0) % n1, c = e / (n0 * n1);
+      const int r = e / n0, a = e - r * n0;
+      const int c = r / n1, b = r - c * n1;
       const int da = g.dlo[0] + a, db = g.dlo[1] + b, dc = g.dlo[2] + c;
       const int sa = g.mode[0] ? g.sh[0] : da + g.sh[0];
       const int sb = g.mode[1] ? g.sh[1] : db + g.sh[1];
       const int sc = g.mode[2] ? g.sh[2] : dc + g.sh[2];
-      const int64_t si = S.off + cell_index(S, sa, sb, sc);
+      const int si = ((sc + kGhost) * sm1 + (sb + kGhost)) * sp + (sa + kGhost);
       if (GATHER) {
-        const int64_t di = (int64_t)D.tile_off + ((int64_t)dc * D.tn[1] + db) * D.tn[0] + da;
-        const int64_t tvol = (int64_t)D.tn[0] * D.tn[1] * D.tn[2];
+        const int tvol = D.tn[0] * D.tn[1] * D.tn[2];
+        T* Tb = dst_arena + D.tile_off + (dc * D.tn[1] + db) * D.tn[0] + da;
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          dst_arena[di + v * tvol] = (T(1) - alpha) * src_old[si + v * S.vstride] + alpha * src_arena[si + v * S.vstride];
+        for (int v = 0; v < NV; ++v) Tb[v * tvol] = (T(1) - alpha) * Ob[si + v * svs] + alpha * Sb[si + v * svs];
       } else {
-        const int64_t di = D.off + cell_index(D, da, db, dc);
+        T* Db = dst_arena + D.off + ((dc + kGhost) * D.m1 + (db + kGhost)) * D.pitch + (da + kGhost);
+        const int dvs = (int)D.vstride;
+        T val[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) dst_arena[di + v * D.vstride] = src_arena[si + v * S.vstride];
+        for (int v = 0; v < NV; ++v) val[v] = Sb[si + v * svs];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Db[v * dvs] = val[v];
       }
     }
   }
@@ -455,42 +583,38 @@ __global__ void reflux_kernel(const RegFace* regs, const int* first, int nuniq, 
 // reductions and host-layout conversion
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, double v) {
-  // non-negative doubles order like their bit patterns
-  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
-}
-
-// Per-cell CFL rate sum_d (|v_d| + c_d) / dx0_d and max signal speed max_d (|v_d| + c_d).
+// Per-cell CFL rate sum_d (|v_d| + c_d) / dx0_d and max signal speed max_d (|v_d| + c_d),
+// reduced with warp shuffles and one atomic per warp.
 template <typename T, int NV>
 __global__ void speed_kernel(const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const T* U,
                              StepParams* params, double idx0, double idy0, double idz0, Phys<T> ph) {
-  double rate = 0.0, speed = 0.0;
+  T rate = T(0), speed = T(0);
+  const T i0 = (T)idx0, i1 = (T)idy0, i2 = (T)idz0;
   for (int s = blockIdx.x; s < nchunk; s += gridDim.x) {
     const ChunkDesc ch = chunks[s];
     const PatchDesc P = desc[ch.patch];
+    const T* Ub = U + P.off;
+    const int vs = (int)P.vstride;
+    const int nx = P.n[0], nxy = P.n[0] * P.n[1];
     for (int e = threadIdx.x; e < ch.count; e += blockDim.x) {
       const int idx = ch.begin + e;
-      const int i = idx % P.n[0], j = (idx / P.n[0]) % P.n[1], k = idx / (P.n[0] * P.n[1]);
-      T u[NV], w[NV];
-      load_cons<T, NV>(U + P.off, P.vstride, cell_index(P, i, j, k), u);
-      cons_to_prim<T, NV>(u, w);
-      T Ud[NV], Fd[NV], c0, c1, c2;
-      state_flux<T, NV, 0>(w, ph, Ud, Fd, c0);
-      state_flux<T, NV, 1>(w, ph, Ud, Fd, c1);
-      state_flux<T, NV, 2>(w, ph, Ud, Fd, c2);
-      const double s0 = (double)(dabs(w[1]) + c0), s1 = (double)(dabs(w[2]) + c1), s2 = (double)(dabs(w[3]) + c2);
-      const double r = s0 * idx0 + s1 * idy0 + s2 * idz0;
-      rate = fmax(rate, r);
-      speed = fmax(speed, fmax(s0, fmax(s1, s2)));
+      const int k = idx / nxy, r2 = idx - k * nxy, j = r2 / nx, i = r2 - j * nx;
+      T u[NV];
+      load_cons<T, NV>(Ub, vs, ((k + kGhost) * P.m1 + (j + kGhost)) * P.pitch + (i + kGhost), u);
+      T r, sp;
+      cell_rate<T, NV>(u, ph, i0, i1, i2, r, sp);
+      rate = dmax(rate, r);
+      speed = dmax(speed, sp);
     }
   }
+  double rd = (double)rate, sd = (double)speed;
   for (int o = 16; o > 0; o >>= 1) {
-    rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-    speed = fmax(speed, __shfl_xor_sync(0xffffffffu, speed, o));
+    rd = fmax(rd, __shfl_xor_sync(0xffffffffu, rd, o));
+    sd = fmax(sd, __shfl_xor_sync(0xffffffffu, sd, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    atomic_max_pos_double(&params->rate_bits, rate);
-    atomic_max_pos_double(&params->speed_bits, speed);
+    atomic_max_pos_double(&params->rate_bits, rd);
+    atomic_max_pos_double(&params->speed_bits, sd);
   }
 }
 

@@ -22,7 +22,8 @@ struct OpsBase {
   virtual size_t elem_size() const = 0;
   // fused RK2 stage over items [0, nitems) of `items` (device pointer)
   virtual cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
-                            const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3], int grid) = 0;
+                            const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3],
+                            const double dx0[3], int fuse_rate, int grid) = 0;
   virtual cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) = 0;
   virtual cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,
                              const void* U, const void* Uold, double alpha) = 0;

@@ -29,7 +29,8 @@ struct Ops final : OpsBase {
   size_t elem_size() const override { return sizeof(T); }
 
   cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
-                    const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3], int grid) override {
+                    const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3],
+                    const double dx0[3], int fuse_rate, int grid) override {
     if (nitems <= 0) return cudaSuccess;
     StageArgs<T> a;
     a.desc = desc;
@@ -42,6 +43,10 @@ struct Ops final : OpsBase {
     a.idx = (T)(1.0 / dx[0]);
     a.idy = (T)(1.0 / dx[1]);
     a.idz = (T)(1.0 / dx[2]);
+    a.idx0 = 1.0 / dx0[0];
+    a.idy0 = 1.0 / dx0[1];
+    a.idz0 = 1.0 / dx0[2];
+    a.fuse_rate = fuse_rate;
     a.ph = ph;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
     const size_t sm = stage_smem_bytes<T, NV>();
@@ -54,7 +59,7 @@ struct Ops final : OpsBase {
 
   cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) override {
     if (nseg <= 0) return cudaSuccess;
-    copy_kernel<T, NV, false><<<grid_for(nseg), 128, 0, s>>>(segs, nseg, desc, static_cast<T*>(arena),
+    copy_kernel<T, NV, false><<<grid_for(nseg), 256, 0, s>>>(segs, nseg, desc, static_cast<T*>(arena),
                                                              static_cast<const T*>(arena), nullptr, T(0));
     return cudaGetLastError();
   }

@@ -123,18 +123,13 @@ __device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (Fl[k] + Fr[k] - a * (Ur[k] - Ul[k]));
   } else {
+    // S_R - S_L > 0 for every state with c > 0 (the kernels flag e <= 0 as non-physical)
     const T SL = dmin(dmin(T(0), vl - cl), vr - cr);
     const T SR = dmax(dmax(T(0), vl + cl), vr + cr);
-    const T den = SR - SL;
-    if (den > T(0)) {
-      const T inv = drcp(den);
-      const T slsr = SL * SR;
+    const T inv = drcp(SR - SL);
+    const T slsr = SL * SR;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) F[k] = (SR * Fl[k] - SL * Fr[k] + slsr * (Ur[k] - Ul[k])) * inv;
-    } else {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (Fl[k] + Fr[k]);
-    }
+    for (int k = 0; k < NV; ++k) F[k] = (SR * Fl[k] - SL * Fr[k] + slsr * (Ur[k] - Ul[k])) * inv;
   }
   if (NV == 9) {
     F[5 + D] = psim;
