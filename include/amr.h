@@ -172,6 +172,31 @@ const char* amr_global_error(void);
 /* Free every device and host resource of the handle (NULL is a no-op). */
 void amr_destroy(amr_handle* h);
 
+/* One RK2 step of ONE uniform level-0 patch covering cfg->base_n, for callers
+ * that must not allocate device memory (a framework that owns the device
+ * allocator, a real-time loop that may not enter cudaMalloc, a process with a
+ * device-memory budget fixed at start-up).  The paper has no counterpart: it
+ * is a deployment variant of amr_step, with the same kernels.
+ *   state_in, state_out: DEVICE arrays owned by the caller, FP64 conserved
+ *     variables [nvar][n2][n1][n0] (interior cells, x fastest); may not alias.
+ *   dt > 0: step size; dt <= 0: CFL step of state_in.
+ *   dt_used: NULL (no synchronisation) or a host pointer that receives the
+ *     step taken; the call then synchronises cfg->cuda_stream and reports
+ *     non-physical states as AMR_ERR_NONPHYSICAL.
+ * No device memory is allocated or freed: the ghosted states, tables and step
+ * parameters live in one 32 MiB array compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  Limit: two
+ * ghosted states must fit, (n0+4)(n1+4)(n2+4) * nvar * bytes * 2 plus tables
+ * <= 32 MiB (about 64^3 cells for FP64 Euler); larger patches return
+ * AMR_ERR_ARG.  The first call on a device resolves that array's address, so
+ * make it before any stream capture.  All calls share the one array and leave
+ * their contents in it: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Work is ordered on
+ * cfg->cuda_stream (NULL: the legacy default stream).  AMR_ERR_ARG for a bad
+ * config or pointer, AMR_ERR_CUDA if a launch or copy fails. */
+amr_status amr_step_patch_noalloc(const amr_config* cfg, const double* state_in, double* state_out, double dt,
+                                  double* dt_used);
+
 #ifdef __cplusplus
 }
 #endif

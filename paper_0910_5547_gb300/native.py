@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "AMR_OK", -1: "AMR_ERR_ARG", -2: "AMR_ERR_NESTING", -3: "AMR_
 EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_patches", "amr_set_state",
            "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
-           "amr_destroy", "amr_set_timing", "amr_get_timing"]
+           "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
 
@@ -112,6 +112,9 @@ def load():
     L.amr_global_error.restype = ctypes.c_char_p
     L.amr_destroy.argtypes = [H]
     L.amr_destroy.restype = None
+    L.amr_step_patch_noalloc.argtypes = [ctypes.POINTER(amr_config), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, dp]
+    L.amr_step_patch_noalloc.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in ("amr_create", "amr_validate_patches", "amr_set_patches", "amr_set_state", "amr_step",
@@ -242,6 +245,25 @@ def amr_get_timing(h) -> dict:
     cnt = (ctypes.c_longlong * n)()
     _check(h, load().amr_get_timing(h, _dp(ms), cnt, n))
     return {c: (float(ms[i]), int(cnt[i])) for i, c in enumerate(TIMING_CLASSES)}
+
+
+def amr_step_patch_noalloc(cfg: amr_config, state_in_ptr: int, state_out_ptr: int, dt: float = 0.0,
+                           sync: bool = True) -> float:
+    """One RK2 step of one uniform patch with no device allocation; the pointers are
+    caller-owned DEVICE arrays (FP64 conserved, [nvar][nz][ny][nx])."""
+    L = load()
+    if sync:
+        used = ctypes.c_double(0.0)
+        st = L.amr_step_patch_noalloc(ctypes.byref(cfg), ctypes.c_void_p(state_in_ptr),
+                                      ctypes.c_void_p(state_out_ptr), dt, ctypes.byref(used))
+        if st != AMR_OK:
+            raise AmrError(st, "amr_step_patch_noalloc failed")
+        return used.value
+    st = L.amr_step_patch_noalloc(ctypes.byref(cfg), ctypes.c_void_p(state_in_ptr), ctypes.c_void_p(state_out_ptr),
+                                  dt, None)
+    if st != AMR_OK:
+        raise AmrError(st, "amr_step_patch_noalloc failed")
+    return float("nan")
 
 
 def amr_destroy(h):
