@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -400,6 +401,7 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
     h->own_stream = true;
   }
   h->ops = make_ops(*cfg);
+  if (const char* e = std::getenv("AMR_OCC")) h->ops->set_stage_occupancy(std::atoi(e));
   void* p = nullptr;
   if (cudaMalloc(&p, sizeof(StepParams)) != cudaSuccess) {
     g_global_err = "cudaMalloc of step parameters failed";
@@ -455,7 +457,9 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   }
   Plan plan;
   std::string msg;
-  amr_status st = build_plan(h->cfg, P, plan, msg);
+  TileParams tp;
+  if (const char* e = std::getenv("AMR_TILE")) std::sscanf(e, "%d,%d,%d", &tp.max_wx, &tp.max_cols, &tp.zchunk);
+  amr_status st = build_plan(h->cfg, P, plan, msg, tp);
   if (st != AMR_OK) return fail(h, st, msg);
   CK(cudaStreamSynchronize(h->stream));
   free_device(h);

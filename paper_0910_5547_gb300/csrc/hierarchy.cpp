@@ -261,7 +261,54 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
   return AMR_OK;
 }
 
-amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan, std::string& msg) {
+void build_items(Plan& plan, const TileParams& tp) {
+  const int max_wx = tp.max_wx > 0 ? std::min(tp.max_wx, kMaxTileX) : kMaxTileX;
+  const int max_cols = tp.max_cols > 0 ? std::min(tp.max_cols, kStageThreads) : kStageThreads;
+  const int zchunk = tp.zchunk > 0 ? tp.zchunk : 32;
+  const std::vector<HPatch>& P = plan.patches;
+  auto split = [](int n, int parts, std::vector<std::pair<int, int>>& out) {
+    out.clear();
+    int base = n / parts, rem = n % parts, s = 0;
+    for (int k = 0; k < parts; ++k) {
+      int w = base + (k < rem ? 1 : 0);
+      out.push_back({s, w});
+      s += w;
+    }
+  };
+  for (size_t l = 0; l < plan.levels.size(); ++l) {
+    LevelPlan& L = plan.levels[l];
+    L.items.clear();
+    L.item_first.clear();
+    L.item_first.push_back(0);
+    for (int i = L.first; i < L.first + L.count; ++i) {
+      const HPatch& p = P[i];
+      std::vector<std::pair<int, int>> xs, ys, zs;
+      split(p.n[0], (p.n[0] + max_wx - 1) / max_wx, xs);
+      int zparts = p.n[2] <= zchunk + zchunk / 2 ? 1 : (p.n[2] + zchunk - 1) / zchunk;
+      split(p.n[2], zparts, zs);
+      for (auto& z : zs)
+        for (auto& x : xs) {
+          // one halo cell per thread: 4 (wx + wy) <= 256; plane with halo within kPlaneMax
+          int wymax = std::min(std::min(max_cols / x.second, kPlaneMax / (x.second + 4) - 4),
+                               kStageThreads / 4 - x.second);
+          wymax = std::max(wymax, 1);
+          split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);
+          for (auto& y : ys) {
+            StageItem it{};
+            it.patch = i;
+            it.x0 = (int16_t)x.first; it.wx = (int16_t)x.second;
+            it.y0 = (int16_t)y.first; it.wy = (int16_t)y.second;
+            it.z0 = (int16_t)z.first; it.wz = (int16_t)z.second;
+            L.items.push_back(it);
+          }
+        }
+      L.item_first.push_back((int)L.items.size());
+    }
+  }
+}
+
+amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan, std::string& msg,
+                      const TileParams& tp) {
   amr_status st = validate_patches(cfg, P, msg);
   if (st != AMR_OK) return st;
   plan = Plan();
@@ -308,43 +355,8 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   plan.tile_elems = toff;
   plan.packed_elems = poff;
 
-  // ---- stage work items: x tiles <= 32 wide, y tiles filling 256 columns, z chunks ----
-  for (int l = 0; l < nlev; ++l) {
-    LevelPlan& L = plan.levels[l];
-    L.item_first.push_back(0);
-    for (int i = L.first; i < L.first + L.count; ++i) {
-      const HPatch& p = P[i];
-      auto split = [](int n, int parts, std::vector<std::pair<int, int>>& out) {
-        out.clear();
-        int base = n / parts, rem = n % parts, s = 0;
-        for (int k = 0; k < parts; ++k) {
-          int w = base + (k < rem ? 1 : 0);
-          out.push_back({s, w});
-          s += w;
-        }
-      };
-      std::vector<std::pair<int, int>> xs, ys, zs;
-      split(p.n[0], (p.n[0] + kMaxTileX - 1) / kMaxTileX, xs);
-      int zparts = p.n[2] <= 48 ? 1 : (p.n[2] + 31) / 32;
-      split(p.n[2], zparts, zs);
-      for (auto& z : zs)
-        for (auto& x : xs) {
-          // one halo cell per thread: 4 (wx + wy) <= 256
-          int wymax = std::min(std::min(kStageThreads / x.second, kPlaneMax / (x.second + 4) - 4),
-                               kStageThreads / 4 - x.second);
-          split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);
-          for (auto& y : ys) {
-            StageItem it{};
-            it.patch = i;
-            it.x0 = (int16_t)x.first; it.wx = (int16_t)x.second;
-            it.y0 = (int16_t)y.first; it.wy = (int16_t)y.second;
-            it.z0 = (int16_t)z.first; it.wz = (int16_t)z.second;
-            L.items.push_back(it);
-          }
-        }
-      L.item_first.push_back((int)L.items.size());
-    }
-  }
+  // ---- stage work items ----
+  build_items(plan, tp);
 
   // ---- ghost fill: sibling copies (incl. periodic images), outflow, prolongation boxes ----
   for (int l = 0; l < nlev; ++l) {

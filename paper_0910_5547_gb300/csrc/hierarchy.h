@@ -52,9 +52,20 @@ struct Plan {
 amr_status validate_config(const amr_config& cfg, std::string& msg);
 amr_status validate_patches(const amr_config& cfg, const std::vector<HPatch>& P, std::string& msg);
 
+// Shape of the stage kernel's work items: x width cap, columns per CTA (<= 256)
+// and z chunk length.  Zero fields take the defaults (32, 256, 32).
+struct TileParams {
+  int max_wx = 0;
+  int max_cols = 0;
+  int zchunk = 0;
+};
+
+// Rebuild only the stage work items of `plan` with another tile shape.
+void build_items(Plan& plan, const TileParams& tp);
+
 // Validate and build every table.  `align` = element alignment of patch
 // offsets (e.g. 64 for 256-byte alignment of FP32 arrays).
 amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan,
-                      std::string& msg);
+                      std::string& msg, const TileParams& tp = TileParams());
 
 }  // namespace amr

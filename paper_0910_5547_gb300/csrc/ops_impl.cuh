@@ -10,7 +10,8 @@ template <typename T, int NV>
 struct Ops final : OpsBase {
   Phys<T> ph{};
   double gamma = 1.4;
-  int max_stage_ctas = 0;
+  int occ = 0;   // 0: default build; 3: three-CTA build (FP32 Euler)
+  static constexpr bool kHasOcc3 = sizeof(T) == 4 && NV == 5;
 
   explicit Ops(const PhysParams& p) {
     gamma = p.gamma;
@@ -24,7 +25,16 @@ struct Ops final : OpsBase {
                          (int)stage_smem_bytes<T, NV>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem_bytes<T, NV>());
+    if (kHasOcc3) {
+      cudaFuncSetAttribute(stage_kernel<T, NV, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)stage_smem_bytes<T, NV>());
+      cudaFuncSetAttribute(stage_kernel<T, NV, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)stage_smem_bytes<T, NV>());
+    }
   }
+
+  int stage_occupancy() const override { return occ == 3 ? 3 : ((sizeof(T) == 4 && NV == 5) ? 2 : 1); }
+  void set_stage_occupancy(int c) override { occ = (kHasOcc3 && c == 3) ? 3 : 0; }
 
   size_t elem_size() const override { return sizeof(T); }
 
@@ -50,8 +60,13 @@ struct Ops final : OpsBase {
     a.ph = ph;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
     const size_t sm = stage_smem_bytes<T, NV>();
-    if (stage == 1) stage_kernel<T, NV, 1><<<g, kStageThreads, sm, s>>>(a);
-    else stage_kernel<T, NV, 2><<<g, kStageThreads, sm, s>>>(a);
+    if (kHasOcc3 && occ == 3) {
+      if (stage == 1) stage_kernel<T, NV, 1, 3><<<g, kStageThreads, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, 3><<<g, kStageThreads, sm, s>>>(a);
+    } else {
+      if (stage == 1) stage_kernel<T, NV, 1><<<g, kStageThreads, sm, s>>>(a);
+      else stage_kernel<T, NV, 2><<<g, kStageThreads, sm, s>>>(a);
+    }
     return cudaGetLastError();
   }
 

@@ -104,8 +104,44 @@ __device__ __forceinline__ void state_flux(const T* w, const Phys<T>& ph, T* U, 
 
 // Interface flux along D from reconstructed left/right states (copied: the MHD
 // branch overwrites the normal field with the Dedner-resolved value).
+// Euler HLL without forming the two physical fluxes: with F = U v_n + P,
+// P = (0, p e_D, p v_n), the two-wave flux
+//   (S_R F_l - S_L F_r + S_L S_R (U_r - U_l)) / (S_R - S_L)
+// equals alpha U_l + beta U_r + (S_R P_l - S_L P_r) / (S_R - S_L) with
+// alpha = S_R (v_l - S_L) / (S_R - S_L) and beta = S_L (S_R - v_r) / (S_R - S_L).
+template <typename T, int D>
+__device__ __forceinline__ void hll_euler(const T* wl, const T* wr, const Phys<T>& ph, T* F) {
+  T Ul[5], Ur[5];
+  const T rl = wl[0], rr = wr[0];
+  const T vl = wl[1 + D], vr = wr[1 + D];
+  Ul[0] = rl; Ul[1] = rl * wl[1]; Ul[2] = rl * wl[2]; Ul[3] = rl * wl[3];
+  Ur[0] = rr; Ur[1] = rr * wr[1]; Ur[2] = rr * wr[2]; Ur[3] = rr * wr[3];
+  const T v2l = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
+  const T v2r = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
+  Ul[4] = rl * (T(0.5) * v2l + wl[4]);
+  Ur[4] = rr * (T(0.5) * v2r + wr[4]);
+  const T pl = ph.gm1 * (rl * wl[4]), pr = ph.gm1 * (rr * wr[4]);
+  const T cl = dsqrt(ph.ggm1 * wl[4]), cr = dsqrt(ph.ggm1 * wr[4]);
+  const T SL = dmin(dmin(T(0), vl - cl), vr - cr);
+  const T SR = dmax(dmax(T(0), vl + cl), vr + cr);
+  const T inv = drcp(SR - SL);
+  const T alpha = SR * (vl - SL) * inv;
+  const T beta = SL * (SR - vr) * inv;
+  const T pS = SR * pl, pSr = SL * pr;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) F[k] = alpha * Ul[k] + beta * Ur[k];
+  F[1 + D] += (pS - pSr) * inv;
+  F[4] += (pS * vl - pSr * vr) * inv;
+}
+
 template <typename T, int NV, int D>
 __device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
+  if (NV == 5) {
+    if (!ph.llf) {
+      hll_euler<T, D>(wl, wr, ph, F);
+      return;
+    }
+  }
   T Bm = T(0), psim = T(0);
   if (NV == 9) {
     const T Bl = wl[5 + D], Br = wr[5 + D];
