@@ -187,14 +187,12 @@ def nested_cubes(base: int, sides: Sequence[int], seed: int, pmin=8, pmax=32) ->
     return patches
 
 
-def sedov_amr(base: int = 128, sides=(192, 224, 224), seed: int = 20092, gamma: float = 1.4,
-              E: float = 1.0, r0_cells: float = 2.0, rho: float = 1.0, p_amb: float = 1e-5) -> Problem:
-    """Static nested hierarchy around a Sedov-Taylor blast (Sec. 6.2 set-up): E deposited in
-    cells whose centre lies within r0 = r0_cells finest cells of the box centre,
-    p_in = 3 (gamma-1) E / (4 pi r0^3); ambient rho and p elsewhere; outflow."""
-    patches = nested_cubes(base, sides, seed)
-    L = len(sides)
-    r0 = r0_cells / (base << L)
+def sedov_prim(patches: List[Patch], base: int, levels: int, gamma: float = 1.4, E: float = 1.0,
+               r0_cells: float = 2.0, rho: float = 1.0, p_amb: float = 1e-5):
+    """Primitive Sedov-Taylor initial data (Sec. 6.2) on any patches of a hierarchy with
+    `levels` refinements over a base^3 unit box: p_in = 3 (gamma-1) E / (4 pi r0^3) in cells
+    whose centre lies within r0 = r0_cells finest cells of the box centre."""
+    r0 = r0_cells / (base << levels)
     p_in = 3.0 * (gamma - 1.0) * E / (4.0 * np.pi * r0 ** 3)
 
     def fn(p, w, x, y, z):
@@ -202,9 +200,19 @@ def sedov_amr(base: int = 128, sides=(192, 224, 224), seed: int = 20092, gamma: 
         w[0] = rho
         w[4] = np.where(np.broadcast_to(r2 <= r0 * r0, w.shape[1:]), p_in, p_amb)
 
-    return Problem("sedov_amr", 5, gamma, (base,) * 3, (OUTFLOW,) * 6, patches,
-                   _fill(patches, (base,) * 3, 5, fn), max_level=L,
-                   meta={"seed": seed, "p_in": p_in, "r0": r0})
+    return _fill(patches, (base,) * 3, 5, fn), p_in, r0
+
+
+def sedov_amr(base: int = 128, sides=(192, 224, 224), seed: int = 20092, gamma: float = 1.4,
+              E: float = 1.0, r0_cells: float = 2.0, rho: float = 1.0, p_amb: float = 1e-5) -> Problem:
+    """Static nested hierarchy around a Sedov-Taylor blast (Sec. 6.2 set-up): E deposited in
+    cells whose centre lies within r0 = r0_cells finest cells of the box centre,
+    p_in = 3 (gamma-1) E / (4 pi r0^3); ambient rho and p elsewhere; outflow."""
+    patches = nested_cubes(base, sides, seed)
+    L = len(sides)
+    prim, p_in, r0 = sedov_prim(patches, base, L, gamma, E, r0_cells, rho, p_amb)
+    return Problem("sedov_amr", 5, gamma, (base,) * 3, (OUTFLOW,) * 6, patches, prim, max_level=L,
+                   meta={"seed": seed, "p_in": p_in, "r0": r0, "sides": tuple(sides)})
 
 
 def orszag_tang(N: int = 192, tile: int | None = 32, seed: int = 20095, gamma: float = 5.0 / 3.0,

@@ -48,6 +48,24 @@ def dist_env():
     return ws, rank, local
 
 
+def stage_traffic():
+    """DRAM bytes per stage-kernel launch (mean of stage 1 and stage 2) from the committed ncu
+    summary, used only while the kernel source is the one that was profiled."""
+    import hashlib
+    import re
+    src = b"".join(open(os.path.join(ROOT, "paper_0910_5547_gb300", "csrc", f), "rb").read()
+                   for f in ("kernels.cuh", "physics.cuh", "amr_types.h"))
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "stage_kernel_fp32_kh256.md")).read()
+        m = re.search(r"source_sha=(\w+) traffic_per_launch=(\d+)", txt)
+        if m and m.group(1) == sha:
+            return int(m.group(2))
+    except OSError:
+        pass
+    return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -192,7 +210,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--only", default="",
-                    help="comma list of phases: fp32,tiled,fp64,plain,e2e (default: all)")
+                    help="comma list of phases: fp32,tiled,fp64,plain,e2e,amr,mhd (default: all)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -216,7 +234,7 @@ def main():
         dist.barrier()
 
     import amr_inputs as ai
-    phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e"}
+    phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e", "amr", "mhd"}
     single = ai.kelvin_helmholtz(N=N, tile=None)          # one 256^3 patch
     tiled = ai.kelvin_helmholtz(N=N, tile=TILE) if phases & {"tiled", "plain"} else None
     cells = N ** 3
@@ -289,6 +307,49 @@ def main():
         if "fp32_tiled_512" in extra:
             extra["batched_fp32_over_plain_fp64"] = extra["fp32_tiled_512"]["value"] / extra["fp64_plain"]["value"]
 
+    def amr_rates(pb, label, fp64_plain_steps=1):
+        """Cell-updates/s (sum over levels of cells_l 2^l per coarse step) of the batched FP32
+        path and the plain per-patch FP64 path on a multi-level hierarchy, plus kernel-class times."""
+        cu = pb.cell_updates_per_coarse_step()
+        so = make_solver(pb, "fp32", True, True, stream)
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        ka = max(3, args.steps // 20)
+        t = timed_steps(torch, so, stream, ka)
+        NV.amr_set_timing(so.h, True)
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        tmk = NV.amr_get_timing(so.h)
+        NV.amr_set_timing(so.h, False)
+        so.check()
+        so.close()
+        out = {"value": ws * cu * ka / max_over_ranks(t), "unit": UNIT, "steps": ka, "patches": len(pb.patches),
+               "levels": pb.nlevels, "cell_updates_per_coarse_step": cu,
+               "class_ms_per_coarse_step": {k: round(v[0] / 2, 3) for k, v in tmk.items() if v[1]},
+               "workload": label}
+        if fp64_plain_steps:
+            sp = make_solver(pb, "fp64", False, False, stream)
+            sp.step(0.0, sync=False)
+            tp = timed_steps(torch, sp, stream, fp64_plain_steps)
+            sp.check()
+            sp.close()
+            out["fp64_plain"] = ws * cu * fp64_plain_steps / max_over_ranks(tp)
+            out["batched_fp32_over_plain_fp64"] = out["value"] / out["fp64_plain"]
+        return out
+
+    if "amr" in phases:
+        extra["amr_static_sedov"] = amr_rates(
+            ai.sedov_amr(), "static 4-level Sedov hierarchy, base 128^3, seeded 8-32 patches, outflow")
+    if "mhd" in phases:
+        ot = ai.orszag_tang(N=192, tile=None)
+        mhd = {"fp32_uniform_192": rate(ot, "fp32", True, True, max(3, args.steps // 4)) * (192 ** 3) / cells}
+        del ot
+        mhd["fp32_over_hydro_fp32_per_cell"] = mhd["fp32_uniform_192"] / value
+        mhd["amr_3level"] = amr_rates(ai.orszag_tang(amr_sides=(96, 96), amr_base=96),
+                                      "GLM-MHD Orszag-Tang, 3 levels, base 96^3", fp64_plain_steps=0)
+        mhd["unit"] = UNIT
+        extra["mhd_orszag_tang"] = mhd
+
     e2e = None
     if "e2e" in phases:
         s = make_solver(single, "fp32", True, True, stream)
@@ -327,9 +388,13 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         **extra,
         "roofline": {"bound": "hbm", "kernel": "stage_kernel (stage 1 + stage 2)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": stage_traffic(),
+                     "algorithmic_per_launch": stage_bytes // 2,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_cell_update": (2 + 3) * V * W,
+                     "note": "achieved = algorithmic bytes of the stage-1 and stage-2 launches over their summed "
+                             "CUDA-event durations; traffic = mean DRAM bytes per launch from the committed ncu "
+                             "capture (null if the kernel source changed since)",
                      "timed_steps": ksteps},
         "step_kernel_ms": step_kernel_ms,
         "cell_update_roofline_frac": value / ws * (2 + 3) * V * W / (peak * 1e9),
