@@ -337,3 +337,51 @@ def cp_alfven(n: int = 32, amp: float = 0.1, rho: float = 1.0, p: float = 0.1, B
 
     return Problem("cp_alfven", 9, gamma, N, (PERIODIC,) * 6, patches, _fill(patches, N, 9, fn),
                    meta={"amp": amp, "speed": Bx / np.sqrt(rho)})
+
+
+def _trilinear_periodic(field: np.ndarray, x, y, z):
+    """Periodic trilinear interpolation of a cell-centred unit-box field [z][y][x] at points."""
+    n = field.shape[0]
+    gx, gy, gz = x * n - 0.5, y * n - 0.5, z * n - 0.5
+    i0, j0, k0 = np.floor(gx).astype(int), np.floor(gy).astype(int), np.floor(gz).astype(int)
+    fx, fy, fz = gx - i0, gy - j0, gz - k0
+    out = 0.0
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                w = (fx if di else 1 - fx) * (fy if dj else 1 - fy) * (fz if dk else 1 - fz)
+                out = out + w * field[(k0 + dk) % n, (j0 + dj) % n, (i0 + di) % n]
+    return out
+
+
+def blast_clumps(base: int = 64, levels: int = 5, side: int = 64, seed: int = 20093, sigma: float = 1.0,
+                 smooth: float = 2.0, gamma: float = 1.4, E: float = 1.0, r0_cells: float = 2.0,
+                 p_amb: float = 1e-5) -> Problem:
+    """Adaptive-AMR workload: a spherical blast (Sec. 6.2 deposit in r <= r0_cells finest cells)
+    in a seeded log-normal clump field rho = exp(sigma g - sigma^2 / 2), g unit-variance Gaussian
+    white noise on the base grid smoothed by a Gaussian of `smooth` base cells (periodic FFT) and
+    sampled trilinearly at every level; pressure p_amb outside the blast; outflow.  The initial
+    hierarchy is `levels` nested centred cubes of `side` cells around the blast (seeded 8-32
+    patches); later hierarchies come from regridding."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = rng.standard_normal((base,) * 3)
+    k = np.fft.fftfreq(base) * base
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    filt = np.exp(-0.5 * (2 * np.pi * smooth / base) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
+    g = np.real(np.fft.ifftn(np.fft.fftn(g) * filt))
+    g = (g - g.mean()) / g.std()
+    patches = nested_cubes(base, (side,) * levels, seed)
+    r0 = r0_cells / (base << levels)
+    p_in = 3.0 * (gamma - 1.0) * E / (4.0 * np.pi * r0 ** 3)
+
+    def fn(p, w, x, y, z):
+        shp = w.shape[1:]
+        X, Y, Z = np.broadcast_arrays(x, y, z)
+        w[0] = np.exp(sigma * _trilinear_periodic(g, X, Y, Z) - 0.5 * sigma ** 2).reshape(shp)
+        r2 = (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2
+        w[4] = np.where(r2 <= r0 * r0, p_in, p_amb)
+
+    return Problem("blast_clumps", 5, gamma, (base,) * 3, (OUTFLOW,) * 6, patches,
+                   _fill(patches, (base,) * 3, 5, fn), max_level=levels,
+                   meta={"seed": seed, "p_in": p_in, "r0": r0})
+

@@ -210,7 +210,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--only", default="",
-                    help="comma list of phases: fp32,tiled,fp64,plain,e2e,amr,mhd (default: all)")
+                    help="comma list of phases: fp32,tiled,fp64,plain,e2e,amr,amr32,mhd,adaptive (default: "
+                         "all but amr32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -234,7 +235,8 @@ def main():
         dist.barrier()
 
     import amr_inputs as ai
-    phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e", "amr", "mhd"}
+    phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e", "amr", "mhd",
+                                                          "adaptive"}
     single = ai.kelvin_helmholtz(N=N, tile=None)          # one 256^3 patch
     tiled = ai.kelvin_helmholtz(N=N, tile=TILE) if phases & {"tiled", "plain"} else None
     cells = N ** 3
@@ -337,9 +339,32 @@ def main():
             out["batched_fp32_over_plain_fp64"] = out["value"] / out["fp64_plain"]
         return out
 
-    if "amr" in phases:
+    if "amr" in phases or "amr32" in phases:
         extra["amr_static_sedov"] = amr_rates(
-            ai.sedov_amr(), "static 4-level Sedov hierarchy, base 128^3, seeded 8-32 patches, outflow")
+            ai.sedov_amr(), "static 4-level Sedov hierarchy, base 128^3, seeded 8-32 patches, outflow",
+            fp64_plain_steps=1 if "amr" in phases else 0)
+    if "adaptive" in phases:
+        pb = ai.blast_clumps()
+        so = make_solver(pb, "fp32", True, True, stream)
+        so.step(0.0)
+        so.regrid(threshold=0.3, buffer=4, block=4, max_patch=32)
+        tot_cu, t_steps, t_regrid, counts = 0, 0.0, 0.0, []
+        for _ in range(4):
+            cu = sum((p.n[0] * p.n[1] * p.n[2]) << p.level for p in so.patches)
+            t_steps += timed_steps(torch, so, stream, 1)
+            t0 = time.perf_counter()
+            so.regrid(threshold=0.3, buffer=4, block=4, max_patch=32)
+            t_regrid += time.perf_counter() - t0
+            tot_cu += cu
+            counts.append([len(so.patches), 1 + max(p.level for p in so.patches)])
+        so.check()
+        so.close()
+        extra["adaptive_blast_clumps"] = {
+            "value": ws * tot_cu / max_over_ranks(t_steps), "value_with_regrid": ws * tot_cu / max_over_ranks(
+                t_steps + t_regrid), "unit": UNIT, "coarse_steps": 4, "cell_updates": tot_cu,
+            "regrid_s": t_regrid, "patches_levels_after_each_regrid": counts,
+            "workload": "blast in a log-normal clump field (sigma 1), base 64^3 + 5 levels, FP32 batched, "
+                        "density-gradient regrid (threshold 0.3) after every coarse step"}
     if "mhd" in phases:
         ot = ai.orszag_tang(N=192, tile=None)
         mhd = {"fp32_uniform_192": rate(ot, "fp32", True, True, max(3, args.steps // 4)) * (192 ** 3) / cells}

@@ -106,6 +106,34 @@ amr_status amr_validate_patches(const amr_config* cfg, int npatch, const amr_pat
 amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches,
                            const double* const* state, int state_kind);
 
+/* Regridding parameters (Sec. 3: grids are created and refined on the host).
+ * Cells of levels min_level .. max_level-1 are flagged where
+ *   max_d |rho(i + e_d) - rho(i - e_d)| / (2 rho(i)) > threshold
+ * (density-gradient criterion, evaluated on the GPU in the bulk precision),
+ * grown by `buffer` cells, and covered by blocks of `block` cells of their
+ * level; refinable blocks (whose 26 neighbours lie inside the level, so the
+ * new patches are properly nested) are merged greedily into boxes whose refined
+ * edge is 2*block .. max_patch fine cells. */
+typedef struct {
+  double threshold;   /* default 0.3 */
+  int buffer;         /* flagged cells grown by this many cells, 0 .. block (default 2) */
+  int block;          /* clustering block edge in cells of the flagged level, even >= 2 (default 4) */
+  int max_patch;      /* largest new patch edge in its own cells, multiple of 2*block (default 32) */
+  int min_level;      /* levels <= min_level are kept as they are (default 0) */
+} amr_regrid_params;
+
+/* Rebuild levels min_level+1 .. max_level from the current state: flag, cluster
+ * on the host, then fill the new patches on the GPU -- same-level cells are
+ * copied from the old patches, the others are prolonged conservatively from the
+ * new parent level.  Totals are conserved.  prm == NULL takes the defaults.
+ * *npatch_out (may be NULL) receives the new patch count.  Synchronises;
+ * invalidates the step graphs. */
+amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_out);
+
+/* Copy up to `capacity` patches of the installed hierarchy (sorted by level) to
+ * out (may be NULL) and return the patch count (-1 before amr_set_patches). */
+int amr_get_patches(const amr_handle* h, amr_patch* out, int capacity);
+
 /* Replace the state of the installed patches from ONE packed host buffer: all
  * patches in patch order, each [nvar][n2][n1][n0] FP64 (amr_state_size doubles).
  * Pinned host memory gives asynchronous copies.  Stream-ordered; no sync. */

@@ -882,3 +882,66 @@ void orc_totals(const orc_sim* s, double* out) {
     }
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Regridding (Sec. 3: the hierarchy is created and refined on the host)     */
+/* ------------------------------------------------------------------------ */
+
+int orc_flags(orc_sim* s, double threshold, unsigned char* out) {
+  for (int l = 0; l < s->nlev; ++l) save_old_level(s, l);
+  for (int l = 0; l < s->nlev; ++l)
+    if (fill_ghosts_level(s, l, 0, 1.0)) return -1;
+  size_t o = 0;
+  for (int pi = 0; pi < s->np; ++pi) {
+    opatch* p = &s->P[pi];
+    const double* R = p->U;  /* density = variable 0 */
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i) {
+          double rho = R[gidx(p, i, j, k)];
+          double g = 0.0, d;
+          d = fabs(R[gidx(p, i + 1, j, k)] - R[gidx(p, i - 1, j, k)]); if (d > g) g = d;
+          d = fabs(R[gidx(p, i, j + 1, k)] - R[gidx(p, i, j - 1, k)]); if (d > g) g = d;
+          d = fabs(R[gidx(p, i, j, k + 1)] - R[gidx(p, i, j, k - 1)]); if (d > g) g = d;
+          out[o++] = (g / (2.0 * rho) > threshold) ? 1 : 0;
+        }
+  }
+  return 0;
+}
+
+orc_sim* orc_regrid_fill(orc_sim* old, int npatch, const orc_patch* patches, int keep_level) {
+  orc_sim* s = orc_create(&old->cfg, npatch, patches);
+  if (!s) return NULL;
+  s->ch_used = old->ch_used;
+  const int V = s->V;
+  for (int l = 0; l < s->nlev; ++l) {
+    for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi) {
+      opatch* p = &s->P[pi];
+      for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+          for (int i = 0; i < p->n[0]; ++i) {
+            int g[3] = {p->lo[0] + i, p->lo[1] + j, p->lo[2] + k};
+            int q = -1;
+            if (l < old->nlev)
+              for (int c = old->lev_first[l]; c < old->lev_first[l] + old->lev_count[l]; ++c)
+                if (contains(&old->P[c], g)) { q = c; break; }
+            size_t dst = gidx(p, i, j, k);
+            if (q >= 0) {
+              const opatch* o = &old->P[q];
+              size_t src = gidx(o, g[0] - o->lo[0], g[1] - o->lo[1], g[2] - o->lo[2]);
+              for (int v = 0; v < V; ++v) p->U[v * p->ncell_g + dst] = o->U[v * o->ncell_g + src];
+            } else {
+              double val[MAXV];
+              if (l <= keep_level || l == 0 || prolong(s, p, g, 1.0, val)) {
+                snprintf(g_err, sizeof g_err, "regrid: cell of patch %d has no source", pi);
+                orc_destroy(s);
+                return NULL;
+              }
+              for (int v = 0; v < V; ++v) p->U[v * p->ncell_g + dst] = val[v];
+            }
+          }
+    }
+  }
+  return s;
+}
+

@@ -74,6 +74,17 @@ int orc_get_ghosted(const orc_sim* s, int patch, int which, double* out);
  * prolongation (done automatically at the start of every coarse-level step). */
 int orc_save_old(orc_sim* s, int level);
 
+/* ---- regridding ----
+ * orc_flags: after filling every level's face ghosts at the current time, one
+ * byte per interior cell of every patch (patch order, [z][y][x]): 1 where
+ * max_d |rho(i+e_d) - rho(i-e_d)| / (2 rho(i)) > threshold.
+ * orc_regrid_fill: a new simulation on `patches`, whose levels <= keep_level are
+ * the old ones unchanged; a cell of a finer level takes the old same-level
+ * value where an old patch holds it, else the conservative prolongation of the
+ * (new) parent level.  Returns NULL on error. */
+int orc_flags(orc_sim* s, double threshold, unsigned char* out);
+orc_sim* orc_regrid_fill(orc_sim* old, int npatch, const orc_patch* patches, int keep_level);
+
 /* ---- point functions, exposed for unit pins ---- */
 double orc_minmod3(double a, double b, double c);
 double orc_minmod2(double a, double b);

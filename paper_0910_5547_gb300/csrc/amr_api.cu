@@ -341,6 +341,149 @@ size_t put(std::vector<unsigned char>& buf, const std::vector<X>& v) {
   return off;
 }
 
+TileParams tile_params() {
+  TileParams tp;
+  if (const char* e = std::getenv("AMR_TILE")) std::sscanf(e, "%d,%d,%d", &tp.max_wx, &tp.max_cols, &tp.zchunk);
+  return tp;
+}
+
+// Device buffers of one installed plan.
+struct DeviceBufs {
+  void* U = nullptr;
+  void* U1 = nullptr;
+  void* Uold = nullptr;
+  void* tile = nullptr;
+  double* packed = nullptr;
+  double* partial = nullptr;
+  double* totals = nullptr;
+  double* regs = nullptr;
+  unsigned char* tables = nullptr;
+};
+
+// Take the buffers out of the handle (graphs are dropped: they refer to them).
+DeviceBufs detach(amr_handle* h) {
+  for (int g = 0; g < 4; ++g) {
+    if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+    h->graph[g] = nullptr;
+  }
+  DeviceBufs b;
+  b.U = h->U; b.U1 = h->U1; b.Uold = h->Uold; b.tile = h->tile;
+  b.packed = h->packed; b.partial = h->partial; b.totals = h->totals; b.regs = h->regs; b.tables = h->tables;
+  h->U = h->U1 = h->Uold = h->tile = nullptr;
+  h->packed = h->partial = h->totals = h->regs = nullptr;
+  h->tables = nullptr;
+  h->dl.clear();
+  h->ready = false;
+  h->rates_valid = false;
+  return b;
+}
+
+void free_bufs(DeviceBufs& b) {
+  void* ptrs[] = {b.U, b.U1, b.Uold, b.tile, b.packed, b.partial, b.totals, b.regs, b.tables};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  b = DeviceBufs();
+}
+
+// Allocate the device state of `plan` and upload its tables (state left zero).
+amr_status install_plan(amr_handle* h, Plan&& plan) {
+  h->plan = std::move(plan);
+  Plan& pl = h->plan;
+  const int nv = pl.nvar;
+  const size_t es = h->ops->elem_size();
+  const int nlev = (int)pl.levels.size();
+  const int npatch = (int)pl.patches.size();
+  // chunks of <= 16384 interior cells
+  h->chunks.clear();
+  for (int i = 0; i < npatch; ++i) {
+    int nc = pl.patches[i].n[0] * pl.patches[i].n[1] * pl.patches[i].n[2];
+    for (int b = 0; b < nc; b += 16384) h->chunks.push_back({i, b, std::min(16384, nc - b)});
+  }
+  h->nchunk = (int)h->chunks.size();
+  std::vector<size_t> reg_off(nlev, 0);
+  size_t nregd = 0;
+  for (int l = 1; l < nlev; ++l) {
+    reg_off[l] = nregd;
+    nregd += 2 * (size_t)nv * pl.levels[l].regs.size();
+  }
+  std::vector<unsigned char> buf;
+  size_t o_desc = put(buf, pl.desc);
+  size_t o_chunks = put(buf, h->chunks);
+  size_t o_cover = put(buf, pl.cover);
+  size_t o_cover_first = put(buf, pl.cover_first);
+  size_t o_packed_off = put(buf, pl.packed_off);
+  std::vector<double> lvol(nlev);
+  for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
+  size_t o_lvol = put(buf, lvol);
+  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; };
+  std::vector<Offs> lo(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = pl.levels[l];
+    lo[l].items = put(buf, L.items);
+    lo[l].ghost = put(buf, L.ghost);
+    lo[l].prolong = put(buf, L.prolong);
+    lo[l].gather = put(buf, L.gather);
+    lo[l].restr = put(buf, L.restrict_segs);
+    lo[l].regs = put(buf, L.regs);
+    lo[l].rf = put(buf, L.reflux_first);
+  }
+  void* p = nullptr;
+  CK(cudaMalloc(&p, buf.size()));
+  h->tables = static_cast<unsigned char*>(p);
+  CK(cudaMemcpyAsync(h->tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  h->d_desc = reinterpret_cast<const PatchDesc*>(h->tables + o_desc);
+  h->d_chunks = reinterpret_cast<const ChunkDesc*>(h->tables + o_chunks);
+  h->d_cover = reinterpret_cast<const CoverBox*>(h->tables + o_cover);
+  h->d_cover_first = reinterpret_cast<const int*>(h->tables + o_cover_first);
+  h->d_packed_off = reinterpret_cast<const int64_t*>(h->tables + o_packed_off);
+  h->d_level_vol = reinterpret_cast<const double*>(h->tables + o_lvol);
+  CK(cudaMalloc(&h->U, pl.arena_elems * es));
+  CK(cudaMalloc(&h->U1, pl.arena_elems * es));
+  CK(cudaMemsetAsync(h->U, 0, pl.arena_elems * es, h->stream));
+  CK(cudaMemsetAsync(h->U1, 0, pl.arena_elems * es, h->stream));
+  if (nlev > 1) {
+    CK(cudaMalloc(&h->Uold, pl.arena_elems * es));
+    CK(cudaMemsetAsync(h->Uold, 0, pl.arena_elems * es, h->stream));
+    CK(cudaMalloc(&h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
+  }
+  CK(cudaMalloc(&p, std::max<int64_t>(pl.packed_elems, 1) * sizeof(double)));
+  h->packed = static_cast<double*>(p);
+  CK(cudaMalloc(&p, (size_t)h->nchunk * nv * sizeof(double)));
+  h->partial = static_cast<double*>(p);
+  CK(cudaMalloc(&p, 16 * sizeof(double)));
+  h->totals = static_cast<double*>(p);
+  if (nregd) {
+    CK(cudaMalloc(&p, nregd * sizeof(double)));
+    h->regs = static_cast<double*>(p);
+    CK(cudaMemsetAsync(h->regs, 0, nregd * sizeof(double), h->stream));
+  }
+  h->dl.assign(nlev, DevLevel());
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = pl.levels[l];
+    DevLevel& D = h->dl[l];
+    D.nitems = (int)L.items.size();
+    D.nghost = (int)L.ghost.size();
+    D.nprolong = (int)L.prolong.size();
+    D.ngather = (int)L.gather.size();
+    D.nrestrict = (int)L.restrict_segs.size();
+    D.nreg = (int)L.regs.size();
+    D.nuniq = L.reflux_first.empty() ? 0 : (int)L.reflux_first.size() - 1;
+    D.items = reinterpret_cast<const StageItem*>(h->tables + lo[l].items);
+    D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
+    D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
+    D.gather = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather);
+    D.restrict_segs = reinterpret_cast<const RestrictSeg*>(h->tables + lo[l].restr);
+    D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
+    D.reflux_first = reinterpret_cast<const int*>(h->tables + lo[l].rf);
+    D.R = h->regs ? h->regs + reg_off[l] : nullptr;
+    const PatchDesc& a = pl.desc[L.first];
+    const PatchDesc& b = pl.desc[L.first + L.count - 1];
+    D.arena_begin = a.off;
+    D.arena_end = b.off + b.vstride * nv;
+  }
+  return AMR_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -457,113 +600,15 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   }
   Plan plan;
   std::string msg;
-  TileParams tp;
-  if (const char* e = std::getenv("AMR_TILE")) std::sscanf(e, "%d,%d,%d", &tp.max_wx, &tp.max_cols, &tp.zchunk);
-  amr_status st = build_plan(h->cfg, P, plan, msg, tp);
+  amr_status st = build_plan(h->cfg, P, plan, msg, tile_params());
   if (st != AMR_OK) return fail(h, st, msg);
   CK(cudaStreamSynchronize(h->stream));
-  free_device(h);
-  h->plan = std::move(plan);
+  DeviceBufs old = detach(h);
+  free_bufs(old);
+  st = install_plan(h, std::move(plan));
+  if (st != AMR_OK) return st;
   Plan& pl = h->plan;
   const int nv = pl.nvar;
-  const size_t es = h->ops->elem_size();
-  const int nlev = (int)pl.levels.size();
-
-  // chunks of <= 16384 interior cells
-  h->chunks.clear();
-  for (int i = 0; i < npatch; ++i) {
-    int nc = P[i].n[0] * P[i].n[1] * P[i].n[2];
-    for (int b = 0; b < nc; b += 16384) h->chunks.push_back({i, b, std::min(16384, nc - b)});
-  }
-  h->nchunk = (int)h->chunks.size();
-
-  // registers
-  std::vector<size_t> reg_off(nlev, 0);
-  size_t nregd = 0;
-  for (int l = 1; l < nlev; ++l) {
-    reg_off[l] = nregd;
-    nregd += 2 * (size_t)nv * pl.levels[l].regs.size();
-  }
-
-  // one table buffer
-  std::vector<unsigned char> buf;
-  size_t o_desc = put(buf, pl.desc);
-  size_t o_chunks = put(buf, h->chunks);
-  size_t o_cover = put(buf, pl.cover);
-  size_t o_cover_first = put(buf, pl.cover_first);
-  size_t o_packed_off = put(buf, pl.packed_off);
-  std::vector<double> lvol(nlev);
-  for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
-  size_t o_lvol = put(buf, lvol);
-  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; };
-  std::vector<Offs> lo(nlev);
-  for (int l = 0; l < nlev; ++l) {
-    LevelPlan& L = pl.levels[l];
-    lo[l].items = put(buf, L.items);
-    lo[l].ghost = put(buf, L.ghost);
-    lo[l].prolong = put(buf, L.prolong);
-    lo[l].gather = put(buf, L.gather);
-    lo[l].restr = put(buf, L.restrict_segs);
-    lo[l].regs = put(buf, L.regs);
-    lo[l].rf = put(buf, L.reflux_first);
-  }
-  void* p = nullptr;
-  CK(cudaMalloc(&p, buf.size()));
-  h->tables = static_cast<unsigned char*>(p);
-  CK(cudaMemcpyAsync(h->tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
-  h->d_desc = reinterpret_cast<const PatchDesc*>(h->tables + o_desc);
-  h->d_chunks = reinterpret_cast<const ChunkDesc*>(h->tables + o_chunks);
-  h->d_cover = reinterpret_cast<const CoverBox*>(h->tables + o_cover);
-  h->d_cover_first = reinterpret_cast<const int*>(h->tables + o_cover_first);
-  h->d_packed_off = reinterpret_cast<const int64_t*>(h->tables + o_packed_off);
-  h->d_level_vol = reinterpret_cast<const double*>(h->tables + o_lvol);
-
-  CK(cudaMalloc(&h->U, pl.arena_elems * es));
-  CK(cudaMalloc(&h->U1, pl.arena_elems * es));
-  CK(cudaMemsetAsync(h->U, 0, pl.arena_elems * es, h->stream));
-  CK(cudaMemsetAsync(h->U1, 0, pl.arena_elems * es, h->stream));
-  if (nlev > 1) {
-    CK(cudaMalloc(&h->Uold, pl.arena_elems * es));
-    CK(cudaMemsetAsync(h->Uold, 0, pl.arena_elems * es, h->stream));
-    CK(cudaMalloc(&h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
-  }
-  CK(cudaMalloc(&p, pl.packed_elems * sizeof(double)));
-  h->packed = static_cast<double*>(p);
-  CK(cudaMalloc(&p, (size_t)h->nchunk * nv * sizeof(double)));
-  h->partial = static_cast<double*>(p);
-  CK(cudaMalloc(&p, 16 * sizeof(double)));
-  h->totals = static_cast<double*>(p);
-  if (nregd) {
-    CK(cudaMalloc(&p, nregd * sizeof(double)));
-    h->regs = static_cast<double*>(p);
-    CK(cudaMemsetAsync(h->regs, 0, nregd * sizeof(double), h->stream));
-  }
-
-  h->dl.assign(nlev, DevLevel());
-  for (int l = 0; l < nlev; ++l) {
-    LevelPlan& L = pl.levels[l];
-    DevLevel& D = h->dl[l];
-    D.nitems = (int)L.items.size();
-    D.nghost = (int)L.ghost.size();
-    D.nprolong = (int)L.prolong.size();
-    D.ngather = (int)L.gather.size();
-    D.nrestrict = (int)L.restrict_segs.size();
-    D.nreg = (int)L.regs.size();
-    D.nuniq = L.reflux_first.empty() ? 0 : (int)L.reflux_first.size() - 1;
-    D.items = reinterpret_cast<const StageItem*>(h->tables + lo[l].items);
-    D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
-    D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
-    D.gather = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather);
-    D.restrict_segs = reinterpret_cast<const RestrictSeg*>(h->tables + lo[l].restr);
-    D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
-    D.reflux_first = reinterpret_cast<const int*>(h->tables + lo[l].rf);
-    D.R = h->regs ? h->regs + reg_off[l] : nullptr;
-    const PatchDesc& a = pl.desc[L.first];
-    const PatchDesc& b = pl.desc[L.first + L.count - 1];
-    D.arena_begin = a.off;
-    D.arena_end = b.off + b.vstride * nv;
-  }
-
   // initial state: pack on the host, one copy, convert on the device
   std::vector<double> host(pl.packed_elems);
   for (int i = 0; i < npatch; ++i) {
@@ -578,6 +623,119 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   CK(cudaStreamSynchronize(h->stream));
   h->ready = true;
   return read_bad(h);
+}
+
+amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_out) {
+  if (!h) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  RegridParams rp;
+  if (prm) {
+    rp.threshold = prm->threshold;
+    rp.buffer = prm->buffer;
+    rp.block = prm->block;
+    rp.max_patch = prm->max_patch;
+    rp.min_level = prm->min_level;
+  }
+  if (!(rp.threshold > 0.0)) return fail(h, AMR_ERR_ARG, "regrid threshold must be > 0");
+  const int nlev = (int)h->dl.size();
+  const size_t es = h->ops->elem_size();
+  Plan& op = h->plan;
+  const int nv = op.nvar;
+  // 1. face ghosts of every level from the current state (parent data taken at the current time)
+  if (nlev > 1)
+    CK(cudaMemcpyAsync(h->Uold, h->U, op.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
+  h->counting = 0;
+  for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+  // 2. density-gradient flags, one byte per interior cell
+  const size_t ncell = (size_t)(op.packed_elems / nv);
+  unsigned char* d_flags = nullptr;
+  CK(cudaMalloc(&d_flags, std::max<size_t>(ncell, 1)));
+  cudaError_t fe = h->ops->flag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, rp.threshold,
+                                d_flags);
+  std::vector<unsigned char> hflags(ncell);
+  if (fe == cudaSuccess)
+    fe = cudaMemcpyAsync(hflags.data(), d_flags, ncell, cudaMemcpyDeviceToHost, h->stream);
+  if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
+  cudaFree(d_flags);
+  CK(fe);
+  h->launches += h->counting + 1;
+  std::vector<std::vector<uint8_t>> flags(op.patches.size());
+  for (size_t i = 0; i < op.patches.size(); ++i) {
+    const HPatch& p = op.patches[i];
+    if (p.level >= h->cfg.max_level) continue;
+    const size_t n = (size_t)p.n[0] * p.n[1] * p.n[2];
+    const size_t o = (size_t)(op.packed_off[i] / nv);
+    flags[i].assign(hflags.begin() + o, hflags.begin() + o + n);
+  }
+  // 3. cluster on the host, build the new hierarchy
+  std::vector<HPatch> newp;
+  std::string msg;
+  amr_status st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
+  if (st != AMR_OK) return fail(h, st, msg);
+  Plan np;
+  st = build_plan(h->cfg, newp, np, msg, tile_params());
+  if (st != AMR_OK) return fail(h, st, "regrid produced an invalid hierarchy: " + msg);
+  RegridFill fill;
+  build_regrid_fill(op.patches, newp, rp.min_level, fill);
+  // 4. new device state, filled from the old one
+  const PatchDesc* old_desc = h->d_desc;
+  const std::vector<HPatch> oldp = op.patches;
+  int64_t keep_end = 0;    // arena range of the kept levels (same patches, same layout)
+  for (size_t i = 0; i < oldp.size(); ++i)
+    if (oldp[i].level <= rp.min_level) keep_end = op.desc[i].off + op.desc[i].vstride * nv;
+  DeviceBufs old = detach(h);
+  st = install_plan(h, std::move(np));
+  if (st != AMR_OK) {
+    free_bufs(old);
+    return st;
+  }
+  std::vector<unsigned char> buf;
+  std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
+  for (size_t l = 0; l < fill.copy.size(); ++l) {
+    o_copy[l] = put(buf, fill.copy[l]);
+    o_fresh[l] = put(buf, fill.fresh[l]);
+  }
+  unsigned char* d_fill = nullptr;
+  cudaError_t e = cudaMalloc(&d_fill, std::max<size_t>(buf.size(), 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_fill, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && keep_end > 0)
+    e = cudaMemcpyAsync(h->U, old.U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
+  const int nl_new = (int)h->dl.size();
+  if (e == cudaSuccess && nl_new > 1)
+    e = cudaMemcpyAsync(h->Uold, h->U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
+  for (int l = rp.min_level + 1; l < nl_new && e == cudaSuccess; ++l) {
+    const DevLevel& L = h->dl[l];
+    // interior cells no old patch covers: conservative prolongation from the (new) parent level
+    e = h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->U, 1.0);
+    if (e == cudaSuccess && l < (int)fill.fresh.size())
+      e = h->ops->prolong(h->stream, reinterpret_cast<const ProlongBox*>(d_fill + o_fresh[l]),
+                          (int)fill.fresh[l].size(), h->d_desc, h->tile, h->U);
+    if (e == cudaSuccess && l < (int)fill.copy.size())
+      e = h->ops->xcopy(h->stream, reinterpret_cast<const CopySeg*>(d_fill + o_copy[l]), (int)fill.copy[l].size(),
+                        h->d_desc, old_desc, h->U, old.U);
+    h->launches += 3;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_fill);
+  free_bufs(old);
+  CK(e);
+  h->ready = true;
+  if (npatch_out) *npatch_out = (int)h->plan.patches.size();
+  return AMR_OK;
+}
+
+int amr_get_patches(const amr_handle* h, amr_patch* out, int capacity) {
+  if (!h || !h->ready) return -1;
+  const int n = (int)h->plan.patches.size();
+  if (out)
+    for (int i = 0; i < n && i < capacity; ++i) {
+      out[i].level = h->plan.patches[i].level;
+      for (int d = 0; d < 3; ++d) {
+        out[i].lo[d] = h->plan.patches[i].lo[d];
+        out[i].n[d] = h->plan.patches[i].n[d];
+      }
+    }
+  return n;
 }
 
 long long amr_state_size(const amr_handle* h) { return (h && h->ready) ? h->plan.packed_elems : 0; }

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <map>
+#include <set>
 #include <tuple>
+#include <memory>
+#include <unordered_map>
 
 namespace amr {
 
@@ -81,6 +84,49 @@ std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) 
   }
   return done;
 }
+
+// Bucket index of the patches of one level: a query returns the patches whose
+// box may intersect a box (each patch listed once), so neighbour searches cost
+// O(neighbours) instead of O(patches).
+class PatchIndex {
+ public:
+  PatchIndex(const std::vector<HPatch>& P, int first, int count, int bs = 32) : P_(P), bs_(bs) {
+    for (int i = first; i < first + count; ++i) {
+      const HPatch& p = P[i];
+      for (int z = fl(p.lo[2]); z <= fl(p.lo[2] + p.n[2] - 1); ++z)
+        for (int y = fl(p.lo[1]); y <= fl(p.lo[1] + p.n[1] - 1); ++y)
+          for (int x = fl(p.lo[0]); x <= fl(p.lo[0] + p.n[0] - 1); ++x) map_[key(x, y, z)].push_back(i);
+    }
+  }
+  // patches intersecting [lo, hi) (no periodic images), ascending patch order
+  void query(const int lo[3], const int hi[3], std::vector<int>& out) const {
+    out.clear();
+    if (lo[0] >= hi[0] || lo[1] >= hi[1] || lo[2] >= hi[2]) return;
+    for (int z = fl(lo[2]); z <= fl(hi[2] - 1); ++z)
+      for (int y = fl(lo[1]); y <= fl(hi[1] - 1); ++y)
+        for (int x = fl(lo[0]); x <= fl(hi[0] - 1); ++x) {
+          auto it = map_.find(key(x, y, z));
+          if (it == map_.end()) continue;
+          for (int i : it->second) {
+            const HPatch& p = P_[i];
+            bool hit = true;
+            for (int d = 0; d < 3 && hit; ++d) hit = p.lo[d] < hi[d] && lo[d] < p.lo[d] + p.n[d];
+            if (hit) out.push_back(i);
+          }
+        }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+  }
+
+ private:
+  int fl(int c) const { return (int)std::floor((double)c / bs_); }
+  static int64_t key(int x, int y, int z) {
+    return ((int64_t)(x + (1 << 20)) << 42) | ((int64_t)(y + (1 << 20)) << 21) | (int64_t)(z + (1 << 20));
+  }
+  const std::vector<HPatch>& P_;
+  int bs_;
+  std::unordered_map<int64_t, std::vector<int>> map_;
+};
 
 // Split boxes with more than `maxc` cells along their longest axis so that
 // one CTA per box keeps the GPU busy for large patches.
@@ -208,17 +254,19 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
     first[l + 1] += first[l];
   }
   // no same-level overlap
+  std::vector<int> cand;
   for (int l = 0; l <= maxl; ++l) {
-    std::vector<int> idx;
-    for (int i = first[l]; i < first[l + 1]; ++i) idx.push_back(i);
-    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return P[a].lo[0] < P[b].lo[0]; });
-    for (size_t a = 0; a < idx.size(); ++a)
-      for (size_t b = a + 1; b < idx.size(); ++b) {
-        if (P[idx[b]].lo[0] >= P[idx[a]].lo[0] + P[idx[a]].n[0]) break;
-        if (boxes_overlap(P[idx[a]], P[idx[b]])) {
-          msg = fmt("patches %d and %d overlap on level %d", idx[a], idx[b], l); return AMR_ERR_NESTING;
+    PatchIndex ix(P, first[l], first[l + 1] - first[l]);
+    for (int a = first[l]; a < first[l + 1]; ++a) {
+      int lo[3], hi[3];
+      for (int d = 0; d < 3; ++d) { lo[d] = P[a].lo[d]; hi[d] = P[a].lo[d] + P[a].n[d]; }
+      ix.query(lo, hi, cand);
+      for (int b : cand)
+        if (b != a && boxes_overlap(P[a], P[b])) {
+          msg = fmt("patches %d and %d overlap on level %d", std::min(a, b), std::max(a, b), l);
+          return AMR_ERR_NESTING;
         }
-      }
+    }
   }
   // level 0 tiles the domain
   int64_t vol0 = 0;
@@ -227,7 +275,8 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
     msg = "level-0 patches must tile the whole domain"; return AMR_ERR_NESTING;
   }
   // proper nesting: footprint grown by two parent cells is covered by the parent level
-  for (int l = 1; l <= maxl; ++l)
+  for (int l = 1; l <= maxl; ++l) {
+    PatchIndex cix(P, first[l - 1], first[l] - first[l - 1]);
     for (int i = first[l]; i < first[l + 1]; ++i) {
       const HPatch& p = P[i];
       std::vector<std::pair<int, int>> iv[3];
@@ -239,7 +288,14 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
         need *= len;
       }
       int64_t got = 0;
-      for (int q = first[l - 1]; q < first[l]; ++q) {
+      // candidate parents: patches meeting the bounding box of the wrapped pieces
+      int blo[3], bhi[3];
+      for (int d = 0; d < 3; ++d) {
+        blo[d] = INT32_MAX; bhi[d] = INT32_MIN;
+        for (auto& r : iv[d]) { blo[d] = std::min(blo[d], r.first); bhi[d] = std::max(bhi[d], r.second); }
+      }
+      cix.query(blo, bhi, cand);
+      for (int q : cand) {
         const HPatch& o = P[q];
         int64_t v = 1;
         for (int d = 0; d < 3 && v; ++d) {
@@ -258,6 +314,7 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
         return AMR_ERR_NESTING;
       }
     }
+  }
   return AMR_OK;
 }
 
@@ -359,8 +416,10 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   build_items(plan, tp);
 
   // ---- ghost fill: sibling copies (incl. periodic images), outflow, prolongation boxes ----
+  std::vector<int> cand;
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
+    PatchIndex six(P, L.first, L.count);
     L.ghost_first.push_back(0);
     L.prolong_first.push_back(0);
     for (int i = L.first; i < L.first + L.count; ++i) {
@@ -387,7 +446,14 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             }
             int A = p.n[t1], B = p.n[t2];
             std::vector<unsigned char> mask((size_t)A * B, 0);
-            for (int q = L.first; q < L.first + L.count; ++q) {
+            {
+              int qlo[3], qhi[3];
+              qlo[d] = G; qhi[d] = G + 1;
+              qlo[t1] = p.lo[t1]; qhi[t1] = p.lo[t1] + p.n[t1];
+              qlo[t2] = p.lo[t2]; qhi[t2] = p.lo[t2] + p.n[t2];
+              six.query(qlo, qhi, cand);
+            }
+            for (int q : cand) {
               const HPatch& o = P[q];
               if (G < o.lo[d] || G >= o.lo[d] + o.n[d]) continue;
               int a0 = std::max(p.lo[t1], o.lo[t1]), a1 = std::min(p.lo[t1] + p.n[t1], o.lo[t1] + o.n[t1]);
@@ -462,6 +528,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   for (int l = 1; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
+    PatchIndex cix(P, C.first, C.count);
     L.gather_first.push_back(0);
     for (int i = L.first; i < L.first + L.count; ++i) {
       const HPatch& p = P[i];
@@ -494,7 +561,15 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
         for (auto& p1 : pieces[1])
           for (auto& p2 : pieces[2]) {
             const Piece* pp[3] = {&p0, &p1, &p2};
-            for (int q = C.first; q < C.first + C.count; ++q) {
+            {
+              int qlo[3], qhi[3];
+              for (int d = 0; d < 3; ++d) {
+                qlo[d] = pp[d]->src;
+                qhi[d] = pp[d]->mode == 1 ? pp[d]->src + 1 : pp[d]->src + pp[d]->len;
+              }
+              cix.query(qlo, qhi, cand);
+            }
+            for (int q : cand) {
               const HPatch& o = P[q];
               CopySeg s{};
               s.dst_patch = i; s.src_patch = q;
@@ -537,9 +612,15 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   for (int l = 1; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
+    PatchIndex cix(P, C.first, C.count);
     for (int i = L.first; i < L.first + L.count; ++i) {
       const HPatch& f = P[i];
-      for (int q = C.first; q < C.first + C.count; ++q) {
+      {
+        int qlo[3], qhi[3];
+        for (int d = 0; d < 3; ++d) { qlo[d] = f.lo[d] / 2; qhi[d] = (f.lo[d] + f.n[d]) / 2; }
+        cix.query(qlo, qhi, cand);
+      }
+      for (int q : cand) {
         const HPatch& o = P[q];
         int lo[3], hi[3];
         bool ok = true;
@@ -571,6 +652,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   for (int l = 1; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
+    PatchIndex fix(P, L.first, L.count), cix(P, C.first, C.count);
     std::vector<RegFace> regs;
     for (int d = 0; d < 3; ++d)
       for (int side = 0; side < 2; ++side)
@@ -587,7 +669,14 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
           int a0 = p.lo[t1] / 2, A = p.n[t1] / 2, b0 = p.lo[t2] / 2, B = p.n[t2] / 2;
           // covered by a level-l patch?
           std::vector<unsigned char> cov2((size_t)A * B, 0);
-          for (int q = L.first; q < L.first + L.count; ++q) {
+          {
+            int qlo[3], qhi[3];
+            qlo[d] = 2 * Cd; qhi[d] = 2 * Cd + 1;
+            qlo[t1] = 2 * a0; qhi[t1] = 2 * (a0 + A);
+            qlo[t2] = 2 * b0; qhi[t2] = 2 * (b0 + B);
+            fix.query(qlo, qhi, cand);
+          }
+          for (int q : cand) {
             const HPatch& o = P[q];
             if (2 * Cd < o.lo[d] || 2 * Cd >= o.lo[d] + o.n[d]) continue;
             int x0 = std::max(a0, o.lo[t1] / 2), x1 = std::min(a0 + A, (o.lo[t1] + o.n[t1]) / 2);
@@ -596,7 +685,14 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
               for (int x = x0; x < x1; ++x) cov2[(size_t)(y - b0) * A + (x - a0)] = 1;
           }
           std::vector<int> owner((size_t)A * B, -1);
-          for (int q = C.first; q < C.first + C.count; ++q) {
+          {
+            int qlo[3], qhi[3];
+            qlo[d] = Cd; qhi[d] = Cd + 1;
+            qlo[t1] = a0; qhi[t1] = a0 + A;
+            qlo[t2] = b0; qhi[t2] = b0 + B;
+            cix.query(qlo, qhi, cand);
+          }
+          for (int q : cand) {
             const HPatch& o = P[q];
             if (Cd < o.lo[d] || Cd >= o.lo[d] + o.n[d]) continue;
             int x0 = std::max(a0, o.lo[t1]), x1 = std::min(a0 + A, o.lo[t1] + o.n[t1]);
@@ -637,6 +733,252 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     L.reflux_first.push_back((int)regs.size());
   }
   return AMR_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Regridding (Sec. 3: hierarchy creation stays on the host)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Key {
+  int x, y, z;
+  bool operator<(const Key& o) const { return std::tie(z, y, x) < std::tie(o.z, o.y, o.x); }
+};
+
+}  // namespace
+
+amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
+                           const std::vector<std::vector<uint8_t>>& flags, const RegridParams& rp,
+                           std::vector<HPatch>& out, std::string& msg) {
+  const int B = rp.block, L = cfg.max_level, l0 = rp.min_level;
+  if (B < 2 || (B & 1) || rp.buffer < 0 || rp.buffer > B || rp.max_patch < 2 * B || rp.max_patch % (2 * B) ||
+      l0 < 0 || l0 > L) {
+    msg = "bad regrid parameters (block even >= 2, 0 <= buffer <= block, max_patch a multiple of 2 block)";
+    return AMR_ERR_ARG;
+  }
+  auto nb = [&](int l, int d) { return (level_n(cfg, l, d) + B - 1) / B; };
+  auto per = [&](int d) { return periodic(cfg, d); };
+  std::vector<std::set<Key>> tags(L + 1);
+  // 1. flagged cells, grown by the buffer, mark blocks of their level (first on a
+  //    per-patch block grid, so each block is inserted once per patch)
+  for (size_t i = 0; i < old.size(); ++i) {
+    const HPatch& p = old[i];
+    if (p.level < l0 || p.level >= L || flags[i].empty()) continue;
+    const int l = p.level;
+    int g0[3], gn[3];
+    for (int d = 0; d < 3; ++d) {
+      g0[d] = (int)std::floor((double)(p.lo[d] - rp.buffer) / B);
+      gn[d] = (int)std::floor((double)(p.lo[d] + p.n[d] - 1 + rp.buffer) / B) - g0[d] + 1;
+    }
+    std::vector<unsigned char> mark((size_t)gn[0] * gn[1] * gn[2], 0);
+    for (int k = 0; k < p.n[2]; ++k)
+      for (int j = 0; j < p.n[1]; ++j)
+        for (int ii = 0; ii < p.n[0]; ++ii) {
+          if (!flags[i][((size_t)k * p.n[1] + j) * p.n[0] + ii]) continue;
+          const int c[3] = {p.lo[0] + ii, p.lo[1] + j, p.lo[2] + k};
+          int b0[3], b1[3];
+          bool ok = true;
+          for (int d = 0; d < 3; ++d) {
+            // blocks touched by [c - buffer, c + buffer]
+            int lo = c[d] - rp.buffer, hi = c[d] + rp.buffer;
+            int N = level_n(cfg, l, d);
+            if (!per(d)) { lo = std::max(lo, 0); hi = std::min(hi, N - 1); }
+            b0[d] = (int)std::floor((double)lo / B) - g0[d];
+            b1[d] = (int)std::floor((double)hi / B) - g0[d];
+            if (b1[d] < b0[d]) ok = false;
+          }
+          if (!ok) continue;
+          for (int z = b0[2]; z <= b1[2]; ++z)
+            for (int y = b0[1]; y <= b1[1]; ++y)
+              for (int x = b0[0]; x <= b1[0]; ++x) mark[((size_t)z * gn[1] + y) * gn[0] + x] = 1;
+        }
+    for (int z = 0; z < gn[2]; ++z)
+      for (int y = 0; y < gn[1]; ++y)
+        for (int x = 0; x < gn[0]; ++x) {
+          if (!mark[((size_t)z * gn[1] + y) * gn[0] + x]) continue;
+          int q[3] = {x + g0[0], y + g0[1], z + g0[2]};
+          for (int d = 0; d < 3; ++d) {
+            int n = nb(l, d);
+            if (per(d)) q[d] = ((q[d] % n) + n) % n;
+          }
+          tags[l].insert({q[0], q[1], q[2]});
+        }
+  }
+  // 2. a tag on level l needs its parent region (and a ring for nesting) refined on level l-1
+  for (int l = L - 1; l > l0; --l)
+    for (const Key& b : tags[l]) {
+      int pb[3] = {b.x >> 1, b.y >> 1, b.z >> 1};
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int q[3] = {pb[0] + dx, pb[1] + dy, pb[2] + dz};
+            bool ok = true;
+            for (int d = 0; d < 3 && ok; ++d) {
+              int n = nb(l - 1, d);
+              if (q[d] < 0 || q[d] >= n) {
+                if (per(d)) q[d] = ((q[d] % n) + n) % n;
+                else ok = false;
+              }
+            }
+            if (ok) tags[l - 1].insert({q[0], q[1], q[2]});
+          }
+    }
+  // 3. top-down: keep levels <= l0, then cluster refinable blocks of each level
+  out.clear();
+  for (const HPatch& p : old)
+    if (p.level <= l0) out.push_back(p);
+  // blocks of level l0 fully covered by its patches
+  std::set<Key> cover;
+  for (const HPatch& p : old) {
+    if (p.level != l0) continue;
+    int a0[3], a1[3];
+    for (int d = 0; d < 3; ++d) {
+      a0[d] = (p.lo[d] + B - 1) / B;
+      a1[d] = (p.lo[d] + p.n[d]) / B;
+      // a partial block at the domain's end counts when the patch reaches the end
+      if (p.lo[d] + p.n[d] == level_n(cfg, l0, d) && level_n(cfg, l0, d) % B) a1[d] += 1;
+    }
+    for (int z = a0[2]; z < a1[2]; ++z)
+      for (int y = a0[1]; y < a1[1]; ++y)
+        for (int x = a0[0]; x < a1[0]; ++x) cover.insert({x, y, z});
+  }
+  const int maxb = rp.max_patch / (2 * B);
+  for (int l = l0; l < L; ++l) {
+    std::set<Key> refine;
+    for (const Key& b : tags[l]) {
+      bool ok = true;
+      for (int dz = -1; dz <= 1 && ok; ++dz)
+        for (int dy = -1; dy <= 1 && ok; ++dy)
+          for (int dx = -1; dx <= 1 && ok; ++dx) {
+            int q[3] = {b.x + dx, b.y + dy, b.z + dz};
+            bool outside = false;
+            for (int d = 0; d < 3; ++d) {
+              int n = nb(l, d);
+              if (q[d] < 0 || q[d] >= n) {
+                if (per(d)) q[d] = ((q[d] % n) + n) % n;
+                else outside = true;
+              }
+            }
+            if (!outside && !cover.count({q[0], q[1], q[2]})) ok = false;
+          }
+      if (ok) refine.insert(b);
+    }
+    if (refine.empty()) break;
+    // greedy box merge in (z, y, x) order: extend along x, then y, then z
+    std::set<Key> done;
+    std::set<Key> next_cover;
+    for (const Key& b : refine) {
+      if (done.count(b)) continue;
+      auto free_ = [&](int x, int y, int z) {
+        return refine.count({x, y, z}) && !done.count({x, y, z});
+      };
+      int nx = 1, ny = 1, nz = 1;
+      while (nx < maxb && free_(b.x + nx, b.y, b.z)) ++nx;
+      auto row_ok = [&](int y, int z) {
+        for (int i = 0; i < nx; ++i)
+          if (!free_(b.x + i, y, z)) return false;
+        return true;
+      };
+      while (ny < maxb && row_ok(b.y + ny, b.z)) ++ny;
+      auto slab_ok = [&](int z) {
+        for (int j = 0; j < ny; ++j)
+          if (!row_ok(b.y + j, z)) return false;
+        return true;
+      };
+      while (nz < maxb && slab_ok(b.z + nz)) ++nz;
+      for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+          for (int x = 0; x < nx; ++x) done.insert({b.x + x, b.y + y, b.z + z});
+      HPatch f{};
+      f.level = l + 1;
+      const int bl[3] = {b.x, b.y, b.z}, bn[3] = {nx, ny, nz};
+      for (int d = 0; d < 3; ++d) {
+        const int Nf = level_n(cfg, l + 1, d);
+        f.lo[d] = 2 * B * bl[d];
+        f.n[d] = std::min(2 * B * bn[d], Nf - f.lo[d]);
+      }
+      out.push_back(f);
+      // blocks of level l+1 covered by the new patch
+      for (int z = f.lo[2] / B; z < (f.lo[2] + f.n[2] + B - 1) / B; ++z)
+        for (int y = f.lo[1] / B; y < (f.lo[1] + f.n[1] + B - 1) / B; ++y)
+          for (int x = f.lo[0] / B; x < (f.lo[0] + f.n[0] + B - 1) / B; ++x) next_cover.insert({x, y, z});
+    }
+    cover.swap(next_cover);
+  }
+  return AMR_OK;
+}
+
+void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch>& newp, int keep_level,
+                       RegridFill& fill) {
+  int L = 0;
+  for (const HPatch& p : newp) L = std::max(L, p.level);
+  fill.copy.assign(L + 1, {});
+  fill.fresh.assign(L + 1, {});
+  std::vector<int> ofirst, ocount;
+  for (size_t q = 0; q < oldp.size(); ++q) {
+    const int l = oldp[q].level;
+    if ((int)ofirst.size() <= l) { ofirst.resize(l + 1, (int)q); ocount.resize(l + 1, 0); }
+    ocount[l]++;
+  }
+  std::vector<std::unique_ptr<PatchIndex>> oix(ofirst.size());
+  for (size_t l = 0; l < ofirst.size(); ++l) oix[l].reset(new PatchIndex(oldp, ofirst[l], ocount[l]));
+  std::vector<int> cand;
+  for (size_t i = 0; i < newp.size(); ++i) {
+    const HPatch& p = newp[i];
+    if (p.level <= keep_level) continue;
+    const int l = p.level;
+    std::vector<unsigned char> mask((size_t)p.n[0] * p.n[1] * p.n[2], 0);
+    const size_t c0 = fill.copy[l].size();
+    cand.clear();
+    if (l < (int)oix.size()) {
+      int qlo[3], qhi[3];
+      for (int d = 0; d < 3; ++d) { qlo[d] = p.lo[d]; qhi[d] = p.lo[d] + p.n[d]; }
+      oix[l]->query(qlo, qhi, cand);
+    }
+    for (int q : cand) {
+      const HPatch& o = oldp[q];
+      if (o.level != l) continue;
+      int lo[3], hi[3];
+      bool ok = true;
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::max(p.lo[d], o.lo[d]);
+        hi[d] = std::min(p.lo[d] + p.n[d], o.lo[d] + o.n[d]);
+        if (lo[d] >= hi[d]) ok = false;
+      }
+      if (!ok) continue;
+      CopySeg sg{};
+      sg.dst_patch = (int)i;
+      sg.src_patch = (int)q;
+      for (int d = 0; d < 3; ++d) {
+        sg.dlo[d] = (int16_t)(lo[d] - p.lo[d]);
+        sg.dn[d] = (int16_t)(hi[d] - lo[d]);
+        sg.sh[d] = (int16_t)(p.lo[d] - o.lo[d]);
+        sg.mode[d] = 0;
+      }
+      fill.copy[l].push_back(sg);
+      for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+          for (int x = lo[0]; x < hi[0]; ++x)
+            mask[((size_t)(z - p.lo[2]) * p.n[1] + (y - p.lo[1])) * p.n[0] + (x - p.lo[0])] = 1;
+    }
+    split_copy(fill.copy[l], c0);
+    const size_t f0 = fill.fresh[l].size();
+    for (int z = 0; z < p.n[2]; ++z) {
+      std::vector<unsigned char> slab(mask.begin() + (size_t)z * p.n[0] * p.n[1],
+                                      mask.begin() + (size_t)(z + 1) * p.n[0] * p.n[1]);
+      for (const Rect& r : mask_rects(slab, p.n[0], p.n[1])) {
+        ProlongBox b{};
+        b.patch = (int)i;
+        b.lo[0] = (int16_t)r.a0; b.n[0] = (int16_t)r.na;
+        b.lo[1] = (int16_t)r.b0; b.n[1] = (int16_t)r.nb;
+        b.lo[2] = (int16_t)z; b.n[2] = 1;
+        fill.fresh[l].push_back(b);
+      }
+    }
+    split_prolong(fill.fresh[l], f0);
+  }
 }
 
 }  // namespace amr

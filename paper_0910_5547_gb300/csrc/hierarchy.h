@@ -3,6 +3,7 @@
 // prolongation boxes, parent-tile gathers, restriction, flux registers,
 // coverage).  Pure C++, no CUDA calls: usable on a host without a GPU.
 #pragma once
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -59,6 +60,33 @@ struct TileParams {
   int max_cols = 0;
   int zchunk = 0;
 };
+
+// Regridding: cluster cells flagged on levels min_level .. max_level-1 into the
+// patches of levels min_level+1 .. max_level (levels <= min_level are kept).
+struct RegridParams {
+  double threshold = 0.3;  // flag where max_d |rho_{i+1} - rho_{i-1}| / (2 rho_i) > threshold
+  int buffer = 2;          // flagged cells are grown by `buffer` cells of their level
+  int block = 4;           // clustering block edge in cells of the flagged level (even)
+  int max_patch = 32;      // largest edge of a new patch in its own cells (multiple of 2*block)
+  int min_level = 0;
+};
+
+// flags[i]: one byte per interior cell of old patch i ([z][y][x]); empty for
+// patches whose level is not flagged.
+amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
+                           const std::vector<std::vector<uint8_t>>& flags, const RegridParams& rp,
+                           std::vector<HPatch>& out, std::string& msg);
+
+// Tables that fill a new hierarchy from an old one: per new level l > keep_level,
+// same-level box copies (dst = new patch, src = old patch, local coordinates)
+// and the interior boxes of new patches that no old patch covers (prolonged
+// from the new parent level).
+struct RegridFill {
+  std::vector<std::vector<CopySeg>> copy;       // per level
+  std::vector<std::vector<ProlongBox>> fresh;   // per level
+};
+void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch>& newp, int keep_level,
+                       RegridFill& fill);
 
 // Rebuild only the stage work items of `plan` with another tile shape.
 void build_items(Plan& plan, const TileParams& tp);

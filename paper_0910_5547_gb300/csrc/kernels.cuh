@@ -734,4 +734,56 @@ __global__ void pack_out_kernel(const ChunkDesc* chunks, int nchunk, const Patch
   }
 }
 
+// ---------------------------------------------------------------------------
+// regridding
+// ---------------------------------------------------------------------------
+
+// One byte per interior cell: 1 where max_d |rho(i + e_d) - rho(i - e_d)| / (2 rho(i)) > threshold
+// (face ghosts must be filled).
+template <typename T, int NV>
+__global__ void flag_kernel(const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const int64_t* packed_off,
+                            const T* U, T threshold, unsigned char* flags) {
+  for (int s = blockIdx.x; s < nchunk; s += gridDim.x) {
+    const ChunkDesc ch = chunks[s];
+    const PatchDesc P = desc[ch.patch];
+    const T* R = U + P.off;   // density is variable 0
+    const int nx = P.n[0], nxy = P.n[0] * P.n[1];
+    const int plane = P.pitch * P.m1;
+    unsigned char* fp = flags + packed_off[ch.patch] / NV;
+    for (int e = threadIdx.x; e < ch.count; e += blockDim.x) {
+      const int idx = ch.begin + e;
+      const int k = idx / nxy, r2 = idx - k * nxy, j = r2 / nx, i = r2 - j * nx;
+      const int c = ((k + kGhost) * P.m1 + (j + kGhost)) * P.pitch + (i + kGhost);
+      const T rho = R[c];
+      const T gx = dabs(R[c + 1] - R[c - 1]);
+      const T gy = dabs(R[c + P.pitch] - R[c - P.pitch]);
+      const T gz = dabs(R[c + plane] - R[c - plane]);
+      const T g = dmax(gx, dmax(gy, gz)) / (T(2) * rho);
+      fp[idx] = g > threshold ? 1 : 0;
+    }
+  }
+}
+
+// Box copies between two hierarchies (interior cells of new patches from old patches).
+template <typename T, int NV>
+__global__ void xcopy_kernel(const CopySeg* segs, int nseg, const PatchDesc* dst_desc, const PatchDesc* src_desc,
+                             T* dst_arena, const T* src_arena) {
+  for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const CopySeg g = segs[s];
+    const PatchDesc D = dst_desc[g.dst_patch];
+    const PatchDesc S = src_desc[g.src_patch];
+    const int n0 = g.dn[0], n1 = g.dn[1], n2 = g.dn[2];
+    const int total = n0 * n1 * n2;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int r = e / n0, a = e - r * n0;
+      const int c = r / n1, b = r - c * n1;
+      const int da = g.dlo[0] + a, db = g.dlo[1] + b, dc = g.dlo[2] + c;
+      const int si = ((dc + g.sh[2] + kGhost) * S.m1 + (db + g.sh[1] + kGhost)) * S.pitch + (da + g.sh[0] + kGhost);
+      const int di = ((dc + kGhost) * D.m1 + (db + kGhost)) * D.pitch + (da + kGhost);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst_arena[D.off + (int64_t)v * D.vstride + di] = src_arena[S.off + (int64_t)v * S.vstride + si];
+    }
+  }
+}
+
 }  // namespace amr

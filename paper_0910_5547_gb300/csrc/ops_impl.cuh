@@ -149,6 +149,21 @@ struct Ops final : OpsBase {
     return cudaGetLastError();
   }
 
+  cudaError_t flag(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                   const int64_t* packed_off, const void* U, double threshold, unsigned char* flags) override {
+    flag_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, packed_off, static_cast<const T*>(U),
+                                                        (T)threshold, flags);
+    return cudaGetLastError();
+  }
+
+  cudaError_t xcopy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* dst_desc,
+                    const PatchDesc* src_desc, void* dst, const void* src) override {
+    if (nseg <= 0) return cudaSuccess;
+    xcopy_kernel<T, NV><<<grid_for(nseg), 256, 0, s>>>(segs, nseg, dst_desc, src_desc, static_cast<T*>(dst),
+                                                       static_cast<const T*>(src));
+    return cudaGetLastError();
+  }
+
   cudaError_t pack_out(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
                        const int64_t* packed_off, const void* U, double* dst) override {
     pack_out_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, packed_off,

@@ -34,7 +34,8 @@ STATUS_NAMES = {0: "AMR_OK", -1: "AMR_ERR_ARG", -2: "AMR_ERR_NESTING", -3: "AMR_
 EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_patches", "amr_set_state",
            "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
-           "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc"]
+           "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
+           "amr_get_patches"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
 
@@ -68,6 +69,11 @@ class amr_config(ctypes.Structure):
 
 class amr_patch(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int), ("lo", ctypes.c_int * 3), ("n", ctypes.c_int * 3)]
+
+
+class amr_regrid_params(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("buffer", ctypes.c_int), ("block", ctypes.c_int),
+                ("max_patch", ctypes.c_int), ("min_level", ctypes.c_int)]
 
 
 _lib = None
@@ -115,6 +121,10 @@ def load():
     L.amr_step_patch_noalloc.argtypes = [ctypes.POINTER(amr_config), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_double, dp]
     L.amr_step_patch_noalloc.restype = ctypes.c_int
+    L.amr_regrid.argtypes = [H, ctypes.POINTER(amr_regrid_params), ctypes.POINTER(ctypes.c_int)]
+    L.amr_regrid.restype = ctypes.c_int
+    L.amr_get_patches.argtypes = [H, ctypes.POINTER(amr_patch), ctypes.c_int]
+    L.amr_get_patches.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in ("amr_create", "amr_validate_patches", "amr_set_patches", "amr_set_state", "amr_step",
@@ -264,6 +274,31 @@ def amr_step_patch_noalloc(cfg: amr_config, state_in_ptr: int, state_out_ptr: in
     if st != AMR_OK:
         raise AmrError(st, "amr_step_patch_noalloc failed")
     return float("nan")
+
+
+class PatchRecord:
+    def __init__(self, level, lo, n):
+        self.level, self.lo, self.n = level, tuple(lo), tuple(n)
+
+    def __repr__(self):
+        return f"Patch(level={self.level}, lo={self.lo}, n={self.n})"
+
+
+def amr_regrid(h, threshold=0.3, buffer=2, block=4, max_patch=32, min_level=0) -> int:
+    prm = amr_regrid_params(threshold, buffer, block, max_patch, min_level)
+    n = ctypes.c_int(0)
+    _check(h, load().amr_regrid(h, ctypes.byref(prm), ctypes.byref(n)))
+    return n.value
+
+
+def amr_get_patches(h) -> list:
+    L = load()
+    n = L.amr_get_patches(h, None, 0)
+    if n < 0:
+        raise AmrError(AMR_ERR_STATE, "no patches installed")
+    arr = (amr_patch * max(n, 1))()
+    L.amr_get_patches(h, arr, n)
+    return [PatchRecord(arr[i].level, arr[i].lo[:], arr[i].n[:]) for i in range(n)]
 
 
 def amr_destroy(h):

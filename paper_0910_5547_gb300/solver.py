@@ -95,3 +95,10 @@ class Solver:
 
     def launches(self) -> int:
         return N.amr_kernel_launches(self.h)
+
+    def regrid(self, **kw) -> int:
+        """Rebuild the refined levels from density-gradient flags (see amr_regrid)."""
+        n = N.amr_regrid(self.h, **kw)
+        self.patches = N.amr_get_patches(self.h)
+        self.offsets = np.cumsum([0] + [self.nvar * p.n[0] * p.n[1] * p.n[2] for p in self.patches])
+        return n

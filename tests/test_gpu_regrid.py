@@ -1,0 +1,72 @@
+"""GPU regridding against the oracle's independent regrid: identical patch lists
+(integer work, exact) and FP64 states within the parity tolerance, across
+regrid -> step -> regrid cycles; FP32 regrid conserves totals."""
+import numpy as np
+import pytest
+
+import amr_inputs as ai
+import oracle as orc
+from oracle import regrid as rg
+from parity import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+from paper_0910_5547_gb300 import Solver  # noqa: E402
+from paper_0910_5547_gb300 import build as B  # noqa: E402
+from paper_0910_5547_gb300 import native as N  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    yield
+
+
+def clumpy(seed, bc):
+    patches = ai.uniform_patches((32,) * 3, (16,) * 3)
+    return ai.random_smooth(patches, (32,) * 3, seed=seed, amp=0.6, bc=(bc,) * 6)
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+def test_regrid_cycles_match_the_oracle_fp64(bc):
+    pb = clumpy(3, bc)
+    o = orc.Oracle(pb, max_level=2, nthreads=8)
+    s = Solver.from_problem(pb, precision="fp64", max_level=2)
+    for cycle in range(3):
+        for _ in range(2):
+            o.step()
+            s.step()
+        o = rg.regrid(o, threshold=0.1, buffer=2, block=4, max_patch=32)
+        s.regrid(threshold=0.1, buffer=2, block=4, max_patch=32)
+        assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
+               [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"cycle {cycle}"
+        assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", f"regrid cycle {cycle}")
+    assert max(p.level for p in s.patches) == 2
+    o.step()
+    s.step()
+    s.check()
+    assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", "after regrid")
+
+
+def test_regrid_fp32_conserves_totals_and_nests():
+    pb = clumpy(5, ai.PERIODIC)
+    s = Solver.from_problem(pb, precision="fp32", max_level=3)
+    for _ in range(3):
+        s.step()
+        t0 = s.totals()
+        n = s.regrid(threshold=0.1)
+        t1 = s.totals()
+        assert n == len(s.patches)
+        assert np.all(np.abs(t1 - t0) <= 2e-6 * np.abs(t0).max()), (t0, t1)
+    c = N.amr_default_config(base_n=(32,) * 3, max_level=3, bc=(ai.PERIODIC,) * 6)
+    assert N.amr_validate_patches(c, s.patches)[0] == N.AMR_OK
+    s.step()
+    s.check()
+
+
+def test_regrid_rejects_bad_parameters():
+    pb = clumpy(5, ai.PERIODIC)
+    s = Solver.from_problem(pb, precision="fp32", max_level=1)
+    with pytest.raises(N.AmrError) as e:
+        s.regrid(block=3)
+    assert e.value.status == N.AMR_ERR_ARG
