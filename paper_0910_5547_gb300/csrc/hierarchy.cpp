@@ -11,6 +11,7 @@
 #include <tuple>
 #include <memory>
 #include <unordered_map>
+#include <unordered_set>
 
 namespace amr {
 
@@ -747,6 +748,18 @@ struct Key {
   bool operator<(const Key& o) const { return std::tie(z, y, x) < std::tie(o.z, o.y, o.x); }
 };
 
+// block coordinates packed into one integer (each in [-2^20, 2^20))
+int64_t pack(int x, int y, int z) {
+  return ((int64_t)(z + (1 << 20)) << 42) | ((int64_t)(y + (1 << 20)) << 21) | (int64_t)(x + (1 << 20));
+}
+Key unpack(int64_t k) {
+  Key r;
+  r.x = (int)(k & ((1 << 21) - 1)) - (1 << 20);
+  r.y = (int)((k >> 21) & ((1 << 21) - 1)) - (1 << 20);
+  r.z = (int)(k >> 42) - (1 << 20);
+  return r;
+}
+
 }  // namespace
 
 amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
@@ -760,7 +773,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   }
   auto nb = [&](int l, int d) { return (level_n(cfg, l, d) + B - 1) / B; };
   auto per = [&](int d) { return periodic(cfg, d); };
-  std::vector<std::set<Key>> tags(L + 1);
+  std::vector<std::unordered_set<int64_t>> tags(L + 1);
   // 1. flagged cells, grown by the buffer, mark blocks of their level (first on a
   //    per-patch block grid, so each block is inserted once per patch)
   for (size_t i = 0; i < old.size(); ++i) {
@@ -803,12 +816,13 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
             int n = nb(l, d);
             if (per(d)) q[d] = ((q[d] % n) + n) % n;
           }
-          tags[l].insert({q[0], q[1], q[2]});
+          tags[l].insert(pack(q[0], q[1], q[2]));
         }
   }
   // 2. a tag on level l needs its parent region (and a ring for nesting) refined on level l-1
   for (int l = L - 1; l > l0; --l)
-    for (const Key& b : tags[l]) {
+    for (int64_t kb : tags[l]) {
+      const Key b = unpack(kb);
       int pb[3] = {b.x >> 1, b.y >> 1, b.z >> 1};
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
@@ -822,7 +836,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
                 else ok = false;
               }
             }
-            if (ok) tags[l - 1].insert({q[0], q[1], q[2]});
+            if (ok) tags[l - 1].insert(pack(q[0], q[1], q[2]));
           }
     }
   // 3. top-down: keep levels <= l0, then cluster refinable blocks of each level
@@ -830,7 +844,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   for (const HPatch& p : old)
     if (p.level <= l0) out.push_back(p);
   // blocks of level l0 fully covered by its patches
-  std::set<Key> cover;
+  std::unordered_set<int64_t> cover;
   for (const HPatch& p : old) {
     if (p.level != l0) continue;
     int a0[3], a1[3];
@@ -842,12 +856,13 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
     }
     for (int z = a0[2]; z < a1[2]; ++z)
       for (int y = a0[1]; y < a1[1]; ++y)
-        for (int x = a0[0]; x < a1[0]; ++x) cover.insert({x, y, z});
+        for (int x = a0[0]; x < a1[0]; ++x) cover.insert(pack(x, y, z));
   }
   const int maxb = rp.max_patch / (2 * B);
   for (int l = l0; l < L; ++l) {
-    std::set<Key> refine;
-    for (const Key& b : tags[l]) {
+    std::unordered_set<int64_t> refine;
+    for (int64_t kb : tags[l]) {
+      const Key b = unpack(kb);
       bool ok = true;
       for (int dz = -1; dz <= 1 && ok; ++dz)
         for (int dy = -1; dy <= 1 && ok; ++dy)
@@ -861,18 +876,23 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
                 else outside = true;
               }
             }
-            if (!outside && !cover.count({q[0], q[1], q[2]})) ok = false;
+            if (!outside && !cover.count(pack(q[0], q[1], q[2]))) ok = false;
           }
-      if (ok) refine.insert(b);
+      if (ok) refine.insert(kb);
     }
     if (refine.empty()) break;
     // greedy box merge in (z, y, x) order: extend along x, then y, then z
-    std::set<Key> done;
-    std::set<Key> next_cover;
-    for (const Key& b : refine) {
-      if (done.count(b)) continue;
+    std::unordered_set<int64_t> done;
+    std::unordered_set<int64_t> next_cover;
+    std::vector<Key> order;
+    order.reserve(refine.size());
+    for (int64_t kb : refine) order.push_back(unpack(kb));
+    std::sort(order.begin(), order.end());   // (z, y, x) order
+    for (const Key& b : order) {
+      if (done.count(pack(b.x, b.y, b.z))) continue;
       auto free_ = [&](int x, int y, int z) {
-        return refine.count({x, y, z}) && !done.count({x, y, z});
+        const int64_t k = pack(x, y, z);
+        return refine.count(k) && !done.count(k);
       };
       int nx = 1, ny = 1, nz = 1;
       while (nx < maxb && free_(b.x + nx, b.y, b.z)) ++nx;
@@ -890,7 +910,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
       while (nz < maxb && slab_ok(b.z + nz)) ++nz;
       for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
-          for (int x = 0; x < nx; ++x) done.insert({b.x + x, b.y + y, b.z + z});
+          for (int x = 0; x < nx; ++x) done.insert(pack(b.x + x, b.y + y, b.z + z));
       HPatch f{};
       f.level = l + 1;
       const int bl[3] = {b.x, b.y, b.z}, bn[3] = {nx, ny, nz};
@@ -903,7 +923,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
       // blocks of level l+1 covered by the new patch
       for (int z = f.lo[2] / B; z < (f.lo[2] + f.n[2] + B - 1) / B; ++z)
         for (int y = f.lo[1] / B; y < (f.lo[1] + f.n[1] + B - 1) / B; ++y)
-          for (int x = f.lo[0] / B; x < (f.lo[0] + f.n[0] + B - 1) / B; ++x) next_cover.insert({x, y, z});
+          for (int x = f.lo[0] / B; x < (f.lo[0] + f.n[0] + B - 1) / B; ++x) next_cover.insert(pack(x, y, z));
     }
     cover.swap(next_cover);
   }
