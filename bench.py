@@ -255,6 +255,8 @@ def main():
 
     def rate(pb, precision, batched, graph, steps):
         so = make_solver(pb, precision, batched, graph, stream)
+        if batched:
+            so.autotune()
         for _ in range(2):
             so.step(0.0, sync=False)
         t = timed_steps(torch, so, stream, steps)
@@ -264,6 +266,7 @@ def main():
 
     # ---- headline: single-patch batched FP32, graph replay, CFL every step ----
     s = make_solver(single, "fp32", True, True, stream)
+    tune_report = s.autotune()
     for _ in range(args.warmup):
         s.step(0.0, sync=False)
     torch.cuda.synchronize()
@@ -314,6 +317,7 @@ def main():
         path and the plain per-patch FP64 path on a multi-level hierarchy, plus kernel-class times."""
         cu = pb.cell_updates_per_coarse_step()
         so = make_solver(pb, "fp32", True, True, stream)
+        so.autotune()
         for _ in range(2):
             so.step(0.0, sync=False)
         ka = max(3, args.steps // 20)
@@ -346,6 +350,7 @@ def main():
     if "adaptive" in phases:
         pb = ai.blast_clumps()
         so = make_solver(pb, "fp32", True, True, stream)
+        so.autotune()
         so.step(0.0)
         so.regrid(threshold=0.3, buffer=4, block=4, max_patch=32)
         tot_cu, t_steps, t_regrid, counts = 0, 0.0, 0.0, []
@@ -422,6 +427,7 @@ def main():
                              "capture (null if the kernel source changed since)",
                      "timed_steps": ksteps},
         "step_kernel_ms": step_kernel_ms,
+        "autotune": [l for l in tune_report.splitlines() if l],
         "cell_update_roofline_frac": value / ws * (2 + 3) * V * W / (peak * 1e9),
         "e2e": e2e,
         "gpu_launches": launches,

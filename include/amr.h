@@ -130,6 +130,15 @@ typedef struct {
  * invalidates the step graphs. */
 amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_out);
 
+/* Autotuner: time the stage kernel over the installed hierarchy for each
+ * candidate work-item shape (x width, columns per CTA, z chunk) and register
+ * budget (2 or 3 resident CTAs per SM for FP32 Euler) and keep the fastest for
+ * this handle (also for later amr_set_patches / amr_regrid).  The state is not
+ * modified (only the stage-1 scratch array is written).  report (may be NULL)
+ * receives one line per candidate with its time.  Synchronises; invalidates
+ * the step graphs. */
+amr_status amr_autotune(amr_handle* h, char* report, int report_len);
+
 /* Copy up to `capacity` patches of the installed hierarchy (sorted by level) to
  * out (may be NULL) and return the patch count (-1 before amr_set_patches). */
 int amr_get_patches(const amr_handle* h, amr_patch* out, int capacity);

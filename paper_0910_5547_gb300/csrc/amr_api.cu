@@ -101,6 +101,9 @@ struct amr_handle {
   bool rates_valid = false;   // stage 2 of the last step left next-step maxima (single level)
   long long launches = 0;
   long long counting = 0;   // launches counted while enqueueing
+  // stage-kernel work items (own buffer: the autotuner swaps the tiling)
+  StageItem* items_dev = nullptr;
+  TileParams tp;            // tile shape in use (autotuned or default)
   // optional per-class event timing (eager steps only)
   bool timing = false;
   int cur_class = 0;
@@ -156,9 +159,11 @@ void free_device(amr_handle* h) {
     h->graph[g] = nullptr;
   }
   h->rates_valid = false;
-  void* ptrs[] = {h->U, h->U1, h->Uold, h->tile, h->packed, h->partial, h->totals, h->regs, h->tables};
+  void* ptrs[] = {h->U, h->U1, h->Uold, h->tile, h->packed, h->partial, h->totals, h->regs, h->tables,
+                  h->items_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  h->items_dev = nullptr;
   h->U = h->U1 = h->Uold = h->tile = nullptr;
   h->packed = h->partial = h->totals = h->regs = nullptr;
   h->tables = nullptr;
@@ -341,10 +346,25 @@ size_t put(std::vector<unsigned char>& buf, const std::vector<X>& v) {
   return off;
 }
 
-TileParams tile_params() {
-  TileParams tp;
-  if (const char* e = std::getenv("AMR_TILE")) std::sscanf(e, "%d,%d,%d", &tp.max_wx, &tp.max_cols, &tp.zchunk);
-  return tp;
+// Upload the stage work items of every level into their own device buffer.
+amr_status upload_items(amr_handle* h) {
+  std::vector<StageItem> all;
+  std::vector<size_t> first;
+  for (const LevelPlan& L : h->plan.levels) {
+    first.push_back(all.size());
+    all.insert(all.end(), L.items.begin(), L.items.end());
+  }
+  if (h->items_dev) cudaFree(h->items_dev);
+  h->items_dev = nullptr;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, std::max<size_t>(all.size(), 1) * sizeof(StageItem)));
+  h->items_dev = static_cast<StageItem*>(p);
+  CK(cudaMemcpyAsync(h->items_dev, all.data(), all.size() * sizeof(StageItem), cudaMemcpyHostToDevice, h->stream));
+  for (size_t l = 0; l < h->dl.size(); ++l) {
+    h->dl[l].items = h->items_dev + first[l];
+    h->dl[l].nitems = (int)h->plan.levels[l].items.size();
+  }
+  return AMR_OK;
 }
 
 // Device buffers of one installed plan.
@@ -358,6 +378,7 @@ struct DeviceBufs {
   double* totals = nullptr;
   double* regs = nullptr;
   unsigned char* tables = nullptr;
+  StageItem* items = nullptr;
 };
 
 // Take the buffers out of the handle (graphs are dropped: they refer to them).
@@ -369,6 +390,8 @@ DeviceBufs detach(amr_handle* h) {
   DeviceBufs b;
   b.U = h->U; b.U1 = h->U1; b.Uold = h->Uold; b.tile = h->tile;
   b.packed = h->packed; b.partial = h->partial; b.totals = h->totals; b.regs = h->regs; b.tables = h->tables;
+  b.items = h->items_dev;
+  h->items_dev = nullptr;
   h->U = h->U1 = h->Uold = h->tile = nullptr;
   h->packed = h->partial = h->totals = h->regs = nullptr;
   h->tables = nullptr;
@@ -379,7 +402,7 @@ DeviceBufs detach(amr_handle* h) {
 }
 
 void free_bufs(DeviceBufs& b) {
-  void* ptrs[] = {b.U, b.U1, b.Uold, b.tile, b.packed, b.partial, b.totals, b.regs, b.tables};
+  void* ptrs[] = {b.U, b.U1, b.Uold, b.tile, b.packed, b.partial, b.totals, b.regs, b.tables, b.items};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   b = DeviceBufs();
@@ -419,7 +442,6 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   std::vector<Offs> lo(nlev);
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = pl.levels[l];
-    lo[l].items = put(buf, L.items);
     lo[l].ghost = put(buf, L.ghost);
     lo[l].prolong = put(buf, L.prolong);
     lo[l].gather = put(buf, L.gather);
@@ -461,14 +483,12 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = pl.levels[l];
     DevLevel& D = h->dl[l];
-    D.nitems = (int)L.items.size();
     D.nghost = (int)L.ghost.size();
     D.nprolong = (int)L.prolong.size();
     D.ngather = (int)L.gather.size();
     D.nrestrict = (int)L.restrict_segs.size();
     D.nreg = (int)L.regs.size();
     D.nuniq = L.reflux_first.empty() ? 0 : (int)L.reflux_first.size() - 1;
-    D.items = reinterpret_cast<const StageItem*>(h->tables + lo[l].items);
     D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
     D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
     D.gather = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather);
@@ -481,7 +501,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     D.arena_begin = a.off;
     D.arena_end = b.off + b.vstride * nv;
   }
-  return AMR_OK;
+  return upload_items(h);
 }
 
 }  // namespace
@@ -544,7 +564,6 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
     h->own_stream = true;
   }
   h->ops = make_ops(*cfg);
-  if (const char* e = std::getenv("AMR_OCC")) h->ops->set_stage_occupancy(std::atoi(e));
   void* p = nullptr;
   if (cudaMalloc(&p, sizeof(StepParams)) != cudaSuccess) {
     g_global_err = "cudaMalloc of step parameters failed";
@@ -600,7 +619,7 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   }
   Plan plan;
   std::string msg;
-  amr_status st = build_plan(h->cfg, P, plan, msg, tile_params());
+  amr_status st = build_plan(h->cfg, P, plan, msg, h->tp);
   if (st != AMR_OK) return fail(h, st, msg);
   CK(cudaStreamSynchronize(h->stream));
   DeviceBufs old = detach(h);
@@ -673,7 +692,7 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
   amr_status st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
   if (st != AMR_OK) return fail(h, st, msg);
   Plan np;
-  st = build_plan(h->cfg, newp, np, msg, tile_params());
+  st = build_plan(h->cfg, newp, np, msg, h->tp);
   if (st != AMR_OK) return fail(h, st, "regrid produced an invalid hierarchy: " + msg);
   RegridFill fill;
   build_regrid_fill(op.patches, newp, rp.min_level, fill);
@@ -722,6 +741,86 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
   h->ready = true;
   if (npatch_out) *npatch_out = (int)h->plan.patches.size();
   return AMR_OK;
+}
+
+amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
+  if (!h) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  struct Cand { TileParams tp; int occ; };
+  std::vector<Cand> cands;
+  const int occs[2] = {0, 3};
+  const int shapes[4][3] = {{32, 256, 32}, {32, 256, 16}, {16, 256, 16}, {32, 256, 64}};
+  for (int o = 0; o < 2; ++o) {
+    if (occs[o] == 3 && !(h->cfg.nvar == 5 && h->cfg.precision == AMR_FP32)) continue;
+    for (auto& sh : shapes) {
+      Cand c;
+      c.tp.max_wx = sh[0]; c.tp.max_cols = sh[1]; c.tp.zchunk = sh[2];
+      c.occ = occs[o];
+      cands.push_back(c);
+    }
+  }
+  // valid ghosts everywhere (stage 1 reads them; U1 is scratch, U is not modified)
+  const int nlev = (int)h->dl.size();
+  const size_t es = h->ops->elem_size();
+  if (nlev > 1) CK(cudaMemcpyAsync(h->Uold, h->U, h->plan.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
+  h->counting = 0;
+  for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const TileParams keep_tp = h->tp;
+  const int keep_occ = h->ops->stage_occupancy() == 3 ? 3 : 0;
+  double best = 1e300;
+  int best_i = -1;
+  std::string rep;
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
+    h->tp = cands[ci].tp;
+    h->ops->set_stage_occupancy(cands[ci].occ);
+    build_items(h->plan, h->tp);
+    amr_status st = upload_items(h);
+    if (st != AMR_OK) break;
+    double t_best = 1e300;
+    for (int rep_i = 0; rep_i < 4; ++rep_i) {
+      CK(cudaEventRecord(e0, h->stream));
+      for (int l = 0; l < nlev; ++l) CK(stage(h, l, 1, h->U, h->U1));
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep_i > 0) t_best = std::min(t_best, (double)ms);   // first run warms up
+    }
+    char line[160];
+    std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d: %.4f ms\n", h->tp.max_wx,
+                  h->tp.max_cols, h->tp.zchunk, cands[ci].occ == 3 ? 3 : h->ops->stage_occupancy(), t_best);
+    rep += line;
+    if (t_best < best) { best = t_best; best_i = (int)ci; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_i < 0) {
+    h->tp = keep_tp;
+    h->ops->set_stage_occupancy(keep_occ);
+  } else {
+    h->tp = cands[best_i].tp;
+    h->ops->set_stage_occupancy(cands[best_i].occ);
+    char line[96];
+    std::snprintf(line, sizeof line, "chosen: candidate %d\n", best_i);
+    rep += line;
+  }
+  build_items(h->plan, h->tp);
+  amr_status st = upload_items(h);
+  for (int g = 0; g < 4; ++g) {
+    if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+    h->graph[g] = nullptr;
+  }
+  CK(cudaMemsetAsync(&h->params->bad, 0, sizeof(unsigned int), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->launches += h->counting;
+  if (report && report_len > 0) {
+    std::strncpy(report, rep.c_str(), (size_t)report_len - 1);
+    report[report_len - 1] = 0;
+  }
+  return st;
 }
 
 int amr_get_patches(const amr_handle* h, amr_patch* out, int capacity) {

@@ -35,7 +35,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
-           "amr_get_patches"]
+           "amr_get_patches", "amr_autotune"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
 
@@ -124,6 +124,8 @@ def load():
     L.amr_regrid.argtypes = [H, ctypes.POINTER(amr_regrid_params), ctypes.POINTER(ctypes.c_int)]
     L.amr_regrid.restype = ctypes.c_int
     L.amr_get_patches.argtypes = [H, ctypes.POINTER(amr_patch), ctypes.c_int]
+    L.amr_autotune.argtypes = [H, ctypes.c_char_p, ctypes.c_int]
+    L.amr_autotune.restype = ctypes.c_int
     L.amr_get_patches.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -289,6 +291,13 @@ def amr_regrid(h, threshold=0.3, buffer=2, block=4, max_patch=32, min_level=0) -
     n = ctypes.c_int(0)
     _check(h, load().amr_regrid(h, ctypes.byref(prm), ctypes.byref(n)))
     return n.value
+
+
+def amr_autotune(h) -> str:
+    """Pick the fastest stage-kernel tiling for the installed hierarchy; returns the report."""
+    buf = ctypes.create_string_buffer(4096)
+    _check(h, load().amr_autotune(h, buf, 4096))
+    return buf.value.decode()
 
 
 def amr_get_patches(h) -> list:

@@ -96,6 +96,10 @@ class Solver:
     def launches(self) -> int:
         return N.amr_kernel_launches(self.h)
 
+    def autotune(self) -> str:
+        """Time the stage kernel's candidate tilings on this hierarchy and keep the fastest."""
+        return N.amr_autotune(self.h)
+
     def regrid(self, **kw) -> int:
         """Rebuild the refined levels from density-gradient flags (see amr_regrid)."""
         n = N.amr_regrid(self.h, **kw)

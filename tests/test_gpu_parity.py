@@ -218,3 +218,20 @@ def test_kernel_launch_counter_counts_graph_nodes():
     s.check()
     per = (s.launches() - n0) / 2
     assert per >= 5            # set_dt + 2 x (ghost copy + stage)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotune_keeps_results_and_reports_candidates(precision):
+    pb = ai.random_smooth(three_level_seeded(), (32,) * 3, seed=14, amp=0.2)
+    s = Solver.from_problem(pb, precision=precision)
+    u0 = s.state_all().copy()
+    rep = s.autotune()
+    assert np.array_equal(s.state_all(), u0)            # tuning does not touch the state
+    lines = [l for l in rep.splitlines() if l.startswith("tile")]
+    assert len(lines) >= 4 and "chosen" in rep
+    o = orc.Oracle(pb, nthreads=8)
+    for _ in range(2):
+        o.step()
+        s.step()
+    s.check()
+    assert_parity(s.all_cons(), o.all_cons(), pb.patches, precision, "autotuned")
