@@ -48,6 +48,20 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(elapsed: float, units_per_rank: float, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    `units_per_rank` units; the job time is the slowest rank's time (max over
+    ranks, all-reduced).  Returns (value, max_elapsed)."""
+    ws = 1
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return ws * units_per_rank / elapsed, elapsed
+
+
 def stage_traffic():
     """DRAM bytes per stage-kernel launch (mean of stage 1 and stage 2) from the committed ncu
     summary, used only while the kernel source is the one that was profiled."""
@@ -247,11 +261,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return aggregate(x, 1.0, dist if ws > 1 else None, device="cuda")[1]
 
     def rate(pb, precision, batched, graph, steps):
         so = make_solver(pb, precision, batched, graph, stream)
@@ -278,8 +288,7 @@ def main():
     barrier()
     launches = s.launches() - n0
     s.check()
-    elapsed = max_over_ranks(elapsed)
-    value = ws * cells * args.steps / elapsed
+    value, elapsed = aggregate(elapsed, cells * args.steps, dist if ws > 1 else None, device="cuda")
 
     # ---- per-kernel event timing (eager launches, same solver and state) ----
     ksteps = max(3, min(args.steps, 20))
