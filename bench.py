@@ -62,14 +62,23 @@ def aggregate(elapsed: float, units_per_rank: float, dist=None, device=None):
     return ws * units_per_rank / elapsed, elapsed
 
 
+def stage_source_sha() -> str:
+    """Hash of the stage kernel's source: its body in kernels.cuh plus physics.cuh and amr_types.h."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_0910_5547_gb300", "csrc")
+    k = open(os.path.join(csrc, "kernels.cuh")).read()
+    a = k.index("template <typename T, int NV, int STAGE")
+    b = k.index("// ----", a)
+    src = k[a:b] + open(os.path.join(csrc, "physics.cuh")).read() + open(os.path.join(csrc, "amr_types.h")).read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def stage_traffic():
     """DRAM bytes per stage-kernel launch (mean of stage 1 and stage 2) from the committed ncu
     summary, used only while the kernel source is the one that was profiled."""
     import hashlib
     import re
-    src = b"".join(open(os.path.join(ROOT, "paper_0910_5547_gb300", "csrc", f), "rb").read()
-                   for f in ("kernels.cuh", "physics.cuh", "amr_types.h"))
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = stage_source_sha()
     try:
         txt = open(os.path.join(ROOT, "profiles", "stage_kernel_fp32_kh256.md")).read()
         m = re.search(r"source_sha=(\w+) traffic_per_launch=(\d+)", txt)

@@ -748,10 +748,10 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
   struct Cand { TileParams tp; int occ; };
   std::vector<Cand> cands;
-  const int occs[2] = {0, 3};
+  const int occs[2] = {0, h->ops->alt_occupancy()};
   const int shapes[4][3] = {{32, 256, 32}, {32, 256, 16}, {16, 256, 16}, {32, 256, 64}};
   for (int o = 0; o < 2; ++o) {
-    if (occs[o] == 3 && !(h->cfg.nvar == 5 && h->cfg.precision == AMR_FP32)) continue;
+    if (o == 1 && occs[1] == 0) continue;
     for (auto& sh : shapes) {
       Cand c;
       c.tp.max_wx = sh[0]; c.tp.max_cols = sh[1]; c.tp.zchunk = sh[2];
@@ -769,7 +769,7 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const TileParams keep_tp = h->tp;
-  const int keep_occ = h->ops->stage_occupancy() == 3 ? 3 : 0;
+  const int keep_occ = h->ops->stage_occupancy();
   double best = 1e300;
   int best_i = -1;
   std::string rep;
@@ -791,7 +791,7 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
     }
     char line[160];
     std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d: %.4f ms\n", h->tp.max_wx,
-                  h->tp.max_cols, h->tp.zchunk, cands[ci].occ == 3 ? 3 : h->ops->stage_occupancy(), t_best);
+                  h->tp.max_cols, h->tp.zchunk, h->ops->stage_occupancy(), t_best);
     rep += line;
     if (t_best < best) { best = t_best; best_i = (int)ci; }
   }

@@ -24,9 +24,10 @@ struct OpsBase {
   virtual cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
                             const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3],
                             const double dx0[3], int fuse_rate, int grid) = 0;
-  // resident CTAs per SM the stage kernel is compiled for (register budget); the
-  // FP32 Euler kernel has a 2- and a 3-CTA build, selected here
+  // resident CTAs per SM the stage kernel is compiled for (register budget);
+  // each variant except FP64 MHD has a second build, selected here
   virtual int stage_occupancy() const = 0;
+  virtual int alt_occupancy() const = 0;   // the other compiled budget (0: none)
   virtual void set_stage_occupancy(int ctas_per_sm) = 0;
   virtual cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) = 0;
   virtual cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,

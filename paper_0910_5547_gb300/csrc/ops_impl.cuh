@@ -10,8 +10,12 @@ template <typename T, int NV>
 struct Ops final : OpsBase {
   Phys<T> ph{};
   double gamma = 1.4;
-  int occ = 0;   // 0: default build; 3: three-CTA build (FP32 Euler)
-  static constexpr bool kHasOcc3 = sizeof(T) == 4 && NV == 5;
+  int occ = 0;   // 0: default build; kAlt: the alternate register budget
+  // default resident CTAs per SM of the stage kernel, and the alternate build
+  // (FP32 Euler: 2 -> 3; FP32 MHD and FP64 Euler: 1 -> 2; FP64 MHD: none)
+  static constexpr int kDef = (sizeof(T) == 4 && NV == 5) ? 2 : 1;
+  static constexpr int kAlt = (sizeof(T) == 4 && NV == 5) ? 3 : 2;
+  static constexpr bool kHasAlt = !(sizeof(T) == 8 && NV == 9);
 
   explicit Ops(const PhysParams& p) {
     gamma = p.gamma;
@@ -25,16 +29,17 @@ struct Ops final : OpsBase {
                          (int)stage_smem_bytes<T, NV>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem_bytes<T, NV>());
-    if (kHasOcc3) {
-      cudaFuncSetAttribute(stage_kernel<T, NV, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (kHasAlt) {
+      cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)stage_smem_bytes<T, NV>());
-      cudaFuncSetAttribute(stage_kernel<T, NV, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(stage_kernel<T, NV, 2, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)stage_smem_bytes<T, NV>());
     }
   }
 
-  int stage_occupancy() const override { return occ == 3 ? 3 : ((sizeof(T) == 4 && NV == 5) ? 2 : 1); }
-  void set_stage_occupancy(int c) override { occ = (kHasOcc3 && c == 3) ? 3 : 0; }
+  int stage_occupancy() const override { return occ == kAlt ? kAlt : kDef; }
+  int alt_occupancy() const override { return kHasAlt ? kAlt : 0; }
+  void set_stage_occupancy(int c) override { occ = (kHasAlt && c == kAlt) ? kAlt : 0; }
 
   size_t elem_size() const override { return sizeof(T); }
 
@@ -60,9 +65,9 @@ struct Ops final : OpsBase {
     a.ph = ph;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
     const size_t sm = stage_smem_bytes<T, NV>();
-    if (kHasOcc3 && occ == 3) {
-      if (stage == 1) stage_kernel<T, NV, 1, 3><<<g, kStageThreads, sm, s>>>(a);
-      else stage_kernel<T, NV, 2, 3><<<g, kStageThreads, sm, s>>>(a);
+    if (kHasAlt && occ == kAlt) {
+      if (stage == 1) stage_kernel<T, NV, 1, kAlt><<<g, kStageThreads, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, kAlt><<<g, kStageThreads, sm, s>>>(a);
     } else {
       if (stage == 1) stage_kernel<T, NV, 1><<<g, kStageThreads, sm, s>>>(a);
       else stage_kernel<T, NV, 2><<<g, kStageThreads, sm, s>>>(a);
