@@ -749,10 +749,12 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   struct Cand { TileParams tp; int occ; };
   std::vector<Cand> cands;
   const int occs[2] = {0, h->ops->alt_occupancy()};
-  const int shapes[4][3] = {{32, 256, 32}, {32, 256, 16}, {16, 256, 16}, {32, 256, 64}};
+  const int shapes[7][3] = {{32, 256, 32}, {32, 256, 16}, {16, 256, 16}, {32, 256, 64},
+                            {16, 128, 8}, {16, 128, 16}, {16, 128, 32}};
   for (int o = 0; o < 2; ++o) {
     if (o == 1 && occs[1] == 0) continue;
     for (auto& sh : shapes) {
+      if (o == 1 && sh[1] == 128) continue;   // the 128-thread build keeps the default register budget
       Cand c;
       c.tp.max_wx = sh[0]; c.tp.max_cols = sh[1]; c.tp.zchunk = sh[2];
       c.occ = occs[o];
@@ -776,6 +778,7 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   for (size_t ci = 0; ci < cands.size(); ++ci) {
     h->tp = cands[ci].tp;
     h->ops->set_stage_occupancy(cands[ci].occ);
+    h->ops->set_stage_threads(h->tp.max_cols);
     build_items(h->plan, h->tp);
     amr_status st = upload_items(h);
     if (st != AMR_OK) break;
@@ -800,9 +803,11 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   if (best_i < 0) {
     h->tp = keep_tp;
     h->ops->set_stage_occupancy(keep_occ);
+    h->ops->set_stage_threads(h->tp.max_cols);
   } else {
     h->tp = cands[best_i].tp;
     h->ops->set_stage_occupancy(cands[best_i].occ);
+    h->ops->set_stage_threads(h->tp.max_cols);
     char line[96];
     std::snprintf(line, sizeof line, "chosen: candidate %d\n", best_i);
     rep += line;

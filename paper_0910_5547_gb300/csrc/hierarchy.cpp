@@ -320,8 +320,9 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
 }
 
 void build_items(Plan& plan, const TileParams& tp) {
-  const int max_wx = tp.max_wx > 0 ? std::min(tp.max_wx, kMaxTileX) : kMaxTileX;
   const int max_cols = tp.max_cols > 0 ? std::min(tp.max_cols, kStageThreads) : kStageThreads;
+  // a tile row plus its four halo rows must fit the threads: 4 (wx + 1) <= max_cols
+  const int max_wx = std::min(tp.max_wx > 0 ? std::min(tp.max_wx, kMaxTileX) : kMaxTileX, max_cols / 4 - 1);
   const int zchunk = tp.zchunk > 0 ? tp.zchunk : 32;
   const std::vector<HPatch>& P = plan.patches;
   auto split = [](int n, int parts, std::vector<std::pair<int, int>>& out) {
@@ -346,9 +347,9 @@ void build_items(Plan& plan, const TileParams& tp) {
       split(p.n[2], zparts, zs);
       for (auto& z : zs)
         for (auto& x : xs) {
-          // one halo cell per thread: 4 (wx + wy) <= 256; plane with halo within kPlaneMax
+          // one halo cell per thread: 4 (wx + wy) <= threads (= max_cols); plane with halo within kPlaneMax
           int wymax = std::min(std::min(max_cols / x.second, kPlaneMax / (x.second + 4) - 4),
-                               kStageThreads / 4 - x.second);
+                               max_cols / 4 - x.second);
           wymax = std::max(wymax, 1);
           split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);
           for (auto& y : ys) {

@@ -123,8 +123,8 @@ __device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, 
 // halo; (2) every cell's x and y limited slopes, computed once, as face
 // states w +- s; (3) every x and y face flux, solved once.  The update then
 // differences the fluxes of the cell's six faces.
-template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1>
-__global__ void __launch_bounds__(kStageThreads, MINB) stage_kernel(StageArgs<T> a) {
+template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1, int NT = kStageThreads>
+__global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* W = reinterpret_cast<T*>(smem_raw);
   T* XL = W + NV * kPlaneMax;

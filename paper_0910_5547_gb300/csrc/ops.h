@@ -29,6 +29,8 @@ struct OpsBase {
   virtual int stage_occupancy() const = 0;
   virtual int alt_occupancy() const = 0;   // the other compiled budget (0: none)
   virtual void set_stage_occupancy(int ctas_per_sm) = 0;
+  // threads per stage CTA: 256 (default) or 128 (same registers per thread, twice the CTAs)
+  virtual void set_stage_threads(int nt) = 0;
   virtual cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) = 0;
   virtual cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,
                              const void* U, const void* Uold, double alpha) = 0;

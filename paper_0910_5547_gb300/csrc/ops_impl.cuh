@@ -16,6 +16,7 @@ struct Ops final : OpsBase {
   static constexpr int kDef = (sizeof(T) == 4 && NV == 5) ? 2 : 1;
   static constexpr int kAlt = (sizeof(T) == 4 && NV == 5) ? 3 : 2;
   static constexpr bool kHasAlt = !(sizeof(T) == 8 && NV == 9);
+  int nt = kStageThreads;   // 256, or 128 (launched with twice the CTAs per SM, same register budget)
 
   explicit Ops(const PhysParams& p) {
     gamma = p.gamma;
@@ -29,6 +30,10 @@ struct Ops final : OpsBase {
                          (int)stage_smem_bytes<T, NV>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem_bytes<T, NV>());
+    cudaFuncSetAttribute(stage_kernel<T, NV, 1, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV>());
+    cudaFuncSetAttribute(stage_kernel<T, NV, 2, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV>());
     if (kHasAlt) {
       cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)stage_smem_bytes<T, NV>());
@@ -37,6 +42,7 @@ struct Ops final : OpsBase {
     }
   }
 
+  void set_stage_threads(int n) override { nt = n == 128 ? 128 : kStageThreads; }
   int stage_occupancy() const override { return occ == kAlt ? kAlt : kDef; }
   int alt_occupancy() const override { return kHasAlt ? kAlt : 0; }
   void set_stage_occupancy(int c) override { occ = (kHasAlt && c == kAlt) ? kAlt : 0; }
@@ -65,7 +71,10 @@ struct Ops final : OpsBase {
     a.ph = ph;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
     const size_t sm = stage_smem_bytes<T, NV>();
-    if (kHasAlt && occ == kAlt) {
+    if (nt == 128) {
+      if (stage == 1) stage_kernel<T, NV, 1, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
+    } else if (kHasAlt && occ == kAlt) {
       if (stage == 1) stage_kernel<T, NV, 1, kAlt><<<g, kStageThreads, sm, s>>>(a);
       else stage_kernel<T, NV, 2, kAlt><<<g, kStageThreads, sm, s>>>(a);
     } else {
