@@ -43,6 +43,32 @@ __device__ __forceinline__ T half_slope(T wm, T w0, T wp, T theta) {
   return T(0.5) * s;
 }
 
+// FP32 form of the same limiter with sm_100-family instructions:
+// min.xorsign.abs gives min(|x|, |y|) with the sign of x*y, so
+// max(min.xorsign.abs(x, y), 0) is min(|x|, |y|) when x and y share a sign and
+// 0 otherwise; the result takes the sign of a.
+__device__ __forceinline__ float half_slope(float wm, float w0, float wp, float theta) {
+  const float a = w0 - wm, b = wp - w0;
+  const float ht = 0.5f * theta;
+  const float cq = fabsf((wp - wm) * 0.25f);
+  float t;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(ht * a), "f"(ht * b));
+  return copysignf(fminf(fmaxf(t, 0.0f), cq), a);
+}
+
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double min3(double a, double b, double c) { return dmin(dmin(a, b), c); }
+__device__ __forceinline__ double max3(double a, double b, double c) { return dmax(dmax(a, b), c); }
+
 // Conserved -> reconstructed variables; returns false for rho <= 0, e <= 0 or NaN.
 template <typename T, int NV>
 __device__ __forceinline__ bool cons_to_prim(const T* u, T* w) {
@@ -122,8 +148,8 @@ __device__ __forceinline__ void hll_euler(const T* wl, const T* wr, const Phys<T
   Ur[4] = rr * (T(0.5) * v2r + wr[4]);
   const T pl = ph.gm1 * (rl * wl[4]), pr = ph.gm1 * (rr * wr[4]);
   const T cl = dsqrt(ph.ggm1 * wl[4]), cr = dsqrt(ph.ggm1 * wr[4]);
-  const T SL = dmin(dmin(T(0), vl - cl), vr - cr);
-  const T SR = dmax(dmax(T(0), vl + cl), vr + cr);
+  const T SL = min3(T(0), vl - cl, vr - cr);
+  const T SR = max3(T(0), vl + cl, vr + cr);
   const T inv = drcp(SR - SL);
   const T alpha = SR * (vl - SL) * inv;
   const T beta = SL * (SR - vr) * inv;
