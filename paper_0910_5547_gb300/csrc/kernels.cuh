@@ -116,13 +116,14 @@ __device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, 
 }
 
 // Fused RK2 stage over work items (patch, wx x wy column block, z range).
-// Each thread owns one column and marches in z: primitives of planes k, k+1,
-// the z slope of plane k and the z-face flux F_{k-1/2} live in registers and
-// the next plane's global loads are issued one iteration ahead.  Per plane,
-// three shared-memory phases: (1) primitives of plane k with a two-cell face
-// halo; (2) every cell's x and y limited slopes, computed once, as face
-// states w +- s; (3) every x and y face flux, solved once.  The update then
-// differences the fluxes of the cell's six faces.
+// Each thread owns one column and marches in z: primitives of two planes, one
+// z slope and the last z-face flux live in registers and the next plane's
+// global loads are issued one iteration ahead.  Shared memory holds, per plane,
+// the primitives with a two-cell face halo, every cell's x and y face states
+// w +- s (each limited slope computed once) and every x and y face flux
+// (each solved once); the update differences the fluxes of the cell's six
+// faces.  The work of plane j is skewed against that of plane j-1 so that
+// one plane costs two barriers.
 template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1, int NT = kStageThreads>
 __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -194,144 +195,124 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       }
     }
 
-    T uD[NV], wA[NV], wB[NV], sA[NV], Fm[NV], hN[NV], unN[NV];
-    if (active) {  // prologue: planes z0-2 .. z0+2
-      T u0[NV], u1[NV], w0[NV], w1[NV];
+    // z-march registers at the start of iteration j: wA = w(j-1), wB = w(j),
+    // sA = slope(j-1), uD = conserved plane j+1 (in flight); Fzm = flux of face
+    // j-3/2 (from the previous iteration).
+    T uD[NV], wA[NV], wB[NV], sA[NV], Fzm[NV], hN[NV], unN[NV];
+    if (active) {  // prologue: planes z0-2 .. z0+1
+      T u0[NV], w0[NV];
       load_cons<T, NV>(Ub, vs, col - 2 * plane, u0);
-      load_cons<T, NV>(Ub, vs, col - plane, u1);
-      load_cons<T, NV>(Ub, vs, col, uD);
+      load_cons<T, NV>(Ub, vs, col - plane, uD);
       cons_to_prim<T, NV>(u0, w0);
-      cons_to_prim<T, NV>(u1, w1);
-      bad |= !cons_to_prim<T, NV>(uD, wA);
+      cons_to_prim<T, NV>(uD, wA);
+      load_cons<T, NV>(Ub, vs, col, uD);
+      bad |= !cons_to_prim<T, NV>(uD, wB);
       load_cons<T, NV>(Ub, vs, col + plane, uD);
-      bad |= !cons_to_prim<T, NV>(uD, wB) && wz > 1;
-      load_cons<T, NV>(Ub, vs, col + 2 * plane, uD);
       if (STAGE == 2) load_cons<T, NV>(Ob, vs, col, unN);
-      T wl[NV], wr[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const T s_m1 = half_slope(w0[v], w1[v], wA[v], ph.theta);
-        sA[v] = half_slope(w1[v], wA[v], wB[v], ph.theta);
-        wl[v] = w1[v] + s_m1;
-        wr[v] = wA[v] - sA[v];
-      }
-      riemann<T, NV, 2>(wl, wr, ph, Fm);
+      for (int v = 0; v < NV; ++v) sA[v] = half_slope(w0[v], wA[v], wB[v], ph.theta);
     }
     if (has_halo) load_cons<T, NV>(Ub, vs, hoff, hN);
 
-    for (int kk = 0; kk < wz; ++kk) {
-      const int kn = kk + 1 < wz ? kk + 1 : kk;   // next plane (clamped: the last prefetch is unused)
-      T Fp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
-      // ---- phase 1: z face k+1/2, primitives of plane k into shared memory ----
+    // Iteration j runs two phases separated by barriers:
+    //   A: z face j-1/2 and the primitives of plane j into shared memory (j < wz);
+    //      x and y face fluxes of plane j-1 (j >= 1)
+    //   B: x and y limited slopes of plane j (j < wz); update of plane j-1 (j >= 1)
+    // Each shared buffer is written in one phase and read in the other.
+    for (int j = 0; j <= wz; ++j) {
+      const bool cur = j < wz, prev = j > 0;
+      T Fzp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
+      // ---- phase A ----
       if (active) {
-        // stage input of the own cell, plane k (read two planes ago: a cache hit), issued
-        // here so that it is in flight across the three shared-memory phases
-        load_cons<T, NV>(Ub, vs, col + kk * plane, uin);
+        // stage input of the own cell, plane j-1 (read earlier: a cache hit)
+        if (prev) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
         T wC[NV], sB[NV], wl[NV], wr[NV];
-        const bool ok = cons_to_prim<T, NV>(uD, wC);        // plane k+2
-        if (kk + 2 < wz) bad |= !ok;
-        load_cons<T, NV>(Ub, vs, col + (kn + 2) * plane, uD);  // prefetch plane k+3
+        const bool ok = cons_to_prim<T, NV>(uD, wC);        // plane j+1
+        if (j + 1 < wz) bad |= !ok;
+        const int jn = j + 2 <= wz + 1 ? j + 2 : wz + 1;   // ghost planes end at wz+1
+        load_cons<T, NV>(Ub, vs, col + jn * plane, uD);      // prefetch plane j+2
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           sB[v] = half_slope(wA[v], wB[v], wC[v], ph.theta);
           wl[v] = wA[v] + sA[v];
           wr[v] = wB[v] - sB[v];
-          W[v * kPlaneMax + me] = wA[v];
-          own[v] = wA[v];
-          un[v] = unN[v];
+          own[v] = wB[v];
         }
-        if (STAGE == 2) load_cons<T, NV>(Ob, vs, col + kn * plane, unN);
-        riemann<T, NV, 2>(wl, wr, ph, Fp);
+        if (cur) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) W[v * kPlaneMax + me] = wB[v];
+        }
+        if (STAGE == 2 && prev) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) un[v] = unN[v];
+          load_cons<T, NV>(Ob, vs, col + (cur ? j : j - 1) * plane, unN);
+        }
+        riemann<T, NV, 2>(wl, wr, ph, Fzp);                  // face j-1/2
 #pragma unroll
         for (int v = 0; v < NV; ++v) { sA[v] = sB[v]; wA[v] = wB[v]; wB[v] = wC[v]; }
       }
-      if (has_halo) {
+      if (has_halo && cur) {
         T w[NV];
         cons_to_prim<T, NV>(hN, w);
-        load_cons<T, NV>(Ub, vs, hoff + kn * plane, hN);
+        load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
 #pragma unroll
         for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
       }
-      __syncthreads();
-      // ---- phase 2: x and y limited slopes once per cell -> face states ----
-      if (active) {
+      if (prev) {
+        if (active) {
+          T wl[NV], wr[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlaneMax + me;
-          const T w0 = own[v];
-          const T sx = half_slope(Wv[-1], w0, Wv[1], ph.theta);
-          const T sy = half_slope(Wv[-sw], w0, Wv[sw], ph.theta);
-          XL[v * kStateMax + xs] = w0 + sx;
-          XR[v * kStateMax + xs] = w0 - sx;
-          YL[v * kStateMax + ys] = w0 + sy;
-          YR[v * kStateMax + ys] = w0 - sy;
+          for (int v = 0; v < NV; ++v) {
+            wl[v] = XL[v * kStateMax + xs - 1];
+            wr[v] = XR[v * kStateMax + xs];
+          }
+          riemann<T, NV, 0>(wl, wr, ph, Fx0);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            wl[v] = YL[v * kStateMax + ys - wx];
+            wr[v] = YR[v * kStateMax + ys];
+          }
+          riemann<T, NV, 1>(wl, wr, ph, Fy0);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            FX[v * nfx + ty * (wx + 1) + tx] = Fx0[v];
+            FY[v * nfy + ty * wx + tx] = Fy0[v];
+          }
         }
-      }
-      if (bkind >= 0) {
-        T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
-        const T sgn = (bkind == 0 || bkind == 2) ? T(1) : T(-1);
+        if (eb < wy) {  // x face at the right edge of row eb
+          T wl[NV], wr[NV], F[NV];
+          const int sl = eb * (wx + 2) + wx;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlaneMax + bpos;
-          const T w0 = Wv[0];
-          dst[v * kStateMax + bslot] = w0 + sgn * half_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
+          for (int v = 0; v < NV; ++v) {
+            wl[v] = XL[v * kStateMax + sl];
+            wr[v] = XR[v * kStateMax + sl + 1];
+          }
+          riemann<T, NV, 0>(wl, wr, ph, F);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) FX[v * nfx + eb * (wx + 1) + wx] = F[v];
+        } else if (eb < wy + wx) {  // y face at the top edge of column eb - wy
+          const int c = eb - wy;
+          T wl[NV], wr[NV], F[NV];
+          const int sl = wy * wx + c;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            wl[v] = YL[v * kStateMax + sl];
+            wr[v] = YR[v * kStateMax + sl + wx];
+          }
+          riemann<T, NV, 1>(wl, wr, ph, F);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) FY[v * nfy + wy * wx + c] = F[v];
         }
-      }
-      __syncthreads();
-      // ---- phase 3: every x and y face flux once ----
-      if (active) {
-        T wl[NV], wr[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          wl[v] = XL[v * kStateMax + xs - 1];
-          wr[v] = XR[v * kStateMax + xs];
-        }
-        riemann<T, NV, 0>(wl, wr, ph, Fx0);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          wl[v] = YL[v * kStateMax + ys - wx];
-          wr[v] = YR[v * kStateMax + ys];
-        }
-        riemann<T, NV, 1>(wl, wr, ph, Fy0);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          FX[v * nfx + ty * (wx + 1) + tx] = Fx0[v];
-          FY[v * nfy + ty * wx + tx] = Fy0[v];
-        }
-      }
-      if (eb < wy) {  // x face at the right edge of row eb
-        T wl[NV], wr[NV], F[NV];
-        const int sl = eb * (wx + 2) + wx;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          wl[v] = XL[v * kStateMax + sl];
-          wr[v] = XR[v * kStateMax + sl + 1];
-        }
-        riemann<T, NV, 0>(wl, wr, ph, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FX[v * nfx + eb * (wx + 1) + wx] = F[v];
-      } else if (eb < wy + wx) {  // y face at the top edge of column eb - wy
-        const int c = eb - wy;
-        T wl[NV], wr[NV], F[NV];
-        const int sl = wy * wx + c;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          wl[v] = YL[v * kStateMax + sl];
-          wr[v] = YR[v * kStateMax + sl + wx];
-        }
-        riemann<T, NV, 1>(wl, wr, ph, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FY[v * nfy + wy * wx + c] = F[v];
       }
       __syncthreads();
-      // ---- update: U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2 ----
-      if (active) {
-        const int c = col + kk * plane;
+      // ---- phase B ----
+      if (active && prev) {  // U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2, plane j-1
+        const int c = col + (j - 1) * plane;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const T Lx = (FX[v * nfx + ty * (wx + 1) + tx + 1] - Fx0[v]) * a.idx;
           const T Ly = (FY[v * nfy + (ty + 1) * wx + tx] - Fy0[v]) * a.idy;
-          const T Lz = (Fp[v] - Fm[v]) * a.idz;
+          const T Lz = (Fzp[v] - Fzm[v]) * a.idz;
           const T L = -(Lx + Ly + Lz);
           if (STAGE == 1) {
             Ob[v * vs + c] = uin[v] + dt * L;
@@ -340,7 +321,6 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
             un[v] = T(0.5) * un[v] + T(0.5) * u2;
             Ob[v * vs + c] = un[v];
           }
-          Fm[v] = Fp[v];
         }
         if (STAGE == 2 && a.fuse_rate) {
           T r, sp;
@@ -349,8 +329,37 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           speed_max = dmax(speed_max, sp);
         }
       }
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fzm[v] = Fzp[v];
+      }
+      if (cur) {
+        if (active) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const T* Wv = W + v * kPlaneMax + me;
+            const T w0 = own[v];
+            const T sx = half_slope(Wv[-1], w0, Wv[1], ph.theta);
+            const T sy = half_slope(Wv[-sw], w0, Wv[sw], ph.theta);
+            XL[v * kStateMax + xs] = w0 + sx;
+            XR[v * kStateMax + xs] = w0 - sx;
+            YL[v * kStateMax + ys] = w0 + sy;
+            YR[v * kStateMax + ys] = w0 - sy;
+          }
+        }
+        if (bkind >= 0) {
+          T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
+          const T sgn = (bkind == 0 || bkind == 2) ? T(1) : T(-1);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const T* Wv = W + v * kPlaneMax + bpos;
+            const T w0 = Wv[0];
+            dst[v * kStateMax + bslot] = w0 + sgn * half_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
+          }
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();  // the next item reuses the shared buffers
   }
   if (bad) atomicOr(&a.params->bad, 1u);
   if (STAGE == 2 && a.fuse_rate) {

@@ -186,8 +186,8 @@ __device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
     for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (Fl[k] + Fr[k] - a * (Ur[k] - Ul[k]));
   } else {
     // S_R - S_L > 0 for every state with c > 0 (the kernels flag e <= 0 as non-physical)
-    const T SL = dmin(dmin(T(0), vl - cl), vr - cr);
-    const T SR = dmax(dmax(T(0), vl + cl), vr + cr);
+    const T SL = min3(T(0), vl - cl, vr - cr);
+    const T SR = max3(T(0), vl + cl, vr + cr);
     const T inv = drcp(SR - SL);
     const T slsr = SL * SR;
 #pragma unroll
