@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 
   const Phys<T> ph = phys_with_ch<T, NV>(a.ph, a.params);
   const T dt = (T)(a.params->dt0 * a.dt_scale);
+  const T dtx = dt * a.idx, dty = dt * a.idy, dtz = dt * a.idz;
+  const T sc = slope_scale<T>();   // face state = w +- sc * limited_slope
   const int t = threadIdx.x;
   bool bad = false;
   T rate_max = T(0), speed_max = T(0);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       load_cons<T, NV>(Ub, vs, col + plane, uD);
       if (STAGE == 2) load_cons<T, NV>(Ob, vs, col, unN);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sA[v] = half_slope(w0[v], wA[v], wB[v], ph.theta);
+      for (int v = 0; v < NV; ++v) sA[v] = limited_slope(w0[v], wA[v], wB[v], ph.theta);
     }
     if (has_halo) load_cons<T, NV>(Ub, vs, hoff, hN);
 
@@ -233,9 +235,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         load_cons<T, NV>(Ub, vs, col + jn * plane, uD);      // prefetch plane j+2
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          sB[v] = half_slope(wA[v], wB[v], wC[v], ph.theta);
-          wl[v] = wA[v] + sA[v];
-          wr[v] = wB[v] - sB[v];
+          sB[v] = limited_slope(wA[v], wB[v], wC[v], ph.theta);
+          wl[v] = wA[v] + sc * sA[v];
+          wr[v] = wB[v] - sc * sB[v];
           own[v] = wB[v];
         }
         if (cur) {
@@ -310,14 +312,12 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         const int c = col + (j - 1) * plane;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T Lx = (FX[v * nfx + ty * (wx + 1) + tx + 1] - Fx0[v]) * a.idx;
-          const T Ly = (FY[v * nfy + (ty + 1) * wx + tx] - Fy0[v]) * a.idy;
-          const T Lz = (Fzp[v] - Fzm[v]) * a.idz;
-          const T L = -(Lx + Ly + Lz);
+          // u + dt L(u), L = -sum_d (F_{d,+} - F_{d,-}) / dx_d
+          const T u2 = uin[v] - dtx * (FX[v * nfx + ty * (wx + 1) + tx + 1] - Fx0[v]) -
+                       dty * (FY[v * nfy + (ty + 1) * wx + tx] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
           if (STAGE == 1) {
-            Ob[v * vs + c] = uin[v] + dt * L;
+            Ob[v * vs + c] = u2;
           } else {
-            const T u2 = uin[v] + dt * L;
             un[v] = T(0.5) * un[v] + T(0.5) * u2;
             Ob[v * vs + c] = un[v];
           }
@@ -339,22 +339,22 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           for (int v = 0; v < NV; ++v) {
             const T* Wv = W + v * kPlaneMax + me;
             const T w0 = own[v];
-            const T sx = half_slope(Wv[-1], w0, Wv[1], ph.theta);
-            const T sy = half_slope(Wv[-sw], w0, Wv[sw], ph.theta);
-            XL[v * kStateMax + xs] = w0 + sx;
-            XR[v * kStateMax + xs] = w0 - sx;
-            YL[v * kStateMax + ys] = w0 + sy;
-            YR[v * kStateMax + ys] = w0 - sy;
+            const T sx = limited_slope(Wv[-1], w0, Wv[1], ph.theta);
+            const T sy = limited_slope(Wv[-sw], w0, Wv[sw], ph.theta);
+            XL[v * kStateMax + xs] = w0 + sc * sx;
+            XR[v * kStateMax + xs] = w0 - sc * sx;
+            YL[v * kStateMax + ys] = w0 + sc * sy;
+            YR[v * kStateMax + ys] = w0 - sc * sy;
           }
         }
         if (bkind >= 0) {
           T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
-          const T sgn = (bkind == 0 || bkind == 2) ? T(1) : T(-1);
+          const T sgn = (bkind == 0 || bkind == 2) ? sc : -sc;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             const T* Wv = W + v * kPlaneMax + bpos;
             const T w0 = Wv[0];
-            dst[v * kStateMax + bslot] = w0 + sgn * half_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
+            dst[v * kStateMax + bslot] = w0 + sgn * limited_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
           }
         }
       }

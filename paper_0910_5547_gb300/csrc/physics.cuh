@@ -43,17 +43,30 @@ __device__ __forceinline__ T half_slope(T wm, T w0, T wp, T theta) {
   return T(0.5) * s;
 }
 
-// FP32 form of the same limiter with sm_100-family instructions:
-// min.xorsign.abs gives min(|x|, |y|) with the sign of x*y, so
-// max(min.xorsign.abs(x, y), 0) is min(|x|, |y|) when x and y share a sign and
+// Limited slope in the scale the stage kernel carries: a face state is
+// w +- kSlopeScale<T> * limited_slope(...).  FP64 carries the half slope itself.
+// FP32 carries four times the half slope, minmod(2 theta a, 2 theta b, w_{i+1} - w_{i-1}),
+// and folds the exact factor 1/4 into the fused multiply-add that forms the
+// face state (the rounding is that of w + s with s the half slope).  It uses
+// min.xorsign.abs (sm_100 family): min(|x|, |y|) with the sign of x*y, so
+// max(min.xorsign.abs(a, b), 0) is min(|a|, |b|) when a and b share a sign and
 // 0 otherwise; the result takes the sign of a.
-__device__ __forceinline__ float half_slope(float wm, float w0, float wp, float theta) {
+template <typename T> struct SlopeScale { static constexpr double v = 1.0; };
+template <> struct SlopeScale<float> { static constexpr double v = 0.25; };
+template <typename T> __device__ __forceinline__ T slope_scale() { return T(SlopeScale<T>::v); }
+
+template <typename T>
+__device__ __forceinline__ T limited_slope(T wm, T w0, T wp, T theta) { return half_slope(wm, w0, wp, theta); }
+
+__device__ __forceinline__ float limited_slope(float wm, float w0, float wp, float theta) {
   const float a = w0 - wm, b = wp - w0;
-  const float ht = 0.5f * theta;
-  const float cq = fabsf((wp - wm) * 0.25f);
   float t;
-  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(ht * a), "f"(ht * b));
-  return copysignf(fminf(fmaxf(t, 0.0f), cq), a);
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(a), "f"(b));
+  return copysignf(fminf(fmaxf(t, 0.0f) * (2.0f * theta), fabsf(wp - wm)), a);
+}
+
+__device__ __forceinline__ float half_slope(float wm, float w0, float wp, float theta) {
+  return 0.25f * limited_slope(wm, w0, wp, theta);
 }
 
 __device__ __forceinline__ float min3(float a, float b, float c) {
@@ -133,31 +146,30 @@ __device__ __forceinline__ void state_flux(const T* w, const Phys<T>& ph, T* U, 
 // Euler HLL without forming the two physical fluxes: with F = U v_n + P,
 // P = (0, p e_D, p v_n), the two-wave flux
 //   (S_R F_l - S_L F_r + S_L S_R (U_r - U_l)) / (S_R - S_L)
-// equals alpha U_l + beta U_r + (S_R P_l - S_L P_r) / (S_R - S_L) with
-// alpha = S_R (v_l - S_L) / (S_R - S_L) and beta = S_L (S_R - v_r) / (S_R - S_L).
+// equals alpha U_l + beta U_r + a P_l - b P_r with a = S_R / (S_R - S_L),
+// b = S_L / (S_R - S_L), alpha = a (v_l - S_L), beta = b (S_R - v_r).  Since
+// U = rho (1, v, v^2/2 + e), alpha U_l + beta U_r is formed from alpha rho_l and
+// beta rho_r and the primitive states without the conserved vectors.
 template <typename T, int D>
 __device__ __forceinline__ void hll_euler(const T* wl, const T* wr, const Phys<T>& ph, T* F) {
-  T Ul[5], Ur[5];
-  const T rl = wl[0], rr = wr[0];
+  const T rl = wl[0], rr = wr[0], el = wl[4], er = wr[4];
   const T vl = wl[1 + D], vr = wr[1 + D];
-  Ul[0] = rl; Ul[1] = rl * wl[1]; Ul[2] = rl * wl[2]; Ul[3] = rl * wl[3];
-  Ur[0] = rr; Ur[1] = rr * wr[1]; Ur[2] = rr * wr[2]; Ur[3] = rr * wr[3];
-  const T v2l = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
-  const T v2r = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-  Ul[4] = rl * (T(0.5) * v2l + wl[4]);
-  Ur[4] = rr * (T(0.5) * v2r + wr[4]);
-  const T pl = ph.gm1 * (rl * wl[4]), pr = ph.gm1 * (rr * wr[4]);
-  const T cl = dsqrt(ph.ggm1 * wl[4]), cr = dsqrt(ph.ggm1 * wr[4]);
+  const T cl = dsqrt(ph.ggm1 * el), cr = dsqrt(ph.ggm1 * er);
   const T SL = min3(T(0), vl - cl, vr - cr);
   const T SR = max3(T(0), vl + cl, vr + cr);
   const T inv = drcp(SR - SL);
-  const T alpha = SR * (vl - SL) * inv;
-  const T beta = SL * (SR - vr) * inv;
-  const T pS = SR * pl, pSr = SL * pr;
+  const T a = SR * inv, b = SL * inv;
+  const T ar = a * (vl - SL) * rl;   // alpha rho_l
+  const T br = b * (SR - vr) * rr;   // beta rho_r
+  const T hl = T(0.5) * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) + el;
+  const T hr = T(0.5) * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) + er;
+  F[0] = ar + br;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) F[k] = alpha * Ul[k] + beta * Ur[k];
-  F[1 + D] += (pS - pSr) * inv;
-  F[4] += (pS * vl - pSr * vr) * inv;
+  for (int k = 1; k < 4; ++k) F[k] = ar * wl[k] + br * wr[k];
+  F[4] = ar * hl + br * hr;
+  const T ql = a * (ph.gm1 * (rl * el)), qr = b * (ph.gm1 * (rr * er));   // a p_l, b p_r
+  F[1 + D] += ql - qr;
+  F[4] += ql * vl - qr * vr;
 }
 
 template <typename T, int NV, int D>
