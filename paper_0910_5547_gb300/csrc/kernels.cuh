@@ -36,10 +36,33 @@ namespace amr {
 constexpr int kFaceMax = 2 * kStageThreads + 88;
 constexpr int kStateMax = kStageThreads + 128;
 
+// FP32 Euler stage kernels also stage their conserved inputs through shared
+// memory, filled by cp.async: a ring of four planes of the stage input (own
+// columns and halo cells) and, in stage 2, a ring of two planes of U^n (own
+// columns).  The other variants load them into registers (their shared memory
+// has no room for the rings at the occupancy they run at).
+template <typename T, int NV>
+__host__ __device__ constexpr bool stage_async() { return NV == 5 && sizeof(T) == 4; }
+constexpr int kRing = 4;
+constexpr int kRingN = 2;
+
 template <typename T, int NV>
 constexpr size_t stage_smem_bytes() {
-  return sizeof(T) * NV * (kPlaneMax + 4 * kStateMax + kFaceMax);
+  return sizeof(T) * NV *
+         (kPlaneMax + 4 * kStateMax + kFaceMax + (stage_async<T, NV>() ? kRing * kPlaneMax + kRingN * kStageThreads : 0));
 }
+
+// Asynchronous global -> shared copy of one element (sm_80+ cp.async).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 struct ChunkDesc {  // a contiguous range of interior cells of one patch
   int patch;
@@ -133,6 +156,12 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   T* YL = XR + NV * kStateMax;
   T* YR = YL + NV * kStateMax;
   T* FX = YR + NV * kStateMax;
+  constexpr bool kAsync = stage_async<T, NV>();
+  // ring of stage-input planes: plane p of the item lives in slot p & 3, [slot][var][plane cell];
+  // ring of U^n planes (stage 2): plane p in slot p & 1, [slot][var][thread].  Each thread
+  // reads back only the cells it copied itself (own column, own halo cell).
+  T* CR = FX + NV * kFaceMax;
+  T* CN = CR + kRing * NV * kPlaneMax;
 
   const Phys<T> ph = phys_with_ch<T, NV>(a.ph, a.params);
   const T dt = (T)(a.params->dt0 * a.dt_scale);
@@ -209,12 +238,31 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       cons_to_prim<T, NV>(uD, wA);
       load_cons<T, NV>(Ub, vs, col, uD);
       bad |= !cons_to_prim<T, NV>(uD, wB);
-      load_cons<T, NV>(Ub, vs, col + plane, uD);
-      if (STAGE == 2) load_cons<T, NV>(Ob, vs, col, unN);
+      if (kAsync) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          CR[v * kPlaneMax + me] = uD[v];                                                 // plane 0, slot 0
+          cp_async_elem(&CR[(NV + v) * kPlaneMax + me], Ub + v * vs + col + plane);     // plane 1, slot 1
+        }
+      } else {
+        load_cons<T, NV>(Ub, vs, col + plane, uD);
+      }
+      if (STAGE == 2 && !kAsync) load_cons<T, NV>(Ob, vs, col, unN);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sA[v] = limited_slope(w0[v], wA[v], wB[v], ph.theta);
     }
-    if (has_halo) load_cons<T, NV>(Ub, vs, hoff, hN);
+    if (kAsync) {
+      if (has_halo) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          cp_async_elem(&CR[v * kPlaneMax + hpos], Ub + v * vs + hoff);
+          if (wz > 1) cp_async_elem(&CR[(NV + v) * kPlaneMax + hpos], Ub + v * vs + hoff + plane);
+        }
+      }
+      cp_async_commit();
+    } else if (has_halo) {
+      load_cons<T, NV>(Ub, vs, hoff, hN);
+    }
 
     // Iteration j runs two phases separated by barriers:
     //   A: z face j-1/2 and the primitives of plane j into shared memory (j < wz);
@@ -225,14 +273,40 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       const bool cur = j < wz, prev = j > 0;
       T Fzp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
       // ---- phase A ----
+      if (kAsync) {  // copies of plane j+2 (ghost planes end at wz+1), then wait for plane j+1
+        const int jn = j + 2;
+        T* slot = CR + (jn & (kRing - 1)) * NV * kPlaneMax;
+        if (active && jn <= wz + 1) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlaneMax + me], Ub + v * vs + col + jn * plane);
+        }
+        if (has_halo && jn < wz) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlaneMax + hpos], Ub + v * vs + hoff + jn * plane);
+        }
+        if (STAGE == 2 && active && cur) {  // U^n of plane j, used by the update of plane j
+          T* sn = CN + (j & (kRingN - 1)) * NV * kStageThreads + t;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) cp_async_elem(&sn[v * kStageThreads], Ob + v * vs + col + j * plane);
+        }
+        cp_async_commit();
+        cp_async_wait1();
+      }
       if (active) {
         // stage input of the own cell, plane j-1 (read earlier: a cache hit)
-        if (prev) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
+        if (!kAsync && prev) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
         T wC[NV], sB[NV], wl[NV], wr[NV];
+        if (kAsync) {
+          const T* slot = CR + ((j + 1) & (kRing - 1)) * NV * kPlaneMax + me;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) uD[v] = slot[v * kPlaneMax];
+        }
         const bool ok = cons_to_prim<T, NV>(uD, wC);        // plane j+1
         if (j + 1 < wz) bad |= !ok;
-        const int jn = j + 2 <= wz + 1 ? j + 2 : wz + 1;   // ghost planes end at wz+1
-        load_cons<T, NV>(Ub, vs, col + jn * plane, uD);      // prefetch plane j+2
+        if (!kAsync) {
+          const int jn = j + 2 <= wz + 1 ? j + 2 : wz + 1;   // ghost planes end at wz+1
+          load_cons<T, NV>(Ub, vs, col + jn * plane, uD);      // prefetch plane j+2
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           sB[v] = limited_slope(wA[v], wB[v], wC[v], ph.theta);
@@ -244,7 +318,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) W[v * kPlaneMax + me] = wB[v];
         }
-        if (STAGE == 2 && prev) {
+        if (STAGE == 2 && prev && !kAsync) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) un[v] = unN[v];
           load_cons<T, NV>(Ob, vs, col + (cur ? j : j - 1) * plane, unN);
@@ -255,8 +329,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       }
       if (has_halo && cur) {
         T w[NV];
+        if (kAsync) {
+          const T* slot = CR + (j & (kRing - 1)) * NV * kPlaneMax + hpos;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlaneMax];
+        }
         cons_to_prim<T, NV>(hN, w);
-        load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
+        if (!kAsync) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
 #pragma unroll
         for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
       }
@@ -310,6 +389,16 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       // ---- phase B ----
       if (active && prev) {  // U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2, plane j-1
         const int c = col + (j - 1) * plane;
+        if (kAsync) {
+          const T* slot = CR + ((j - 1) & (kRing - 1)) * NV * kPlaneMax + me;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) uin[v] = slot[v * kPlaneMax];
+          if (STAGE == 2) {
+            const T* sn = CN + ((j - 1) & (kRingN - 1)) * NV * kStageThreads + t;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) un[v] = sn[v * kStageThreads];
+          }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           // u + dt L(u), L = -sum_d (F_{d,+} - F_{d,-}) / dx_d
