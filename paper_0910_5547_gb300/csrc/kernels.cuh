@@ -265,10 +265,17 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     }
 
     // Iteration j runs two phases separated by barriers:
-    //   A: z face j-1/2 and the primitives of plane j into shared memory (j < wz);
-    //      x and y face fluxes of plane j-1 (j >= 1)
-    //   B: x and y limited slopes of plane j (j < wz); update of plane j-1 (j >= 1)
-    // Each shared buffer is written in one phase and read in the other.
+    //   A: z face j-1/2 and the primitives of plane j into shared memory;
+    //      x and y face fluxes of plane j-1
+    //   B: update of plane j-1; x and y limited slopes of plane j
+    // Each shared buffer is written in one phase and read in the other.  For
+    // MHD (kMerge) the arithmetic of a phase runs as one straight-line block so
+    // that the three Riemann solves of phase A can interleave: at j = 0 the x/y
+    // fluxes are solved from stale face states and at j = wz the slopes from a
+    // stale plane, and the results are overwritten before anything reads them;
+    // only the global stores of the update and the CFL maxima are predicated.
+    // Euler skips that work (measured faster).
+    constexpr bool kMerge = NV == 9;
     for (int j = 0; j <= wz; ++j) {
       const bool cur = j < wz, prev = j > 0;
       T Fzp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
@@ -292,10 +299,22 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         cp_async_commit();
         cp_async_wait1();
       }
+      if (has_halo && cur) {
+        T w[NV];
+        if (kAsync) {
+          const T* slot = CR + (j & (kRing - 1)) * NV * kPlaneMax + hpos;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlaneMax];
+        }
+        cons_to_prim<T, NV>(hN, w);
+        if (!kAsync) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
+      }
       if (active) {
-        // stage input of the own cell, plane j-1 (read earlier: a cache hit)
-        if (!kAsync && prev) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
-        T wC[NV], sB[NV], wl[NV], wr[NV];
+        // stage input of the own cell, plane j-1 (read earlier: a cache hit; plane -1 is a ghost plane)
+        if (!kAsync) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
+        T wC[NV], sB[NV], wl[NV], wr[NV], xl[NV], xr[NV], yl[NV], yr[NV];
         if (kAsync) {
           const T* slot = CR + ((j + 1) & (kRing - 1)) * NV * kPlaneMax + me;
 #pragma unroll
@@ -313,81 +332,77 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           wl[v] = wA[v] + sc * sA[v];
           wr[v] = wB[v] - sc * sB[v];
           own[v] = wB[v];
+          W[v * kPlaneMax + me] = wB[v];
         }
-        if (cur) {
+        if (kMerge) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) W[v * kPlaneMax + me] = wB[v];
+          for (int v = 0; v < NV; ++v) {
+            xl[v] = XL[v * kStateMax + xs - 1];
+            xr[v] = XR[v * kStateMax + xs];
+            yl[v] = YL[v * kStateMax + ys - wx];
+            yr[v] = YR[v * kStateMax + ys];
+          }
         }
-        if (STAGE == 2 && prev && !kAsync) {
+        if (STAGE == 2 && !kAsync) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) un[v] = unN[v];
           load_cons<T, NV>(Ob, vs, col + (cur ? j : j - 1) * plane, unN);
         }
         riemann<T, NV, 2>(wl, wr, ph, Fzp);                  // face j-1/2
+        if (kMerge || prev) {
+          if (!kMerge) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { sA[v] = sB[v]; wA[v] = wB[v]; wB[v] = wC[v]; }
-      }
-      if (has_halo && cur) {
-        T w[NV];
-        if (kAsync) {
-          const T* slot = CR + (j & (kRing - 1)) * NV * kPlaneMax + hpos;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlaneMax];
-        }
-        cons_to_prim<T, NV>(hN, w);
-        if (!kAsync) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
-      }
-      if (prev) {
-        if (active) {
-          T wl[NV], wr[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            wl[v] = XL[v * kStateMax + xs - 1];
-            wr[v] = XR[v * kStateMax + xs];
+            for (int v = 0; v < NV; ++v) {
+              xl[v] = XL[v * kStateMax + xs - 1];
+              xr[v] = XR[v * kStateMax + xs];
+              yl[v] = YL[v * kStateMax + ys - wx];
+              yr[v] = YR[v * kStateMax + ys];
+            }
           }
-          riemann<T, NV, 0>(wl, wr, ph, Fx0);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            wl[v] = YL[v * kStateMax + ys - wx];
-            wr[v] = YR[v * kStateMax + ys];
-          }
-          riemann<T, NV, 1>(wl, wr, ph, Fy0);
+          riemann<T, NV, 0>(xl, xr, ph, Fx0);                // x face of plane j-1
+          riemann<T, NV, 1>(yl, yr, ph, Fy0);                // y face of plane j-1
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             FX[v * nfx + ty * (wx + 1) + tx] = Fx0[v];
             FY[v * nfy + ty * wx + tx] = Fy0[v];
           }
         }
-        if (eb < wy) {  // x face at the right edge of row eb
-          T wl[NV], wr[NV], F[NV];
-          const int sl = eb * (wx + 2) + wx;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            wl[v] = XL[v * kStateMax + sl];
-            wr[v] = XR[v * kStateMax + sl + 1];
-          }
-          riemann<T, NV, 0>(wl, wr, ph, F);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) FX[v * nfx + eb * (wx + 1) + wx] = F[v];
-        } else if (eb < wy + wx) {  // y face at the top edge of column eb - wy
-          const int c = eb - wy;
-          T wl[NV], wr[NV], F[NV];
-          const int sl = wy * wx + c;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            wl[v] = YL[v * kStateMax + sl];
-            wr[v] = YR[v * kStateMax + sl + wx];
-          }
-          riemann<T, NV, 1>(wl, wr, ph, F);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) FY[v * nfy + wy * wx + c] = F[v];
+        for (int v = 0; v < NV; ++v) {
+          sA[v] = sB[v];
+          wA[v] = wB[v];
+          wB[v] = wC[v];
         }
+      }
+      if (!(kMerge || prev)) {
+        // no x/y fluxes at j = 0
+      } else if (eb < wy) {  // x face at the right edge of row eb
+        T wl[NV], wr[NV], F[NV];
+        const int sl = eb * (wx + 2) + wx;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          wl[v] = XL[v * kStateMax + sl];
+          wr[v] = XR[v * kStateMax + sl + 1];
+        }
+        riemann<T, NV, 0>(wl, wr, ph, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) FX[v * nfx + eb * (wx + 1) + wx] = F[v];
+      } else if (eb < wy + wx) {  // y face at the top edge of column eb - wy
+        const int c = eb - wy;
+        T wl[NV], wr[NV], F[NV];
+        const int sl = wy * wx + c;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          wl[v] = YL[v * kStateMax + sl];
+          wr[v] = YR[v * kStateMax + sl + wx];
+        }
+        riemann<T, NV, 1>(wl, wr, ph, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) FY[v * nfy + wy * wx + c] = F[v];
       }
       __syncthreads();
       // ---- phase B ----
-      if (active && prev) {  // U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2, plane j-1
+      if (active && (kMerge || prev)) {  // U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2, plane j-1
         const int c = col + (j - 1) * plane;
         if (kAsync) {
           const T* slot = CR + ((j - 1) & (kRing - 1)) * NV * kPlaneMax + me;
@@ -405,46 +420,46 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           const T u2 = uin[v] - dtx * (FX[v * nfx + ty * (wx + 1) + tx + 1] - Fx0[v]) -
                        dty * (FY[v * nfy + (ty + 1) * wx + tx] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
           if (STAGE == 1) {
-            Ob[v * vs + c] = u2;
+            if (prev) Ob[v * vs + c] = u2;
           } else {
             un[v] = T(0.5) * un[v] + T(0.5) * u2;
-            Ob[v * vs + c] = un[v];
+            if (prev) Ob[v * vs + c] = un[v];
           }
         }
         if (STAGE == 2 && a.fuse_rate) {
           T r, sp;
           cell_rate<T, NV>(un, ph, (T)a.idx0, (T)a.idy0, (T)a.idz0, r, sp);
-          rate_max = dmax(rate_max, r);
-          speed_max = dmax(speed_max, sp);
+          if (prev) {
+            rate_max = dmax(rate_max, r);
+            speed_max = dmax(speed_max, sp);
+          }
         }
       }
       if (active) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) Fzm[v] = Fzp[v];
       }
-      if (cur) {
-        if (active) {
+      if (active && (kMerge || cur)) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const T* Wv = W + v * kPlaneMax + me;
-            const T w0 = own[v];
-            const T sx = limited_slope(Wv[-1], w0, Wv[1], ph.theta);
-            const T sy = limited_slope(Wv[-sw], w0, Wv[sw], ph.theta);
-            XL[v * kStateMax + xs] = w0 + sc * sx;
-            XR[v * kStateMax + xs] = w0 - sc * sx;
-            YL[v * kStateMax + ys] = w0 + sc * sy;
-            YR[v * kStateMax + ys] = w0 - sc * sy;
-          }
+        for (int v = 0; v < NV; ++v) {
+          const T* Wv = W + v * kPlaneMax + me;
+          const T w0 = own[v];
+          const T sx = limited_slope(Wv[-1], w0, Wv[1], ph.theta);
+          const T sy = limited_slope(Wv[-sw], w0, Wv[sw], ph.theta);
+          XL[v * kStateMax + xs] = w0 + sc * sx;
+          XR[v * kStateMax + xs] = w0 - sc * sx;
+          YL[v * kStateMax + ys] = w0 + sc * sy;
+          YR[v * kStateMax + ys] = w0 - sc * sy;
         }
-        if (bkind >= 0) {
-          T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
-          const T sgn = (bkind == 0 || bkind == 2) ? sc : -sc;
+      }
+      if (bkind >= 0 && (kMerge || cur)) {
+        T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
+        const T sgn = (bkind == 0 || bkind == 2) ? sc : -sc;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const T* Wv = W + v * kPlaneMax + bpos;
-            const T w0 = Wv[0];
-            dst[v * kStateMax + bslot] = w0 + sgn * limited_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
-          }
+        for (int v = 0; v < NV; ++v) {
+          const T* Wv = W + v * kPlaneMax + bpos;
+          const T w0 = Wv[0];
+          dst[v * kStateMax + bslot] = w0 + sgn * limited_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
         }
       }
       __syncthreads();
