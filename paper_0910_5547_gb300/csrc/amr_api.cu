@@ -61,6 +61,13 @@ struct DevLevel {
   const RegFace* regs = nullptr;
   const int* reflux_first = nullptr;
   double* R = nullptr;  // registers: [2][nvar][nreg]
+  // flattened boxes of the batched ghost copy, gather and prolongation launches
+  struct Flat {
+    const void* boxes = nullptr;
+    const int* first = nullptr;
+    const int* chunk_box = nullptr;
+    int nchunk = 0, total = 0;
+  } fghost, fgather, fprolong;
   int64_t arena_begin = 0, arena_end = 0;  // element range of the level's patches
 };
 
@@ -184,13 +191,27 @@ double level_dx(const amr_handle* h, int l, int d) { return h->dx0[d] / (double)
 cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha) {
   const DevLevel& L = h->dl[l];
   const LevelPlan& LP = h->plan.levels[l];
+  const bool batched = h->cfg.batched != 0;
   if (l > 0) {
     h->cur_class = AMR_T_PARENT;
-    LK(h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->Uold, alpha));
-    LK(h->ops->prolong(h->stream, L.prolong, L.nprolong, h->d_desc, h->tile, arr));
+    if (batched) {
+      const DevLevel::Flat& G = L.fgather;
+      const DevLevel::Flat& P = L.fprolong;
+      LK(h->ops->gather_flat(h->stream, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk,
+                             G.total, h->tile, h->U, h->Uold, alpha));
+      LK(h->ops->prolong_flat(h->stream, static_cast<const FlatProlong*>(P.boxes), P.first, P.chunk_box, P.nchunk,
+                              P.total, h->tile, arr));
+    } else {
+      LK(h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->Uold, alpha));
+      LK(h->ops->prolong(h->stream, L.prolong, L.nprolong, h->d_desc, h->tile, arr));
+    }
   }
   h->cur_class = AMR_T_GHOST;
-  if (h->cfg.batched || L.nghost == 0) {
+  if (batched) {
+    const DevLevel::Flat& G = L.fghost;
+    LK(h->ops->ghost_copy_flat(h->stream, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk,
+                               G.total, arr));
+  } else if (L.nghost == 0) {
     LK(h->ops->ghost_copy(h->stream, L.ghost, L.nghost, h->d_desc, arr));
   } else {
     for (int p = 0; p < LP.count; ++p) {
@@ -438,10 +459,15 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   std::vector<double> lvol(nlev);
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
   size_t o_lvol = put(buf, lvol);
-  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; };
+  struct FlatOffs { size_t boxes, first, chunk; };
+  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; FlatOffs fg, fa, fp; };
   std::vector<Offs> lo(nlev);
+  auto put_flat = [&](const auto& f) { return FlatOffs{put(buf, f.boxes), put(buf, f.first), put(buf, f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = pl.levels[l];
+    lo[l].fg = put_flat(L.fghost);
+    lo[l].fa = put_flat(L.fgather);
+    lo[l].fp = put_flat(L.fprolong);
     lo[l].ghost = put(buf, L.ghost);
     lo[l].prolong = put(buf, L.prolong);
     lo[l].gather = put(buf, L.gather);
@@ -496,6 +522,16 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
     D.reflux_first = reinterpret_cast<const int*>(h->tables + lo[l].rf);
     D.R = h->regs ? h->regs + reg_off[l] : nullptr;
+    auto set_flat = [&](DevLevel::Flat& F, const auto& f, const FlatOffs& o) {
+      F.boxes = h->tables + o.boxes;
+      F.first = reinterpret_cast<const int*>(h->tables + o.first);
+      F.chunk_box = reinterpret_cast<const int*>(h->tables + o.chunk);
+      F.nchunk = (int)f.chunk_box.size();
+      F.total = f.total;
+    };
+    set_flat(D.fghost, L.fghost, lo[l].fg);
+    set_flat(D.fgather, L.fgather, lo[l].fa);
+    set_flat(D.fprolong, L.fprolong, lo[l].fp);
     const PatchDesc& a = pl.desc[L.first];
     const PatchDesc& b = pl.desc[L.first + L.count - 1];
     D.arena_begin = a.off;

@@ -59,6 +59,40 @@ struct CopySeg {
   uint8_t pad;
 };
 
+// Batched box launches (ghost copies, parent-tile gathers, prolongation) run
+// over flattened boxes with precomputed strides: a CTA of kBoxThreads takes a
+// chunk of consecutive cells of the launch (several cells per thread), which
+// may span several boxes, so that small boxes do not leave CTAs idle.
+constexpr int kBoxThreads = 256;
+constexpr int kCopyPerThread = 4;
+constexpr int kCopyChunk = kBoxThreads * kCopyPerThread;
+constexpr int kProlongPerThread = 2;
+constexpr int kProlongChunk = kBoxThreads * kProlongPerThread;
+
+// Copy box: cell (a, b, c) of the box goes from src0 + a ssx + b ssy + c ssz
+// (variable stride svs; ssx/ssy/ssz = 0 on an axis held constant) to
+// dst0 + a + b dsy + c dsz (variable stride dvs).
+struct alignas(16) FlatCopy {
+  int64_t dst0, src0;
+  int dvs, svs;
+  int dsy, dsz;
+  int ssx, ssy, ssz;
+  int n0, n1;
+  int pad;
+};
+
+// Prolongation box: fine cell (a, b, c) at dst0 + a + b dsy + c dsz has the
+// global fine coordinate g = g0 + (a, b, c) and parent tile cell
+// (g >> 1) - cb, i.e. tile0 + cx + cy tsy + cz tsz (variable stride tvol).
+struct alignas(16) FlatProlong {
+  int64_t dst0, tile0;
+  int dvs, dsy, dsz;
+  int tvol, tsy, tsz;
+  int g0[3];
+  int cb[3];
+  int n0, n1;
+};
+
 // Box of fine ghost cells filled by prolongation from the parent tile.
 struct ProlongBox {
   int patch;

@@ -366,6 +366,94 @@ void build_items(Plan& plan, const TileParams& tp) {
   }
 }
 
+namespace {
+
+template <class B>
+void finish_flat(FlatList<B>& f, const std::vector<int>& cells, int chunk) {
+  f.first.assign(cells.size() + 1, 0);
+  for (size_t i = 0; i < cells.size(); ++i) f.first[i + 1] = f.first[i] + cells[i];
+  f.total = f.first.back();
+  const int nch = (f.total + chunk - 1) / chunk;
+  f.chunk_box.assign(nch, 0);
+  size_t b = 0;
+  for (int k = 0; k < nch; ++k) {
+    const int e = k * chunk;
+    while (f.first[b + 1] <= e) ++b;
+    f.chunk_box[k] = (int)b;
+  }
+}
+
+// Copy boxes with the source mapping of CopySeg folded into strides: per axis
+// the source coordinate is dlo + i + sh (translate) or sh (constant).
+void flatten_copies(const Plan& plan, const std::vector<CopySeg>& segs, bool gather, FlatList<FlatCopy>& f) {
+  f = FlatList<FlatCopy>();
+  std::vector<int> cells;
+  for (const CopySeg& g : segs) {
+    const PatchDesc& D = plan.desc[g.dst_patch];
+    const PatchDesc& S = plan.desc[g.src_patch];
+    FlatCopy c{};
+    int s0[3];
+    for (int d = 0; d < 3; ++d) s0[d] = g.mode[d] ? g.sh[d] : g.dlo[d] + g.sh[d];
+    c.src0 = S.off + ((int64_t)(s0[2] + kGhost) * S.m1 + (s0[1] + kGhost)) * S.pitch + (s0[0] + kGhost);
+    c.svs = (int)S.vstride;
+    c.ssx = g.mode[0] ? 0 : 1;
+    c.ssy = g.mode[1] ? 0 : S.pitch;
+    c.ssz = g.mode[2] ? 0 : S.pitch * S.m1;
+    if (gather) {
+      c.dst0 = D.tile_off + ((int64_t)g.dlo[2] * D.tn[1] + g.dlo[1]) * D.tn[0] + g.dlo[0];
+      c.dvs = D.tn[0] * D.tn[1] * D.tn[2];
+      c.dsy = D.tn[0];
+      c.dsz = D.tn[0] * D.tn[1];
+    } else {
+      c.dst0 = D.off + ((int64_t)(g.dlo[2] + kGhost) * D.m1 + (g.dlo[1] + kGhost)) * D.pitch + (g.dlo[0] + kGhost);
+      c.dvs = (int)D.vstride;
+      c.dsy = D.pitch;
+      c.dsz = D.pitch * D.m1;
+    }
+    c.n0 = g.dn[0];
+    c.n1 = g.dn[1];
+    f.boxes.push_back(c);
+    cells.push_back(g.dn[0] * g.dn[1] * g.dn[2]);
+  }
+  finish_flat(f, cells, kCopyChunk);
+}
+
+void flatten_prolong(const Plan& plan, const std::vector<ProlongBox>& boxes, FlatList<FlatProlong>& f) {
+  f = FlatList<FlatProlong>();
+  std::vector<int> cells;
+  for (const ProlongBox& b : boxes) {
+    const PatchDesc& D = plan.desc[b.patch];
+    FlatProlong c{};
+    c.dst0 = D.off + cell_index(D, b.lo[0], b.lo[1], b.lo[2]);
+    c.tile0 = D.tile_off;
+    c.dvs = (int)D.vstride;
+    c.dsy = D.pitch;
+    c.dsz = D.pitch * D.m1;
+    c.tvol = D.tn[0] * D.tn[1] * D.tn[2];
+    c.tsy = D.tn[0];
+    c.tsz = D.tn[0] * D.tn[1];
+    for (int d = 0; d < 3; ++d) {
+      c.g0[d] = D.lo[d] + b.lo[d];
+      c.cb[d] = (D.lo[d] >> 1) - 2;
+    }
+    c.n0 = b.n[0];
+    c.n1 = b.n[1];
+    f.boxes.push_back(c);
+    cells.push_back(b.n[0] * b.n[1] * b.n[2]);
+  }
+  finish_flat(f, cells, kProlongChunk);
+}
+
+}  // namespace
+
+void build_flat(Plan& plan) {
+  for (LevelPlan& L : plan.levels) {
+    flatten_copies(plan, L.ghost, false, L.fghost);
+    flatten_copies(plan, L.gather, true, L.fgather);
+    flatten_prolong(plan, L.prolong, L.fprolong);
+  }
+}
+
 amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan, std::string& msg,
                       const TileParams& tp) {
   amr_status st = validate_patches(cfg, P, msg);
@@ -734,6 +822,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     }
     L.reflux_first.push_back((int)regs.size());
   }
+  build_flat(plan);
   return AMR_OK;
 }
 

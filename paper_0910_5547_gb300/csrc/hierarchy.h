@@ -18,6 +18,16 @@ struct HPatch {
   int n[3];
 };
 
+// Flattened boxes of one batched launch: prefix sums of their cell counts and,
+// per chunk of `chunk` cells, the box holding the chunk's first cell.
+template <class B>
+struct FlatList {
+  std::vector<B> boxes;
+  std::vector<int> first;      // size boxes + 1
+  std::vector<int> chunk_box;  // size ceil(total / chunk)
+  int total = 0;
+};
+
 struct LevelPlan {
   int first = 0, count = 0;                  // patch range [first, first + count)
   std::vector<StageItem> items;              // stage work items, grouped by patch
@@ -31,6 +41,8 @@ struct LevelPlan {
   std::vector<RestrictSeg> restrict_segs;    // this level -> parent (level >= 1)
   std::vector<RegFace> regs;                 // coarse-fine faces of this level (level >= 1), sorted by coarse cell
   std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell
+  FlatList<FlatCopy> fghost, fgather;        // the ghost and gather boxes, flattened (batched launches)
+  FlatList<FlatProlong> fprolong;            // the prolongation boxes, flattened
   int64_t cells = 0;
 };
 
@@ -87,6 +99,10 @@ struct RegridFill {
 };
 void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch>& newp, int keep_level,
                        RegridFill& fill);
+
+// Flattened box lists of every level (FlatList) from its ghost, gather and
+// prolongation boxes; build_plan calls it.
+void build_flat(Plan& plan);
 
 // Rebuild only the stage work items of `plan` with another tile shape.
 void build_items(Plan& plan, const TileParams& tp);

@@ -483,6 +483,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 // ghost fill and parent-tile gather
 // ---------------------------------------------------------------------------
 
+// Parent data at fraction alpha of the parent step: (1 - alpha) U_old + alpha U,
+// with one fixed rounding order for every kernel that forms it.
+template <typename T>
+__device__ __forceinline__ T time_lerp(T u_old, T u, T alpha) {
+  return fma(alpha, u, (T(1) - alpha) * u_old);
+}
+
 // One CTA per box: dst cell (a, b, c) = dlo + (i, j, k) takes the src cell whose
 // local coordinate per axis is (dst + sh) (translate) or sh (constant).
 template <typename T, int NV, bool GATHER>
@@ -510,7 +517,7 @@ __global__ void copy_kernel(const CopySeg* segs, int nseg, const PatchDesc* desc
         const int tvol = D.tn[0] * D.tn[1] * D.tn[2];
         T* Tb = dst_arena + D.tile_off + (dc * D.tn[1] + db) * D.tn[0] + da;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Tb[v * tvol] = (T(1) - alpha) * Ob[si + v * svs] + alpha * Sb[si + v * svs];
+        for (int v = 0; v < NV; ++v) Tb[v * tvol] = time_lerp(Ob[si + v * svs], Sb[si + v * svs], alpha);
       } else {
         T* Db = dst_arena + D.off + ((dc + kGhost) * D.m1 + (db + kGhost)) * D.pitch + (da + kGhost);
         const int dvs = (int)D.vstride;
@@ -550,7 +557,8 @@ __global__ void prolong_kernel(const ProlongBox* boxes, int nbox, const PatchDes
       const int c2 = (g2 >> 1) - (D.lo[2] >> 1) + 2;
       const int64_t ci = ((int64_t)c2 * D.tn[1] + c1) * D.tn[0] + c0;
       const int64_t st[3] = {1, (int64_t)D.tn[0], (int64_t)D.tn[0] * D.tn[1]};
-      const T sg[3] = {(g0 & 1) ? T(1) : T(-1), (g1 & 1) ? T(1) : T(-1), (g2 & 1) ? T(1) : T(-1)};
+      const T sg[3] = {(g0 & 1) ? T(0.25) : T(-0.25), (g1 & 1) ? T(0.25) : T(-0.25),
+                       (g2 & 1) ? T(0.25) : T(-0.25)};
       const int64_t di = D.off + cell_index(D, li, lj, lk);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -560,10 +568,105 @@ __global__ void prolong_kernel(const ProlongBox* boxes, int nbox, const PatchDes
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const T up = tv[ci + st[d]], um = tv[ci - st[d]];
-          const T sl = minmod2(up - uc, uc - um);
-          val = val + sg[d] * T(0.25) * sl;
+          val = fma(sg[d], minmod2(up - uc, uc - um), val);
         }
         dst_arena[di + v * D.vstride] = val;
+      }
+    }
+  }
+}
+
+// Batched ghost copy (GATHER = false) or parent-tile gather with time
+// interpolation (GATHER = true) over flattened boxes: CTA k takes cells
+// [k kCopyChunk, (k+1) kCopyChunk) of the launch, kCopyPerThread per thread,
+// all loads issued before the stores.  Same values as copy_kernel.
+template <typename T, int NV, bool GATHER>
+__global__ void __launch_bounds__(kBoxThreads) box_copy_kernel(const FlatCopy* boxes, const int* first,
+                                                               const int* chunk_box, int nchunk, int total, T* dst,
+                                                               const T* src, const T* old, T alpha) {
+  for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
+    int b = chunk_box[k];
+    T val[kCopyPerThread][NV];
+    int64_t di[kCopyPerThread];
+    int dvs[kCopyPerThread];
+#pragma unroll
+    for (int i = 0; i < kCopyPerThread; ++i) {
+      const int e = k * kCopyChunk + i * kBoxThreads + (int)threadIdx.x;
+      di[i] = -1;
+      if (e < total) {
+        while (first[b + 1] <= e) ++b;
+        const FlatCopy g = boxes[b];
+        const int q = e - first[b];
+        const int r = q / g.n0, a = q - r * g.n0;
+        const int c = r / g.n1, y = r - c * g.n1;
+        const int64_t so = g.src0 + (int64_t)a * g.ssx + (int64_t)y * g.ssy + (int64_t)c * g.ssz;
+        di[i] = g.dst0 + a + (int64_t)y * g.dsy + (int64_t)c * g.dsz;
+        dvs[i] = g.dvs;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int64_t sv = so + (int64_t)v * g.svs;
+          val[i][v] = GATHER ? time_lerp(old[sv], src[sv], alpha) : src[sv];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kCopyPerThread; ++i) {
+      if (di[i] >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dst[di[i] + (int64_t)v * dvs[i]] = val[i][v];
+      }
+    }
+  }
+}
+
+// Batched prolongation over flattened boxes (chunks of kProlongChunk cells);
+// same values as prolong_kernel.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kBoxThreads) box_prolong_kernel(const FlatProlong* boxes, const int* first,
+                                                                  const int* chunk_box, int nchunk, int total,
+                                                                  const T* tile, T* dst) {
+  for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
+    int b = chunk_box[k];
+    T val[kProlongPerThread][NV];
+    int64_t di[kProlongPerThread];
+    int dvs[kProlongPerThread];
+#pragma unroll
+    for (int i = 0; i < kProlongPerThread; ++i) {
+      const int e = k * kProlongChunk + i * kBoxThreads + (int)threadIdx.x;
+      di[i] = -1;
+      if (e < total) {
+        while (first[b + 1] <= e) ++b;
+        const FlatProlong g = boxes[b];
+        const int q = e - first[b];
+        const int r = q / g.n0, a = q - r * g.n0;
+        const int c = r / g.n1, y = r - c * g.n1;
+        const int gx = g.g0[0] + a, gy = g.g0[1] + y, gz = g.g0[2] + c;
+        const int64_t ci = g.tile0 + ((gx >> 1) - g.cb[0]) + (int64_t)((gy >> 1) - g.cb[1]) * g.tsy +
+                           (int64_t)((gz >> 1) - g.cb[2]) * g.tsz;
+        const int st[3] = {1, g.tsy, g.tsz};
+        const T sg[3] = {(gx & 1) ? T(0.25) : T(-0.25), (gy & 1) ? T(0.25) : T(-0.25),
+                         (gz & 1) ? T(0.25) : T(-0.25)};
+        di[i] = g.dst0 + a + (int64_t)y * g.dsy + (int64_t)c * g.dsz;
+        dvs[i] = g.dvs;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* tv = tile + ci + (int64_t)v * g.tvol;
+          const T uc = tv[0];
+          T u = uc;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const T up = tv[st[d]], um = tv[-st[d]];
+            u = fma(sg[d], minmod2(up - uc, uc - um), u);
+          }
+          val[i][v] = u;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kProlongPerThread; ++i) {
+      if (di[i] >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dst[di[i] + (int64_t)v * dvs[i]] = val[i][v];
       }
     }
   }

@@ -32,6 +32,14 @@ struct OpsBase {
   // threads per stage CTA: 256 (default) or 128 (same registers per thread, twice the CTAs)
   virtual void set_stage_threads(int nt) = 0;
   virtual cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) = 0;
+  // batched forms over flattened boxes (same values as ghost_copy / gather / prolong)
+  virtual cudaError_t ghost_copy_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box,
+                                      int nchunk, int total, void* arena) = 0;
+  virtual cudaError_t gather_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box,
+                                  int nchunk, int total, void* tile, const void* U, const void* Uold,
+                                  double alpha) = 0;
+  virtual cudaError_t prolong_flat(cudaStream_t s, const FlatProlong* boxes, const int* first, const int* chunk_box,
+                                   int nchunk, int total, const void* tile, void* arena) = 0;
   virtual cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,
                              const void* U, const void* Uold, double alpha) = 0;
   virtual cudaError_t prolong(cudaStream_t s, const ProlongBox* boxes, int nbox, const PatchDesc* desc,

@@ -93,6 +93,31 @@ struct Ops final : OpsBase {
     return cudaGetLastError();
   }
 
+  cudaError_t ghost_copy_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box,
+                              int nchunk, int total, void* arena) override {
+    if (nchunk <= 0) return cudaSuccess;
+    box_copy_kernel<T, NV, false><<<grid_for(nchunk), kBoxThreads, 0, s>>>(
+        boxes, first, chunk_box, nchunk, total, static_cast<T*>(arena), static_cast<const T*>(arena), nullptr, T(0));
+    return cudaGetLastError();
+  }
+
+  cudaError_t gather_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box, int nchunk,
+                          int total, void* tile, const void* U, const void* Uold, double alpha) override {
+    if (nchunk <= 0) return cudaSuccess;
+    box_copy_kernel<T, NV, true><<<grid_for(nchunk), kBoxThreads, 0, s>>>(
+        boxes, first, chunk_box, nchunk, total, static_cast<T*>(tile), static_cast<const T*>(U),
+        static_cast<const T*>(Uold), (T)alpha);
+    return cudaGetLastError();
+  }
+
+  cudaError_t prolong_flat(cudaStream_t s, const FlatProlong* boxes, const int* first, const int* chunk_box,
+                           int nchunk, int total, const void* tile, void* arena) override {
+    if (nchunk <= 0) return cudaSuccess;
+    box_prolong_kernel<T, NV><<<grid_for(nchunk), kBoxThreads, 0, s>>>(
+        boxes, first, chunk_box, nchunk, total, static_cast<const T*>(tile), static_cast<T*>(arena));
+    return cudaGetLastError();
+  }
+
   cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,
                      const void* U, const void* Uold, double alpha) override {
     if (nseg <= 0) return cudaSuccess;
