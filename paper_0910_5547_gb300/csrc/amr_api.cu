@@ -67,7 +67,7 @@ struct DevLevel {
     const int* first = nullptr;
     const int* chunk_box = nullptr;
     int nchunk = 0, total = 0;
-  } fghost, fgather, fprolong;
+  } fghost, fgather, fprolong, frestrict;
   int64_t arena_begin = 0, arena_end = 0;  // element range of the level's patches
 };
 
@@ -272,7 +272,13 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
     if ((e = advance(h, l + 1, 0.5)) != cudaSuccess) return e;
     DevLevel& K = h->dl[l + 1];
     h->cur_class = AMR_T_SYNC;
-    LK(h->ops->restrict_(h->stream, K.restrict_segs, K.nrestrict, h->d_desc, h->U));
+    if (h->cfg.batched) {
+      const DevLevel::Flat& R = K.frestrict;
+      LK(h->ops->restrict_flat(h->stream, static_cast<const FlatCopy*>(R.boxes), R.first, R.chunk_box, R.nchunk,
+                               R.total, h->U));
+    } else {
+      LK(h->ops->restrict_(h->stream, K.restrict_segs, K.nrestrict, h->d_desc, h->U));
+    }
     double dxc[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
     if (K.nuniq) LK(h->ops->reflux(h->stream, K.regs, K.reflux_first, K.nuniq, K.nreg, h->d_desc, K.R, h->U, dxc));
   }
@@ -460,7 +466,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
   size_t o_lvol = put(buf, lvol);
   struct FlatOffs { size_t boxes, first, chunk; };
-  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; FlatOffs fg, fa, fp; };
+  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
   std::vector<Offs> lo(nlev);
   auto put_flat = [&](const auto& f) { return FlatOffs{put(buf, f.boxes), put(buf, f.first), put(buf, f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
@@ -468,6 +474,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     lo[l].fg = put_flat(L.fghost);
     lo[l].fa = put_flat(L.fgather);
     lo[l].fp = put_flat(L.fprolong);
+    lo[l].fr = put_flat(L.frestrict);
     lo[l].ghost = put(buf, L.ghost);
     lo[l].prolong = put(buf, L.prolong);
     lo[l].gather = put(buf, L.gather);
@@ -532,6 +539,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     set_flat(D.fghost, L.fghost, lo[l].fg);
     set_flat(D.fgather, L.fgather, lo[l].fa);
     set_flat(D.fprolong, L.fprolong, lo[l].fp);
+    set_flat(D.frestrict, L.frestrict, lo[l].fr);
     const PatchDesc& a = pl.desc[L.first];
     const PatchDesc& b = pl.desc[L.first + L.count - 1];
     D.arena_begin = a.off;

@@ -68,10 +68,14 @@ constexpr int kCopyPerThread = 4;
 constexpr int kCopyChunk = kBoxThreads * kCopyPerThread;
 constexpr int kProlongPerThread = 2;
 constexpr int kProlongChunk = kBoxThreads * kProlongPerThread;
+constexpr int kRestrictPerThread = 2;
+constexpr int kRestrictChunk = kBoxThreads * kRestrictPerThread;
 
 // Copy box: cell (a, b, c) of the box goes from src0 + a ssx + b ssy + c ssz
 // (variable stride svs; ssx/ssy/ssz = 0 on an axis held constant) to
-// dst0 + a + b dsy + c dsz (variable stride dvs).
+// dst0 + a + b dsy + c dsz (variable stride dvs).  A restriction box uses the
+// same record: coarse cell (a, b, c) at dst0 + a + b dsy + c dsz averages the
+// fine cells src0 + (2a + i) + (2b + j) ssy + (2c + k) ssz, i, j, k in {0, 1}.
 struct alignas(16) FlatCopy {
   int64_t dst0, src0;
   int dvs, svs;

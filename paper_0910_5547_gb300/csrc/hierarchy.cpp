@@ -444,6 +444,32 @@ void flatten_prolong(const Plan& plan, const std::vector<ProlongBox>& boxes, Fla
   finish_flat(f, cells, kProlongChunk);
 }
 
+void flatten_restrict(const Plan& plan, const std::vector<RestrictSeg>& segs, FlatList<FlatCopy>& f) {
+  f = FlatList<FlatCopy>();
+  std::vector<int> cells;
+  for (const RestrictSeg& r : segs) {
+    const PatchDesc& C = plan.desc[r.coarse];
+    const PatchDesc& F = plan.desc[r.fine];
+    FlatCopy c{};
+    int f0[3];
+    for (int d = 0; d < 3; ++d) f0[d] = 2 * (C.lo[d] + r.clo[d]) - F.lo[d];
+    c.dst0 = C.off + cell_index(C, r.clo[0], r.clo[1], r.clo[2]);
+    c.dvs = (int)C.vstride;
+    c.dsy = C.pitch;
+    c.dsz = C.pitch * C.m1;
+    c.src0 = F.off + cell_index(F, f0[0], f0[1], f0[2]);
+    c.svs = (int)F.vstride;
+    c.ssx = 1;
+    c.ssy = F.pitch;
+    c.ssz = F.pitch * F.m1;
+    c.n0 = r.cn[0];
+    c.n1 = r.cn[1];
+    f.boxes.push_back(c);
+    cells.push_back(r.cn[0] * r.cn[1] * r.cn[2]);
+  }
+  finish_flat(f, cells, kRestrictChunk);
+}
+
 }  // namespace
 
 void build_flat(Plan& plan) {
@@ -451,6 +477,7 @@ void build_flat(Plan& plan) {
     flatten_copies(plan, L.ghost, false, L.fghost);
     flatten_copies(plan, L.gather, true, L.fgather);
     flatten_prolong(plan, L.prolong, L.fprolong);
+    flatten_restrict(plan, L.restrict_segs, L.frestrict);
   }
 }
 

@@ -43,6 +43,7 @@ struct LevelPlan {
   std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell
   FlatList<FlatCopy> fghost, fgather;        // the ghost and gather boxes, flattened (batched launches)
   FlatList<FlatProlong> fprolong;            // the prolongation boxes, flattened
+  FlatList<FlatCopy> frestrict;              // the restriction boxes (this level -> parent), flattened
   int64_t cells = 0;
 };
 

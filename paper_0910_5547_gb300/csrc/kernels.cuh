@@ -708,6 +708,57 @@ __global__ void restrict_kernel(const RestrictSeg* segs, int nseg, const PatchDe
   }
 }
 
+// Batched restriction over flattened boxes (chunks of kRestrictChunk coarse
+// cells); same pairwise sums as restrict_kernel.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kBoxThreads) box_restrict_kernel(const FlatCopy* boxes, const int* first,
+                                                                   const int* chunk_box, int nchunk, int total, T* U) {
+  for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
+    int b = chunk_box[k];
+    T val[kRestrictPerThread][NV];
+    int64_t di[kRestrictPerThread];
+    int dvs[kRestrictPerThread];
+#pragma unroll
+    for (int i = 0; i < kRestrictPerThread; ++i) {
+      const int e = k * kRestrictChunk + i * kBoxThreads + (int)threadIdx.x;
+      di[i] = -1;
+      if (e < total) {
+        while (first[b + 1] <= e) ++b;
+        const FlatCopy g = boxes[b];
+        const int q = e - first[b];
+        const int r = q / g.n0, a = q - r * g.n0;
+        const int c = r / g.n1, y = r - c * g.n1;
+        const int64_t f = g.src0 + 2 * a + (int64_t)(2 * y) * g.ssy + (int64_t)(2 * c) * g.ssz;
+        di[i] = g.dst0 + a + (int64_t)y * g.dsy + (int64_t)c * g.dsz;
+        dvs[i] = g.dvs;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* Y = U + f + (int64_t)v * g.svs;
+          T zs[2];
+#pragma unroll
+          for (int dz = 0; dz < 2; ++dz) {
+            T ys[2];
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+              const T* row = Y + (int64_t)dy * g.ssy + (int64_t)dz * g.ssz;
+              ys[dy] = row[0] + row[1];
+            }
+            zs[dz] = ys[0] + ys[1];
+          }
+          val[i][v] = T(0.125) * (zs[0] + zs[1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kRestrictPerThread; ++i) {
+      if (di[i] >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[di[i] + (int64_t)v * dvs[i]] = val[i][v];
+      }
+    }
+  }
+}
+
 template <typename T, int NV>
 __device__ __forceinline__ void face_flux_dir(const T* base, const PatchDesc& P, int i, int j, int k, int d,
                                               const Phys<T>& ph, T* F) {

@@ -38,6 +38,8 @@ struct OpsBase {
   virtual cudaError_t gather_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box,
                                   int nchunk, int total, void* tile, const void* U, const void* Uold,
                                   double alpha) = 0;
+  virtual cudaError_t restrict_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box,
+                                    int nchunk, int total, void* U) = 0;
   virtual cudaError_t prolong_flat(cudaStream_t s, const FlatProlong* boxes, const int* first, const int* chunk_box,
                                    int nchunk, int total, const void* tile, void* arena) = 0;
   virtual cudaError_t gather(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* tile,

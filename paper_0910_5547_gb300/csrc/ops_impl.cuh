@@ -110,6 +110,14 @@ struct Ops final : OpsBase {
     return cudaGetLastError();
   }
 
+  cudaError_t restrict_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box, int nchunk,
+                            int total, void* U) override {
+    if (nchunk <= 0) return cudaSuccess;
+    box_restrict_kernel<T, NV><<<grid_for(nchunk), kBoxThreads, 0, s>>>(boxes, first, chunk_box, nchunk, total,
+                                                                         static_cast<T*>(U));
+    return cudaGetLastError();
+  }
+
   cudaError_t prolong_flat(cudaStream_t s, const FlatProlong* boxes, const int* first, const int* chunk_box,
                            int nchunk, int total, const void* tile, void* arena) override {
     if (nchunk <= 0) return cudaSuccess;
