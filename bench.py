@@ -372,12 +372,15 @@ def main():
         so.step(0.0)
         so.regrid(threshold=0.3, buffer=4, block=4, max_patch=32)
         tot_cu, t_steps, t_regrid, counts = 0, 0.0, 0.0, []
+        phases_s = {k: 0.0 for k in NV.REGRID_PHASES}
         for _ in range(4):
             cu = sum((p.n[0] * p.n[1] * p.n[2]) << p.level for p in so.patches)
             t_steps += timed_steps(torch, so, stream, 1)
             t0 = time.perf_counter()
             so.regrid(threshold=0.3, buffer=4, block=4, max_patch=32)
             t_regrid += time.perf_counter() - t0
+            for k, v in NV.amr_get_regrid_timing(so.h).items():
+                phases_s[k] += v
             tot_cu += cu
             counts.append([len(so.patches), 1 + max(p.level for p in so.patches)])
         so.check()
@@ -385,7 +388,8 @@ def main():
         extra["adaptive_blast_clumps"] = {
             "value": ws * tot_cu / max_over_ranks(t_steps), "value_with_regrid": ws * tot_cu / max_over_ranks(
                 t_steps + t_regrid), "unit": UNIT, "coarse_steps": 4, "cell_updates": tot_cu,
-            "regrid_s": t_regrid, "patches_levels_after_each_regrid": counts,
+            "regrid_s": t_regrid, "regrid_phases_s": {k: round(v, 4) for k, v in phases_s.items()},
+            "patches_levels_after_each_regrid": counts,
             "workload": "blast in a log-normal clump field (sigma 1), base 64^3 + 5 levels, FP32 batched, "
                         "density-gradient regrid (threshold 0.3) after every coarse step"}
     if "mhd" in phases:

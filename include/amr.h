@@ -130,6 +130,20 @@ typedef struct {
  * invalidates the step graphs. */
 amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_out);
 
+/* Host wall-clock phases of the last amr_regrid on this handle (seconds). */
+enum {
+  AMR_RG_FLAG = 0,      /* ghost refresh, GPU flag kernel, flag download */
+  AMR_RG_CLUSTER = 1,   /* host clustering into the new patches */
+  AMR_RG_PLAN = 2,      /* host launch tables of the new hierarchy */
+  AMR_RG_FILLTAB = 3,   /* host tables that fill the new hierarchy from the old one */
+  AMR_RG_INSTALL = 4,   /* device allocation and table upload */
+  AMR_RG_FILL = 5,      /* GPU fill of the new state (copies, prolongation), synchronised */
+  AMR_RG_NPHASE = 6
+};
+/* sec[0 .. n-1] receives the phases (n <= AMR_RG_NPHASE); zeros before the
+ * first regrid.  No GPU work. */
+amr_status amr_get_regrid_timing(const amr_handle* h, double* sec, int n);
+
 /* Autotuner: time the stage kernel over the installed hierarchy for each
  * candidate work-item shape (x width, columns per CTA, z chunk) and register
  * budget (2 or 3 resident CTAs per SM for FP32 Euler) and keep the fastest for

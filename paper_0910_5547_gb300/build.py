@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
         jobs.append((cmd, obj))
     for src in HOST_UNITS:
         obj = os.path.join(BUILD, src.replace(".cpp", ".o"))
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", CSRC, "-I", INCLUDE, "-c", os.path.join(CSRC, src),
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", CSRC, "-I", INCLUDE, "-c", os.path.join(CSRC, src),
                "-o", obj]
         jobs.append((cmd, obj))
 
@@ -84,7 +84,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
             if verbose and log.strip():
                 print(log, file=sys.stderr)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)

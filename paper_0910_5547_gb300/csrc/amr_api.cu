@@ -6,6 +6,7 @@
 // graph and replayed.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -75,6 +76,7 @@ struct DevLevel {
 
 struct amr_handle {
   amr_config cfg{};
+  double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the last regrid
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   OpsBase* ops = nullptr;
@@ -688,9 +690,23 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   return read_bad(h);
 }
 
+amr_status amr_get_regrid_timing(const amr_handle* h, double* sec, int n) {
+  if (!h || !sec || n < 1 || n > AMR_RG_NPHASE) return AMR_ERR_ARG;
+  for (int i = 0; i < n; ++i) sec[i] = h->regrid_sec[i];
+  return AMR_OK;
+}
+
 amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_out) {
   if (!h) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  using clk = std::chrono::steady_clock;
+  auto t_mark = clk::now();
+  auto lap = [&](int phase) {
+    const auto t = clk::now();
+    h->regrid_sec[phase] = std::chrono::duration<double>(t - t_mark).count();
+    t_mark = t;
+  };
+  for (double& x : h->regrid_sec) x = 0.0;
   RegridParams rp;
   if (prm) {
     rp.threshold = prm->threshold;
@@ -730,16 +746,20 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
     const size_t o = (size_t)(op.packed_off[i] / nv);
     flags[i].assign(hflags.begin() + o, hflags.begin() + o + n);
   }
+  lap(AMR_RG_FLAG);
   // 3. cluster on the host, build the new hierarchy
   std::vector<HPatch> newp;
   std::string msg;
   amr_status st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
   if (st != AMR_OK) return fail(h, st, msg);
+  lap(AMR_RG_CLUSTER);
   Plan np;
   st = build_plan(h->cfg, newp, np, msg, h->tp);
   if (st != AMR_OK) return fail(h, st, "regrid produced an invalid hierarchy: " + msg);
+  lap(AMR_RG_PLAN);
   RegridFill fill;
   build_regrid_fill(op.patches, newp, rp.min_level, fill);
+  lap(AMR_RG_FILLTAB);
   // 4. new device state, filled from the old one
   const PatchDesc* old_desc = h->d_desc;
   const std::vector<HPatch> oldp = op.patches;
@@ -754,6 +774,12 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
   }
   std::vector<unsigned char> buf;
   std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
+  cudaError_t ei = cudaStreamSynchronize(h->stream);   // uploads of the new tables done
+  if (ei != cudaSuccess) {
+    free_bufs(old);
+    CK(ei);
+  }
+  lap(AMR_RG_INSTALL);
   for (size_t l = 0; l < fill.copy.size(); ++l) {
     o_copy[l] = put(buf, fill.copy[l]);
     o_fresh[l] = put(buf, fill.fresh[l]);
@@ -782,6 +808,7 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
   cudaFree(d_fill);
   free_bufs(old);
   CK(e);
+  lap(AMR_RG_FILL);
   h->ready = true;
   if (npatch_out) *npatch_out = (int)h->plan.patches.size();
   return AMR_OK;

@@ -10,6 +10,10 @@
 #include <set>
 #include <tuple>
 #include <memory>
+#include <array>
+#include <thread>
+#include <atomic>
+#include <climits>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -61,54 +65,117 @@ std::vector<std::pair<int, int>> wrap_interval(const amr_config& c, int l, int d
 // Decompose the cells with mask == 0 of an A x B grid into rectangles
 // (row runs merged across consecutive rows with identical extent).
 struct Rect { int a0, na, b0, nb; };
-std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) {
+std::vector<Rect> mask_rects(const unsigned char* m, int A, int B) {
   std::vector<Rect> done;
-  std::map<std::pair<int, int>, int> open;  // (a0, na) -> index into done
+  // runs of the previous row that are still open: (a0, na, index into done)
+  std::vector<std::array<int, 3>> open, next;
   for (int b = 0; b < B; ++b) {
-    std::map<std::pair<int, int>, int> next;
+    next.clear();
+    size_t oi = 0;   // open runs are in increasing a0 order, like the runs of this row
     int a = 0;
     while (a < A) {
       if (m[(size_t)b * A + a]) { ++a; continue; }
       int s = a;
       while (a < A && !m[(size_t)b * A + a]) ++a;
-      auto key = std::make_pair(s, a - s);
-      auto it = open.find(key);
-      if (it != open.end()) {
-        done[it->second].nb += 1;
-        next[key] = it->second;
+      while (oi < open.size() && open[oi][0] < s) ++oi;
+      if (oi < open.size() && open[oi][0] == s && open[oi][1] == a - s) {
+        done[open[oi][2]].nb += 1;
+        next.push_back(open[oi]);
       } else {
         done.push_back({s, a - s, b, 1});
-        next[key] = (int)done.size() - 1;
+        next.push_back({s, a - s, (int)done.size() - 1});
       }
     }
     open.swap(next);
   }
   return done;
 }
+std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) { return mask_rects(m.data(), A, B); }
+
+// f(i) for i in [0, n) on the host's cores (chunks of 8 indices per grab);
+// every caller writes only to slot i of its outputs, so the result does not
+// depend on the thread count.
+template <class F>
+void parallel_for(int n, F&& f) {
+  const int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u);
+  if (n < 64 || nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (;;) {
+      const int i0 = next.fetch_add(8);
+      if (i0 >= n) break;
+      const int i1 = std::min(i0 + 8, n);
+      for (int i = i0; i < i1; ++i) f(i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < std::min(nt, (n + 7) / 8); ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+}
 
 // Bucket index of the patches of one level: a query returns the patches whose
-// box may intersect a box (each patch listed once), so neighbour searches cost
-// O(neighbours) instead of O(patches).
+// box intersects a box (each patch listed once, ascending), so neighbour
+// searches cost O(neighbours) instead of O(patches).  Buckets form a dense
+// grid over the patches' bounding box (cells of edge bs_, bs_ doubled until
+// the grid has at most 4M buckets), stored as CSR.
 class PatchIndex {
  public:
   PatchIndex(const std::vector<HPatch>& P, int first, int count, int bs = 32) : P_(P), bs_(bs) {
-    for (int i = first; i < first + count; ++i) {
-      const HPatch& p = P[i];
+    if (count <= 0) {
+      for (int d = 0; d < 3; ++d) { g0_[d] = 0; gn_[d] = 1; }
+      start_.assign(2, 0);
+      return;
+    }
+    int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int i = first; i < first + count; ++i)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], P[i].lo[d]);
+        hi[d] = std::max(hi[d], P[i].lo[d] + P[i].n[d]);
+      }
+    for (;;) {
+      int64_t nbk = 1;
+      for (int d = 0; d < 3; ++d) {
+        g0_[d] = fl(lo[d]);
+        gn_[d] = fl(hi[d] - 1) - g0_[d] + 1;
+        nbk *= gn_[d];
+      }
+      if (nbk <= (int64_t)1 << 22) break;
+      bs_ *= 2;
+    }
+    const size_t nbk = (size_t)gn_[0] * gn_[1] * gn_[2];
+    start_.assign(nbk + 1, 0);
+    auto each_bucket = [&](const HPatch& p, auto&& f) {
       for (int z = fl(p.lo[2]); z <= fl(p.lo[2] + p.n[2] - 1); ++z)
         for (int y = fl(p.lo[1]); y <= fl(p.lo[1] + p.n[1] - 1); ++y)
-          for (int x = fl(p.lo[0]); x <= fl(p.lo[0] + p.n[0] - 1); ++x) map_[key(x, y, z)].push_back(i);
-    }
+          for (int x = fl(p.lo[0]); x <= fl(p.lo[0] + p.n[0] - 1); ++x) f(bucket(x, y, z));
+    };
+    for (int i = first; i < first + count; ++i) each_bucket(P[i], [&](size_t k) { start_[k + 1]++; });
+    for (size_t k = 0; k < nbk; ++k) start_[k + 1] += start_[k];
+    items_.resize(start_[nbk]);
+    std::vector<int> fillp(start_.begin(), start_.end() - 1);
+    for (int i = first; i < first + count; ++i) each_bucket(P[i], [&](size_t k) { items_[fillp[k]++] = i; });
   }
-  // patches intersecting [lo, hi) (no periodic images), ascending patch order
+  // patches intersecting [lo, hi) (no periodic images), ascending patch order;
+  // const and safe to call from several threads
   void query(const int lo[3], const int hi[3], std::vector<int>& out) const {
     out.clear();
-    if (lo[0] >= hi[0] || lo[1] >= hi[1] || lo[2] >= hi[2]) return;
-    for (int z = fl(lo[2]); z <= fl(hi[2] - 1); ++z)
-      for (int y = fl(lo[1]); y <= fl(hi[1] - 1); ++y)
-        for (int x = fl(lo[0]); x <= fl(hi[0] - 1); ++x) {
-          auto it = map_.find(key(x, y, z));
-          if (it == map_.end()) continue;
-          for (int i : it->second) {
+    if (lo[0] >= hi[0] || lo[1] >= hi[1] || lo[2] >= hi[2] || items_.empty()) return;
+    int b0[3], b1[3];
+    for (int d = 0; d < 3; ++d) {
+      b0[d] = std::max(fl(lo[d]) - g0_[d], 0);
+      b1[d] = std::min(fl(hi[d] - 1) - g0_[d], gn_[d] - 1);
+      if (b0[d] > b1[d]) return;
+    }
+    for (int z = b0[2]; z <= b1[2]; ++z)
+      for (int y = b0[1]; y <= b1[1]; ++y)
+        for (int x = b0[0]; x <= b1[0]; ++x) {
+          const size_t k = ((size_t)z * gn_[1] + y) * gn_[0] + x;
+          for (int e = start_[k]; e < start_[k + 1]; ++e) {
+            const int i = items_[e];
             const HPatch& p = P_[i];
             bool hit = true;
             for (int d = 0; d < 3 && hit; ++d) hit = p.lo[d] < hi[d] && lo[d] < p.lo[d] + p.n[d];
@@ -120,13 +187,14 @@ class PatchIndex {
   }
 
  private:
-  int fl(int c) const { return (int)std::floor((double)c / bs_); }
-  static int64_t key(int x, int y, int z) {
-    return ((int64_t)(x + (1 << 20)) << 42) | ((int64_t)(y + (1 << 20)) << 21) | (int64_t)(z + (1 << 20));
+  int fl(int c) const { return c >= 0 ? c / bs_ : -((-c + bs_ - 1) / bs_); }
+  size_t bucket(int x, int y, int z) const {
+    return ((size_t)(z - g0_[2]) * gn_[1] + (y - g0_[1])) * gn_[0] + (x - g0_[0]);
   }
   const std::vector<HPatch>& P_;
   int bs_;
-  std::unordered_map<int64_t, std::vector<int>> map_;
+  int g0_[3], gn_[3];
+  std::vector<int> start_, items_;
 };
 
 // Split boxes with more than `maxc` cells along their longest axis so that
@@ -533,109 +601,123 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   build_items(plan, tp);
 
   // ---- ghost fill: sibling copies (incl. periodic images), outflow, prolongation boxes ----
-  std::vector<int> cand;
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
     PatchIndex six(P, L.first, L.count);
+    std::vector<std::vector<CopySeg>> gs(L.count);
+    std::vector<std::vector<ProlongBox>> ps(L.count);
+    std::vector<std::string> err(L.count);
+    parallel_for(L.count, [&](int ii) {
+      const int i = L.first + ii;
+      std::vector<CopySeg>& Gv = gs[ii];
+      std::vector<ProlongBox>& Pv = ps[ii];
+      std::vector<int> cand;
+      const HPatch& p = P[i];
+        for (int d = 0; d < 3; ++d) {
+          int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          int Nl = level_n(cfg, l, d);
+          for (int side = 0; side < 2; ++side)
+            for (int gg = 0; gg < kGhost; ++gg) {
+              int loc = side ? p.n[d] + gg : -1 - gg;
+              int G = p.lo[d] + loc;
+              if (G < 0 || G >= Nl) {
+                if (!periodic(cfg, d)) {  // outflow: zero-gradient copy of the boundary cell
+                  CopySeg s{};
+                  s.dst_patch = i; s.src_patch = i;
+                  s.dlo[d] = (int16_t)loc; s.dn[d] = 1; s.mode[d] = 1;
+                  s.sh[d] = (int16_t)(side ? p.n[d] - 1 : 0);
+                  s.dlo[t1] = 0; s.dn[t1] = (int16_t)p.n[t1]; s.mode[t1] = 0; s.sh[t1] = 0;
+                  s.dlo[t2] = 0; s.dn[t2] = (int16_t)p.n[t2]; s.mode[t2] = 0; s.sh[t2] = 0;
+                  Gv.push_back(s);
+                  continue;
+                }
+                G = ((G % Nl) + Nl) % Nl;
+              }
+              int A = p.n[t1], B = p.n[t2];
+              std::vector<unsigned char> mask((size_t)A * B, 0);
+              {
+                int qlo[3], qhi[3];
+                qlo[d] = G; qhi[d] = G + 1;
+                qlo[t1] = p.lo[t1]; qhi[t1] = p.lo[t1] + p.n[t1];
+                qlo[t2] = p.lo[t2]; qhi[t2] = p.lo[t2] + p.n[t2];
+                six.query(qlo, qhi, cand);
+              }
+              for (int q : cand) {
+                const HPatch& o = P[q];
+                if (G < o.lo[d] || G >= o.lo[d] + o.n[d]) continue;
+                int a0 = std::max(p.lo[t1], o.lo[t1]), a1 = std::min(p.lo[t1] + p.n[t1], o.lo[t1] + o.n[t1]);
+                int b0 = std::max(p.lo[t2], o.lo[t2]), b1 = std::min(p.lo[t2] + p.n[t2], o.lo[t2] + o.n[t2]);
+                if (a0 >= a1 || b0 >= b1) continue;
+                CopySeg s{};
+                s.dst_patch = i; s.src_patch = q;
+                s.dlo[d] = (int16_t)loc; s.dn[d] = 1; s.mode[d] = 0;
+                s.sh[d] = (int16_t)((G - o.lo[d]) - loc);
+                s.dlo[t1] = (int16_t)(a0 - p.lo[t1]); s.dn[t1] = (int16_t)(a1 - a0); s.sh[t1] = (int16_t)(p.lo[t1] - o.lo[t1]);
+                s.dlo[t2] = (int16_t)(b0 - p.lo[t2]); s.dn[t2] = (int16_t)(b1 - b0); s.sh[t2] = (int16_t)(p.lo[t2] - o.lo[t2]);
+                Gv.push_back(s);
+                for (int b = b0; b < b1; ++b)
+                  for (int a = a0; a < a1; ++a) mask[(size_t)(b - p.lo[t2]) * A + (a - p.lo[t1])] = 1;
+              }
+              std::vector<Rect> rects = mask_rects(mask, A, B);
+              if (!rects.empty() && l == 0) {
+                err[ii] = fmt("level-0 patch %d has uncovered ghost cells", i);
+                return;
+              }
+              for (const Rect& r : rects) {
+                ProlongBox pb{};
+                pb.patch = i;
+                pb.lo[d] = (int16_t)loc; pb.n[d] = 1;
+                pb.lo[t1] = (int16_t)r.a0; pb.n[t1] = (int16_t)r.na;
+                pb.lo[t2] = (int16_t)r.b0; pb.n[t2] = (int16_t)r.nb;
+                Pv.push_back(pb);
+              }
+            }
+        }
+        // merge the two ghost layers of a face into one two-deep segment where
+        // both layers copy from the same source with the same mapping
+        {
+          const int g0 = 0;
+          std::vector<CopySeg> segs(Gv.begin() + g0, Gv.end());
+          std::vector<char> used(segs.size(), 0);
+          std::vector<CopySeg> merged;
+          for (size_t a = 0; a < segs.size(); ++a) {
+            if (used[a]) continue;
+            CopySeg m = segs[a];
+            for (size_t b = a + 1; b < segs.size(); ++b) {
+              if (used[b]) continue;
+              const CopySeg& o = segs[b];
+              int d = -1;
+              for (int k = 0; k < 3; ++k)
+                if (m.dn[k] == 1 && o.dn[k] == 1 && (o.dlo[k] == m.dlo[k] - 1 || o.dlo[k] == m.dlo[k] + 1)) d = k;
+              if (d < 0 || o.src_patch != m.src_patch) continue;
+              bool same = true;
+              for (int k = 0; k < 3 && same; ++k) {
+                same = o.mode[k] == m.mode[k] && o.sh[k] == m.sh[k];
+                if (k != d) same = same && o.dlo[k] == m.dlo[k] && o.dn[k] == m.dn[k];
+              }
+              if (!same) continue;
+              m.dlo[d] = std::min(m.dlo[d], o.dlo[d]);
+              m.dn[d] = 2;
+              used[b] = 1;
+              break;
+            }
+            merged.push_back(m);
+          }
+          Gv.resize(g0);
+          Gv.insert(Gv.end(), merged.begin(), merged.end());
+          split_copy(Gv, g0);
+        }
+        split_prolong(Pv, 0);
+    });
     L.ghost_first.push_back(0);
     L.prolong_first.push_back(0);
-    for (int i = L.first; i < L.first + L.count; ++i) {
-      const HPatch& p = P[i];
-      for (int d = 0; d < 3; ++d) {
-        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        int Nl = level_n(cfg, l, d);
-        for (int side = 0; side < 2; ++side)
-          for (int gg = 0; gg < kGhost; ++gg) {
-            int loc = side ? p.n[d] + gg : -1 - gg;
-            int G = p.lo[d] + loc;
-            if (G < 0 || G >= Nl) {
-              if (!periodic(cfg, d)) {  // outflow: zero-gradient copy of the boundary cell
-                CopySeg s{};
-                s.dst_patch = i; s.src_patch = i;
-                s.dlo[d] = (int16_t)loc; s.dn[d] = 1; s.mode[d] = 1;
-                s.sh[d] = (int16_t)(side ? p.n[d] - 1 : 0);
-                s.dlo[t1] = 0; s.dn[t1] = (int16_t)p.n[t1]; s.mode[t1] = 0; s.sh[t1] = 0;
-                s.dlo[t2] = 0; s.dn[t2] = (int16_t)p.n[t2]; s.mode[t2] = 0; s.sh[t2] = 0;
-                L.ghost.push_back(s);
-                continue;
-              }
-              G = ((G % Nl) + Nl) % Nl;
-            }
-            int A = p.n[t1], B = p.n[t2];
-            std::vector<unsigned char> mask((size_t)A * B, 0);
-            {
-              int qlo[3], qhi[3];
-              qlo[d] = G; qhi[d] = G + 1;
-              qlo[t1] = p.lo[t1]; qhi[t1] = p.lo[t1] + p.n[t1];
-              qlo[t2] = p.lo[t2]; qhi[t2] = p.lo[t2] + p.n[t2];
-              six.query(qlo, qhi, cand);
-            }
-            for (int q : cand) {
-              const HPatch& o = P[q];
-              if (G < o.lo[d] || G >= o.lo[d] + o.n[d]) continue;
-              int a0 = std::max(p.lo[t1], o.lo[t1]), a1 = std::min(p.lo[t1] + p.n[t1], o.lo[t1] + o.n[t1]);
-              int b0 = std::max(p.lo[t2], o.lo[t2]), b1 = std::min(p.lo[t2] + p.n[t2], o.lo[t2] + o.n[t2]);
-              if (a0 >= a1 || b0 >= b1) continue;
-              CopySeg s{};
-              s.dst_patch = i; s.src_patch = q;
-              s.dlo[d] = (int16_t)loc; s.dn[d] = 1; s.mode[d] = 0;
-              s.sh[d] = (int16_t)((G - o.lo[d]) - loc);
-              s.dlo[t1] = (int16_t)(a0 - p.lo[t1]); s.dn[t1] = (int16_t)(a1 - a0); s.sh[t1] = (int16_t)(p.lo[t1] - o.lo[t1]);
-              s.dlo[t2] = (int16_t)(b0 - p.lo[t2]); s.dn[t2] = (int16_t)(b1 - b0); s.sh[t2] = (int16_t)(p.lo[t2] - o.lo[t2]);
-              L.ghost.push_back(s);
-              for (int b = b0; b < b1; ++b)
-                for (int a = a0; a < a1; ++a) mask[(size_t)(b - p.lo[t2]) * A + (a - p.lo[t1])] = 1;
-            }
-            std::vector<Rect> rects = mask_rects(mask, A, B);
-            if (!rects.empty() && l == 0) {
-              msg = fmt("level-0 patch %d has uncovered ghost cells", i);
-              return AMR_ERR_NESTING;
-            }
-            for (const Rect& r : rects) {
-              ProlongBox pb{};
-              pb.patch = i;
-              pb.lo[d] = (int16_t)loc; pb.n[d] = 1;
-              pb.lo[t1] = (int16_t)r.a0; pb.n[t1] = (int16_t)r.na;
-              pb.lo[t2] = (int16_t)r.b0; pb.n[t2] = (int16_t)r.nb;
-              L.prolong.push_back(pb);
-            }
-          }
+    for (int ii = 0; ii < L.count; ++ii) {
+      if (!err[ii].empty()) {
+        msg = err[ii];
+        return AMR_ERR_NESTING;
       }
-      // merge the two ghost layers of a face into one two-deep segment where
-      // both layers copy from the same source with the same mapping
-      {
-        const int g0 = L.ghost_first.back();
-        std::vector<CopySeg> segs(L.ghost.begin() + g0, L.ghost.end());
-        std::vector<char> used(segs.size(), 0);
-        std::vector<CopySeg> merged;
-        for (size_t a = 0; a < segs.size(); ++a) {
-          if (used[a]) continue;
-          CopySeg m = segs[a];
-          for (size_t b = a + 1; b < segs.size(); ++b) {
-            if (used[b]) continue;
-            const CopySeg& o = segs[b];
-            int d = -1;
-            for (int k = 0; k < 3; ++k)
-              if (m.dn[k] == 1 && o.dn[k] == 1 && (o.dlo[k] == m.dlo[k] - 1 || o.dlo[k] == m.dlo[k] + 1)) d = k;
-            if (d < 0 || o.src_patch != m.src_patch) continue;
-            bool same = true;
-            for (int k = 0; k < 3 && same; ++k) {
-              same = o.mode[k] == m.mode[k] && o.sh[k] == m.sh[k];
-              if (k != d) same = same && o.dlo[k] == m.dlo[k] && o.dn[k] == m.dn[k];
-            }
-            if (!same) continue;
-            m.dlo[d] = std::min(m.dlo[d], o.dlo[d]);
-            m.dn[d] = 2;
-            used[b] = 1;
-            break;
-          }
-          merged.push_back(m);
-        }
-        L.ghost.resize(g0);
-        L.ghost.insert(L.ghost.end(), merged.begin(), merged.end());
-        split_copy(L.ghost, g0);
-      }
-      split_prolong(L.prolong, L.prolong_first.back());
+      L.ghost.insert(L.ghost.end(), gs[ii].begin(), gs[ii].end());
+      L.prolong.insert(L.prolong.end(), ps[ii].begin(), ps[ii].end());
       L.ghost_first.push_back((int)L.ghost.size());
       L.prolong_first.push_back((int)L.prolong.size());
     }
@@ -646,84 +728,95 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
     PatchIndex cix(P, C.first, C.count);
-    L.gather_first.push_back(0);
-    for (int i = L.first; i < L.first + L.count; ++i) {
+    std::vector<std::vector<CopySeg>> as(L.count);
+    std::vector<std::string> err(L.count);
+    parallel_for(L.count, [&](int ii) {
+      const int i = L.first + ii;
+      std::vector<CopySeg>& Av = as[ii];
+      std::vector<int> cand;
       const HPatch& p = P[i];
-      struct Piece { int a, len, mode, src; };
-      std::vector<Piece> pieces[3];
-      for (int d = 0; d < 3; ++d) {
-        int Nc = level_n(cfg, l - 1, d);
-        int T0 = p.lo[d] / 2 - 2, tn = p.n[d] / 2 + 4;
-        int t = 0;
-        while (t < tn) {
-          int Cg = T0 + t;
-          int kind = Cg < 0 ? 0 : (Cg < Nc ? 1 : 2);
-          int e = t;
-          while (e < tn) {
-            int Cc = T0 + e;
-            int k2 = Cc < 0 ? 0 : (Cc < Nc ? 1 : 2);
-            if (k2 != kind) break;
-            ++e;
+        struct Piece { int a, len, mode, src; };
+        std::vector<Piece> pieces[3];
+        for (int d = 0; d < 3; ++d) {
+          int Nc = level_n(cfg, l - 1, d);
+          int T0 = p.lo[d] / 2 - 2, tn = p.n[d] / 2 + 4;
+          int t = 0;
+          while (t < tn) {
+            int Cg = T0 + t;
+            int kind = Cg < 0 ? 0 : (Cg < Nc ? 1 : 2);
+            int e = t;
+            while (e < tn) {
+              int Cc = T0 + e;
+              int k2 = Cc < 0 ? 0 : (Cc < Nc ? 1 : 2);
+              if (k2 != kind) break;
+              ++e;
+            }
+            Piece pc{t, e - t, 0, 0};
+            if (kind == 1) { pc.mode = 0; pc.src = Cg; }
+            else if (periodic(cfg, d)) { pc.mode = 0; pc.src = kind == 0 ? Cg + Nc : Cg - Nc; }
+            else { pc.mode = 1; pc.src = kind == 0 ? 0 : Nc - 1; }
+            pieces[d].push_back(pc);
+            t = e;
           }
-          Piece pc{t, e - t, 0, 0};
-          if (kind == 1) { pc.mode = 0; pc.src = Cg; }
-          else if (periodic(cfg, d)) { pc.mode = 0; pc.src = kind == 0 ? Cg + Nc : Cg - Nc; }
-          else { pc.mode = 1; pc.src = kind == 0 ? 0 : Nc - 1; }
-          pieces[d].push_back(pc);
-          t = e;
         }
-      }
-      int64_t covered = 0;
-      for (auto& p0 : pieces[0])
-        for (auto& p1 : pieces[1])
-          for (auto& p2 : pieces[2]) {
-            const Piece* pp[3] = {&p0, &p1, &p2};
-            {
-              int qlo[3], qhi[3];
-              for (int d = 0; d < 3; ++d) {
-                qlo[d] = pp[d]->src;
-                qhi[d] = pp[d]->mode == 1 ? pp[d]->src + 1 : pp[d]->src + pp[d]->len;
-              }
-              cix.query(qlo, qhi, cand);
-            }
-            for (int q : cand) {
-              const HPatch& o = P[q];
-              CopySeg s{};
-              s.dst_patch = i; s.src_patch = q;
-              bool ok = true;
-              int64_t vol = 1;
-              for (int d = 0; d < 3 && ok; ++d) {
-                const Piece& pc = *pp[d];
-                if (pc.mode == 1) {
-                  if (pc.src < o.lo[d] || pc.src >= o.lo[d] + o.n[d]) { ok = false; break; }
-                  s.dlo[d] = (int16_t)pc.a; s.dn[d] = (int16_t)pc.len; s.mode[d] = 1;
-                  s.sh[d] = (int16_t)(pc.src - o.lo[d]);
-                  vol *= pc.len;
-                } else {
-                  int a = std::max(pc.src, o.lo[d]), b = std::min(pc.src + pc.len, o.lo[d] + o.n[d]);
-                  if (a >= b) { ok = false; break; }
-                  int dst0 = pc.a + (a - pc.src);
-                  s.dlo[d] = (int16_t)dst0; s.dn[d] = (int16_t)(b - a); s.mode[d] = 0;
-                  s.sh[d] = (int16_t)((a - o.lo[d]) - dst0);
-                  vol *= (b - a);
+        int64_t covered = 0;
+        for (auto& p0 : pieces[0])
+          for (auto& p1 : pieces[1])
+            for (auto& p2 : pieces[2]) {
+              const Piece* pp[3] = {&p0, &p1, &p2};
+              {
+                int qlo[3], qhi[3];
+                for (int d = 0; d < 3; ++d) {
+                  qlo[d] = pp[d]->src;
+                  qhi[d] = pp[d]->mode == 1 ? pp[d]->src + 1 : pp[d]->src + pp[d]->len;
                 }
+                cix.query(qlo, qhi, cand);
               }
-              if (!ok) continue;
-              covered += vol;
-              L.gather.push_back(s);
+              for (int q : cand) {
+                const HPatch& o = P[q];
+                CopySeg s{};
+                s.dst_patch = i; s.src_patch = q;
+                bool ok = true;
+                int64_t vol = 1;
+                for (int d = 0; d < 3 && ok; ++d) {
+                  const Piece& pc = *pp[d];
+                  if (pc.mode == 1) {
+                    if (pc.src < o.lo[d] || pc.src >= o.lo[d] + o.n[d]) { ok = false; break; }
+                    s.dlo[d] = (int16_t)pc.a; s.dn[d] = (int16_t)pc.len; s.mode[d] = 1;
+                    s.sh[d] = (int16_t)(pc.src - o.lo[d]);
+                    vol *= pc.len;
+                  } else {
+                    int a = std::max(pc.src, o.lo[d]), b = std::min(pc.src + pc.len, o.lo[d] + o.n[d]);
+                    if (a >= b) { ok = false; break; }
+                    int dst0 = pc.a + (a - pc.src);
+                    s.dlo[d] = (int16_t)dst0; s.dn[d] = (int16_t)(b - a); s.mode[d] = 0;
+                    s.sh[d] = (int16_t)((a - o.lo[d]) - dst0);
+                    vol *= (b - a);
+                  }
+                }
+                if (!ok) continue;
+                covered += vol;
+                Av.push_back(s);
+              }
             }
-          }
-      split_copy(L.gather, L.gather_first.back());
-      const PatchDesc& d = plan.desc[i];
-      if (covered != (int64_t)d.tn[0] * d.tn[1] * d.tn[2]) {
-        msg = fmt("patch %d: parent tile not covered by level %d", i, l - 1);
+        split_copy(Av, 0);
+        const PatchDesc& d = plan.desc[i];
+        if (covered != (int64_t)d.tn[0] * d.tn[1] * d.tn[2])
+          err[ii] = fmt("patch %d: parent tile not covered by level %d", i, l - 1);
+    });
+    L.gather_first.push_back(0);
+    for (int ii = 0; ii < L.count; ++ii) {
+      if (!err[ii].empty()) {
+        msg = err[ii];
         return AMR_ERR_NESTING;
       }
+      L.gather.insert(L.gather.end(), as[ii].begin(), as[ii].end());
       L.gather_first.push_back((int)L.gather.size());
     }
   }
 
   // ---- restriction segments and coverage boxes ----
+  std::vector<int> cand;
   plan.cover_first.assign(np + 1, 0);
   std::vector<std::vector<CoverBox>> cov(np);
   for (int l = 1; l < nlev; ++l) {
@@ -770,17 +863,21 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
     PatchIndex fix(P, L.first, L.count), cix(P, C.first, C.count);
-    std::vector<RegFace> regs;
-    for (int d = 0; d < 3; ++d)
-      for (int side = 0; side < 2; ++side)
-        for (int i = L.first; i < L.first + L.count; ++i) {
+    // tasks in (d, side, patch) order; concatenated in that order below
+    const int ntask = 6 * L.count;
+    std::vector<std::vector<RegFace>> rs(ntask);
+    std::vector<std::string> err(ntask);
+    parallel_for(ntask, [&](int task) {
+      const int d = task / (2 * L.count), side = (task / L.count) % 2, i = L.first + task % L.count;
+      std::vector<RegFace>& Rv = rs[task];
+      std::vector<int> cand;
           const HPatch& p = P[i];
           int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
           int xf = side ? p.lo[d] + p.n[d] : p.lo[d];
           int Cd = side ? xf / 2 : xf / 2 - 1;
           int Nc = level_n(cfg, l - 1, d);
           if (Cd < 0 || Cd >= Nc) {
-            if (!periodic(cfg, d)) continue;
+            if (!periodic(cfg, d)) return;
             Cd = ((Cd % Nc) + Nc) % Nc;
           }
           int a0 = p.lo[t1] / 2, A = p.n[t1] / 2, b0 = p.lo[t2] / 2, B = p.n[t2] / 2;
@@ -821,7 +918,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             for (int a = 0; a < A; ++a) {
               if (cov2[(size_t)b * A + a]) continue;
               int q = owner[(size_t)b * A + a];
-              if (q < 0) { msg = fmt("patch %d: coarse neighbour cell outside level %d", i, l - 1); return AMR_ERR_NESTING; }
+              if (q < 0) { err[task] = fmt("patch %d: coarse neighbour cell outside level %d", i, l - 1); return; }
               const HPatch& o = P[q];
               RegFace r{};
               r.fpatch = i; r.cpatch = q;
@@ -832,9 +929,17 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
               r.fface[d] = (int16_t)(side ? p.n[d] : 0);
               r.fface[t1] = (int16_t)(2 * (a0 + a) - p.lo[t1]);
               r.fface[t2] = (int16_t)(2 * (b0 + b) - p.lo[t2]);
-              regs.push_back(r);
+              Rv.push_back(r);
             }
-        }
+            });
+    std::vector<RegFace> regs;
+    for (int task = 0; task < ntask; ++task) {
+      if (!err[task].empty()) {
+        msg = err[task];
+        return AMR_ERR_NESTING;
+      }
+      regs.insert(regs.end(), rs[task].begin(), rs[task].end());
+    }
     // group by coarse cell, keeping the (d, side) order inside a cell
     std::stable_sort(regs.begin(), regs.end(), [](const RegFace& a, const RegFace& b) {
       return std::make_tuple(a.cpatch, a.cidx[2], a.cidx[1], a.cidx[0]) <
@@ -877,6 +982,70 @@ Key unpack(int64_t k) {
   return r;
 }
 
+// Set of packed block keys (all >= 0): open addressing with linear probing in
+// a power-of-two table kept at most half full; the slot hash is the 64-bit
+// finaliser of MurmurHash3.  Membership only -- iteration order is not used
+// for any result.
+class KeySet {
+ public:
+  KeySet() : slots_(16, kEmpty), mask_(15) {}
+  bool insert(int64_t k) {
+    if (2 * (n_ + 1) > slots_.size()) grow();
+    size_t h = mix(k) & mask_;
+    while (slots_[h] != kEmpty) {
+      if (slots_[h] == k) return false;
+      h = (h + 1) & mask_;
+    }
+    slots_[h] = k;
+    ++n_;
+    return true;
+  }
+  size_t count(int64_t k) const {
+    size_t h = mix(k) & mask_;
+    while (slots_[h] != kEmpty) {
+      if (slots_[h] == k) return 1;
+      h = (h + 1) & mask_;
+    }
+    return 0;
+  }
+  size_t size() const { return n_; }
+  bool empty() const { return n_ == 0; }
+  void swap(KeySet& o) {
+    slots_.swap(o.slots_);
+    std::swap(n_, o.n_);
+    std::swap(mask_, o.mask_);
+  }
+  std::vector<int64_t> keys() const {
+    std::vector<int64_t> out;
+    out.reserve(n_);
+    for (int64_t k : slots_)
+      if (k != kEmpty) out.push_back(k);
+    return out;
+  }
+
+ private:
+  static constexpr int64_t kEmpty = -1;
+  static size_t mix(int64_t k) {
+    uint64_t x = (uint64_t)k;
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return (size_t)x;
+  }
+  void grow() {
+    std::vector<int64_t> old(slots_.size() * 2, kEmpty);
+    old.swap(slots_);
+    mask_ = slots_.size() - 1;
+    n_ = 0;
+    for (int64_t k : old)
+      if (k != kEmpty) insert(k);
+  }
+  std::vector<int64_t> slots_;
+  size_t n_ = 0, mask_;
+};
+
 }  // namespace
 
 amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
@@ -890,12 +1059,14 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   }
   auto nb = [&](int l, int d) { return (level_n(cfg, l, d) + B - 1) / B; };
   auto per = [&](int d) { return periodic(cfg, d); };
-  std::vector<std::unordered_set<int64_t>> tags(L + 1);
+  std::vector<KeySet> tags(L + 1);
   // 1. flagged cells, grown by the buffer, mark blocks of their level (first on a
-  //    per-patch block grid, so each block is inserted once per patch)
-  for (size_t i = 0; i < old.size(); ++i) {
+  //    per-patch block grid, so each block is listed once per patch; patches in
+  //    parallel, then inserted in patch order)
+  std::vector<std::vector<int64_t>> pk(old.size());
+  parallel_for((int)old.size(), [&](int i) {
     const HPatch& p = old[i];
-    if (p.level < l0 || p.level >= L || flags[i].empty()) continue;
+    if (p.level < l0 || p.level >= L || flags[i].empty()) return;
     const int l = p.level;
     int g0[3], gn[3];
     for (int d = 0; d < 3; ++d) {
@@ -933,14 +1104,21 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
             int n = nb(l, d);
             if (per(d)) q[d] = ((q[d] % n) + n) % n;
           }
-          tags[l].insert(pack(q[0], q[1], q[2]));
+          pk[i].push_back(pack(q[0], q[1], q[2]));
         }
-  }
+  });
+  for (size_t i = 0; i < old.size(); ++i)
+    for (int64_t k : pk[i]) tags[old[i].level].insert(k);
   // 2. a tag on level l needs its parent region (and a ring for nesting) refined on level l-1
-  for (int l = L - 1; l > l0; --l)
-    for (int64_t kb : tags[l]) {
+  for (int l = L - 1; l > l0; --l) {
+    KeySet parents;   // parent blocks of the tags (8 children share one)
+    for (int64_t kb : tags[l].keys()) {
       const Key b = unpack(kb);
-      int pb[3] = {b.x >> 1, b.y >> 1, b.z >> 1};
+      parents.insert(pack(b.x >> 1, b.y >> 1, b.z >> 1));
+    }
+    for (int64_t kp : parents.keys()) {
+      const Key b = unpack(kp);
+      int pb[3] = {b.x, b.y, b.z};
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
@@ -956,12 +1134,13 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
             if (ok) tags[l - 1].insert(pack(q[0], q[1], q[2]));
           }
     }
+  }
   // 3. top-down: keep levels <= l0, then cluster refinable blocks of each level
   out.clear();
   for (const HPatch& p : old)
     if (p.level <= l0) out.push_back(p);
   // blocks of level l0 fully covered by its patches
-  std::unordered_set<int64_t> cover;
+  KeySet cover;
   for (const HPatch& p : old) {
     if (p.level != l0) continue;
     int a0[3], a1[3];
@@ -977,8 +1156,11 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   }
   const int maxb = rp.max_patch / (2 * B);
   for (int l = l0; l < L; ++l) {
-    std::unordered_set<int64_t> refine;
-    for (int64_t kb : tags[l]) {
+    KeySet refine;
+    const std::vector<int64_t> tl = tags[l].keys();
+    std::vector<unsigned char> refinable(tl.size(), 0);
+    parallel_for((int)tl.size(), [&](int ti) {
+      const int64_t kb = tl[ti];
       const Key b = unpack(kb);
       bool ok = true;
       for (int dz = -1; dz <= 1 && ok; ++dz)
@@ -995,15 +1177,17 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
             }
             if (!outside && !cover.count(pack(q[0], q[1], q[2]))) ok = false;
           }
-      if (ok) refine.insert(kb);
-    }
+      refinable[ti] = ok;
+    });
+    for (size_t ti = 0; ti < tl.size(); ++ti)
+      if (refinable[ti]) refine.insert(tl[ti]);
     if (refine.empty()) break;
     // greedy box merge in (z, y, x) order: extend along x, then y, then z
-    std::unordered_set<int64_t> done;
-    std::unordered_set<int64_t> next_cover;
+    KeySet done;
+    KeySet next_cover;
     std::vector<Key> order;
     order.reserve(refine.size());
-    for (int64_t kb : refine) order.push_back(unpack(kb));
+    for (int64_t kb : refine.keys()) order.push_back(unpack(kb));
     std::sort(order.begin(), order.end());   // (z, y, x) order
     for (const Key& b : order) {
       if (done.count(pack(b.x, b.y, b.z))) continue;
@@ -1061,14 +1245,18 @@ void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch
   }
   std::vector<std::unique_ptr<PatchIndex>> oix(ofirst.size());
   for (size_t l = 0; l < ofirst.size(); ++l) oix[l].reset(new PatchIndex(oldp, ofirst[l], ocount[l]));
-  std::vector<int> cand;
-  for (size_t i = 0; i < newp.size(); ++i) {
+  const int nnew = (int)newp.size();
+  std::vector<std::vector<CopySeg>> cs(nnew);
+  std::vector<std::vector<ProlongBox>> fs(nnew);
+  parallel_for(nnew, [&](int ii) {
+    const size_t i = (size_t)ii;
     const HPatch& p = newp[i];
-    if (p.level <= keep_level) continue;
+    if (p.level <= keep_level) return;
     const int l = p.level;
+    std::vector<int> cand;
+    std::vector<CopySeg>& Cv = cs[ii];
+    std::vector<ProlongBox>& Fv = fs[ii];
     std::vector<unsigned char> mask((size_t)p.n[0] * p.n[1] * p.n[2], 0);
-    const size_t c0 = fill.copy[l].size();
-    cand.clear();
     if (l < (int)oix.size()) {
       int qlo[3], qhi[3];
       for (int d = 0; d < 3; ++d) { qlo[d] = p.lo[d]; qhi[d] = p.lo[d] + p.n[d]; }
@@ -1094,27 +1282,29 @@ void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch
         sg.sh[d] = (int16_t)(p.lo[d] - o.lo[d]);
         sg.mode[d] = 0;
       }
-      fill.copy[l].push_back(sg);
+      Cv.push_back(sg);
       for (int z = lo[2]; z < hi[2]; ++z)
         for (int y = lo[1]; y < hi[1]; ++y)
           for (int x = lo[0]; x < hi[0]; ++x)
             mask[((size_t)(z - p.lo[2]) * p.n[1] + (y - p.lo[1])) * p.n[0] + (x - p.lo[0])] = 1;
     }
-    split_copy(fill.copy[l], c0);
-    const size_t f0 = fill.fresh[l].size();
+    split_copy(Cv, 0);
     for (int z = 0; z < p.n[2]; ++z) {
-      std::vector<unsigned char> slab(mask.begin() + (size_t)z * p.n[0] * p.n[1],
-                                      mask.begin() + (size_t)(z + 1) * p.n[0] * p.n[1]);
-      for (const Rect& r : mask_rects(slab, p.n[0], p.n[1])) {
+      for (const Rect& r : mask_rects(mask.data() + (size_t)z * p.n[0] * p.n[1], p.n[0], p.n[1])) {
         ProlongBox b{};
         b.patch = (int)i;
         b.lo[0] = (int16_t)r.a0; b.n[0] = (int16_t)r.na;
         b.lo[1] = (int16_t)r.b0; b.n[1] = (int16_t)r.nb;
         b.lo[2] = (int16_t)z; b.n[2] = 1;
-        fill.fresh[l].push_back(b);
+        Fv.push_back(b);
       }
     }
-    split_prolong(fill.fresh[l], f0);
+    split_prolong(Fv, 0);
+  });
+  for (int ii = 0; ii < nnew; ++ii) {
+    const int l = newp[ii].level;
+    fill.copy[l].insert(fill.copy[l].end(), cs[ii].begin(), cs[ii].end());
+    fill.fresh[l].insert(fill.fresh[l].end(), fs[ii].begin(), fs[ii].end());
   }
 }
 

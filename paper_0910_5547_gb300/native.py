@@ -35,7 +35,8 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
-           "amr_get_patches", "amr_autotune"]
+           "amr_get_patches", "amr_autotune", "amr_get_regrid_timing"]
+REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
 
@@ -126,6 +127,8 @@ def load():
     L.amr_get_patches.argtypes = [H, ctypes.POINTER(amr_patch), ctypes.c_int]
     L.amr_autotune.argtypes = [H, ctypes.c_char_p, ctypes.c_int]
     L.amr_autotune.restype = ctypes.c_int
+    L.amr_get_regrid_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    L.amr_get_regrid_timing.restype = ctypes.c_int
     L.amr_get_patches.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -298,6 +301,13 @@ def amr_autotune(h) -> str:
     buf = ctypes.create_string_buffer(4096)
     _check(h, load().amr_autotune(h, buf, 4096))
     return buf.value.decode()
+
+
+def amr_get_regrid_timing(h) -> dict:
+    """Host seconds of the phases of the last amr_regrid (REGRID_PHASES)."""
+    buf = (ctypes.c_double * len(REGRID_PHASES))()
+    _check(h, load().amr_get_regrid_timing(h, buf, len(REGRID_PHASES)))
+    return {k: buf[i] for i, k in enumerate(REGRID_PHASES)}
 
 
 def amr_get_patches(h) -> list:
