@@ -154,6 +154,24 @@ def sod(n: int = 32, axis: int = 0, ny: int | None = None, tile: int | None = No
                    t_end=t_end, meta={"axis": axis})
 
 
+def double_rarefaction(n: int = 32, ny: int = 8, tile: int | None = None, u: float = 2.0, p: float = 1e-6,
+                       gamma: float = 1.4) -> Problem:
+    """Two periodic pairs of receding streams along x (rho = 1, vx = -u for x < 0.5 and +u
+    beyond, pressure p): strong rarefactions at x = 0.5 and x = 0 drive the middle towards
+    vacuum, the workload of the positivity floor."""
+    N = [n, ny, ny]
+    t = tile or max(N)
+    patches = uniform_patches(N, (min(t, N[0]), min(t, N[1]), min(t, N[2])))
+
+    def fn(pt, w, x, y, z):
+        left = np.broadcast_to(x < 0.5, w.shape[1:])
+        w[0] = 1.0
+        w[1] = np.where(left, -u, u)
+        w[4] = p
+
+    return Problem("double_rarefaction", 5, gamma, tuple(N), (PERIODIC,) * 6, patches, _fill(patches, N, 5, fn))
+
+
 def kelvin_helmholtz(N: int = 256, tile: int | None = 32, seed: int = 20091, amp: float = 0.01,
                      gamma: float = 1.4) -> Problem:
     """Periodic shear layer: rho = 2, vx = +0.5 inside |y - 0.5| < 0.25, rho = 1, vx = -0.5

@@ -53,6 +53,8 @@ class OrcConfig(ctypes.Structure):
         ("bc", ctypes.c_int * 6),
         ("max_level", ctypes.c_int),
         ("ch", ctypes.c_double),
+        ("p_floor", ctypes.c_double),
+        ("glm_alpha", ctypes.c_double),
         ("nthreads", ctypes.c_int),
     ]
 
@@ -122,7 +124,7 @@ def _dp(a: np.ndarray):
 
 def make_config(nvar=5, gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(OUTFLOW,) * 6,
                 riemann=HLL, plm_literal=False, max_level=0, ch=0.0, domain_lo=(0.0, 0.0, 0.0),
-                domain_hi=(1.0, 1.0, 1.0), nthreads=0) -> OrcConfig:
+                domain_hi=(1.0, 1.0, 1.0), nthreads=0, p_floor=0.0, glm_alpha=0.0) -> OrcConfig:
     c = OrcConfig()
     c.nvar, c.riemann, c.plm_literal = nvar, riemann, int(plm_literal)
     c.gamma, c.theta, c.cfl = gamma, theta, cfl
@@ -131,6 +133,7 @@ def make_config(nvar=5, gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(
     c.domain_hi[:] = list(domain_hi)
     c.bc[:] = list(bc)
     c.max_level, c.ch, c.nthreads = max_level, ch, nthreads
+    c.p_floor, c.glm_alpha = p_floor, glm_alpha
     return c
 
 
@@ -264,8 +267,8 @@ def prim_to_cons(w, nvar=5, gamma=1.4) -> np.ndarray:
     return u
 
 
-def cons_to_prim(u, nvar=5, gamma=1.4) -> np.ndarray:
-    cfg = make_config(nvar=nvar, gamma=gamma)
+def cons_to_prim(u, nvar=5, gamma=1.4, p_floor=0.0) -> np.ndarray:
+    cfg = make_config(nvar=nvar, gamma=gamma, p_floor=p_floor)
     u = np.ascontiguousarray(u, dtype=np.float64)
     w = np.zeros(nvar)
     lib().orc_cons_to_prim(ctypes.byref(cfg), _dp(u), _dp(w))

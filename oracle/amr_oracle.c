@@ -74,6 +74,13 @@ static void cons_to_rec(const orc_config* c, const double* u, double* r) {
   if (c->nvar == 9) mag = 0.5 * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
   r[0] = rho; r[1] = vx; r[2] = vy; r[3] = vz;
   r[4] = (u[4] - kin - mag) / rho;
+  /* optional positivity floor: the reconstructed specific internal energy is
+   * raised to p_floor / ((gamma - 1) rho); U itself is never changed, so the
+   * update stays conservative */
+  if (c->p_floor > 0.0) {
+    double ef = c->p_floor / ((c->gamma - 1.0) * rho);
+    if (r[4] < ef) r[4] = ef;
+  }
   if (c->nvar == 9) { r[5] = u[5]; r[6] = u[6]; r[7] = u[7]; r[8] = u[8]; }
 }
 
@@ -774,6 +781,17 @@ static int advance_level(orc_sim* s, int l, double dt, double alpha0) {
             p->U[gi] = 0.5 * p->U[gi] + 0.5 * U2[gi];
           }
     free(U2);
+    /* GLM damping source d psi / dt = -(glm_alpha c_h / dx_min) psi, split from
+     * the hyperbolic step and integrated exactly over dt */
+    if (V == 9 && s->cfg.glm_alpha > 0.0) {
+      double dxm = dx[0];
+      if (dx[1] < dxm) dxm = dx[1];
+      if (dx[2] < dxm) dxm = dx[2];
+      const double f = exp(-s->cfg.glm_alpha * ch * dt / dxm);
+      for (int k = 0; k < p->n[2]; ++k)
+        for (int j = 0; j < p->n[1]; ++j)
+          for (int i = 0; i < p->n[0]; ++i) p->U[8 * p->ncell_g + gidx(p, i, j, k)] *= f;
+    }
   }
   accumulate_registers(s, l, dt);
   if (has_children) {

@@ -39,6 +39,8 @@ typedef struct {
   int bc[6];          /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
   int max_level;
   double ch;          /* GLM cleaning speed; <= 0: max signal speed at the start of each coarse step */
+  double p_floor;     /* pressure floor of the reconstructed variables (0 = off): e >= p_floor / ((gamma-1) rho) */
+  double glm_alpha;   /* GLM damping: psi *= exp(-glm_alpha c_h dt_l / min_d dx_l) after every level step (0 = off) */
   int nthreads;       /* OpenMP threads over patches; <= 0: library default */
 } orc_config;
 
