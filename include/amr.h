@@ -65,6 +65,10 @@ typedef struct {
   int max_level;         /* deepest level allowed, 0 .. 12 */
   int ref_ratio;         /* must be 2 (0 means 2) */
   double ch;             /* GLM cleaning speed; <= 0: max signal speed at each coarse step start */
+  double p_floor;        /* >= 0; > 0: the reconstructed pressure (faces, wave speeds, CFL) is at least
+                            p_floor; the conserved state is never changed (0 = off) */
+  double glm_alpha;      /* >= 0; GLM damping: after every level step psi *= exp(-glm_alpha c_h dt_l /
+                            min_d dx_l) (0 = pure hyperbolic cleaning) */
   int batched;           /* 1: one launch per kernel per level; 0: one launch per patch ("plain") */
   int use_graph;         /* 1: capture a coarse step as a CUDA graph and replay it */
   void* cuda_stream;     /* cudaStream_t to run on; NULL: the library creates its own */
@@ -209,6 +213,11 @@ enum {
  * launch counts (count[c]) since timing was switched on, and resets them. */
 amr_status amr_set_timing(amr_handle* h, int on);
 amr_status amr_get_timing(amr_handle* h, double* ms, long long* count, int nclass);
+
+/* Number of primitive recoveries of interior cells (one per cell per stage)
+ * in which the pressure floor acted since the last call (read and reset).
+ * Synchronises. */
+amr_status amr_floor_count(amr_handle* h, long long* count);
 
 /* Number of kernels the library launched so far (graph replays count every
  * kernel node) -- used to report launches in a timed region. */

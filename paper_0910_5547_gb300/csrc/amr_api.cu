@@ -181,7 +181,7 @@ void free_device(amr_handle* h) {
 }
 
 OpsBase* make_ops(const amr_config& c) {
-  PhysParams p{c.gamma, c.theta, c.ch, c.riemann == AMR_LLF ? 1 : 0};
+  PhysParams p{c.gamma, c.theta, c.ch, c.riemann == AMR_LLF ? 1 : 0, c.p_floor, c.glm_alpha};
   if (c.nvar == 5) return c.precision == AMR_FP32 ? make_ops_f32_euler(p) : make_ops_f64_euler(p);
   return c.precision == AMR_FP32 ? make_ops_f32_mhd(p) : make_ops_f64_mhd(p);
 }
@@ -998,6 +998,17 @@ amr_status amr_conserved_totals(amr_handle* h, double* out) {
   h->launches += 2;
   CK(cudaMemcpyAsync(out, h->totals, h->plan.nvar * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_floor_count(amr_handle* h, long long* count) {
+  if (!h || !count) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, &h->params->floor_hits, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemsetAsync(&h->params->floor_hits, 0, sizeof v, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *count = (long long)v;
   return AMR_OK;
 }
 

@@ -129,6 +129,8 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   ph.ggm1 = (T)(cfg.gamma * (cfg.gamma - 1.0));
   ph.theta = (T)cfg.theta;
   ph.llf = cfg.riemann == AMR_LLF ? 1 : 0;
+  ph.efl = (T)(cfg.p_floor / (cfg.gamma - 1.0));
+  ph.glm_alpha = (T)cfg.glm_alpha;
   double dx[3];
   for (int d = 0; d < 3; ++d) dx[d] = (cfg.domain_hi[d] - cfg.domain_lo[d]) / cfg.base_n[d];
   const int nchunk = (int)chunks.size();

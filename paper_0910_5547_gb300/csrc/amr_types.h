@@ -140,6 +140,7 @@ struct StepParams {
   // next step's CFL rate and signal speed without another pass over the state
   unsigned long long next_rate_bits;
   unsigned long long next_speed_bits;
+  unsigned long long floor_hits;   // interior primitive recoveries raised by the pressure floor
 };
 
 }  // namespace amr

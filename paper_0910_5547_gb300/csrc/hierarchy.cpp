@@ -290,6 +290,8 @@ amr_status validate_config(const amr_config& c, std::string& msg) {
   }
   if (c.batched != 0 && c.batched != 1) { msg = "batched must be 0 or 1"; return AMR_ERR_ARG; }
   if (c.nvar == 9 && c.ch > 0.0 && !std::isfinite(c.ch)) { msg = "ch must be finite"; return AMR_ERR_ARG; }
+  if (!(c.p_floor >= 0.0) || !std::isfinite(c.p_floor)) { msg = "p_floor must be finite and >= 0"; return AMR_ERR_ARG; }
+  if (!(c.glm_alpha >= 0.0) || !std::isfinite(c.glm_alpha)) { msg = "glm_alpha must be finite and >= 0"; return AMR_ERR_ARG; }
   return AMR_OK;
 }
 

@@ -113,7 +113,7 @@ template <typename T, int NV>
 __device__ __forceinline__ void cell_rate(const T* u, const Phys<T>& ph, T idx0, T idy0, T idz0, T& rate,
                                           T& speed) {
   T w[NV];
-  cons_to_prim<T, NV>(u, w);
+  cons_to_prim<T, NV>(u, w, ph.efl);
   T c0, c1, c2;
   if (NV == 5) {
     c0 = c1 = c2 = dsqrt(ph.ggm1 * w[4]);
@@ -169,7 +169,15 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   const T sc = slope_scale<T>();   // face state = w +- sc * limited_slope
   const int t = threadIdx.x;
   bool bad = false;
+  int floor_hits = 0;
   T rate_max = T(0), speed_max = T(0);
+  // GLM damping after the stage-2 average: psi *= exp(-alpha c_h dt_l / min_d dx_l);
+  // dt_l / dx_l is the same on every level (dt0 / dx0)
+  T damp = T(1);
+  if (NV == 9 && STAGE == 2 && a.ph.glm_alpha > T(0)) {
+    const double idmax = fmax(a.idx0, fmax(a.idy0, a.idz0));
+    damp = (T)exp(-(double)a.ph.glm_alpha * a.params->ch * a.params->dt0 * idmax);
+  }
 
   for (int itn = blockIdx.x; itn < a.nitems; itn += gridDim.x) {
     const StageItem it = a.items[itn];
@@ -234,10 +242,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       T u0[NV], w0[NV];
       load_cons<T, NV>(Ub, vs, col - 2 * plane, u0);
       load_cons<T, NV>(Ub, vs, col - plane, uD);
-      cons_to_prim<T, NV>(u0, w0);
-      cons_to_prim<T, NV>(uD, wA);
+      cons_to_prim<T, NV>(u0, w0, ph.efl);
+      cons_to_prim<T, NV>(uD, wA, ph.efl);
       load_cons<T, NV>(Ub, vs, col, uD);
-      bad |= !cons_to_prim<T, NV>(uD, wB);
+      bad |= !cons_to_prim<T, NV>(uD, wB, ph.efl, &floor_hits);   // plane 0: an interior plane
       if (kAsync) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlaneMax];
         }
-        cons_to_prim<T, NV>(hN, w);
+        cons_to_prim<T, NV>(hN, w, ph.efl);
         if (!kAsync) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
 #pragma unroll
         for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
@@ -320,8 +328,12 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) uD[v] = slot[v * kPlaneMax];
         }
-        const bool ok = cons_to_prim<T, NV>(uD, wC);        // plane j+1
-        if (j + 1 < wz) bad |= !ok;
+        int hit = 0;
+        const bool ok = cons_to_prim<T, NV>(uD, wC, ph.efl, &hit);   // plane j+1
+        if (j + 1 < wz) {   // interior planes are checked and counted once each
+          bad |= !ok;
+          floor_hits += hit;
+        }
         if (!kAsync) {
           const int jn = j + 2 <= wz + 1 ? j + 2 : wz + 1;   // ghost planes end at wz+1
           load_cons<T, NV>(Ub, vs, col + jn * plane, uD);      // prefetch plane j+2
@@ -423,6 +435,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
             if (prev) Ob[v * vs + c] = u2;
           } else {
             un[v] = T(0.5) * un[v] + T(0.5) * u2;
+            if (NV == 9 && v == 8) un[v] *= damp;
             if (prev) Ob[v * vs + c] = un[v];
           }
         }
@@ -466,6 +479,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     }
   }
   if (bad) atomicOr(&a.params->bad, 1u);
+  if (floor_hits) atomicAdd(&a.params->floor_hits, (unsigned long long)floor_hits);
   if (STAGE == 2 && a.fuse_rate) {
     double r = (double)rate_max, sp = (double)speed_max;
     for (int o = 16; o > 0; o >>= 1) {

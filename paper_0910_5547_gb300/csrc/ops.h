@@ -15,6 +15,7 @@ struct ChunkDesc;
 struct PhysParams {  // host copy of the physics constants
   double gamma, theta, ch_fixed;
   int llf;
+  double p_floor, glm_alpha;
 };
 
 struct OpsBase {

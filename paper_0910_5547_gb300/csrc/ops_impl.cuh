@@ -26,6 +26,8 @@ struct Ops final : OpsBase {
     ph.theta = (T)p.theta;
     ph.llf = p.llf;
     ph.ch = ph.ch2 = ph.half_inv_ch = T(0);
+    ph.efl = (T)(p.p_floor / (p.gamma - 1.0));
+    ph.glm_alpha = (T)p.glm_alpha;
     cudaFuncSetAttribute(stage_kernel<T, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem_bytes<T, NV>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -20,6 +20,8 @@ struct Phys {
   T ch2;       // ch^2
   T half_inv_ch;  // 1 / (2 ch)
   int llf;     // 1: the printed Sec. 4 flux with lambda_0; 0: two-wave HLL
+  T efl;       // p_floor / (gamma - 1): the specific internal energy floor is efl / rho
+  T glm_alpha; // GLM damping parameter (0 = off)
 };
 
 template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
@@ -83,14 +85,20 @@ __device__ __forceinline__ double min3(double a, double b, double c) { return dm
 __device__ __forceinline__ double max3(double a, double b, double c) { return dmax(dmax(a, b), c); }
 
 // Conserved -> reconstructed variables; returns false for rho <= 0, e <= 0 or NaN.
+// The specific internal energy is raised to the floor efl / rho (efl = 0: no
+// floor for a physical state); *hits (if given) counts where it acted.
 template <typename T, int NV>
-__device__ __forceinline__ bool cons_to_prim(const T* u, T* w) {
+__device__ __forceinline__ bool cons_to_prim(const T* u, T* w, T efl, int* hits = nullptr) {
   T rho = u[0];
   T r = drcp(rho);
   T vx = u[1] * r, vy = u[2] * r, vz = u[3] * r;
   T E = u[4];
   if (NV == 9) E = E - T(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
   T e = E * r - T(0.5) * (vx * vx + vy * vy + vz * vz);
+  const T ef = efl * r;
+  const bool low = e < ef;
+  if (hits) *hits += low ? 1 : 0;
+  e = low ? ef : e;
   w[0] = rho; w[1] = vx; w[2] = vy; w[3] = vz; w[4] = e;
   if (NV == 9) { w[5] = u[5]; w[6] = u[6]; w[7] = u[7]; w[8] = u[8]; }
   return (rho > T(0)) && (e > T(0));
@@ -223,7 +231,7 @@ __device__ __forceinline__ void face_flux_from_array(const T* base, int64_t vstr
     T u[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] = base[v * vstride + c1 + (q - 2) * step];
-    cons_to_prim<T, NV>(u, w[q]);
+    cons_to_prim<T, NV>(u, w[q], ph.efl);
   }
   T wl[NV], wr[NV];
 #pragma unroll

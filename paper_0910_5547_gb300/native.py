@@ -35,7 +35,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
-           "amr_get_patches", "amr_autotune", "amr_get_regrid_timing"]
+           "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -62,6 +62,8 @@ class amr_config(ctypes.Structure):
         ("max_level", ctypes.c_int),
         ("ref_ratio", ctypes.c_int),
         ("ch", ctypes.c_double),
+        ("p_floor", ctypes.c_double),
+        ("glm_alpha", ctypes.c_double),
         ("batched", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
@@ -129,6 +131,8 @@ def load():
     L.amr_autotune.restype = ctypes.c_int
     L.amr_get_regrid_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     L.amr_get_regrid_timing.restype = ctypes.c_int
+    L.amr_floor_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
+    L.amr_floor_count.restype = ctypes.c_int
     L.amr_get_patches.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -301,6 +305,13 @@ def amr_autotune(h) -> str:
     buf = ctypes.create_string_buffer(4096)
     _check(h, load().amr_autotune(h, buf, 4096))
     return buf.value.decode()
+
+
+def amr_floor_count(h) -> int:
+    """Interior primitive recoveries raised by the pressure floor since the last call."""
+    n = ctypes.c_longlong(0)
+    _check(h, load().amr_floor_count(h, ctypes.byref(n)))
+    return int(n.value)
 
 
 def amr_get_regrid_timing(h) -> dict:

@@ -22,7 +22,8 @@ class Solver:
     def __init__(self, patches: Sequence, state: Sequence[np.ndarray], *, nvar=5, precision="fp64",
                  gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(0,) * 6, max_level=None,
                  riemann="hll", ch=0.0, batched=True, use_graph=True, domain_lo=(0.0, 0.0, 0.0),
-                 domain_hi=(1.0, 1.0, 1.0), kind=N.AMR_STATE_PRIMITIVE, stream=None):
+                 domain_hi=(1.0, 1.0, 1.0), kind=N.AMR_STATE_PRIMITIVE, stream=None, p_floor=0.0,
+                 glm_alpha=0.0):
         self.patches = list(patches)
         self.nvar = nvar
         if max_level is None:
@@ -30,7 +31,8 @@ class Solver:
         self.cfg = N.amr_default_config(
             nvar=nvar, precision=N.AMR_FP32 if precision == "fp32" else N.AMR_FP64,
             riemann=N.AMR_LLF if riemann == "llf" else N.AMR_HLL, gamma=gamma, theta=theta, cfl=cfl,
-            base_n=base_n, bc=bc, max_level=max_level, ch=ch, batched=int(batched), use_graph=int(use_graph),
+            base_n=base_n, bc=bc, max_level=max_level, ch=ch, p_floor=p_floor, glm_alpha=glm_alpha,
+            batched=int(batched), use_graph=int(use_graph),
             domain_lo=domain_lo, domain_hi=domain_hi, cuda_stream=stream)
         self.h = N.amr_create(self.cfg)
         N.amr_set_patches(self.h, self.patches, state, kind)
@@ -57,6 +59,10 @@ class Solver:
 
     def step(self, dt: float = 0.0, sync: bool = True) -> float:
         return N.amr_step(self.h, dt, sync)
+
+    def floor_count(self) -> int:
+        """Interior cells (per stage) in which the pressure floor acted since the last call."""
+        return N.amr_floor_count(self.h)
 
     def cfl_dt(self) -> float:
         return N.amr_cfl_dt(self.h)
