@@ -192,6 +192,45 @@ def kelvin_helmholtz(N: int = 256, tile: int | None = 32, seed: int = 20091, amp
                    _fill(patches, (N, N, N), 5, fn), meta={"seed": seed})
 
 
+def mhd_turbulence(N: int = 128, tile: int | None = None, mach: float = 10.0, gamma: float = 1.001,
+                   beta: float = 0.1, slope: float = -2.0, seed: int = 20096) -> Problem:
+    """Decaying MHD turbulence (Sec. 7): uniform density rho = 1 and sound speed 1
+    (p = 1 / gamma), an isotropic random velocity field with the Burgers-like energy
+    spectrum E(k) ~ k^slope (slope -2; E summed over shells |k| = k, i.e. mode power
+    |v_k|^2 ~ k^(slope - 2)) for 1 <= |k| <= N/2 with seeded random phases, each
+    component drawn independently, scaled to an rms Mach number `mach`; a uniform
+    field B = (B0, 0, 0) with plasma beta 2 p / B0^2 = beta (Heaviside units, energy
+    B^2/2), psi = 0; periodic, nvar = 9."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = np.fft.fftfreq(N) * N
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(kk)
+    band = (kk >= 1.0) & (kk <= N / 2)
+    amp[band] = kk[band] ** ((slope - 2.0) / 2.0)
+    vel = []
+    for _ in range(3):
+        coef = amp * (rng.standard_normal(kk.shape) + 1j * rng.standard_normal(kk.shape))
+        vel.append(np.real(np.fft.ifftn(coef)))      # [z][y][x]
+    vel = np.array(vel)
+    p0 = 1.0 / gamma
+    vel *= mach / np.sqrt(np.mean(np.sum(vel * vel, axis=0)))
+    b0 = np.sqrt(2.0 * p0 / beta)
+    t = tile or N
+    patches = uniform_patches((N, N, N), (t, t, t))
+
+    def fn(p, w, x, y, z):
+        sl = (slice(p.lo[2], p.lo[2] + p.n[2]), slice(p.lo[1], p.lo[1] + p.n[1]), slice(p.lo[0], p.lo[0] + p.n[0]))
+        w[0] = 1.0
+        for d in range(3):
+            w[1 + d] = vel[d][sl]
+        w[4] = p0
+        w[5] = b0
+
+    return Problem("mhd_turbulence", 9, gamma, (N, N, N), (PERIODIC,) * 6, patches, _fill(patches, (N, N, N), 9, fn),
+                   meta={"seed": seed, "mach": mach, "beta": beta})
+
+
 def nested_cubes(base: int, sides: Sequence[int], seed: int, pmin=8, pmax=32) -> List[Patch]:
     """Level 0 = whole box tiled by seeded 8..32 patches; level l >= 1 = a centred cube of
     `sides[l-1]` level-l cells, tiled the same way."""

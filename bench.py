@@ -89,6 +89,20 @@ def stage_traffic():
     return None
 
 
+def turbulence_diagnostics(packed, n, gamma):
+    """Mean Mach number |v| / c_s, magnetic energy sum B^2/2 dV and kinetic energy of a
+    single-patch 9-variable state (unit box)."""
+    import numpy as np
+    u = packed.reshape(9, n, n, n)
+    rho = u[0]
+    v2 = (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / rho ** 2
+    b2 = u[5] ** 2 + u[6] ** 2 + u[7] ** 2
+    p = (gamma - 1.0) * (u[4] - 0.5 * rho * v2 - 0.5 * b2)
+    mach = float(np.mean(np.sqrt(v2 / (gamma * p / rho))))
+    dv = 1.0 / n ** 3
+    return mach, float(0.5 * b2.sum() * dv), float(0.5 * (rho * v2).sum() * dv)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -397,6 +411,26 @@ def main():
         mhd = {"fp32_uniform_192": rate(ot, "fp32", True, True, max(3, args.steps // 4)) * (192 ** 3) / cells}
         del ot
         mhd["fp32_over_hydro_fp32_per_cell"] = mhd["fp32_uniform_192"] / value
+        # Sec. 7 decaying turbulence: 128^3, Mach 10, gamma 1.001, beta 0.1, with the
+        # paper's two diagnostics (mean Mach number, magnetic energy) around the timed steps
+        turb = ai.mhd_turbulence(N=128)
+        so = make_solver(turb, "fp32", True, True, stream)
+        so.autotune()
+        d0 = turbulence_diagnostics(so.state_all(), 128, turb.gamma)
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        kt = max(3, args.steps // 4)
+        tt = timed_steps(torch, so, stream, kt)
+        so.check()
+        d1 = turbulence_diagnostics(so.state_all(), 128, turb.gamma)
+        so.close()
+        mhd["turbulence_128"] = {"value": ws * 128 ** 3 * kt / max_over_ranks(tt), "unit": UNIT, "steps": kt,
+                                 "mean_mach": [d0[0], d1[0]], "magnetic_energy": [d0[1], d1[1]],
+                                 "kinetic_energy": [d0[2], d1[2]],
+                                 "workload": "decaying MHD turbulence 128^3, Mach 10, gamma 1.001, beta 0.1, "
+                                             "P(k) ~ k^-2 (seeded); diagnostics before and after the "
+                                             f"{kt + 2} steps"}
+        del turb
         mhd["amr_3level"] = amr_rates(ai.orszag_tang(amr_sides=(96, 96), amr_base=96),
                                       "GLM-MHD Orszag-Tang, 3 levels, base 96^3", fp64_plain_steps=0)
         mhd["unit"] = UNIT

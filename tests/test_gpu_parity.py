@@ -235,3 +235,28 @@ def test_autotune_keeps_results_and_reports_candidates(precision):
         s.step()
     s.check()
     assert_parity(s.all_cons(), o.all_cons(), pb.patches, precision, "autotuned")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mhd_turbulence_parity(precision):
+    """Sec. 7 decaying MHD turbulence (Mach 10, gamma 1.001, beta 0.1) at 32^3 in 16^3
+    patches, three CFL steps."""
+    pb = ai.mhd_turbulence(N=32, tile=16)
+    o, s = run_pair(pb, precision, steps=3)
+    assert_parity(s.all_cons(), o.all_cons(), pb.patches, precision, "mhd-turbulence")
+
+
+def test_mhd_turbulence_decays_in_one_crossing_time():
+    """Sec. 7: a significant fraction of the turbulent kinetic energy decays within one
+    dynamical (flow crossing) time L / v_rms = 0.1; FP32 batched at 32^3."""
+    pb = ai.mhd_turbulence(N=32, tile=16)
+    s = Solver.from_problem(pb, precision="fp32")
+
+    def kinetic():
+        return sum(float(np.sum(0.5 * (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / u[0])) for u in s.all_cons())
+
+    k0 = kinetic()
+    n = s.run_to(0.1)
+    s.check()
+    assert n > 50
+    assert kinetic() < 0.6 * k0

@@ -228,3 +228,29 @@ def test_mhd_periodic_conservation_and_cleaning_speed():
     assert np.all(np.abs(t1 - t0) <= 1e-14 * np.abs(t0).max() + 1e-15), (t1 - t0)
     # cleaning speed = the largest signal speed |v_d| + c_f,d at the step start (> sound + flow)
     assert o.last_ch() > 1.0
+
+
+def test_mhd_turbulence_recipe():
+    """Sec. 7 decaying-turbulence set-up: uniform rho, sound speed 1, rms Mach number
+    exactly the requested one, uniform B_x with the requested plasma beta, psi = 0,
+    and a Burgers-like velocity spectrum: the energy summed over shells falls as k^-2."""
+    N = 32
+    pb = ai.mhd_turbulence(N=N, tile=16, mach=10.0, gamma=1.001, beta=0.1, seed=3)
+    v2 = sum(float(np.sum(w[1] ** 2 + w[2] ** 2 + w[3] ** 2)) for w in pb.prim) / N ** 3
+    p0 = 1.0 / 1.001
+    assert math.isclose(math.sqrt(v2) / math.sqrt(1.001 * p0), 10.0, rel_tol=1e-12)
+    for w in pb.prim:
+        assert np.all(w[0] == 1.0) and np.allclose(w[4], p0) and np.all(w[6:] == 0.0)
+        assert np.allclose(2.0 * w[4] / w[5] ** 2, 0.1)
+    vx = np.zeros((N, N, N))
+    for p, w in zip(pb.patches, pb.prim):
+        vx[p.lo[2]:p.lo[2] + p.n[2], p.lo[1]:p.lo[1] + p.n[1], p.lo[0]:p.lo[0] + p.n[0]] = w[1]
+    F = np.abs(np.fft.fftn(vx)) ** 2
+    k = np.fft.fftfreq(N) * N
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    ks = np.arange(2, 13)
+    pw = [F[(kk > s - 0.5) & (kk < s + 0.5)].sum() for s in ks]
+    slope = np.polyfit(np.log(ks), np.log(pw), 1)[0]
+    assert -2.4 < slope < -1.6, slope
+    assert F[kk > N / 2 + 1].max() < 1e-20 * F.max()    # no power beyond the band
