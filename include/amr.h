@@ -30,6 +30,8 @@
 #ifndef AMR_GB300_H
 #define AMR_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -72,6 +74,15 @@ typedef struct {
   int batched;           /* 1: one launch per kernel per level; 0: one launch per patch ("plain") */
   int use_graph;         /* 1: capture a coarse step as a CUDA graph and replay it */
   void* cuda_stream;     /* cudaStream_t to run on; NULL: the library creates its own */
+  /* Device memory: when dev_alloc and dev_free are both set, every device buffer of
+   * the handle comes from dev_alloc(bytes, stream, alloc_ctx) (NULL = failure, the call
+   * returns AMR_ERR_CUDA) and goes back through dev_free(ptr, stream, alloc_ctx), both
+   * ordered on the handle's stream (e.g. a framework's caching allocator); otherwise
+   * the library uses cudaMallocAsync / cudaFreeAsync on that stream.  All of it is
+   * released by amr_destroy (and old buffers by amr_set_patches / amr_regrid). */
+  void* (*dev_alloc)(size_t bytes, void* stream, void* alloc_ctx);
+  void (*dev_free)(void* ptr, void* stream, void* alloc_ctx);
+  void* alloc_ctx;
 } amr_config;
 
 /* One patch: `n` interior cells per axis starting at `lo` in the index space of

@@ -162,6 +162,23 @@ cudaEvent_t next_event(amr_handle* h, int* idx) {
     h->counting += 1;                                              \
   } while (0)
 
+// Device memory of a handle: the caller's allocator (dev_alloc / dev_free) or
+// stream-ordered cudaMallocAsync / cudaFreeAsync on the handle's stream.
+cudaError_t dmalloc(amr_handle* h, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  if (h->cfg.dev_alloc && h->cfg.dev_free) {
+    *p = h->cfg.dev_alloc(bytes, h->stream, h->cfg.alloc_ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, h->stream);
+}
+
+void dfree(amr_handle* h, void* p) {
+  if (!p) return;
+  if (h->cfg.dev_alloc && h->cfg.dev_free) h->cfg.dev_free(p, h->stream, h->cfg.alloc_ctx);
+  else cudaFreeAsync(p, h->stream);
+}
+
 void free_device(amr_handle* h) {
   for (int g = 0; g < 4; ++g) {
     if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
@@ -170,8 +187,7 @@ void free_device(amr_handle* h) {
   h->rates_valid = false;
   void* ptrs[] = {h->U, h->U1, h->Uold, h->tile, h->packed, h->partial, h->totals, h->regs, h->tables,
                   h->items_dev};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dfree(h, p);
   h->items_dev = nullptr;
   h->U = h->U1 = h->Uold = h->tile = nullptr;
   h->packed = h->partial = h->totals = h->regs = nullptr;
@@ -383,10 +399,10 @@ amr_status upload_items(amr_handle* h) {
     first.push_back(all.size());
     all.insert(all.end(), L.items.begin(), L.items.end());
   }
-  if (h->items_dev) cudaFree(h->items_dev);
+  dfree(h, h->items_dev);
   h->items_dev = nullptr;
   void* p = nullptr;
-  CK(cudaMalloc(&p, std::max<size_t>(all.size(), 1) * sizeof(StageItem)));
+  CK(dmalloc(h, &p, std::max<size_t>(all.size(), 1) * sizeof(StageItem)));
   h->items_dev = static_cast<StageItem*>(p);
   CK(cudaMemcpyAsync(h->items_dev, all.data(), all.size() * sizeof(StageItem), cudaMemcpyHostToDevice, h->stream));
   for (size_t l = 0; l < h->dl.size(); ++l) {
@@ -430,10 +446,9 @@ DeviceBufs detach(amr_handle* h) {
   return b;
 }
 
-void free_bufs(DeviceBufs& b) {
+void free_bufs(amr_handle* h, DeviceBufs& b) {
   void* ptrs[] = {b.U, b.U1, b.Uold, b.tile, b.packed, b.partial, b.totals, b.regs, b.tables, b.items};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dfree(h, p);
   b = DeviceBufs();
 }
 
@@ -485,7 +500,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     lo[l].rf = put(buf, L.reflux_first);
   }
   void* p = nullptr;
-  CK(cudaMalloc(&p, buf.size()));
+  CK(dmalloc(h, &p, buf.size()));
   h->tables = static_cast<unsigned char*>(p);
   CK(cudaMemcpyAsync(h->tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
   h->d_desc = reinterpret_cast<const PatchDesc*>(h->tables + o_desc);
@@ -494,23 +509,23 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   h->d_cover_first = reinterpret_cast<const int*>(h->tables + o_cover_first);
   h->d_packed_off = reinterpret_cast<const int64_t*>(h->tables + o_packed_off);
   h->d_level_vol = reinterpret_cast<const double*>(h->tables + o_lvol);
-  CK(cudaMalloc(&h->U, pl.arena_elems * es));
-  CK(cudaMalloc(&h->U1, pl.arena_elems * es));
+  CK(dmalloc(h, &h->U, pl.arena_elems * es));
+  CK(dmalloc(h, &h->U1, pl.arena_elems * es));
   CK(cudaMemsetAsync(h->U, 0, pl.arena_elems * es, h->stream));
   CK(cudaMemsetAsync(h->U1, 0, pl.arena_elems * es, h->stream));
   if (nlev > 1) {
-    CK(cudaMalloc(&h->Uold, pl.arena_elems * es));
+    CK(dmalloc(h, &h->Uold, pl.arena_elems * es));
     CK(cudaMemsetAsync(h->Uold, 0, pl.arena_elems * es, h->stream));
-    CK(cudaMalloc(&h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
+    CK(dmalloc(h, &h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
   }
-  CK(cudaMalloc(&p, std::max<int64_t>(pl.packed_elems, 1) * sizeof(double)));
+  CK(dmalloc(h, &p, std::max<int64_t>(pl.packed_elems, 1) * sizeof(double)));
   h->packed = static_cast<double*>(p);
-  CK(cudaMalloc(&p, (size_t)h->nchunk * nv * sizeof(double)));
+  CK(dmalloc(h, &p, (size_t)h->nchunk * nv * sizeof(double)));
   h->partial = static_cast<double*>(p);
-  CK(cudaMalloc(&p, 16 * sizeof(double)));
+  CK(dmalloc(h, &p, 16 * sizeof(double)));
   h->totals = static_cast<double*>(p);
   if (nregd) {
-    CK(cudaMalloc(&p, nregd * sizeof(double)));
+    CK(dmalloc(h, &p, nregd * sizeof(double)));
     h->regs = static_cast<double*>(p);
     CK(cudaMemsetAsync(h->regs, 0, nregd * sizeof(double), h->stream));
   }
@@ -611,8 +626,8 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
   }
   h->ops = make_ops(*cfg);
   void* p = nullptr;
-  if (cudaMalloc(&p, sizeof(StepParams)) != cudaSuccess) {
-    g_global_err = "cudaMalloc of step parameters failed";
+  if (dmalloc(h, &p, sizeof(StepParams)) != cudaSuccess) {
+    g_global_err = "allocation of the step parameters failed";
     amr_destroy(h);
     return AMR_ERR_CUDA;
   }
@@ -669,7 +684,7 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   if (st != AMR_OK) return fail(h, st, msg);
   CK(cudaStreamSynchronize(h->stream));
   DeviceBufs old = detach(h);
-  free_bufs(old);
+  free_bufs(h, old);
   st = install_plan(h, std::move(plan));
   if (st != AMR_OK) return st;
   Plan& pl = h->plan;
@@ -728,14 +743,14 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
   // 2. density-gradient flags, one byte per interior cell
   const size_t ncell = (size_t)(op.packed_elems / nv);
   unsigned char* d_flags = nullptr;
-  CK(cudaMalloc(&d_flags, std::max<size_t>(ncell, 1)));
+  CK(dmalloc(h, reinterpret_cast<void**>(&d_flags), std::max<size_t>(ncell, 1)));
   cudaError_t fe = h->ops->flag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, rp.threshold,
                                 d_flags);
   std::vector<unsigned char> hflags(ncell);
   if (fe == cudaSuccess)
     fe = cudaMemcpyAsync(hflags.data(), d_flags, ncell, cudaMemcpyDeviceToHost, h->stream);
   if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
-  cudaFree(d_flags);
+  dfree(h, d_flags);
   CK(fe);
   h->launches += h->counting + 1;
   std::vector<std::vector<uint8_t>> flags(op.patches.size());
@@ -769,14 +784,14 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
   DeviceBufs old = detach(h);
   st = install_plan(h, std::move(np));
   if (st != AMR_OK) {
-    free_bufs(old);
+    free_bufs(h, old);
     return st;
   }
   std::vector<unsigned char> buf;
   std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
   cudaError_t ei = cudaStreamSynchronize(h->stream);   // uploads of the new tables done
   if (ei != cudaSuccess) {
-    free_bufs(old);
+    free_bufs(h, old);
     CK(ei);
   }
   lap(AMR_RG_INSTALL);
@@ -785,7 +800,7 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
     o_fresh[l] = put(buf, fill.fresh[l]);
   }
   unsigned char* d_fill = nullptr;
-  cudaError_t e = cudaMalloc(&d_fill, std::max<size_t>(buf.size(), 1));
+  cudaError_t e = dmalloc(h, reinterpret_cast<void**>(&d_fill), std::max<size_t>(buf.size(), 1));
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_fill, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && keep_end > 0)
     e = cudaMemcpyAsync(h->U, old.U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
@@ -805,8 +820,8 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
     h->launches += 3;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d_fill);
-  free_bufs(old);
+  dfree(h, d_fill);
+  free_bufs(h, old);
   CK(e);
   lap(AMR_RG_FILL);
   h->ready = true;
@@ -1062,7 +1077,8 @@ void amr_destroy(amr_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_device(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-  if (h->params) cudaFree(h->params);
+  dfree(h, h->params);
+  if (h->stream) cudaStreamSynchronize(h->stream);   // stream-ordered frees done
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h->ops;
   delete h;

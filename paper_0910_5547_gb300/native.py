@@ -47,6 +47,11 @@ class AmrError(RuntimeError):
         self.msg = msg
 
 
+# Device allocator callbacks of amr_config (dev_alloc / dev_free).
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class amr_config(ctypes.Structure):
     _fields_ = [
         ("nvar", ctypes.c_int),
@@ -67,6 +72,9 @@ class amr_config(ctypes.Structure):
         ("batched", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
+        ("dev_alloc", ALLOC_FN),
+        ("dev_free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
     ]
 
 
@@ -164,6 +172,22 @@ def amr_default_config(**overrides) -> amr_config:
         else:
             setattr(c, k, v)
     return c
+
+
+def torch_allocator():
+    """(dev_alloc, dev_free) callbacks that take the handle's device memory from
+    PyTorch's caching allocator on the handle's stream.  Keep the returned pair alive
+    as long as the handle."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        s = torch.cuda.ExternalStream(stream) if stream else None
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=s))
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
 
 
 def make_patches(patches: Sequence) -> ctypes.Array:

@@ -96,3 +96,27 @@ def test_bad_config_is_rejected(field, value):
 def test_unpaired_periodic_faces_rejected():
     st, msg = N.amr_validate_patches(cfg(bc=(1, 0, 0, 0, 0, 0)), [P(0, (0, 0, 0), (32, 32, 32))])
     assert st == N.AMR_ERR_ARG and "periodic" in msg
+
+
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """The ctypes amr_config has the size and field offsets of the C struct in
+    include/amr.h (compiled here with the host C compiler)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in N.amr_config._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"amr.h\"\nint main(void) {\n"
+                   "  printf(\"%zu\\n\", sizeof(amr_config));\n"
+                   + "".join(f"  printf(\"%zu\\n\", offsetof(amr_config, {f}));\n" for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(N.amr_config)
+    assert got[1:] == [getattr(N.amr_config, f).offset for f in fields]

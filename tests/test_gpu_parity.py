@@ -260,3 +260,29 @@ def test_mhd_turbulence_decays_in_one_crossing_time():
     s.check()
     assert n > 50
     assert kinetic() < 0.6 * k0
+
+
+def test_torch_allocator_path_is_bitwise_and_accounted():
+    """Device memory taken from PyTorch's caching allocator (amr_config.dev_alloc /
+    dev_free): the same bits as the library's own stream-ordered allocations, the
+    arena shows up in torch's accounting, and is returned by close() and by a regrid."""
+    import torch
+    pb = ai.random_smooth(three_level_seeded(), (32,) * 3, seed=4)
+    base = torch.cuda.memory_allocated()
+    s_t = Solver.from_problem(pb, precision="fp32", allocator="torch")
+    held = torch.cuda.memory_allocated() - base
+    cells = sum(p.n[0] * p.n[1] * p.n[2] for p in pb.patches)
+    assert held > 2 * 5 * 4 * cells          # at least U and U1
+    s_d = Solver.from_problem(pb, precision="fp32")
+    for _ in range(2):
+        s_t.step(0.0)
+        s_d.step(0.0)
+    for a, b in zip(s_t.all_cons(), s_d.all_cons()):
+        assert np.array_equal(a, b)
+    s_t.regrid(threshold=0.05, buffer=2, block=4, max_patch=16)
+    s_t.step(0.0)
+    s_t.check()
+    s_t.close()
+    s_d.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
