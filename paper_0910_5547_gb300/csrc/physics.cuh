@@ -26,11 +26,21 @@ struct Phys {
 
 template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
 template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
-__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+// FP32: the approximate PTX square root and reciprocal with subnormals flushed
+// (no FP32 quantity of the method is subnormal), one instruction each.
+__device__ __forceinline__ float dsqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double dabs(double x) { return fabs(x); }
-__device__ __forceinline__ float drcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float drcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double drcp(double x) { return 1.0 / x; }
 
 // Half of the limited slope of cell i from (w_{i-1}, w_i, w_{i+1}):
