@@ -30,10 +30,13 @@ namespace amr {
 // Shared memory of a stage CTA, per variable: the primitive plane with its
 // face halo, (wy + 4) x (wx + 4) <= kPlaneMax cells; four face-state arrays
 // (left/right states of x faces, (wx + 2) wy <= kStateMax, and of y faces,
-// (wy + 2) wx <= kStateMax); and the x/y face fluxes, wy (wx + 1) + (wy + 1) wx
-// = 2 wx wy + wx + wy <= kFaceMax.  The planner keeps wx * wy <= 256, wx <= 32,
-// 4 (wx + wy) <= 256 and (wx + 4)(wy + 4) <= kPlaneMax.
-constexpr int kFaceMax = 2 * kStageThreads + 88;
+// (wy + 2) wx <= kStateMax); and the x face fluxes, wy (wx + 1) <= kFaceX, and
+// y face fluxes, (wy + 1) wx <= kFaceY.  The planner keeps wx * wy <= 256,
+// wx <= 32, 4 (wx + wy) <= 256 (so wy <= 63) and (wx + 4)(wy + 4) <= kPlaneMax.
+// Fixed strides keep every shared-memory address an immediate offset.
+constexpr int kFaceX = kStageThreads + 64;
+constexpr int kFaceY = kStageThreads + 32;
+constexpr int kFaceMax = kFaceX + kFaceY;
 constexpr int kStateMax = kStageThreads + 128;
 
 // FP32 Euler stage kernels also stage their conserved inputs through shared
@@ -185,9 +188,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     const int wx = it.wx, wy = it.wy, wz = it.wz;
     const int sw = wx + 4;
     const int ncol = wx * wy;
-    const int nfx = wy * (wx + 1);
-    const int nfy = wx * (wy + 1);
-    T* FY = FX + NV * nfx;
+    constexpr int nfx = kFaceX, nfy = kFaceY;
+    T* FY = FX + NV * kFaceX;
     const bool active = t < ncol;
     const int tx = active ? t % wx : 0, ty = active ? t / wx : 0;
     const T* Ub = a.Uin + P.off;
