@@ -49,12 +49,16 @@ __global__ void noalloc_finalize(StepParams* p, double cfl, double ch_fixed, int
 
 size_t align256(size_t a) { return (a + 255) / 256 * 256; }
 
+// CTAs per SM of the default stage-kernel variant (its shared-memory layout depends on it)
+template <typename T, int NV>
+constexpr int kDefCtas = (sizeof(T) == 4 && NV == 5) ? 2 : 1;
+
 template <typename T, int NV>
 void set_smem_attributes() {
   cudaFuncSetAttribute(stage_kernel<T, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)stage_smem_bytes<T, NV>());
+                       (int)stage_smem_bytes<T, NV, kDefCtas<T, NV>>());
   cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)stage_smem_bytes<T, NV>());
+                       (int)stage_smem_bytes<T, NV, kDefCtas<T, NV>>());
 }
 
 // One-time set-up per device (the device must be current): resolve the device
@@ -161,7 +165,7 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   a.ph = ph;
   const int nseg = (int)L.ghost.size();
   const int gseg = nseg < 65535 ? nseg : 65535;
-  const size_t sm = stage_smem_bytes<T, NV>();
+  const size_t sm = stage_smem_bytes<T, NV, kDefCtas<T, NV>>();
   copy_kernel<T, NV, false><<<gseg, 256, 0, s>>>(ghost, nseg, desc, U, U, nullptr, T(0));
   a.Uin = U;
   a.Uout = U1;

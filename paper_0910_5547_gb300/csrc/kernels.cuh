@@ -44,15 +44,27 @@ constexpr int kStateMax = kStageThreads + 128;
 // columns and halo cells) and, in stage 2, a ring of two planes of U^n (own
 // columns).  The other variants load them into registers (their shared memory
 // has no room for the rings at the occupancy they run at).
-template <typename T, int NV>
-__host__ __device__ constexpr bool stage_async() { return NV == 5 && sizeof(T) == 4; }
 constexpr int kRing = 4;
 constexpr int kRingN = 2;
 
 template <typename T, int NV>
+__host__ __device__ constexpr size_t stage_smem_base() {
+  return sizeof(T) * NV * (kPlaneMax + 4 * kStateMax + kFaceMax);
+}
+template <typename T, int NV>
+__host__ __device__ constexpr size_t stage_smem_rings() {
+  return sizeof(T) * NV * (kRing * kPlaneMax + kRingN * kStageThreads);
+}
+// The rings are used where the CTAs per SM a variant asks for (MINB) still fit
+// in the SM's 228 KB of shared memory (1 KB reserved per CTA).
+template <typename T, int NV, int MINB>
+__host__ __device__ constexpr bool stage_async() {
+  return NV == 5 && sizeof(T) == 4 &&
+         (size_t)MINB * (stage_smem_base<T, NV>() + stage_smem_rings<T, NV>() + 1024) <= (size_t)228 * 1024;
+}
+template <typename T, int NV, int MINB = 2>
 constexpr size_t stage_smem_bytes() {
-  return sizeof(T) * NV *
-         (kPlaneMax + 4 * kStateMax + kFaceMax + (stage_async<T, NV>() ? kRing * kPlaneMax + kRingN * kStageThreads : 0));
+  return stage_smem_base<T, NV>() + (stage_async<T, NV, MINB>() ? stage_smem_rings<T, NV>() : 0);
 }
 
 // Asynchronous global -> shared copy of one element (sm_80+ cp.async).
@@ -159,7 +171,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   T* YL = XR + NV * kStateMax;
   T* YR = YL + NV * kStateMax;
   T* FX = YR + NV * kStateMax;
-  constexpr bool kAsync = stage_async<T, NV>();
+  constexpr bool kAsync = stage_async<T, NV, MINB>();
   // ring of stage-input planes: plane p of the item lives in slot p & 3, [slot][var][plane cell];
   // ring of U^n planes (stage 2): plane p in slot p & 1, [slot][var][thread].  Each thread
   // reads back only the cells it copied itself (own column, own halo cell).

@@ -28,19 +28,19 @@ struct Ops final : OpsBase {
     ph.ch = ph.ch2 = ph.half_inv_ch = T(0);
     ph.efl = (T)(p.p_floor / (p.gamma - 1.0));
     ph.glm_alpha = (T)p.glm_alpha;
-    cudaFuncSetAttribute(stage_kernel<T, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV>());
-    cudaFuncSetAttribute(stage_kernel<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV>());
+    cudaFuncSetAttribute(stage_kernel<T, NV, 1, kDef>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV, kDef>());
+    cudaFuncSetAttribute(stage_kernel<T, NV, 2, kDef>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV, kDef>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 1, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV>());
+                         (int)stage_smem_bytes<T, NV, 2 * kDef>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 2, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV>());
+                         (int)stage_smem_bytes<T, NV, 2 * kDef>());
     if (kHasAlt) {
       cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)stage_smem_bytes<T, NV>());
+                           (int)stage_smem_bytes<T, NV, kAlt>());
       cudaFuncSetAttribute(stage_kernel<T, NV, 2, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)stage_smem_bytes<T, NV>());
+                           (int)stage_smem_bytes<T, NV, kAlt>());
     }
   }
 
@@ -72,16 +72,18 @@ struct Ops final : OpsBase {
     a.fuse_rate = fuse_rate;
     a.ph = ph;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
-    const size_t sm = stage_smem_bytes<T, NV>();
     if (nt == 128) {
+      const size_t sm = stage_smem_bytes<T, NV, 2 * kDef>();
       if (stage == 1) stage_kernel<T, NV, 1, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
       else stage_kernel<T, NV, 2, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
     } else if (kHasAlt && occ == kAlt) {
+      const size_t sm = stage_smem_bytes<T, NV, kAlt>();
       if (stage == 1) stage_kernel<T, NV, 1, kAlt><<<g, kStageThreads, sm, s>>>(a);
       else stage_kernel<T, NV, 2, kAlt><<<g, kStageThreads, sm, s>>>(a);
     } else {
-      if (stage == 1) stage_kernel<T, NV, 1><<<g, kStageThreads, sm, s>>>(a);
-      else stage_kernel<T, NV, 2><<<g, kStageThreads, sm, s>>>(a);
+      const size_t sm = stage_smem_bytes<T, NV, kDef>();
+      if (stage == 1) stage_kernel<T, NV, 1, kDef><<<g, kStageThreads, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, kDef><<<g, kStageThreads, sm, s>>>(a);
     }
     return cudaGetLastError();
   }
