@@ -257,6 +257,9 @@ struct orc_sim {
   oreg** reg; int* nreg;            /* per level l >= 1 */
   double ch_used;
   int err;
+  orc_regrid_hook hook;    /* regrid after level steps (NULL: none) */
+  void* hook_ctx;
+  int hook_max_level;
 };
 
 static size_t gidx(const opatch* p, int i, int j, int k) { /* ghost-extended local index */
@@ -800,6 +803,10 @@ static int advance_level(orc_sim* s, int l, double dt, double alpha0) {
     restrict_level(s, l + 1);
     reflux_level(s, l + 1);
   }
+  /* rebuild the finer levels after this level's step (the step of the parent
+   * has reached fraction alpha0 + 1/2 of its own step) */
+  if (s->hook && l <= s->hook_max_level && l < s->cfg.max_level)
+    if (s->hook(s->hook_ctx, l, l == 0 ? 1.0 : alpha0 + 0.5)) return -1;
   return 0;
 }
 
@@ -927,6 +934,36 @@ int orc_flags(orc_sim* s, double threshold, unsigned char* out) {
   return 0;
 }
 
+void orc_set_regrid_hook(orc_sim* s, int max_level, orc_regrid_hook hook, void* ctx) {
+  s->hook = hook;
+  s->hook_ctx = ctx;
+  s->hook_max_level = max_level;
+}
+
+int orc_flags_at(orc_sim* s, double threshold, int level, double alpha, unsigned char* out) {
+  if (level < 0 || level >= s->nlev) return -1;
+  if (fill_ghosts_level(s, level, 0, level == 0 ? 1.0 : alpha)) return -1;
+  for (int l = level + 1; l < s->nlev; ++l)
+    if (fill_ghosts_level(s, l, 0, 1.0)) return -1;
+  size_t o = 0;
+  for (int pi = 0; pi < s->np; ++pi) {
+    opatch* p = &s->P[pi];
+    const double* R = p->U;
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i) {
+          if (p->level < level) { out[o++] = 0; continue; }
+          double rho = R[gidx(p, i, j, k)];
+          double g = 0.0, d;
+          d = fabs(R[gidx(p, i + 1, j, k)] - R[gidx(p, i - 1, j, k)]); if (d > g) g = d;
+          d = fabs(R[gidx(p, i, j + 1, k)] - R[gidx(p, i, j - 1, k)]); if (d > g) g = d;
+          d = fabs(R[gidx(p, i, j, k + 1)] - R[gidx(p, i, j, k - 1)]); if (d > g) g = d;
+          out[o++] = (g / (2.0 * rho) > threshold) ? 1 : 0;
+        }
+  }
+  return 0;
+}
+
 orc_sim* orc_regrid_fill(orc_sim* old, int npatch, const orc_patch* patches, int keep_level) {
   orc_sim* s = orc_create(&old->cfg, npatch, patches);
   if (!s) return NULL;
@@ -963,3 +1000,34 @@ orc_sim* orc_regrid_fill(orc_sim* old, int npatch, const orc_patch* patches, int
   return s;
 }
 
+
+int orc_regrid_inplace(orc_sim* s, int npatch, const orc_patch* patches, int keep_level) {
+  orc_sim* n = orc_regrid_fill(s, npatch, patches, keep_level);
+  if (!n) return -1;
+  const int V = s->V;
+  /* kept levels: same patches in the same order, same register faces */
+  for (int l = 0; l <= keep_level && l < s->nlev; ++l) {
+    if (l >= n->nlev || n->lev_count[l] != s->lev_count[l]) { orc_destroy(n); return -1; }
+    for (int pi = s->lev_first[l]; pi < s->lev_first[l] + s->lev_count[l]; ++pi) {
+      const opatch* a = &s->P[pi];
+      opatch* b = &n->P[pi];
+      memcpy(b->Uold, a->Uold, (size_t)a->n[0] * a->n[1] * a->n[2] * V * sizeof(double));
+    }
+    if (l >= 1) {
+      if (n->nreg[l] != s->nreg[l]) { orc_destroy(n); return -1; }
+      for (int e = 0; e < s->nreg[l]; ++e)
+        for (int v = 0; v < V; ++v) {
+          n->reg[l][e].Rc[v] = s->reg[l][e].Rc[v];
+          n->reg[l][e].Rf[v] = s->reg[l][e].Rf[v];
+        }
+    }
+  }
+  n->hook = s->hook;
+  n->hook_ctx = s->hook_ctx;
+  n->hook_max_level = s->hook_max_level;
+  orc_sim tmp = *s;
+  *s = *n;
+  *n = tmp;
+  orc_destroy(n);
+  return 0;
+}

@@ -87,6 +87,25 @@ int orc_save_old(orc_sim* s, int level);
 int orc_flags(orc_sim* s, double threshold, unsigned char* out);
 orc_sim* orc_regrid_fill(orc_sim* old, int npatch, const orc_patch* patches, int keep_level);
 
+/* ---- regrid in the middle of a coarse step (Sec. 3: after each step of a level,
+ * the finer levels are rebuilt) ----
+ * orc_set_regrid_hook: during orc_step, after every completed step of a level
+ * l <= max_level (its own children advanced, restricted and refluxed) call
+ * hook(ctx, l, alpha) with alpha the time fraction of l's parent step reached
+ * (0.5 or 1; 1 for level 0); a non-zero return aborts the step.  hook NULL
+ * removes it.
+ * orc_flags_at: the flags of orc_flags at that moment: face ghosts of level l
+ * from its parent at fraction alpha, of the finer levels at fraction 1, without
+ * touching the saved old-time states; only levels >= l are meaningful.
+ * orc_regrid_inplace: replace the hierarchy of `s` by `patches` (levels <= keep
+ * unchanged, finer levels filled as by orc_regrid_fill), keeping the old-time
+ * states and flux registers of the kept levels so the step can continue.
+ * Returns 0 or -1. */
+typedef int (*orc_regrid_hook)(void* ctx, int level, double alpha);
+void orc_set_regrid_hook(orc_sim* s, int max_level, orc_regrid_hook hook, void* ctx);
+int orc_flags_at(orc_sim* s, double threshold, int level, double alpha, unsigned char* out);
+int orc_regrid_inplace(orc_sim* s, int npatch, const orc_patch* patches, int keep_level);
+
 /* ---- point functions, exposed for unit pins ---- */
 double orc_minmod3(double a, double b, double c);
 double orc_minmod2(double a, double b);

@@ -203,3 +203,65 @@ def regrid(o: Oracle, threshold=0.3, buffer=2, block=4, max_patch=32, min_level=
     new.patches = newp
     new._h = h
     return new
+
+
+def flags_at(o: Oracle, threshold: float, level: int, alpha: float) -> List[np.ndarray]:
+    """Flags in the middle of a coarse step, after a step of `level` (see orc_flags_at)."""
+    total = sum(p.n[0] * p.n[1] * p.n[2] for p in o.patches)
+    out = np.zeros(total, dtype=np.uint8)
+    L = lib()
+    L.orc_flags_at.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                               ctypes.POINTER(ctypes.c_ubyte)]
+    L.orc_flags_at.restype = ctypes.c_int
+    if L.orc_flags_at(o._h, threshold, level, alpha, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))) != 0:
+        raise RuntimeError("oracle flags failed")
+    res, k = [], 0
+    for p in o.patches:
+        n = p.n[0] * p.n[1] * p.n[2]
+        res.append(out[k:k + n].reshape(p.n[2], p.n[1], p.n[0]))
+        k += n
+    return res
+
+
+_HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double)
+
+
+def set_regrid_schedule(o: Oracle, max_level: int, threshold=0.3, buffer=2, block=4, max_patch=32):
+    """From now on every orc_step rebuilds the levels finer than l after each step of a
+    level l <= max_level (flag, cluster, fill in place); o.patches follows the hierarchy
+    and o.regrid_log records (level, new patch list) of every rebuild.
+    max_level < 0 removes the schedule."""
+    L = lib()
+    L.orc_set_regrid_hook.argtypes = [ctypes.c_void_p, ctypes.c_int, _HOOK, ctypes.c_void_p]
+    L.orc_set_regrid_hook.restype = None
+    L.orc_regrid_inplace.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(OrcPatch), ctypes.c_int]
+    L.orc_regrid_inplace.restype = ctypes.c_int
+    if max_level < 0:
+        L.orc_set_regrid_hook(o._h, -1, _HOOK(), None)
+        o._regrid_hook = None
+        return
+    cfg = o.cfg
+    o.regrid_log = []
+
+    def hook(ctx, level, alpha):
+        try:
+            fl = flags_at(o, threshold, level, alpha)
+            newp = cluster(o.patches, fl, tuple(cfg.base_n), tuple(cfg.bc), cfg.max_level, threshold, buffer,
+                           block, max_patch, level)
+            arr = (OrcPatch * len(newp))()
+            for i, p in enumerate(newp):
+                arr[i].level = p.level
+                arr[i].lo[:] = list(p.lo)
+                arr[i].n[:] = list(p.n)
+            if L.orc_regrid_inplace(o._h, len(newp), arr, level) != 0:
+                return -1
+            o.patches = newp
+            o.regrid_log.append((level, list(newp)))
+            return 0
+        except Exception:            # noqa: BLE001 -- reported to the C caller as a failed step
+            import traceback
+            traceback.print_exc()
+            return -1
+
+    o._regrid_hook = _HOOK(hook)
+    L.orc_set_regrid_hook(o._h, max_level, o._regrid_hook, None)

@@ -87,3 +87,61 @@ def test_regridded_hierarchies_are_properly_nested():
     st, msg = N.amr_validate_patches(c, o.patches)
     assert st == N.AMR_OK, msg
     assert max(p.level for p in o.patches) >= 2
+
+
+def _validate(patches, bc, n=32, max_level=3):
+    from paper_0910_5547_gb300 import build as B
+    from paper_0910_5547_gb300 import native as N
+    B.build()
+    c = N.amr_default_config(base_n=(n,) * 3, max_level=max_level, bc=(bc,) * 6)
+    return N.amr_validate_patches(c, patches)
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+def test_midstep_regrid_conserves_and_nests(bc):
+    """Sec. 3 recursion with the finer levels rebuilt after every step of levels
+    <= 1: the rebuilds happen after each level-1 step (twice per coarse step) and
+    each level-0 step, the totals hold to round-off (periodic) and every
+    hierarchy met along the way is properly nested."""
+    pb = _clumpy(seed=12, bc=bc)
+    o = orc.Oracle(pb, max_level=3)
+    o.step()
+    o = rg.regrid(o, threshold=0.1)
+    t0 = o.totals()
+    rg.set_regrid_schedule(o, 1, threshold=0.1)
+    for _ in range(2):
+        o.step()
+    assert [lv for lv, _ in o.regrid_log] == [1, 1, 0, 1, 1, 0]
+    if bc == ai.PERIODIC:
+        assert np.all(np.abs(o.totals() - t0) <= 1e-13 * np.abs(t0).max())
+    for _, pl in o.regrid_log:
+        st, msg = _validate(pl, bc)
+        assert st == 0, msg
+    assert max(p.level for p in o.patches) >= 2
+
+
+def test_midstep_regrid_of_a_uniform_state_changes_nothing():
+    pb = ai.uniform(ai.uniform_patches((16,) * 3, (8,) * 3), (16,) * 3)
+    o = orc.Oracle(pb, max_level=2)
+    u0 = o.all_cons()
+    rg.set_regrid_schedule(o, 1)
+    o.step(0.01)
+    assert [p.level for p in o.patches] == [0] * 8
+    for a, b in zip(u0, o.all_cons()):
+        assert np.array_equal(a, b)
+
+
+def test_removed_schedule_is_a_plain_step():
+    pb = _clumpy(seed=13)
+    runs = []
+    for sched in (False, True):
+        o = orc.Oracle(pb, max_level=2)
+        o.step()
+        o = rg.regrid(o, threshold=0.1)
+        if sched:
+            rg.set_regrid_schedule(o, 1, threshold=0.1)
+            rg.set_regrid_schedule(o, -1)
+        o.step()
+        runs.append(o.all_cons())
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
