@@ -155,9 +155,21 @@ enum {
   AMR_RG_FILL = 5,      /* GPU fill of the new state (copies, prolongation), synchronised */
   AMR_RG_NPHASE = 6
 };
-/* sec[0 .. n-1] receives the phases (n <= AMR_RG_NPHASE); zeros before the
- * first regrid.  No GPU work. */
-amr_status amr_get_regrid_timing(const amr_handle* h, double* sec, int n);
+/* sec[0 .. n-1] receives the phases (n <= AMR_RG_NPHASE) summed over the regrids
+ * (explicit or scheduled) since the last call, then resets them.  No GPU work. */
+amr_status amr_get_regrid_timing(amr_handle* h, double* sec, int n);
+
+/* Regrid schedule (Sec. 3: the hierarchy below a level is rebuilt after each of
+ * its steps): from the next amr_step on, after every completed step of a level
+ * l <= max_level (its finer levels advanced, restricted and refluxed) the levels
+ * finer than l are rebuilt as by amr_regrid with min_level = l -- flags on
+ * levels >= l, whose face ghosts come from the parent at the time reached --
+ * and the step continues on the new hierarchy (the saved old-time states and
+ * flux registers of levels <= l carry over).  Scheduled steps run eagerly (no
+ * graph) and synchronise at each rebuild.  prm NULL takes the defaults
+ * (prm->min_level is ignored); max_level < 0 removes the schedule.
+ * AMR_ERR_ARG on bad parameters; a failed rebuild fails the amr_step. */
+amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, int max_level);
 
 /* Autotuner: time the stage kernel over the installed hierarchy for each
  * candidate work-item shape (x width, columns per CTA, z chunk) and register

@@ -76,7 +76,12 @@ struct DevLevel {
 
 struct amr_handle {
   amr_config cfg{};
-  double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the last regrid
+  double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the regrids since the last query
+  // regrid schedule: after each step of a level l <= sched_level, rebuild the finer levels
+  bool sched_on = false;
+  int sched_level = -1;
+  RegridParams sched_rp;
+  amr_status sched_status = AMR_OK;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   OpsBase* ops = nullptr;
@@ -258,6 +263,8 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
   return cudaSuccess;
 }
 
+amr_status regrid_impl(amr_handle* h, const RegridParams& rp, int mid_level, double alpha);
+
 cudaError_t advance(amr_handle* h, int l, double alpha0) {
   const int nlev = (int)h->dl.size();
   const bool kids = l + 1 < nlev;
@@ -299,6 +306,15 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
     }
     double dxc[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
     if (K.nuniq) LK(h->ops->reflux(h->stream, K.regs, K.reflux_first, K.nuniq, K.nreg, h->d_desc, K.R, h->U, dxc));
+  }
+  // scheduled regrid: rebuild the levels finer than l now that l has completed a
+  // step (its parent has reached fraction alpha0 + 1/2 of its own step)
+  if (h->sched_on && l <= h->sched_level && l < h->cfg.max_level) {
+    const amr_status st = regrid_impl(h, h->sched_rp, l, l == 0 ? 1.0 : alpha0 + 0.5);
+    if (st != AMR_OK) {
+      h->sched_status = st;
+      return cudaErrorUnknown;
+    }
   }
   return cudaSuccess;
 }
@@ -347,7 +363,7 @@ cudaError_t enqueue_step(amr_handle* h, int variant) {
 
 amr_status run_step(amr_handle* h, bool cfl) {
   const int g = step_variant(h, cfl);
-  if (h->cfg.use_graph && !h->timing) {
+  if (h->cfg.use_graph && !h->timing && !h->sched_on) {
     if (!h->graph[g]) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -364,8 +380,11 @@ amr_status run_step(amr_handle* h, bool cfl) {
     h->launches += h->graph_launches[g];
   } else {
     h->counting = 0;
-    CK(enqueue_step(h, g));
+    h->sched_status = AMR_OK;
+    const cudaError_t e = enqueue_step(h, g);
     h->launches += h->counting;
+    if (h->sched_status != AMR_OK) return h->sched_status;   // message set by the regrid
+    CK(e);
   }
   if (fused_rates(h)) h->rates_valid = true;
   return AMR_OK;
@@ -565,6 +584,142 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   return upload_items(h);
 }
 
+// Flag, cluster, plan and refill.  mid_level < 0: between coarse steps (levels
+// above rp.min_level rebuilt, parent data at the current time).  mid_level >= 0:
+// in the middle of a coarse step, right after a step of level mid_level whose
+// parent has reached fraction alpha of its step: the levels above mid_level are
+// rebuilt, ghosts of mid_level come from its parent at alpha, and the old-time
+// states and flux registers of the kept levels carry over so the step goes on.
+amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, double alpha) {
+  using clk = std::chrono::steady_clock;
+  auto t_mark = clk::now();
+  auto lap = [&](int phase) {
+    const auto t = clk::now();
+    h->regrid_sec[phase] += std::chrono::duration<double>(t - t_mark).count();
+    t_mark = t;
+  };
+  RegridParams rp = rp_in;
+  const bool mid = mid_level >= 0;
+  if (mid) rp.min_level = mid_level;
+  const int nlev = (int)h->dl.size();
+  const size_t es = h->ops->elem_size();
+  Plan& op = h->plan;
+  const int nv = op.nvar;
+  // 1. face ghosts of the flagged levels at the current time
+  if (mid) {
+    // the saved old-time states are still needed by the step: parent data of the
+    // stepped level at fraction alpha, of the finer levels at fraction 1
+    CK(fill_ghosts(h, mid_level, h->U, mid_level == 0 ? 1.0 : alpha));
+    for (int l = mid_level + 1; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+  } else {
+    if (nlev > 1)
+      CK(cudaMemcpyAsync(h->Uold, h->U, op.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
+    h->counting = 0;
+    for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+  }
+  // 2. density-gradient flags, one byte per interior cell
+  const size_t ncell = (size_t)(op.packed_elems / nv);
+  unsigned char* d_flags = nullptr;
+  CK(dmalloc(h, reinterpret_cast<void**>(&d_flags), std::max<size_t>(ncell, 1)));
+  cudaError_t fe = h->ops->flag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, rp.threshold,
+                                d_flags);
+  std::vector<unsigned char> hflags(ncell);
+  if (fe == cudaSuccess)
+    fe = cudaMemcpyAsync(hflags.data(), d_flags, ncell, cudaMemcpyDeviceToHost, h->stream);
+  if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
+  dfree(h, d_flags);
+  CK(fe);
+  if (!mid) h->launches += h->counting + 1;
+  else h->counting += 1;
+  std::vector<std::vector<uint8_t>> flags(op.patches.size());
+  for (size_t i = 0; i < op.patches.size(); ++i) {
+    const HPatch& p = op.patches[i];
+    if (p.level >= h->cfg.max_level) continue;
+    const size_t n = (size_t)p.n[0] * p.n[1] * p.n[2];
+    const size_t o = (size_t)(op.packed_off[i] / nv);
+    flags[i].assign(hflags.begin() + o, hflags.begin() + o + n);
+  }
+  lap(AMR_RG_FLAG);
+  // 3. cluster on the host, build the new hierarchy
+  std::vector<HPatch> newp;
+  std::string msg;
+  amr_status st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
+  if (st != AMR_OK) return fail(h, st, msg);
+  lap(AMR_RG_CLUSTER);
+  Plan np;
+  st = build_plan(h->cfg, newp, np, msg, h->tp);
+  if (st != AMR_OK) return fail(h, st, "regrid produced an invalid hierarchy: " + msg);
+  lap(AMR_RG_PLAN);
+  RegridFill fill;
+  build_regrid_fill(op.patches, newp, rp.min_level, fill);
+  lap(AMR_RG_FILLTAB);
+  // 4. new device state, filled from the old one
+  const PatchDesc* old_desc = h->d_desc;
+  const std::vector<HPatch> oldp = op.patches;
+  int64_t keep_end = 0;    // arena range of the kept levels (same patches, same layout)
+  for (size_t i = 0; i < oldp.size(); ++i)
+    if (oldp[i].level <= rp.min_level) keep_end = op.desc[i].off + op.desc[i].vstride * nv;
+  // flux registers of the kept levels (same faces, same order, same layout)
+  size_t keep_regs = 0;
+  if (mid) {
+    for (int l = 1; l <= rp.min_level && l < (int)op.levels.size(); ++l) {
+      if (l >= (int)np.levels.size() || np.levels[l].regs.size() != op.levels[l].regs.size())
+        return fail(h, AMR_ERR_STATE, "regrid: the kept levels changed");
+      keep_regs += 2 * (size_t)nv * op.levels[l].regs.size();
+    }
+  }
+  DeviceBufs old = detach(h);
+  st = install_plan(h, std::move(np));
+  if (st != AMR_OK) {
+    free_bufs(h, old);
+    return st;
+  }
+  std::vector<unsigned char> buf;
+  std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
+  cudaError_t ei = cudaStreamSynchronize(h->stream);   // uploads of the new tables done
+  if (ei != cudaSuccess) {
+    free_bufs(h, old);
+    CK(ei);
+  }
+  lap(AMR_RG_INSTALL);
+  for (size_t l = 0; l < fill.copy.size(); ++l) {
+    o_copy[l] = put(buf, fill.copy[l]);
+    o_fresh[l] = put(buf, fill.fresh[l]);
+  }
+  unsigned char* d_fill = nullptr;
+  cudaError_t e = dmalloc(h, reinterpret_cast<void**>(&d_fill), std::max<size_t>(buf.size(), 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_fill, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && keep_end > 0)
+    e = cudaMemcpyAsync(h->U, old.U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
+  const int nl_new = (int)h->dl.size();
+  if (e == cudaSuccess && nl_new > 1 && keep_end > 0)
+    e = cudaMemcpyAsync(h->Uold, (mid && old.Uold) ? old.Uold : h->U, keep_end * es, cudaMemcpyDeviceToDevice,
+                        h->stream);   // (no old-time state yet when the kept levels had no children)
+  if (e == cudaSuccess && keep_regs > 0)
+    e = cudaMemcpyAsync(h->regs, old.regs, keep_regs * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  for (int l = rp.min_level + 1; l < nl_new && e == cudaSuccess; ++l) {
+    const DevLevel& L = h->dl[l];
+    // interior cells no old patch covers: conservative prolongation from the (new) parent level
+    e = h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->U, 1.0);
+    if (e == cudaSuccess && l < (int)fill.fresh.size())
+      e = h->ops->prolong(h->stream, reinterpret_cast<const ProlongBox*>(d_fill + o_fresh[l]),
+                          (int)fill.fresh[l].size(), h->d_desc, h->tile, h->U);
+    if (e == cudaSuccess && l < (int)fill.copy.size())
+      e = h->ops->xcopy(h->stream, reinterpret_cast<const CopySeg*>(d_fill + o_copy[l]), (int)fill.copy[l].size(),
+                        h->d_desc, old_desc, h->U, old.U);
+    if (mid) h->counting += 3;
+    else h->launches += 3;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dfree(h, d_fill);
+  free_bufs(h, old);
+  CK(e);
+  lap(AMR_RG_FILL);
+  h->ready = true;
+  return AMR_OK;
+}
+
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -705,23 +860,16 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
   return read_bad(h);
 }
 
-amr_status amr_get_regrid_timing(const amr_handle* h, double* sec, int n) {
+amr_status amr_get_regrid_timing(amr_handle* h, double* sec, int n) {
   if (!h || !sec || n < 1 || n > AMR_RG_NPHASE) return AMR_ERR_ARG;
   for (int i = 0; i < n; ++i) sec[i] = h->regrid_sec[i];
+  for (double& x : h->regrid_sec) x = 0.0;
   return AMR_OK;
 }
 
 amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_out) {
   if (!h) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
-  using clk = std::chrono::steady_clock;
-  auto t_mark = clk::now();
-  auto lap = [&](int phase) {
-    const auto t = clk::now();
-    h->regrid_sec[phase] = std::chrono::duration<double>(t - t_mark).count();
-    t_mark = t;
-  };
-  for (double& x : h->regrid_sec) x = 0.0;
   RegridParams rp;
   if (prm) {
     rp.threshold = prm->threshold;
@@ -731,101 +879,38 @@ amr_status amr_regrid(amr_handle* h, const amr_regrid_params* prm, int* npatch_o
     rp.min_level = prm->min_level;
   }
   if (!(rp.threshold > 0.0)) return fail(h, AMR_ERR_ARG, "regrid threshold must be > 0");
-  const int nlev = (int)h->dl.size();
-  const size_t es = h->ops->elem_size();
-  Plan& op = h->plan;
-  const int nv = op.nvar;
-  // 1. face ghosts of every level from the current state (parent data taken at the current time)
-  if (nlev > 1)
-    CK(cudaMemcpyAsync(h->Uold, h->U, op.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
-  h->counting = 0;
-  for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
-  // 2. density-gradient flags, one byte per interior cell
-  const size_t ncell = (size_t)(op.packed_elems / nv);
-  unsigned char* d_flags = nullptr;
-  CK(dmalloc(h, reinterpret_cast<void**>(&d_flags), std::max<size_t>(ncell, 1)));
-  cudaError_t fe = h->ops->flag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, rp.threshold,
-                                d_flags);
-  std::vector<unsigned char> hflags(ncell);
-  if (fe == cudaSuccess)
-    fe = cudaMemcpyAsync(hflags.data(), d_flags, ncell, cudaMemcpyDeviceToHost, h->stream);
-  if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
-  dfree(h, d_flags);
-  CK(fe);
-  h->launches += h->counting + 1;
-  std::vector<std::vector<uint8_t>> flags(op.patches.size());
-  for (size_t i = 0; i < op.patches.size(); ++i) {
-    const HPatch& p = op.patches[i];
-    if (p.level >= h->cfg.max_level) continue;
-    const size_t n = (size_t)p.n[0] * p.n[1] * p.n[2];
-    const size_t o = (size_t)(op.packed_off[i] / nv);
-    flags[i].assign(hflags.begin() + o, hflags.begin() + o + n);
-  }
-  lap(AMR_RG_FLAG);
-  // 3. cluster on the host, build the new hierarchy
-  std::vector<HPatch> newp;
-  std::string msg;
-  amr_status st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
-  if (st != AMR_OK) return fail(h, st, msg);
-  lap(AMR_RG_CLUSTER);
-  Plan np;
-  st = build_plan(h->cfg, newp, np, msg, h->tp);
-  if (st != AMR_OK) return fail(h, st, "regrid produced an invalid hierarchy: " + msg);
-  lap(AMR_RG_PLAN);
-  RegridFill fill;
-  build_regrid_fill(op.patches, newp, rp.min_level, fill);
-  lap(AMR_RG_FILLTAB);
-  // 4. new device state, filled from the old one
-  const PatchDesc* old_desc = h->d_desc;
-  const std::vector<HPatch> oldp = op.patches;
-  int64_t keep_end = 0;    // arena range of the kept levels (same patches, same layout)
-  for (size_t i = 0; i < oldp.size(); ++i)
-    if (oldp[i].level <= rp.min_level) keep_end = op.desc[i].off + op.desc[i].vstride * nv;
-  DeviceBufs old = detach(h);
-  st = install_plan(h, std::move(np));
-  if (st != AMR_OK) {
-    free_bufs(h, old);
-    return st;
-  }
-  std::vector<unsigned char> buf;
-  std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
-  cudaError_t ei = cudaStreamSynchronize(h->stream);   // uploads of the new tables done
-  if (ei != cudaSuccess) {
-    free_bufs(h, old);
-    CK(ei);
-  }
-  lap(AMR_RG_INSTALL);
-  for (size_t l = 0; l < fill.copy.size(); ++l) {
-    o_copy[l] = put(buf, fill.copy[l]);
-    o_fresh[l] = put(buf, fill.fresh[l]);
-  }
-  unsigned char* d_fill = nullptr;
-  cudaError_t e = dmalloc(h, reinterpret_cast<void**>(&d_fill), std::max<size_t>(buf.size(), 1));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_fill, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess && keep_end > 0)
-    e = cudaMemcpyAsync(h->U, old.U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
-  const int nl_new = (int)h->dl.size();
-  if (e == cudaSuccess && nl_new > 1)
-    e = cudaMemcpyAsync(h->Uold, h->U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
-  for (int l = rp.min_level + 1; l < nl_new && e == cudaSuccess; ++l) {
-    const DevLevel& L = h->dl[l];
-    // interior cells no old patch covers: conservative prolongation from the (new) parent level
-    e = h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->U, 1.0);
-    if (e == cudaSuccess && l < (int)fill.fresh.size())
-      e = h->ops->prolong(h->stream, reinterpret_cast<const ProlongBox*>(d_fill + o_fresh[l]),
-                          (int)fill.fresh[l].size(), h->d_desc, h->tile, h->U);
-    if (e == cudaSuccess && l < (int)fill.copy.size())
-      e = h->ops->xcopy(h->stream, reinterpret_cast<const CopySeg*>(d_fill + o_copy[l]), (int)fill.copy[l].size(),
-                        h->d_desc, old_desc, h->U, old.U);
-    h->launches += 3;
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  dfree(h, d_fill);
-  free_bufs(h, old);
-  CK(e);
-  lap(AMR_RG_FILL);
-  h->ready = true;
+  const amr_status st = regrid_impl(h, rp, -1, 1.0);
+  if (st != AMR_OK) return st;
   if (npatch_out) *npatch_out = (int)h->plan.patches.size();
+  return AMR_OK;
+}
+
+amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, int max_level) {
+  if (!h) return AMR_ERR_ARG;
+  if (max_level < 0) {
+    h->sched_on = false;
+    h->sched_level = -1;
+    return AMR_OK;
+  }
+  RegridParams rp;
+  if (prm) {
+    rp.threshold = prm->threshold;
+    rp.buffer = prm->buffer;
+    rp.block = prm->block;
+    rp.max_patch = prm->max_patch;
+  }
+  if (!(rp.threshold > 0.0)) return fail(h, AMR_ERR_ARG, "regrid threshold must be > 0");
+  if (rp.block < 2 || (rp.block & 1) || rp.buffer < 0 || rp.buffer > rp.block || rp.max_patch < 2 * rp.block ||
+      rp.max_patch % (2 * rp.block))
+    return fail(h, AMR_ERR_ARG, "bad regrid parameters (block even >= 2, 0 <= buffer <= block, "
+                                "max_patch a multiple of 2 block)");
+  h->sched_rp = rp;
+  h->sched_level = max_level;
+  h->sched_on = true;
+  for (int g = 0; g < 4; ++g) {   // scheduled steps run eagerly
+    if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+    h->graph[g] = nullptr;
+  }
   return AMR_OK;
 }
 

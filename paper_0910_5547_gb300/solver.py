@@ -61,8 +61,6 @@ class Solver:
     def __del__(self):
         self.close()
 
-    def step(self, dt: float = 0.0, sync: bool = True) -> float:
-        return N.amr_step(self.h, dt, sync)
 
     def floor_count(self) -> int:
         """Interior cells (per stage) in which the pressure floor acted since the last call."""
@@ -109,6 +107,21 @@ class Solver:
     def autotune(self) -> str:
         """Time the stage kernel's candidate tilings on this hierarchy and keep the fastest."""
         return N.amr_autotune(self.h)
+
+    def set_regrid_schedule(self, max_level: int, **kw):
+        """Rebuild the finer levels after every step of a level <= max_level during step()."""
+        N.amr_set_regrid_schedule(self.h, max_level, **kw)
+        self._scheduled = max_level >= 0
+
+    def step(self, dt: float = 0.0, sync: bool = True) -> float:
+        used = N.amr_step(self.h, dt, sync)
+        if getattr(self, "_scheduled", False):
+            self._refresh_patches()
+        return used
+
+    def _refresh_patches(self):
+        self.patches = N.amr_get_patches(self.h)
+        self.offsets = np.cumsum([0] + [self.nvar * p.n[0] * p.n[1] * p.n[2] for p in self.patches])
 
     def regrid(self, **kw) -> int:
         """Rebuild the refined levels from density-gradient flags (see amr_regrid)."""

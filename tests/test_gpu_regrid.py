@@ -70,3 +70,59 @@ def test_regrid_rejects_bad_parameters():
     with pytest.raises(N.AmrError) as e:
         s.regrid(block=3)
     assert e.value.status == N.AMR_ERR_ARG
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+def test_scheduled_midstep_regrid_matches_the_oracle_fp64(bc):
+    """Finer levels rebuilt after every step of levels <= 1 inside each coarse step
+    (Sec. 3 recursion): after every coarse step the GPU hierarchy equals the oracle's
+    (exact) and the state matches within the FP64 parity tolerance."""
+    pb = clumpy(12, bc)
+    o = orc.Oracle(pb, max_level=3, nthreads=8)
+    s = Solver.from_problem(pb, precision="fp64", max_level=3)
+    o.step()
+    s.step()
+    o = rg.regrid(o, threshold=0.1)
+    s.regrid(threshold=0.1)
+    rg.set_regrid_schedule(o, 1, threshold=0.1)
+    s.set_regrid_schedule(1, threshold=0.1)
+    for k in range(2):
+        o.step()
+        s.step()
+        assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
+               [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"coarse step {k}"
+        assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", f"scheduled regrid, coarse step {k}")
+    assert len(o.regrid_log) == 6
+    assert max(p.level for p in s.patches) >= 2
+    ph = N.amr_get_regrid_timing(s.h)
+    assert ph["cluster"] > 0.0 and ph["plan"] > 0.0
+    s.check()
+
+
+def test_scheduled_regrid_fp32_conserves_and_nests():
+    pb = clumpy(14, ai.PERIODIC)
+    s = Solver.from_problem(pb, precision="fp32", max_level=3)
+    s.step()
+    s.regrid(threshold=0.1)
+    s.set_regrid_schedule(1, threshold=0.1)
+    t0 = s.totals()
+    for _ in range(2):
+        s.step()
+        c = N.amr_default_config(base_n=(32,) * 3, max_level=3, bc=(ai.PERIODIC,) * 6)
+        assert N.amr_validate_patches(c, s.patches)[0] == N.AMR_OK
+    t1 = s.totals()
+    assert np.all(np.abs(t1 - t0) <= 2e-6 * np.abs(t0).max()), (t0, t1)
+    s.set_regrid_schedule(-1)
+    s.step()
+    s.check()
+
+
+def test_regrid_schedule_rejects_bad_parameters():
+    s = Solver.from_problem(clumpy(3, ai.PERIODIC), precision="fp32", max_level=2)
+    with pytest.raises(N.AmrError):
+        s.set_regrid_schedule(1, block=3)
+    with pytest.raises(N.AmrError):
+        s.set_regrid_schedule(1, threshold=0.0)
+    s.set_regrid_schedule(-1)
+    s.step()
+    s.check()
