@@ -242,6 +242,11 @@ amr_status amr_get_timing(amr_handle* h, double* ms, long long* count, int nclas
  * Synchronises. */
 amr_status amr_floor_count(amr_handle* h, long long* count);
 
+/* Cell-updates performed by amr_step so far: the sum over every level step of
+ * the level's interior cells at that moment (a level-l cell counts 2^l times
+ * per coarse step; rebuilt hierarchies count as they are stepped). */
+long long amr_cell_updates(const amr_handle* h);
+
 /* Number of kernels the library launched so far (graph replays count every
  * kernel node) -- used to report launches in a timed region. */
 long long amr_kernel_launches(const amr_handle* h);

@@ -78,6 +78,8 @@ struct amr_handle {
   amr_config cfg{};
   double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the regrids since the last query
   // regrid schedule: after each step of a level l <= sched_level, rebuild the finer levels
+  long long cell_updates = 0;   // interior cells advanced by amr_step, summed over level steps
+  bool capturing = false;       // advance() is being captured into a graph (not executed)
   bool sched_on = false;
   int sched_level = -1;
   RegridParams sched_rp;
@@ -266,6 +268,7 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
 amr_status regrid_impl(amr_handle* h, const RegridParams& rp, int mid_level, double alpha);
 
 cudaError_t advance(amr_handle* h, int l, double alpha0) {
+  if (!h->capturing) h->cell_updates += h->plan.levels[l].cells;
   const int nlev = (int)h->dl.size();
   const bool kids = l + 1 < nlev;
   DevLevel& L = h->dl[l];
@@ -368,7 +371,9 @@ amr_status run_step(amr_handle* h, bool cfl) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       h->counting = 0;
+      h->capturing = true;
       cudaError_t e = enqueue_step(h, g);
+      h->capturing = false;
       cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
       if (e != cudaSuccess) return fail(h, AMR_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
       CK(e2);
@@ -378,6 +383,7 @@ amr_status run_step(amr_handle* h, bool cfl) {
     }
     CK(cudaGraphLaunch(h->graph[g], h->stream));
     h->launches += h->graph_launches[g];
+    for (size_t l = 0; l < h->plan.levels.size(); ++l) h->cell_updates += h->plan.levels[l].cells << l;
   } else {
     h->counting = 0;
     h->sched_status = AMR_OK;
@@ -591,6 +597,8 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
 // rebuilt, ghosts of mid_level come from its parent at alpha, and the old-time
 // states and flux registers of the kept levels carry over so the step goes on.
 amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, double alpha) {
+  // the work already queued on the stream (e.g. the level steps) is not regrid time
+  CK(cudaStreamSynchronize(h->stream));
   using clk = std::chrono::steady_clock;
   auto t_mark = clk::now();
   auto lap = [&](int phase) {
@@ -1154,6 +1162,8 @@ amr_status amr_get_timing(amr_handle* h, double* ms, long long* count, int nclas
 }
 
 long long amr_kernel_launches(const amr_handle* h) { return h ? h->launches : 0; }
+
+long long amr_cell_updates(const amr_handle* h) { return h ? h->cell_updates : 0; }
 
 const char* amr_last_error(const amr_handle* h) { return h ? h->err.c_str() : "null handle"; }
 

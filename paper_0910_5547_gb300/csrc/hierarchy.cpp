@@ -636,7 +636,6 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 G = ((G % Nl) + Nl) % Nl;
               }
               int A = p.n[t1], B = p.n[t2];
-              std::vector<unsigned char> mask((size_t)A * B, 0);
               {
                 int qlo[3], qhi[3];
                 qlo[d] = G; qhi[d] = G + 1;
@@ -644,6 +643,8 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 qlo[t2] = p.lo[t2]; qhi[t2] = p.lo[t2] + p.n[t2];
                 six.query(qlo, qhi, cand);
               }
+              const size_t g0 = Gv.size();
+              int64_t area = 0;      // same-level patches do not overlap: the covered area sums
               for (int q : cand) {
                 const HPatch& o = P[q];
                 if (G < o.lo[d] || G >= o.lo[d] + o.n[d]) continue;
@@ -657,10 +658,18 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 s.dlo[t1] = (int16_t)(a0 - p.lo[t1]); s.dn[t1] = (int16_t)(a1 - a0); s.sh[t1] = (int16_t)(p.lo[t1] - o.lo[t1]);
                 s.dlo[t2] = (int16_t)(b0 - p.lo[t2]); s.dn[t2] = (int16_t)(b1 - b0); s.sh[t2] = (int16_t)(p.lo[t2] - o.lo[t2]);
                 Gv.push_back(s);
-                for (int b = b0; b < b1; ++b)
-                  for (int a = a0; a < a1; ++a) mask[(size_t)(b - p.lo[t2]) * A + (a - p.lo[t1])] = 1;
+                area += (int64_t)(a1 - a0) * (b1 - b0);
               }
-              std::vector<Rect> rects = mask_rects(mask, A, B);
+              std::vector<Rect> rects;
+              if (area < (int64_t)A * B) {   // uncovered parts of the face layer: prolongation boxes
+                std::vector<unsigned char> mask((size_t)A * B, 0);
+                for (size_t e = g0; e < Gv.size(); ++e) {
+                  const CopySeg& c = Gv[e];
+                  for (int b = c.dlo[t2]; b < c.dlo[t2] + c.dn[t2]; ++b)
+                    for (int a = c.dlo[t1]; a < c.dlo[t1] + c.dn[t1]; ++a) mask[(size_t)b * A + a] = 1;
+                }
+                rects = mask_rects(mask, A, B);
+              }
               if (!rects.empty() && l == 0) {
                 err[ii] = fmt("level-0 patch %d has uncovered ghost cells", i);
                 return;
@@ -942,11 +951,22 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
       }
       regs.insert(regs.end(), rs[task].begin(), rs[task].end());
     }
-    // group by coarse cell, keeping the (d, side) order inside a cell
-    std::stable_sort(regs.begin(), regs.end(), [](const RegFace& a, const RegFace& b) {
-      return std::make_tuple(a.cpatch, a.cidx[2], a.cidx[1], a.cidx[0]) <
-             std::make_tuple(b.cpatch, b.cidx[2], b.cidx[1], b.cidx[0]);
-    });
+    // group by coarse cell, keeping the (d, side) order inside a cell: a stable
+    // counting sort by coarse patch, then a stable sort by cell inside each patch
+    {
+      std::vector<int> start(np + 1, 0);
+      for (const RegFace& r : regs) start[r.cpatch + 1]++;
+      for (int c = 0; c < np; ++c) start[c + 1] += start[c];
+      std::vector<RegFace> by(regs.size());
+      std::vector<int> pos(start.begin(), start.end() - 1);
+      for (const RegFace& r : regs) by[pos[r.cpatch]++] = r;
+      parallel_for(np, [&](int c) {
+        std::stable_sort(by.begin() + start[c], by.begin() + start[c + 1], [](const RegFace& a, const RegFace& b) {
+          return std::make_tuple(a.cidx[2], a.cidx[1], a.cidx[0]) < std::make_tuple(b.cidx[2], b.cidx[1], b.cidx[0]);
+        });
+      });
+      regs.swap(by);
+    }
     L.regs = regs;
     L.reflux_first.clear();
     for (size_t e = 0; e < regs.size(); ++e) {

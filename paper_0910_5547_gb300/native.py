@@ -36,7 +36,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
            "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count",
-           "amr_set_regrid_schedule"]
+           "amr_set_regrid_schedule", "amr_cell_updates"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -137,6 +137,8 @@ def load():
     L.amr_regrid.restype = ctypes.c_int
     L.amr_set_regrid_schedule.argtypes = [H, ctypes.POINTER(amr_regrid_params), ctypes.c_int]
     L.amr_set_regrid_schedule.restype = ctypes.c_int
+    L.amr_cell_updates.argtypes = [H]
+    L.amr_cell_updates.restype = ctypes.c_longlong
     L.amr_get_patches.argtypes = [H, ctypes.POINTER(amr_patch), ctypes.c_int]
     L.amr_autotune.argtypes = [H, ctypes.c_char_p, ctypes.c_int]
     L.amr_autotune.restype = ctypes.c_int
@@ -332,6 +334,11 @@ def amr_set_regrid_schedule(h, max_level: int, threshold=0.3, buffer=2, block=4,
     (max_level < 0: no schedule)."""
     prm = amr_regrid_params(threshold, buffer, block, max_patch, 0)
     _check(h, load().amr_set_regrid_schedule(h, ctypes.byref(prm), int(max_level)))
+
+
+def amr_cell_updates(h) -> int:
+    """Interior cell-updates performed by amr_step so far (sum over level steps)."""
+    return int(load().amr_cell_updates(h))
 
 
 def amr_autotune(h) -> str:
