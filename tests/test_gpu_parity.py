@@ -286,3 +286,16 @@ def test_torch_allocator_path_is_bitwise_and_accounted():
     s_d.close()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == base
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_cell_update_counter(graph):
+    """amr_cell_updates: each coarse step adds sum_l cells_l 2^l, with graph replay and eagerly."""
+    pb = ai.random_smooth(three_level_seeded(), (32,) * 3, seed=4)
+    s = Solver.from_problem(pb, precision="fp32", use_graph=graph)
+    per_step = sum((p.n[0] * p.n[1] * p.n[2]) << p.level for p in pb.patches)
+    c0 = N.amr_cell_updates(s.h)
+    for _ in range(3):
+        s.step(0.0, sync=False)
+    s.check()
+    assert N.amr_cell_updates(s.h) - c0 == 3 * per_step
