@@ -943,38 +943,65 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
               Rv.push_back(r);
             }
             });
-    std::vector<RegFace> regs;
-    for (int task = 0; task < ntask; ++task) {
+    for (int task = 0; task < ntask; ++task)
       if (!err[task].empty()) {
         msg = err[task];
         return AMR_ERR_NESTING;
       }
-      regs.insert(regs.end(), rs[task].begin(), rs[task].end());
-    }
-    // group by coarse cell, keeping the (d, side) order inside a cell: a stable
-    // counting sort by coarse patch, then a stable sort by cell inside each patch
+    // group by coarse cell, keeping the task order ((d, side, patch)) inside a
+    // cell: a stable counting sort by coarse patch over chunks of tasks (per-chunk
+    // histograms, parallel scatter), then a stable sort by cell inside each patch
+    const int nchunk = std::max(1, std::min(64, ntask / 64));
+    auto chunk_lo = [&](int k) { return (int)((int64_t)ntask * k / nchunk); };
+    std::vector<std::vector<int>> hist(nchunk, std::vector<int>(np, 0));
+    parallel_for(nchunk, [&](int k) {
+      for (int task = chunk_lo(k); task < chunk_lo(k + 1); ++task)
+        for (const RegFace& r : rs[task]) hist[k][r.cpatch]++;
+    });
+    std::vector<int> start(np + 1, 0);
     {
-      std::vector<int> start(np + 1, 0);
-      for (const RegFace& r : regs) start[r.cpatch + 1]++;
-      for (int c = 0; c < np; ++c) start[c + 1] += start[c];
-      std::vector<RegFace> by(regs.size());
-      std::vector<int> pos(start.begin(), start.end() - 1);
-      for (const RegFace& r : regs) by[pos[r.cpatch]++] = r;
-      parallel_for(np, [&](int c) {
-        std::stable_sort(by.begin() + start[c], by.begin() + start[c + 1], [](const RegFace& a, const RegFace& b) {
-          return std::make_tuple(a.cidx[2], a.cidx[1], a.cidx[0]) < std::make_tuple(b.cidx[2], b.cidx[1], b.cidx[0]);
-        });
+      size_t run = 0;
+      for (int c = 0; c < np; ++c) {
+        start[c] = (int)run;
+        for (int k = 0; k < nchunk; ++k) {
+          const int n = hist[k][c];
+          hist[k][c] = (int)run;   // first slot of chunk k's registers of coarse patch c
+          run += n;
+        }
+      }
+      start[np] = (int)run;
+    }
+    std::vector<RegFace> regs(start[np]);
+    parallel_for(nchunk, [&](int k) {
+      std::vector<int>& pos = hist[k];
+      for (int task = chunk_lo(k); task < chunk_lo(k + 1); ++task)
+        for (const RegFace& r : rs[task]) regs[pos[r.cpatch]++] = r;
+    });
+    std::vector<std::vector<int>>().swap(hist);
+    std::vector<std::vector<RegFace>>().swap(rs);
+    auto same_cell = [](const RegFace& a, const RegFace& b) {
+      return a.cpatch == b.cpatch && a.cidx[0] == b.cidx[0] && a.cidx[1] == b.cidx[1] && a.cidx[2] == b.cidx[2];
+    };
+    // per coarse patch: sort by cell, count the unique cells (CSR built below)
+    std::vector<int> nuniq(np + 1, 0);
+    parallel_for(np, [&](int c) {
+      std::stable_sort(regs.begin() + start[c], regs.begin() + start[c + 1], [](const RegFace& x, const RegFace& y) {
+        return std::make_tuple(x.cidx[2], x.cidx[1], x.cidx[0]) < std::make_tuple(y.cidx[2], y.cidx[1], y.cidx[0]);
       });
-      regs.swap(by);
-    }
-    L.regs = regs;
-    L.reflux_first.clear();
-    for (size_t e = 0; e < regs.size(); ++e) {
-      if (e == 0 || regs[e].cpatch != regs[e - 1].cpatch || regs[e].cidx[0] != regs[e - 1].cidx[0] ||
-          regs[e].cidx[1] != regs[e - 1].cidx[1] || regs[e].cidx[2] != regs[e - 1].cidx[2])
-        L.reflux_first.push_back((int)e);
-    }
-    L.reflux_first.push_back((int)regs.size());
+      int u = 0;
+      for (int e = start[c]; e < start[c + 1]; ++e)
+        if (e == start[c] || !same_cell(regs[e], regs[e - 1])) ++u;
+      nuniq[c + 1] = u;
+    });
+    for (int c = 0; c < np; ++c) nuniq[c + 1] += nuniq[c];
+    L.reflux_first.assign(nuniq[np] + 1, 0);
+    parallel_for(np, [&](int c) {
+      int u = nuniq[c];
+      for (int e = start[c]; e < start[c + 1]; ++e)
+        if (e == start[c] || !same_cell(regs[e], regs[e - 1])) L.reflux_first[u++] = e;
+    });
+    L.reflux_first[nuniq[np]] = (int)regs.size();
+    L.regs.swap(regs);
   }
   build_flat(plan);
   return AMR_OK;
@@ -1066,6 +1093,60 @@ class KeySet {
   }
   std::vector<int64_t> slots_;
   size_t n_ = 0, mask_;
+};
+
+// Set of block coordinates inside a known box [lo, hi): a dense bitmap when the
+// box has at most 2^28 blocks, else a KeySet.  Coordinates outside the box are
+// never members.
+class BlockSet {
+ public:
+  void reset(const int lo[3], const int hi[3]) {
+    int64_t vol = 1;
+    for (int d = 0; d < 3; ++d) {
+      lo_[d] = lo[d];
+      n_[d] = std::max(hi[d] - lo[d], 0);
+      vol *= n_[d];
+    }
+    dense_ = vol <= ((int64_t)1 << 28);
+    bits_.assign(dense_ ? (size_t)((vol + 63) / 64) : 0, 0);
+    hash_ = KeySet();
+    count_ = 0;
+  }
+  void insert(int x, int y, int z) {
+    if (dense_) {
+      int64_t i;
+      if (!index(x, y, z, i)) return;
+      uint64_t& w = bits_[i >> 6];
+      const uint64_t m = (uint64_t)1 << (i & 63);
+      if (!(w & m)) { w |= m; ++count_; }
+    } else if (inside(x, y, z) && hash_.insert(pack(x, y, z))) {
+      ++count_;
+    }
+  }
+  bool count(int x, int y, int z) const {
+    if (dense_) {
+      int64_t i;
+      return index(x, y, z, i) && ((bits_[i >> 6] >> (i & 63)) & 1);
+    }
+    return inside(x, y, z) && hash_.count(pack(x, y, z));
+  }
+  bool empty() const { return count_ == 0; }
+
+ private:
+  bool inside(int x, int y, int z) const {
+    return x >= lo_[0] && x < lo_[0] + n_[0] && y >= lo_[1] && y < lo_[1] + n_[1] && z >= lo_[2] &&
+           z < lo_[2] + n_[2];
+  }
+  bool index(int x, int y, int z, int64_t& i) const {
+    if (!inside(x, y, z)) return false;
+    i = ((int64_t)(z - lo_[2]) * n_[1] + (y - lo_[1])) * n_[0] + (x - lo_[0]);
+    return true;
+  }
+  int lo_[3] = {0, 0, 0}, n_[3] = {0, 0, 0};
+  bool dense_ = true;
+  std::vector<uint64_t> bits_;
+  KeySet hash_;
+  size_t count_ = 0;
 };
 
 }  // namespace
@@ -1162,23 +1243,36 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   for (const HPatch& p : old)
     if (p.level <= l0) out.push_back(p);
   // blocks of level l0 fully covered by its patches
-  KeySet cover;
-  for (const HPatch& p : old) {
-    if (p.level != l0) continue;
-    int a0[3], a1[3];
-    for (int d = 0; d < 3; ++d) {
-      a0[d] = (p.lo[d] + B - 1) / B;
-      a1[d] = (p.lo[d] + p.n[d]) / B;
-      // a partial block at the domain's end counts when the patch reaches the end
-      if (p.lo[d] + p.n[d] == level_n(cfg, l0, d) && level_n(cfg, l0, d) % B) a1[d] += 1;
+  BlockSet cover;
+  {
+    auto block_range = [&](const HPatch& p, int* a0, int* a1) {
+      for (int d = 0; d < 3; ++d) {
+        a0[d] = (p.lo[d] + B - 1) / B;
+        a1[d] = (p.lo[d] + p.n[d]) / B;
+        // a partial block at the domain's end counts when the patch reaches the end
+        if (p.lo[d] + p.n[d] == level_n(cfg, l0, d) && level_n(cfg, l0, d) % B) a1[d] += 1;
+      }
+    };
+    int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (const HPatch& p : old) {
+      if (p.level != l0) continue;
+      int a0[3], a1[3];
+      block_range(p, a0, a1);
+      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], a0[d]); hi[d] = std::max(hi[d], a1[d]); }
     }
-    for (int z = a0[2]; z < a1[2]; ++z)
-      for (int y = a0[1]; y < a1[1]; ++y)
-        for (int x = a0[0]; x < a1[0]; ++x) cover.insert(pack(x, y, z));
+    if (lo[0] > hi[0]) for (int d = 0; d < 3; ++d) lo[d] = hi[d] = 0;
+    cover.reset(lo, hi);
+    for (const HPatch& p : old) {
+      if (p.level != l0) continue;
+      int a0[3], a1[3];
+      block_range(p, a0, a1);
+      for (int z = a0[2]; z < a1[2]; ++z)
+        for (int y = a0[1]; y < a1[1]; ++y)
+          for (int x = a0[0]; x < a1[0]; ++x) cover.insert(x, y, z);
+    }
   }
   const int maxb = rp.max_patch / (2 * B);
   for (int l = l0; l < L; ++l) {
-    KeySet refine;
     const std::vector<int64_t> tl = tags[l].keys();
     std::vector<unsigned char> refinable(tl.size(), 0);
     parallel_for((int)tl.size(), [&](int ti) {
@@ -1197,26 +1291,34 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
                 else outside = true;
               }
             }
-            if (!outside && !cover.count(pack(q[0], q[1], q[2]))) ok = false;
+            if (!outside && !cover.count(q[0], q[1], q[2])) ok = false;
           }
       refinable[ti] = ok;
     });
-    for (size_t ti = 0; ti < tl.size(); ++ti)
-      if (refinable[ti]) refine.insert(tl[ti]);
-    if (refine.empty()) break;
-    // greedy box merge in (z, y, x) order: extend along x, then y, then z
-    KeySet done;
-    KeySet next_cover;
     std::vector<Key> order;
-    order.reserve(refine.size());
-    for (int64_t kb : refine.keys()) order.push_back(unpack(kb));
+    int rlo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, rhi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (size_t ti = 0; ti < tl.size(); ++ti)
+      if (refinable[ti]) {
+        const Key b = unpack(tl[ti]);
+        order.push_back(b);
+        const int c[3] = {b.x, b.y, b.z};
+        for (int d = 0; d < 3; ++d) { rlo[d] = std::min(rlo[d], c[d]); rhi[d] = std::max(rhi[d], c[d] + 1); }
+      }
+    if (order.empty()) break;
+    BlockSet refine, done, next_cover;
+    refine.reset(rlo, rhi);
+    done.reset(rlo, rhi);
+    for (const Key& b : order) refine.insert(b.x, b.y, b.z);
+    {
+      int clo[3], chi[3];   // blocks of level l+1 under the refined blocks
+      for (int d = 0; d < 3; ++d) { clo[d] = 2 * rlo[d]; chi[d] = 2 * rhi[d]; }
+      next_cover.reset(clo, chi);
+    }
+    // greedy box merge in (z, y, x) order: extend along x, then y, then z
     std::sort(order.begin(), order.end());   // (z, y, x) order
     for (const Key& b : order) {
-      if (done.count(pack(b.x, b.y, b.z))) continue;
-      auto free_ = [&](int x, int y, int z) {
-        const int64_t k = pack(x, y, z);
-        return refine.count(k) && !done.count(k);
-      };
+      if (done.count(b.x, b.y, b.z)) continue;
+      auto free_ = [&](int x, int y, int z) { return refine.count(x, y, z) && !done.count(x, y, z); };
       int nx = 1, ny = 1, nz = 1;
       while (nx < maxb && free_(b.x + nx, b.y, b.z)) ++nx;
       auto row_ok = [&](int y, int z) {
@@ -1233,7 +1335,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
       while (nz < maxb && slab_ok(b.z + nz)) ++nz;
       for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
-          for (int x = 0; x < nx; ++x) done.insert(pack(b.x + x, b.y + y, b.z + z));
+          for (int x = 0; x < nx; ++x) done.insert(b.x + x, b.y + y, b.z + z);
       HPatch f{};
       f.level = l + 1;
       const int bl[3] = {b.x, b.y, b.z}, bn[3] = {nx, ny, nz};
@@ -1246,9 +1348,9 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
       // blocks of level l+1 covered by the new patch
       for (int z = f.lo[2] / B; z < (f.lo[2] + f.n[2] + B - 1) / B; ++z)
         for (int y = f.lo[1] / B; y < (f.lo[1] + f.n[1] + B - 1) / B; ++y)
-          for (int x = f.lo[0] / B; x < (f.lo[0] + f.n[0] + B - 1) / B; ++x) next_cover.insert(pack(x, y, z));
+          for (int x = f.lo[0] / B; x < (f.lo[0] + f.n[0] + B - 1) / B; ++x) next_cover.insert(x, y, z);
     }
-    cover.swap(next_cover);
+    std::swap(cover, next_cover);
   }
   return AMR_OK;
 }
