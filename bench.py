@@ -188,21 +188,46 @@ def timed_steps(torch, s, stream, steps, dt=0.0):
     return e0.elapsed_time(e1) / 1e3
 
 
-def cpu_baseline(steps=2):
+def l1_errors(got, ref):
+    """Per-variable L1 relative error over all cells (momentum components against the
+    momentum norm, as the parity tests measure FP32)."""
+    import numpy as np
+    nv = ref[0].shape[0]
+    num = np.zeros(nv)
+    den = np.zeros(nv)
+    for g, r in zip(got, ref):
+        num += np.abs(g - r).reshape(nv, -1).sum(axis=1)
+        den += np.abs(r).reshape(nv, -1).sum(axis=1)
+    den[1:4] = den[1:4].sum()
+    return num / np.maximum(den, 1e-300)
+
+
+def cpu_baseline(steps=2, stream=None):
     """The FP64 oracle as it stands, all host cores, on a bounded sample: `steps`
-    RK2 steps of the full 256^3 / 32^3-patch workload."""
+    RK2 steps of the full 256^3 / 32^3-patch workload.  The same steps (the oracle's
+    dt sequence) also run through the library in FP32 and FP64, and the L1 errors of
+    their final states against the oracle's are reported beside the timing."""
     import amr_inputs as ai
     import oracle as orc
     cores = len(os.sched_getaffinity(0))
     pb = ai.kelvin_helmholtz(N=N, tile=TILE)
     o = orc.Oracle(pb, nthreads=cores)
     t = time.perf_counter()
-    for _ in range(steps):
-        o.step()
+    dts = [o.step() for _ in range(steps)]
     dt = time.perf_counter() - t
-    return {"value": N ** 3 * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} RK2 steps (CFL dt) of the full 256^3 periodic workload, 512 patches of 32^3, "
-                      f"FP64, OpenMP over patches; {dt:.1f} s wall"}
+    out = {"value": N ** 3 * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{steps} RK2 steps (CFL dt) of the full 256^3 periodic workload, 512 patches of 32^3, "
+                     f"FP64, OpenMP over patches; {dt:.1f} s wall"}
+    ref = o.all_cons()
+    del o
+    for prec in ("fp32", "fp64"):
+        s = make_solver(pb, prec, True, True, stream)
+        for d in dts:
+            s.step(d, sync=False)
+        s.check()
+        out[f"{prec}_l1_vs_oracle"] = float(l1_errors(s.all_cons(), ref).max())
+        s.close()
+    return out
 
 
 def run_reference(args):
@@ -305,12 +330,18 @@ def main():
     torch.cuda.synchronize()
     s.check()
     n0 = s.launches()
+    tot0 = s.totals()
     barrier()
     with ClockSampler(local) as clk:
         elapsed = timed_steps(torch, s, stream, args.steps)
     barrier()
     launches = s.launches() - n0
     s.check()
+    tot1 = s.totals()
+    # periodic box: mass, momentum and energy are conserved; drift of the FP32 state
+    # over the timed steps, measured by the FP64 totals (momentum against its norm)
+    scale = [abs(tot0[0]), max(abs(tot0[1]), abs(tot0[2]), abs(tot0[3]), abs(tot0[0])), 0, 0, abs(tot0[4])]
+    drift = {k: float(abs(tot1[i] - tot0[i]) / scale[i]) for i, k in ((0, "mass"), (1, "x_momentum"), (4, "energy"))}
     value, elapsed = aggregate(elapsed, cells * args.steps, dist if ws > 1 else None, device="cuda")
 
     # ---- per-kernel event timing (eager launches, same solver and state) ----
@@ -490,7 +521,7 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu else cpu_baseline(args.cpu_steps)
+    cpu = None if args.no_cpu else cpu_baseline(args.cpu_steps, stream)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -513,6 +544,8 @@ def main():
         "step_kernel_ms": step_kernel_ms,
         "autotune": [l for l in tune_report.splitlines() if l],
         "cell_update_roofline_frac": value / ws * (2 + 3) * V * W / (peak * 1e9),
+        "conservation_drift": {**drift, "steps": args.steps, "note": "relative change of the FP64 totals of "
+                               "the FP32 state over the timed steps (periodic box)"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
