@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+
+#include <nvtx3/nvToolsExt.h>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -20,6 +22,18 @@
 #include "ops.h"
 
 using namespace amr;
+
+namespace {
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -268,6 +282,9 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
 amr_status regrid_impl(amr_handle* h, const RegridParams& rp, int mid_level, double alpha);
 
 cudaError_t advance(amr_handle* h, int l, double alpha0) {
+  static const char* names[] = {"level 0 step", "level 1 step", "level 2 step", "level 3 step", "level 4 step",
+                                "level 5 step", "level 6 step", "level 7+ step"};
+  Range range(names[l < 7 ? l : 7]);
   if (!h->capturing) h->cell_updates += h->plan.levels[l].cells;
   const int nlev = (int)h->dl.size();
   const bool kids = l + 1 < nlev;
@@ -597,6 +614,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
 // rebuilt, ghosts of mid_level come from its parent at alpha, and the old-time
 // states and flux registers of the kept levels carry over so the step goes on.
 amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, double alpha) {
+  Range range(mid_level >= 0 ? "regrid (inside a step)" : "regrid");
   // the work already queued on the stream (e.g. the level steps) is not regrid time
   CK(cudaStreamSynchronize(h->stream));
   using clk = std::chrono::steady_clock;
@@ -924,6 +942,7 @@ amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, 
 
 amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   if (!h) return AMR_ERR_ARG;
+  Range range("amr_autotune");
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
   struct Cand { TileParams tp; int occ; };
   std::vector<Cand> cands;
@@ -1039,6 +1058,7 @@ amr_status amr_set_state(amr_handle* h, const double* packed, int state_kind) {
 
 amr_status amr_step(amr_handle* h, double dt, double* dt_used) {
   if (!h) return AMR_ERR_ARG;
+  Range range("amr_step");
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
   if (!std::isfinite(dt)) return fail(h, AMR_ERR_ARG, "dt must be finite");
   const bool cfl = !(dt > 0.0);
