@@ -298,6 +298,12 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     // only the global stores of the update and the CFL maxima are predicated.
     // Euler skips that work (measured faster).
     constexpr bool kMerge = NV == 9;
+    // the own cell's low-side face states (x and y), kept in registers from the
+    // slopes of plane j to the fluxes of plane j in the next iteration; only
+    // the tile-boundary cells' states go through shared memory
+    T xrOwn[NV], yrOwn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xrOwn[v] = yrOwn[v] = T(0);
     for (int j = 0; j <= wz; ++j) {
       const bool cur = j < wz, prev = j > 0;
       T Fzp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
@@ -364,9 +370,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             xl[v] = XL[v * kStateMax + xs - 1];
-            xr[v] = XR[v * kStateMax + xs];
+            xr[v] = xrOwn[v];
             yl[v] = YL[v * kStateMax + ys - wx];
-            yr[v] = YR[v * kStateMax + ys];
+            yr[v] = yrOwn[v];
           }
         }
         if (STAGE == 2 && !kAsync) {
@@ -380,9 +386,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
               xl[v] = XL[v * kStateMax + xs - 1];
-              xr[v] = XR[v * kStateMax + xs];
+              xr[v] = xrOwn[v];
               yl[v] = YL[v * kStateMax + ys - wx];
-              yr[v] = YR[v * kStateMax + ys];
+              yr[v] = yrOwn[v];
             }
           }
           riemann<T, NV, 0>(xl, xr, ph, Fx0);                // x face of plane j-1
@@ -474,9 +480,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           const T sx = limited_slope(Wv[-1], w0, Wv[1], ph.theta);
           const T sy = limited_slope(Wv[-sw], w0, Wv[sw], ph.theta);
           XL[v * kStateMax + xs] = w0 + sc * sx;
-          XR[v * kStateMax + xs] = w0 - sc * sx;
+          xrOwn[v] = w0 - sc * sx;
           YL[v * kStateMax + ys] = w0 + sc * sy;
-          YR[v * kStateMax + ys] = w0 - sc * sy;
+          yrOwn[v] = w0 - sc * sy;
         }
       }
       if (bkind >= 0 && (kMerge || cur)) {
