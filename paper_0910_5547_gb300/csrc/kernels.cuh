@@ -5,15 +5,23 @@
 //                    HLL/LLF flux, flux difference L(U) and the stage update
 //                    U1 = U + dt L(U) (stage 1) or U = U/2 + (U1 + dt L(U1))/2
 //                    (stage 2, Sec. 5.1), one CTA per x-y column block
-//                    marching through z with a double-buffered shared-memory
-//                    plane and z-fluxes carried in registers.
-//   copy_kernel      ghost fill by box copies (siblings, periodic images,
-//                    outflow) and parent-tile gathers with linear time
-//                    interpolation.
-//   prolong_kernel   conservative minmod prolongation into fine ghost cells.
+//                    marching through z: two barrier-separated phases per
+//                    plane (plane j skewed against j-1), x/y states and fluxes
+//                    through shared memory, z faces in registers, FP32 Euler
+//                    inputs staged by cp.async rings.
+//   box_copy_kernel  batched ghost fill (siblings, periodic images, outflow)
+//                    and parent-tile gathers with linear time interpolation,
+//                    over flattened boxes in fixed chunks of cells per CTA;
+//                    copy_kernel is the one-CTA-per-box form (plain launches).
+//   box_prolong_kernel / prolong_kernel
+//                    conservative minmod prolongation into fine ghost cells.
 //   reg_*_kernel     FP64 flux registers at coarse-fine faces.
 //   reflux_kernel    register correction of uncovered coarse cells.
-//   restrict_kernel  mean of the 8 children (pairwise sums).
+//   box_restrict_kernel / restrict_kernel
+//                    mean of the 8 children (pairwise sums).
+//   flag_kernel, xcopy_kernel
+//                    regrid: density-gradient flags; copies from the old
+//                    hierarchy into the new one.
 //   speed_kernel     CFL rate / max signal speed reduction (warp shuffles).
 //   totals_kernel    FP64 conserved totals over leaf cells (fixed order).
 //   pack kernels     FP64 host layout <-> ghosted device arena.
