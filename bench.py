@@ -202,6 +202,23 @@ def l1_errors(got, ref):
     return num / np.maximum(den, 1e-300)
 
 
+def cpu_model():
+    """CPU model string of the host (x86 'model name', else the Arm implementer/part codes)."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        return "unknown"
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return f"Arm implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return "unknown"
+
+
 def cpu_baseline(steps=2, stream=None):
     """The FP64 oracle as it stands, all host cores, on a bounded sample: `steps`
     RK2 steps of the full 256^3 / 32^3-patch workload.  The same steps (the oracle's
@@ -220,6 +237,16 @@ def cpu_baseline(steps=2, stream=None):
                      f"FP64, OpenMP over patches; {dt:.1f} s wall"}
     ref = o.all_cons()
     del o
+    # single thread: one RK2 step of a 128^3 sub-box of the same workload (same patches)
+    sub = ai.kelvin_helmholtz(N=128, tile=TILE)
+    o1 = orc.Oracle(sub, nthreads=1)
+    t = time.perf_counter()
+    o1.step()
+    dt1 = time.perf_counter() - t
+    del o1
+    out["single_thread"] = {"value": 128 ** 3 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"1 RK2 step of a 128^3 periodic sub-box, 64 patches of 32^3; {dt1:.1f} s wall"}
+    out["cpu_model"] = cpu_model()
     for prec in ("fp32", "fp64"):
         s = make_solver(pb, prec, True, True, stream)
         for d in dts:
@@ -257,7 +284,8 @@ def run_reference(args):
                    "full_box": f"{N}^3", "dt": "CFL 0.4 every step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_cores, "kind": "oracle",
                          "sample": f"each step = one RK2 step of a {n}^3 periodic sub-box of the 256^3 "
-                                   f"Kelvin-Helmholtz workload (same 32^3 patches), FP64 oracle, OpenMP"},
+                                   f"Kelvin-Helmholtz workload (same 32^3 patches), FP64 oracle, OpenMP",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -476,16 +504,20 @@ def main():
         so = make_solver(turb, "fp32", True, True, stream)
         so.autotune()
         d0 = turbulence_diagnostics(so.state_all(), 128, turb.gamma)
+        b0 = so.divb_norms()
         for _ in range(2):
             so.step(0.0, sync=False)
         kt = max(3, args.steps // 4)
         tt = timed_steps(torch, so, stream, kt)
         so.check()
         d1 = turbulence_diagnostics(so.state_all(), 128, turb.gamma)
+        b1 = so.divb_norms()
         so.close()
         mhd["turbulence_128"] = {"value": ws * 128 ** 3 * kt / max_over_ranks(tt), "unit": UNIT, "steps": kt,
                                  "mean_mach": [d0[0], d1[0]], "magnetic_energy": [d0[1], d1[1]],
                                  "kinetic_energy": [d0[2], d1[2]],
+                                 "divb_l1_over_b_l1": [b0[0] / b0[2], b1[0] / b1[2]],
+                                 "divb_max_over_b_max": [b0[1] / b0[3], b1[1] / b1[3]],
                                  "workload": "decaying MHD turbulence 128^3, Mach 10, gamma 1.001, beta 0.1, "
                                              "P(k) ~ k^-2 (seeded); diagnostics before and after the "
                                              f"{kt + 2} steps"}

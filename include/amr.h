@@ -214,6 +214,17 @@ amr_status amr_get_state_all(amr_handle* h, double* packed);
  * volume, accumulated in FP64 in a fixed order.  Synchronises. */
 amr_status amr_conserved_totals(amr_handle* h, double* out);
 
+/* GLM-MHD diagnostic of the divergence constraint that psi controls (Sec. 7.1;
+ * the paper prints no norm, this is the plain centred difference).  Refills the
+ * face ghosts of every level at the current time (ghost and old-time buffers
+ * only, as before regrid flagging; the next step refills them anyway), then over
+ * leaf cells, with D = sum_d (B_d(i+e_d) - B_d(i-e_d)) / (2 dx_d) and
+ * b = |B| / min_d dx_d on the cell's level:
+ *   out[0] = sum |D| dV,  out[1] = max |D|,  out[2] = sum b dV,  out[3] = max b
+ * (FP64; out[0]/out[2] and out[1]/out[3] are dimensionless).  out: 4 caller-owned
+ * host doubles.  Call between steps.  AMR_ERR_ARG when nvar != 9.  Synchronises. */
+amr_status amr_divb_norms(amr_handle* h, double* out);
+
 /* Query: device-detected non-physical state since the last call (clears it).
  * Synchronises.  Returns AMR_OK or AMR_ERR_NONPHYSICAL. */
 amr_status amr_check(amr_handle* h);

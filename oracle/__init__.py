@@ -97,6 +97,8 @@ def lib():
             L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_double, dp]
             L.orc_step.restype = ctypes.c_int
             L.orc_totals.argtypes = [ctypes.c_void_p, dp]
+            L.orc_divb.argtypes = [ctypes.c_void_p, dp]
+            L.orc_divb.restype = ctypes.c_int
             L.orc_last_ch.argtypes = [ctypes.c_void_p]
             L.orc_last_ch.restype = ctypes.c_double
             L.orc_fill_ghosts.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double]
@@ -221,6 +223,14 @@ class Oracle:
     def totals(self) -> np.ndarray:
         out = np.zeros(self.nvar)
         lib().orc_totals(self._h, _dp(out))
+        return out
+
+    def divb_norms(self) -> np.ndarray:
+        """[sum |div B| dV, max |div B|, sum |B|/dx_min dV, max |B|/dx_min] over
+        leaf cells after a ghost refill at the current time (GLM-MHD only)."""
+        out = np.zeros(4)
+        if lib().orc_divb(self._h, _dp(out)) != 0:
+            raise RuntimeError("oracle div B needs nvar = 9 and a valid ghost fill")
         return out
 
     def last_ch(self) -> float:

@@ -908,6 +908,51 @@ void orc_totals(const orc_sim* s, double* out) {
   }
 }
 
+/* Divergence of B over leaf cells (Sec. 7.1: the GLM field psi exists to keep
+ * div B small; the paper prints no diagnostic, this one is the plain central
+ * difference of the cell-centred field).  Face ghosts of every level are first
+ * refilled at the current time, as for the regrid flags. */
+int orc_divb(orc_sim* s, double* out) {
+  if (s->V != 9) return -1;
+  for (int l = 0; l < s->nlev; ++l) save_old_level(s, l);
+  for (int l = 0; l < s->nlev; ++l)
+    if (fill_ghosts_level(s, l, 0, 1.0)) return -1;
+  double l1 = 0.0, dmax = 0.0, bsum = 0.0, bmax = 0.0;
+  for (int pi = 0; pi < s->np; ++pi) {
+    const opatch* p = &s->P[pi];
+    double h[3], vol = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      h[d] = s->dx0[d] / (double)(1 << p->level);
+      vol *= h[d];
+    }
+    const double hmin = fmin(h[0], fmin(h[1], h[2]));
+    const double* Bx = p->U + 5 * p->ncell_g;
+    const double* By = p->U + 6 * p->ncell_g;
+    const double* Bz = p->U + 7 * p->ncell_g;
+    for (int k = 0; k < p->n[2]; ++k)
+      for (int j = 0; j < p->n[1]; ++j)
+        for (int i = 0; i < p->n[0]; ++i) {
+          if (p->covered && p->covered[((size_t)k * p->n[1] + j) * p->n[0] + i]) continue;
+          /* d(B_d)/dx_d by the centred difference over two cells, summed over d */
+          const double ddx = (Bx[gidx(p, i + 1, j, k)] - Bx[gidx(p, i - 1, j, k)]) / (2.0 * h[0]);
+          const double ddy = (By[gidx(p, i, j + 1, k)] - By[gidx(p, i, j - 1, k)]) / (2.0 * h[1]);
+          const double ddz = (Bz[gidx(p, i, j, k + 1)] - Bz[gidx(p, i, j, k - 1)]) / (2.0 * h[2]);
+          const double div = fabs(ddx + ddy + ddz);
+          const size_t c = gidx(p, i, j, k);
+          const double bm = sqrt(Bx[c] * Bx[c] + By[c] * By[c] + Bz[c] * Bz[c]) / hmin;
+          l1 += div * vol;
+          bsum += bm * vol;
+          if (div > dmax) dmax = div;
+          if (bm > bmax) bmax = bm;
+        }
+  }
+  out[0] = l1;
+  out[1] = dmax;
+  out[2] = bsum;
+  out[3] = bmax;
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Regridding (Sec. 3: the hierarchy is created and refined on the host)     */
 /* ------------------------------------------------------------------------ */

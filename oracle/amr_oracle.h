@@ -66,6 +66,12 @@ int orc_step(orc_sim* s, double dt, double* dt_used);
 void orc_totals(const orc_sim* s, double* out);
 /* Cleaning speed used by the last step (MHD). */
 double orc_last_ch(const orc_sim* s);
+/* GLM-MHD only (-1 otherwise): refill the face ghosts of every level at the
+ * current time, then over leaf cells, with D = sum_d (B_d(i+e_d) - B_d(i-e_d)) / (2 dx_d)
+ * and b = |B| / min_d dx_d of the cell's level:
+ *   out[0] = sum |D| dV,  out[1] = max |D|,  out[2] = sum b dV,  out[3] = max b.
+ * out[0]/out[2] and out[1]/out[3] are dimensionless divergence errors. */
+int orc_divb(orc_sim* s, double* out);
 
 /* ---- test hooks: fill the face ghosts of one level (state 0: U, 1: U1) at
  * parent-time fraction alpha, and read a patch's full ghosted array

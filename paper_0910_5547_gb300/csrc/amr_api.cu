@@ -100,6 +100,7 @@ struct amr_handle {
   amr_status sched_status = AMR_OK;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaMemPool_t pool = nullptr;   // stream-ordered device memory (no caller allocator)
   OpsBase* ops = nullptr;
   std::string err;
   Plan plan;
@@ -184,14 +185,28 @@ cudaEvent_t next_event(amr_handle* h, int* idx) {
   } while (0)
 
 // Device memory of a handle: the caller's allocator (dev_alloc / dev_free) or
-// stream-ordered cudaMallocAsync / cudaFreeAsync on the handle's stream.
+// stream-ordered allocations on the handle's stream from the handle's own memory
+// pool.  The pool keeps freed memory mapped (release threshold: unlimited), so a
+// regrid that swaps a multi-GB arena for a new one reuses the pages instead of
+// mapping fresh ones; amr_destroy returns it all.
 cudaError_t dmalloc(amr_handle* h, void** p, size_t bytes) {
   bytes = std::max<size_t>(bytes, 256);
   if (h->cfg.dev_alloc && h->cfg.dev_free) {
     *p = h->cfg.dev_alloc(bytes, h->stream, h->cfg.alloc_ctx);
     return *p ? cudaSuccess : cudaErrorMemoryAllocation;
   }
+  if (h->pool) return cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
   return cudaMallocAsync(p, bytes, h->stream);
+}
+
+// The packed FP64 staging buffer of the host copies (set/get state) is made on
+// first use after each install: regrids never need it.
+cudaError_t ensure_packed(amr_handle* h) {
+  if (h->packed) return cudaSuccess;
+  void* p = nullptr;
+  cudaError_t e = dmalloc(h, &p, std::max<int64_t>(h->plan.packed_elems, 1) * sizeof(double));
+  if (e == cudaSuccess) h->packed = static_cast<double*>(p);
+  return e;
 }
 
 void dfree(amr_handle* h, void* p) {
@@ -560,8 +575,6 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     CK(cudaMemsetAsync(h->Uold, 0, pl.arena_elems * es, h->stream));
     CK(dmalloc(h, &h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
   }
-  CK(dmalloc(h, &p, std::max<int64_t>(pl.packed_elems, 1) * sizeof(double)));
-  h->packed = static_cast<double*>(p);
   CK(dmalloc(h, &p, (size_t)h->nchunk * nv * sizeof(double)));
   h->partial = static_cast<double*>(p);
   CK(dmalloc(h, &p, 16 * sizeof(double)));
@@ -806,6 +819,23 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
     h->own_stream = true;
   }
   h->ops = make_ops(*cfg);
+  if (!(cfg->dev_alloc && cfg->dev_free)) {
+    int dev = 0;
+    cudaError_t pe = cudaGetDevice(&dev);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    uint64_t keep = UINT64_MAX;
+    if (pe == cudaSuccess) pe = cudaMemPoolCreate(&h->pool, &props);
+    if (pe == cudaSuccess) pe = cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      g_global_err = "creation of the device memory pool failed";
+      amr_destroy(h);
+      return AMR_ERR_CUDA;
+    }
+  }
   void* p = nullptr;
   if (dmalloc(h, &p, sizeof(StepParams)) != cudaSuccess) {
     g_global_err = "allocation of the step parameters failed";
@@ -876,6 +906,7 @@ amr_status amr_set_patches(amr_handle* h, int npatch, const amr_patch* patches, 
     size_t n = (size_t)P[i].n[0] * P[i].n[1] * P[i].n[2] * nv;
     std::memcpy(host.data() + pl.packed_off[i], state[i], n * sizeof(double));
   }
+  CK(ensure_packed(h));
   CK(cudaMemcpyAsync(h->packed, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemsetAsync(&h->params->bad, 0, sizeof(unsigned int), h->stream));
   CK(h->ops->pack_in(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->packed, h->U,
@@ -1048,6 +1079,7 @@ amr_status amr_set_state(amr_handle* h, const double* packed, int state_kind) {
   if (!packed) return fail(h, AMR_ERR_ARG, "null state buffer");
   if (state_kind != AMR_STATE_CONSERVED && state_kind != AMR_STATE_PRIMITIVE)
     return fail(h, AMR_ERR_ARG, "bad state_kind");
+  CK(ensure_packed(h));
   CK(cudaMemcpyAsync(h->packed, packed, h->plan.packed_elems * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(h->ops->pack_in(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->packed, h->U,
                      state_kind == AMR_STATE_PRIMITIVE, h->params));
@@ -1097,6 +1129,7 @@ amr_status amr_cfl_dt(amr_handle* h, double* dt) {
 amr_status amr_get_state_all(amr_handle* h, double* packed) {
   if (!h || !packed) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  CK(ensure_packed(h));
   CK(h->ops->pack_out(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, h->packed));
   h->launches += 1;
   CK(cudaMemcpyAsync(packed, h->packed, h->plan.packed_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1108,6 +1141,7 @@ amr_status amr_get_state(amr_handle* h, int patch, double* out) {
   if (!h || !out) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
   if (patch < 0 || patch >= (int)h->plan.patches.size()) return fail(h, AMR_ERR_ARG, "patch index out of range");
+  CK(ensure_packed(h));
   CK(h->ops->pack_out(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, h->packed));
   h->launches += 1;
   const HPatch& P = h->plan.patches[patch];
@@ -1125,6 +1159,25 @@ amr_status amr_conserved_totals(amr_handle* h, double* out) {
                     h->d_level_vol, h->partial, h->totals));
   h->launches += 2;
   CK(cudaMemcpyAsync(out, h->totals, h->plan.nvar * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_divb_norms(amr_handle* h, double* out) {
+  if (!h || !out) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  if (h->plan.nvar != 9) return fail(h, AMR_ERR_ARG, "div B needs nvar = 9 (GLM-MHD)");
+  Range range("div B");
+  const int nlev = (int)h->dl.size();
+  const size_t es = h->ops->elem_size();
+  if (nlev > 1)
+    CK(cudaMemcpyAsync(h->Uold, h->U, h->plan.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
+  h->counting = 0;
+  for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+  CK(h->ops->divb(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, h->d_cover, h->d_cover_first, h->dx0,
+                  h->partial, h->totals));
+  h->launches += h->counting + 2;
+  CK(cudaMemcpyAsync(out, h->totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return AMR_OK;
 }
@@ -1194,6 +1247,7 @@ void amr_destroy(amr_handle* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   dfree(h, h->params);
   if (h->stream) cudaStreamSynchronize(h->stream);   // stream-ordered frees done
+  if (h->pool) cudaMemPoolDestroy(h->pool);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h->ops;
   delete h;

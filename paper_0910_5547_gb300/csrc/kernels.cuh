@@ -24,6 +24,7 @@
 //                    hierarchy into the new one.
 //   speed_kernel     CFL rate / max signal speed reduction (warp shuffles).
 //   totals_kernel    FP64 conserved totals over leaf cells (fixed order).
+//   divb_kernel      GLM-MHD: FP64 norms of the centred div B over leaf cells.
 //   pack kernels     FP64 host layout <-> ghosted device arena.
 #pragma once
 #include <cuda_runtime.h>
@@ -976,6 +977,83 @@ __global__ void totals_final_kernel(const double* partial, int nchunk, double* o
     double s = 0.0;
     for (int c = 0; c < nchunk; ++c) s += partial[(size_t)c * NV + v];
     out[v] = s;
+  }
+}
+
+// div B over the leaf cells of each chunk (GLM-MHD, face ghosts filled): per chunk
+// {sum |D| dV, max |D|, sum |B|/dx_min dV, max |B|/dx_min} with
+// D = sum_d (B_d(i + e_d) - B_d(i - e_d)) / (2 dx_d), in FP64 without contraction.
+template <typename T, int NV>
+__global__ void divb_kernel(const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const T* U,
+                            const CoverBox* cover, const int* cover_first, double dx0, double dy0, double dz0,
+                            double* partial) {
+  static_assert(NV == 9, "div B needs the magnetic field");
+  __shared__ double red[4][256];
+  for (int s = blockIdx.x; s < nchunk; s += gridDim.x) {
+    const ChunkDesc ch = chunks[s];
+    const PatchDesc P = desc[ch.patch];
+    const int cb0 = cover_first[ch.patch], cb1 = cover_first[ch.patch + 1];
+    const double sc = 1.0 / (double)(1 << P.level);
+    const double hx = dx0 * sc, hy = dy0 * sc, hz = dz0 * sc;
+    const double vol = __dmul_rn(__dmul_rn(hx, hy), hz);
+    const double hmin = fmin(hx, fmin(hy, hz));
+    const T* Bx = U + P.off + 5 * P.vstride;
+    const T* By = U + P.off + 6 * P.vstride;
+    const T* Bz = U + P.off + 7 * P.vstride;
+    const int plane = P.pitch * P.m1;
+    double l1 = 0.0, dmx = 0.0, bs = 0.0, bmx = 0.0;
+    for (int e = threadIdx.x; e < ch.count; e += blockDim.x) {
+      const int idx = ch.begin + e;
+      const int i = idx % P.n[0], j = (idx / P.n[0]) % P.n[1], k = idx / (P.n[0] * P.n[1]);
+      bool covered = false;
+      for (int b = cb0; b < cb1 && !covered; ++b) {
+        const CoverBox cb = cover[b];
+        covered = i >= cb.lo[0] && i < cb.lo[0] + cb.n[0] && j >= cb.lo[1] && j < cb.lo[1] + cb.n[1] &&
+                  k >= cb.lo[2] && k < cb.lo[2] + cb.n[2];
+      }
+      if (covered) continue;
+      const int64_t c = cell_index(P, i, j, k);
+      const double ddx = ((double)Bx[c + 1] - (double)Bx[c - 1]) / (2.0 * hx);
+      const double ddy = ((double)By[c + P.pitch] - (double)By[c - P.pitch]) / (2.0 * hy);
+      const double ddz = ((double)Bz[c + plane] - (double)Bz[c - plane]) / (2.0 * hz);
+      const double dv = fabs(__dadd_rn(__dadd_rn(ddx, ddy), ddz));
+      const double bx = Bx[c], by = By[c], bz = Bz[c];
+      const double bm =
+          sqrt(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz))) / hmin;
+      l1 += __dmul_rn(dv, vol);
+      bs += __dmul_rn(bm, vol);
+      dmx = fmax(dmx, dv);
+      bmx = fmax(bmx, bm);
+    }
+    red[0][threadIdx.x] = l1;
+    red[1][threadIdx.x] = dmx;
+    red[2][threadIdx.x] = bs;
+    red[3][threadIdx.x] = bmx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) {
+        red[0][threadIdx.x] += red[0][threadIdx.x + o];
+        red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + o]);
+        red[2][threadIdx.x] += red[2][threadIdx.x + o];
+        red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + o]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < 4) partial[(size_t)s * 4 + threadIdx.x] = red[threadIdx.x][0];
+    __syncthreads();
+  }
+}
+
+template <int NQ>   // NQ = 4 norms per chunk: even ones summed, odd ones maxed
+__global__ void divb_final_kernel(const double* partial, int nchunk, double* out) {
+  const int v = threadIdx.x;
+  if (v < NQ) {
+    double a = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const double x = partial[(size_t)c * NQ + v];
+      a = (v & 1) ? fmax(a, x) : a + x;
+    }
+    out[v] = a;
   }
 }
 

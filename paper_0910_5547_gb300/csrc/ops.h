@@ -59,6 +59,10 @@ struct OpsBase {
   virtual cudaError_t totals(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
                              const void* U, const CoverBox* cover, const int* cover_first, const double* level_vol,
                              double* partial, double* out) = 0;
+  // GLM-MHD only (cudaErrorInvalidValue otherwise): out[4] = div B norms over leaf cells
+  virtual cudaError_t divb(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
+                           const void* U, const CoverBox* cover, const int* cover_first, const double dx0[3],
+                           double* partial, double* out) = 0;
   virtual cudaError_t pack_in(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
                               const int64_t* packed_off, const double* src, void* U, int prim, StepParams* prm) = 0;
   virtual cudaError_t flag(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,

@@ -193,6 +193,19 @@ struct Ops final : OpsBase {
     return cudaGetLastError();
   }
 
+  cudaError_t divb(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const void* U,
+                   const CoverBox* cover, const int* cover_first, const double dx0[3], double* partial,
+                   double* out) override {
+    if constexpr (NV == 9) {
+      divb_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, static_cast<const T*>(U), cover,
+                                                          cover_first, dx0[0], dx0[1], dx0[2], partial);
+      divb_final_kernel<4><<<1, 32, 0, s>>>(partial, nchunk, out);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
+
   cudaError_t pack_in(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
                       const int64_t* packed_off, const double* src, void* U, int prim, StepParams* prm) override {
     pack_in_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, packed_off, src,

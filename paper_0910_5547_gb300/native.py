@@ -36,7 +36,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
            "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count",
-           "amr_set_regrid_schedule", "amr_cell_updates"]
+           "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -146,6 +146,8 @@ def load():
     L.amr_get_regrid_timing.restype = ctypes.c_int
     L.amr_floor_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
     L.amr_floor_count.restype = ctypes.c_int
+    L.amr_divb_norms.argtypes = [H, dp]
+    L.amr_divb_norms.restype = ctypes.c_int
     L.amr_get_patches.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -267,6 +269,13 @@ def amr_get_state_all(h, out: np.ndarray | None = None) -> np.ndarray:
 def amr_conserved_totals(h, nvar: int) -> np.ndarray:
     out = np.zeros(nvar, dtype=np.float64)
     _check(h, load().amr_conserved_totals(h, _dp(out)))
+    return out
+
+
+def amr_divb_norms(h) -> np.ndarray:
+    """[sum |div B| dV, max |div B|, sum |B|/dx_min dV, max |B|/dx_min] over leaf cells."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(h, load().amr_divb_norms(h, _dp(out)))
     return out
 
 

@@ -98,6 +98,11 @@ class Solver:
     def totals(self) -> np.ndarray:
         return N.amr_conserved_totals(self.h, self.nvar)
 
+    def divb_norms(self) -> np.ndarray:
+        """GLM-MHD: [sum |div B| dV, max |div B|, sum |B|/dx_min dV, max |B|/dx_min]
+        over leaf cells (centred differences after a ghost refill)."""
+        return N.amr_divb_norms(self.h)
+
     def check(self):
         N.amr_check(self.h)
 
