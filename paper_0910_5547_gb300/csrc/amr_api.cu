@@ -101,6 +101,8 @@ struct amr_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaMemPool_t pool = nullptr;   // stream-ordered device memory (no caller allocator)
+  unsigned char* stage = nullptr; // pinned host staging of the table uploads
+  size_t stage_cap = 0, stage_cap_seen = 0;
   OpsBase* ops = nullptr;
   std::string err;
   Plan plan;
@@ -440,12 +442,46 @@ amr_status read_bad(amr_handle* h) {
   return AMR_OK;
 }
 
-template <typename X>
-size_t put(std::vector<unsigned char>& buf, const std::vector<X>& v) {
-  size_t off = (buf.size() + 255) / 256 * 256;
-  buf.resize(off + v.size() * sizeof(X) + 1);
-  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(X));
-  return off;
+// Layout of many host tables in one upload buffer (256-byte aligned offsets),
+// assigned first and copied afterwards in parallel pieces, so no buffer grows
+// or is zero-filled on the way.  The source vectors must outlive copy_to().
+struct TablePack {
+  struct Item { const unsigned char* src; size_t bytes, off; };
+  std::vector<Item> items;
+  size_t size = 1;
+  template <typename X, typename A>
+  size_t add(const std::vector<X, A>& v) {
+    const size_t off = (size + 255) / 256 * 256;
+    items.push_back({reinterpret_cast<const unsigned char*>(v.data()), v.size() * sizeof(X), off});
+    size = off + v.size() * sizeof(X) + 1;
+    return off;
+  }
+  void copy_to(unsigned char* dst) const {
+    constexpr size_t kPiece = size_t(1) << 20;
+    std::vector<Item> pieces;
+    for (const Item& it : items)
+      for (size_t b = 0; b < it.bytes; b += kPiece)
+        pieces.push_back({it.src + b, std::min(kPiece, it.bytes - b), it.off + b});
+    parallel_run((int)pieces.size(), [&](int i) { std::memcpy(dst + pieces[i].off, pieces[i].src, pieces[i].bytes); });
+  }
+};
+
+// Pinned host staging of at least `bytes` (kept across installs, doubled when
+// short).  Waits for the stream first: the previous upload may still read it.
+cudaError_t host_stage(amr_handle* h, size_t bytes) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess || bytes <= h->stage_cap) return e;
+  if (h->stage) cudaFreeHost(h->stage);
+  h->stage = nullptr;
+  h->stage_cap = 0;
+  const size_t cap = std::max(bytes, 2 * h->stage_cap_seen);
+  e = cudaMallocHost(reinterpret_cast<void**>(&h->stage), cap);
+  if (e != cudaSuccess) {
+    h->stage = nullptr;
+    return e;
+  }
+  h->stage_cap = h->stage_cap_seen = cap;
+  return cudaSuccess;
 }
 
 // Upload the stage work items of every level into their own device buffer.
@@ -530,36 +566,38 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     reg_off[l] = nregd;
     nregd += 2 * (size_t)nv * pl.levels[l].regs.size();
   }
-  std::vector<unsigned char> buf;
-  size_t o_desc = put(buf, pl.desc);
-  size_t o_chunks = put(buf, h->chunks);
-  size_t o_cover = put(buf, pl.cover);
-  size_t o_cover_first = put(buf, pl.cover_first);
-  size_t o_packed_off = put(buf, pl.packed_off);
+  TablePack buf;
+  size_t o_desc = buf.add(pl.desc);
+  size_t o_chunks = buf.add(h->chunks);
+  size_t o_cover = buf.add(pl.cover);
+  size_t o_cover_first = buf.add(pl.cover_first);
+  size_t o_packed_off = buf.add(pl.packed_off);
   std::vector<double> lvol(nlev);
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
-  size_t o_lvol = put(buf, lvol);
+  size_t o_lvol = buf.add(lvol);
   struct FlatOffs { size_t boxes, first, chunk; };
   struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
   std::vector<Offs> lo(nlev);
-  auto put_flat = [&](const auto& f) { return FlatOffs{put(buf, f.boxes), put(buf, f.first), put(buf, f.chunk_box)}; };
+  auto put_flat = [&](const auto& f) { return FlatOffs{buf.add(f.boxes), buf.add(f.first), buf.add(f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = pl.levels[l];
     lo[l].fg = put_flat(L.fghost);
     lo[l].fa = put_flat(L.fgather);
     lo[l].fp = put_flat(L.fprolong);
     lo[l].fr = put_flat(L.frestrict);
-    lo[l].ghost = put(buf, L.ghost);
-    lo[l].prolong = put(buf, L.prolong);
-    lo[l].gather = put(buf, L.gather);
-    lo[l].restr = put(buf, L.restrict_segs);
-    lo[l].regs = put(buf, L.regs);
-    lo[l].rf = put(buf, L.reflux_first);
+    lo[l].ghost = buf.add(L.ghost);
+    lo[l].prolong = buf.add(L.prolong);
+    lo[l].gather = buf.add(L.gather);
+    lo[l].restr = buf.add(L.restrict_segs);
+    lo[l].regs = buf.add(L.regs);
+    lo[l].rf = buf.add(L.reflux_first);
   }
   void* p = nullptr;
-  CK(dmalloc(h, &p, buf.size()));
+  CK(dmalloc(h, &p, buf.size));
   h->tables = static_cast<unsigned char*>(p);
-  CK(cudaMemcpyAsync(h->tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(host_stage(h, buf.size));
+  buf.copy_to(h->stage);
+  CK(cudaMemcpyAsync(h->tables, h->stage, buf.size, cudaMemcpyHostToDevice, h->stream));
   h->d_desc = reinterpret_cast<const PatchDesc*>(h->tables + o_desc);
   h->d_chunks = reinterpret_cast<const ChunkDesc*>(h->tables + o_chunks);
   h->d_cover = reinterpret_cast<const CoverBox*>(h->tables + o_cover);
@@ -713,7 +751,7 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
     free_bufs(h, old);
     return st;
   }
-  std::vector<unsigned char> buf;
+  TablePack buf;
   std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
   cudaError_t ei = cudaStreamSynchronize(h->stream);   // uploads of the new tables done
   if (ei != cudaSuccess) {
@@ -722,12 +760,16 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   }
   lap(AMR_RG_INSTALL);
   for (size_t l = 0; l < fill.copy.size(); ++l) {
-    o_copy[l] = put(buf, fill.copy[l]);
-    o_fresh[l] = put(buf, fill.fresh[l]);
+    o_copy[l] = buf.add(fill.copy[l]);
+    o_fresh[l] = buf.add(fill.fresh[l]);
   }
   unsigned char* d_fill = nullptr;
-  cudaError_t e = dmalloc(h, reinterpret_cast<void**>(&d_fill), std::max<size_t>(buf.size(), 1));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_fill, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = dmalloc(h, reinterpret_cast<void**>(&d_fill), buf.size);
+  if (e == cudaSuccess) e = host_stage(h, buf.size);
+  if (e == cudaSuccess) {
+    buf.copy_to(h->stage);
+    e = cudaMemcpyAsync(d_fill, h->stage, buf.size, cudaMemcpyHostToDevice, h->stream);
+  }
   if (e == cudaSuccess && keep_end > 0)
     e = cudaMemcpyAsync(h->U, old.U, keep_end * es, cudaMemcpyDeviceToDevice, h->stream);
   const int nl_new = (int)h->dl.size();
@@ -1248,6 +1290,7 @@ void amr_destroy(amr_handle* h) {
   dfree(h, h->params);
   if (h->stream) cudaStreamSynchronize(h->stream);   // stream-ordered frees done
   if (h->pool) cudaMemPoolDestroy(h->pool);
+  if (h->stage) cudaFreeHost(h->stage);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h->ops;
   delete h;

@@ -12,6 +12,10 @@
 #include <memory>
 #include <array>
 #include <thread>
+#include <mutex>
+#include <condition_variable>
+#include <functional>
+#include <unistd.h>
 #include <atomic>
 #include <climits>
 #include <unordered_map>
@@ -92,29 +96,99 @@ std::vector<Rect> mask_rects(const unsigned char* m, int A, int B) {
 }
 std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) { return mask_rects(m.data(), A, B); }
 
-// f(i) for i in [0, n) on the host's cores (chunks of 8 indices per grab);
-// every caller writes only to slot i of its outputs, so the result does not
-// depend on the thread count.
+// Persistent worker threads for the planner's parallel loops (spawning threads
+// per loop costs a few hundred microseconds, and a rebuild runs dozens of loops).
+// A job is f(i) for i in [0, n), grabbed in chunks of 8 by the caller and the
+// workers.  run() returns false (the caller then loops serially) when called
+// from inside a job, while another thread's job is running, or in a child
+// process forked after the workers started.
+class WorkerPool {
+ public:
+  static WorkerPool& instance() {
+    static WorkerPool pool;
+    return pool;
+  }
+  bool run(int n, const std::function<void(int)>& f) {
+    if (inside_ || nt_ <= 1 || getpid() != pid_) return false;
+    std::unique_lock<std::mutex> busy(busy_, std::try_to_lock);
+    if (!busy.owns_lock()) return false;
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      job_ = &f;
+      n_ = n;
+      next_.store(0);
+      pending_ = (int)threads_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> lk(m_);
+    done_.wait(lk, [&] { return pending_ == 0; });
+    job_ = nullptr;
+    return true;
+  }
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_)
+      if (t.joinable()) t.join();
+  }
+
+ private:
+  WorkerPool() : pid_(getpid()) {
+    nt_ = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u);
+    for (int t = 1; t < nt_; ++t) threads_.emplace_back([this] { loop(); });
+  }
+  void work() {
+    inside_ = true;
+    for (;;) {
+      const int i0 = next_.fetch_add(8);
+      if (i0 >= n_) break;
+      const int i1 = std::min(i0 + 8, n_);
+      for (int i = i0; i < i1; ++i) (*job_)(i);
+    }
+    inside_ = false;
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      std::unique_lock<std::mutex> lk(m_);
+      cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      lk.unlock();
+      work();
+      lk.lock();
+      if (--pending_ == 0) done_.notify_one();
+    }
+  }
+  static thread_local bool inside_;
+  const pid_t pid_;
+  int nt_ = 1;
+  std::vector<std::thread> threads_;
+  std::mutex busy_, m_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* job_ = nullptr;
+  int n_ = 0;
+  std::atomic<int> next_{0};
+  int pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+thread_local bool WorkerPool::inside_ = false;
+
+// f(i) for i in [0, n) on the host's cores; every caller writes only to slot i
+// of its outputs, so the result does not depend on the thread count.
 template <class F>
 void parallel_for(int n, F&& f) {
-  const int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u);
-  if (n < 64 || nt <= 1) {
-    for (int i = 0; i < n; ++i) f(i);
-    return;
+  if (n >= 64) {
+    const std::function<void(int)> job = [&](int i) { f(i); };
+    if (WorkerPool::instance().run(n, job)) return;
   }
-  std::atomic<int> next(0);
-  auto work = [&]() {
-    for (;;) {
-      const int i0 = next.fetch_add(8);
-      if (i0 >= n) break;
-      const int i1 = std::min(i0 + 8, n);
-      for (int i = i0; i < i1; ++i) f(i);
-    }
-  };
-  std::vector<std::thread> th;
-  for (int t = 1; t < std::min(nt, (n + 7) / 8); ++t) th.emplace_back(work);
-  work();
-  for (auto& t : th) t.join();
+  for (int i = 0; i < n; ++i) f(i);
 }
 
 // Bucket index of the patches of one level: a query returns the patches whose
@@ -324,20 +398,30 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
     if (first[l + 1] == 0) { msg = fmt("level %d has no patches", l); return AMR_ERR_NESTING; }
     first[l + 1] += first[l];
   }
-  // no same-level overlap
-  std::vector<int> cand;
+  // no same-level overlap (patches checked in parallel; the first failing one
+  // in patch order is reported)
   for (int l = 0; l <= maxl; ++l) {
     PatchIndex ix(P, first[l], first[l + 1] - first[l]);
-    for (int a = first[l]; a < first[l + 1]; ++a) {
+    const int n = first[l + 1] - first[l];
+    std::vector<int> hit(n, -1);
+    parallel_for(n, [&](int k) {
+      const int a = first[l] + k;
+      std::vector<int> cand;
       int lo[3], hi[3];
       for (int d = 0; d < 3; ++d) { lo[d] = P[a].lo[d]; hi[d] = P[a].lo[d] + P[a].n[d]; }
       ix.query(lo, hi, cand);
       for (int b : cand)
         if (b != a && boxes_overlap(P[a], P[b])) {
-          msg = fmt("patches %d and %d overlap on level %d", std::min(a, b), std::max(a, b), l);
-          return AMR_ERR_NESTING;
+          hit[k] = b;
+          return;
         }
-    }
+    });
+    for (int k = 0; k < n; ++k)
+      if (hit[k] >= 0) {
+        const int a = first[l] + k, b = hit[k];
+        msg = fmt("patches %d and %d overlap on level %d", std::min(a, b), std::max(a, b), l);
+        return AMR_ERR_NESTING;
+      }
   }
   // level 0 tiles the domain
   int64_t vol0 = 0;
@@ -348,7 +432,11 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
   // proper nesting: footprint grown by two parent cells is covered by the parent level
   for (int l = 1; l <= maxl; ++l) {
     PatchIndex cix(P, first[l - 1], first[l] - first[l - 1]);
-    for (int i = first[l]; i < first[l + 1]; ++i) {
+    const int n = first[l + 1] - first[l];
+    std::vector<unsigned char> bad(n, 0);
+    parallel_for(n, [&](int k) {
+      const int i = first[l] + k;
+      std::vector<int> cand;
       const HPatch& p = P[i];
       std::vector<std::pair<int, int>> iv[3];
       int64_t need = 1;
@@ -379,12 +467,14 @@ amr_status validate_patches(const amr_config& c, const std::vector<HPatch>& P, s
         }
         got += v;
       }
-      if (got != need) {
+      bad[k] = got != need;
+    });
+    for (int k = 0; k < n; ++k)
+      if (bad[k]) {
         msg = fmt("patch %d (level %d) is not properly nested: its footprint grown by 2 parent cells "
-                  "is not covered by level %d", i, l, l - 1);
+                  "is not covered by level %d", first[l] + k, l, l - 1);
         return AMR_ERR_NESTING;
       }
-    }
   }
   return AMR_OK;
 }
@@ -541,6 +631,8 @@ void flatten_restrict(const Plan& plan, const std::vector<RestrictSeg>& segs, Fl
 }
 
 }  // namespace
+
+void parallel_run(int n, const std::function<void(int)>& f) { parallel_for(n, f); }
 
 void build_flat(Plan& plan) {
   for (LevelPlan& L : plan.levels) {
@@ -949,33 +1041,35 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
         return AMR_ERR_NESTING;
       }
     // group by coarse cell, keeping the task order ((d, side, patch)) inside a
-    // cell: a stable counting sort by coarse patch over chunks of tasks (per-chunk
-    // histograms, parallel scatter), then a stable sort by cell inside each patch
+    // cell: a stable counting sort by coarse patch (all of level l-1) over chunks
+    // of tasks (per-chunk histograms, parallel scatter), then a stable sort by cell
+    // inside each coarse patch
+    const int c0 = C.first, nc = C.count;
     const int nchunk = std::max(1, std::min(64, ntask / 64));
     auto chunk_lo = [&](int k) { return (int)((int64_t)ntask * k / nchunk); };
-    std::vector<std::vector<int>> hist(nchunk, std::vector<int>(np, 0));
+    std::vector<std::vector<int>> hist(nchunk, std::vector<int>(nc, 0));
     parallel_for(nchunk, [&](int k) {
       for (int task = chunk_lo(k); task < chunk_lo(k + 1); ++task)
-        for (const RegFace& r : rs[task]) hist[k][r.cpatch]++;
+        for (const RegFace& r : rs[task]) hist[k][r.cpatch - c0]++;
     });
-    std::vector<int> start(np + 1, 0);
+    std::vector<int> start(nc + 1, 0);
     {
       size_t run = 0;
-      for (int c = 0; c < np; ++c) {
+      for (int c = 0; c < nc; ++c) {
         start[c] = (int)run;
         for (int k = 0; k < nchunk; ++k) {
           const int n = hist[k][c];
-          hist[k][c] = (int)run;   // first slot of chunk k's registers of coarse patch c
+          hist[k][c] = (int)run;   // first slot of chunk k's registers of coarse patch c0 + c
           run += n;
         }
       }
-      start[np] = (int)run;
+      start[nc] = (int)run;
     }
-    std::vector<RegFace> regs(start[np]);
+    RegVec regs(start[nc]);   // not zero-filled: the scatter threads touch the pages first
     parallel_for(nchunk, [&](int k) {
       std::vector<int>& pos = hist[k];
       for (int task = chunk_lo(k); task < chunk_lo(k + 1); ++task)
-        for (const RegFace& r : rs[task]) regs[pos[r.cpatch]++] = r;
+        for (const RegFace& r : rs[task]) regs[pos[r.cpatch - c0]++] = r;
     });
     std::vector<std::vector<int>>().swap(hist);
     std::vector<std::vector<RegFace>>().swap(rs);
@@ -983,8 +1077,8 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
       return a.cpatch == b.cpatch && a.cidx[0] == b.cidx[0] && a.cidx[1] == b.cidx[1] && a.cidx[2] == b.cidx[2];
     };
     // per coarse patch: sort by cell, count the unique cells (CSR built below)
-    std::vector<int> nuniq(np + 1, 0);
-    parallel_for(np, [&](int c) {
+    std::vector<int> nuniq(nc + 1, 0);
+    parallel_for(nc, [&](int c) {
       std::stable_sort(regs.begin() + start[c], regs.begin() + start[c + 1], [](const RegFace& x, const RegFace& y) {
         return std::make_tuple(x.cidx[2], x.cidx[1], x.cidx[0]) < std::make_tuple(y.cidx[2], y.cidx[1], y.cidx[0]);
       });
@@ -993,14 +1087,14 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
         if (e == start[c] || !same_cell(regs[e], regs[e - 1])) ++u;
       nuniq[c + 1] = u;
     });
-    for (int c = 0; c < np; ++c) nuniq[c + 1] += nuniq[c];
-    L.reflux_first.assign(nuniq[np] + 1, 0);
-    parallel_for(np, [&](int c) {
+    for (int c = 0; c < nc; ++c) nuniq[c + 1] += nuniq[c];
+    L.reflux_first.assign(nuniq[nc] + 1, 0);
+    parallel_for(nc, [&](int c) {
       int u = nuniq[c];
       for (int e = start[c]; e < start[c + 1]; ++e)
         if (e == start[c] || !same_cell(regs[e], regs[e - 1])) L.reflux_first[u++] = e;
     });
-    L.reflux_first[nuniq[np]] = (int)regs.size();
+    L.reflux_first[nuniq[nc]] = (int)regs.size();
     L.regs.swap(regs);
   }
   build_flat(plan);
@@ -1149,6 +1243,68 @@ class BlockSet {
   size_t count_ = 0;
 };
 
+// Tagged blocks of one level over its whole block grid [0, n): a dense bitmap
+// whose set() may be called from many threads when the grid has at most 2^28
+// blocks, else a KeySet (set() from one thread only).  keys() lists the members
+// in (z, y, x) order.
+class TagGrid {
+ public:
+  void reset(const int n[3]) {
+    int64_t vol = 1;
+    for (int d = 0; d < 3; ++d) {
+      n_[d] = std::max(n[d], 0);
+      vol *= n_[d];
+    }
+    dense_ = vol <= ((int64_t)1 << 28);
+    bits_.assign(dense_ ? (size_t)((vol + 63) / 64) : 0, 0);
+    hash_ = KeySet();
+  }
+  bool dense() const { return dense_; }
+  void set(int x, int y, int z) {
+    if (dense_) {
+      const int64_t i = ((int64_t)z * n_[1] + y) * n_[0] + x;
+      __atomic_fetch_or(&bits_[(size_t)(i >> 6)], (uint64_t)1 << (i & 63), __ATOMIC_RELAXED);
+    } else {
+      hash_.insert(pack(x, y, z));
+    }
+  }
+  std::vector<Key> keys() const {
+    std::vector<Key> out;
+    if (!dense_) {
+      for (int64_t k : hash_.keys()) out.push_back(unpack(k));
+      std::sort(out.begin(), out.end());
+      return out;
+    }
+    // runs of words in parallel, each run's members in order, concatenated
+    const size_t nw = bits_.size();
+    const int nrun = (int)std::min<size_t>(256, (nw + 4095) / 4096);
+    std::vector<std::vector<Key>> part(std::max(nrun, 1));
+    parallel_for(nrun, [&](int r) {
+      const size_t w0 = nw * r / nrun, w1 = nw * (r + 1) / nrun;
+      for (size_t w = w0; w < w1; ++w) {
+        uint64_t b = bits_[w];
+        while (b) {
+          const int64_t i = (int64_t)(w << 6) + __builtin_ctzll(b);
+          b &= b - 1;
+          const int64_t row = i / n_[0];
+          part[r].push_back(Key{(int)(i - row * n_[0]), (int)(row % n_[1]), (int)(row / n_[1])});
+        }
+      }
+    });
+    size_t tot = 0;
+    for (const auto& v : part) tot += v.size();
+    out.reserve(tot);
+    for (const auto& v : part) out.insert(out.end(), v.begin(), v.end());
+    return out;
+  }
+
+ private:
+  int n_[3] = {0, 0, 0};
+  bool dense_ = true;
+  std::vector<uint64_t> bits_;
+  KeySet hash_;
+};
+
 }  // namespace
 
 amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
@@ -1162,10 +1318,14 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   }
   auto nb = [&](int l, int d) { return (level_n(cfg, l, d) + B - 1) / B; };
   auto per = [&](int d) { return periodic(cfg, d); };
-  std::vector<KeySet> tags(L + 1);
+  std::vector<TagGrid> tags(L + 1);   // level L (the finest allowed) is never flagged
+  for (int l = l0; l < L; ++l) {
+    const int n[3] = {nb(l, 0), nb(l, 1), nb(l, 2)};
+    tags[l].reset(n);
+  }
   // 1. flagged cells, grown by the buffer, mark blocks of their level (first on a
   //    per-patch block grid, so each block is listed once per patch; patches in
-  //    parallel, then inserted in patch order)
+  //    parallel, straight into a dense tag grid, else listed and inserted after)
   std::vector<std::vector<int64_t>> pk(old.size());
   parallel_for((int)old.size(), [&](int i) {
     const HPatch& p = old[i];
@@ -1207,21 +1367,29 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
             int n = nb(l, d);
             if (per(d)) q[d] = ((q[d] % n) + n) % n;
           }
-          pk[i].push_back(pack(q[0], q[1], q[2]));
+          if (tags[l].dense()) tags[l].set(q[0], q[1], q[2]);
+          else pk[i].push_back(pack(q[0], q[1], q[2]));
         }
   });
   for (size_t i = 0; i < old.size(); ++i)
-    for (int64_t k : pk[i]) tags[old[i].level].insert(k);
+    for (int64_t k : pk[i]) {
+      const Key b = unpack(k);
+      tags[old[i].level].set(b.x, b.y, b.z);
+    }
   // 2. a tag on level l needs its parent region (and a ring for nesting) refined on level l-1
   for (int l = L - 1; l > l0; --l) {
-    KeySet parents;   // parent blocks of the tags (8 children share one)
-    for (int64_t kb : tags[l].keys()) {
-      const Key b = unpack(kb);
-      parents.insert(pack(b.x >> 1, b.y >> 1, b.z >> 1));
+    TagGrid parents;   // parent blocks of the tags (8 children share one)
+    {
+      const int n[3] = {nb(l - 1, 0), nb(l - 1, 1), nb(l - 1, 2)};
+      parents.reset(n);
     }
-    for (int64_t kp : parents.keys()) {
-      const Key b = unpack(kp);
-      int pb[3] = {b.x, b.y, b.z};
+    const std::vector<Key> tk = tags[l].keys();
+    auto parent_of = [&](int t) { parents.set(tk[t].x >> 1, tk[t].y >> 1, tk[t].z >> 1); };
+    if (parents.dense()) parallel_for((int)tk.size(), parent_of);
+    else for (int t = 0; t < (int)tk.size(); ++t) parent_of(t);
+    const std::vector<Key> pk2 = parents.keys();
+    auto ring = [&](int t) {
+      const int pb[3] = {pk2[t].x, pk2[t].y, pk2[t].z};
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
@@ -1234,9 +1402,11 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
                 else ok = false;
               }
             }
-            if (ok) tags[l - 1].insert(pack(q[0], q[1], q[2]));
+            if (ok) tags[l - 1].set(q[0], q[1], q[2]);
           }
-    }
+    };
+    if (tags[l - 1].dense()) parallel_for((int)pk2.size(), ring);
+    else for (int t = 0; t < (int)pk2.size(); ++t) ring(t);
   }
   // 3. top-down: keep levels <= l0, then cluster refinable blocks of each level
   out.clear();
@@ -1272,12 +1442,18 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
     }
   }
   const int maxb = rp.max_patch / (2 * B);
+  // blocks of level l covered by its patches: `cover` for l0, afterwards the
+  // refined blocks of level l-1 seen through the parent coordinates
+  BlockSet prev_refine;
+  bool coarse_cover = false;
+  auto cover_count = [&](int x, int y, int z) {
+    return coarse_cover ? prev_refine.count(x >> 1, y >> 1, z >> 1) : cover.count(x, y, z);
+  };
   for (int l = l0; l < L; ++l) {
-    const std::vector<int64_t> tl = tags[l].keys();
+    const std::vector<Key> tl = tags[l].keys();   // (z, y, x) order
     std::vector<unsigned char> refinable(tl.size(), 0);
     parallel_for((int)tl.size(), [&](int ti) {
-      const int64_t kb = tl[ti];
-      const Key b = unpack(kb);
+      const Key b = tl[ti];
       bool ok = true;
       for (int dz = -1; dz <= 1 && ok; ++dz)
         for (int dy = -1; dy <= 1 && ok; ++dy)
@@ -1291,7 +1467,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
                 else outside = true;
               }
             }
-            if (!outside && !cover.count(q[0], q[1], q[2])) ok = false;
+            if (!outside && !cover_count(q[0], q[1], q[2])) ok = false;
           }
       refinable[ti] = ok;
     });
@@ -1299,23 +1475,18 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
     int rlo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, rhi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
     for (size_t ti = 0; ti < tl.size(); ++ti)
       if (refinable[ti]) {
-        const Key b = unpack(tl[ti]);
+        const Key b = tl[ti];
         order.push_back(b);
         const int c[3] = {b.x, b.y, b.z};
         for (int d = 0; d < 3; ++d) { rlo[d] = std::min(rlo[d], c[d]); rhi[d] = std::max(rhi[d], c[d] + 1); }
       }
     if (order.empty()) break;
-    BlockSet refine, done, next_cover;
+    BlockSet refine, done;
     refine.reset(rlo, rhi);
     done.reset(rlo, rhi);
     for (const Key& b : order) refine.insert(b.x, b.y, b.z);
-    {
-      int clo[3], chi[3];   // blocks of level l+1 under the refined blocks
-      for (int d = 0; d < 3; ++d) { clo[d] = 2 * rlo[d]; chi[d] = 2 * rhi[d]; }
-      next_cover.reset(clo, chi);
-    }
-    // greedy box merge in (z, y, x) order: extend along x, then y, then z
-    std::sort(order.begin(), order.end());   // (z, y, x) order
+    // greedy box merge in (z, y, x) order (the order of the tags): extend along x,
+    // then y, then z
     for (const Key& b : order) {
       if (done.count(b.x, b.y, b.z)) continue;
       auto free_ = [&](int x, int y, int z) { return refine.count(x, y, z) && !done.count(x, y, z); };
@@ -1345,12 +1516,11 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
         f.n[d] = std::min(2 * B * bn[d], Nf - f.lo[d]);
       }
       out.push_back(f);
-      // blocks of level l+1 covered by the new patch
-      for (int z = f.lo[2] / B; z < (f.lo[2] + f.n[2] + B - 1) / B; ++z)
-        for (int y = f.lo[1] / B; y < (f.lo[1] + f.n[1] + B - 1) / B; ++y)
-          for (int x = f.lo[0] / B; x < (f.lo[0] + f.n[0] + B - 1) / B; ++x) next_cover.insert(x, y, z);
     }
-    std::swap(cover, next_cover);
+    // every refinable block is now in a new patch: a block of level l+1 lies in
+    // the new patches exactly when its parent block (coordinates halved) is one
+    std::swap(prev_refine, refine);
+    coarse_cover = true;
   }
   return AMR_OK;
 }

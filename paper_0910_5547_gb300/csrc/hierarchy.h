@@ -4,7 +4,10 @@
 // coverage).  Pure C++, no CUDA calls: usable on a host without a GPU.
 #pragma once
 #include <cstdint>
+#include <functional>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/amr.h"
@@ -28,6 +31,23 @@ struct FlatList {
   int total = 0;
 };
 
+// std::allocator that default-initialises (no zero fill of trivial types), for
+// large tables that are written in parallel right after allocation.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind { using other = NoInitAlloc<U>; };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    if constexpr (sizeof...(A) == 0) ::new (static_cast<void*>(p)) U;
+    else ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+using RegVec = std::vector<RegFace, NoInitAlloc<RegFace>>;
+
 struct LevelPlan {
   int first = 0, count = 0;                  // patch range [first, first + count)
   std::vector<StageItem> items;              // stage work items, grouped by patch
@@ -39,7 +59,7 @@ struct LevelPlan {
   std::vector<CopySeg> gather;               // parent-tile gathers (level >= 1), grouped by fine patch
   std::vector<int> gather_first;
   std::vector<RestrictSeg> restrict_segs;    // this level -> parent (level >= 1)
-  std::vector<RegFace> regs;                 // coarse-fine faces of this level (level >= 1), sorted by coarse cell
+  RegVec regs;                               // coarse-fine faces of this level (level >= 1), sorted by coarse cell
   std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell
   FlatList<FlatCopy> fghost, fgather;        // the ghost and gather boxes, flattened (batched launches)
   FlatList<FlatProlong> fprolong;            // the prolongation boxes, flattened
@@ -112,5 +132,8 @@ void build_items(Plan& plan, const TileParams& tp);
 // offsets (e.g. 64 for 256-byte alignment of FP32 arrays).
 amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan,
                       std::string& msg, const TileParams& tp = TileParams());
+
+// f(0) .. f(n-1) on the host cores (the planner's thread pool policy).
+void parallel_run(int n, const std::function<void(int)>& f);
 
 }  // namespace amr
