@@ -694,33 +694,85 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
     h->counting = 0;
     for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
   }
-  // 2. density-gradient flags, one byte per interior cell
-  const size_t ncell = (size_t)(op.packed_elems / nv);
-  unsigned char* d_flags = nullptr;
-  CK(dmalloc(h, reinterpret_cast<void**>(&d_flags), std::max<size_t>(ncell, 1)));
-  cudaError_t fe = h->ops->flag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, rp.threshold,
-                                d_flags);
-  std::vector<unsigned char> hflags(ncell);
-  if (fe == cudaSuccess)
-    fe = cudaMemcpyAsync(hflags.data(), d_flags, ncell, cudaMemcpyDeviceToHost, h->stream);
-  if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
-  dfree(h, d_flags);
-  CK(fe);
-  if (!mid) h->launches += h->counting + 1;
-  else h->counting += 1;
-  std::vector<std::vector<uint8_t>> flags(op.patches.size());
-  for (size_t i = 0; i < op.patches.size(); ++i) {
-    const HPatch& p = op.patches[i];
-    if (p.level >= h->cfg.max_level) continue;
-    const size_t n = (size_t)p.n[0] * p.n[1] * p.n[2];
-    const size_t o = (size_t)(op.packed_off[i] / nv);
-    flags[i].assign(hflags.begin() + o, hflags.begin() + o + n);
-  }
-  lap(AMR_RG_FLAG);
-  // 3. cluster on the host, build the new hierarchy
-  std::vector<HPatch> newp;
+  // 2. density-gradient criterion.  Block tags made on the GPU when every
+  //    flagged level's block grid fits a bitmap (only the bitmaps come back);
+  //    otherwise one byte per interior cell, tagged on the host.
   std::string msg;
-  amr_status st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
+  {
+    amr_status pst = check_regrid_params(h->cfg, rp, msg);
+    if (pst != AMR_OK) return fail(h, pst, msg);
+  }
+  const int L = h->cfg.max_level;
+  TagArgs ta{};
+  ta.l0 = rp.min_level;
+  ta.L = L;
+  ta.block = rp.block;
+  ta.buffer = rp.buffer;
+  bool dev_tags = L < kTagLevels;
+  long long nwords = 0;
+  for (int d = 0; d < 3; ++d) ta.per[d] = h->cfg.bc[2 * d] == AMR_BC_PERIODIC;
+  for (int l = rp.min_level; l < L && dev_tags; ++l) {
+    const int64_t nbt = regrid_tag_blocks(h->cfg, rp, l, ta.nb[l]);
+    for (int d = 0; d < 3; ++d) ta.N[l][d] = h->cfg.base_n[d] << l;
+    ta.off[l] = nwords;
+    nwords += 2 * ((nbt + 63) / 64);
+    dev_tags = nbt <= kTagDenseMax;
+  }
+  std::vector<HPatch> newp;
+  amr_status st = AMR_OK;
+  if (dev_tags) {
+    unsigned int* d_words = nullptr;
+    CK(dmalloc(h, reinterpret_cast<void**>(&d_words), std::max<long long>(nwords, 2) * sizeof(unsigned int)));
+    std::vector<uint32_t> hw((size_t)nwords);
+    cudaError_t fe = cudaMemsetAsync(d_words, 0, std::max<long long>(nwords, 2) * sizeof(unsigned int), h->stream);
+    if (fe == cudaSuccess && nwords > 0)
+      fe = h->ops->tag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, rp.threshold, ta, d_words);
+    if (fe == cudaSuccess && nwords > 0)
+      fe = cudaMemcpyAsync(hw.data(), d_words, nwords * sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
+    if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
+    dfree(h, d_words);
+    CK(fe);
+    if (!mid) h->launches += h->counting + 1;
+    else h->counting += 1;
+    std::vector<std::vector<uint64_t>> words(L);
+    for (int l = rp.min_level; l < L; ++l) {
+      const size_t n64 = (size_t)((l + 1 < L ? ta.off[l + 1] : nwords) - ta.off[l]) / 2;
+      words[l].resize(n64);
+      const uint32_t* w = hw.data() + ta.off[l];
+      parallel_run((int)((n64 + 4095) / 4096), [&](int b) {
+        for (size_t k = (size_t)b * 4096; k < std::min(n64, (size_t)(b + 1) * 4096); ++k)
+          words[l][k] = (uint64_t)w[2 * k] | ((uint64_t)w[2 * k + 1] << 32);
+      });
+    }
+    lap(AMR_RG_FLAG);
+    // 3. cluster on the host, build the new hierarchy
+    st = cluster_patches_tagged(h->cfg, op.patches, words, rp, newp, msg);
+  } else {
+    const size_t ncell = (size_t)(op.packed_elems / nv);
+    unsigned char* d_flags = nullptr;
+    CK(dmalloc(h, reinterpret_cast<void**>(&d_flags), std::max<size_t>(ncell, 1)));
+    cudaError_t fe = h->ops->flag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U,
+                                  rp.threshold, d_flags);
+    std::vector<unsigned char> hflags(ncell);
+    if (fe == cudaSuccess)
+      fe = cudaMemcpyAsync(hflags.data(), d_flags, ncell, cudaMemcpyDeviceToHost, h->stream);
+    if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
+    dfree(h, d_flags);
+    CK(fe);
+    if (!mid) h->launches += h->counting + 1;
+    else h->counting += 1;
+    std::vector<std::vector<uint8_t>> flags(op.patches.size());
+    for (size_t i = 0; i < op.patches.size(); ++i) {
+      const HPatch& p = op.patches[i];
+      if (p.level >= L) continue;
+      const size_t n = (size_t)p.n[0] * p.n[1] * p.n[2];
+      const size_t o = (size_t)(op.packed_off[i] / nv);
+      flags[i].assign(hflags.begin() + o, hflags.begin() + o + n);
+    }
+    lap(AMR_RG_FLAG);
+    // 3. cluster on the host, build the new hierarchy
+    st = cluster_patches(h->cfg, op.patches, flags, rp, newp, msg);
+  }
   if (st != AMR_OK) return fail(h, st, msg);
   lap(AMR_RG_CLUSTER);
   Plan np;

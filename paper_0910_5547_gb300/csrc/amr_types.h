@@ -122,6 +122,20 @@ struct RegFace {
   int8_t pad;
 };
 
+// Regrid block tagging on the device: levels [l0, L) of a hierarchy with at
+// most kTagLevels levels, each with a dense bitmap of its block grid (bit i =
+// block (x, y, z), i = (z nb1 + y) nb0 + x) starting at 32-bit word off[l] of
+// one buffer (off[l] even, so the host reads 64-bit words).
+constexpr int kTagLevels = 13;
+struct TagArgs {
+  int l0, L;
+  int block, buffer;
+  int per[3];                 // periodic axes
+  int N[kTagLevels][3];       // cells per axis of each level
+  int nb[kTagLevels][3];      // blocks per axis of each level
+  long long off[kTagLevels];  // first word of each level's bitmap
+};
+
 // Box of a coarse patch covered by a finer level (excluded from totals).
 struct CoverBox {
   int16_t lo[3], n[3];

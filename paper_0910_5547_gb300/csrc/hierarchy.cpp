@@ -1260,6 +1260,14 @@ class TagGrid {
     hash_ = KeySet();
   }
   bool dense() const { return dense_; }
+  // take a dense bitmap made elsewhere (bit i = block (x, y, z) with
+  // i = (z n1 + y) n0 + x, 64 bits per word); false if the grid is not dense or
+  // the size differs
+  bool adopt(std::vector<uint64_t>& words) {
+    if (!dense_ || words.size() != bits_.size()) return false;
+    bits_.swap(words);
+    return true;
+  }
   void set(int x, int y, int z) {
     if (dense_) {
       const int64_t i = ((int64_t)z * n_[1] + y) * n_[0] + x;
@@ -1307,15 +1315,55 @@ class TagGrid {
 
 }  // namespace
 
-amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
-                           const std::vector<std::vector<uint8_t>>& flags, const RegridParams& rp,
-                           std::vector<HPatch>& out, std::string& msg) {
-  const int B = rp.block, L = cfg.max_level, l0 = rp.min_level;
+amr_status check_regrid_params(const amr_config& cfg, const RegridParams& rp, std::string& msg) {
+  const int B = rp.block;
   if (B < 2 || (B & 1) || rp.buffer < 0 || rp.buffer > B || rp.max_patch < 2 * B || rp.max_patch % (2 * B) ||
-      l0 < 0 || l0 > L) {
+      rp.min_level < 0 || rp.min_level > cfg.max_level) {
     msg = "bad regrid parameters (block even >= 2, 0 <= buffer <= block, max_patch a multiple of 2 block)";
     return AMR_ERR_ARG;
   }
+  return AMR_OK;
+}
+
+int64_t regrid_tag_blocks(const amr_config& cfg, const RegridParams& rp, int level, int nb[3]) {
+  int64_t v = 1;
+  for (int d = 0; d < 3; ++d) {
+    nb[d] = (level_n(cfg, level, d) + rp.block - 1) / rp.block;
+    v *= nb[d];
+  }
+  return v;
+}
+
+namespace {
+amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old, std::vector<TagGrid>& tags,
+                          const RegridParams& rp, std::vector<HPatch>& out, std::string& msg);
+}  // namespace
+
+amr_status cluster_patches_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
+                                  std::vector<std::vector<uint64_t>>& words, const RegridParams& rp,
+                                  std::vector<HPatch>& out, std::string& msg) {
+  amr_status st = check_regrid_params(cfg, rp, msg);
+  if (st != AMR_OK) return st;
+  const int L = cfg.max_level;
+  std::vector<TagGrid> tags(L + 1);
+  for (int l = rp.min_level; l < L; ++l) {
+    int n[3];
+    regrid_tag_blocks(cfg, rp, l, n);
+    tags[l].reset(n);
+    if (l >= (int)words.size() || !tags[l].adopt(words[l])) {
+      msg = "regrid: block tags of a level do not match its block grid";
+      return AMR_ERR_ARG;
+    }
+  }
+  return cluster_tagged(cfg, old, tags, rp, out, msg);
+}
+
+amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
+                           const std::vector<std::vector<uint8_t>>& flags, const RegridParams& rp,
+                           std::vector<HPatch>& out, std::string& msg) {
+  amr_status st = check_regrid_params(cfg, rp, msg);
+  if (st != AMR_OK) return st;
+  const int B = rp.block, L = cfg.max_level, l0 = rp.min_level;
   auto nb = [&](int l, int d) { return (level_n(cfg, l, d) + B - 1) / B; };
   auto per = [&](int d) { return periodic(cfg, d); };
   std::vector<TagGrid> tags(L + 1);   // level L (the finest allowed) is never flagged
@@ -1376,6 +1424,17 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
       const Key b = unpack(k);
       tags[old[i].level].set(b.x, b.y, b.z);
     }
+  return cluster_tagged(cfg, old, tags, rp, out, msg);
+}
+
+namespace {
+// Steps 2-3 of the clustering from the block tags of levels min_level .. L-1.
+amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old, std::vector<TagGrid>& tags,
+                          const RegridParams& rp, std::vector<HPatch>& out, std::string& msg) {
+  (void)msg;
+  const int B = rp.block, L = cfg.max_level, l0 = rp.min_level;
+  auto nb = [&](int l, int d) { return (level_n(cfg, l, d) + B - 1) / B; };
+  auto per = [&](int d) { return periodic(cfg, d); };
   // 2. a tag on level l needs its parent region (and a ring for nesting) refined on level l-1
   for (int l = L - 1; l > l0; --l) {
     TagGrid parents;   // parent blocks of the tags (8 children share one)
@@ -1524,6 +1583,7 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
   }
   return AMR_OK;
 }
+}  // namespace
 
 void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch>& newp, int keep_level,
                        RegridFill& fill) {

@@ -104,11 +104,27 @@ struct RegridParams {
   int min_level = 0;
 };
 
+amr_status check_regrid_params(const amr_config& cfg, const RegridParams& rp, std::string& msg);
+
 // flags[i]: one byte per interior cell of old patch i ([z][y][x]); empty for
 // patches whose level is not flagged.
 amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
                            const std::vector<std::vector<uint8_t>>& flags, const RegridParams& rp,
                            std::vector<HPatch>& out, std::string& msg);
+
+// Block grid of a flagged level (blocks of rp.block cells per axis): fills nb,
+// returns the block count.  A level whose count is at most kTagDenseMax can be
+// tagged as a bitmap.
+constexpr int64_t kTagDenseMax = (int64_t)1 << 28;
+int64_t regrid_tag_blocks(const amr_config& cfg, const RegridParams& rp, int level, int nb[3]);
+
+// The same clustering from block tags made elsewhere (the GPU): words[l] for
+// levels min_level .. max_level-1 is the level's bitmap, bit i = block (x, y, z)
+// with i = (z nb1 + y) nb0 + x, ceil(blocks / 64) words; the flagged cells grown
+// by rp.buffer, as cluster_patches marks them.  words are consumed.
+amr_status cluster_patches_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
+                                  std::vector<std::vector<uint64_t>>& words, const RegridParams& rp,
+                                  std::vector<HPatch>& out, std::string& msg);
 
 // Tables that fill a new hierarchy from an old one: per new level l > keep_level,
 // same-level box copies (dst = new patch, src = old patch, local coordinates)

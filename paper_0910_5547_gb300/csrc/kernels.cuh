@@ -19,7 +19,7 @@
 //   reflux_kernel    register correction of uncovered coarse cells.
 //   box_restrict_kernel / restrict_kernel
 //                    mean of the 8 children (pairwise sums).
-//   flag_kernel, xcopy_kernel
+//   flag_kernel, tag_kernel, xcopy_kernel
 //                    regrid: density-gradient flags; copies from the old
 //                    hierarchy into the new one.
 //   speed_kernel     CFL rate / max signal speed reduction (warp shuffles).
@@ -1125,8 +1125,20 @@ __global__ void pack_out_kernel(const ChunkDesc* chunks, int nchunk, const Patch
 // regridding
 // ---------------------------------------------------------------------------
 
-// One byte per interior cell: 1 where max_d |rho(i + e_d) - rho(i - e_d)| / (2 rho(i)) > threshold
-// (face ghosts must be filled).
+// Density-gradient criterion of one interior cell (face ghosts filled):
+// max_d |rho(i + e_d) - rho(i - e_d)| / (2 rho(i)) > threshold, in the bulk precision.
+template <typename T>
+__device__ __forceinline__ bool density_flag(const PatchDesc& P, const T* R, int c, T threshold) {
+  const int plane = P.pitch * P.m1;
+  const T rho = R[c];
+  const T gx = dabs(R[c + 1] - R[c - 1]);
+  const T gy = dabs(R[c + P.pitch] - R[c - P.pitch]);
+  const T gz = dabs(R[c + plane] - R[c - plane]);
+  const T g = dmax(gx, dmax(gy, gz)) / (T(2) * rho);
+  return g > threshold;
+}
+
+// One byte per interior cell: 1 where the density-gradient criterion holds.
 template <typename T, int NV>
 __global__ void flag_kernel(const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const int64_t* packed_off,
                             const T* U, T threshold, unsigned char* flags) {
@@ -1135,18 +1147,60 @@ __global__ void flag_kernel(const ChunkDesc* chunks, int nchunk, const PatchDesc
     const PatchDesc P = desc[ch.patch];
     const T* R = U + P.off;   // density is variable 0
     const int nx = P.n[0], nxy = P.n[0] * P.n[1];
-    const int plane = P.pitch * P.m1;
     unsigned char* fp = flags + packed_off[ch.patch] / NV;
     for (int e = threadIdx.x; e < ch.count; e += blockDim.x) {
       const int idx = ch.begin + e;
       const int k = idx / nxy, r2 = idx - k * nxy, j = r2 / nx, i = r2 - j * nx;
       const int c = ((k + kGhost) * P.m1 + (j + kGhost)) * P.pitch + (i + kGhost);
-      const T rho = R[c];
-      const T gx = dabs(R[c + 1] - R[c - 1]);
-      const T gy = dabs(R[c + P.pitch] - R[c - P.pitch]);
-      const T gz = dabs(R[c + plane] - R[c - plane]);
-      const T g = dmax(gx, dmax(gy, gz)) / (T(2) * rho);
-      fp[idx] = g > threshold ? 1 : 0;
+      fp[idx] = density_flag(P, R, c, threshold) ? 1 : 0;
+    }
+  }
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Regrid tagging: every flagged cell of a level in [l0, L), grown by `buffer`
+// cells (clipped at outflow faces), marks the blocks it touches in its level's
+// bitmap (periodic block coordinates wrapped), as the host clustering does from
+// the byte flags.
+template <typename T, int NV>
+__global__ void tag_kernel(const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const T* U, T threshold,
+                           TagArgs a, unsigned int* words) {
+  for (int s = blockIdx.x; s < nchunk; s += gridDim.x) {
+    const ChunkDesc ch = chunks[s];
+    const PatchDesc P = desc[ch.patch];
+    const int l = P.level;
+    if (l < a.l0 || l >= a.L) continue;
+    const T* R = U + P.off;
+    const int nx = P.n[0], nxy = P.n[0] * P.n[1];
+    unsigned int* w = words + a.off[l];
+    for (int e = threadIdx.x; e < ch.count; e += blockDim.x) {
+      const int idx = ch.begin + e;
+      const int k = idx / nxy, r2 = idx - k * nxy, j = r2 / nx, i = r2 - j * nx;
+      const int c = ((k + kGhost) * P.m1 + (j + kGhost)) * P.pitch + (i + kGhost);
+      if (!density_flag(P, R, c, threshold)) continue;
+      const int cell[3] = {P.lo[0] + i, P.lo[1] + j, P.lo[2] + k};
+      int b0[3], b1[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int lo = cell[d] - a.buffer, hi = cell[d] + a.buffer;
+        if (!a.per[d]) {
+          lo = max(lo, 0);
+          hi = min(hi, a.N[l][d] - 1);
+        }
+        b0[d] = floor_div(lo, a.block);
+        b1[d] = floor_div(hi, a.block);
+      }
+      for (int z = b0[2]; z <= b1[2]; ++z)
+        for (int y = b0[1]; y <= b1[1]; ++y)
+          for (int x = b0[0]; x <= b1[0]; ++x) {
+            int q[3] = {x, y, z};
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+              if (a.per[d]) q[d] = ((q[d] % a.nb[l][d]) + a.nb[l][d]) % a.nb[l][d];
+            const long long bi = ((long long)q[2] * a.nb[l][1] + q[1]) * a.nb[l][0] + q[0];
+            atomicOr(w + (bi >> 5), 1u << (bi & 31));
+          }
     }
   }
 }

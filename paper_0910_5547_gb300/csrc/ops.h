@@ -67,6 +67,8 @@ struct OpsBase {
                               const int64_t* packed_off, const double* src, void* U, int prim, StepParams* prm) = 0;
   virtual cudaError_t flag(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
                            const int64_t* packed_off, const void* U, double threshold, unsigned char* flags) = 0;
+  virtual cudaError_t tag(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const void* U,
+                          double threshold, const TagArgs& a, unsigned int* words) = 0;
   virtual cudaError_t xcopy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* dst_desc,
                             const PatchDesc* src_desc, void* dst, const void* src) = 0;
   virtual cudaError_t pack_out(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,

@@ -220,6 +220,13 @@ struct Ops final : OpsBase {
     return cudaGetLastError();
   }
 
+  cudaError_t tag(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc, const void* U,
+                  double threshold, const TagArgs& a, unsigned int* words) override {
+    tag_kernel<T, NV><<<grid_for(nchunk), 256, 0, s>>>(chunks, nchunk, desc, static_cast<const T*>(U), (T)threshold,
+                                                       a, words);
+    return cudaGetLastError();
+  }
+
   cudaError_t xcopy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* dst_desc,
                     const PatchDesc* src_desc, void* dst, const void* src) override {
     if (nseg <= 0) return cudaSuccess;

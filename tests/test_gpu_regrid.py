@@ -126,3 +126,28 @@ def test_regrid_schedule_rejects_bad_parameters():
     s.set_regrid_schedule(-1)
     s.step()
     s.check()
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+def test_block_tags_on_gpu_and_byte_flags_agree(bc):
+    """The regrid tags blocks on the GPU when every flagged level's block grid fits
+    a 2^28-bit map, else downloads one byte per cell and tags on the host.  With
+    max_level 12 the deep levels' grids exceed that (host path); with max_level 3
+    they do not (GPU path).  The same flags then give the same new hierarchy and
+    the same filled state, and both agree with the oracle."""
+    pb = clumpy(7, bc)
+    runs = []
+    for ml in (3, 12):
+        s = Solver.from_problem(pb, precision="fp64", max_level=ml)
+        s.step(0.002)
+        s.regrid(threshold=0.1, buffer=2, block=2, max_patch=16, min_level=0)
+        s.check()
+        runs.append(([(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches], s.all_cons()))
+    assert runs[0][0] == runs[1][0]
+    assert max(p[0] for p in runs[0][0]) == 1
+    for a, b in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(a, b)
+    o = orc.Oracle(pb, max_level=3, nthreads=8)
+    o.step(0.002)
+    o = rg.regrid(o, threshold=0.1, buffer=2, block=2, max_patch=16)
+    assert runs[0][0] == [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches]
