@@ -169,10 +169,10 @@ class ClockSampler:
         return out
 
 
-def make_solver(pb, precision, batched, graph, stream):
+def make_solver(pb, precision, batched, graph, stream, **kw):
     from paper_0910_5547_gb300 import Solver
     return Solver.from_problem(pb, precision=precision, batched=batched, use_graph=graph,
-                               stream=stream.cuda_stream)
+                               stream=stream.cuda_stream, **kw)
 
 
 def timed_steps(torch, s, stream, steps, dt=0.0):
@@ -300,7 +300,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--only", default="",
-                    help="comma list of phases: fp32,tiled,fp64,plain,e2e,amr,amr32,mhd,adaptive (default: "
+                    help="comma list of phases: fp32,tiled,fp64,fluxrec,plain,e2e,amr,amr32,mhd,adaptive (default: "
                          "all but amr32)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -326,6 +326,7 @@ def main():
 
     import amr_inputs as ai
     phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e", "amr", "mhd",
+                                                          "fluxrec",
                                                           "adaptive"}
     single = ai.kelvin_helmholtz(N=N, tile=None)          # one 256^3 patch
     tiled = ai.kelvin_helmholtz(N=N, tile=TILE) if phases & {"tiled", "plain"} else None
@@ -396,6 +397,29 @@ def main():
     if "fp64" in phases:
         extra["fp64_batched"] = {"value": rate(single, "fp64", True, True, k64), "unit": UNIT, "steps": k64,
                                  "workload": "single 256^3 patch, batched + graph"}
+    if "fluxrec" in phases:
+        # the direct flux reconstruction variant (Sec. 4's second class of schemes) on the
+        # same single 256^3 patch: rate with graph replay, stage-kernel event times
+        so = make_solver(single, "fp32", True, True, stream, riemann="fluxrec")
+        so.autotune()
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        kf = max(3, args.steps // 4)
+        tf = timed_steps(torch, so, stream, kf)
+        NV.amr_set_timing(so.h, True)
+        for _ in range(ksteps):
+            so.step(0.0, sync=False)
+        tmf = NV.amr_get_timing(so.h)
+        NV.amr_set_timing(so.h, False)
+        so.check()
+        so.close()
+        tsf = (tmf["stage1"][0] + tmf["stage2"][0]) / ksteps
+        extra["fluxrec_fp32"] = {
+            "value": ws * cells * kf / max_over_ranks(tf), "unit": UNIT, "steps": kf,
+            "stage_ms": {"stage1": round(tmf["stage1"][0] / ksteps, 4), "stage2": round(tmf["stage2"][0] / ksteps, 4)},
+            "stage_hbm_frac": stage_bytes / (tsf / 1e3) / 1e9 / peak,
+            "workload": "Kelvin-Helmholtz 256^3 single patch, FP32, riemann=fluxrec (Lax-Friedrichs split fluxes "
+                        "reconstructed by PLM), batched + graph"}
     if "plain" in phases:
         extra["fp64_plain"] = {"value": rate(tiled, "fp64", False, False, k64), "unit": UNIT, "steps": k64,
                                "workload": "512 patches of 32^3, one stage-kernel and ghost-copy launch per patch, "

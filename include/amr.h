@@ -10,7 +10,12 @@
  *   - Sec. 4, PLM reconstruction of (rho, e, vx, vy, vz) with the generalised
  *     minmod limiter (theta) and half the limited slope added at each face;
  *   - Sec. 4, the HLL interface flux (AMR_HLL: two-wave HLL with the signal
- *     speeds v_d +- c; AMR_LLF: the flux formula as printed, with lambda_0);
+ *     speeds v_d +- c; AMR_LLF: the flux formula as printed, with lambda_0),
+ *     or the direct flux reconstruction Sec. 4 names as the other class of
+ *     schemes (AMR_FLUXREC, Euler only: Lax-Friedrichs split fluxes
+ *     F+- = (F(U) +- alpha U) / 2, alpha the largest |v_d| + c of the four
+ *     stencil cells, F+ reconstructed from the left and F- from the right
+ *     with the same PLM);
  *   - Sec. 5.1, TVD-RK2 as two identical Euler stages and an average:
  *     U1 = U + dt L(U), U2 = U1 + dt L(U1), U^{n+1} = U/2 + U2/2;
  *   - Sec. 3, Berger-Colella recursion: every patch is an initial-boundary
@@ -49,14 +54,14 @@ typedef enum {
 } amr_status;
 
 enum { AMR_FP64 = 0, AMR_FP32 = 1 };                 /* bulk precision of state and arithmetic */
-enum { AMR_HLL = 0, AMR_LLF = 1 };                    /* interface flux */
+enum { AMR_HLL = 0, AMR_LLF = 1, AMR_FLUXREC = 2 };   /* interface flux */
 enum { AMR_BC_OUTFLOW = 0, AMR_BC_PERIODIC = 1 };     /* per domain face */
 enum { AMR_STATE_CONSERVED = 0, AMR_STATE_PRIMITIVE = 1 };
 
 typedef struct {
   int nvar;              /* 5 (Euler) or 9 (GLM-MHD) */
   int precision;         /* AMR_FP64 or AMR_FP32; flux registers and totals are FP64 always */
-  int riemann;           /* AMR_HLL or AMR_LLF */
+  int riemann;           /* AMR_HLL, AMR_LLF or AMR_FLUXREC (nvar 5 only) */
   double gamma;          /* adiabatic index, > 1 */
   double theta;          /* generalised minmod parameter, 0 <= theta <= 2 */
   double cfl;            /* Courant number for the CFL step (0, 1] */
@@ -209,6 +214,24 @@ amr_status amr_get_state(amr_handle* h, int patch, double* out);
 /* Copy all patches' conserved state into one packed host buffer (layout as in
  * amr_set_state).  Synchronises. */
 amr_status amr_get_state_all(amr_handle* h, double* packed);
+
+/* Stream-ordered copies that overlap the compute: the library keeps two device
+ * staging slots per direction and one copy stream per direction.
+ * amr_set_state_async: as amr_set_state, but returns at once; the host buffer
+ *   (pinned for a true asynchronous copy) must stay unchanged until a later
+ *   amr_wait_state / synchronising call has returned.  Work enqueued after it
+ *   (amr_step) sees the new state.
+ * amr_get_state_all_async: enqueues the download of the state as of this point
+ *   in stream order into the caller's host buffer and returns a ticket; the
+ *   buffer is valid once amr_wait_state(h, ticket) has returned.
+ * Up to two transfers per direction are in flight; a third waits (on the GPU)
+ * for the slot of the first.  Pinned host buffers make the copies run beside
+ * the steps; pageable ones still work, with the driver's staging. */
+amr_status amr_set_state_async(amr_handle* h, const double* packed, int state_kind);
+amr_status amr_get_state_all_async(amr_handle* h, double* packed, long long* ticket);
+/* Wait until the download of `ticket` has landed in host memory.  AMR_ERR_ARG for
+ * a ticket this handle did not issue. */
+amr_status amr_wait_state(amr_handle* h, long long ticket);
 
 /* out[nvar]: sum over leaf cells (not covered by a finer patch) of U * cell
  * volume, accumulated in FP64 in a fixed order.  Synchronises. */

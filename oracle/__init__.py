@@ -35,7 +35,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-HLL, LLF = 0, 1
+HLL, LLF, FLUXREC = 0, 1, 2
 OUTFLOW, PERIODIC = 0, 1
 
 
@@ -116,6 +116,7 @@ def lib():
             L.orc_prim_to_cons.argtypes = [cp, dp, dp]
             L.orc_cons_to_prim.argtypes = [cp, dp, dp]
             L.orc_riemann.argtypes = [cp, dp, dp, ctypes.c_int, ctypes.c_double, dp]
+            L.orc_fluxrec_face.argtypes = [cp, dp, ctypes.c_int, dp]
             _lib = L
     return _lib
 
@@ -290,6 +291,16 @@ def phys_flux(w, d, nvar=5, gamma=1.4, ch=1.0) -> np.ndarray:
     w = np.ascontiguousarray(w, dtype=np.float64)
     f = np.zeros(nvar)
     lib().orc_phys_flux(ctypes.byref(cfg), _dp(w), d, ch, _dp(f))
+    return f
+
+
+def fluxrec_face(u4, d, gamma=1.4, theta=1.5) -> np.ndarray:
+    """Direct flux reconstruction (Euler) at the face between rows 1 and 2 of
+    four conserved states u4[4][5] along axis d."""
+    cfg = make_config(nvar=5, gamma=gamma, theta=theta, riemann=FLUXREC)
+    u4 = np.ascontiguousarray(u4, dtype=np.float64)
+    f = np.zeros(5)
+    lib().orc_fluxrec_face(ctypes.byref(cfg), _dp(u4), d, _dp(f))
     return f
 
 

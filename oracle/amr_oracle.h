@@ -24,12 +24,13 @@
 extern "C" {
 #endif
 
-enum { ORC_HLL = 0, ORC_LLF = 1 };
+enum { ORC_HLL = 0, ORC_LLF = 1, ORC_FLUXREC = 2 };
 enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1 };
 
 typedef struct {
   int nvar;           /* 5 (Euler) or 9 (GLM-MHD) */
-  int riemann;        /* ORC_HLL (two-wave HLL) or ORC_LLF (the printed Sec. 4 flux) */
+  int riemann;        /* ORC_HLL (two-wave HLL), ORC_LLF (the printed Sec. 4 flux) or
+                         ORC_FLUXREC (direct flux reconstruction, Euler only) */
   int plm_literal;    /* 1: add the full limited slope at faces (printed PLM), 0: half slope */
   double gamma;
   double theta;       /* generalised-minmod parameter, 0 <= theta <= 2 */
@@ -123,6 +124,10 @@ void orc_prim_to_cons(const orc_config* cfg, const double* w, double* u);
 void orc_cons_to_prim(const orc_config* cfg, const double* u, double* w);
 /* Interface flux from primitive left/right states along dir. */
 void orc_riemann(const orc_config* cfg, const double* wl, const double* wr, int dir, double ch, double* f);
+/* Direct flux reconstruction at the face between cells 1 and 2 of four conserved
+ * states u4[4][nvar] along dir (Euler): Lax-Friedrichs split fluxes, each
+ * reconstructed by PLM from its upwind side. */
+void orc_fluxrec_face(const orc_config* cfg, const double* u4, int dir, double* f);
 
 #ifdef __cplusplus
 }

@@ -103,6 +103,14 @@ struct amr_handle {
   cudaMemPool_t pool = nullptr;   // stream-ordered device memory (no caller allocator)
   unsigned char* stage = nullptr; // pinned host staging of the table uploads
   size_t stage_cap = 0, stage_cap_seen = 0;
+  // asynchronous state copies: one copy stream per direction, two device slots
+  // per direction (packed FP64), events that order slot reuse across streams
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  double* in_slot[2] = {nullptr, nullptr};
+  double* out_slot[2] = {nullptr, nullptr};
+  int64_t slot_elems = -1;
+  cudaEvent_t ev_h2d[2] = {}, ev_in_used[2] = {}, ev_packout[2] = {}, ev_d2h[2] = {};
+  long long n_in = 0, n_out = 0;
   OpsBase* ops = nullptr;
   std::string err;
   Plan plan;
@@ -201,6 +209,64 @@ cudaError_t dmalloc(amr_handle* h, void** p, size_t bytes) {
   return cudaMallocAsync(p, bytes, h->stream);
 }
 
+void dfree(amr_handle* h, void* p);
+
+// Copy streams, events and device slots of the asynchronous state copies, sized
+// for the installed hierarchy (remade after a regrid or a new patch set, once
+// the copies in flight are done).
+cudaError_t ensure_async(amr_handle* h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->cs_in) {
+    e = cudaStreamCreateWithFlags(&h->cs_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs_out, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      cudaEvent_t* evs[4] = {&h->ev_h2d[k], &h->ev_in_used[k], &h->ev_packout[k], &h->ev_d2h[k]};
+      for (cudaEvent_t* ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (h->slot_elems == h->plan.packed_elems) return cudaSuccess;
+  e = cudaStreamSynchronize(h->cs_in);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->cs_out);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < 2; ++k) {
+    dfree(h, h->in_slot[k]);
+    dfree(h, h->out_slot[k]);
+    h->in_slot[k] = h->out_slot[k] = nullptr;
+  }
+  h->slot_elems = -1;
+  const size_t bytes = std::max<int64_t>(h->plan.packed_elems, 1) * sizeof(double);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    void* p = nullptr;
+    e = dmalloc(h, &p, bytes);
+    h->in_slot[k] = static_cast<double*>(p);
+    if (e == cudaSuccess) e = dmalloc(h, &p, bytes);
+    h->out_slot[k] = static_cast<double*>(p);
+  }
+  // the slots are allocated in the order of the handle's stream; the copy streams
+  // use them next
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) h->slot_elems = h->plan.packed_elems;
+  return e;
+}
+
+void release_async(amr_handle* h) {
+  if (h->cs_in) cudaStreamSynchronize(h->cs_in);
+  if (h->cs_out) cudaStreamSynchronize(h->cs_out);
+  for (int k = 0; k < 2; ++k) {
+    dfree(h, h->in_slot[k]);
+    dfree(h, h->out_slot[k]);
+    h->in_slot[k] = h->out_slot[k] = nullptr;
+    cudaEvent_t evs[4] = {h->ev_h2d[k], h->ev_in_used[k], h->ev_packout[k], h->ev_d2h[k]};
+    for (cudaEvent_t ev : evs)
+      if (ev) cudaEventDestroy(ev);
+  }
+  if (h->cs_in) cudaStreamDestroy(h->cs_in);
+  if (h->cs_out) cudaStreamDestroy(h->cs_out);
+  h->cs_in = h->cs_out = nullptr;
+}
+
 // The packed FP64 staging buffer of the host copies (set/get state) is made on
 // first use after each install: regrids never need it.
 cudaError_t ensure_packed(amr_handle* h) {
@@ -235,7 +301,8 @@ void free_device(amr_handle* h) {
 }
 
 OpsBase* make_ops(const amr_config& c) {
-  PhysParams p{c.gamma, c.theta, c.ch, c.riemann == AMR_LLF ? 1 : 0, c.p_floor, c.glm_alpha};
+  PhysParams p{c.gamma, c.theta, c.ch, c.riemann == AMR_LLF ? 1 : 0, c.p_floor, c.glm_alpha,
+               c.riemann == AMR_FLUXREC ? 1 : 0};
   if (c.nvar == 5) return c.precision == AMR_FP32 ? make_ops_f32_euler(p) : make_ops_f64_euler(p);
   return c.precision == AMR_FP32 ? make_ops_f32_mhd(p) : make_ops_f64_mhd(p);
 }
@@ -1231,6 +1298,53 @@ amr_status amr_get_state_all(amr_handle* h, double* packed) {
   return AMR_OK;
 }
 
+amr_status amr_set_state_async(amr_handle* h, const double* packed, int state_kind) {
+  if (!h) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  if (!packed) return fail(h, AMR_ERR_ARG, "null state buffer");
+  if (state_kind != AMR_STATE_CONSERVED && state_kind != AMR_STATE_PRIMITIVE)
+    return fail(h, AMR_ERR_ARG, "bad state_kind");
+  CK(ensure_async(h));
+  const int k = (int)(h->n_in & 1);
+  CK(cudaStreamWaitEvent(h->cs_in, h->ev_in_used[k], 0));   // the slot's previous conversion is done
+  CK(cudaMemcpyAsync(h->in_slot[k], packed, h->plan.packed_elems * sizeof(double), cudaMemcpyHostToDevice,
+                     h->cs_in));
+  CK(cudaEventRecord(h->ev_h2d[k], h->cs_in));
+  CK(cudaStreamWaitEvent(h->stream, h->ev_h2d[k], 0));
+  CK(h->ops->pack_in(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->in_slot[k], h->U,
+                     state_kind == AMR_STATE_PRIMITIVE, h->params));
+  CK(cudaEventRecord(h->ev_in_used[k], h->stream));
+  h->launches += 1;
+  h->rates_valid = false;
+  h->n_in += 1;
+  return AMR_OK;
+}
+
+amr_status amr_get_state_all_async(amr_handle* h, double* packed, long long* ticket) {
+  if (!h || !packed || !ticket) return AMR_ERR_ARG;
+  if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
+  CK(ensure_async(h));
+  const int k = (int)(h->n_out & 1);
+  CK(cudaStreamWaitEvent(h->stream, h->ev_d2h[k], 0));   // the slot's previous download is done
+  CK(h->ops->pack_out(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, h->out_slot[k]));
+  CK(cudaEventRecord(h->ev_packout[k], h->stream));
+  CK(cudaStreamWaitEvent(h->cs_out, h->ev_packout[k], 0));
+  CK(cudaMemcpyAsync(packed, h->out_slot[k], h->plan.packed_elems * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->cs_out));
+  CK(cudaEventRecord(h->ev_d2h[k], h->cs_out));
+  h->launches += 1;
+  *ticket = h->n_out++;
+  return AMR_OK;
+}
+
+amr_status amr_wait_state(amr_handle* h, long long ticket) {
+  if (!h) return AMR_ERR_ARG;
+  if (ticket < 0 || ticket >= h->n_out) return fail(h, AMR_ERR_ARG, "unknown ticket");
+  // a later download from the same slot completes after this one (one copy stream)
+  CK(cudaEventSynchronize(h->ev_d2h[ticket & 1]));
+  return AMR_OK;
+}
+
 amr_status amr_get_state(amr_handle* h, int patch, double* out) {
   if (!h || !out) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
@@ -1337,6 +1451,7 @@ const char* amr_last_error(const amr_handle* h) { return h ? h->err.c_str() : "n
 void amr_destroy(amr_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  release_async(h);
   free_device(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   dfree(h, h->params);

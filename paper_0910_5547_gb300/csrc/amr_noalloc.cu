@@ -133,6 +133,7 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   ph.ggm1 = (T)(cfg.gamma * (cfg.gamma - 1.0));
   ph.theta = (T)cfg.theta;
   ph.llf = cfg.riemann == AMR_LLF ? 1 : 0;
+  ph.fluxrec = (NV == 5 && cfg.riemann == AMR_FLUXREC) ? 1 : 0;
   ph.efl = (T)(cfg.p_floor / (cfg.gamma - 1.0));
   ph.glm_alpha = (T)cfg.glm_alpha;
   double dx[3];
@@ -169,11 +170,13 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   copy_kernel<T, NV, false><<<gseg, 256, 0, s>>>(ghost, nseg, desc, U, U, nullptr, T(0));
   a.Uin = U;
   a.Uout = U1;
-  stage_kernel<T, NV, 1><<<a.nitems, kStageThreads, sm, s>>>(a);
+  if (ph.fluxrec) fluxrec_stage_kernel<T, 1><<<a.nitems, kStageThreads, 0, s>>>(a);
+  else stage_kernel<T, NV, 1><<<a.nitems, kStageThreads, sm, s>>>(a);
   copy_kernel<T, NV, false><<<gseg, 256, 0, s>>>(ghost, nseg, desc, U1, U1, nullptr, T(0));
   a.Uin = U1;
   a.Uout = U;
-  stage_kernel<T, NV, 2><<<a.nitems, kStageThreads, sm, s>>>(a);
+  if (ph.fluxrec) fluxrec_stage_kernel<T, 2><<<a.nitems, kStageThreads, 0, s>>>(a);
+  else stage_kernel<T, NV, 2><<<a.nitems, kStageThreads, sm, s>>>(a);
   pack_out_kernel<T, NV><<<grid_chunks, 256, 0, s>>>(dchunks, nchunk, desc, poff, U, out);
   if (cudaGetLastError() != cudaSuccess) return AMR_ERR_CUDA;
   if (dt_used) {

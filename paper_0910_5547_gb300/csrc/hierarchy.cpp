@@ -344,7 +344,11 @@ void split_restrict(std::vector<RestrictSeg>& v) {
 amr_status validate_config(const amr_config& c, std::string& msg) {
   if (c.nvar != 5 && c.nvar != 9) { msg = "nvar must be 5 (Euler) or 9 (GLM-MHD)"; return AMR_ERR_ARG; }
   if (c.precision != AMR_FP64 && c.precision != AMR_FP32) { msg = "precision must be AMR_FP64 or AMR_FP32"; return AMR_ERR_ARG; }
-  if (c.riemann != AMR_HLL && c.riemann != AMR_LLF) { msg = "riemann must be AMR_HLL or AMR_LLF"; return AMR_ERR_ARG; }
+  if (c.riemann != AMR_HLL && c.riemann != AMR_LLF && c.riemann != AMR_FLUXREC) {
+    msg = "riemann must be AMR_HLL, AMR_LLF or AMR_FLUXREC";
+    return AMR_ERR_ARG;
+  }
+  if (c.riemann == AMR_FLUXREC && c.nvar != 5) { msg = "AMR_FLUXREC is for the Euler system (nvar 5)"; return AMR_ERR_ARG; }
   if (!(c.gamma > 1.0) || !std::isfinite(c.gamma)) { msg = "gamma must be > 1"; return AMR_ERR_ARG; }
   if (!(c.theta >= 0.0 && c.theta <= 2.0)) { msg = "theta must lie in [0, 2]"; return AMR_ERR_ARG; }
   if (!(c.cfl > 0.0 && c.cfl <= 1.0)) { msg = "cfl must lie in (0, 1]"; return AMR_ERR_ARG; }

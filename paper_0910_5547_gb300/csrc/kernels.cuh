@@ -23,6 +23,7 @@
 //                    regrid: density-gradient flags; copies from the old
 //                    hierarchy into the new one.
 //   speed_kernel     CFL rate / max signal speed reduction (warp shuffles).
+//   fluxrec_stage_kernel  the RK2 stage with direct flux reconstruction (Euler).
 //   totals_kernel    FP64 conserved totals over leaf cells (fixed order).
 //   divb_kernel      GLM-MHD: FP64 norms of the centred div B over leaf cells.
 //   pack kernels     FP64 host layout <-> ghosted device arena.
@@ -516,6 +517,86 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
     }
     if ((t & 31) == 0) {
+      atomic_max_pos_double(&a.params->next_rate_bits, r);
+      atomic_max_pos_double(&a.params->next_speed_bits, sp);
+    }
+  }
+}
+
+// RK2 stage with direct flux reconstruction (Euler, the AMR_FLUXREC variant)
+// over the same work items: each thread owns one column of the item and marches
+// in z; the x and y face fluxes of its cell are formed from the four-cell
+// conserved stencils (L1-cached global loads), the z flux of the face below is
+// carried from the previous plane.  No shared memory and no barriers.
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(kStageThreads) fluxrec_stage_kernel(StageArgs<T> a) {
+  const Phys<T> ph = phys_with_ch<T, 5>(a.ph, a.params);
+  const T dt = (T)(a.params->dt0 * a.dt_scale);
+  const T dtx = dt * a.idx, dty = dt * a.idy, dtz = dt * a.idz;
+  bool ok = true;
+  int floor_hits = 0;
+  T rate_max = T(0), speed_max = T(0);
+  auto face = [&](const T* in, int64_t vs, int64_t c1, int64_t step, int d, T* F) {
+    T u[4][5];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[q][v] = in[v * vs + c1 + (q - 2) * step];
+    if (d == 0) fluxrec_face<T, 0>(u, ph, F, ok, nullptr);
+    else if (d == 1) fluxrec_face<T, 1>(u, ph, F, ok, nullptr);
+    else fluxrec_face<T, 2>(u, ph, F, ok, nullptr);
+  };
+  for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    const StageItem w = a.items[it];
+    const PatchDesc P = a.desc[w.patch];
+    const int ncol = w.wx * w.wy;
+    if ((int)threadIdx.x >= ncol) continue;
+    const int i = w.x0 + (int)threadIdx.x % w.wx, j = w.y0 + (int)threadIdx.x / w.wx;
+    const T* in = a.Uin + P.off;
+    T* out = a.Uout + P.off;
+    const int64_t vs = P.vstride, sy = P.pitch, sz = (int64_t)P.pitch * P.m1;
+    T Fzm[5], Fzp[5], Fx0[5], Fx1[5], Fy0[5], Fy1[5];
+    face(in, vs, cell_index(P, i, j, w.z0), sz, 2, Fzm);
+    for (int k = w.z0; k < w.z0 + w.wz; ++k) {
+      const int64_t c = cell_index(P, i, j, k);
+      face(in, vs, c, 1, 0, Fx0);
+      face(in, vs, c + 1, 1, 0, Fx1);
+      face(in, vs, c, sy, 1, Fy0);
+      face(in, vs, c + sy, sy, 1, Fy1);
+      face(in, vs, c + sz, sz, 2, Fzp);
+      T uin[5], un[5], wc[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) uin[v] = in[v * vs + c];
+      ok &= cons_to_prim<T, 5>(uin, wc, ph.efl, &floor_hits);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        // u + dt L(u), L = -sum_d (F_{d,+} - F_{d,-}) / dx_d
+        const T u2 = uin[v] - dtx * (Fx1[v] - Fx0[v]) - dty * (Fy1[v] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
+        if (STAGE == 1) {
+          out[v * vs + c] = u2;
+        } else {
+          un[v] = T(0.5) * out[v * vs + c] + T(0.5) * u2;
+          out[v * vs + c] = un[v];
+        }
+        Fzm[v] = Fzp[v];
+      }
+      if (STAGE == 2 && a.fuse_rate) {
+        T r, sp;
+        cell_rate<T, 5>(un, ph, (T)a.idx0, (T)a.idy0, (T)a.idz0, r, sp);
+        rate_max = dmax(rate_max, r);
+        speed_max = dmax(speed_max, sp);
+      }
+    }
+  }
+  if (!ok) atomicOr(&a.params->bad, 1u);
+  if (floor_hits) atomicAdd(&a.params->floor_hits, (unsigned long long)floor_hits);
+  if (STAGE == 2 && a.fuse_rate) {
+    double r = (double)rate_max, sp = (double)speed_max;
+    for (int o = 16; o > 0; o >>= 1) {
+      r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+      sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
       atomic_max_pos_double(&a.params->next_rate_bits, r);
       atomic_max_pos_double(&a.params->next_speed_bits, sp);
     }

@@ -16,6 +16,7 @@ struct PhysParams {  // host copy of the physics constants
   double gamma, theta, ch_fixed;
   int llf;
   double p_floor, glm_alpha;
+  int fluxrec;
 };
 
 struct OpsBase {

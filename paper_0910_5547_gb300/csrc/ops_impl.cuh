@@ -25,6 +25,7 @@ struct Ops final : OpsBase {
     ph.ggm1 = (T)(p.gamma * (p.gamma - 1.0));
     ph.theta = (T)p.theta;
     ph.llf = p.llf;
+    ph.fluxrec = NV == 5 ? p.fluxrec : 0;
     ph.ch = ph.ch2 = ph.half_inv_ch = T(0);
     ph.efl = (T)(p.p_floor / (p.gamma - 1.0));
     ph.glm_alpha = (T)p.glm_alpha;
@@ -72,6 +73,13 @@ struct Ops final : OpsBase {
     a.fuse_rate = fuse_rate;
     a.ph = ph;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
+    if constexpr (NV == 5) {
+      if (ph.fluxrec) {
+        if (stage == 1) fluxrec_stage_kernel<T, 1><<<g, kStageThreads, 0, s>>>(a);
+        else fluxrec_stage_kernel<T, 2><<<g, kStageThreads, 0, s>>>(a);
+        return cudaGetLastError();
+      }
+    }
     if (nt == 128) {
       const size_t sm = stage_smem_bytes<T, NV, 2 * kDef>();
       if (stage == 1) stage_kernel<T, NV, 1, 2 * kDef, 128><<<g, 128, sm, s>>>(a);

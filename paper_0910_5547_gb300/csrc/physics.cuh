@@ -20,6 +20,7 @@ struct Phys {
   T ch2;       // ch^2
   T half_inv_ch;  // 1 / (2 ch)
   int llf;     // 1: the printed Sec. 4 flux with lambda_0; 0: two-wave HLL
+  int fluxrec; // 1: direct flux reconstruction (Euler; replaces the Riemann solve)
   T efl;       // p_floor / (gamma - 1): the specific internal energy floor is efl / rho
   T glm_alpha; // GLM damping parameter (0 = off)
 };
@@ -229,12 +230,58 @@ __device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
   }
 }
 
+// Direct flux reconstruction (Euler) at the face between cells 1 and 2 of the
+// conserved stencil u[0..3] along D: Lax-Friedrichs splitting
+// F+- = (F(U) +- alpha U) / 2 with alpha = max over the four cells of |v_D| + c,
+// F+ reconstructed from the left, F- from the right, each with the Sec. 4
+// half-slope PLM; F = F+ + F-.
+template <typename T, int D>
+__device__ __forceinline__ void fluxrec_face(const T (&u)[4][5], const Phys<T>& ph, T* F, bool& ok, int* hits) {
+  T f[4][5];
+  T alpha = T(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    T w[5];
+    ok &= cons_to_prim<T, 5>(u[q], w, ph.efl, hits);
+    const T p = ph.gm1 * (w[0] * w[4]);
+    const T vd = w[1 + D];
+    alpha = dmax(alpha, dabs(vd) + dsqrt(ph.ggm1 * w[4]));
+    f[q][0] = u[q][1 + D];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[q][1 + k] = u[q][1 + k] * vd + (k == D ? p : T(0));
+    f[q][4] = (u[q][4] + p) * vd;
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    T fp[4], fm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      fp[q] = T(0.5) * (f[q][v] + alpha * u[q][v]);
+      fm[q] = T(0.5) * (f[q][v] - alpha * u[q][v]);
+    }
+    F[v] = (fp[1] + half_slope(fp[0], fp[1], fp[2], ph.theta)) +
+           (fm[2] - half_slope(fm[1], fm[2], fm[3], ph.theta));
+  }
+}
+
 // Interface flux along D at the face between cells (c1 - e_D) and c1 of an
 // array holding conserved variables, stencil c1-2 .. c1+1 (used by the flux
 // register kernels: same arithmetic as the stage kernel's faces).
 template <typename T, int NV, int D>
 __device__ __forceinline__ void face_flux_from_array(const T* base, int64_t vstride, int64_t c1, int64_t step,
                                                      const Phys<T>& ph, T* F) {
+  if constexpr (NV == 5) {
+    if (ph.fluxrec) {
+      T u[4][5];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[q][v] = base[v * vstride + c1 + (q - 2) * step];
+      bool ok = true;
+      fluxrec_face<T, D>(u, ph, F, ok, nullptr);
+      return;
+    }
+  }
   T w[4][NV];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {

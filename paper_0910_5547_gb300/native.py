@@ -23,7 +23,7 @@ AMR_ERR_NONPHYSICAL = -4
 AMR_ERR_TIMEOUT = -5
 AMR_ERR_STATE = -6
 AMR_FP64, AMR_FP32 = 0, 1
-AMR_HLL, AMR_LLF = 0, 1
+AMR_HLL, AMR_LLF, AMR_FLUXREC = 0, 1, 2
 AMR_BC_OUTFLOW, AMR_BC_PERIODIC = 0, 1
 AMR_STATE_CONSERVED, AMR_STATE_PRIMITIVE = 0, 1
 
@@ -36,7 +36,8 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
            "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count",
-           "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms"]
+           "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms", "amr_set_state_async",
+           "amr_get_state_all_async", "amr_wait_state"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -148,6 +149,12 @@ def load():
     L.amr_floor_count.restype = ctypes.c_int
     L.amr_divb_norms.argtypes = [H, dp]
     L.amr_divb_norms.restype = ctypes.c_int
+    L.amr_set_state_async.argtypes = [H, dp, ctypes.c_int]
+    L.amr_set_state_async.restype = ctypes.c_int
+    L.amr_get_state_all_async.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.amr_get_state_all_async.restype = ctypes.c_int
+    L.amr_wait_state.argtypes = [H, ctypes.c_longlong]
+    L.amr_wait_state.restype = ctypes.c_int
     L.amr_get_patches.restype = ctypes.c_int
     L.amr_set_timing.argtypes = [H, ctypes.c_int]
     L.amr_get_timing.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -270,6 +277,25 @@ def amr_conserved_totals(h, nvar: int) -> np.ndarray:
     out = np.zeros(nvar, dtype=np.float64)
     _check(h, load().amr_conserved_totals(h, _dp(out)))
     return out
+
+
+def amr_set_state_async(h, packed: np.ndarray, kind: int = AMR_STATE_CONSERVED) -> None:
+    """Enqueue the upload of a packed FP64 state; keep `packed` unchanged until a
+    later amr_wait_state has returned."""
+    assert packed.dtype == np.float64 and packed.flags.c_contiguous
+    _check(h, load().amr_set_state_async(h, _dp(packed), kind))
+
+
+def amr_get_state_all_async(h, out: np.ndarray) -> int:
+    """Enqueue the download of the state into `out`; returns the ticket to wait for."""
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    t = ctypes.c_longlong(-1)
+    _check(h, load().amr_get_state_all_async(h, _dp(out), ctypes.byref(t)))
+    return t.value
+
+
+def amr_wait_state(h, ticket: int) -> None:
+    _check(h, load().amr_wait_state(h, ticket))
 
 
 def amr_divb_norms(h) -> np.ndarray:

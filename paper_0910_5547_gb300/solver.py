@@ -30,7 +30,8 @@ class Solver:
             max_level = max(p.level for p in self.patches)
         self.cfg = N.amr_default_config(
             nvar=nvar, precision=N.AMR_FP32 if precision == "fp32" else N.AMR_FP64,
-            riemann=N.AMR_LLF if riemann == "llf" else N.AMR_HLL, gamma=gamma, theta=theta, cfl=cfl,
+            riemann={"hll": N.AMR_HLL, "llf": N.AMR_LLF, "fluxrec": N.AMR_FLUXREC}[riemann], gamma=gamma,
+            theta=theta, cfl=cfl,
             base_n=base_n, bc=bc, max_level=max_level, ch=ch, p_floor=p_floor, glm_alpha=glm_alpha,
             batched=int(batched), use_graph=int(use_graph),
             domain_lo=domain_lo, domain_hi=domain_hi, cuda_stream=stream)

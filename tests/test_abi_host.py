@@ -93,6 +93,14 @@ def test_bad_config_is_rejected(field, value):
     assert st == N.AMR_ERR_ARG, msg
 
 
+def test_flux_reconstruction_is_euler_only():
+    one = [P(0, (0, 0, 0), (32, 32, 32))]
+    assert N.amr_validate_patches(cfg(riemann=N.AMR_FLUXREC), one)[0] == N.AMR_OK
+    st, msg = N.amr_validate_patches(cfg(riemann=N.AMR_FLUXREC, nvar=9), one)
+    assert st == N.AMR_ERR_ARG and "FLUXREC" in msg
+    assert N.amr_validate_patches(cfg(riemann=3), one)[0] == N.AMR_ERR_ARG
+
+
 def test_unpaired_periodic_faces_rejected():
     st, msg = N.amr_validate_patches(cfg(bc=(1, 0, 0, 0, 0, 0)), [P(0, (0, 0, 0), (32, 32, 32))])
     assert st == N.AMR_ERR_ARG and "periodic" in msg
