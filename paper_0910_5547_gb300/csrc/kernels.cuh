@@ -559,12 +559,16 @@ __global__ void __launch_bounds__(kStageThreads) fluxrec_stage_kernel(StageArgs<
     face(in, vs, cell_index(P, i, j, w.z0), sz, 2, Fzm);
     for (int k = w.z0; k < w.z0 + w.wz; ++k) {
       const int64_t c = cell_index(P, i, j, k);
+      T uin[5], un[5], wc[5];
+      if (STAGE == 2) {   // U^n, loaded ahead of the face work that hides its latency
+#pragma unroll
+        for (int v = 0; v < 5; ++v) un[v] = out[v * vs + c];
+      }
       face(in, vs, c, 1, 0, Fx0);
       face(in, vs, c + 1, 1, 0, Fx1);
       face(in, vs, c, sy, 1, Fy0);
       face(in, vs, c + sy, sy, 1, Fy1);
       face(in, vs, c + sz, sz, 2, Fzp);
-      T uin[5], un[5], wc[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) uin[v] = in[v * vs + c];
       ok &= cons_to_prim<T, 5>(uin, wc, ph.efl, &floor_hits);
@@ -575,7 +579,7 @@ __global__ void __launch_bounds__(kStageThreads) fluxrec_stage_kernel(StageArgs<
         if (STAGE == 1) {
           out[v * vs + c] = u2;
         } else {
-          un[v] = T(0.5) * out[v * vs + c] + T(0.5) * u2;
+          un[v] = T(0.5) * un[v] + T(0.5) * u2;
           out[v * vs + c] = un[v];
         }
         Fzm[v] = Fzp[v];
