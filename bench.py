@@ -367,6 +367,8 @@ def main():
     launches = s.launches() - n0
     s.check()
     tot1 = s.totals()
+    # median of single-step device times (graph replay, CUDA events per step), beside the mean
+    per_step = [timed_steps(torch, s, stream, 1) * 1e3 for _ in range(max(5, min(args.steps, 30)))]
     # periodic box: mass, momentum and energy are conserved; drift of the FP32 state
     # over the timed steps, measured by the FP64 totals (momentum against its norm)
     scale = [abs(tot0[0]), max(abs(tot0[1]), abs(tot0[2]), abs(tot0[3]), abs(tot0[0])), 0, 0, abs(tot0[4])]
@@ -609,7 +611,11 @@ def main():
                      "note": "achieved = algorithmic bytes of the stage-1 and stage-2 launches over their summed "
                              "CUDA-event durations; traffic = mean DRAM bytes per launch from the committed ncu "
                              "capture (null if the kernel source changed since)",
-                     "timed_steps": ksteps},
+                     "timed_steps": ksteps,
+                     "frac_of_nominal_7900": achieved / 7900.0,
+                     "traffic_bytes_per_cell_update": (None if stage_traffic() is None
+                                                       else 2 * stage_traffic() / cells)},
+        "step_ms_median": statistics.median(per_step),
         "step_kernel_ms": step_kernel_ms,
         "autotune": [l for l in tune_report.splitlines() if l],
         "cell_update_roofline_frac": value / ws * (2 + 3) * V * W / (peak * 1e9),
