@@ -391,6 +391,45 @@ def main():
     step_kernel_ms = {k: round(v[0] / ksteps, 4) for k, v in tm.items() if v[1]}
     s.close()
 
+    e2e = None
+    if "e2e" in phases:
+        # end to end through the C ABI: every step uploads its input state (FP64, pinned)
+        # and downloads its result; the uploads and downloads run on the library's copy
+        # streams beside the steps (two steps in flight).  Measured before the other
+        # workloads build and free tens of GB of host arrays: pinned buffers allocated
+        # after that moved data markedly slower on the same box.
+        s = make_solver(single, "fp32", True, True, stream)
+        nstate = NV.amr_state_size(s.h)
+        h_in = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        h_out = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        h_in[0][:] = s.state_all()
+        h_in[1][:] = h_in[0]
+        ke = max(3, min(args.steps, 20))
+
+        def e2e_steps(n):
+            tickets = []
+            for k in range(n):
+                if k >= 2:
+                    NV.amr_wait_state(s.h, tickets[k - 2])   # buffers k % 2 are free again
+                NV.amr_set_state_async(s.h, h_in[k % 2], NV.AMR_STATE_CONSERVED)
+                s.step(0.0, sync=False)
+                tickets.append(NV.amr_get_state_all_async(s.h, h_out[k % 2]))
+            for t in tickets[-2:]:
+                NV.amr_wait_state(s.h, t)
+
+        e2e_steps(3)
+        barrier()
+        t = time.perf_counter()
+        e2e_steps(ke)
+        e2e_t = max_over_ranks(time.perf_counter() - t)
+        s.check()
+        s.close()
+        e2e = {"value": ws * cells * ke / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nstate * 8,
+               "d2h_bytes_per_step": nstate * 8, "steps": ke,
+               "note": "per step: packed FP64 conserved state host->device (pinned), one RK2 step (CFL), "
+                       "state device->host, through amr_set_state_async / amr_step / amr_get_state_all_async; "
+                       "copies of neighbouring steps overlap on the library's copy streams"}
+
     extra = {}
     k64 = max(3, args.steps // 10)
     if "tiled" in phases:
@@ -552,43 +591,6 @@ def main():
                                       "GLM-MHD Orszag-Tang, 3 levels, base 96^3", fp64_plain_steps=0)
         mhd["unit"] = UNIT
         extra["mhd_orszag_tang"] = mhd
-
-    e2e = None
-    if "e2e" in phases:
-        # end to end through the C ABI: every step uploads its input state (FP64, pinned)
-        # and downloads its result; the uploads and downloads run on the library's copy
-        # streams beside the steps (two steps in flight)
-        s = make_solver(single, "fp32", True, True, stream)
-        nstate = NV.amr_state_size(s.h)
-        h_in = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-        h_out = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-        h_in[0][:] = s.state_all()
-        h_in[1][:] = h_in[0]
-        ke = max(3, min(args.steps, 20))
-
-        def e2e_steps(n):
-            tickets = []
-            for k in range(n):
-                if k >= 2:
-                    NV.amr_wait_state(s.h, tickets[k - 2])   # buffers k % 2 are free again
-                NV.amr_set_state_async(s.h, h_in[k % 2], NV.AMR_STATE_CONSERVED)
-                s.step(0.0, sync=False)
-                tickets.append(NV.amr_get_state_all_async(s.h, h_out[k % 2]))
-            for t in tickets[-2:]:
-                NV.amr_wait_state(s.h, t)
-
-        e2e_steps(3)
-        barrier()
-        t = time.perf_counter()
-        e2e_steps(ke)
-        e2e_t = max_over_ranks(time.perf_counter() - t)
-        s.check()
-        s.close()
-        e2e = {"value": ws * cells * ke / e2e_t, "unit": UNIT, "h2d_bytes_per_step": nstate * 8,
-               "d2h_bytes_per_step": nstate * 8, "steps": ke,
-               "note": "per step: packed FP64 conserved state host->device (pinned), one RK2 step (CFL), "
-                       "state device->host, through amr_set_state_async / amr_step / amr_get_state_all_async; "
-                       "copies of neighbouring steps overlap on the library's copy streams"}
 
     if rank != 0:
         return
