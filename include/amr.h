@@ -116,6 +116,14 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out);
 amr_status amr_validate_patches(const amr_config* cfg, int npatch, const amr_patch* patches,
                                 char* msg, int msg_len);
 
+/* Owner rank of every patch for a run over nranks GPUs (the partition a
+ * multi-GPU run would use; a run here has one GPU): each level's patches, in
+ * Morton order of their centres on the finest level's cells, are cut into
+ * contiguous ranges of nearly equal cell counts, one per rank.  owner: npatch
+ * caller-owned ints.  Host only.  AMR_ERR_ARG on bad arguments. */
+amr_status amr_partition_patches(const amr_config* cfg, int npatch, const amr_patch* patches, int nranks,
+                                 int* owner);
+
 /* Install a patch set (validated as above) and its initial state.  state is a
  * HOST array of npatch pointers; state[i] holds patch i's interior cells, FP64,
  * layout [nvar][n2][n1][n0] (x fastest); state_kind selects conserved U or

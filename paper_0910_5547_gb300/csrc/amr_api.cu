@@ -1014,6 +1014,23 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
   return AMR_OK;
 }
 
+amr_status amr_partition_patches(const amr_config* cfg, int npatch, const amr_patch* patches, int nranks,
+                                 int* owner) {
+  if (!cfg || npatch <= 0 || !patches || nranks < 1 || !owner) return AMR_ERR_ARG;
+  std::vector<HPatch> P(npatch);
+  for (int i = 0; i < npatch; ++i) {
+    P[i].level = patches[i].level;
+    for (int d = 0; d < 3; ++d) {
+      P[i].lo[d] = patches[i].lo[d];
+      P[i].n[d] = patches[i].n[d];
+      if (P[i].lo[d] < 0 || P[i].n[d] < 1 || P[i].level < 0 || P[i].level > 12) return AMR_ERR_ARG;
+    }
+  }
+  const std::vector<int> o = morton_partition(*cfg, P, nranks);
+  std::memcpy(owner, o.data(), npatch * sizeof(int));
+  return AMR_OK;
+}
+
 amr_status amr_validate_patches(const amr_config* cfg, int npatch, const amr_patch* patches, char* msg,
                                 int msg_len) {
   std::string m;

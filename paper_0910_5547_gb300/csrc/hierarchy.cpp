@@ -638,6 +638,58 @@ void flatten_restrict(const Plan& plan, const std::vector<RestrictSeg>& segs, Fl
 
 void parallel_run(int n, const std::function<void(int)>& f) { parallel_for(n, f); }
 
+namespace {
+// Bits of x spread to every third position (x < 2^21).
+uint64_t spread3(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | (x << 32)) & 0x1f00000000ffffULL;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+  x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+  x = (x | (x << 2)) & 0x1249249249249249ULL;
+  return x;
+}
+}  // namespace
+
+std::vector<int> morton_partition(const amr_config& cfg, const std::vector<HPatch>& P, int nranks) {
+  const int np = (int)P.size();
+  std::vector<int> owner(np, 0);
+  if (nranks <= 1 || np == 0) return owner;
+  int L = 0;
+  for (const HPatch& p : P) L = std::max(L, p.level);
+  // coarsen the curve so the finest level's coordinates fit 21 bits per axis
+  int sh = 0;
+  for (int d = 0; d < 3; ++d)
+    while (((int64_t)std::max(cfg.base_n[d], 1) << L) >> sh >= ((int64_t)1 << 21)) ++sh;
+  for (int l = 0; l <= L; ++l) {
+    // the level's patches in Morton order of their centres (finest-level cells,
+    // so that the orders of different levels follow the same curve)
+    std::vector<std::pair<uint64_t, int>> ord;
+    int64_t total = 0;
+    for (int i = 0; i < np; ++i) {
+      if (P[i].level != l) continue;
+      uint64_t c[3];
+      for (int d = 0; d < 3; ++d)
+        c[d] = (uint64_t)((((int64_t)2 * P[i].lo[d] + P[i].n[d]) << (L - l)) >> (1 + sh));
+      const uint64_t key = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+      ord.push_back({key, i});
+      total += (int64_t)P[i].n[0] * P[i].n[1] * P[i].n[2];
+    }
+    std::sort(ord.begin(), ord.end());
+    // contiguous ranges: rank r takes the patches whose cell-count prefix midpoint
+    // falls in [r, r+1) * total / nranks
+    int64_t run = 0;
+    for (const auto& e : ord) {
+      const HPatch& p = P[e.second];
+      const int64_t w = (int64_t)p.n[0] * p.n[1] * p.n[2];
+      const int64_t mid2 = 2 * run + w;   // twice the midpoint
+      owner[e.second] = (int)std::min<int64_t>(nranks - 1, mid2 * nranks / (2 * std::max<int64_t>(total, 1)));
+      run += w;
+    }
+  }
+  return owner;
+}
+
 void build_flat(Plan& plan) {
   for (LevelPlan& L : plan.levels) {
     flatten_copies(plan, L.ghost, false, L.fghost);

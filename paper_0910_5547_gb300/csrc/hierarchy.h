@@ -149,6 +149,11 @@ void build_items(Plan& plan, const TileParams& tp);
 amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan,
                       std::string& msg, const TileParams& tp = TileParams());
 
+// Owner rank of every patch for a run over nranks GPUs: each level's patches in
+// Morton order of their centres (on the finest level's cells), cut into
+// contiguous ranges of nearly equal cell counts.  nranks <= 1: all 0.
+std::vector<int> morton_partition(const amr_config& cfg, const std::vector<HPatch>& P, int nranks);
+
 // f(0) .. f(n-1) on the host cores (the planner's thread pool policy).
 void parallel_run(int n, const std::function<void(int)>& f);
 

@@ -37,7 +37,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
            "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count",
            "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms", "amr_set_state_async",
-           "amr_get_state_all_async", "amr_wait_state"]
+           "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -217,6 +217,21 @@ def amr_create(cfg: amr_config) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     _check(None, load().amr_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
+
+
+def amr_partition_patches(cfg: amr_config, patches: Sequence, nranks: int) -> np.ndarray:
+    """Owner rank per patch (Morton ranges of equal cell counts per level); host only."""
+    arr = make_patches(patches)
+    out = np.zeros(len(patches), dtype=np.int32)
+    L = load()
+    L.amr_partition_patches.argtypes = [ctypes.POINTER(amr_config), ctypes.c_int, ctypes.POINTER(amr_patch),
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.amr_partition_patches.restype = ctypes.c_int
+    st = L.amr_partition_patches(ctypes.byref(cfg), len(patches), arr, nranks,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if st != AMR_OK:
+        raise AmrError(st, "amr_partition_patches")
+    return out
 
 
 def amr_validate_patches(cfg: amr_config, patches: Sequence):
