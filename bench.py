@@ -524,6 +524,7 @@ def main():
         t_sched = timed_steps(torch, so, stream, 4)
         cu_sched = NV.amr_cell_updates(so.h) - c0
         ph_sched = NV.amr_get_regrid_timing(so.h)
+        counts_sched = NV.amr_get_regrid_counts(so.h)
         sched_shape = [len(so.patches), 1 + max(p.level for p in so.patches)]
         so.check()
         so.close()
@@ -549,6 +550,7 @@ def main():
             "value": ws * cu_sched / max_over_ranks(max(t_sched - rg_s, 1e-9)), "unit": UNIT,
             "coarse_steps": 4, "cell_updates": cu_sched, "regrid_s": rg_s,
             "regrid_phases_s": {k: round(v, 4) for k, v in ph_sched.items()},
+            "regrids_new_vs_unchanged": list(counts_sched),
             "patches_levels_at_end": sched_shape,
             "regrid_between_coarse_steps": {
                 "value": ws * tot_cu / max_over_ranks(t_steps),

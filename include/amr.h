@@ -171,6 +171,11 @@ enum {
 /* sec[0 .. n-1] receives the phases (n <= AMR_RG_NPHASE) summed over the regrids
  * (explicit or scheduled) since the last call, then resets them.  No GPU work. */
 amr_status amr_get_regrid_timing(amr_handle* h, double* sec, int n);
+/* counts[0]: regrids (explicit or scheduled) that installed a new hierarchy;
+ * counts[1]: regrids whose clustering reproduced the installed hierarchy (the
+ * state is then left as it is: the refill would copy every cell onto itself).
+ * Totals since amr_create.  No GPU work. */
+amr_status amr_get_regrid_counts(amr_handle* h, long long* counts);
 
 /* Regrid schedule (Sec. 3: the hierarchy below a level is rebuilt after each of
  * its steps): from the next amr_step on, after every completed step of a level

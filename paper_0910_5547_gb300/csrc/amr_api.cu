@@ -91,6 +91,7 @@ struct DevLevel {
 struct amr_handle {
   amr_config cfg{};
   double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the regrids since the last query
+  long long regrid_counts[2] = {0, 0};     // regrids that rebuilt the hierarchy / found it unchanged
   // regrid schedule: after each step of a level l <= sched_level, rebuild the finer levels
   long long cell_updates = 0;   // interior cells advanced by amr_step, summed over level steps
   bool capturing = false;       // advance() is being captured into a graph (not executed)
@@ -842,6 +843,18 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   }
   if (st != AMR_OK) return fail(h, st, msg);
   lap(AMR_RG_CLUSTER);
+  // the same hierarchy again: the refill would copy every cell onto itself
+  bool same = newp.size() == op.patches.size();
+  for (size_t i = 0; same && i < newp.size(); ++i) {
+    const HPatch &a = newp[i], &b = op.patches[i];
+    same = a.level == b.level && a.lo[0] == b.lo[0] && a.lo[1] == b.lo[1] && a.lo[2] == b.lo[2] &&
+           a.n[0] == b.n[0] && a.n[1] == b.n[1] && a.n[2] == b.n[2];
+  }
+  if (same) {
+    h->regrid_counts[1] += 1;
+    return AMR_OK;
+  }
+  h->regrid_counts[0] += 1;
   Plan np;
   st = build_plan(h->cfg, newp, np, msg, h->tp);
   if (st != AMR_OK) return fail(h, st, "regrid produced an invalid hierarchy: " + msg);
@@ -1404,6 +1417,13 @@ amr_status amr_divb_norms(amr_handle* h, double* out) {
   h->launches += h->counting + 2;
   CK(cudaMemcpyAsync(out, h->totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+amr_status amr_get_regrid_counts(amr_handle* h, long long* counts) {
+  if (!h || !counts) return AMR_ERR_ARG;
+  counts[0] = h->regrid_counts[0];
+  counts[1] = h->regrid_counts[1];
   return AMR_OK;
 }
 

@@ -37,7 +37,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
            "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count",
            "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms", "amr_set_state_async",
-           "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches"]
+           "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches", "amr_get_regrid_counts"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -292,6 +292,16 @@ def amr_conserved_totals(h, nvar: int) -> np.ndarray:
     out = np.zeros(nvar, dtype=np.float64)
     _check(h, load().amr_conserved_totals(h, _dp(out)))
     return out
+
+
+def amr_get_regrid_counts(h) -> tuple:
+    """(regrids that installed a new hierarchy, regrids that found it unchanged)."""
+    c = (ctypes.c_longlong * 2)()
+    L = load()
+    L.amr_get_regrid_counts.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]
+    L.amr_get_regrid_counts.restype = ctypes.c_int
+    _check(h, L.amr_get_regrid_counts(h, c))
+    return int(c[0]), int(c[1])
 
 
 def amr_set_state_async(h, packed: np.ndarray, kind: int = AMR_STATE_CONSERVED) -> None:
