@@ -550,7 +550,7 @@ def main():
             "value": ws * cu_sched / max_over_ranks(max(t_sched - rg_s, 1e-9)), "unit": UNIT,
             "coarse_steps": 4, "cell_updates": cu_sched, "regrid_s": rg_s,
             "regrid_phases_s": {k: round(v, 4) for k, v in ph_sched.items()},
-            "regrids_new_vs_unchanged": list(counts_sched),
+            "regrids_new_unchanged_memo": list(counts_sched),
             "patches_levels_at_end": sched_shape,
             "regrid_between_coarse_steps": {
                 "value": ws * tot_cu / max_over_ranks(t_steps),

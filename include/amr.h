@@ -173,8 +173,10 @@ enum {
 amr_status amr_get_regrid_timing(amr_handle* h, double* sec, int n);
 /* counts[0]: regrids (explicit or scheduled) that installed a new hierarchy;
  * counts[1]: regrids whose clustering reproduced the installed hierarchy (the
- * state is then left as it is: the refill would copy every cell onto itself).
- * Totals since amr_create.  No GPU work. */
+ * state is then left as it is: the refill would copy every cell onto itself);
+ * counts[2]: regrids whose block tags, kept levels and parameters equalled those
+ * of the previous clustering at the same min_level, which was then reused.
+ * Totals since amr_create; counts holds 3 values.  No GPU work. */
 amr_status amr_get_regrid_counts(amr_handle* h, long long* counts);
 
 /* Regrid schedule (Sec. 3: the hierarchy below a level is rebuilt after each of

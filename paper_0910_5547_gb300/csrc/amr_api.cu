@@ -92,6 +92,16 @@ struct amr_handle {
   amr_config cfg{};
   double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the regrids since the last query
   long long regrid_counts[2] = {0, 0};     // regrids that rebuilt the hierarchy / found it unchanged
+  // last clustering per min_level: its inputs (kept levels, parameters, block tags)
+  // and its result; the clustering is a function of these alone
+  struct ClusterMemo {
+    bool valid = false;
+    RegridParams rp;
+    std::vector<HPatch> kept, result;
+    std::vector<std::vector<uint64_t>> words;
+  };
+  ClusterMemo memo[kTagLevels];
+  long long memo_hits = 0;
   // regrid schedule: after each step of a level l <= sched_level, rebuild the finer levels
   long long cell_updates = 0;   // interior cells advanced by amr_step, summed over level steps
   bool capturing = false;       // advance() is being captured into a graph (not executed)
@@ -813,8 +823,35 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
       });
     }
     lap(AMR_RG_FLAG);
-    // 3. cluster on the host, build the new hierarchy
-    st = cluster_patches_tagged(h->cfg, op.patches, words, rp, newp, msg);
+    // 3. cluster on the host, build the new hierarchy (or reuse the last clustering
+    //    of this min_level when all of its inputs are the same)
+    std::vector<HPatch> kept;
+    for (const HPatch& p : op.patches)
+      if (p.level <= rp.min_level) kept.push_back(p);
+    auto same_patches = [](const std::vector<HPatch>& a, const std::vector<HPatch>& b) {
+      if (a.size() != b.size()) return false;
+      for (size_t i = 0; i < a.size(); ++i)
+        if (std::memcmp(&a[i], &b[i], sizeof(HPatch)) != 0) return false;
+      return true;
+    };
+    auto& M = h->memo[rp.min_level];
+    const bool hit = M.valid && M.rp.threshold == rp.threshold && M.rp.buffer == rp.buffer &&
+                     M.rp.block == rp.block && M.rp.max_patch == rp.max_patch && same_patches(M.kept, kept) &&
+                     M.words == words;
+    if (hit) {
+      newp = M.result;
+      h->memo_hits += 1;
+    } else {
+      M.valid = false;
+      M.words = words;   // cluster_patches_tagged consumes its copy
+      st = cluster_patches_tagged(h->cfg, op.patches, words, rp, newp, msg);
+      if (st == AMR_OK) {
+        M.rp = rp;
+        M.kept = kept;
+        M.result = newp;
+        M.valid = true;
+      }
+    }
   } else {
     const size_t ncell = (size_t)(op.packed_elems / nv);
     unsigned char* d_flags = nullptr;
@@ -1424,6 +1461,7 @@ amr_status amr_get_regrid_counts(amr_handle* h, long long* counts) {
   if (!h || !counts) return AMR_ERR_ARG;
   counts[0] = h->regrid_counts[0];
   counts[1] = h->regrid_counts[1];
+  counts[2] = h->memo_hits;
   return AMR_OK;
 }
 

@@ -295,13 +295,14 @@ def amr_conserved_totals(h, nvar: int) -> np.ndarray:
 
 
 def amr_get_regrid_counts(h) -> tuple:
-    """(regrids that installed a new hierarchy, regrids that found it unchanged)."""
-    c = (ctypes.c_longlong * 2)()
+    """(regrids that installed a new hierarchy, regrids that found it unchanged,
+    regrids that reused the previous clustering of their min_level)."""
+    c = (ctypes.c_longlong * 3)()
     L = load()
     L.amr_get_regrid_counts.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]
     L.amr_get_regrid_counts.restype = ctypes.c_int
     _check(h, L.amr_get_regrid_counts(h, c))
-    return int(c[0]), int(c[1])
+    return int(c[0]), int(c[1]), int(c[2])
 
 
 def amr_set_state_async(h, packed: np.ndarray, kind: int = AMR_STATE_CONSERVED) -> None:
