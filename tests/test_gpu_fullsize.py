@@ -177,3 +177,35 @@ def test_sedov_4level_one_coarse_step_sampled_cells(precision):
         got = cons[i][:, g[2] - p.lo[2], g[1] - p.lo[1], g[0] - p.lo[0]]
         err = np.abs(got - want) / np.maximum(np.abs(want), np.array([1.0, 1e-3, 1e-3, 1e-3, 1e-3]))
         assert err.max() <= tol, (g, got, want)
+
+
+# ---------------------------------------------------------------------------
+# Adaptive blast in clumps (base 64^3 + 5 levels): one coarse step with the
+# workload's regrid cadence (15 rebuilds inside the step)
+# ---------------------------------------------------------------------------
+
+def test_adaptive_full_size_one_coarse_step_invariants():
+    """The gas at the outflow walls is at rest at the ambient pressure for the
+    first coarse step, so mass and energy are conserved and the momentum fluxes
+    of opposite walls cancel; every rebuilt hierarchy stays properly nested and
+    every state physical."""
+    from paper_0910_5547_gb300 import native as N
+    pb = ai.blast_clumps()
+    rkw = dict(threshold=0.3, buffer=4, block=4, max_patch=32)
+    s = Solver.from_problem(pb, precision="fp32")
+    s.step(0.0)
+    s.regrid(**rkw)
+    t0 = s.totals()
+    c0 = N.amr_get_regrid_counts(s.h)
+    s.set_regrid_schedule(pb.max_level - 2, **rkw)
+    s.step(0.0)
+    s.check()
+    t1 = s.totals()
+    c1 = N.amr_get_regrid_counts(s.h)
+    assert (c1[0] + c1[1]) - (c0[0] + c0[1]) == 1 + 2 + 4 + 8     # after each step of levels 0..3
+    assert abs(t1[0] - t0[0]) <= 2e-6 * t0[0] and abs(t1[4] - t0[4]) <= 2e-6 * t0[4], (t0, t1)
+    pscale = np.sqrt(2.0 * t0[0] * t0[4])
+    assert np.all(np.abs(t1[1:4] - t0[1:4]) <= 2e-6 * pscale), (t0, t1)
+    cfg = N.amr_default_config(base_n=pb.base_n, max_level=pb.max_level, bc=pb.bc)
+    assert N.amr_validate_patches(cfg, s.patches)[0] == N.AMR_OK
+    assert max(p.level for p in s.patches) == pb.max_level
