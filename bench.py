@@ -247,6 +247,24 @@ def cpu_baseline(steps=2, stream=None):
     out["single_thread"] = {"value": 128 ** 3 / dt1, "unit": UNIT, "cores": 1,
                             "sample": f"1 RK2 step of a 128^3 periodic sub-box, 64 patches of 32^3; {dt1:.1f} s wall"}
     out["cpu_model"] = cpu_model()
+    # the other workloads, one (coarse) step each, all cores
+    per = {}
+    for name, mk, dt, what in (
+            ("sedov_4level", ai.sedov_amr, 2.0e-7, "one coarse step (15 level steps) of the static 4-level "
+                                                   "Sedov hierarchy, dt 2e-7"),
+            ("adaptive_initial", ai.blast_clumps, 0.0, "one coarse step of the adaptive workload's initial "
+                                                      "6-level hierarchy (no regrid), CFL dt"),
+            ("orszag_tang_192", lambda: ai.orszag_tang(N=192, tile=32), 0.0, "one RK2 step of GLM-MHD "
+                                                                              "Orszag-Tang 192^3, CFL dt")):
+        pbx = mk()
+        ox = orc.Oracle(pbx, nthreads=cores)
+        t = time.perf_counter()
+        ox.step(dt)
+        dtx = time.perf_counter() - t
+        per[name] = {"value": pbx.cell_updates_per_coarse_step() / dtx, "unit": UNIT,
+                     "sample": f"{what}; {dtx:.1f} s wall"}
+        del ox, pbx
+    out["per_config"] = per
     for prec in ("fp32", "fp64"):
         s = make_solver(pb, prec, True, True, stream)
         for d in dts:
