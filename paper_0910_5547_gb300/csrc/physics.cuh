@@ -169,8 +169,44 @@ __device__ __forceinline__ void state_flux(const T* w, const Phys<T>& ph, T* U, 
 // b = S_L / (S_R - S_L), alpha = a (v_l - S_L), beta = b (S_R - v_r).  Since
 // U = rho (1, v, v^2/2 + e), alpha U_l + beta U_r is formed from alpha rho_l and
 // beta rho_r and the primitive states without the conserved vectors.
+// FP32: the left and right halves of the solve as packed pairs (one
+// instruction for two FMUL / FADD / FFMA lanes on sm_100 and later).
+template <int D>
+__device__ __forceinline__ void hll_euler_f32x2(const float* wl, const float* wr, const Phys<float>& ph, float* F) {
+  const float2 rho = make_float2(wl[0], wr[0]);
+  const float2 e = make_float2(wl[4], wr[4]);
+  const float2 v = make_float2(wl[1 + D], wr[1 + D]);
+  const float2 c2 = __fmul2_rn(make_float2(ph.ggm1, ph.ggm1), e);
+  const float2 c = make_float2(dsqrt(c2.x), dsqrt(c2.y));
+  const float2 lo = __fadd2_rn(v, make_float2(-c.x, -c.y));   // v - c
+  const float2 hi = __fadd2_rn(v, c);                            // v + c
+  const float SL = min3(0.0f, lo.x, lo.y);
+  const float SR = max3(0.0f, hi.x, hi.y);
+  const float inv = drcp(SR - SL);
+  const float2 ab = __fmul2_rn(make_float2(SR, SL), make_float2(inv, inv));            // (a, b)
+  const float2 d = __fadd2_rn(make_float2(v.x, SR), make_float2(-SL, -v.y));           // (v_l - S_L, S_R - v_r)
+  const float2 abr = __fmul2_rn(__fmul2_rn(ab, d), rho);                                // (alpha rho_l, beta rho_r)
+  float2 s2 = __fmul2_rn(make_float2(wl[1], wr[1]), make_float2(wl[1], wr[1]));
+  s2 = __ffma2_rn(make_float2(wl[2], wr[2]), make_float2(wl[2], wr[2]), s2);
+  s2 = __ffma2_rn(make_float2(wl[3], wr[3]), make_float2(wl[3], wr[3]), s2);
+  const float2 h = __ffma2_rn(make_float2(0.5f, 0.5f), s2, e);                        // v^2/2 + e
+  const float2 ar2 = make_float2(abr.x, abr.x), br2 = make_float2(abr.y, abr.y);
+  const float2 f12 = __ffma2_rn(br2, make_float2(wr[1], wr[2]), __fmul2_rn(ar2, make_float2(wl[1], wl[2])));
+  const float2 f34 = __ffma2_rn(br2, make_float2(wr[3], h.y), __fmul2_rn(ar2, make_float2(wl[3], h.x)));
+  F[0] = abr.x + abr.y;
+  F[1] = f12.x; F[2] = f12.y; F[3] = f34.x; F[4] = f34.y;
+  // a p_l and b p_r, p = (gamma - 1) rho e
+  const float2 q = __fmul2_rn(ab, __fmul2_rn(make_float2(ph.gm1, ph.gm1), __fmul2_rn(rho, e)));
+  F[1 + D] += q.x - q.y;
+  F[4] += q.x * v.x - q.y * v.y;
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void hll_euler(const T* wl, const T* wr, const Phys<T>& ph, T* F) {
+  if constexpr (sizeof(T) == 4) {
+    hll_euler_f32x2<D>(wl, wr, ph, F);
+    return;
+  }
   const T rl = wl[0], rr = wr[0], el = wl[4], er = wr[4];
   const T vl = wl[1 + D], vr = wr[1 + D];
   const T cl = dsqrt(ph.ggm1 * el), cr = dsqrt(ph.ggm1 * er);
