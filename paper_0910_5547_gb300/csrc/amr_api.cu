@@ -92,7 +92,8 @@ struct amr_handle {
   amr_config cfg{};
   double regrid_sec[AMR_RG_NPHASE] = {};   // host phases of the regrids since the last query
   long long regrid_counts[2] = {0, 0};     // regrids that rebuilt the hierarchy / found it unchanged
-  // last clustering per min_level: its inputs (kept levels, parameters, block tags)
+  // last clustering per min_level: its inputs (kept levels, parameters, refinable
+  // block bitmaps)
   // and its result; the clustering is a function of these alone
   struct ClusterMemo {
     bool valid = false;
@@ -219,6 +220,97 @@ cudaError_t dmalloc(amr_handle* h, void** p, size_t bytes) {
   if (h->pool) return cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
   return cudaMallocAsync(p, bytes, h->stream);
 }
+
+// ---- block bitmaps of the regrid on the GPU: bit i = block (x, y, z) with
+// i = (z n1 + y) n0 + x, 32 bits per word from word `off` of a buffer; every
+// kernel writes whole words (one thread per word), so no stale bit survives ----
+struct BGrid {
+  int n0, n1, n2;
+  long long off;     // first word
+  long long nw;      // words (two per 64 bits of the grid, the host's layout)
+};
+
+__device__ __forceinline__ bool bit_at(const unsigned* w, const BGrid& g, int x, int y, int z) {
+  const long long i = ((long long)z * g.n1 + y) * g.n0 + x;
+  return (w[g.off + (i >> 5)] >> (i & 31)) & 1u;
+}
+
+// parent block q of level l-1 is set when one of its 8 children is tagged on level l
+__global__ void bm_downsample(const unsigned* fine, BGrid F, unsigned* out, BGrid G) {
+  const long long total = (long long)G.n0 * G.n1 * G.n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < G.nw; t += (long long)gridDim.x * blockDim.x) {
+    unsigned word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const long long i = t * 32 + b;
+      if (i >= total) break;
+      const int x = (int)(i % G.n0), y = (int)((i / G.n0) % G.n1), z = (int)(i / ((long long)G.n0 * G.n1));
+      bool v = false;
+      for (int dz = 0; dz < 2 && !v; ++dz)
+        for (int dy = 0; dy < 2 && !v; ++dy)
+          for (int dx = 0; dx < 2 && !v; ++dx) {
+            const int cx = 2 * x + dx, cy = 2 * y + dy, cz = 2 * z + dz;
+            if (cx < F.n0 && cy < F.n1 && cz < F.n2) v = bit_at(fine, F, cx, cy, cz);
+          }
+      word |= (unsigned)v << b;
+    }
+    out[G.off + t] = word;
+  }
+}
+
+// one axis of a 3-cell box filter: OR (dilate) or AND (erode) of the cell and its
+// two neighbours along `axis`; a periodic axis wraps, otherwise a neighbour
+// outside the grid is 0 for OR and 1 for AND (outside an outflow face counts as
+// covered)
+__global__ void bm_box_axis(const unsigned* src, BGrid S, unsigned* dst, BGrid D, int axis, int periodic,
+                            int erode) {
+  const long long total = (long long)S.n0 * S.n1 * S.n2;
+  const int n[3] = {S.n0, S.n1, S.n2};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < D.nw; t += (long long)gridDim.x * blockDim.x) {
+    unsigned word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const long long i = t * 32 + b;
+      if (i >= total) break;
+      const int c[3] = {(int)(i % S.n0), (int)((i / S.n0) % S.n1), (int)(i / ((long long)S.n0 * S.n1))};
+      bool v = erode != 0;
+      for (int s = -1; s <= 1; ++s) {
+        int r[3] = {c[0], c[1], c[2]};
+        r[axis] += s;
+        if (r[axis] < 0 || r[axis] >= n[axis]) {
+          if (!periodic) continue;
+          r[axis] = ((r[axis] % n[axis]) + n[axis]) % n[axis];
+        }
+        const bool q = bit_at(src, S, r[0], r[1], r[2]);
+        v = erode ? (v && q) : (v || q);
+      }
+      word |= (unsigned)v << b;
+    }
+    dst[D.off + t] = word;
+  }
+}
+
+// cover of level l: block q is covered when its parent block (q / 2) is refinable
+__global__ void bm_from_parent(const unsigned* parent, BGrid P, unsigned* out, BGrid G) {
+  const long long total = (long long)G.n0 * G.n1 * G.n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < G.nw; t += (long long)gridDim.x * blockDim.x) {
+    unsigned word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const long long i = t * 32 + b;
+      if (i >= total) break;
+      const int x = (int)(i % G.n0), y = (int)((i / G.n0) % G.n1), z = (int)(i / ((long long)G.n0 * G.n1));
+      word |= (unsigned)bit_at(parent, P, x >> 1, y >> 1, z >> 1) << b;
+    }
+    out[G.off + t] = word;
+  }
+}
+
+// dst = a | b (op 0) or a & b (op 1), word by word
+__global__ void bm_combine(unsigned* dst, long long dst_off, const unsigned* a, long long a_off, const unsigned* b,
+                           long long b_off, long long nw, int op) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nw; t += (long long)gridDim.x * blockDim.x)
+    dst[dst_off + t] = op ? (a[a_off + t] & b[b_off + t]) : (a[a_off + t] | b[b_off + t]);
+}
+
+int bm_grid(long long nw) { return (int)std::min<long long>(std::max<long long>((nw + 255) / 256, 1), 65535); }
 
 void dfree(amr_handle* h, void* p);
 
@@ -799,19 +891,75 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   std::vector<HPatch> newp;
   amr_status st = AMR_OK;
   if (dev_tags) {
-    unsigned int* d_words = nullptr;
-    CK(dmalloc(h, reinterpret_cast<void**>(&d_words), std::max<long long>(nwords, 2) * sizeof(unsigned int)));
+    // block tags, then (all on the GPU) the parent rings of finer tags, finest
+    // level first, and the refinable blocks of every level, coarsest first: tagged
+    // and with all 26 neighbours covered (the first level by its own patches, a
+    // finer one by the refinable blocks of its parent level); only those bitmaps
+    // come back, and the host keeps the greedy box merge
+    auto grid = [&](int l, long long off) {
+      const long long nbt = (long long)ta.nb[l][0] * ta.nb[l][1] * ta.nb[l][2];
+      return BGrid{ta.nb[l][0], ta.nb[l][1], ta.nb[l][2], off, 2 * ((nbt + 63) / 64)};
+    };
+    long long maxnw = 2;
+    for (int l = rp.min_level; l < L; ++l) maxnw = std::max(maxnw, grid(l, 0).nw);
+    unsigned int *d_words = nullptr, *d_ref = nullptr, *d_tmp = nullptr;
+    const size_t wbytes = std::max<long long>(nwords, 2) * sizeof(unsigned int);
+    cudaError_t fe = dmalloc(h, reinterpret_cast<void**>(&d_words), wbytes);
+    if (fe == cudaSuccess) fe = dmalloc(h, reinterpret_cast<void**>(&d_ref), wbytes);
+    if (fe == cudaSuccess) fe = dmalloc(h, reinterpret_cast<void**>(&d_tmp), 2 * maxnw * sizeof(unsigned int));
     std::vector<uint32_t> hw((size_t)nwords);
-    cudaError_t fe = cudaMemsetAsync(d_words, 0, std::max<long long>(nwords, 2) * sizeof(unsigned int), h->stream);
-    if (fe == cudaSuccess && nwords > 0)
+    int nlaunch = 0;
+    if (fe == cudaSuccess) fe = cudaMemsetAsync(d_words, 0, wbytes, h->stream);
+    if (fe == cudaSuccess && nwords > 0) {
       fe = h->ops->tag(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, rp.threshold, ta, d_words);
-    if (fe == cudaSuccess && nwords > 0)
-      fe = cudaMemcpyAsync(hw.data(), d_words, nwords * sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
-    if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
+      ++nlaunch;
+    }
+    unsigned int *tA = d_tmp, *tB = d_tmp + maxnw;
+    auto box3 = [&](BGrid g, int erode) {   // tA -> (x) tB -> (y) tA -> (z) tB
+      const BGrid a{g.n0, g.n1, g.n2, 0, g.nw};
+      bm_box_axis<<<bm_grid(g.nw), 256, 0, h->stream>>>(tA, a, tB, a, 0, ta.per[0], erode);
+      bm_box_axis<<<bm_grid(g.nw), 256, 0, h->stream>>>(tB, a, tA, a, 1, ta.per[1], erode);
+      bm_box_axis<<<bm_grid(g.nw), 256, 0, h->stream>>>(tA, a, tB, a, 2, ta.per[2], erode);
+      nlaunch += 3;
+    };
+    for (int l = L - 1; l > rp.min_level && fe == cudaSuccess && nwords > 0; --l) {
+      const BGrid f = grid(l, ta.off[l]), g = grid(l - 1, ta.off[l - 1]);
+      bm_downsample<<<bm_grid(g.nw), 256, 0, h->stream>>>(d_words, f, tA, BGrid{g.n0, g.n1, g.n2, 0, g.nw});
+      box3(g, 0);
+      bm_combine<<<bm_grid(g.nw), 256, 0, h->stream>>>(d_words, g.off, d_words, g.off, tB, 0, g.nw, 0);
+      nlaunch += 2;
+      fe = cudaGetLastError();
+    }
+    if (fe == cudaSuccess && nwords > 0) {
+      const std::vector<uint64_t> base = regrid_base_cover(h->cfg, op.patches, rp);
+      std::vector<uint32_t> b32(2 * base.size());
+      for (size_t k = 0; k < base.size(); ++k) {
+        b32[2 * k] = (uint32_t)(base[k] & 0xffffffffu);
+        b32[2 * k + 1] = (uint32_t)(base[k] >> 32);
+      }
+      fe = cudaMemcpyAsync(tA, b32.data(), b32.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
+      for (int l = rp.min_level; l < L && fe == cudaSuccess; ++l) {
+        const BGrid g = grid(l, ta.off[l]);
+        if (l > rp.min_level)
+          bm_from_parent<<<bm_grid(g.nw), 256, 0, h->stream>>>(d_ref, grid(l - 1, ta.off[l - 1]), tA,
+                                                                BGrid{g.n0, g.n1, g.n2, 0, g.nw});
+        box3(g, 1);
+        bm_combine<<<bm_grid(g.nw), 256, 0, h->stream>>>(d_ref, g.off, d_words, g.off, tB, 0, g.nw, 1);
+        nlaunch += 1 + (l > rp.min_level ? 1 : 0);
+        fe = cudaGetLastError();
+      }
+      if (fe == cudaSuccess)
+        fe = cudaMemcpyAsync(hw.data(), d_ref, nwords * sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
+      if (fe == cudaSuccess) fe = cudaStreamSynchronize(h->stream);
+    } else if (fe == cudaSuccess) {
+      fe = cudaStreamSynchronize(h->stream);
+    }
     dfree(h, d_words);
+    dfree(h, d_ref);
+    dfree(h, d_tmp);
     CK(fe);
-    if (!mid) h->launches += h->counting + 1;
-    else h->counting += 1;
+    if (!mid) h->launches += h->counting + nlaunch;
+    else h->counting += nlaunch;
     std::vector<std::vector<uint64_t>> words(L);
     for (int l = rp.min_level; l < L; ++l) {
       const size_t n64 = (size_t)((l + 1 < L ? ta.off[l + 1] : nwords) - ta.off[l]) / 2;
@@ -823,8 +971,8 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
       });
     }
     lap(AMR_RG_FLAG);
-    // 3. cluster on the host, build the new hierarchy (or reuse the last clustering
-    //    of this min_level when all of its inputs are the same)
+    // 3. merge the refinable blocks into patches on the host (or reuse the last
+    //    clustering of this min_level when all of its inputs are the same)
     std::vector<HPatch> kept;
     for (const HPatch& p : op.patches)
       if (p.level <= rp.min_level) kept.push_back(p);
@@ -843,8 +991,8 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
       h->memo_hits += 1;
     } else {
       M.valid = false;
-      M.words = words;   // cluster_patches_tagged consumes its copy
-      st = cluster_patches_tagged(h->cfg, op.patches, words, rp, newp, msg);
+      M.words = words;   // cluster_patches_refinable consumes its copy
+      st = cluster_patches_refinable(h->cfg, op.patches, words, rp, newp, msg);
       if (st == AMR_OK) {
         M.rp = rp;
         M.kept = kept;

@@ -1484,6 +1484,53 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
 }
 
 namespace {
+// Greedy box merge of the refinable blocks `order` of level l (in (z, y, x)
+// order, bounding box [rlo, rhi)): from each block not yet taken, extend along
+// x, then y, then z while every block is refinable and free, up to max_patch
+// fine cells; each box becomes a patch of level l+1.  `refine` receives the
+// refinable set.
+void merge_boxes(const amr_config& cfg, const RegridParams& rp, int l, const std::vector<Key>& order,
+                 const int rlo[3], const int rhi[3], std::vector<HPatch>& out, BlockSet& refine) {
+  const int B = rp.block;
+  const int maxb = rp.max_patch / (2 * B);
+  BlockSet done;
+  refine.reset(rlo, rhi);
+  done.reset(rlo, rhi);
+  for (const Key& b : order) refine.insert(b.x, b.y, b.z);
+  // greedy box merge in (z, y, x) order (the order of the tags): extend along x,
+  // then y, then z
+  for (const Key& b : order) {
+    if (done.count(b.x, b.y, b.z)) continue;
+    auto free_ = [&](int x, int y, int z) { return refine.count(x, y, z) && !done.count(x, y, z); };
+    int nx = 1, ny = 1, nz = 1;
+    while (nx < maxb && free_(b.x + nx, b.y, b.z)) ++nx;
+    auto row_ok = [&](int y, int z) {
+      for (int i = 0; i < nx; ++i)
+        if (!free_(b.x + i, y, z)) return false;
+      return true;
+    };
+    while (ny < maxb && row_ok(b.y + ny, b.z)) ++ny;
+    auto slab_ok = [&](int z) {
+      for (int j = 0; j < ny; ++j)
+        if (!row_ok(b.y + j, z)) return false;
+      return true;
+    };
+    while (nz < maxb && slab_ok(b.z + nz)) ++nz;
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) done.insert(b.x + x, b.y + y, b.z + z);
+    HPatch f{};
+    f.level = l + 1;
+    const int bl[3] = {b.x, b.y, b.z}, bn[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+      const int Nf = level_n(cfg, l + 1, d);
+      f.lo[d] = 2 * B * bl[d];
+      f.n[d] = std::min(2 * B * bn[d], Nf - f.lo[d]);
+    }
+    out.push_back(f);
+  }
+}
+
 // Steps 2-3 of the clustering from the block tags of levels min_level .. L-1.
 amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old, std::vector<TagGrid>& tags,
                           const RegridParams& rp, std::vector<HPatch>& out, std::string& msg) {
@@ -1556,7 +1603,6 @@ amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
           for (int x = a0[0]; x < a1[0]; ++x) cover.insert(x, y, z);
     }
   }
-  const int maxb = rp.max_patch / (2 * B);
   // blocks of level l covered by its patches: `cover` for l0, afterwards the
   // refined blocks of level l-1 seen through the parent coordinates
   BlockSet prev_refine;
@@ -1596,42 +1642,8 @@ amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
         for (int d = 0; d < 3; ++d) { rlo[d] = std::min(rlo[d], c[d]); rhi[d] = std::max(rhi[d], c[d] + 1); }
       }
     if (order.empty()) break;
-    BlockSet refine, done;
-    refine.reset(rlo, rhi);
-    done.reset(rlo, rhi);
-    for (const Key& b : order) refine.insert(b.x, b.y, b.z);
-    // greedy box merge in (z, y, x) order (the order of the tags): extend along x,
-    // then y, then z
-    for (const Key& b : order) {
-      if (done.count(b.x, b.y, b.z)) continue;
-      auto free_ = [&](int x, int y, int z) { return refine.count(x, y, z) && !done.count(x, y, z); };
-      int nx = 1, ny = 1, nz = 1;
-      while (nx < maxb && free_(b.x + nx, b.y, b.z)) ++nx;
-      auto row_ok = [&](int y, int z) {
-        for (int i = 0; i < nx; ++i)
-          if (!free_(b.x + i, y, z)) return false;
-        return true;
-      };
-      while (ny < maxb && row_ok(b.y + ny, b.z)) ++ny;
-      auto slab_ok = [&](int z) {
-        for (int j = 0; j < ny; ++j)
-          if (!row_ok(b.y + j, z)) return false;
-        return true;
-      };
-      while (nz < maxb && slab_ok(b.z + nz)) ++nz;
-      for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-          for (int x = 0; x < nx; ++x) done.insert(b.x + x, b.y + y, b.z + z);
-      HPatch f{};
-      f.level = l + 1;
-      const int bl[3] = {b.x, b.y, b.z}, bn[3] = {nx, ny, nz};
-      for (int d = 0; d < 3; ++d) {
-        const int Nf = level_n(cfg, l + 1, d);
-        f.lo[d] = 2 * B * bl[d];
-        f.n[d] = std::min(2 * B * bn[d], Nf - f.lo[d]);
-      }
-      out.push_back(f);
-    }
+    BlockSet refine;
+    merge_boxes(cfg, rp, l, order, rlo, rhi, out, refine);
     // every refinable block is now in a new patch: a block of level l+1 lies in
     // the new patches exactly when its parent block (coordinates halved) is one
     std::swap(prev_refine, refine);
@@ -1640,6 +1652,61 @@ amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
   return AMR_OK;
 }
 }  // namespace
+
+std::vector<uint64_t> regrid_base_cover(const amr_config& cfg, const std::vector<HPatch>& old,
+                                        const RegridParams& rp) {
+  const int B = rp.block, l0 = rp.min_level;
+  int nb[3];
+  const int64_t nbt = regrid_tag_blocks(cfg, rp, l0, nb);
+  std::vector<uint64_t> w((size_t)((nbt + 63) / 64), 0);
+  for (const HPatch& p : old) {
+    if (p.level != l0) continue;
+    int a0[3], a1[3];
+    for (int d = 0; d < 3; ++d) {   // the blocks fully inside p (as the clustering's cover)
+      a0[d] = (p.lo[d] + B - 1) / B;
+      a1[d] = (p.lo[d] + p.n[d]) / B;
+      if (p.lo[d] + p.n[d] == level_n(cfg, l0, d) && level_n(cfg, l0, d) % B) a1[d] += 1;
+    }
+    for (int z = a0[2]; z < a1[2]; ++z)
+      for (int y = a0[1]; y < a1[1]; ++y)
+        for (int x = a0[0]; x < a1[0]; ++x) {
+          const int64_t i = ((int64_t)z * nb[1] + y) * nb[0] + x;
+          w[(size_t)(i >> 6)] |= (uint64_t)1 << (i & 63);
+        }
+  }
+  return w;
+}
+
+amr_status cluster_patches_refinable(const amr_config& cfg, const std::vector<HPatch>& old,
+                                     std::vector<std::vector<uint64_t>>& refinable, const RegridParams& rp,
+                                     std::vector<HPatch>& out, std::string& msg) {
+  amr_status st = check_regrid_params(cfg, rp, msg);
+  if (st != AMR_OK) return st;
+  const int L = cfg.max_level, l0 = rp.min_level;
+  out.clear();
+  for (const HPatch& p : old)
+    if (p.level <= l0) out.push_back(p);
+  for (int l = l0; l < L; ++l) {
+    int n[3];
+    regrid_tag_blocks(cfg, rp, l, n);
+    TagGrid R;
+    R.reset(n);
+    if (l >= (int)refinable.size() || !R.adopt(refinable[l])) {
+      msg = "regrid: refinable blocks of a level do not match its block grid";
+      return AMR_ERR_ARG;
+    }
+    const std::vector<Key> order = R.keys();   // (z, y, x) order
+    if (order.empty()) break;
+    int rlo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, rhi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (const Key& b : order) {
+      const int c[3] = {b.x, b.y, b.z};
+      for (int d = 0; d < 3; ++d) { rlo[d] = std::min(rlo[d], c[d]); rhi[d] = std::max(rhi[d], c[d] + 1); }
+    }
+    BlockSet refine;
+    merge_boxes(cfg, rp, l, order, rlo, rhi, out, refine);
+  }
+  return AMR_OK;
+}
 
 void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch>& newp, int keep_level,
                        RegridFill& fill) {

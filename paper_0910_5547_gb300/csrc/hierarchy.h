@@ -126,6 +126,22 @@ amr_status cluster_patches_tagged(const amr_config& cfg, const std::vector<HPatc
                                   std::vector<std::vector<uint64_t>>& words, const RegridParams& rp,
                                   std::vector<HPatch>& out, std::string& msg);
 
+// Blocks of level min_level fully inside one of its patches (a partial block at
+// the domain's end counts when the patch reaches the end): the cover of the
+// clustering's first level, as a dense bitmap laid out as the block tags.
+std::vector<uint64_t> regrid_base_cover(const amr_config& cfg, const std::vector<HPatch>& old,
+                                        const RegridParams& rp);
+
+// The clustering's last step (the greedy box merge) from the refinable blocks of
+// levels min_level .. max_level-1 made elsewhere (the GPU), dense bitmaps laid
+// out as the block tags: a block is refinable when it is tagged (after the
+// parent rings of finer tags) and all 26 neighbours inside the domain are
+// covered (level min_level: regrid_base_cover; finer levels: the parent block is
+// refinable).  Gives the same patches as cluster_patches.  refinable is consumed.
+amr_status cluster_patches_refinable(const amr_config& cfg, const std::vector<HPatch>& old,
+                                     std::vector<std::vector<uint64_t>>& refinable, const RegridParams& rp,
+                                     std::vector<HPatch>& out, std::string& msg);
+
 // Tables that fill a new hierarchy from an old one: per new level l > keep_level,
 // same-level box copies (dst = new patch, src = old patch, local coordinates)
 // and the interior boxes of new patches that no old patch covers (prolonged
