@@ -1395,25 +1395,6 @@ amr_status cluster_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
                           const RegridParams& rp, std::vector<HPatch>& out, std::string& msg);
 }  // namespace
 
-amr_status cluster_patches_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
-                                  std::vector<std::vector<uint64_t>>& words, const RegridParams& rp,
-                                  std::vector<HPatch>& out, std::string& msg) {
-  amr_status st = check_regrid_params(cfg, rp, msg);
-  if (st != AMR_OK) return st;
-  const int L = cfg.max_level;
-  std::vector<TagGrid> tags(L + 1);
-  for (int l = rp.min_level; l < L; ++l) {
-    int n[3];
-    regrid_tag_blocks(cfg, rp, l, n);
-    tags[l].reset(n);
-    if (l >= (int)words.size() || !tags[l].adopt(words[l])) {
-      msg = "regrid: block tags of a level do not match its block grid";
-      return AMR_ERR_ARG;
-    }
-  }
-  return cluster_tagged(cfg, old, tags, rp, out, msg);
-}
-
 amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old,
                            const std::vector<std::vector<uint8_t>>& flags, const RegridParams& rp,
                            std::vector<HPatch>& out, std::string& msg) {

@@ -118,14 +118,6 @@ amr_status cluster_patches(const amr_config& cfg, const std::vector<HPatch>& old
 constexpr int64_t kTagDenseMax = (int64_t)1 << 28;
 int64_t regrid_tag_blocks(const amr_config& cfg, const RegridParams& rp, int level, int nb[3]);
 
-// The same clustering from block tags made elsewhere (the GPU): words[l] for
-// levels min_level .. max_level-1 is the level's bitmap, bit i = block (x, y, z)
-// with i = (z nb1 + y) nb0 + x, ceil(blocks / 64) words; the flagged cells grown
-// by rp.buffer, as cluster_patches marks them.  words are consumed.
-amr_status cluster_patches_tagged(const amr_config& cfg, const std::vector<HPatch>& old,
-                                  std::vector<std::vector<uint64_t>>& words, const RegridParams& rp,
-                                  std::vector<HPatch>& out, std::string& msg);
-
 // Blocks of level min_level fully inside one of its patches (a partial block at
 // the domain's end counts when the patch reaches the end): the cover of the
 // clustering's first level, as a dense bitmap laid out as the block tags.
