@@ -151,3 +151,23 @@ def test_block_tags_on_gpu_and_byte_flags_agree(bc):
     o.step(0.002)
     o = rg.regrid(o, threshold=0.1, buffer=2, block=2, max_patch=16)
     assert runs[0][0] == [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches]
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+@pytest.mark.parametrize("block,buffer", [(2, 0), (2, 2), (8, 0), (8, 8)])
+def test_block_and_buffer_sizes_match_the_oracle(bc, block, buffer):
+    """The GPU's block tags, parent rings and refinable sets for other block and
+    buffer sizes: the same three-level hierarchy as the oracle's clustering, and
+    the refilled state within the FP64 parity tolerance."""
+    pb = clumpy(21, bc)
+    o = orc.Oracle(pb, max_level=2, nthreads=8)
+    s = Solver.from_problem(pb, precision="fp64", max_level=2)
+    kw = dict(threshold=0.1, buffer=buffer, block=block, max_patch=4 * block)
+    for cycle in range(2):
+        o.step()
+        s.step()
+        o = rg.regrid(o, **kw)
+        s.regrid(**kw)
+        assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
+               [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"cycle {cycle}"
+        assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", f"regrid block {block} buffer {buffer}")
