@@ -852,6 +852,11 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   const size_t es = h->ops->elem_size();
   Plan& op = h->plan;
   const int nv = op.nvar;
+  std::string msg;
+  {
+    amr_status pst = check_regrid_params(h->cfg, rp, msg);
+    if (pst != AMR_OK) return fail(h, pst, msg);
+  }
   // 1. face ghosts of the flagged levels at the current time
   if (mid) {
     // the saved old-time states are still needed by the step: parent data of the
@@ -864,14 +869,10 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
     h->counting = 0;
     for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
   }
-  // 2. density-gradient criterion.  Block tags made on the GPU when every
-  //    flagged level's block grid fits a bitmap (only the bitmaps come back);
-  //    otherwise one byte per interior cell, tagged on the host.
-  std::string msg;
-  {
-    amr_status pst = check_regrid_params(h->cfg, rp, msg);
-    if (pst != AMR_OK) return fail(h, pst, msg);
-  }
+  // 2. density-gradient criterion.  Block tags and refinable blocks made on the
+  //    GPU when every flagged level's block grid fits a bitmap (only the
+  //    refinable bitmaps come back); otherwise one byte per interior cell, and
+  //    the host clusters.
   const int L = h->cfg.max_level;
   TagArgs ta{};
   ta.l0 = rp.min_level;
