@@ -171,3 +171,47 @@ def test_block_and_buffer_sizes_match_the_oracle(bc, block, buffer):
         assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
                [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"cycle {cycle}"
         assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", f"regrid block {block} buffer {buffer}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mhd_regrid_matches_the_oracle_with_div_b(precision):
+    """GLM-MHD on a regridded hierarchy: the same patches as the oracle's regrid,
+    the refilled and stepped state within the parity tolerance, and the div B
+    norms of the new hierarchy alike."""
+    patches = ai.uniform_patches((32,) * 3, (16,) * 3)
+    pb = ai.random_smooth(patches, (32,) * 3, nvar=9, gamma=5.0 / 3.0, seed=13, amp=0.6)
+    o = orc.Oracle(pb, max_level=2, nthreads=8, ch=1.5)
+    s = Solver.from_problem(pb, precision=precision, max_level=2, ch=1.5)
+    kw = dict(threshold=0.1, buffer=2, block=4, max_patch=32)
+    for cycle in range(2):
+        o.step(0.002)
+        s.step(0.002)
+        o = rg.regrid(o, **kw)
+        s.regrid(**kw)
+        assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
+               [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"cycle {cycle}"
+    o.step(0.002)
+    s.step(0.002)
+    s.check()
+    assert max(p.level for p in s.patches) >= 1
+    assert_parity(s.all_cons(), o.all_cons(), o.patches, precision, "mhd regrid")
+    want, got = o.divb_norms(), s.divb_norms()
+    if precision == "fp64":
+        assert np.allclose(got, want, rtol=1e-10, atol=1e-12 * want[2])
+    else:
+        assert abs(got[0] - want[0]) <= 2e-5 * want[2] and np.allclose(got[2:], want[2:], rtol=2e-6)
+
+
+def test_flux_reconstruction_regrid_matches_the_oracle():
+    pb = clumpy(17, ai.PERIODIC)
+    o = orc.Oracle(pb, max_level=2, nthreads=8, riemann=orc.FLUXREC)
+    s = Solver.from_problem(pb, precision="fp64", max_level=2, riemann="fluxrec")
+    kw = dict(threshold=0.1, buffer=2, block=4, max_patch=32)
+    for cycle in range(2):
+        o.step()
+        s.step()
+        o = rg.regrid(o, **kw)
+        s.regrid(**kw)
+        assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
+               [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"cycle {cycle}"
+        assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", f"fluxrec regrid {cycle}")
