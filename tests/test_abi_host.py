@@ -75,6 +75,11 @@ def test_validation_status_codes(patches, base, maxl, want):
     assert st == want, msg
 
 
+def test_empty_patch_set_is_rejected():
+    st, msg = N.amr_validate_patches(cfg(), [])
+    assert st == N.AMR_ERR_ARG, msg
+
+
 def test_periodic_nesting_wraps_around_the_domain():
     base = (16, 16, 16)
     pats = [P(0, (0, 0, 0), (16, 16, 16)), P(1, (0, 8, 8), (8, 8, 8))]

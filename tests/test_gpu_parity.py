@@ -205,6 +205,14 @@ def test_state_calls_before_set_patches_fail_cleanly():
         with pytest.raises(N.AmrError) as e:
             N.amr_step(h, 0.1)
         assert e.value.status == N.AMR_ERR_STATE
+        for call in (lambda: N.amr_divb_norms(h), lambda: N.amr_set_state_async(h, np.zeros(8)),
+                     lambda: N.amr_get_state_all_async(h, np.zeros(8)), lambda: N.amr_conserved_totals(h, 5)):
+            with pytest.raises(N.AmrError) as e:
+                call()
+            assert e.value.status == N.AMR_ERR_STATE
+        with pytest.raises(N.AmrError) as e:
+            N.amr_wait_state(h, 0)                 # no download was issued
+        assert e.value.status == N.AMR_ERR_ARG
     finally:
         N.amr_destroy(h)
 
