@@ -1360,7 +1360,7 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   for (int o = 0; o < 2; ++o) {
     if (o == 1 && occs[1] == 0) continue;
     for (auto& sh : shapes) {
-      if (o == 1 && sh[1] == 128) continue;   // the 128-thread build keeps the default register budget
+      if (o == 1 && sh[1] == 128 && !h->ops->has_alt128()) continue;   // no second 128-thread budget
       Cand c;
       c.tp.max_wx = sh[0]; c.tp.max_cols = sh[1]; c.tp.zchunk = sh[2];
       c.occ = occs[o];
@@ -1400,7 +1400,7 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
     }
     char line[160];
     std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d: %.4f ms\n", h->tp.max_wx,
-                  h->tp.max_cols, h->tp.zchunk, h->ops->stage_occupancy(), t_best);
+                  h->tp.max_cols, h->tp.zchunk, h->ops->resident_ctas(), t_best);
     rep += line;
     if (t_best < best) { best = t_best; best_i = (int)ci; }
   }

@@ -19,6 +19,9 @@ constexpr int kMaxVar = 9;
 constexpr int kStageThreads = 256;  // threads of one stage-kernel CTA (one per x-y column)
 constexpr int kMaxTileX = 32;
 constexpr int kPlaneMax = 432;    // max (wx + 4) * (wy + 4) of a stage tile
+// 128-thread stage CTAs: wx * wy <= 128 and wx + wy <= 32 give (wx + 4)(wy + 4) <= 272
+constexpr int kPlaneMax128 = 272;
+AMR_HD constexpr int stage_plane_max(int nt) { return nt == 128 ? kPlaneMax128 : kPlaneMax; }
 
 // Device view of one patch.  Arrays U, U1 and Uold share the same layout and
 // offsets: var v, ghosted local cell (i, j, k) with -2 <= i < n0 + 2 sits at

@@ -511,8 +511,9 @@ void build_items(Plan& plan, const TileParams& tp) {
       split(p.n[2], zparts, zs);
       for (auto& z : zs)
         for (auto& x : xs) {
-          // one halo cell per thread: 4 (wx + wy) <= threads (= max_cols); plane with halo within kPlaneMax
-          int wymax = std::min(std::min(max_cols / x.second, kPlaneMax / (x.second + 4) - 4),
+          // one halo cell per thread: 4 (wx + wy) <= threads (= max_cols); plane with halo within
+          // the shared-memory plane of the CTA size that runs the tile
+          int wymax = std::min(std::min(max_cols / x.second, stage_plane_max(max_cols) / (x.second + 4) - 4),
                                max_cols / 4 - x.second);
           wymax = std::max(wymax, 1);
           split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);

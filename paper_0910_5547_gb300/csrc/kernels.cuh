@@ -37,17 +37,22 @@
 
 namespace amr {
 
-// Shared memory of a stage CTA, per variable: the primitive plane with its
-// face halo, (wy + 4) x (wx + 4) <= kPlaneMax cells; four face-state arrays
-// (left/right states of x faces, (wx + 2) wy <= kStateMax, and of y faces,
-// (wy + 2) wx <= kStateMax); and the x face fluxes, wy (wx + 1) <= kFaceX, and
-// y face fluxes, (wy + 1) wx <= kFaceY.  The planner keeps wx * wy <= 256,
-// wx <= 32, 4 (wx + wy) <= 256 (so wy <= 63) and (wx + 4)(wy + 4) <= kPlaneMax.
-// Fixed strides keep every shared-memory address an immediate offset.
-constexpr int kFaceX = kStageThreads + 64;
-constexpr int kFaceY = kStageThreads + 32;
-constexpr int kFaceMax = kFaceX + kFaceY;
-constexpr int kStateMax = kStageThreads + 128;
+// Shared memory of a stage CTA of NT threads, per variable: the primitive
+// plane with its face halo, (wy + 4) x (wx + 4) <= plane cells; four face-state
+// arrays (left/right states of x faces, (wx + 2) wy <= state, and of y faces,
+// (wy + 2) wx <= state); and the x face fluxes, wy (wx + 1) <= facex, and y
+// face fluxes, (wy + 1) wx <= facey.  The planner keeps wx * wy <= NT, wx <= 32,
+// 4 (wx + wy) <= NT and (wx + 4)(wy + 4) <= plane; for NT = 256 that bounds
+// wy <= 63, for NT = 128 wx, wy <= 31.  Fixed strides keep every shared-memory
+// address an immediate offset.
+template <int NT>
+struct StageDims {
+  static constexpr int plane = NT == 128 ? kPlaneMax128 : kPlaneMax;
+  static constexpr int state = NT == 128 ? NT + 64 : NT + 128;
+  static constexpr int facex = NT + 64;
+  static constexpr int facey = NT + 32;
+  static constexpr int face = facex + facey;
+};
 
 // FP32 Euler stage kernels also stage their conserved inputs through shared
 // memory, filled by cp.async: a ring of four planes of the stage input (own
@@ -57,24 +62,26 @@ constexpr int kStateMax = kStageThreads + 128;
 constexpr int kRing = 4;
 constexpr int kRingN = 2;
 
-template <typename T, int NV>
+template <typename T, int NV, int NT = kStageThreads>
 __host__ __device__ constexpr size_t stage_smem_base() {
-  return sizeof(T) * NV * (kPlaneMax + 4 * kStateMax + kFaceMax);
+  using D = StageDims<NT>;
+  return sizeof(T) * NV * (D::plane + 4 * D::state + D::face);
 }
-template <typename T, int NV>
+template <typename T, int NV, int NT = kStageThreads>
 __host__ __device__ constexpr size_t stage_smem_rings() {
-  return sizeof(T) * NV * (kRing * kPlaneMax + kRingN * kStageThreads);
+  return sizeof(T) * NV * (kRing * StageDims<NT>::plane + kRingN * NT);
 }
 // The rings are used where the CTAs per SM a variant asks for (MINB) still fit
 // in the SM's 228 KB of shared memory (1 KB reserved per CTA).
-template <typename T, int NV, int MINB>
+template <typename T, int NV, int MINB, int NT = kStageThreads>
 __host__ __device__ constexpr bool stage_async() {
   return NV == 5 && sizeof(T) == 4 &&
-         (size_t)MINB * (stage_smem_base<T, NV>() + stage_smem_rings<T, NV>() + 1024) <= (size_t)228 * 1024;
+         (size_t)MINB * (stage_smem_base<T, NV, NT>() + stage_smem_rings<T, NV, NT>() + 1024) <=
+             (size_t)228 * 1024;
 }
-template <typename T, int NV, int MINB = 2>
+template <typename T, int NV, int MINB = 2, int NT = kStageThreads>
 constexpr size_t stage_smem_bytes() {
-  return stage_smem_base<T, NV>() + (stage_async<T, NV, MINB>() ? stage_smem_rings<T, NV>() : 0);
+  return stage_smem_base<T, NV, NT>() + (stage_async<T, NV, MINB, NT>() ? stage_smem_rings<T, NV, NT>() : 0);
 }
 
 // Asynchronous global -> shared copy of one element (sm_80+ cp.async).
@@ -175,18 +182,24 @@ __device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, 
 template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1, int NT = kStageThreads>
 __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kPlane = StageDims<NT>::plane, kState = StageDims<NT>::state;
+  constexpr int kFaceX = StageDims<NT>::facex, kFaceY = StageDims<NT>::facey;
   T* W = reinterpret_cast<T*>(smem_raw);
-  T* XL = W + NV * kPlaneMax;
-  T* XR = XL + NV * kStateMax;
-  T* YL = XR + NV * kStateMax;
-  T* YR = YL + NV * kStateMax;
-  T* FX = YR + NV * kStateMax;
-  constexpr bool kAsync = stage_async<T, NV, MINB>();
+  T* XL = W + NV * kPlane;
+  T* XR = XL + NV * kState;
+  T* YL = XR + NV * kState;
+  T* YR = YL + NV * kState;
+  T* FX = YR + NV * kState;
+  constexpr bool kAsync = stage_async<T, NV, MINB, NT>();
+  // 128-thread builds at 3+ CTAs per SM (FP32 MHD, 168 registers) read the stage
+  // input and U^n of the updated cell in phase B instead of carrying register
+  // prefetches through phase A: no spills, latency covered by 12 warps per SM
+  constexpr bool kLean = !kAsync && NT == 128 && MINB >= 3;
   // ring of stage-input planes: plane p of the item lives in slot p & 3, [slot][var][plane cell];
   // ring of U^n planes (stage 2): plane p in slot p & 1, [slot][var][thread].  Each thread
   // reads back only the cells it copied itself (own column, own halo cell).
-  T* CR = FX + NV * kFaceMax;
-  T* CN = CR + kRing * NV * kPlaneMax;
+  T* CR = FX + NV * StageDims<NT>::face;
+  T* CN = CR + kRing * NV * kPlane;
 
   const Phys<T> ph = phys_with_ch<T, NV>(a.ph, a.params);
   const T dt = (T)(a.params->dt0 * a.dt_scale);
@@ -273,13 +286,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (kAsync) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          CR[v * kPlaneMax + me] = uD[v];                                                 // plane 0, slot 0
-          cp_async_elem(&CR[(NV + v) * kPlaneMax + me], Ub + v * vs + col + plane);     // plane 1, slot 1
+          CR[v * kPlane + me] = uD[v];                                                 // plane 0, slot 0
+          cp_async_elem(&CR[(NV + v) * kPlane + me], Ub + v * vs + col + plane);     // plane 1, slot 1
         }
       } else {
         load_cons<T, NV>(Ub, vs, col + plane, uD);
       }
-      if (STAGE == 2 && !kAsync) load_cons<T, NV>(Ob, vs, col, unN);
+      if (STAGE == 2 && !kAsync && !kLean) load_cons<T, NV>(Ob, vs, col, unN);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sA[v] = limited_slope(w0[v], wA[v], wB[v], ph.theta);
     }
@@ -287,8 +300,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (has_halo) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          cp_async_elem(&CR[v * kPlaneMax + hpos], Ub + v * vs + hoff);
-          if (wz > 1) cp_async_elem(&CR[(NV + v) * kPlaneMax + hpos], Ub + v * vs + hoff + plane);
+          cp_async_elem(&CR[v * kPlane + hpos], Ub + v * vs + hoff);
+          if (wz > 1) cp_async_elem(&CR[(NV + v) * kPlane + hpos], Ub + v * vs + hoff + plane);
         }
       }
       cp_async_commit();
@@ -320,19 +333,19 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       // ---- phase A ----
       if (kAsync) {  // copies of plane j+2 (ghost planes end at wz+1), then wait for plane j+1
         const int jn = j + 2;
-        T* slot = CR + (jn & (kRing - 1)) * NV * kPlaneMax;
+        T* slot = CR + (jn & (kRing - 1)) * NV * kPlane;
         if (active && jn <= wz + 1) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlaneMax + me], Ub + v * vs + col + jn * plane);
+          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlane + me], Ub + v * vs + col + jn * plane);
         }
         if (has_halo && jn < wz) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlaneMax + hpos], Ub + v * vs + hoff + jn * plane);
+          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlane + hpos], Ub + v * vs + hoff + jn * plane);
         }
         if (STAGE == 2 && active && cur) {  // U^n of plane j, used by the update of plane j
-          T* sn = CN + (j & (kRingN - 1)) * NV * kStageThreads + t;
+          T* sn = CN + (j & (kRingN - 1)) * NV * NT + t;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&sn[v * kStageThreads], Ob + v * vs + col + j * plane);
+          for (int v = 0; v < NV; ++v) cp_async_elem(&sn[v * NT], Ob + v * vs + col + j * plane);
         }
         cp_async_commit();
         cp_async_wait1();
@@ -340,23 +353,23 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (has_halo && cur) {
         T w[NV];
         if (kAsync) {
-          const T* slot = CR + (j & (kRing - 1)) * NV * kPlaneMax + hpos;
+          const T* slot = CR + (j & (kRing - 1)) * NV * kPlane + hpos;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlaneMax];
+          for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlane];
         }
         cons_to_prim<T, NV>(hN, w, ph.efl);
         if (!kAsync) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) W[v * kPlaneMax + hpos] = w[v];
+        for (int v = 0; v < NV; ++v) W[v * kPlane + hpos] = w[v];
       }
       if (active) {
         // stage input of the own cell, plane j-1 (read earlier: a cache hit; plane -1 is a ghost plane)
-        if (!kAsync) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
+        if (!kAsync && !kLean) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
         T wC[NV], sB[NV], wl[NV], wr[NV], xl[NV], xr[NV], yl[NV], yr[NV];
         if (kAsync) {
-          const T* slot = CR + ((j + 1) & (kRing - 1)) * NV * kPlaneMax + me;
+          const T* slot = CR + ((j + 1) & (kRing - 1)) * NV * kPlane + me;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) uD[v] = slot[v * kPlaneMax];
+          for (int v = 0; v < NV; ++v) uD[v] = slot[v * kPlane];
         }
         int hit = 0;
         const bool ok = cons_to_prim<T, NV>(uD, wC, ph.efl, &hit);   // plane j+1
@@ -374,18 +387,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           wl[v] = wA[v] + sc * sA[v];
           wr[v] = wB[v] - sc * sB[v];
           own[v] = wB[v];
-          W[v * kPlaneMax + me] = wB[v];
+          W[v * kPlane + me] = wB[v];
         }
         if (kMerge) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            xl[v] = XL[v * kStateMax + xs - 1];
+            xl[v] = XL[v * kState + xs - 1];
             xr[v] = xrOwn[v];
-            yl[v] = YL[v * kStateMax + ys - wx];
+            yl[v] = YL[v * kState + ys - wx];
             yr[v] = yrOwn[v];
           }
         }
-        if (STAGE == 2 && !kAsync) {
+        if (STAGE == 2 && !kAsync && !kLean) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) un[v] = unN[v];
           load_cons<T, NV>(Ob, vs, col + (cur ? j : j - 1) * plane, unN);
@@ -395,9 +408,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           if (!kMerge) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              xl[v] = XL[v * kStateMax + xs - 1];
+              xl[v] = XL[v * kState + xs - 1];
               xr[v] = xrOwn[v];
-              yl[v] = YL[v * kStateMax + ys - wx];
+              yl[v] = YL[v * kState + ys - wx];
               yr[v] = yrOwn[v];
             }
           }
@@ -423,8 +436,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         const int sl = eb * (wx + 2) + wx;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          wl[v] = XL[v * kStateMax + sl];
-          wr[v] = XR[v * kStateMax + sl + 1];
+          wl[v] = XL[v * kState + sl];
+          wr[v] = XR[v * kState + sl + 1];
         }
         riemann<T, NV, 0>(wl, wr, ph, F);
 #pragma unroll
@@ -435,8 +448,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         const int sl = wy * wx + c;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          wl[v] = YL[v * kStateMax + sl];
-          wr[v] = YR[v * kStateMax + sl + wx];
+          wl[v] = YL[v * kState + sl];
+          wr[v] = YR[v * kState + sl + wx];
         }
         riemann<T, NV, 1>(wl, wr, ph, F);
 #pragma unroll
@@ -446,14 +459,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       // ---- phase B ----
       if (active && (kMerge || prev)) {  // U1 = U + dt L(U)  |  U = U^n / 2 + (U1 + dt L(U1)) / 2, plane j-1
         const int c = col + (j - 1) * plane;
+        if (kLean) {
+          load_cons<T, NV>(Ub, vs, c, uin);
+          if (STAGE == 2) load_cons<T, NV>(Ob, vs, c, un);
+        }
         if (kAsync) {
-          const T* slot = CR + ((j - 1) & (kRing - 1)) * NV * kPlaneMax + me;
+          const T* slot = CR + ((j - 1) & (kRing - 1)) * NV * kPlane + me;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) uin[v] = slot[v * kPlaneMax];
+          for (int v = 0; v < NV; ++v) uin[v] = slot[v * kPlane];
           if (STAGE == 2) {
-            const T* sn = CN + ((j - 1) & (kRingN - 1)) * NV * kStageThreads + t;
+            const T* sn = CN + ((j - 1) & (kRingN - 1)) * NV * NT + t;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) un[v] = sn[v * kStageThreads];
+            for (int v = 0; v < NV; ++v) un[v] = sn[v * NT];
           }
         }
 #pragma unroll
@@ -485,13 +502,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (active && (kMerge || cur)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlaneMax + me;
+          const T* Wv = W + v * kPlane + me;
           const T w0 = own[v];
           const T sx = limited_slope(Wv[-1], w0, Wv[1], ph.theta);
           const T sy = limited_slope(Wv[-sw], w0, Wv[sw], ph.theta);
-          XL[v * kStateMax + xs] = w0 + sc * sx;
+          XL[v * kState + xs] = w0 + sc * sx;
           xrOwn[v] = w0 - sc * sx;
-          YL[v * kStateMax + ys] = w0 + sc * sy;
+          YL[v * kState + ys] = w0 + sc * sy;
           yrOwn[v] = w0 - sc * sy;
         }
       }
@@ -500,9 +517,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         const T sgn = (bkind == 0 || bkind == 2) ? sc : -sc;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlaneMax + bpos;
+          const T* Wv = W + v * kPlane + bpos;
           const T w0 = Wv[0];
-          dst[v * kStateMax + bslot] = w0 + sgn * limited_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
+          dst[v * kState + bslot] = w0 + sgn * limited_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
         }
       }
       __syncthreads();

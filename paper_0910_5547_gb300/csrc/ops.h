@@ -33,6 +33,10 @@ struct OpsBase {
   virtual void set_stage_occupancy(int ctas_per_sm) = 0;
   // threads per stage CTA: 256 (default) or 128 (same registers per thread, twice the CTAs)
   virtual void set_stage_threads(int nt) = 0;
+  // whether the 128-thread build also has an alternate (smaller) register budget
+  virtual bool has_alt128() const = 0;
+  // resident CTAs per SM of the build the next stage launch uses
+  virtual int resident_ctas() const = 0;
   virtual cudaError_t ghost_copy(cudaStream_t s, const CopySeg* segs, int nseg, const PatchDesc* desc, void* arena) = 0;
   // batched forms over flattened boxes (same values as ghost_copy / gather / prolong)
   virtual cudaError_t ghost_copy_flat(cudaStream_t s, const FlatCopy* boxes, const int* first, const int* chunk_box,

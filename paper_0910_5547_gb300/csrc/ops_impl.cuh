@@ -16,6 +16,9 @@ struct Ops final : OpsBase {
   static constexpr int kDef = (sizeof(T) == 4 && NV == 5) ? 2 : 1;
   static constexpr int kAlt = (sizeof(T) == 4 && NV == 5) ? 3 : 2;
   static constexpr bool kHasAlt = !(sizeof(T) == 8 && NV == 9);
+  // 128-thread CTAs: 2 kDef per SM with the default registers; FP32 MHD also
+  // has a 3-per-SM build (168 registers: 12 warps instead of 8)
+  static constexpr int kAlt128 = (sizeof(T) == 4 && NV == 9) ? 3 : 0;
   int nt = kStageThreads;   // 256, or 128 (launched with twice the CTAs per SM, same register budget)
 
   explicit Ops(const PhysParams& p) {
@@ -34,9 +37,15 @@ struct Ops final : OpsBase {
     cudaFuncSetAttribute(stage_kernel<T, NV, 2, kDef>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem_bytes<T, NV, kDef>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 1, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, 2 * kDef>());
+                         (int)stage_smem_bytes<T, NV, 2 * kDef, 128>());
     cudaFuncSetAttribute(stage_kernel<T, NV, 2, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, 2 * kDef>());
+                         (int)stage_smem_bytes<T, NV, 2 * kDef, 128>());
+    if constexpr (kAlt128 > 0) {
+      cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)stage_smem_bytes<T, NV, kAlt128, 128>());
+      cudaFuncSetAttribute(stage_kernel<T, NV, 2, kAlt128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)stage_smem_bytes<T, NV, kAlt128, 128>());
+    }
     if (kHasAlt) {
       cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)stage_smem_bytes<T, NV, kAlt>());
@@ -49,6 +58,11 @@ struct Ops final : OpsBase {
   int stage_occupancy() const override { return occ == kAlt ? kAlt : kDef; }
   int alt_occupancy() const override { return kHasAlt ? kAlt : 0; }
   void set_stage_occupancy(int c) override { occ = (kHasAlt && c == kAlt) ? kAlt : 0; }
+  bool has_alt128() const override { return kAlt128 > 0; }
+  int resident_ctas() const override {
+    if (nt == 128) return (kAlt128 > 0 && occ == kAlt) ? kAlt128 : 2 * kDef;
+    return occ == kAlt ? kAlt : kDef;
+  }
 
   size_t elem_size() const override { return sizeof(T); }
 
@@ -80,8 +94,16 @@ struct Ops final : OpsBase {
         return cudaGetLastError();
       }
     }
+    if constexpr (kAlt128 > 0) {
+      if (nt == 128 && occ == kAlt) {
+        const size_t sm = stage_smem_bytes<T, NV, kAlt128, 128>();
+        if (stage == 1) stage_kernel<T, NV, 1, kAlt128, 128><<<g, 128, sm, s>>>(a);
+        else stage_kernel<T, NV, 2, kAlt128, 128><<<g, 128, sm, s>>>(a);
+        return cudaGetLastError();
+      }
+    }
     if (nt == 128) {
-      const size_t sm = stage_smem_bytes<T, NV, 2 * kDef>();
+      const size_t sm = stage_smem_bytes<T, NV, 2 * kDef, 128>();
       if (stage == 1) stage_kernel<T, NV, 1, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
       else stage_kernel<T, NV, 2, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
     } else if (kHasAlt && occ == kAlt) {

@@ -227,6 +227,47 @@ __device__ __forceinline__ void hll_euler(const T* wl, const T* wr, const Phys<T
   F[4] += ql * vl - qr * vr;
 }
 
+// GLM-MHD HLL in the same form as hll_euler: with F = U v_n + P,
+// P = (0, pt e_D - B B_n, pt v_n - B_n (B.v), -v B_n, 0), the two-wave flux is
+// alpha U_l + beta U_r + a P_l - b P_r, so neither side's conserved vector nor
+// physical flux is formed.  wl/wr carry the Dedner-resolved normal field Bm.
+template <typename T, int D>
+__device__ __forceinline__ void hll_mhd(const T* wl, const T* wr, const Phys<T>& ph, T Bm, T* F) {
+  T pt[2], c[2], B2[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T* w = s ? wr : wl;
+    const T b2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+    const T a2 = ph.ggm1 * w[4];
+    const T r = drcp(w[0]);
+    const T q = a2 + b2 * r;
+    const T disc = dmax(q * q - T(4) * a2 * (Bm * Bm * r), T(0));
+    c[s] = dsqrt(T(0.5) * (q + dsqrt(disc)));
+    pt[s] = ph.gm1 * w[0] * w[4] + T(0.5) * b2;
+    B2[s] = b2;
+  }
+  const T vl = wl[1 + D], vr = wr[1 + D];
+  const T SL = min3(T(0), vl - c[0], vr - c[1]);
+  const T SR = max3(T(0), vl + c[0], vr + c[1]);
+  const T inv = drcp(SR - SL);
+  const T a = SR * inv, b = SL * inv;
+  const T al = a * (vl - SL), be = b * (SR - vr);
+  const T ar = al * wl[0], br = be * wr[0];
+  F[0] = ar + br;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    F[1 + k] = ar * wl[1 + k] + br * wr[1 + k] - Bm * (a * wl[5 + k] - b * wr[5 + k]);
+    if (k != D) F[5 + k] = al * wl[5 + k] + be * wr[5 + k] - Bm * (a * wl[1 + k] - b * wr[1 + k]);
+  }
+  F[1 + D] += a * pt[0] - b * pt[1];
+  const T hl = T(0.5) * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) + wl[4];
+  const T hr = T(0.5) * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) + wr[4];
+  const T bvl = wl[5] * wl[1] + wl[6] * wl[2] + wl[7] * wl[3];
+  const T bvr = wr[5] * wr[1] + wr[6] * wr[2] + wr[7] * wr[3];
+  F[4] = ar * hl + br * hr + T(0.5) * (al * B2[0] + be * B2[1]) + a * (pt[0] * vl - Bm * bvl) -
+         b * (pt[1] * vr - Bm * bvr);
+}
+
 template <typename T, int NV, int D>
 __device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
   if (NV == 5) {
@@ -242,6 +283,12 @@ __device__ __forceinline__ void riemann(T* wl, T* wr, const Phys<T>& ph, T* F) {
     psim = T(0.5) * (wl[8] + wr[8]) - T(0.5) * ph.ch * (Br - Bl);
     wl[5 + D] = Bm;
     wr[5 + D] = Bm;
+    if (!ph.llf) {
+      hll_mhd<T, D>(wl, wr, ph, Bm, F);
+      F[5 + D] = psim;
+      F[8] = ph.ch2 * Bm;
+      return;
+    }
   }
   T Ul[NV], Ur[NV], Fl[NV], Fr[NV], cl, cr;
   state_flux<T, NV, D>(wl, ph, Ul, Fl, cl);
