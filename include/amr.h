@@ -191,6 +191,22 @@ amr_status amr_get_regrid_counts(amr_handle* h, long long* counts);
  * AMR_ERR_ARG on bad parameters; a failed rebuild fails the amr_step. */
 amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, int max_level);
 
+/* Stage-kernel work items and build, the choice amr_autotune makes, set
+ * directly (fixed tiles for reproducible timings and profiles):
+ *   max_wx       x width cap of a work item, 1..32 (0: 32)
+ *   max_cols     columns per CTA: 256 or 128 (128-thread CTAs); 0: 256
+ *   zchunk       z planes per work item, >= 1 (0: 32)
+ *   ctas_per_sm  resident CTAs per SM of the compiled build to run (register
+ *                budget), one of: FP32 Euler 2 or 3 (256 columns), 4 (128);
+ *                FP32 GLM-MHD 1 or 2 (256), 2 or 3 (128); FP64 Euler 1 or 2
+ *                (256), 2 (128); FP64 GLM-MHD 1 (256), 2 (128); 0: the
+ *                default build of that column count.
+ * The direct flux reconstruction variant (AMR_FLUXREC) uses only max_wx,
+ * max_cols and zchunk.  May be called before amr_set_patches; applies to later
+ * hierarchies too.  AMR_ERR_ARG for a value outside these sets (the previous
+ * tiling stays).  Invalidates the step graphs. */
+amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, int ctas_per_sm);
+
 /* Autotuner: time the stage kernel over the installed hierarchy for each
  * candidate work-item shape (x width, columns per CTA, z chunk) and register
  * budget (2 or 3 resident CTAs per SM for FP32 Euler) and keep the fastest for

@@ -1348,6 +1348,40 @@ amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, 
   return AMR_OK;
 }
 
+amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, int ctas_per_sm) {
+  if (!h) return AMR_ERR_ARG;
+  if (max_wx < 0 || max_wx > kMaxTileX) return fail(h, AMR_ERR_ARG, "max_wx must be in 0..32");
+  if (max_cols != 0 && max_cols != 128 && max_cols != kStageThreads)
+    return fail(h, AMR_ERR_ARG, "max_cols must be 0, 128 or 256");
+  if (zchunk < 0) return fail(h, AMR_ERR_ARG, "zchunk must be >= 0");
+  if (ctas_per_sm < 0) return fail(h, AMR_ERR_ARG, "ctas_per_sm must be >= 0");
+  const int keep_occ = h->ops->stage_occupancy();
+  h->ops->set_stage_threads(max_cols == 128 ? 128 : kStageThreads);
+  int occ = -1;
+  for (int o : {0, h->ops->alt_occupancy()}) {
+    h->ops->set_stage_occupancy(o);
+    if (ctas_per_sm == 0 ? o == 0 : h->ops->resident_ctas() == ctas_per_sm) {
+      occ = o;
+      break;
+    }
+  }
+  if (occ < 0) {
+    h->ops->set_stage_occupancy(keep_occ);
+    h->ops->set_stage_threads(h->tp.max_cols);
+    return fail(h, AMR_ERR_ARG, "no stage-kernel build with that many CTAs per SM for this column count");
+  }
+  h->tp.max_wx = max_wx;
+  h->tp.max_cols = max_cols;
+  h->tp.zchunk = zchunk;
+  for (int g = 0; g < 4; ++g) {
+    if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+    h->graph[g] = nullptr;
+  }
+  if (!h->ready) return AMR_OK;
+  build_items(h->plan, h->tp);
+  return upload_items(h);
+}
+
 amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   if (!h) return AMR_ERR_ARG;
   Range range("amr_autotune");

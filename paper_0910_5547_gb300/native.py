@@ -35,7 +35,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_state_size", "amr_step", "amr_cfl_dt", "amr_get_state", "amr_get_state_all",
            "amr_conserved_totals", "amr_check", "amr_kernel_launches", "amr_last_error", "amr_global_error",
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
-           "amr_get_patches", "amr_autotune", "amr_get_regrid_timing", "amr_floor_count",
+           "amr_get_patches", "amr_autotune", "amr_set_tiling", "amr_get_regrid_timing", "amr_floor_count",
            "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms", "amr_set_state_async",
            "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches", "amr_get_regrid_counts"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
@@ -143,6 +143,8 @@ def load():
     L.amr_get_patches.argtypes = [H, ctypes.POINTER(amr_patch), ctypes.c_int]
     L.amr_autotune.argtypes = [H, ctypes.c_char_p, ctypes.c_int]
     L.amr_autotune.restype = ctypes.c_int
+    L.amr_set_tiling.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.amr_set_tiling.restype = ctypes.c_int
     L.amr_get_regrid_timing.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     L.amr_get_regrid_timing.restype = ctypes.c_int
     L.amr_floor_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
@@ -400,6 +402,11 @@ def amr_set_regrid_schedule(h, max_level: int, threshold=0.3, buffer=2, block=4,
 def amr_cell_updates(h) -> int:
     """Interior cell-updates performed by amr_step so far (sum over level steps)."""
     return int(load().amr_cell_updates(h))
+
+
+def amr_set_tiling(h, max_wx: int = 0, max_cols: int = 0, zchunk: int = 0, ctas_per_sm: int = 0) -> None:
+    """Fix the stage-kernel work items (x width cap, columns per CTA, z chunk) and build (CTAs per SM)."""
+    _check(h, load().amr_set_tiling(h, max_wx, max_cols, zchunk, ctas_per_sm))
 
 
 def amr_autotune(h) -> str:

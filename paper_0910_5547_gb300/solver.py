@@ -110,6 +110,10 @@ class Solver:
     def launches(self) -> int:
         return N.amr_kernel_launches(self.h)
 
+    def set_tiling(self, max_wx: int = 0, max_cols: int = 0, zchunk: int = 0, ctas_per_sm: int = 0) -> None:
+        """Fix the stage-kernel work items and build instead of autotuning (0 = default)."""
+        N.amr_set_tiling(self.h, max_wx, max_cols, zchunk, ctas_per_sm)
+
     def autotune(self) -> str:
         """Time the stage kernel's candidate tilings on this hierarchy and keep the fastest."""
         return N.amr_autotune(self.h)

@@ -35,6 +35,10 @@ def test_library_exports_every_declared_symbol():
     assert sorted(N.EXPORTS) == names
 
 
+def test_tiling_on_a_null_handle_is_rejected():
+    assert N.load().amr_set_tiling(None, 0, 0, 0, 0) == N.AMR_ERR_ARG
+
+
 def cfg(**kw):
     return N.amr_default_config(**kw)
 
