@@ -415,26 +415,29 @@ def main():
     if "e2e" in phases:
         # end to end through the C ABI: every step uploads its input state (FP64, pinned)
         # and downloads its result; the uploads and downloads run on the library's copy
-        # streams beside the steps (two steps in flight).  Measured before the other
-        # workloads build and free tens of GB of host arrays: pinned buffers allocated
-        # after that moved data markedly slower on the same box.
+        # streams beside the steps (three steps in flight, three host buffers per
+        # direction).  Measured before the other workloads build and free tens of GB of
+        # host arrays: pinned buffers allocated after that moved data markedly slower on
+        # the same box.
         s = make_solver(single, "fp32", True, True, stream)
         nstate = NV.amr_state_size(s.h)
-        h_in = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-        h_out = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        depth = 3
+        h_in = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(depth)]
+        h_out = [torch.empty(nstate, dtype=torch.float64, pin_memory=True).numpy() for _ in range(depth)]
         h_in[0][:] = s.state_all()
-        h_in[1][:] = h_in[0]
+        for b in h_in[1:]:
+            b[:] = h_in[0]
         ke = max(3, min(args.steps, 20))
 
         def e2e_steps(n):
             tickets = []
             for k in range(n):
-                if k >= 2:
-                    NV.amr_wait_state(s.h, tickets[k - 2])   # buffers k % 2 are free again
-                NV.amr_set_state_async(s.h, h_in[k % 2], NV.AMR_STATE_CONSERVED)
+                if k >= depth:
+                    NV.amr_wait_state(s.h, tickets[k - depth])   # buffers k % depth are free again
+                NV.amr_set_state_async(s.h, h_in[k % depth], NV.AMR_STATE_CONSERVED)
                 s.step(0.0, sync=False)
-                tickets.append(NV.amr_get_state_all_async(s.h, h_out[k % 2]))
-            for t in tickets[-2:]:
+                tickets.append(NV.amr_get_state_all_async(s.h, h_out[k % depth]))
+            for t in tickets[-depth:]:
                 NV.amr_wait_state(s.h, t)
 
         e2e_steps(3)

@@ -246,7 +246,7 @@ amr_status amr_get_state(amr_handle* h, int patch, double* out);
  * amr_set_state).  Synchronises. */
 amr_status amr_get_state_all(amr_handle* h, double* packed);
 
-/* Stream-ordered copies that overlap the compute: the library keeps two device
+/* Stream-ordered copies that overlap the compute: the library keeps three device
  * staging slots per direction and one copy stream per direction.
  * amr_set_state_async: as amr_set_state, but returns at once; the host buffer
  *   (pinned for a true asynchronous copy) must stay unchanged until a later
@@ -255,8 +255,9 @@ amr_status amr_get_state_all(amr_handle* h, double* packed);
  * amr_get_state_all_async: enqueues the download of the state as of this point
  *   in stream order into the caller's host buffer and returns a ticket; the
  *   buffer is valid once amr_wait_state(h, ticket) has returned.
- * Up to two transfers per direction are in flight; a third waits (on the GPU)
- * for the slot of the first.  Pinned host buffers make the copies run beside
+ * Up to three transfers per direction are in flight; a fourth waits (on the
+ * GPU) for the slot of the first.  A host loop that reuses three buffers per
+ * direction and waits for ticket k-3 before step k keeps the host link busy.  Pinned host buffers make the copies run beside
  * the steps; pageable ones still work, with the driver's staging. */
 amr_status amr_set_state_async(amr_handle* h, const double* packed, int state_kind);
 amr_status amr_get_state_all_async(amr_handle* h, double* packed, long long* ticket);

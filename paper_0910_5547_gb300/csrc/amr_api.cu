@@ -115,13 +115,14 @@ struct amr_handle {
   cudaMemPool_t pool = nullptr;   // stream-ordered device memory (no caller allocator)
   unsigned char* stage = nullptr; // pinned host staging of the table uploads
   size_t stage_cap = 0, stage_cap_seen = 0;
-  // asynchronous state copies: one copy stream per direction, two device slots
-  // per direction (packed FP64), events that order slot reuse across streams
+  // asynchronous state copies: one copy stream per direction, kSlots device
+  // slots per direction (packed FP64), events that order slot reuse across streams
+  static constexpr int kSlots = 3;
   cudaStream_t cs_in = nullptr, cs_out = nullptr;
-  double* in_slot[2] = {nullptr, nullptr};
-  double* out_slot[2] = {nullptr, nullptr};
+  double* in_slot[kSlots] = {};
+  double* out_slot[kSlots] = {};
   int64_t slot_elems = -1;
-  cudaEvent_t ev_h2d[2] = {}, ev_in_used[2] = {}, ev_packout[2] = {}, ev_d2h[2] = {};
+  cudaEvent_t ev_h2d[kSlots] = {}, ev_in_used[kSlots] = {}, ev_packout[kSlots] = {}, ev_d2h[kSlots] = {};
   long long n_in = 0, n_out = 0;
   OpsBase* ops = nullptr;
   std::string err;
@@ -322,7 +323,7 @@ cudaError_t ensure_async(amr_handle* h) {
   if (!h->cs_in) {
     e = cudaStreamCreateWithFlags(&h->cs_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs_out, cudaStreamNonBlocking);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < amr_handle::kSlots && e == cudaSuccess; ++k) {
       cudaEvent_t* evs[4] = {&h->ev_h2d[k], &h->ev_in_used[k], &h->ev_packout[k], &h->ev_d2h[k]};
       for (cudaEvent_t* ev : evs)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -333,14 +334,14 @@ cudaError_t ensure_async(amr_handle* h) {
   e = cudaStreamSynchronize(h->cs_in);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->cs_out);
   if (e != cudaSuccess) return e;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < amr_handle::kSlots; ++k) {
     dfree(h, h->in_slot[k]);
     dfree(h, h->out_slot[k]);
     h->in_slot[k] = h->out_slot[k] = nullptr;
   }
   h->slot_elems = -1;
   const size_t bytes = std::max<int64_t>(h->plan.packed_elems, 1) * sizeof(double);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < amr_handle::kSlots && e == cudaSuccess; ++k) {
     void* p = nullptr;
     e = dmalloc(h, &p, bytes);
     h->in_slot[k] = static_cast<double*>(p);
@@ -357,7 +358,7 @@ cudaError_t ensure_async(amr_handle* h) {
 void release_async(amr_handle* h) {
   if (h->cs_in) cudaStreamSynchronize(h->cs_in);
   if (h->cs_out) cudaStreamSynchronize(h->cs_out);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < amr_handle::kSlots; ++k) {
     dfree(h, h->in_slot[k]);
     dfree(h, h->out_slot[k]);
     h->in_slot[k] = h->out_slot[k] = nullptr;
@@ -1555,7 +1556,7 @@ amr_status amr_set_state_async(amr_handle* h, const double* packed, int state_ki
   if (state_kind != AMR_STATE_CONSERVED && state_kind != AMR_STATE_PRIMITIVE)
     return fail(h, AMR_ERR_ARG, "bad state_kind");
   CK(ensure_async(h));
-  const int k = (int)(h->n_in & 1);
+  const int k = (int)(h->n_in % amr_handle::kSlots);
   CK(cudaStreamWaitEvent(h->cs_in, h->ev_in_used[k], 0));   // the slot's previous conversion is done
   CK(cudaMemcpyAsync(h->in_slot[k], packed, h->plan.packed_elems * sizeof(double), cudaMemcpyHostToDevice,
                      h->cs_in));
@@ -1574,7 +1575,7 @@ amr_status amr_get_state_all_async(amr_handle* h, double* packed, long long* tic
   if (!h || !packed || !ticket) return AMR_ERR_ARG;
   if (!h->ready) return fail(h, AMR_ERR_STATE, "amr_set_patches has not been called");
   CK(ensure_async(h));
-  const int k = (int)(h->n_out & 1);
+  const int k = (int)(h->n_out % amr_handle::kSlots);
   CK(cudaStreamWaitEvent(h->stream, h->ev_d2h[k], 0));   // the slot's previous download is done
   CK(h->ops->pack_out(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->d_packed_off, h->U, h->out_slot[k]));
   CK(cudaEventRecord(h->ev_packout[k], h->stream));
@@ -1591,7 +1592,7 @@ amr_status amr_wait_state(amr_handle* h, long long ticket) {
   if (!h) return AMR_ERR_ARG;
   if (ticket < 0 || ticket >= h->n_out) return fail(h, AMR_ERR_ARG, "unknown ticket");
   // a later download from the same slot completes after this one (one copy stream)
-  CK(cudaEventSynchronize(h->ev_d2h[ticket & 1]));
+  CK(cudaEventSynchronize(h->ev_d2h[ticket % amr_handle::kSlots]));
   return AMR_OK;
 }
 

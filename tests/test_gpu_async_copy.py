@@ -1,8 +1,10 @@
 """Stream-ordered state copies through the C ABI (amr_set_state_async,
 amr_get_state_all_async, amr_wait_state): a pipelined loop whose uploads and
 downloads overlap the steps gives bitwise the states of the synchronous loop,
-with a different input every step (so the two staging slots per direction
-cannot be confused); the slots follow a regrid; unknown tickets are rejected."""
+with a different input every step (so the three staging slots per direction
+cannot be confused), with two or three host input buffers in rotation (the
+loop waits for the download of step k - depth before reusing a buffer); the
+slots follow a regrid; unknown tickets are rejected."""
 import numpy as np
 import pytest
 
@@ -27,13 +29,14 @@ def _pinned(n):
     return torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
 
 
+@pytest.mark.parametrize("depth", [2, 3])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_pipelined_loop_equals_synchronous_loop(precision):
+def test_pipelined_loop_equals_synchronous_loop(precision, depth):
     pb = ai.kelvin_helmholtz(N=32, tile=16)
     s = Solver.from_problem(pb, precision=precision)
     base = s.state_all().copy()
     n = base.size
-    ins = [base * (1.0 + 0.01 * k) for k in range(5)]   # scaled conserved states: same v and e
+    ins = [base * (1.0 + 0.01 * k) for k in range(7)]   # scaled conserved states: same v and e
     dt = 0.5 * s.cfl_dt()
     want = []
     for x in ins:
@@ -42,13 +45,14 @@ def test_pipelined_loop_equals_synchronous_loop(precision):
         out = np.empty(n)
         N.amr_get_state_all(s.h, out)
         want.append(out)
-    h_in = [_pinned(n) for _ in range(2)]
+    h_in = [_pinned(n) for _ in range(depth)]
     h_out = [_pinned(n) for _ in range(len(ins))]
     tickets = []
     for k, x in enumerate(ins):
-        N.amr_wait_state(s.h, tickets[k - 2]) if k >= 2 else None   # the input buffer k-2 is free again
-        h_in[k % 2][:] = x
-        N.amr_set_state_async(s.h, h_in[k % 2])
+        if k >= depth:
+            N.amr_wait_state(s.h, tickets[k - depth])   # the input buffer of step k - depth is free again
+        h_in[k % depth][:] = x
+        N.amr_set_state_async(s.h, h_in[k % depth])
         s.step(dt, sync=False)
         tickets.append(N.amr_get_state_all_async(s.h, h_out[k]))
     for t in tickets:
