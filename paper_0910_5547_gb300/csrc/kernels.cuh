@@ -96,6 +96,72 @@ __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Shared-memory arrays of the stage kernel hold NV variables of S cells.
+// GLM-MHD groups them by G = 16 / sizeof(T) variables: variable v < NG*G of
+// cell c at (v / G) * S * G + c * G + v % G, the remaining NV % G variables one
+// array of S cells each after the groups.  A cell's nine variables then load
+// and store as 16-byte vectors (2 vectors + 1 scalar in FP32), and a
+// quarter-warp of consecutive cells covers all 32 banks even when a warp spans
+// two tile rows.  Euler keeps one array per variable (G = 1; measured no
+// faster grouped).
+template <typename T, int NV>
+__host__ __device__ constexpr int sgroup() {
+  return NV == 9 ? 16 / (int)sizeof(T) : 1;
+}
+template <typename T, int NV, int S>
+__host__ __device__ constexpr int sidx(int v, int c) {
+  constexpr int G = sgroup<T, NV>(), NG = NV / G;
+  return v < NG * G ? (v / G) * S * G + c * G + v % G : NG * G * S + (v - NG * G) * S + c;
+}
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+template <typename T, int NV, int S>
+__device__ __forceinline__ void sload(const T* base, int c, T* out) {
+  constexpr int G = sgroup<T, NV>(), NG = NV / G;
+  if constexpr (G == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = base[v * S + c];
+  } else {
+    using V = typename Vec16<T>::type;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const V x = *reinterpret_cast<const V*>(base + g * S * G + c * G);
+      if constexpr (G == 4) {
+        out[4 * g] = x.x; out[4 * g + 1] = x.y; out[4 * g + 2] = x.z; out[4 * g + 3] = x.w;
+      } else {
+        out[2 * g] = x.x; out[2 * g + 1] = x.y;
+      }
+    }
+#pragma unroll
+    for (int v = NG * G; v < NV; ++v) out[v] = base[NG * G * S + (v - NG * G) * S + c];
+  }
+}
+
+template <typename T, int NV, int S>
+__device__ __forceinline__ void sstore(T* base, int c, const T* in) {
+  constexpr int G = sgroup<T, NV>(), NG = NV / G;
+  if constexpr (G == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) base[v * S + c] = in[v];
+  } else {
+    using V = typename Vec16<T>::type;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      V x;
+      if constexpr (G == 4) {
+        x.x = in[4 * g]; x.y = in[4 * g + 1]; x.z = in[4 * g + 2]; x.w = in[4 * g + 3];
+      } else {
+        x.x = in[2 * g]; x.y = in[2 * g + 1];
+      }
+      *reinterpret_cast<V*>(base + g * S * G + c * G) = x;
+    }
+#pragma unroll
+    for (int v = NG * G; v < NV; ++v) base[NG * G * S + (v - NG * G) * S + c] = in[v];
+  }
+}
+
 struct ChunkDesc {  // a contiguous range of interior cells of one patch
   int patch;
   int begin;
@@ -223,7 +289,6 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     const int wx = it.wx, wy = it.wy, wz = it.wz;
     const int sw = wx + 4;
     const int ncol = wx * wy;
-    constexpr int nfx = kFaceX, nfy = kFaceY;
     T* FY = FX + NV * kFaceX;
     const bool active = t < ncol;
     const int tx = active ? t % wx : 0, ty = active ? t / wx : 0;
@@ -285,10 +350,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       bad |= !cons_to_prim<T, NV>(uD, wB, ph.efl, &floor_hits);   // plane 0: an interior plane
       if (kAsync) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          CR[v * kPlane + me] = uD[v];                                                 // plane 0, slot 0
-          cp_async_elem(&CR[(NV + v) * kPlane + me], Ub + v * vs + col + plane);     // plane 1, slot 1
-        }
+        for (int v = 0; v < NV; ++v)   // plane 1, slot 1
+          cp_async_elem(&CR[NV * kPlane + sidx<T, NV, kPlane>(v, me)], Ub + v * vs + col + plane);
+        sstore<T, NV, kPlane>(CR, me, uD);   // plane 0, slot 0
       } else {
         load_cons<T, NV>(Ub, vs, col + plane, uD);
       }
@@ -300,13 +364,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (has_halo) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          cp_async_elem(&CR[v * kPlane + hpos], Ub + v * vs + hoff);
-          if (wz > 1) cp_async_elem(&CR[(NV + v) * kPlane + hpos], Ub + v * vs + hoff + plane);
+          cp_async_elem(&CR[sidx<T, NV, kPlane>(v, hpos)], Ub + v * vs + hoff);
+          if (wz > 1) cp_async_elem(&CR[NV * kPlane + sidx<T, NV, kPlane>(v, hpos)], Ub + v * vs + hoff + plane);
         }
       }
       cp_async_commit();
     } else if (has_halo) {
-      load_cons<T, NV>(Ub, vs, hoff, hN);
+      if (!kLean) load_cons<T, NV>(Ub, vs, hoff, hN);
     }
 
     // Iteration j runs two phases separated by barriers:
@@ -336,16 +400,17 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         T* slot = CR + (jn & (kRing - 1)) * NV * kPlane;
         if (active && jn <= wz + 1) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlane + me], Ub + v * vs + col + jn * plane);
+          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[sidx<T, NV, kPlane>(v, me)], Ub + v * vs + col + jn * plane);
         }
         if (has_halo && jn < wz) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[v * kPlane + hpos], Ub + v * vs + hoff + jn * plane);
+          for (int v = 0; v < NV; ++v)
+            cp_async_elem(&slot[sidx<T, NV, kPlane>(v, hpos)], Ub + v * vs + hoff + jn * plane);
         }
         if (STAGE == 2 && active && cur) {  // U^n of plane j, used by the update of plane j
-          T* sn = CN + (j & (kRingN - 1)) * NV * NT + t;
+          T* sn = CN + (j & (kRingN - 1)) * NV * NT;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&sn[v * NT], Ob + v * vs + col + j * plane);
+          for (int v = 0; v < NV; ++v) cp_async_elem(&sn[sidx<T, NV, NT>(v, t)], Ob + v * vs + col + j * plane);
         }
         cp_async_commit();
         cp_async_wait1();
@@ -353,23 +418,19 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (has_halo && cur) {
         T w[NV];
         if (kAsync) {
-          const T* slot = CR + (j & (kRing - 1)) * NV * kPlane + hpos;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) hN[v] = slot[v * kPlane];
+          sload<T, NV, kPlane>(CR + (j & (kRing - 1)) * NV * kPlane, hpos, hN);
         }
+        if (kLean) load_cons<T, NV>(Ub, vs, hoff + j * plane, hN);
         cons_to_prim<T, NV>(hN, w, ph.efl);
-        if (!kAsync) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) W[v * kPlane + hpos] = w[v];
+        if (!kAsync && !kLean) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
+        sstore<T, NV, kPlane>(W, hpos, w);
       }
       if (active) {
         // stage input of the own cell, plane j-1 (read earlier: a cache hit; plane -1 is a ghost plane)
         if (!kAsync && !kLean) load_cons<T, NV>(Ub, vs, col + (j - 1) * plane, uin);
         T wC[NV], sB[NV], wl[NV], wr[NV], xl[NV], xr[NV], yl[NV], yr[NV];
         if (kAsync) {
-          const T* slot = CR + ((j + 1) & (kRing - 1)) * NV * kPlane + me;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) uD[v] = slot[v * kPlane];
+          sload<T, NV, kPlane>(CR + ((j + 1) & (kRing - 1)) * NV * kPlane, me, uD);
         }
         int hit = 0;
         const bool ok = cons_to_prim<T, NV>(uD, wC, ph.efl, &hit);   // plane j+1
@@ -387,14 +448,14 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           wl[v] = wA[v] + sc * sA[v];
           wr[v] = wB[v] - sc * sB[v];
           own[v] = wB[v];
-          W[v * kPlane + me] = wB[v];
         }
+        sstore<T, NV, kPlane>(W, me, wB);
         if (kMerge) {
+          sload<T, NV, kState>(XL, xs - 1, xl);
+          sload<T, NV, kState>(YL, ys - wx, yl);
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            xl[v] = XL[v * kState + xs - 1];
             xr[v] = xrOwn[v];
-            yl[v] = YL[v * kState + ys - wx];
             yr[v] = yrOwn[v];
           }
         }
@@ -406,21 +467,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         riemann<T, NV, 2>(wl, wr, ph, Fzp);                  // face j-1/2
         if (kMerge || prev) {
           if (!kMerge) {
+            sload<T, NV, kState>(XL, xs - 1, xl);
+            sload<T, NV, kState>(YL, ys - wx, yl);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              xl[v] = XL[v * kState + xs - 1];
               xr[v] = xrOwn[v];
-              yl[v] = YL[v * kState + ys - wx];
               yr[v] = yrOwn[v];
             }
           }
           riemann<T, NV, 0>(xl, xr, ph, Fx0);                // x face of plane j-1
           riemann<T, NV, 1>(yl, yr, ph, Fy0);                // y face of plane j-1
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            FX[v * nfx + ty * (wx + 1) + tx] = Fx0[v];
-            FY[v * nfy + ty * wx + tx] = Fy0[v];
-          }
+          sstore<T, NV, kFaceX>(FX, ty * (wx + 1) + tx, Fx0);
+          sstore<T, NV, kFaceY>(FY, ty * wx + tx, Fy0);
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -434,26 +492,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       } else if (eb < wy) {  // x face at the right edge of row eb
         T wl[NV], wr[NV], F[NV];
         const int sl = eb * (wx + 2) + wx;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          wl[v] = XL[v * kState + sl];
-          wr[v] = XR[v * kState + sl + 1];
-        }
+        sload<T, NV, kState>(XL, sl, wl);
+        sload<T, NV, kState>(XR, sl + 1, wr);
         riemann<T, NV, 0>(wl, wr, ph, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FX[v * nfx + eb * (wx + 1) + wx] = F[v];
+        sstore<T, NV, kFaceX>(FX, eb * (wx + 1) + wx, F);
       } else if (eb < wy + wx) {  // y face at the top edge of column eb - wy
         const int c = eb - wy;
         T wl[NV], wr[NV], F[NV];
         const int sl = wy * wx + c;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          wl[v] = YL[v * kState + sl];
-          wr[v] = YR[v * kState + sl + wx];
-        }
+        sload<T, NV, kState>(YL, sl, wl);
+        sload<T, NV, kState>(YR, sl + wx, wr);
         riemann<T, NV, 1>(wl, wr, ph, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FY[v * nfy + wy * wx + c] = F[v];
+        sstore<T, NV, kFaceY>(FY, wy * wx + c, F);
       }
       __syncthreads();
       // ---- phase B ----
@@ -464,20 +514,16 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           if (STAGE == 2) load_cons<T, NV>(Ob, vs, c, un);
         }
         if (kAsync) {
-          const T* slot = CR + ((j - 1) & (kRing - 1)) * NV * kPlane + me;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) uin[v] = slot[v * kPlane];
-          if (STAGE == 2) {
-            const T* sn = CN + ((j - 1) & (kRingN - 1)) * NV * NT + t;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) un[v] = sn[v * NT];
-          }
+          sload<T, NV, kPlane>(CR + ((j - 1) & (kRing - 1)) * NV * kPlane, me, uin);
+          if (STAGE == 2) sload<T, NV, NT>(CN + ((j - 1) & (kRingN - 1)) * NV * NT, t, un);
         }
+        T fxp[NV], fyp[NV];
+        sload<T, NV, kFaceX>(FX, ty * (wx + 1) + tx + 1, fxp);
+        sload<T, NV, kFaceY>(FY, (ty + 1) * wx + tx, fyp);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           // u + dt L(u), L = -sum_d (F_{d,+} - F_{d,-}) / dx_d
-          const T u2 = uin[v] - dtx * (FX[v * nfx + ty * (wx + 1) + tx + 1] - Fx0[v]) -
-                       dty * (FY[v * nfy + (ty + 1) * wx + tx] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
+          const T u2 = uin[v] - dtx * (fxp[v] - Fx0[v]) - dty * (fyp[v] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
           if (STAGE == 1) {
             if (prev) Ob[v * vs + c] = u2;
           } else {
@@ -500,27 +546,36 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         for (int v = 0; v < NV; ++v) Fzm[v] = Fzp[v];
       }
       if (active && (kMerge || cur)) {
+        T wm[NV], wp[NV], xs_l[NV], ys_l[NV];
+        sload<T, NV, kPlane>(W, me - 1, wm);
+        sload<T, NV, kPlane>(W, me + 1, wp);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlane + me;
-          const T w0 = own[v];
-          const T sx = limited_slope(Wv[-1], w0, Wv[1], ph.theta);
-          const T sy = limited_slope(Wv[-sw], w0, Wv[sw], ph.theta);
-          XL[v * kState + xs] = w0 + sc * sx;
-          xrOwn[v] = w0 - sc * sx;
-          YL[v * kState + ys] = w0 + sc * sy;
-          yrOwn[v] = w0 - sc * sy;
+          const T sx = limited_slope(wm[v], own[v], wp[v], ph.theta);
+          xs_l[v] = own[v] + sc * sx;
+          xrOwn[v] = own[v] - sc * sx;
         }
+        sstore<T, NV, kState>(XL, xs, xs_l);
+        sload<T, NV, kPlane>(W, me - sw, wm);
+        sload<T, NV, kPlane>(W, me + sw, wp);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T sy = limited_slope(wm[v], own[v], wp[v], ph.theta);
+          ys_l[v] = own[v] + sc * sy;
+          yrOwn[v] = own[v] - sc * sy;
+        }
+        sstore<T, NV, kState>(YL, ys, ys_l);
       }
       if (bkind >= 0 && (kMerge || cur)) {
         T* dst = bkind == 0 ? XL : (bkind == 1 ? XR : (bkind == 2 ? YL : YR));
         const T sgn = (bkind == 0 || bkind == 2) ? sc : -sc;
+        T wm[NV], w0[NV], wp[NV];
+        sload<T, NV, kPlane>(W, bpos - bstep, wm);
+        sload<T, NV, kPlane>(W, bpos, w0);
+        sload<T, NV, kPlane>(W, bpos + bstep, wp);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const T* Wv = W + v * kPlane + bpos;
-          const T w0 = Wv[0];
-          dst[v * kState + bslot] = w0 + sgn * limited_slope(Wv[-bstep], w0, Wv[bstep], ph.theta);
-        }
+        for (int v = 0; v < NV; ++v) w0[v] = w0[v] + sgn * limited_slope(wm[v], w0[v], wp[v], ph.theta);
+        sstore<T, NV, kState>(dst, bslot, w0);
       }
       __syncthreads();
     }
