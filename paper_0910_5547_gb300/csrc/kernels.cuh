@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   T* FX = YR + NV * kState;
   constexpr bool kAsync = stage_async<T, NV, MINB, NT>();
   // 128-thread builds at 3+ CTAs per SM (FP32 MHD, 168 registers) read the stage
-  // input and U^n of the updated cell in phase B instead of carrying register
-  // prefetches through phase A: no spills, latency covered by 12 warps per SM
+  // input and U^n of the updated cell in phase B, and the halo cell when it is
+  // converted, instead of carrying register prefetches through phase A (8-16 B
+  // of spills left); the latency is covered by 12 warps per SM
   constexpr bool kLean = !kAsync && NT == 128 && MINB >= 3;
   // ring of stage-input planes: plane p of the item lives in slot p & 3, [slot][var][plane cell];
   // ring of U^n planes (stage 2): plane p in slot p & 1, [slot][var][thread].  Each thread
