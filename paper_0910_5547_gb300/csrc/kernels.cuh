@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           own[v] = wB[v];
         }
         sstore<T, NV, kPlane>(W, me, wB);
-        if (kMerge) {
+        {   // own x/y face states of plane j-1 (read at j = 0 too: in bounds, unused)
           sload<T, NV, kState>(XL, xs - 1, xl);
           sload<T, NV, kState>(YL, ys - wx, yl);
 #pragma unroll
@@ -467,15 +467,6 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         }
         riemann<T, NV, 2>(wl, wr, ph, Fzp);                  // face j-1/2
         if (kMerge || prev) {
-          if (!kMerge) {
-            sload<T, NV, kState>(XL, xs - 1, xl);
-            sload<T, NV, kState>(YL, ys - wx, yl);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              xr[v] = xrOwn[v];
-              yr[v] = yrOwn[v];
-            }
-          }
           riemann<T, NV, 0>(xl, xr, ph, Fx0);                // x face of plane j-1
           riemann<T, NV, 1>(yl, yr, ph, Fy0);                // y face of plane j-1
           sstore<T, NV, kFaceX>(FX, ty * (wx + 1) + tx, Fx0);
