@@ -63,13 +63,10 @@ def aggregate(elapsed: float, units_per_rank: float, dist=None, device=None):
 
 
 def stage_source_sha() -> str:
-    """Hash of the stage kernel's source: its body in kernels.cuh plus physics.cuh and amr_types.h."""
+    """Hash of the stage kernel's source: kernels.cuh (all of it), physics.cuh and amr_types.h."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_0910_5547_gb300", "csrc")
-    k = open(os.path.join(csrc, "kernels.cuh")).read()
-    a = k.index("template <typename T, int NV, int STAGE")
-    b = k.index("// ----", a)
-    src = k[a:b] + open(os.path.join(csrc, "physics.cuh")).read() + open(os.path.join(csrc, "amr_types.h")).read()
+    src = "".join(open(os.path.join(csrc, f)).read() for f in ("kernels.cuh", "physics.cuh", "amr_types.h"))
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
