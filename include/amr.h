@@ -208,8 +208,8 @@ amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, 
 amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, int ctas_per_sm);
 
 /* Autotuner: time the stage kernel over the installed hierarchy for each
- * candidate work-item shape (x width, columns per CTA, z chunk) and register
- * budget (2 or 3 resident CTAs per SM for FP32 Euler) and keep the fastest for
+ * candidate work-item shape (x width, columns per CTA, z chunk) and compiled
+ * build (resident CTAs per SM, as listed at amr_set_tiling) and keep the fastest for
  * this handle (also for later amr_set_patches / amr_regrid).  The state is not
  * modified (only the stage-1 scratch array is written).  report (may be NULL)
  * receives one line per candidate with its time.  Synchronises; invalidates
