@@ -36,6 +36,7 @@ _lock = threading.Lock()
 _lib = None
 
 HLL, LLF, FLUXREC = 0, 1, 2
+PLM, WENO3 = 0, 1
 OUTFLOW, PERIODIC = 0, 1
 
 
@@ -56,6 +57,7 @@ class OrcConfig(ctypes.Structure):
         ("p_floor", ctypes.c_double),
         ("glm_alpha", ctypes.c_double),
         ("nthreads", ctypes.c_int),
+        ("recon", ctypes.c_int),
     ]
 
 
@@ -112,6 +114,7 @@ def lib():
             L.orc_minmod2.argtypes = [ctypes.c_double] * 2
             L.orc_minmod2.restype = ctypes.c_double
             L.orc_plm_face.argtypes = [cp, dp, dp, dp]
+            L.orc_weno3_face.argtypes = [dp, dp, dp]
             L.orc_phys_flux.argtypes = [cp, dp, ctypes.c_int, ctypes.c_double, dp]
             L.orc_prim_to_cons.argtypes = [cp, dp, dp]
             L.orc_cons_to_prim.argtypes = [cp, dp, dp]
@@ -127,7 +130,7 @@ def _dp(a: np.ndarray):
 
 def make_config(nvar=5, gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(OUTFLOW,) * 6,
                 riemann=HLL, plm_literal=False, max_level=0, ch=0.0, domain_lo=(0.0, 0.0, 0.0),
-                domain_hi=(1.0, 1.0, 1.0), nthreads=0, p_floor=0.0, glm_alpha=0.0) -> OrcConfig:
+                domain_hi=(1.0, 1.0, 1.0), nthreads=0, p_floor=0.0, glm_alpha=0.0, recon=PLM) -> OrcConfig:
     c = OrcConfig()
     c.nvar, c.riemann, c.plm_literal = nvar, riemann, int(plm_literal)
     c.gamma, c.theta, c.cfl = gamma, theta, cfl
@@ -137,6 +140,7 @@ def make_config(nvar=5, gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(
     c.bc[:] = list(bc)
     c.max_level, c.ch, c.nthreads = max_level, ch, nthreads
     c.p_floor, c.glm_alpha = p_floor, glm_alpha
+    c.recon = recon
     return c
 
 
@@ -267,6 +271,14 @@ def plm_face(u4: Sequence[float], theta=1.5, plm_literal=False):
     u = np.ascontiguousarray(u4, dtype=np.float64)
     ul, ur = np.zeros(1), np.zeros(1)
     lib().orc_plm_face(ctypes.byref(cfg), _dp(u), _dp(ul), _dp(ur))
+    return float(ul[0]), float(ur[0])
+
+
+def weno3_face(u4: Sequence[float]):
+    """Third-order WENO states (left, right) of the face between u4[1] and u4[2]."""
+    u = np.ascontiguousarray(u4, dtype=np.float64)
+    ul, ur = np.zeros(1), np.zeros(1)
+    lib().orc_weno3_face(_dp(u), _dp(ul), _dp(ur))
     return float(ul[0]), float(ur[0])
 
 

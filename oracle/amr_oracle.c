@@ -64,6 +64,27 @@ void orc_plm_face(const orc_config* cfg, const double* u, double* ul, double* ur
   *ur = u[2] + h * orc_minmod3((u[2] - u[3]) * th, (u[1] - u[2]) * th, (u[1] - u[3]) / 2.0);
 }
 
+/* Third-order WENO (Jiang and Shu 1996, r = 2) value at the face between
+ * cells b and c, taken from the side of cell b, with a the cell beyond b:
+ * the two linear candidates through (a, b) and (b, c), q0 = (3b - a)/2 and
+ * q1 = (b + c)/2, have the linear weights 1/3 and 2/3 (their blend is the
+ * third-order value (-a + 5b + 2c)/6), replaced by the nonlinear weights
+ * w_k proportional to d_k / (eps + beta_k)^2 with the smoothness indicators
+ * beta0 = (b - a)^2, beta1 = (c - b)^2 and eps = 1e-6. */
+static double weno3_side(double a, double b, double c) {
+  const double eps = 1e-6;
+  const double q0 = 1.5 * b - 0.5 * a, q1 = 0.5 * (b + c);
+  const double b0 = (b - a) * (b - a), b1 = (c - b) * (c - b);
+  const double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+  const double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+  return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+void orc_weno3_face(const double* u, double* ul, double* ur) {
+  *ul = weno3_side(u[0], u[1], u[2]);   /* right face of cell i-1 */
+  *ur = weno3_side(u[3], u[2], u[1]);   /* left face of cell i (mirror image) */
+}
+
 /* Reconstructed variables R = (rho, vx, vy, vz, e, Bx, By, Bz, psi), e the
  * specific internal energy (the listing of Sec. 5.1 loads Rho, Eint, Vx, Vy, Vz). */
 static void cons_to_rec(const orc_config* c, const double* u, double* r) {
@@ -409,6 +430,10 @@ orc_sim* orc_create(const orc_config* cfg, int npatch, const orc_patch* patches)
     snprintf(g_err, sizeof g_err, "riemann must be HLL, LLF or FLUXREC (Euler only)");
     return NULL;
   }
+  if ((cfg->recon != ORC_PLM && cfg->recon != ORC_WENO3) || (cfg->recon == ORC_WENO3 && cfg->riemann == ORC_FLUXREC)) {
+    snprintf(g_err, sizeof g_err, "recon must be PLM or WENO3 (WENO3 with HLL or LLF)");
+    return NULL;
+  }
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->cfg = *cfg;
   s->V = cfg->nvar;
@@ -679,7 +704,8 @@ static void patch_fluxes(orc_sim* s, opatch* p, const double* X, double ch) {
           }
           for (int v = 0; v < V; ++v) {
             for (int c = 0; c < 4; ++c) col[c] = r4[c][v];
-            orc_plm_face(&s->cfg, col, &rl[v], &rr[v]);
+            if (s->cfg.recon == ORC_WENO3) orc_weno3_face(col, &rl[v], &rr[v]);
+            else orc_plm_face(&s->cfg, col, &rl[v], &rr[v]);
           }
           riemann_rec(&s->cfg, rl, rr, d, ch, Ftmp);
           size_t fi = fidx(p, d, i, j, k);

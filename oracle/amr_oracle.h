@@ -25,6 +25,7 @@ extern "C" {
 #endif
 
 enum { ORC_HLL = 0, ORC_LLF = 1, ORC_FLUXREC = 2 };
+enum { ORC_PLM = 0, ORC_WENO3 = 1 };
 enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1 };
 
 typedef struct {
@@ -43,6 +44,9 @@ typedef struct {
   double p_floor;     /* pressure floor of the reconstructed variables (0 = off): e >= p_floor / ((gamma-1) rho) */
   double glm_alpha;   /* GLM damping: psi *= exp(-glm_alpha c_h dt_l / min_d dx_l) after every level step (0 = off) */
   int nthreads;       /* OpenMP threads over patches; <= 0: library default */
+  int recon;          /* face states: ORC_PLM (Sec. 4) or ORC_WENO3 (third-order WENO on the same
+                         three-cell stencils, a higher-order scheme in the sense of the abstract);
+                         ORC_WENO3 with ORC_HLL or ORC_LLF only */
 } orc_config;
 
 typedef struct { int level; int lo[3]; int n[3]; } orc_patch;
@@ -124,6 +128,8 @@ void orc_prim_to_cons(const orc_config* cfg, const double* w, double* u);
 void orc_cons_to_prim(const orc_config* cfg, const double* u, double* w);
 /* Interface flux from primitive left/right states along dir. */
 void orc_riemann(const orc_config* cfg, const double* wl, const double* wr, int dir, double ch, double* f);
+/* Third-order WENO face states of face i-1/2 from u4 = (u_{i-2}, u_{i-1}, u_i, u_{i+1}). */
+void orc_weno3_face(const double* u, double* ul, double* ur);
 /* Direct flux reconstruction at the face between cells 1 and 2 of four conserved
  * states u4[4][nvar] along dir (Euler): Lax-Friedrichs split fluxes, each
  * reconstructed by PLM from its upwind side. */
