@@ -55,6 +55,7 @@ typedef enum {
 
 enum { AMR_FP64 = 0, AMR_FP32 = 1 };                 /* bulk precision of state and arithmetic */
 enum { AMR_HLL = 0, AMR_LLF = 1, AMR_FLUXREC = 2 };   /* interface flux */
+enum { AMR_PLM = 0, AMR_WENO3 = 1 };                  /* face states */
 enum { AMR_BC_OUTFLOW = 0, AMR_BC_PERIODIC = 1 };     /* per domain face */
 enum { AMR_STATE_CONSERVED = 0, AMR_STATE_PRIMITIVE = 1 };
 
@@ -88,6 +89,11 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* stream, void* alloc_ctx);
   void (*dev_free)(void* ptr, void* stream, void* alloc_ctx);
   void* alloc_ctx;
+  int recon;             /* face states of the reconstructed variables: AMR_PLM (Sec. 4, default) or
+                            AMR_WENO3 (third-order WENO, Jiang-Shu r = 2, on the same three-cell
+                            stencils: the abstract's higher-order shock-capturing extension); AMR_WENO3
+                            needs AMR_HLL or AMR_LLF and runs the default stage-kernel build (the
+                            tiling's ctas_per_sm does not apply); amr_step_patch_noalloc: AMR_PLM only */
 } amr_config;
 
 /* One patch: `n` interior cells per axis starting at `lo` in the index space of
@@ -347,7 +353,8 @@ void amr_destroy(amr_handle* h);
  * their contents in it: calls that overlap on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  Work is ordered on
  * cfg->cuda_stream (NULL: the legacy default stream).  AMR_ERR_ARG for a bad
- * config or pointer, AMR_ERR_CUDA if a launch or copy fails. */
+ * config or pointer (and for recon = AMR_WENO3), AMR_ERR_CUDA if a launch or
+ * copy fails. */
 amr_status amr_step_patch_noalloc(const amr_config* cfg, const double* state_in, double* state_out, double dt,
                                   double* dt_used);
 

@@ -406,7 +406,7 @@ void free_device(amr_handle* h) {
 
 OpsBase* make_ops(const amr_config& c) {
   PhysParams p{c.gamma, c.theta, c.ch, c.riemann == AMR_LLF ? 1 : 0, c.p_floor, c.glm_alpha,
-               c.riemann == AMR_FLUXREC ? 1 : 0};
+               c.riemann == AMR_FLUXREC ? 1 : 0, c.recon == AMR_WENO3 ? 1 : 0};
   if (c.nvar == 5) return c.precision == AMR_FP32 ? make_ops_f32_euler(p) : make_ops_f64_euler(p);
   return c.precision == AMR_FP32 ? make_ops_f32_mhd(p) : make_ops_f64_mhd(p);
 }
@@ -1149,6 +1149,7 @@ void amr_default_config(amr_config* c) {
   c->batched = 1;
   c->use_graph = 1;
   c->cuda_stream = nullptr;
+  c->recon = AMR_PLM;
 }
 
 const char* amr_global_error(void) { return g_global_err.c_str(); }

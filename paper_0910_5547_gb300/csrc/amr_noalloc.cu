@@ -197,6 +197,7 @@ extern "C" amr_status amr_step_patch_noalloc(const amr_config* cfg, const double
   if (!cfg || !state_in || !state_out || !std::isfinite(dt)) return AMR_ERR_ARG;
   std::string msg;
   if (validate_config(*cfg, msg) != AMR_OK) return AMR_ERR_ARG;
+  if (cfg->recon != AMR_PLM) return AMR_ERR_ARG;   // the WENO3 build is not compiled into this path
   std::vector<HPatch> P(1);
   P[0].level = 0;
   for (int d = 0; d < 3; ++d) {

@@ -349,6 +349,11 @@ amr_status validate_config(const amr_config& c, std::string& msg) {
     return AMR_ERR_ARG;
   }
   if (c.riemann == AMR_FLUXREC && c.nvar != 5) { msg = "AMR_FLUXREC is for the Euler system (nvar 5)"; return AMR_ERR_ARG; }
+  if (c.recon != AMR_PLM && c.recon != AMR_WENO3) { msg = "recon must be AMR_PLM or AMR_WENO3"; return AMR_ERR_ARG; }
+  if (c.recon == AMR_WENO3 && c.riemann == AMR_FLUXREC) {
+    msg = "AMR_WENO3 reconstructs the states of an AMR_HLL / AMR_LLF solve, not split fluxes";
+    return AMR_ERR_ARG;
+  }
   if (!(c.gamma > 1.0) || !std::isfinite(c.gamma)) { msg = "gamma must be > 1"; return AMR_ERR_ARG; }
   if (!(c.theta >= 0.0 && c.theta <= 2.0)) { msg = "theta must lie in [0, 2]"; return AMR_ERR_ARG; }
   if (!(c.cfl > 0.0 && c.cfl <= 1.0)) { msg = "cfl must lie in (0, 1]"; return AMR_ERR_ARG; }

@@ -245,7 +245,8 @@ __device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, 
 // (each solved once); the update differences the fluxes of the cell's six
 // faces.  The work of plane j is skewed against that of plane j-1 so that
 // one plane costs two barriers.
-template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1, int NT = kStageThreads>
+template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1, int NT = kStageThreads,
+          bool WENO = false>
 __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kPlane = StageDims<NT>::plane, kState = StageDims<NT>::state;
@@ -359,7 +360,14 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       }
       if (STAGE == 2 && !kAsync && !kLean) load_cons<T, NV>(Ob, vs, col, unN);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sA[v] = limited_slope(w0[v], wA[v], wB[v], ph.theta);
+      for (int v = 0; v < NV; ++v) {
+        if constexpr (WENO) {
+          T dm;
+          weno3_offsets(w0[v], wA[v], wB[v], sA[v], dm);   // sA: offset of the upper face
+        } else {
+          sA[v] = limited_slope(w0[v], wA[v], wB[v], ph.theta);
+        }
+      }
     }
     if (kAsync) {
       if (has_halo) {
@@ -445,9 +453,16 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          sB[v] = limited_slope(wA[v], wB[v], wC[v], ph.theta);
-          wl[v] = wA[v] + sc * sA[v];
-          wr[v] = wB[v] - sc * sB[v];
+          if constexpr (WENO) {
+            T dm;
+            weno3_offsets(wA[v], wB[v], wC[v], sB[v], dm);
+            wl[v] = wA[v] + sA[v];
+            wr[v] = wB[v] - dm;
+          } else {
+            sB[v] = limited_slope(wA[v], wB[v], wC[v], ph.theta);
+            wl[v] = wA[v] + sc * sA[v];
+            wr[v] = wB[v] - sc * sB[v];
+          }
           own[v] = wB[v];
         }
         sstore<T, NV, kPlane>(W, me, wB);
@@ -543,18 +558,32 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         sload<T, NV, kPlane>(W, me + 1, wp);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T sx = limited_slope(wm[v], own[v], wp[v], ph.theta);
-          xs_l[v] = own[v] + sc * sx;
-          xrOwn[v] = own[v] - sc * sx;
+          if constexpr (WENO) {
+            T dp, dm;
+            weno3_offsets(wm[v], own[v], wp[v], dp, dm);
+            xs_l[v] = own[v] + dp;
+            xrOwn[v] = own[v] - dm;
+          } else {
+            const T sx = limited_slope(wm[v], own[v], wp[v], ph.theta);
+            xs_l[v] = own[v] + sc * sx;
+            xrOwn[v] = own[v] - sc * sx;
+          }
         }
         sstore<T, NV, kState>(XL, xs, xs_l);
         sload<T, NV, kPlane>(W, me - sw, wm);
         sload<T, NV, kPlane>(W, me + sw, wp);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T sy = limited_slope(wm[v], own[v], wp[v], ph.theta);
-          ys_l[v] = own[v] + sc * sy;
-          yrOwn[v] = own[v] - sc * sy;
+          if constexpr (WENO) {
+            T dp, dm;
+            weno3_offsets(wm[v], own[v], wp[v], dp, dm);
+            ys_l[v] = own[v] + dp;
+            yrOwn[v] = own[v] - dm;
+          } else {
+            const T sy = limited_slope(wm[v], own[v], wp[v], ph.theta);
+            ys_l[v] = own[v] + sc * sy;
+            yrOwn[v] = own[v] - sc * sy;
+          }
         }
         sstore<T, NV, kState>(YL, ys, ys_l);
       }
@@ -566,7 +595,15 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         sload<T, NV, kPlane>(W, bpos, w0);
         sload<T, NV, kPlane>(W, bpos + bstep, wp);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) w0[v] = w0[v] + sgn * limited_slope(wm[v], w0[v], wp[v], ph.theta);
+        for (int v = 0; v < NV; ++v) {
+          if constexpr (WENO) {   // XL / YL: the face toward wp; XR / YR: toward wm
+            T dp, dm;
+            weno3_offsets(wm[v], w0[v], wp[v], dp, dm);
+            w0[v] = (bkind == 0 || bkind == 2) ? w0[v] + dp : w0[v] - dm;
+          } else {
+            w0[v] = w0[v] + sgn * limited_slope(wm[v], w0[v], wp[v], ph.theta);
+          }
+        }
         sstore<T, NV, kState>(dst, bslot, w0);
       }
       __syncthreads();

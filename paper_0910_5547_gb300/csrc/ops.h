@@ -17,6 +17,7 @@ struct PhysParams {  // host copy of the physics constants
   int llf;
   double p_floor, glm_alpha;
   int fluxrec;
+  int weno;   // third-order WENO face states (the default build only)
 };
 
 struct OpsBase {

@@ -11,6 +11,7 @@ struct Ops final : OpsBase {
   Phys<T> ph{};
   double gamma = 1.4;
   int occ = 0;   // 0: default build; kAlt: the alternate register budget
+  bool weno = false;   // third-order WENO face states: the default build with WENO = true
   // default resident CTAs per SM of the stage kernel, and the alternate build
   // (FP32 Euler: 2 -> 3; FP32 MHD and FP64 Euler: 1 -> 2; FP64 MHD: none)
   static constexpr int kDef = (sizeof(T) == 4 && NV == 5) ? 2 : 1;
@@ -29,6 +30,8 @@ struct Ops final : OpsBase {
     ph.theta = (T)p.theta;
     ph.llf = p.llf;
     ph.fluxrec = NV == 5 ? p.fluxrec : 0;
+    weno = p.weno != 0;
+    ph.weno = p.weno != 0 ? 1 : 0;
     ph.ch = ph.ch2 = ph.half_inv_ch = T(0);
     ph.efl = (T)(p.p_floor / (p.gamma - 1.0));
     ph.glm_alpha = (T)p.glm_alpha;
@@ -46,6 +49,10 @@ struct Ops final : OpsBase {
       cudaFuncSetAttribute(stage_kernel<T, NV, 2, kAlt128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)stage_smem_bytes<T, NV, kAlt128, 128>());
     }
+    cudaFuncSetAttribute(stage_kernel<T, NV, 1, kDef, kStageThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV, kDef>());
+    cudaFuncSetAttribute(stage_kernel<T, NV, 2, kDef, kStageThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem_bytes<T, NV, kDef>());
     if (kHasAlt) {
       cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)stage_smem_bytes<T, NV, kAlt>());
@@ -93,6 +100,12 @@ struct Ops final : OpsBase {
         else fluxrec_stage_kernel<T, 2><<<g, kStageThreads, 0, s>>>(a);
         return cudaGetLastError();
       }
+    }
+    if (weno) {   // any tiling's items fit the 256-thread CTA
+      const size_t sm = stage_smem_bytes<T, NV, kDef>();
+      if (stage == 1) stage_kernel<T, NV, 1, kDef, kStageThreads, true><<<g, kStageThreads, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, kDef, kStageThreads, true><<<g, kStageThreads, sm, s>>>(a);
+      return cudaGetLastError();
     }
     if constexpr (kAlt128 > 0) {
       if (nt == 128 && occ == kAlt) {

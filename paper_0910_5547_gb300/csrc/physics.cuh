@@ -23,6 +23,7 @@ struct Phys {
   int fluxrec; // 1: direct flux reconstruction (Euler; replaces the Riemann solve)
   T efl;       // p_floor / (gamma - 1): the specific internal energy floor is efl / rho
   T glm_alpha; // GLM damping parameter (0 = off)
+  int weno;    // 1: third-order WENO face states (flux-register faces; the stage kernel has its own build)
 };
 
 template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
@@ -158,6 +159,26 @@ __device__ __forceinline__ void state_flux(const T* w, const Phys<T>& ph, T* U, 
     F[5] = vn * Bx - vx * Bn; F[6] = vn * By - vy * Bn; F[7] = vn * Bz - vz * Bn;
     F[8] = T(0);
   }
+}
+
+// Third-order WENO face states (Jiang and Shu, r = 2; the higher-order scheme
+// the abstract says the framework extends to) on the PLM stencil of a cell w0
+// with neighbours wm, wp: the face toward wp is w0 + dp, the face toward wm is
+// w0 - dm.  Each blends the half differences dl = w0 - wm and dr = wp - w0
+// with linear weights 1/3 (the difference away from the face) and 2/3 (toward
+// it), turned into nonlinear weights by (eps + d^2)^-2, eps = 1e-6.  The weight
+// is formed from the ratio of the two indicators, so large jumps send it to its
+// limit instead of overflowing.
+template <typename T>
+__device__ __forceinline__ void weno3_offsets(T wm, T w0, T wp, T& dp, T& dm) {
+  const T eps = T(1e-6);
+  const T dl = w0 - wm, dr = wp - w0;
+  const T gl = eps + dl * dl, gr = eps + dr * dr;
+  const T ql = gr * drcp(gl), qr = gl * drcp(gr);
+  const T wr_p = T(2) * drcp(T(2) + ql * ql);   // weight of dr at the face toward wp
+  const T wl_m = T(2) * drcp(T(2) + qr * qr);   // weight of dl at the face toward wm
+  dp = T(0.5) * (dl + wr_p * (dr - dl));
+  dm = T(0.5) * (dr + wl_m * (dl - dr));
 }
 
 // Interface flux along D from reconstructed left/right states (copied: the MHD
@@ -376,8 +397,16 @@ __device__ __forceinline__ void face_flux_from_array(const T* base, int64_t vstr
   T wl[NV], wr[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    wl[v] = w[1][v] + half_slope(w[0][v], w[1][v], w[2][v], ph.theta);
-    wr[v] = w[2][v] - half_slope(w[1][v], w[2][v], w[3][v], ph.theta);
+    if (ph.weno) {
+      T dp, dm;
+      weno3_offsets(w[0][v], w[1][v], w[2][v], dp, dm);
+      wl[v] = w[1][v] + dp;
+      weno3_offsets(w[1][v], w[2][v], w[3][v], dp, dm);
+      wr[v] = w[2][v] - dm;
+    } else {
+      wl[v] = w[1][v] + half_slope(w[0][v], w[1][v], w[2][v], ph.theta);
+      wr[v] = w[2][v] - half_slope(w[1][v], w[2][v], w[3][v], ph.theta);
+    }
   }
   riemann<T, NV, D>(wl, wr, ph, F);
 }

@@ -24,6 +24,7 @@ AMR_ERR_TIMEOUT = -5
 AMR_ERR_STATE = -6
 AMR_FP64, AMR_FP32 = 0, 1
 AMR_HLL, AMR_LLF, AMR_FLUXREC = 0, 1, 2
+AMR_PLM, AMR_WENO3 = 0, 1
 AMR_BC_OUTFLOW, AMR_BC_PERIODIC = 0, 1
 AMR_STATE_CONSERVED, AMR_STATE_PRIMITIVE = 0, 1
 
@@ -77,6 +78,7 @@ class amr_config(ctypes.Structure):
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
+        ("recon", ctypes.c_int),
     ]
 
 

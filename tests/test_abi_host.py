@@ -95,7 +95,7 @@ def test_periodic_nesting_wraps_around_the_domain():
 
 
 @pytest.mark.parametrize("field,value", [("nvar", 7), ("precision", 3), ("gamma", 1.0), ("theta", 2.5),
-                                         ("cfl", 0.0), ("ref_ratio", 4), ("max_level", 13)])
+                                         ("cfl", 0.0), ("ref_ratio", 4), ("max_level", 13), ("recon", 2)])
 def test_bad_config_is_rejected(field, value):
     c = cfg(**{field: value})
     st, msg = N.amr_validate_patches(c, [P(0, (0, 0, 0), (32, 32, 32))])
@@ -108,6 +108,15 @@ def test_flux_reconstruction_is_euler_only():
     st, msg = N.amr_validate_patches(cfg(riemann=N.AMR_FLUXREC, nvar=9), one)
     assert st == N.AMR_ERR_ARG and "FLUXREC" in msg
     assert N.amr_validate_patches(cfg(riemann=3), one)[0] == N.AMR_ERR_ARG
+
+
+def test_weno3_needs_a_riemann_solve():
+    one = [P(0, (0, 0, 0), (32, 32, 32))]
+    for nvar in (5, 9):
+        for r in (N.AMR_HLL, N.AMR_LLF):
+            assert N.amr_validate_patches(cfg(recon=N.AMR_WENO3, riemann=r, nvar=nvar), one)[0] == N.AMR_OK
+    st, msg = N.amr_validate_patches(cfg(recon=N.AMR_WENO3, riemann=N.AMR_FLUXREC), one)
+    assert st == N.AMR_ERR_ARG and "WENO3" in msg
 
 
 def test_unpaired_periodic_faces_rejected():
