@@ -316,7 +316,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--only", default="",
-                    help="comma list of phases: fp32,tiled,fp64,fluxrec,plain,e2e,amr,amr32,mhd,adaptive (default: "
+                    help="comma list of phases: fp32,tiled,fp64,fluxrec,weno3,plain,e2e,amr,amr32,mhd,adaptive (default: "
                          "all but amr32)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -342,7 +342,7 @@ def main():
 
     import amr_inputs as ai
     phases = set(args.only.split(",")) if args.only else {"fp32", "tiled", "fp64", "plain", "e2e", "amr", "mhd",
-                                                          "fluxrec",
+                                                          "fluxrec", "weno3",
                                                           "adaptive"}
     single = ai.kelvin_helmholtz(N=N, tile=None)          # one 256^3 patch
     tiled = ai.kelvin_helmholtz(N=N, tile=TILE) if phases & {"tiled", "plain"} else None
@@ -458,6 +458,29 @@ def main():
     if "fp64" in phases:
         extra["fp64_batched"] = {"value": rate(single, "fp64", True, True, k64), "unit": UNIT, "steps": k64,
                                  "workload": "single 256^3 patch, batched + graph"}
+    if "weno3" in phases:
+        # third-order WENO face states (recon = weno3) on the same single 256^3 patch
+        so = make_solver(single, "fp32", True, True, stream, recon="weno3")
+        so.autotune()
+        for _ in range(2):
+            so.step(0.0, sync=False)
+        kw3 = max(3, sub // 4)
+        tw3 = timed_steps(torch, so, stream, kw3)
+        NV.amr_set_timing(so.h, True)
+        for _ in range(ksteps):
+            so.step(0.0, sync=False)
+        tmw = NV.amr_get_timing(so.h)
+        NV.amr_set_timing(so.h, False)
+        so.check()
+        so.close()
+        tsw = (tmw["stage1"][0] + tmw["stage2"][0]) / ksteps
+        extra["weno3_fp32"] = {
+            "value": ws * cells * kw3 / max_over_ranks(tw3), "unit": UNIT, "steps": kw3,
+            "stage_ms": {"stage1": round(tmw["stage1"][0] / ksteps, 4), "stage2": round(tmw["stage2"][0] / ksteps, 4)},
+            "stage_hbm_frac": stage_bytes / (tsw / 1e3) / 1e9 / peak,
+            "workload": "Kelvin-Helmholtz 256^3 single patch, FP32, HLL on third-order WENO face states "
+                        "(recon=weno3), batched + graph"}
+
     if "fluxrec" in phases:
         # the direct flux reconstruction variant (Sec. 4's second class of schemes) on the
         # same single 256^3 patch: rate with graph replay, stage-kernel event times
