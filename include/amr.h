@@ -234,18 +234,29 @@ amr_status amr_set_state(amr_handle* h, const double* packed, int state_kind);
 /* Number of doubles in the packed state (sum over patches of nvar * cells). */
 long long amr_state_size(const amr_handle* h);
 
-/* Advance one coarse step.  dt > 0: use it; dt <= 0: CFL step from the current
- * state, dt0 = cfl / max over all cells of sum_d (|v_d| + c_d) / dx0_d (level
- * l uses dt0 / 2^l).  If dt_used is not NULL the call synchronises and stores
- * the step taken and reports device-detected non-physical states; with
- * dt_used == NULL the step is only enqueued. */
+/* Advance one coarse step: the Berger-Colella level recursion of Sec. 3 (each
+ * level l >= 1 takes two sub-steps per parent step, then restriction and
+ * refluxing of its parent's cells), every level step being the Sec. 5.1
+ * three-line RK2 form U1 = U + dt L(U), U2 = U1 + dt L(U1), U = U/2 + U2/2 of
+ * the Sec. 4 method of lines, L(U) the flux difference of the PLM face states
+ * and the HLL (or LLF) flux of Sec. 4 (Sec. 7.1 for GLM-MHD), face ghosts
+ * refilled before each stage.  dt > 0: use it; dt <= 0: CFL step from the
+ * current state, dt0 = cfl / max over all cells of sum_d (|v_d| + c_d) / dx0_d
+ * (level l uses dt0 / 2^l; the paper states no CFL rule).  If dt_used is not
+ * NULL the call synchronises and stores the step taken and reports
+ * device-detected non-physical states (AMR_ERR_NONPHYSICAL); with dt_used ==
+ * NULL the step is only enqueued.  AMR_ERR_STATE before amr_set_patches,
+ * AMR_ERR_CUDA if a launch fails. */
 amr_status amr_step(amr_handle* h, double dt, double* dt_used);
 
 /* CFL step of the current state (synchronises). */
 amr_status amr_cfl_dt(amr_handle* h, double* dt);
 
-/* Copy patch `patch`'s interior conserved state, FP64 [nvar][n2][n1][n0], to
- * the caller's host buffer.  Synchronises. */
+/* Copy patch `patch`'s interior conserved state U of Sec. 4 (Sec. 7.1 for
+ * GLM-MHD: rho, rho v, rho E + B^2/2, B, psi), FP64 [nvar][n2][n1][n0], to the
+ * caller's host buffer (nvar * n0 * n1 * n2 doubles, caller-owned); an FP32
+ * state is widened exactly.  Synchronises.  AMR_ERR_ARG for a bad patch index
+ * or NULL out, AMR_ERR_STATE before amr_set_patches. */
 amr_status amr_get_state(amr_handle* h, int patch, double* out);
 
 /* Copy all patches' conserved state into one packed host buffer (layout as in
@@ -271,8 +282,11 @@ amr_status amr_get_state_all_async(amr_handle* h, double* packed, long long* tic
  * a ticket this handle did not issue. */
 amr_status amr_wait_state(amr_handle* h, long long ticket);
 
-/* out[nvar]: sum over leaf cells (not covered by a finer patch) of U * cell
- * volume, accumulated in FP64 in a fixed order.  Synchronises. */
+/* out[nvar] (caller-owned): sum over leaf cells (not covered by a finer patch)
+ * of U * cell volume, the integrals of the Sec. 4 conservation law U_t + div F
+ * = 0 that a conservative update with refluxing (Sec. 3) keeps constant up to
+ * boundary fluxes; accumulated in FP64 in a fixed order whatever the bulk
+ * precision.  Synchronises.  AMR_ERR_STATE before amr_set_patches. */
 amr_status amr_conserved_totals(amr_handle* h, double* out);
 
 /* GLM-MHD diagnostic of the divergence constraint that psi controls (Sec. 7.1;
@@ -338,7 +352,8 @@ void amr_destroy(amr_handle* h);
  * device-memory budget fixed at start-up).  The paper has no counterpart: it
  * is a deployment variant of amr_step, with the same kernels.
  *   state_in, state_out: DEVICE arrays owned by the caller, FP64 conserved
- *     variables [nvar][n2][n1][n0] (interior cells, x fastest); may not alias.
+ *     variables [nvar][n2][n1][n0] (interior cells, x fastest); the two ranges
+ *     may not overlap (AMR_ERR_ARG if they do).
  *   dt > 0: step size; dt <= 0: CFL step of state_in.
  *   dt_used: NULL (no synchronisation) or a host pointer that receives the
  *     step taken; the call then synchronises cfg->cuda_stream and reports
