@@ -10,3 +10,13 @@ for p in (ROOT, os.path.join(ROOT, "tests")):
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Worst parity errors of the session (vector and per-variable metrics)."""
+    try:
+        import parity
+    except ImportError:
+        return
+    for line in parity.summary_lines():
+        terminalreporter.write_line(line)

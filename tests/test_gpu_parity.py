@@ -96,6 +96,11 @@ def test_two_level_amr(precision, bc):
 def test_three_level_amr_parity_and_conservation(precision):
     pb = ai.random_smooth(three_level_seeded(), (32,) * 3, seed=5, amp=0.2)
     t0 = Solver.from_problem(pb, precision=precision).totals()
+    # the GPU's initial totals (its own primitive -> conserved conversion) against the oracle's;
+    # the oracle adds the cells one after another (error bound (N-1) u, 3.6e-12 relative for
+    # 32^3 cells), the GPU in a fixed tree
+    t0_o = orc.Oracle(pb).totals()
+    np.testing.assert_allclose(t0, t0_o, rtol=0, atol=(4e-12 if precision == "fp64" else 1e-7) * np.abs(t0_o).max())
     o, s = run_pair(pb, precision, steps=2)
     assert_parity(s.all_cons(), o.all_cons(), pb.patches, precision, "amr3")
     t1 = s.totals()
@@ -115,6 +120,8 @@ def test_sedov_small_hierarchy_outflow():
 def test_orszag_tang_mhd(precision):
     pb = ai.orszag_tang(N=32, tile=16)
     t0 = Solver.from_problem(pb, precision=precision).totals()
+    t0_o = orc.Oracle(pb).totals()   # summation orders differ, as above
+    np.testing.assert_allclose(t0, t0_o, rtol=0, atol=(4e-12 if precision == "fp64" else 1e-7) * np.abs(t0_o).max())
     o, s = run_pair(pb, precision, steps=4)
     assert_parity(s.all_cons(), o.all_cons(), pb.patches, precision, "ot32")
     scale = np.abs(t0).max()
