@@ -198,6 +198,11 @@ extern "C" amr_status amr_step_patch_noalloc(const amr_config* cfg, const double
   std::string msg;
   if (validate_config(*cfg, msg) != AMR_OK) return AMR_ERR_ARG;
   if (cfg->recon != AMR_PLM) return AMR_ERR_ARG;   // the WENO3 build is not compiled into this path
+  {   // the output is written while the input is still being read: the two ranges may not overlap
+    const uintptr_t bytes = (uintptr_t)cfg->nvar * cfg->base_n[0] * cfg->base_n[1] * cfg->base_n[2] * sizeof(double);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(state_in), b = reinterpret_cast<uintptr_t>(state_out);
+    if (a < b + bytes && b < a + bytes) return AMR_ERR_ARG;
+  }
   std::vector<HPatch> P(1);
   P[0].level = 0;
   for (int d = 0; d < 3; ++d) {
