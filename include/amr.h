@@ -58,6 +58,7 @@ enum { AMR_HLL = 0, AMR_LLF = 1, AMR_FLUXREC = 2 };   /* interface flux */
 enum { AMR_PLM = 0, AMR_WENO3 = 1 };                  /* face states */
 enum { AMR_BC_OUTFLOW = 0, AMR_BC_PERIODIC = 1 };     /* per domain face */
 enum { AMR_STATE_CONSERVED = 0, AMR_STATE_PRIMITIVE = 1 };
+enum { AMR_GHOST_DIRECT = 0, AMR_GHOST_COPY = 1 };    /* how stages read same-level ghost cells */
 
 typedef struct {
   int nvar;              /* 5 (Euler) or 9 (GLM-MHD) */
@@ -94,6 +95,12 @@ typedef struct {
                             stencils: the abstract's higher-order shock-capturing extension); AMR_WENO3
                             needs AMR_HLL or AMR_LLF and runs the default stage-kernel build (the
                             tiling's ctas_per_sm does not apply); amr_step_patch_noalloc: AMR_PLM only */
+  int ghost_fill;        /* AMR_GHOST_DIRECT (0, default): a stage reads the two ghost layers of a patch
+                            face straight from the same-level neighbour that holds the whole face (or from
+                            the patch's own boundary cells at an outflow face), and only the other faces
+                            are copied or prolonged into ghost cells; AMR_GHOST_COPY: every face is
+                            filled into ghost cells before each stage.  Same results bit for bit;
+                            AMR_FLUXREC always copies. */
 } amr_config;
 
 /* One patch: `n` interior cells per axis starting at `lo` in the index space of
@@ -372,6 +379,15 @@ void amr_destroy(amr_handle* h);
  * copy fails. */
 amr_status amr_step_patch_noalloc(const amr_config* cfg, const double* state_in, double* state_out, double dt,
                                   double* dt_used);
+
+/* Arithmetic ceilings of the current device for the stage kernels' rooflines
+ * (a measurement helper; the paper has no counterpart): out[0] = FP32 and
+ * out[1] = FP64 fused multiply-add rates of the CUDA cores in FLOP/s (2 per
+ * FMA), each the best of three timed launches of independent FMA chains on
+ * every SM.  out: 2 caller-owned doubles.  Allocates and frees a small device
+ * buffer and synchronises the device; takes about 30 ms.  AMR_ERR_ARG for
+ * NULL, AMR_ERR_CUDA if no GPU or a launch fails. */
+amr_status amr_peak_fma_rates(double* out);
 
 #ifdef __cplusplus
 }

@@ -67,11 +67,14 @@ __global__ void finalize_speed_kernel(StepParams* params, double cfl, double ch_
 __global__ void set_dt_kernel(StepParams* params, double dt) { params->dt0 = dt; }
 
 struct DevLevel {
-  int nitems = 0, nghost = 0, nprolong = 0, ngather = 0, nrestrict = 0, nreg = 0, nuniq = 0;
+  int nitems = 0, nghost = 0, nghost_stage = 0, nprolong = 0, ngather = 0, ngather_ghost = 0, nrestrict = 0,
+      nreg = 0, nuniq = 0;
   const StageItem* items = nullptr;
-  const CopySeg* ghost = nullptr;
+  const CopySeg* ghost = nullptr;          // every face ghost segment (diagnostics, regrid flags)
+  const CopySeg* ghost_stage = nullptr;    // the faces a stage does not read directly
   const ProlongBox* prolong = nullptr;
-  const CopySeg* gather = nullptr;
+  const CopySeg* gather = nullptr;         // whole parent tiles (regrid fill)
+  const CopySeg* gather_ghost = nullptr;   // the tile cells the per-stage prolongation reads
   const RestrictSeg* restrict_segs = nullptr;
   const RegFace* regs = nullptr;
   const int* reflux_first = nullptr;
@@ -415,7 +418,12 @@ double level_dx(const amr_handle* h, int l, int d) { return h->dx0[d] / (double)
 
 // ---- one coarse step -------------------------------------------------------
 
-cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha) {
+// Face ghosts of level l in arr: parent data at fraction alpha of the parent step
+// prolonged into coarse-fine faces, then same-level copies.  all = false: only
+// the faces the stage kernel does not read straight from their source
+// (PatchDesc::face); all = true: every face (for kernels that read ghost cells
+// themselves: regrid flags, div B).
+cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha, bool all = false) {
   const DevLevel& L = h->dl[l];
   const LevelPlan& LP = h->plan.levels[l];
   const bool batched = h->cfg.batched != 0;
@@ -429,21 +437,23 @@ cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha) {
       LK(h->ops->prolong_flat(h->stream, static_cast<const FlatProlong*>(P.boxes), P.first, P.chunk_box, P.nchunk,
                               P.total, h->tile, arr));
     } else {
-      LK(h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->Uold, alpha));
+      LK(h->ops->gather(h->stream, L.gather_ghost, L.ngather_ghost, h->d_desc, h->tile, h->U, h->Uold, alpha));
       LK(h->ops->prolong(h->stream, L.prolong, L.nprolong, h->d_desc, h->tile, arr));
     }
   }
   h->cur_class = AMR_T_GHOST;
-  if (batched) {
+  if (all) {
+    LK(h->ops->ghost_copy(h->stream, L.ghost, L.nghost, h->d_desc, arr));
+  } else if (batched) {
     const DevLevel::Flat& G = L.fghost;
     LK(h->ops->ghost_copy_flat(h->stream, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk,
                                G.total, arr));
-  } else if (L.nghost == 0) {
-    LK(h->ops->ghost_copy(h->stream, L.ghost, L.nghost, h->d_desc, arr));
+  } else if (L.nghost_stage == 0) {
+    LK(h->ops->ghost_copy(h->stream, L.ghost_stage, L.nghost_stage, h->d_desc, arr));
   } else {
     for (int p = 0; p < LP.count; ++p) {
-      int a = LP.ghost_first[p], b = LP.ghost_first[p + 1];
-      if (b > a) LK(h->ops->ghost_copy(h->stream, L.ghost + a, b - a, h->d_desc, arr));
+      int a = LP.ghost_stage_first[p], b = LP.ghost_stage_first[p + 1];
+      if (b > a) LK(h->ops->ghost_copy(h->stream, L.ghost_stage + a, b - a, h->d_desc, arr));
     }
   }
   return cudaSuccess;
@@ -747,7 +757,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
   size_t o_lvol = buf.add(lvol);
   struct FlatOffs { size_t boxes, first, chunk; };
-  struct Offs { size_t items, ghost, prolong, gather, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
+  struct Offs { size_t items, ghost, ghost_stage, prolong, gather, gather_ghost, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
   std::vector<Offs> lo(nlev);
   auto put_flat = [&](const auto& f) { return FlatOffs{buf.add(f.boxes), buf.add(f.first), buf.add(f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
@@ -757,8 +767,10 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     lo[l].fp = put_flat(L.fprolong);
     lo[l].fr = put_flat(L.frestrict);
     lo[l].ghost = buf.add(L.ghost);
+    lo[l].ghost_stage = buf.add(L.ghost_stage);
     lo[l].prolong = buf.add(L.prolong);
     lo[l].gather = buf.add(L.gather);
+    lo[l].gather_ghost = buf.add(L.gather_ghost);
     lo[l].restr = buf.add(L.restrict_segs);
     lo[l].regs = buf.add(L.regs);
     lo[l].rf = buf.add(L.reflux_first);
@@ -798,14 +810,18 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     LevelPlan& L = pl.levels[l];
     DevLevel& D = h->dl[l];
     D.nghost = (int)L.ghost.size();
+    D.nghost_stage = (int)L.ghost_stage.size();
     D.nprolong = (int)L.prolong.size();
     D.ngather = (int)L.gather.size();
+    D.ngather_ghost = (int)L.gather_ghost.size();
     D.nrestrict = (int)L.restrict_segs.size();
     D.nreg = (int)L.regs.size();
     D.nuniq = L.reflux_first.empty() ? 0 : (int)L.reflux_first.size() - 1;
     D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
+    D.ghost_stage = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost_stage);
     D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
     D.gather = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather);
+    D.gather_ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather_ghost);
     D.restrict_segs = reinterpret_cast<const RestrictSeg*>(h->tables + lo[l].restr);
     D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
     D.reflux_first = reinterpret_cast<const int*>(h->tables + lo[l].rf);
@@ -862,13 +878,13 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   if (mid) {
     // the saved old-time states are still needed by the step: parent data of the
     // stepped level at fraction alpha, of the finer levels at fraction 1
-    CK(fill_ghosts(h, mid_level, h->U, mid_level == 0 ? 1.0 : alpha));
-    for (int l = mid_level + 1; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+    CK(fill_ghosts(h, mid_level, h->U, mid_level == 0 ? 1.0 : alpha, true));
+    for (int l = mid_level + 1; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0, true));
   } else {
     if (nlev > 1)
       CK(cudaMemcpyAsync(h->Uold, h->U, op.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
     h->counting = 0;
-    for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+    for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0, true));
   }
   // 2. density-gradient criterion.  Block tags and refinable blocks made on the
   //    GPU when every flagged level's block grid fits a bitmap (only the
@@ -1393,8 +1409,11 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   const int occs[2] = {0, h->ops->alt_occupancy()};
   const int shapes[7][3] = {{32, 256, 32}, {32, 256, 16}, {16, 256, 16}, {32, 256, 64},
                             {16, 128, 8}, {16, 128, 16}, {16, 128, 32}};
+  // the WENO3 stage runs one build (256 threads, default register budget) for every
+  // tiling, so only the work-item shapes are tuned
+  const bool one_build = h->cfg.recon == AMR_WENO3;
   for (int o = 0; o < 2; ++o) {
-    if (o == 1 && occs[1] == 0) continue;
+    if (o == 1 && (occs[1] == 0 || one_build)) continue;
     for (auto& sh : shapes) {
       if (o == 1 && sh[1] == 128 && !h->ops->has_alt128()) continue;   // no second 128-thread budget
       Cand c;
@@ -1435,8 +1454,9 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
       if (rep_i > 0) t_best = std::min(t_best, (double)ms);   // first run warms up
     }
     char line[160];
-    std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d: %.4f ms\n", h->tp.max_wx,
-                  h->tp.max_cols, h->tp.zchunk, h->ops->resident_ctas(), t_best);
+    std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d: %.4f ms%s\n", h->tp.max_wx,
+                  h->tp.max_cols, h->tp.zchunk, h->ops->resident_ctas(), t_best,
+                  one_build ? " (WENO3: default 256-thread build)" : "");
     rep += line;
     if (t_best < best) { best = t_best; best_i = (int)ci; }
   }
@@ -1633,7 +1653,7 @@ amr_status amr_divb_norms(amr_handle* h, double* out) {
   if (nlev > 1)
     CK(cudaMemcpyAsync(h->Uold, h->U, h->plan.arena_elems * es, cudaMemcpyDeviceToDevice, h->stream));
   h->counting = 0;
-  for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0));
+  for (int l = 0; l < nlev; ++l) CK(fill_ghosts(h, l, h->U, 1.0, true));
   CK(h->ops->divb(h->stream, h->d_chunks, h->nchunk, h->d_desc, h->U, h->d_cover, h->d_cover_first, h->dx0,
                   h->partial, h->totals));
   h->launches += h->counting + 2;

@@ -23,6 +23,22 @@ constexpr int kPlaneMax = 432;    // max (wx + 4) * (wy + 4) of a stage tile
 constexpr int kPlaneMax128 = 272;
 AMR_HD constexpr int stage_plane_max(int nt) { return nt == 128 ? kPlaneMax128 : kPlaneMax; }
 
+// Where the stage kernel reads the two ghost layers of one face of a patch: the
+// ghost cell at local (i, j, k) of that face holds variable v at element
+//   base + i * sx + j * sy + k * sz + v * vs
+// of the state arena.  Three kinds, chosen by the planner per face:
+//   own ghost cells (filled by the ghost-copy and prolongation kernels before
+//     each stage): the patch's own layout;
+//   a same-level neighbour (or the patch itself across a periodic boundary)
+//     whose interior holds the whole two-layer face: its layout, translated;
+//   an outflow boundary: the patch's own boundary cells (stride 0 along the
+//     face normal: zero-gradient extension).
+struct FaceSrc {
+  int64_t base;
+  int sx, sy, sz;
+  int vs;
+};
+
 // Device view of one patch.  Arrays U, U1 and Uold share the same layout and
 // offsets: var v, ghosted local cell (i, j, k) with -2 <= i < n0 + 2 sits at
 //   off + v * vstride + ((k + 2) * m1 + (j + 2)) * pitch + (i + 2)
@@ -36,6 +52,7 @@ struct PatchDesc {
   int lo[3];         // level index of interior cell (0,0,0)
   int tile_off;      // parent-tile offset (elements) for level >= 1, else -1
   int tn[3];         // parent tile extent (n/2 + 4), level >= 1
+  FaceSrc face[6];   // ghost source of the faces x-lo, x-hi, y-lo, y-hi, z-lo, z-hi
 };
 
 AMR_HD inline int64_t cell_index(const PatchDesc& p, int i, int j, int k) {

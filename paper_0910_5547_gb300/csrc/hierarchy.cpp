@@ -96,6 +96,34 @@ std::vector<Rect> mask_rects(const unsigned char* m, int A, int B) {
 }
 std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) { return mask_rects(m.data(), A, B); }
 
+// Disjoint boxes covering the cells with need != 0 of an n0 x n1 x n2 grid:
+// rectangles of each z slice, merged across consecutive slices with identical
+// rectangles.
+struct Box3 { int lo[3], n[3]; };
+std::vector<Box3> need_boxes(const std::vector<unsigned char>& need, int n0, int n1, int n2) {
+  std::vector<Box3> done;
+  std::vector<std::pair<Rect, int>> open, next;
+  std::vector<unsigned char> inv((size_t)n0 * n1);
+  for (int z = 0; z < n2; ++z) {
+    for (size_t e = 0; e < inv.size(); ++e) inv[e] = need[(size_t)z * n0 * n1 + e] ? 0 : 1;
+    next.clear();
+    for (const Rect& r : mask_rects(inv, n0, n1)) {
+      int hit = -1;
+      for (const auto& o : open)
+        if (o.first.a0 == r.a0 && o.first.na == r.na && o.first.b0 == r.b0 && o.first.nb == r.nb) hit = o.second;
+      if (hit >= 0) {
+        done[hit].n[2] += 1;
+      } else {
+        done.push_back({{r.a0, r.b0, z}, {r.na, r.nb, 1}});
+        hit = (int)done.size() - 1;
+      }
+      next.push_back({r, hit});
+    }
+    open.swap(next);
+  }
+  return done;
+}
+
 // Persistent worker threads for the planner's parallel loops (spawning threads
 // per loop costs a few hundred microseconds, and a rebuild runs dozens of loops).
 // A job is f(i) for i in [0, n), grabbed in chunks of 8 by the caller and the
@@ -350,6 +378,10 @@ amr_status validate_config(const amr_config& c, std::string& msg) {
   }
   if (c.riemann == AMR_FLUXREC && c.nvar != 5) { msg = "AMR_FLUXREC is for the Euler system (nvar 5)"; return AMR_ERR_ARG; }
   if (c.recon != AMR_PLM && c.recon != AMR_WENO3) { msg = "recon must be AMR_PLM or AMR_WENO3"; return AMR_ERR_ARG; }
+  if (c.ghost_fill != AMR_GHOST_DIRECT && c.ghost_fill != AMR_GHOST_COPY) {
+    msg = "ghost_fill must be AMR_GHOST_DIRECT or AMR_GHOST_COPY";
+    return AMR_ERR_ARG;
+  }
   if (c.recon == AMR_WENO3 && c.riemann == AMR_FLUXREC) {
     msg = "AMR_WENO3 reconstructs the states of an AMR_HLL / AMR_LLF solve, not split fluxes";
     return AMR_ERR_ARG;
@@ -696,10 +728,62 @@ std::vector<int> morton_partition(const amr_config& cfg, const std::vector<HPatc
   return owner;
 }
 
+// The stage kernel's view of a face read from the patch's own ghost cells.
+FaceSrc own_face(const PatchDesc& d) {
+  FaceSrc f;
+  f.base = d.off + cell_index(d, 0, 0, 0);
+  f.sx = 1;
+  f.sy = d.pitch;
+  f.sz = d.pitch * d.m1;
+  f.vs = (int)d.vstride;
+  return f;
+}
+
+// Face (2 axis + side) of the patch that a ghost segment fills.
+int seg_face(const CopySeg& s, const HPatch& p) {
+  for (int a = 0; a < 3; ++a) {
+    if (s.dlo[a] < 0) return 2 * a;
+    if (s.dlo[a] >= p.n[a]) return 2 * a + 1;
+  }
+  return 0;   // not reached: ghost segments lie outside the interior along one axis
+}
+
+// Faces of patch i whose two ghost layers come, whole, from one source cell box
+// through one mapping (one same-level patch by translation, the patch itself
+// across a periodic boundary, or its boundary cells at an outflow face): the
+// stage kernel can read them there (desc.face), and the ghost copy skips them.
+void classify_faces(Plan& plan, int i, const std::vector<CopySeg>& segs, std::array<uint8_t, 6>& direct) {
+  const HPatch& p = plan.patches[i];
+  for (int f = 0; f < 6; ++f) {
+    const int d = f / 2, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const CopySeg* first = nullptr;
+    bool same = true;
+    int64_t vol = 0;
+    for (const CopySeg& s : segs) {
+      if (seg_face(s, p) != f) continue;
+      if (!first) first = &s;
+      for (int a = 0; a < 3; ++a)
+        same = same && s.src_patch == first->src_patch && s.mode[a] == first->mode[a] && s.sh[a] == first->sh[a];
+      vol += (int64_t)s.dn[0] * s.dn[1] * s.dn[2];
+    }
+    direct[f] = 0;
+    if (!first || !same || vol != (int64_t)kGhost * p.n[t1] * p.n[t2]) continue;
+    if (first->mode[t1] != 0 || first->mode[t2] != 0) continue;
+    const PatchDesc& q = plan.desc[first->src_patch];
+    FaceSrc& fs = plan.desc[i].face[f];
+    fs.base = q.off + cell_index(q, first->sh[0], first->sh[1], first->sh[2]);
+    fs.sx = first->mode[0] ? 0 : 1;
+    fs.sy = first->mode[1] ? 0 : q.pitch;
+    fs.sz = first->mode[2] ? 0 : q.pitch * q.m1;
+    fs.vs = (int)q.vstride;
+    direct[f] = 1;
+  }
+}
+
 void build_flat(Plan& plan) {
   for (LevelPlan& L : plan.levels) {
-    flatten_copies(plan, L.ghost, false, L.fghost);
-    flatten_copies(plan, L.gather, true, L.fgather);
+    flatten_copies(plan, L.ghost_stage, false, L.fghost);
+    flatten_copies(plan, L.gather_ghost, true, L.fgather);
     flatten_prolong(plan, L.prolong, L.fprolong);
     flatten_restrict(plan, L.restrict_segs, L.frestrict);
   }
@@ -749,12 +833,18 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     poff += (int64_t)p.n[0] * p.n[1] * p.n[2] * plan.nvar;
   }
   if (toff > INT32_MAX) { msg = "parent tiles exceed 2^31 elements"; return AMR_ERR_ARG; }
+  for (int i = 0; i < np; ++i)
+    for (int f = 0; f < 6; ++f) plan.desc[i].face[f] = own_face(plan.desc[i]);
   plan.arena_elems = off;
   plan.tile_elems = toff;
   plan.packed_elems = poff;
 
   // ---- stage work items ----
   build_items(plan, tp);
+  // faces whose ghost layers a stage reads straight from a neighbour (or outflow boundary cells)
+  const bool direct_ok = cfg.ghost_fill == AMR_GHOST_DIRECT && cfg.riemann != AMR_FLUXREC;
+  std::vector<std::array<uint8_t, 6>> direct(np);
+  for (auto& a : direct) a.fill(0);
 
   // ---- ghost fill: sibling copies (incl. periodic images), outflow, prolongation boxes ----
   for (int l = 0; l < nlev; ++l) {
@@ -873,6 +963,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
           split_copy(Gv, g0);
         }
         split_prolong(Pv, 0);
+        if (direct_ok) classify_faces(plan, i, Gv, direct[i]);
     });
     L.ghost_first.push_back(0);
     L.prolong_first.push_back(0);
@@ -893,19 +984,21 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
     PatchIndex cix(P, C.first, C.count);
-    std::vector<std::vector<CopySeg>> as(L.count);
+    std::vector<std::vector<CopySeg>> as(L.count), gs_ghost(L.count);
     std::vector<std::string> err(L.count);
     parallel_for(L.count, [&](int ii) {
       const int i = L.first + ii;
       std::vector<CopySeg>& Av = as[ii];
       std::vector<int> cand;
       const HPatch& p = P[i];
-        struct Piece { int a, len, mode, src; };
+      struct Piece { int a, len, mode, src; };
+      // gathers of the tile cells [blo, bhi) per axis into out; returns the cells covered
+      auto gather_box = [&](const int* blo, const int* bhi, std::vector<CopySeg>& out) -> int64_t {
         std::vector<Piece> pieces[3];
         for (int d = 0; d < 3; ++d) {
           int Nc = level_n(cfg, l - 1, d);
-          int T0 = p.lo[d] / 2 - 2, tn = p.n[d] / 2 + 4;
-          int t = 0;
+          int T0 = p.lo[d] / 2 - 2, tn = bhi[d];
+          int t = blo[d];
           while (t < tn) {
             int Cg = T0 + t;
             int kind = Cg < 0 ? 0 : (Cg < Nc ? 1 : 2);
@@ -961,13 +1054,52 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 }
                 if (!ok) continue;
                 covered += vol;
-                Av.push_back(s);
+                out.push_back(s);
               }
             }
+        return covered;
+      };
+      const PatchDesc& d = plan.desc[i];
+      {
+        const int blo[3] = {0, 0, 0}, bhi[3] = {d.tn[0], d.tn[1], d.tn[2]};
+        const int64_t covered = gather_box(blo, bhi, Av);
         split_copy(Av, 0);
-        const PatchDesc& d = plan.desc[i];
         if (covered != (int64_t)d.tn[0] * d.tn[1] * d.tn[2])
           err[ii] = fmt("patch %d: parent tile not covered by level %d", i, l - 1);
+      }
+      // the per-stage ghost fill reads only the parents of the prolongation boxes
+      // and their face neighbours (the minmod stencil): gather those tile cells
+      // (a patch whose ghost cells all come from siblings gathers nothing)
+      std::vector<unsigned char> need((size_t)d.tn[0] * d.tn[1] * d.tn[2], 0);
+      int64_t nneed = 0;
+      for (int b = L.prolong_first[ii]; b < L.prolong_first[ii + 1]; ++b) {
+        const ProlongBox& pb = L.prolong[b];
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+          const int t0 = ((p.lo[a] + pb.lo[a]) >> 1) - (p.lo[a] >> 1) + 2;
+          const int t1 = ((p.lo[a] + pb.lo[a] + pb.n[a] - 1) >> 1) - (p.lo[a] >> 1) + 2;
+          lo[a] = std::max(t0 - 1, 0);
+          hi[a] = std::min(t1 + 1, (int)d.tn[a] - 1);
+        }
+        for (int z = lo[2]; z <= hi[2]; ++z)
+          for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+              unsigned char& m = need[((size_t)z * d.tn[1] + y) * d.tn[0] + x];
+              nneed += m ? 0 : 1;
+              m = 1;
+            }
+      }
+      if (nneed > 0) {
+        int64_t got = 0;
+        for (const Box3& bx : need_boxes(need, d.tn[0], d.tn[1], d.tn[2])) {
+          const int blo[3] = {bx.lo[0], bx.lo[1], bx.lo[2]};
+          const int bhi[3] = {bx.lo[0] + bx.n[0], bx.lo[1] + bx.n[1], bx.lo[2] + bx.n[2]};
+          got += gather_box(blo, bhi, gs_ghost[ii]);
+        }
+        split_copy(gs_ghost[ii], 0);
+        if (got != nneed && err[ii].empty())
+          err[ii] = fmt("patch %d: parent cells of its prolongation not covered by level %d", i, l - 1);
+      }
     });
     L.gather_first.push_back(0);
     for (int ii = 0; ii < L.count; ++ii) {
@@ -977,6 +1109,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
       }
       L.gather.insert(L.gather.end(), as[ii].begin(), as[ii].end());
       L.gather_first.push_back((int)L.gather.size());
+      L.gather_ghost.insert(L.gather_ghost.end(), gs_ghost[ii].begin(), gs_ghost[ii].end());
     }
   }
 
@@ -1158,6 +1291,29 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     });
     L.reflux_first[nuniq[nc]] = (int)regs.size();
     L.regs.swap(regs);
+  }
+  // the coarse-side register flux reads two cells on either side of a coarse-fine
+  // face: where that stencil leaves the coarse patch, its ghost cells are read,
+  // so that face of the coarse patch keeps copied ghost cells
+  for (int l = 1; l < nlev && direct_ok; ++l)
+    for (const RegFace& r : plan.levels[l].regs) {
+      const int f = r.cidx[r.d] + (r.cside > 0 ? 1 : 0);   // face index between cells f-1 and f
+      if (f - 2 < 0) direct[r.cpatch][2 * r.d] = 0;
+      if (f + 1 >= P[r.cpatch].n[r.d]) direct[r.cpatch][2 * r.d + 1] = 0;
+    }
+  for (int i = 0; i < np; ++i)
+    for (int f = 0; f < 6; ++f)
+      if (!direct[i][f]) plan.desc[i].face[f] = own_face(plan.desc[i]);
+  // per-stage ghost copies: the segments of the faces that are not read directly
+  for (LevelPlan& L : plan.levels) {
+    L.ghost_stage.clear();
+    L.ghost_stage_first.assign(1, 0);
+    for (int ii = 0; ii < L.count; ++ii) {
+      const int i = L.first + ii;
+      for (int e = L.ghost_first[ii]; e < L.ghost_first[ii + 1]; ++e)
+        if (!direct[i][seg_face(L.ghost[e], P[i])]) L.ghost_stage.push_back(L.ghost[e]);
+      L.ghost_stage_first.push_back((int)L.ghost_stage.size());
+    }
   }
   build_flat(plan);
   return AMR_OK;

@@ -54,10 +54,13 @@ struct LevelPlan {
   std::vector<int> item_first;               // per patch of the level: first item (size count + 1)
   std::vector<CopySeg> ghost;                // sibling copies + outflow boundary, grouped by dst patch
   std::vector<int> ghost_first;              // per patch (size count + 1)
+  std::vector<CopySeg> ghost_stage;          // the ghost segments of the faces a stage does not read
+  std::vector<int> ghost_stage_first;        //   directly (desc.face), per patch (size count + 1)
   std::vector<ProlongBox> prolong;           // fine ghosts from the parent tile (level >= 1)
   std::vector<int> prolong_first;
-  std::vector<CopySeg> gather;               // parent-tile gathers (level >= 1), grouped by fine patch
-  std::vector<int> gather_first;
+  std::vector<CopySeg> gather;               // parent-tile gathers (level >= 1), whole tiles, grouped by fine patch
+  std::vector<int> gather_first;             //   (the regrid fill prolongs whole new patches from them)
+  std::vector<CopySeg> gather_ghost;         // the part of each tile the per-stage prolongation reads
   std::vector<RestrictSeg> restrict_segs;    // this level -> parent (level >= 1)
   RegVec regs;                               // coarse-fine faces of this level (level >= 1), sorted by coarse cell
   std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell

@@ -305,7 +305,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     // this thread's halo cell (one per thread, 4 (wx + wy) <= blockDim)
     const int nhalo = 4 * (wx + wy);
     const bool has_halo = t < nhalo;
-    int hoff = 0, hpos = 0;
+    // this thread's halo cell at plane z0, planes hpl and variables hvs elements apart:
+    // an interior cell of the patch, or a ghost cell of an x/y face read where the
+    // face's source lies (own ghost cells, a neighbour's interior, outflow boundary cells)
+    const T* hsrc = Ub;
+    int hpl = plane, hvs = vs, hpos = 0;
     if (has_halo) {
       int hx, hy;
       if (t < 4 * wy) {
@@ -318,7 +322,16 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         hx = c;
         hy = r < 2 ? r - 2 : wy + (r - 2);
       }
-      hoff = ((it.z0 + kGhost) * P.m1 + (it.y0 + hy + kGhost)) * P.pitch + (it.x0 + hx + kGhost);
+      const int lx = it.x0 + hx, ly = it.y0 + hy;
+      const int f = lx < 0 ? 0 : (lx >= P.n[0] ? 1 : (ly < 0 ? 2 : (ly >= P.n[1] ? 3 : -1)));
+      if (f < 0) {
+        hsrc = Ub + ((it.z0 + kGhost) * P.m1 + (ly + kGhost)) * P.pitch + (lx + kGhost);
+      } else {
+        const FaceSrc fs = a.desc[it.patch].face[f];
+        hsrc = a.Uin + (fs.base + (int64_t)lx * fs.sx + (int64_t)ly * fs.sy + (int64_t)it.z0 * fs.sz);
+        hpl = fs.sz;
+        hvs = fs.vs;
+      }
       hpos = (hy + 2) * sw + (hx + 2);
     }
     // this thread's boundary slope (the halo cell next to the block edge), if any
@@ -338,25 +351,42 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       }
     }
 
+    // source of this column's plane z0 + p and its variable stride: the patch's own
+    // array inside it; below and above it the z faces' sources (warp-uniform branch)
+    auto col_src = [&](int p, int& svs) -> const T* {
+      const int lz = it.z0 + p;
+      if (lz >= 0 && lz < P.n[2]) {
+        svs = vs;
+        return Ub + col + p * plane;
+      }
+      const FaceSrc fs = a.desc[it.patch].face[lz < 0 ? 4 : 5];
+      svs = fs.vs;
+      return a.Uin + (fs.base + (int64_t)(it.x0 + tx) * fs.sx + (int64_t)(it.y0 + ty) * fs.sy + (int64_t)lz * fs.sz);
+    };
+
     // z-march registers at the start of iteration j: wA = w(j-1), wB = w(j),
     // sA = slope(j-1), uD = conserved plane j+1 (in flight); Fzm = flux of face
     // j-3/2 (from the previous iteration).
     T uD[NV], wA[NV], wB[NV], sA[NV], Fzm[NV], hN[NV], unN[NV];
     if (active) {  // prologue: planes z0-2 .. z0+1
       T u0[NV], w0[NV];
-      load_cons<T, NV>(Ub, vs, col - 2 * plane, u0);
-      load_cons<T, NV>(Ub, vs, col - plane, uD);
+      int svs;
+      const T* s0 = col_src(-2, svs);
+      load_cons<T, NV>(s0, svs, 0, u0);
+      s0 = col_src(-1, svs);
+      load_cons<T, NV>(s0, svs, 0, uD);
       cons_to_prim<T, NV>(u0, w0, ph.efl);
       cons_to_prim<T, NV>(uD, wA, ph.efl);
       load_cons<T, NV>(Ub, vs, col, uD);
       bad |= !cons_to_prim<T, NV>(uD, wB, ph.efl, &floor_hits);   // plane 0: an interior plane
+      s0 = col_src(1, svs);
       if (kAsync) {
 #pragma unroll
         for (int v = 0; v < NV; ++v)   // plane 1, slot 1
-          cp_async_elem(&CR[NV * kPlane + sidx<T, NV, kPlane>(v, me)], Ub + v * vs + col + plane);
+          cp_async_elem(&CR[NV * kPlane + sidx<T, NV, kPlane>(v, me)], s0 + v * svs);
         sstore<T, NV, kPlane>(CR, me, uD);   // plane 0, slot 0
       } else {
-        load_cons<T, NV>(Ub, vs, col + plane, uD);
+        load_cons<T, NV>(s0, svs, 0, uD);
       }
       if (STAGE == 2 && !kAsync && !kLean) load_cons<T, NV>(Ob, vs, col, unN);
 #pragma unroll
@@ -373,13 +403,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
       if (has_halo) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          cp_async_elem(&CR[sidx<T, NV, kPlane>(v, hpos)], Ub + v * vs + hoff);
-          if (wz > 1) cp_async_elem(&CR[NV * kPlane + sidx<T, NV, kPlane>(v, hpos)], Ub + v * vs + hoff + plane);
+          cp_async_elem(&CR[sidx<T, NV, kPlane>(v, hpos)], hsrc + v * hvs);
+          if (wz > 1) cp_async_elem(&CR[NV * kPlane + sidx<T, NV, kPlane>(v, hpos)], hsrc + v * hvs + hpl);
         }
       }
       cp_async_commit();
     } else if (has_halo) {
-      if (!kLean) load_cons<T, NV>(Ub, vs, hoff, hN);
+      if (!kLean) load_cons<T, NV>(hsrc, hvs, 0, hN);
     }
 
     // Iteration j runs two phases separated by barriers:
@@ -408,13 +438,15 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         const int jn = j + 2;
         T* slot = CR + (jn & (kRing - 1)) * NV * kPlane;
         if (active && jn <= wz + 1) {
+          int svs;
+          const T* src = col_src(jn, svs);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[sidx<T, NV, kPlane>(v, me)], Ub + v * vs + col + jn * plane);
+          for (int v = 0; v < NV; ++v) cp_async_elem(&slot[sidx<T, NV, kPlane>(v, me)], src + v * svs);
         }
         if (has_halo && jn < wz) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            cp_async_elem(&slot[sidx<T, NV, kPlane>(v, hpos)], Ub + v * vs + hoff + jn * plane);
+            cp_async_elem(&slot[sidx<T, NV, kPlane>(v, hpos)], hsrc + v * hvs + jn * hpl);
         }
         if (STAGE == 2 && active && cur) {  // U^n of plane j, used by the update of plane j
           T* sn = CN + (j & (kRingN - 1)) * NV * NT;
@@ -429,9 +461,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         if (kAsync) {
           sload<T, NV, kPlane>(CR + (j & (kRing - 1)) * NV * kPlane, hpos, hN);
         }
-        if (kLean) load_cons<T, NV>(Ub, vs, hoff + j * plane, hN);
+        if (kLean) load_cons<T, NV>(hsrc, hvs, j * hpl, hN);
         cons_to_prim<T, NV>(hN, w, ph.efl);
-        if (!kAsync && !kLean) load_cons<T, NV>(Ub, vs, hoff + (j + 1 < wz ? j + 1 : j) * plane, hN);
+        if (!kAsync && !kLean) load_cons<T, NV>(hsrc, hvs, (j + 1 < wz ? j + 1 : j) * hpl, hN);
         sstore<T, NV, kPlane>(W, hpos, w);
       }
       if (active) {
@@ -449,7 +481,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         }
         if (!kAsync) {
           const int jn = j + 2 <= wz + 1 ? j + 2 : wz + 1;   // ghost planes end at wz+1
-          load_cons<T, NV>(Ub, vs, col + jn * plane, uD);      // prefetch plane j+2
+          int svs;
+          const T* src = col_src(jn, svs);
+          load_cons<T, NV>(src, svs, 0, uD);                   // prefetch plane j+2
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {

@@ -27,6 +27,7 @@ AMR_HLL, AMR_LLF, AMR_FLUXREC = 0, 1, 2
 AMR_PLM, AMR_WENO3 = 0, 1
 AMR_BC_OUTFLOW, AMR_BC_PERIODIC = 0, 1
 AMR_STATE_CONSERVED, AMR_STATE_PRIMITIVE = 0, 1
+AMR_GHOST_DIRECT, AMR_GHOST_COPY = 0, 1
 
 STATUS_NAMES = {0: "AMR_OK", -1: "AMR_ERR_ARG", -2: "AMR_ERR_NESTING", -3: "AMR_ERR_CUDA",
                 -4: "AMR_ERR_NONPHYSICAL", -5: "AMR_ERR_TIMEOUT", -6: "AMR_ERR_STATE"}
@@ -38,7 +39,8 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_destroy", "amr_set_timing", "amr_get_timing", "amr_step_patch_noalloc", "amr_regrid",
            "amr_get_patches", "amr_autotune", "amr_set_tiling", "amr_get_regrid_timing", "amr_floor_count",
            "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms", "amr_set_state_async",
-           "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches", "amr_get_regrid_counts"]
+           "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches", "amr_get_regrid_counts",
+           "amr_peak_fma_rates"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -79,6 +81,7 @@ class amr_config(ctypes.Structure):
         ("dev_free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
         ("recon", ctypes.c_int),
+        ("ghost_fill", ctypes.c_int),
     ]
 
 
@@ -136,6 +139,8 @@ def load():
     L.amr_step_patch_noalloc.argtypes = [ctypes.POINTER(amr_config), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_double, dp]
     L.amr_step_patch_noalloc.restype = ctypes.c_int
+    L.amr_peak_fma_rates.argtypes = [dp]
+    L.amr_peak_fma_rates.restype = ctypes.c_int
     L.amr_regrid.argtypes = [H, ctypes.POINTER(amr_regrid_params), ctypes.POINTER(ctypes.c_int)]
     L.amr_regrid.restype = ctypes.c_int
     L.amr_set_regrid_schedule.argtypes = [H, ctypes.POINTER(amr_regrid_params), ctypes.c_int]
@@ -377,6 +382,15 @@ def amr_step_patch_noalloc(cfg: amr_config, state_in_ptr: int, state_out_ptr: in
     if st != AMR_OK:
         raise AmrError(st, "amr_step_patch_noalloc failed")
     return float("nan")
+
+
+def amr_peak_fma_rates() -> dict:
+    """FP32 and FP64 FMA rates of the current device's CUDA cores, FLOP/s."""
+    out = (ctypes.c_double * 2)()
+    st = load().amr_peak_fma_rates(out)
+    if st != AMR_OK:
+        raise AmrError(st, "amr_peak_fma_rates failed")
+    return {"fp32_flops": out[0], "fp64_flops": out[1]}
 
 
 class PatchRecord:
