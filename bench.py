@@ -70,20 +70,28 @@ def stage_source_sha() -> str:
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
-def stage_traffic():
-    """DRAM bytes per stage-kernel launch (mean of stage 1 and stage 2) from the committed ncu
-    summary, used only while the kernel source is the one that was profiled."""
-    import hashlib
+def stage_profile():
+    """From the committed ncu summary of the FP32 stage kernel on this workload, used only
+    while the kernel source is the one that was profiled: DRAM bytes per stage-kernel launch
+    (mean of stage 1 and stage 2) and warp instructions per cell-update (both stages)."""
     import re
     sha = stage_source_sha()
+    out = {"traffic_per_launch": None, "warp_inst_per_cell_update": None}
     try:
         txt = open(os.path.join(ROOT, "profiles", "stage_kernel_fp32_kh256.md")).read()
-        m = re.search(r"source_sha=(\w+) traffic_per_launch=(\d+)", txt)
-        if m and m.group(1) == sha:
-            return int(m.group(2))
     except OSError:
-        pass
-    return None
+        return out
+    m = re.search(r"source_sha=(\w+) traffic_per_launch=(\d+)", txt)
+    if m and m.group(1) == sha:
+        out["traffic_per_launch"] = int(m.group(2))
+        k = re.search(r"warp_inst_per_cell_update=([0-9.]+)", txt)
+        if k:
+            out["warp_inst_per_cell_update"] = float(k.group(1))
+    return out
+
+
+def stage_traffic():
+    return stage_profile()["traffic_per_launch"]
 
 
 def turbulence_diagnostics(packed, n, gamma):
@@ -185,18 +193,42 @@ def timed_steps(torch, s, stream, steps, dt=0.0):
     return e0.elapsed_time(e1) / 1e3
 
 
-def l1_errors(got, ref):
-    """Per-variable L1 relative error over all cells (momentum components against the
-    momentum norm, as the parity tests measure FP32)."""
+def parity_errors(got, ref):
+    """Errors of single-level states against the oracle's, per variable over all
+    cells: the vector-normalised L1 (momentum components against the momentum
+    norm, as the parity tests assert for FP32) and the per-variable L1 and max
+    (each variable against its own norm; a field that is zero in the problem
+    against the density's)."""
     import numpy as np
     nv = ref[0].shape[0]
     num = np.zeros(nv)
     den = np.zeros(nv)
+    mx = np.zeros(nv)
+    rmx = np.zeros(nv)
     for g, r in zip(got, ref):
-        num += np.abs(g - r).reshape(nv, -1).sum(axis=1)
-        den += np.abs(r).reshape(nv, -1).sum(axis=1)
-    den[1:4] = den[1:4].sum()
-    return num / np.maximum(den, 1e-300)
+        d = np.abs(g - r).reshape(nv, -1)
+        a = np.abs(r).reshape(nv, -1)
+        num += d.sum(axis=1)
+        den += a.sum(axis=1)
+        mx = np.maximum(mx, d.max(axis=1))
+        rmx = np.maximum(rmx, a.max(axis=1))
+    vden = den.copy()
+    vden[1:4] = den[1:4].sum()
+    den[den < 1e-12 * den[0]] = den[0]
+    rmx[rmx < 1e-12 * rmx[0]] = rmx[0]
+    return {"l1_vector_metric": float((num / vden).max()), "l1_per_variable": [float(x) for x in num / den],
+            "max_per_variable": [float(x) for x in mx / rmx]}
+
+
+def chosen_tiling(report: str):
+    """(max_wx, max_cols, zchunk, ctas_per_sm) of the candidate the autotuner kept."""
+    import re
+    lines = [l for l in report.splitlines() if l.startswith("tile ")]
+    m = re.search(r"chosen: candidate (\d+)", report)
+    if not m:
+        return None
+    t = re.match(r"tile wx<=(\d+) cols<=(\d+) z=(\d+) ctas/SM=(\d+)", lines[int(m.group(1))])
+    return tuple(int(x) for x in t.groups()) if t else None
 
 
 def cpu_model():
@@ -216,15 +248,22 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_baseline(steps=2, stream=None):
-    """The FP64 oracle as it stands, all host cores, on a bounded sample: `steps`
-    RK2 steps of the full 256^3 / 32^3-patch workload.  The same steps (the oracle's
-    dt sequence) also run through the library in FP32 and FP64, and the L1 errors of
-    their final states against the oracle's are reported beside the timing."""
+def cpu_baseline(steps, parity_steps, stream, tiling):
+    """The FP64 oracle as it stands, all host cores, on a bounded sample: the first
+    `steps` RK2 steps of the full 256^3 / 32^3-patch workload are timed.  The oracle
+    then continues to `parity_steps` steps, and the same dt sequence (the oracle's
+    CFL steps) runs through the library in FP32 and FP64, on the single 256^3 patch
+    with the headline's tiling (the configuration `value` times) and on the 512
+    patches of 32^3; every cell of their final states is compared with the oracle's."""
+    import numpy as np
+
     import amr_inputs as ai
     import oracle as orc
     cores = len(os.sched_getaffinity(0))
     pb = ai.kelvin_helmholtz(N=N, tile=TILE)
+    single = ai.kelvin_helmholtz(N=N, tile=None)
+    assert all(np.array_equal(w, single.prim[0][:, p.lo[2]:p.lo[2] + p.n[2], p.lo[1]:p.lo[1] + p.n[1],
+                                                 p.lo[0]:p.lo[0] + p.n[0]]) for p, w in zip(pb.patches, pb.prim))
     o = orc.Oracle(pb, nthreads=cores)
     t = time.perf_counter()
     dts = [o.step() for _ in range(steps)]
@@ -232,8 +271,35 @@ def cpu_baseline(steps=2, stream=None):
     out = {"value": N ** 3 * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{steps} RK2 steps (CFL dt) of the full 256^3 periodic workload, 512 patches of 32^3, "
                      f"FP64, OpenMP over patches; {dt:.1f} s wall"}
+    t = time.perf_counter()
+    dts += [o.step() for _ in range(max(0, parity_steps - steps))]
+    t_rest = time.perf_counter() - t
     ref = o.all_cons()
     del o
+    parity = {"steps": len(dts), "dt": "the oracle's CFL steps (0.4), replayed by the GPU solvers",
+              "oracle_s": round(dt + t_rest, 1)}
+    for prec in ("fp32", "fp64"):
+        for name, prob in (("single_256", single), ("tiled_512", pb)):
+            s = make_solver(prob, prec, True, True, stream)
+            if name == "single_256" and tiling and prec == "fp32":
+                s.set_tiling(*tiling)
+            for d in dts:
+                s.step(d, sync=False)
+            s.check()
+            got = s.all_cons()
+            s.close()
+            if name == "single_256":
+                full = np.empty((5, N, N, N))
+                for p, u in zip(pb.patches, ref):
+                    full[:, p.lo[2]:p.lo[2] + p.n[2], p.lo[1]:p.lo[1] + p.n[1], p.lo[0]:p.lo[0] + p.n[0]] = u
+                parity[f"{prec}_{name}"] = parity_errors(got, [full])
+                del full
+            else:
+                parity[f"{prec}_{name}"] = parity_errors(got, ref)
+            del got
+    parity["tiling_single_256_fp32"] = list(tiling) if tiling else None
+    out["parity"] = parity
+    del ref
     # single thread: one RK2 step of a 128^3 sub-box of the same workload (same patches)
     sub = ai.kelvin_helmholtz(N=128, tile=TILE)
     o1 = orc.Oracle(sub, nthreads=1)
@@ -262,13 +328,6 @@ def cpu_baseline(steps=2, stream=None):
                      "sample": f"{what}; {dtx:.1f} s wall"}
         del ox, pbx
     out["per_config"] = per
-    for prec in ("fp32", "fp64"):
-        s = make_solver(pb, prec, True, True, stream)
-        for d in dts:
-            s.step(d, sync=False)
-        s.check()
-        out[f"{prec}_l1_vs_oracle"] = float(l1_errors(s.all_cons(), ref).max())
-        s.close()
     return out
 
 
@@ -315,6 +374,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--parity-steps", type=int, default=100,
+                    help="RK2 steps of the full-size comparison with the oracle (the oracle's first --cpu-steps "
+                         "steps are the timed CPU baseline)")
     ap.add_argument("--only", default="",
                     help="comma list of phases: fp32,tiled,fp64,fluxrec,weno3,plain,e2e,amr,amr32,mhd,adaptive (default: "
                          "all but amr32)")
@@ -405,6 +467,21 @@ def main():
     achieved = stage_bytes / ((t1 + t2) / ksteps / 1e3) / 1e9
     peak, peak_kind = peaks()
     step_kernel_ms = {k: round(v[0] / ksteps, 4) for k, v in tm.items() if v[1]}
+    # issue ceiling: the profiled warp instructions per cell-update issued at one per cycle
+    # by each of the 4 schedulers of every SM, at the median SM clock of the timed region
+    prof = stage_profile()
+    clocks = clk.summary()
+    issue = None
+    if prof["warp_inst_per_cell_update"] and clocks.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        t_issue = prof["warp_inst_per_cell_update"] * cells / (sms * 4 * clocks["sm_mhz"] * 1e6)
+        t_stage = (t1 + t2) / ksteps / 1e3
+        issue = {"warp_inst_per_cell_update": prof["warp_inst_per_cell_update"], "sms": sms,
+                 "sm_mhz": clocks["sm_mhz"], "min_stage_ms_per_step": t_issue * 1e3,
+                 "frac": t_issue / t_stage,
+                 "note": "stage 1 + stage 2 time at one warp instruction per cycle per scheduler "
+                         "(instruction count from the committed ncu capture) over the measured time"}
+    alu = NV.amr_peak_fma_rates()
     s.close()
 
     sub = min(args.steps, 200)   # step counts of the other workloads follow this, not the headline's
@@ -464,8 +541,9 @@ def main():
         so.autotune()
         for _ in range(2):
             so.step(0.0, sync=False)
-        kw3 = max(3, sub // 4)
-        tw3 = timed_steps(torch, so, stream, kw3)
+        kw3 = max(3, sub)
+        with ClockSampler(local) as clk3:
+            tw3 = timed_steps(torch, so, stream, kw3)
         NV.amr_set_timing(so.h, True)
         for _ in range(ksteps):
             so.step(0.0, sync=False)
@@ -477,7 +555,7 @@ def main():
         extra["weno3_fp32"] = {
             "value": ws * cells * kw3 / max_over_ranks(tw3), "unit": UNIT, "steps": kw3,
             "stage_ms": {"stage1": round(tmw["stage1"][0] / ksteps, 4), "stage2": round(tmw["stage2"][0] / ksteps, 4)},
-            "stage_hbm_frac": stage_bytes / (tsw / 1e3) / 1e9 / peak,
+            "stage_hbm_frac": stage_bytes / (tsw / 1e3) / 1e9 / peak, "clocks": clk3.summary(),
             "workload": "Kelvin-Helmholtz 256^3 single patch, FP32, HLL on third-order WENO face states "
                         "(recon=weno3), batched + graph"}
 
@@ -505,11 +583,22 @@ def main():
             "workload": "Kelvin-Helmholtz 256^3 single patch, FP32, riemann=fluxrec (Lax-Friedrichs split fluxes "
                         "reconstructed by PLM), batched + graph"}
     if "plain" in phases:
+        plain = "512 patches of 32^3, one stage-kernel and ghost-copy launch per patch, no graph"
         extra["fp64_plain"] = {"value": rate(tiled, "fp64", False, False, k64), "unit": UNIT, "steps": k64,
-                               "workload": "512 patches of 32^3, one stage-kernel and ghost-copy launch per patch, "
-                                           "no graph"}
+                               "workload": plain}
+        extra["fp32_plain"] = {"value": rate(tiled, "fp32", False, False, k64), "unit": UNIT, "steps": k64,
+                               "workload": plain}
+        extra["fp64_batched_tiled_512"] = {"value": rate(tiled, "fp64", True, True, k64), "unit": UNIT,
+                                           "steps": k64, "workload": "512 patches of 32^3, batched + graph"}
         if "fp32_tiled_512" in extra:
-            extra["batched_fp32_over_plain_fp64"] = extra["fp32_tiled_512"]["value"] / extra["fp64_plain"]["value"]
+            b32, p32 = extra["fp32_tiled_512"]["value"], extra["fp32_plain"]["value"]
+            b64, p64 = extra["fp64_batched_tiled_512"]["value"], extra["fp64_plain"]["value"]
+            extra["batched_fp32_over_plain_fp64"] = b32 / p64
+            extra["speedup_decomposition_kh512"] = {
+                "batched_fp32_over_plain_fp64": b32 / p64,
+                "batching_at_fp32": b32 / p32, "batching_at_fp64": b64 / p64,
+                "precision_batched": b32 / b64, "precision_plain": p32 / p64,
+                "note": "batched FP32 / plain FP64 = batching x precision, taken in either order"}
 
     def amr_rates(pb, label, fp64_plain_steps=1):
         """Cell-updates/s (sum over levels of cells_l 2^l per coarse step) of the batched FP32
@@ -528,18 +617,32 @@ def main():
         NV.amr_set_timing(so.h, False)
         so.check()
         so.close()
-        out = {"value": ws * cu * ka / max_over_ranks(t), "unit": UNIT, "steps": ka, "patches": len(pb.patches),
+        value = ws * cu * ka / max_over_ranks(t)
+        bpc = 5 * pb.nvar * 4              # algorithmic bytes per cell-update, FP32
+        out = {"value": value, "unit": UNIT, "steps": ka, "patches": len(pb.patches),
                "levels": pb.nlevels, "cell_updates_per_coarse_step": cu,
                "class_ms_per_coarse_step": {k: round(v[0] / 2, 3) for k, v in tmk.items() if v[1]},
+               "roofline": {"bound": "hbm", "achieved": value / ws * bpc / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": value / ws * bpc / 1e9 / peak, "peak_kind": peak_kind,
+                            "algorithmic_bytes_per_cell_update": bpc,
+                            "note": "whole coarse step (every kernel class) against the interior cell-updates' "
+                                    "algorithmic bytes"},
                "workload": label}
         if fp64_plain_steps:
-            sp = make_solver(pb, "fp64", False, False, stream)
-            sp.step(0.0, sync=False)
-            tp = timed_steps(torch, sp, stream, fp64_plain_steps)
-            sp.check()
-            sp.close()
-            out["fp64_plain"] = ws * cu * fp64_plain_steps / max_over_ranks(tp)
-            out["batched_fp32_over_plain_fp64"] = out["value"] / out["fp64_plain"]
+            def one(precision, batched, steps):
+                sp = make_solver(pb, precision, batched, batched, stream)
+                sp.step(0.0, sync=False)
+                tp = timed_steps(torch, sp, stream, steps)
+                sp.check()
+                sp.close()
+                return ws * cu * steps / max_over_ranks(tp)
+            out["fp64_plain"] = one("fp64", False, fp64_plain_steps)
+            out["fp32_plain"] = one("fp32", False, 1)
+            out["fp64_batched"] = one("fp64", True, 2)
+            out["batched_fp32_over_plain_fp64"] = value / out["fp64_plain"]
+            out["speedup_decomposition"] = {
+                "batching_at_fp32": value / out["fp32_plain"], "batching_at_fp64": out["fp64_batched"] / out["fp64_plain"],
+                "precision_batched": value / out["fp64_batched"], "precision_plain": out["fp32_plain"] / out["fp64_plain"]}
         return out
 
     if "amr" in phases or "amr32" in phases:
@@ -639,7 +742,8 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu else cpu_baseline(args.cpu_steps, stream)
+    cpu = None if args.no_cpu else cpu_baseline(args.cpu_steps, max(args.parity_steps, args.cpu_steps), stream,
+                                                chosen_tiling(tune_report))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -661,7 +765,10 @@ def main():
                      "timed_steps": ksteps,
                      "frac_of_nominal_7900": achieved / 7900.0,
                      "traffic_bytes_per_cell_update": (None if stage_traffic() is None
-                                                       else 2 * stage_traffic() / cells)},
+                                                       else 2 * stage_traffic() / cells),
+                     "issue_ceiling": issue,
+                     "alu_peaks_tflops": {"fp32_fma": alu["fp32_flops"] / 1e12,
+                                          "fp64_fma": alu["fp64_flops"] / 1e12}},
         "step_ms_median": statistics.median(per_step),
         "step_kernel_ms": step_kernel_ms,
         "autotune": [l for l in tune_report.splitlines() if l],
@@ -670,8 +777,9 @@ def main():
                                "the FP32 state over the timed steps (periodic box)"},
         "e2e": e2e,
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "cpu_baseline": cpu,
+        "parity": None if cpu is None else cpu.pop("parity"),
     }
     print(json.dumps(line), flush=True)
 

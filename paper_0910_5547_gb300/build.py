@@ -24,6 +24,7 @@ FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 UNITS = [
     ("amr_api.cu", []),
     ("amr_noalloc.cu", []),
+    ("peak_probe.cu", []),
     ("ops_f64_euler.cu", []),
     ("ops_f32_euler.cu", FP32_FLAGS),
     ("ops_f64_mhd.cu", []),
