@@ -221,14 +221,15 @@ def parity_errors(got, ref):
 
 
 def chosen_tiling(report: str):
-    """(max_wx, max_cols, zchunk, ctas_per_sm) of the candidate the autotuner kept."""
+    """(max_wx, max_cols, zchunk, ctas_per_sm, persistent) of the candidate the autotuner kept."""
     import re
     lines = [l for l in report.splitlines() if l.startswith("tile ")]
     m = re.search(r"chosen: candidate (\d+)", report)
     if not m:
         return None
-    t = re.match(r"tile wx<=(\d+) cols<=(\d+) z=(\d+) ctas/SM=(\d+)", lines[int(m.group(1))])
-    return tuple(int(x) for x in t.groups()) if t else None
+    line = lines[int(m.group(1))]
+    t = re.match(r"tile wx<=(\d+) cols<=(\d+) z=(\d+) ctas/SM=(\d+)", line)
+    return tuple(int(x) for x in t.groups()) + (1 if " persistent" in line else 0,) if t else None
 
 
 def cpu_model():
@@ -282,7 +283,8 @@ def cpu_baseline(steps, parity_steps, stream, tiling):
         for name, prob in (("single_256", single), ("tiled_512", pb)):
             s = make_solver(prob, prec, True, True, stream)
             if name == "single_256" and tiling and prec == "fp32":
-                s.set_tiling(*tiling)
+                s.set_tiling(*tiling[:4])
+                s.set_persistent(tiling[4])
             for d in dts:
                 s.step(d, sync=False)
             s.check()
@@ -605,7 +607,7 @@ def main():
         path and the plain per-patch FP64 path on a multi-level hierarchy, plus kernel-class times."""
         cu = pb.cell_updates_per_coarse_step()
         so = make_solver(pb, "fp32", True, True, stream)
-        so.autotune()
+        chosen = chosen_tiling(so.autotune())
         for _ in range(2):
             so.step(0.0, sync=False)
         ka = max(3, sub // 20)
@@ -628,6 +630,19 @@ def main():
                             "note": "whole coarse step (every kernel class) against the interior cell-updates' "
                                     "algorithmic bytes"},
                "workload": label}
+        if chosen:
+            # the other stage launch form (persistent CTAs or one CTA per work item), same tiling
+            so = make_solver(pb, "fp32", True, True, stream)
+            so.set_tiling(*chosen[:4])
+            so.set_persistent(1 - chosen[4])
+            for _ in range(2):
+                so.step(0.0, sync=False)
+            t_other = timed_steps(torch, so, stream, ka)
+            so.check()
+            so.close()
+            out["launch_form"] = {"chosen": "persistent" if chosen[4] else "one CTA per item",
+                                  "tiling": list(chosen[:4]),
+                                  "other_form_value": ws * cu * ka / max_over_ranks(t_other)}
         if fp64_plain_steps:
             def one(precision, batched, steps):
                 sp = make_solver(pb, precision, batched, batched, stream)

@@ -220,6 +220,17 @@ amr_status amr_set_regrid_schedule(amr_handle* h, const amr_regrid_params* prm, 
  * tiling stays).  Invalidates the step graphs. */
 amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, int ctas_per_sm);
 
+/* Launch form of the batched stage kernels (a scheduling choice; the paper,
+ * which sends one grid at a time to the GPU (Sec. 3), has no counterpart):
+ *   0: one CTA per work item (a level's launch has as many CTAs as items);
+ *   1: persistent -- one wave of resident CTAs (SMs x CTAs per SM of the build
+ *      in use) that take the level's items one after another from a counter in
+ *      device memory (an atomic fetch per item; no CTA waits on another);
+ *  -1: the autotuner times both forms and keeps the faster (default; before
+ *      amr_autotune runs, one CTA per item).
+ * Same results bit for bit.  AMR_ERR_ARG for another mode. */
+amr_status amr_set_persistent(amr_handle* h, int mode);
+
 /* Autotuner: time the stage kernel over the installed hierarchy for each
  * candidate work-item shape (x width, columns per CTA, z chunk) and compiled
  * build (resident CTAs per SM, as listed at amr_set_tiling) and keep the fastest for

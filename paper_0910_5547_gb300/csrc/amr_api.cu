@@ -161,6 +161,8 @@ struct amr_handle {
   // stage-kernel work items (own buffer: the autotuner swaps the tiling)
   StageItem* items_dev = nullptr;
   TileParams tp;            // tile shape in use (autotuned or default)
+  int sms = 0;              // SMs of the device (persistent stage grids)
+  int persist_mode = -1;    // -1: the autotuner decides; 0 / 1: one CTA per item / persistent CTAs
   // optional per-class event timing (eager steps only)
   bool timing = false;
   int cur_class = 0;
@@ -466,7 +468,9 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
   h->cur_class = s == 1 ? AMR_T_STAGE1 : AMR_T_STAGE2;
   const int fuse = (s == 2 && h->dl.size() == 1) ? 1 : 0;
   if (h->cfg.batched) {
-    LK(h->ops->stage(s, h->stream, h->d_desc, L.items, L.nitems, in, out, h->params, l, dx, h->dx0, fuse, 0));
+    // persistent: one wave of resident CTAs takes the level's items from a device counter
+    const int grid = h->tp.persistent ? h->sms * h->ops->resident_ctas() : 0;
+    LK(h->ops->stage(s, h->stream, h->d_desc, L.items, L.nitems, in, out, h->params, l, dx, h->dx0, fuse, grid));
   } else {
     for (int p = 0; p < LP.count; ++p) {
       int a = LP.item_first[p], b = LP.item_first[p + 1];
@@ -1197,6 +1201,16 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
     h->own_stream = true;
   }
   h->ops = make_ops(*cfg);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+      cudaGetLastError();
+      g_global_err = "device query failed";
+      amr_destroy(h);
+      return AMR_ERR_CUDA;
+    }
+  }
   if (!(cfg->dev_alloc && cfg->dev_free)) {
     int dev = 0;
     cudaError_t pe = cudaGetDevice(&dev);
@@ -1391,6 +1405,7 @@ amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, i
   h->tp.max_wx = max_wx;
   h->tp.max_cols = max_cols;
   h->tp.zchunk = zchunk;
+  h->tp.persistent = h->persist_mode == 1 ? 1 : 0;
   for (int g = 0; g < 4; ++g) {
     if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
     h->graph[g] = nullptr;
@@ -1398,6 +1413,20 @@ amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, i
   if (!h->ready) return AMR_OK;
   build_items(h->plan, h->tp);
   return upload_items(h);
+}
+
+amr_status amr_set_persistent(amr_handle* h, int mode) {
+  if (!h) return AMR_ERR_ARG;
+  if (mode < -1 || mode > 1) return fail(h, AMR_ERR_ARG, "mode must be -1, 0 or 1");
+  h->persist_mode = mode;
+  if (mode >= 0 && h->tp.persistent != mode) {
+    h->tp.persistent = mode;
+    for (int g = 0; g < 4; ++g) {
+      if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+      h->graph[g] = nullptr;
+    }
+  }
+  return AMR_OK;
 }
 
 amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
@@ -1412,14 +1441,20 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
   // the WENO3 stage runs one build (256 threads, default register budget) for every
   // tiling, so only the work-item shapes are tuned
   const bool one_build = h->cfg.recon == AMR_WENO3;
-  for (int o = 0; o < 2; ++o) {
-    if (o == 1 && (occs[1] == 0 || one_build)) continue;
-    for (auto& sh : shapes) {
-      if (o == 1 && sh[1] == 128 && !h->ops->has_alt128()) continue;   // no second 128-thread budget
-      Cand c;
-      c.tp.max_wx = sh[0]; c.tp.max_cols = sh[1]; c.tp.zchunk = sh[2];
-      c.occ = occs[o];
-      cands.push_back(c);
+  // launch forms: one CTA per work item, and persistent CTAs fed by a device
+  // counter (default build only), unless amr_set_persistent fixed one
+  for (int pers = 0; pers < 2; ++pers) {
+    if (h->persist_mode >= 0 && pers != h->persist_mode) continue;
+    for (int o = 0; o < 2; ++o) {
+      if (o == 1 && (occs[1] == 0 || one_build || pers == 1)) continue;
+      for (auto& sh : shapes) {
+        if (o == 1 && sh[1] == 128 && !h->ops->has_alt128()) continue;   // no second 128-thread budget
+        Cand c;
+        c.tp.max_wx = sh[0]; c.tp.max_cols = sh[1]; c.tp.zchunk = sh[2];
+        c.tp.persistent = pers;
+        c.occ = occs[o];
+        cands.push_back(c);
+      }
     }
   }
   // valid ghosts everywhere (stage 1 reads them; U1 is scratch, U is not modified)
@@ -1454,9 +1489,9 @@ amr_status amr_autotune(amr_handle* h, char* report, int report_len) {
       if (rep_i > 0) t_best = std::min(t_best, (double)ms);   // first run warms up
     }
     char line[160];
-    std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d: %.4f ms%s\n", h->tp.max_wx,
-                  h->tp.max_cols, h->tp.zchunk, h->ops->resident_ctas(), t_best,
-                  one_build ? " (WENO3: default 256-thread build)" : "");
+    std::snprintf(line, sizeof line, "tile wx<=%d cols<=%d z=%d ctas/SM=%d%s: %.4f ms%s\n", h->tp.max_wx,
+                  h->tp.max_cols, h->tp.zchunk, h->ops->resident_ctas(), h->tp.persistent ? " persistent" : "",
+                  t_best, one_build ? " (WENO3: default 256-thread build)" : "");
     rep += line;
     if (t_best < best) { best = t_best; best_i = (int)ci; }
   }

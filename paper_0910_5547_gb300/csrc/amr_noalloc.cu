@@ -163,6 +163,7 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   a.idy0 = 1.0 / dx[1];
   a.idz0 = 1.0 / dx[2];
   a.fuse_rate = 0;
+  a.dynamic = 0;
   a.ph = ph;
   const int nseg = (int)L.ghost.size();
   const int gseg = nseg < 65535 ? nseg : 65535;

@@ -175,6 +175,10 @@ struct StepParams {
   unsigned long long next_rate_bits;
   unsigned long long next_speed_bits;
   unsigned long long floor_hits;   // interior primitive recoveries raised by the pressure floor
+  // persistent stage launches: next work item to hand out and CTAs finished
+  // (zero between launches: the last CTA of a launch resets them)
+  unsigned int work_next;
+  unsigned int work_done;
 };
 
 }  // namespace amr

@@ -95,6 +95,7 @@ struct TileParams {
   int max_wx = 0;
   int max_cols = 0;
   int zchunk = 0;
+  int persistent = 0;   // batched stages: persistent CTAs taking items from a device counter
 };
 
 // Regridding: cluster cells flagged on levels min_level .. max_level-1 into the

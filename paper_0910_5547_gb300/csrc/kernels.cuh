@@ -180,6 +180,7 @@ struct StageArgs {
   T idx, idy, idz;   // 1 / dx of the level
   double idx0, idy0, idz0;  // 1 / dx of level 0 (CFL rate)
   int fuse_rate;     // stage 2: accumulate the CFL rate of the new state
+  int dynamic;       // persistent CTAs take items from params->work_next (stage_kernel)
   Phys<T> ph;
 };
 
@@ -285,7 +286,16 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     damp = (T)exp(-(double)a.ph.glm_alpha * a.params->ch * a.params->dt0 * idmax);
   }
 
-  for (int itn = blockIdx.x; itn < a.nitems; itn += gridDim.x) {
+  // work items: one per CTA, or (a.dynamic) persistent CTAs that take the next
+  // item from a device counter until none is left
+  __shared__ int s_next;
+  int itn = blockIdx.x;
+  if (a.dynamic) {
+    if (t == 0) s_next = (int)atomicAdd(&a.params->work_next, 1u);
+    __syncthreads();
+    itn = s_next;
+  }
+  for (; itn < a.nitems;) {
     const StageItem it = a.items[itn];
     const PatchDesc P = a.desc[it.patch];
     const int wx = it.wx, wy = it.wy, wz = it.wz;
@@ -641,6 +651,22 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         sstore<T, NV, kState>(dst, bslot, w0);
       }
       __syncthreads();
+    }
+    if (a.dynamic) {   // every thread has read s_next (barriers since); fetch the next item
+      if (t == 0) s_next = (int)atomicAdd(&a.params->work_next, 1u);
+      __syncthreads();
+      itn = s_next;
+    } else {
+      itn += gridDim.x;
+    }
+  }
+  if (a.dynamic && t == 0) {
+    // the last CTA to finish (all CTAs have made their final fetch) resets the
+    // counters for the next launch on the stream
+    __threadfence();
+    if (atomicAdd(&a.params->work_done, 1u) == gridDim.x - 1) {
+      a.params->work_next = 0u;
+      a.params->work_done = 0u;
     }
   }
   if (bad) atomicOr(&a.params->bad, 1u);

@@ -93,6 +93,8 @@ struct Ops final : OpsBase {
     a.idz0 = 1.0 / dx0[2];
     a.fuse_rate = fuse_rate;
     a.ph = ph;
+    // grid > 0: that many persistent CTAs, items handed out by a device counter
+    a.dynamic = grid > 0 ? 1 : 0;
     const int g = grid > 0 ? (grid < nitems ? grid : nitems) : nitems;
     if constexpr (NV == 5) {
       if (ph.fluxrec) {

@@ -116,6 +116,10 @@ class Solver:
         """Fix the stage-kernel work items and build instead of autotuning (0 = default)."""
         N.amr_set_tiling(self.h, max_wx, max_cols, zchunk, ctas_per_sm)
 
+    def set_persistent(self, mode: int) -> None:
+        """Stage launch form: 0 one CTA per work item, 1 persistent CTAs, -1 the autotuner decides."""
+        N.amr_set_persistent(self.h, mode)
+
     def autotune(self) -> str:
         """Time the stage kernel's candidate tilings on this hierarchy and keep the fastest."""
         return N.amr_autotune(self.h)
