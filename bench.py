@@ -212,12 +212,14 @@ def parity_errors(got, ref):
         den += a.sum(axis=1)
         mx = np.maximum(mx, d.max(axis=1))
         rmx = np.maximum(rmx, a.max(axis=1))
+    ref_norm = den.copy()
     vden = den.copy()
     vden[1:4] = den[1:4].sum()
     den[den < 1e-12 * den[0]] = den[0]
     rmx[rmx < 1e-12 * rmx[0]] = rmx[0]
     return {"l1_vector_metric": float((num / vden).max()), "l1_per_variable": [float(x) for x in num / den],
-            "max_per_variable": [float(x) for x in mx / rmx]}
+            "max_per_variable": [float(x) for x in mx / rmx],
+            "reference_l1_norm_per_variable": [float(x) for x in ref_norm]}
 
 
 def chosen_tiling(report: str):
@@ -376,6 +378,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--tiling", default="",
+                    help="max_wx,max_cols,zchunk,ctas_per_sm,persistent for the headline solver instead of the "
+                         "autotuner's choice (reproducible profiles)")
     ap.add_argument("--parity-steps", type=int, default=100,
                     help="RK2 steps of the full-size comparison with the oracle (the oracle's first --cpu-steps "
                          "steps are the timed CPU baseline)")
@@ -433,7 +438,14 @@ def main():
 
     # ---- headline: single-patch batched FP32, graph replay, CFL every step ----
     s = make_solver(single, "fp32", True, True, stream)
-    tune_report = s.autotune()
+    if args.tiling:
+        fixed = [int(x) for x in args.tiling.split(",")]
+        s.set_tiling(*fixed[:4])
+        s.set_persistent(fixed[4] if len(fixed) > 4 else 0)
+        tune_report = ("tile wx<=%d cols<=%d z=%d ctas/SM=%d%s: fixed\nchosen: candidate 0\n"
+                       % (*fixed[:4], " persistent" if len(fixed) > 4 and fixed[4] else ""))
+    else:
+        tune_report = s.autotune()
     for _ in range(args.warmup):
         s.step(0.0, sync=False)
     torch.cuda.synchronize()

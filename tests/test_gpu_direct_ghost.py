@@ -87,3 +87,17 @@ def test_mid_step_rebuilds():
         s.close()
     assert out[0][1] == out[1][1]
     same(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_coarse_fine_faces_on_coarse_patch_boundaries(precision):
+    """A fine block whose footprint is exactly one coarse patch: every coarse-fine
+    face lies on a face of a neighbouring coarse patch, so the coarse-side flux
+    register stencils reach into those patches' ghost cells (those faces must
+    keep copied ghost cells)."""
+    patches = ai.uniform_patches((16, 16, 16), (8, 8, 8))
+    patches += [ai.Patch(1, (x, y, z), (8, 8, 8)) for z in (16, 24) for y in (16, 24) for x in (16, 24)]
+    pb = ai.random_smooth(patches, (16,) * 3, seed=12, amp=0.2)
+    same(*run(pb, 3, precision=precision))
+    pb9 = ai.random_smooth(patches, (16,) * 3, nvar=9, seed=13, amp=0.2)
+    same(*run(pb9, 2, precision=precision))
