@@ -67,13 +67,11 @@ __global__ void finalize_speed_kernel(StepParams* params, double cfl, double ch_
 __global__ void set_dt_kernel(StepParams* params, double dt) { params->dt0 = dt; }
 
 struct DevLevel {
-  int nitems = 0, nghost = 0, nghost_stage = 0, nprolong = 0, ngather = 0, ngather_ghost = 0, nrestrict = 0,
-      nreg = 0, nuniq = 0;
+  int nitems = 0, nghost = 0, nghost_stage = 0, nprolong = 0, ngather_ghost = 0, nrestrict = 0, nreg = 0, nuniq = 0;
   const StageItem* items = nullptr;
   const CopySeg* ghost = nullptr;          // every face ghost segment (diagnostics, regrid flags)
   const CopySeg* ghost_stage = nullptr;    // the faces a stage does not read directly
   const ProlongBox* prolong = nullptr;
-  const CopySeg* gather = nullptr;         // whole parent tiles (regrid fill)
   const CopySeg* gather_ghost = nullptr;   // the tile cells the per-stage prolongation reads
   const RestrictSeg* restrict_segs = nullptr;
   const RegFace* regs = nullptr;
@@ -761,7 +759,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
   size_t o_lvol = buf.add(lvol);
   struct FlatOffs { size_t boxes, first, chunk; };
-  struct Offs { size_t items, ghost, ghost_stage, prolong, gather, gather_ghost, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
+  struct Offs { size_t items, ghost, ghost_stage, prolong, gather_ghost, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
   std::vector<Offs> lo(nlev);
   auto put_flat = [&](const auto& f) { return FlatOffs{buf.add(f.boxes), buf.add(f.first), buf.add(f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
@@ -773,7 +771,6 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     lo[l].ghost = buf.add(L.ghost);
     lo[l].ghost_stage = buf.add(L.ghost_stage);
     lo[l].prolong = buf.add(L.prolong);
-    lo[l].gather = buf.add(L.gather);
     lo[l].gather_ghost = buf.add(L.gather_ghost);
     lo[l].restr = buf.add(L.restrict_segs);
     lo[l].regs = buf.add(L.regs);
@@ -816,7 +813,6 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     D.nghost = (int)L.ghost.size();
     D.nghost_stage = (int)L.ghost_stage.size();
     D.nprolong = (int)L.prolong.size();
-    D.ngather = (int)L.gather.size();
     D.ngather_ghost = (int)L.gather_ghost.size();
     D.nrestrict = (int)L.restrict_segs.size();
     D.nreg = (int)L.regs.size();
@@ -824,7 +820,6 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
     D.ghost_stage = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost_stage);
     D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
-    D.gather = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather);
     D.gather_ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather_ghost);
     D.restrict_segs = reinterpret_cast<const RestrictSeg*>(h->tables + lo[l].restr);
     D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
@@ -1068,6 +1063,9 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   lap(AMR_RG_PLAN);
   RegridFill fill;
   build_regrid_fill(op.patches, newp, rp.min_level, fill);
+  std::vector<std::vector<CopySeg>> fill_gather;   // parent cells of the fresh boxes' prolongation
+  build_fill_gathers(h->cfg, np, fill.fresh, fill_gather, msg);
+  if (!msg.empty()) return fail(h, AMR_ERR_NESTING, "regrid fill: " + msg);
   lap(AMR_RG_FILLTAB);
   // 4. new device state, filled from the old one
   const PatchDesc* old_desc = h->d_desc;
@@ -1091,7 +1089,7 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
     return st;
   }
   TablePack buf;
-  std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size());
+  std::vector<size_t> o_copy(fill.copy.size()), o_fresh(fill.fresh.size()), o_fg(fill.fresh.size());
   cudaError_t ei = cudaStreamSynchronize(h->stream);   // uploads of the new tables done
   if (ei != cudaSuccess) {
     free_bufs(h, old);
@@ -1101,6 +1099,7 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   for (size_t l = 0; l < fill.copy.size(); ++l) {
     o_copy[l] = buf.add(fill.copy[l]);
     o_fresh[l] = buf.add(fill.fresh[l]);
+    o_fg[l] = buf.add(fill_gather[l]);
   }
   unsigned char* d_fill = nullptr;
   cudaError_t e = dmalloc(h, reinterpret_cast<void**>(&d_fill), buf.size);
@@ -1120,7 +1119,9 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   for (int l = rp.min_level + 1; l < nl_new && e == cudaSuccess; ++l) {
     const DevLevel& L = h->dl[l];
     // interior cells no old patch covers: conservative prolongation from the (new) parent level
-    e = h->ops->gather(h->stream, L.gather, L.ngather, h->d_desc, h->tile, h->U, h->U, 1.0);
+    if (l < (int)fill.fresh.size())
+      e = h->ops->gather(h->stream, reinterpret_cast<const CopySeg*>(d_fill + o_fg[l]), (int)fill_gather[l].size(),
+                         h->d_desc, h->tile, h->U, h->U, 1.0);
     if (e == cudaSuccess && l < (int)fill.fresh.size())
       e = h->ops->prolong(h->stream, reinterpret_cast<const ProlongBox*>(d_fill + o_fresh[l]),
                           (int)fill.fresh[l].size(), h->d_desc, h->tile, h->U);

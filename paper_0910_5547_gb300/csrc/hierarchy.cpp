@@ -728,6 +728,157 @@ std::vector<int> morton_partition(const amr_config& cfg, const std::vector<HPatc
   return owner;
 }
 
+// Gather segments into the parent tile of fine patch i (level l >= 1) for the
+// tile cells that the prolongation of `boxes` (fine local cells of patch i)
+// reads: the parents of those cells and their face neighbours (the minmod
+// stencil), as disjoint boxes of the tile, each split over the parent-level
+// patches (periodic images, outflow clamps) that hold it.  cix indexes level
+// l - 1.  err is set if a needed parent cell lies outside level l - 1.
+void prolong_gathers(const amr_config& cfg, const Plan& plan, const PatchIndex& cix, int i, const ProlongBox* boxes,
+                     int nbox, std::vector<CopySeg>& out, std::string& err) {
+  const std::vector<HPatch>& P = plan.patches;
+  const HPatch& p = P[i];
+  const PatchDesc& dsc = plan.desc[i];
+  const int l = p.level;
+  struct Piece { int a, len, mode, src; };
+  std::vector<int> cand;
+  // gathers of the tile cells [blo, bhi) per axis; returns the cells covered
+  auto gather_box = [&](const int* blo, const int* bhi) -> int64_t {
+    std::vector<Piece> pieces[3];
+    for (int d = 0; d < 3; ++d) {
+      const int Nc = level_n(cfg, l - 1, d);
+      const int T0 = p.lo[d] / 2 - 2;
+      int t = blo[d];
+      while (t < bhi[d]) {
+        const int Cg = T0 + t;
+        const int kind = Cg < 0 ? 0 : (Cg < Nc ? 1 : 2);
+        int e = t;
+        while (e < bhi[d]) {
+          const int Cc = T0 + e;
+          if ((Cc < 0 ? 0 : (Cc < Nc ? 1 : 2)) != kind) break;
+          ++e;
+        }
+        Piece pc{t, e - t, 0, 0};
+        if (kind == 1) { pc.mode = 0; pc.src = Cg; }
+        else if (periodic(cfg, d)) { pc.mode = 0; pc.src = kind == 0 ? Cg + Nc : Cg - Nc; }
+        else { pc.mode = 1; pc.src = kind == 0 ? 0 : Nc - 1; }
+        pieces[d].push_back(pc);
+        t = e;
+      }
+    }
+    int64_t covered = 0;
+    for (auto& p0 : pieces[0])
+      for (auto& p1 : pieces[1])
+        for (auto& p2 : pieces[2]) {
+          const Piece* pp[3] = {&p0, &p1, &p2};
+          int qlo[3], qhi[3];
+          for (int d = 0; d < 3; ++d) {
+            qlo[d] = pp[d]->src;
+            qhi[d] = pp[d]->mode == 1 ? pp[d]->src + 1 : pp[d]->src + pp[d]->len;
+          }
+          cix.query(qlo, qhi, cand);
+          for (int q : cand) {
+            const HPatch& o = P[q];
+            CopySeg s{};
+            s.dst_patch = i; s.src_patch = q;
+            bool ok = true;
+            int64_t vol = 1;
+            for (int d = 0; d < 3 && ok; ++d) {
+              const Piece& pc = *pp[d];
+              if (pc.mode == 1) {
+                if (pc.src < o.lo[d] || pc.src >= o.lo[d] + o.n[d]) { ok = false; break; }
+                s.dlo[d] = (int16_t)pc.a; s.dn[d] = (int16_t)pc.len; s.mode[d] = 1;
+                s.sh[d] = (int16_t)(pc.src - o.lo[d]);
+                vol *= pc.len;
+              } else {
+                const int a = std::max(pc.src, o.lo[d]), b = std::min(pc.src + pc.len, o.lo[d] + o.n[d]);
+                if (a >= b) { ok = false; break; }
+                const int dst0 = pc.a + (a - pc.src);
+                s.dlo[d] = (int16_t)dst0; s.dn[d] = (int16_t)(b - a); s.mode[d] = 0;
+                s.sh[d] = (int16_t)((a - o.lo[d]) - dst0);
+                vol *= (b - a);
+              }
+            }
+            if (!ok) continue;
+            covered += vol;
+            out.push_back(s);
+          }
+        }
+    return covered;
+  };
+  std::vector<unsigned char> need((size_t)dsc.tn[0] * dsc.tn[1] * dsc.tn[2], 0);
+  int64_t nneed = 0;
+  int blo_all[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, bhi_all[3] = {-1, -1, -1};   // bounding box (inclusive)
+  for (int b = 0; b < nbox; ++b) {
+    const ProlongBox& pb = boxes[b];
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      const int t0 = ((p.lo[a] + pb.lo[a]) >> 1) - (p.lo[a] >> 1) + 2;
+      const int t1 = ((p.lo[a] + pb.lo[a] + pb.n[a] - 1) >> 1) - (p.lo[a] >> 1) + 2;
+      lo[a] = std::max(t0 - 1, 0);
+      hi[a] = std::min(t1 + 1, dsc.tn[a] - 1);
+      blo_all[a] = std::min(blo_all[a], lo[a]);
+      bhi_all[a] = std::max(bhi_all[a], hi[a]);
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          unsigned char& m = need[((size_t)z * dsc.tn[1] + y) * dsc.tn[0] + x];
+          nneed += m ? 0 : 1;
+          m = 1;
+        }
+  }
+  if (nneed == 0) return;
+  const size_t first = out.size();
+  int64_t got = 0, want = nneed;
+  const int64_t bvol = (int64_t)(bhi_all[0] - blo_all[0] + 1) * (bhi_all[1] - blo_all[1] + 1) *
+                       (bhi_all[2] - blo_all[2] + 1);
+  if (2 * nneed >= bvol) {
+    // the needed cells fill at least half of their bounding box: gather the box
+    // (fewer, larger copies; the extra cells are read but never used)
+    const int blo[3] = {blo_all[0], blo_all[1], blo_all[2]};
+    const int bhi[3] = {bhi_all[0] + 1, bhi_all[1] + 1, bhi_all[2] + 1};
+    got = gather_box(blo, bhi);
+    want = bvol;
+  } else {
+    for (const Box3& bx : need_boxes(need, dsc.tn[0], dsc.tn[1], dsc.tn[2])) {
+      const int blo[3] = {bx.lo[0], bx.lo[1], bx.lo[2]};
+      const int bhi[3] = {bx.lo[0] + bx.n[0], bx.lo[1] + bx.n[1], bx.lo[2] + bx.n[2]};
+      got += gather_box(blo, bhi);
+    }
+  }
+  split_copy(out, first);
+  if (got != want) err = fmt("patch %d: parent cells of its prolongation not covered by level %d", i, l - 1);
+}
+
+void build_fill_gathers(const amr_config& cfg, const Plan& plan, const std::vector<std::vector<ProlongBox>>& fresh,
+                        std::vector<std::vector<CopySeg>>& out, std::string& msg) {
+  out.assign(fresh.size(), {});
+  for (size_t l = 1; l < fresh.size() && l < plan.levels.size(); ++l) {
+    const std::vector<ProlongBox>& F = fresh[l];
+    if (F.empty()) continue;
+    // the fresh boxes grouped by patch (they come grouped, patch by patch)
+    std::vector<std::pair<int, int>> runs;   // [begin, end) of each patch's boxes
+    for (int b = 0; b < (int)F.size();) {
+      int e = b + 1;
+      while (e < (int)F.size() && F[e].patch == F[b].patch) ++e;
+      runs.push_back({b, e});
+      b = e;
+    }
+    PatchIndex cix(plan.patches, plan.levels[l - 1].first, plan.levels[l - 1].count);
+    std::vector<std::vector<CopySeg>> segs(runs.size());
+    std::vector<std::string> err(runs.size());
+    parallel_for((int)runs.size(), [&](int r) {
+      prolong_gathers(cfg, plan, cix, F[runs[r].first].patch, F.data() + runs[r].first,
+                      runs[r].second - runs[r].first, segs[r], err[r]);
+    });
+    for (size_t r = 0; r < runs.size(); ++r) {
+      if (!err[r].empty() && msg.empty()) msg = err[r];
+      out[l].insert(out[l].end(), segs[r].begin(), segs[r].end());
+    }
+  }
+}
+
 // The stage kernel's view of a face read from the patch's own ghost cells.
 FaceSrc own_face(const PatchDesc& d) {
   FaceSrc f;
@@ -979,136 +1130,25 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     }
   }
 
-  // ---- parent-tile gathers (level >= 1): tile = footprint grown by 2 parent cells ----
+  // ---- parent-cell gathers (level >= 1) ----
+  // each stage gathers, time-interpolated, only the parent cells the
+  // prolongation of the patch's coarse-fine ghost cells reads (a patch whose
+  // ghost cells all come from siblings gathers nothing); the regrid fill
+  // gathers for its own prolongation boxes (build_fill_gathers)
   for (int l = 1; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
-    const LevelPlan& C = plan.levels[l - 1];
-    PatchIndex cix(P, C.first, C.count);
-    std::vector<std::vector<CopySeg>> as(L.count), gs_ghost(L.count);
+    PatchIndex cix(P, plan.levels[l - 1].first, plan.levels[l - 1].count);
+    std::vector<std::vector<CopySeg>> gs_ghost(L.count);
     std::vector<std::string> err(L.count);
     parallel_for(L.count, [&](int ii) {
-      const int i = L.first + ii;
-      std::vector<CopySeg>& Av = as[ii];
-      std::vector<int> cand;
-      const HPatch& p = P[i];
-      struct Piece { int a, len, mode, src; };
-      // gathers of the tile cells [blo, bhi) per axis into out; returns the cells covered
-      auto gather_box = [&](const int* blo, const int* bhi, std::vector<CopySeg>& out) -> int64_t {
-        std::vector<Piece> pieces[3];
-        for (int d = 0; d < 3; ++d) {
-          int Nc = level_n(cfg, l - 1, d);
-          int T0 = p.lo[d] / 2 - 2, tn = bhi[d];
-          int t = blo[d];
-          while (t < tn) {
-            int Cg = T0 + t;
-            int kind = Cg < 0 ? 0 : (Cg < Nc ? 1 : 2);
-            int e = t;
-            while (e < tn) {
-              int Cc = T0 + e;
-              int k2 = Cc < 0 ? 0 : (Cc < Nc ? 1 : 2);
-              if (k2 != kind) break;
-              ++e;
-            }
-            Piece pc{t, e - t, 0, 0};
-            if (kind == 1) { pc.mode = 0; pc.src = Cg; }
-            else if (periodic(cfg, d)) { pc.mode = 0; pc.src = kind == 0 ? Cg + Nc : Cg - Nc; }
-            else { pc.mode = 1; pc.src = kind == 0 ? 0 : Nc - 1; }
-            pieces[d].push_back(pc);
-            t = e;
-          }
-        }
-        int64_t covered = 0;
-        for (auto& p0 : pieces[0])
-          for (auto& p1 : pieces[1])
-            for (auto& p2 : pieces[2]) {
-              const Piece* pp[3] = {&p0, &p1, &p2};
-              {
-                int qlo[3], qhi[3];
-                for (int d = 0; d < 3; ++d) {
-                  qlo[d] = pp[d]->src;
-                  qhi[d] = pp[d]->mode == 1 ? pp[d]->src + 1 : pp[d]->src + pp[d]->len;
-                }
-                cix.query(qlo, qhi, cand);
-              }
-              for (int q : cand) {
-                const HPatch& o = P[q];
-                CopySeg s{};
-                s.dst_patch = i; s.src_patch = q;
-                bool ok = true;
-                int64_t vol = 1;
-                for (int d = 0; d < 3 && ok; ++d) {
-                  const Piece& pc = *pp[d];
-                  if (pc.mode == 1) {
-                    if (pc.src < o.lo[d] || pc.src >= o.lo[d] + o.n[d]) { ok = false; break; }
-                    s.dlo[d] = (int16_t)pc.a; s.dn[d] = (int16_t)pc.len; s.mode[d] = 1;
-                    s.sh[d] = (int16_t)(pc.src - o.lo[d]);
-                    vol *= pc.len;
-                  } else {
-                    int a = std::max(pc.src, o.lo[d]), b = std::min(pc.src + pc.len, o.lo[d] + o.n[d]);
-                    if (a >= b) { ok = false; break; }
-                    int dst0 = pc.a + (a - pc.src);
-                    s.dlo[d] = (int16_t)dst0; s.dn[d] = (int16_t)(b - a); s.mode[d] = 0;
-                    s.sh[d] = (int16_t)((a - o.lo[d]) - dst0);
-                    vol *= (b - a);
-                  }
-                }
-                if (!ok) continue;
-                covered += vol;
-                out.push_back(s);
-              }
-            }
-        return covered;
-      };
-      const PatchDesc& d = plan.desc[i];
-      {
-        const int blo[3] = {0, 0, 0}, bhi[3] = {d.tn[0], d.tn[1], d.tn[2]};
-        const int64_t covered = gather_box(blo, bhi, Av);
-        split_copy(Av, 0);
-        if (covered != (int64_t)d.tn[0] * d.tn[1] * d.tn[2])
-          err[ii] = fmt("patch %d: parent tile not covered by level %d", i, l - 1);
-      }
-      // the per-stage ghost fill reads only the parents of the prolongation boxes
-      // and their face neighbours (the minmod stencil): gather those tile cells
-      // (a patch whose ghost cells all come from siblings gathers nothing)
-      std::vector<unsigned char> need((size_t)d.tn[0] * d.tn[1] * d.tn[2], 0);
-      int64_t nneed = 0;
-      for (int b = L.prolong_first[ii]; b < L.prolong_first[ii + 1]; ++b) {
-        const ProlongBox& pb = L.prolong[b];
-        int lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {
-          const int t0 = ((p.lo[a] + pb.lo[a]) >> 1) - (p.lo[a] >> 1) + 2;
-          const int t1 = ((p.lo[a] + pb.lo[a] + pb.n[a] - 1) >> 1) - (p.lo[a] >> 1) + 2;
-          lo[a] = std::max(t0 - 1, 0);
-          hi[a] = std::min(t1 + 1, (int)d.tn[a] - 1);
-        }
-        for (int z = lo[2]; z <= hi[2]; ++z)
-          for (int y = lo[1]; y <= hi[1]; ++y)
-            for (int x = lo[0]; x <= hi[0]; ++x) {
-              unsigned char& m = need[((size_t)z * d.tn[1] + y) * d.tn[0] + x];
-              nneed += m ? 0 : 1;
-              m = 1;
-            }
-      }
-      if (nneed > 0) {
-        int64_t got = 0;
-        for (const Box3& bx : need_boxes(need, d.tn[0], d.tn[1], d.tn[2])) {
-          const int blo[3] = {bx.lo[0], bx.lo[1], bx.lo[2]};
-          const int bhi[3] = {bx.lo[0] + bx.n[0], bx.lo[1] + bx.n[1], bx.lo[2] + bx.n[2]};
-          got += gather_box(blo, bhi, gs_ghost[ii]);
-        }
-        split_copy(gs_ghost[ii], 0);
-        if (got != nneed && err[ii].empty())
-          err[ii] = fmt("patch %d: parent cells of its prolongation not covered by level %d", i, l - 1);
-      }
+      const int a = L.prolong_first[ii], b = L.prolong_first[ii + 1];
+      if (b > a) prolong_gathers(cfg, plan, cix, L.first + ii, L.prolong.data() + a, b - a, gs_ghost[ii], err[ii]);
     });
-    L.gather_first.push_back(0);
     for (int ii = 0; ii < L.count; ++ii) {
       if (!err[ii].empty()) {
         msg = err[ii];
         return AMR_ERR_NESTING;
       }
-      L.gather.insert(L.gather.end(), as[ii].begin(), as[ii].end());
-      L.gather_first.push_back((int)L.gather.size());
       L.gather_ghost.insert(L.gather_ghost.end(), gs_ghost[ii].begin(), gs_ghost[ii].end());
     }
   }
@@ -1295,12 +1335,22 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   // the coarse-side register flux reads two cells on either side of a coarse-fine
   // face: where that stencil leaves the coarse patch, its ghost cells are read,
   // so that face of the coarse patch keeps copied ghost cells
-  for (int l = 1; l < nlev && direct_ok; ++l)
-    for (const RegFace& r : plan.levels[l].regs) {
-      const int f = r.cidx[r.d] + (r.cside > 0 ? 1 : 0);   // face index between cells f-1 and f
-      if (f - 2 < 0) direct[r.cpatch][2 * r.d] = 0;
-      if (f + 1 >= P[r.cpatch].n[r.d]) direct[r.cpatch][2 * r.d + 1] = 0;
-    }
+  for (int l = 1; l < nlev && direct_ok; ++l) {
+    // the registers are sorted by coarse patch: one task per coarse patch over its range
+    const LevelPlan& L = plan.levels[l];
+    const int c0 = plan.levels[l - 1].first;
+    parallel_for(plan.levels[l - 1].count, [&](int c) {
+      const int cp = c0 + c;
+      auto lo = std::lower_bound(L.regs.begin(), L.regs.end(), cp,
+                                 [](const RegFace& r, int v) { return r.cpatch < v; });
+      for (auto it = lo; it != L.regs.end() && it->cpatch == cp; ++it) {
+        const RegFace& r = *it;
+        const int f = r.cidx[r.d] + (r.cside > 0 ? 1 : 0);   // face index between cells f-1 and f
+        if (f - 2 < 0) direct[cp][2 * r.d] = 0;
+        if (f + 1 >= P[cp].n[r.d]) direct[cp][2 * r.d + 1] = 0;
+      }
+    });
+  }
   for (int i = 0; i < np; ++i)
     for (int f = 0; f < 6; ++f)
       if (!direct[i][f]) plan.desc[i].face[f] = own_face(plan.desc[i]);

@@ -58,9 +58,8 @@ struct LevelPlan {
   std::vector<int> ghost_stage_first;        //   directly (desc.face), per patch (size count + 1)
   std::vector<ProlongBox> prolong;           // fine ghosts from the parent tile (level >= 1)
   std::vector<int> prolong_first;
-  std::vector<CopySeg> gather;               // parent-tile gathers (level >= 1), whole tiles, grouped by fine patch
-  std::vector<int> gather_first;             //   (the regrid fill prolongs whole new patches from them)
-  std::vector<CopySeg> gather_ghost;         // the part of each tile the per-stage prolongation reads
+  std::vector<CopySeg> gather_ghost;         // parent-cell gathers (level >= 1): the tile cells the per-stage
+                                             //   prolongation reads, grouped by fine patch
   std::vector<RestrictSeg> restrict_segs;    // this level -> parent (level >= 1)
   RegVec regs;                               // coarse-fine faces of this level (level >= 1), sorted by coarse cell
   std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell
@@ -146,6 +145,11 @@ struct RegridFill {
   std::vector<std::vector<CopySeg>> copy;       // per level
   std::vector<std::vector<ProlongBox>> fresh;   // per level
 };
+// Gathers into the parent tiles of the fresh (prolonged) boxes of a regrid fill,
+// per level; msg is set if a parent cell is missing.
+void build_fill_gathers(const amr_config& cfg, const Plan& plan, const std::vector<std::vector<ProlongBox>>& fresh,
+                        std::vector<std::vector<CopySeg>>& out, std::string& msg);
+
 void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch>& newp, int keep_level,
                        RegridFill& fill);
 
