@@ -1252,6 +1252,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             for (int y = y0; y < y1; ++y)
               for (int x = x0; x < x1; ++x) owner[(size_t)(y - b0) * A + (x - a0)] = q;
           }
+          Rv.reserve((size_t)A * B);
           for (int b = 0; b < B; ++b)
             for (int a = 0; a < A; ++a) {
               if (cov2[(size_t)b * A + a]) continue;
@@ -1314,9 +1315,12 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     // per coarse patch: sort by cell, count the unique cells (CSR built below)
     std::vector<int> nuniq(nc + 1, 0);
     parallel_for(nc, [&](int c) {
-      std::stable_sort(regs.begin() + start[c], regs.begin() + start[c + 1], [](const RegFace& x, const RegFace& y) {
-        return std::make_tuple(x.cidx[2], x.cidx[1], x.cidx[0]) < std::make_tuple(y.cidx[2], y.cidx[1], y.cidx[0]);
-      });
+      // (z, y, x) order of the coarse cell as one key (cell indices are >= 0)
+      auto key = [](const RegFace& r) {
+        return ((uint64_t)(uint16_t)r.cidx[2] << 32) | ((uint64_t)(uint16_t)r.cidx[1] << 16) | (uint16_t)r.cidx[0];
+      };
+      std::stable_sort(regs.begin() + start[c], regs.begin() + start[c + 1],
+                       [&](const RegFace& x, const RegFace& y) { return key(x) < key(y); });
       int u = 0;
       for (int e = start[c]; e < start[c + 1]; ++e)
         if (e == start[c] || !same_cell(regs[e], regs[e - 1])) ++u;

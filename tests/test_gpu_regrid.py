@@ -215,3 +215,27 @@ def test_flux_reconstruction_regrid_matches_the_oracle():
         assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
                [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"cycle {cycle}"
         assert_parity(s.all_cons(), o.all_cons(), o.patches, "fp64", f"fluxrec regrid {cycle}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_weno3_scheduled_midstep_regrid_matches_the_oracle(precision):
+    """Third-order WENO face states through the mid-step rebuilds of a regrid
+    schedule (finer levels rebuilt after every step of levels <= 1): the same
+    hierarchies as the oracle's, and the states within the parity tolerance."""
+    pb = clumpy(21, ai.PERIODIC)
+    o = orc.Oracle(pb, max_level=3, nthreads=8, recon=orc.WENO3)
+    s = Solver.from_problem(pb, precision=precision, max_level=3, recon="weno3")
+    o.step()
+    s.step()
+    o = rg.regrid(o, threshold=0.1)
+    s.regrid(threshold=0.1)
+    rg.set_regrid_schedule(o, 1, threshold=0.1)
+    s.set_regrid_schedule(1, threshold=0.1)
+    for k in range(2):
+        dt = o.step()
+        s.step(dt)
+        assert [(p.level, tuple(p.lo), tuple(p.n)) for p in s.patches] == \
+               [(p.level, tuple(p.lo), tuple(p.n)) for p in o.patches], f"coarse step {k}"
+        assert_parity(s.all_cons(), o.all_cons(), o.patches, precision, f"weno3 scheduled regrid {k}")
+    assert max(p.level for p in s.patches) >= 2
+    s.check()
