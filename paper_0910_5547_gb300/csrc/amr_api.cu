@@ -67,15 +67,18 @@ __global__ void finalize_speed_kernel(StepParams* params, double cfl, double ch_
 __global__ void set_dt_kernel(StepParams* params, double dt) { params->dt0 = dt; }
 
 struct DevLevel {
-  int nitems = 0, nghost = 0, nghost_stage = 0, nprolong = 0, ngather_ghost = 0, nrestrict = 0, nreg = 0, nuniq = 0;
+  int nitems = 0, nghost = 0, nghost_stage = 0, nprolong = 0, ngather_ghost = 0, nrestrict = 0, nreg = 0, nrect = 0;
   const StageItem* items = nullptr;
   const CopySeg* ghost = nullptr;          // every face ghost segment (diagnostics, regrid flags)
   const CopySeg* ghost_stage = nullptr;    // the faces a stage does not read directly
   const ProlongBox* prolong = nullptr;
   const CopySeg* gather_ghost = nullptr;   // the tile cells the per-stage prolongation reads
   const RestrictSeg* restrict_segs = nullptr;
-  const RegFace* regs = nullptr;
-  const int* reflux_first = nullptr;
+  const RegRect* regs = nullptr;           // register rectangles (flattened: reg_first, reg_chunk)
+  const int* reg_first = nullptr;
+  const int* reg_chunk = nullptr;
+  int reg_pass[7] = {0, 0, 0, 0, 0, 0, 0};  // reflux passes: registers of fine faces (d, side) = p / 2, p % 2
+  int reg_ordered[6] = {0, 0, 0, 0, 0, 0};  // pass p has rectangles sharing cells with others
   double* R = nullptr;  // registers: [2][nvar][nreg]
   // flattened boxes of the batched ghost copy, gather and prolongation launches
   struct Flat {
@@ -501,17 +504,25 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
   h->cur_class = AMR_T_REG;
   if (kids) {
     DevLevel& K = h->dl[l + 1];
-    if (K.nreg) LK(h->ops->reg_coarse(h->stream, K.regs, K.nreg, h->d_desc, h->U, K.R, h->params, l, 1));
+    if (K.nreg)
+      LK(h->ops->reg_coarse(h->stream, K.regs, K.reg_first, K.reg_chunk, K.nrect, K.nreg, h->d_desc, h->U, K.R,
+                            h->params, l, 1));
   }
-  if (l > 0 && L.nreg) LK(h->ops->reg_fine(h->stream, L.regs, L.nreg, h->d_desc, h->U, L.R, h->params, l));
+  if (l > 0 && L.nreg)
+    LK(h->ops->reg_fine(h->stream, L.regs, L.reg_first, L.reg_chunk, L.nrect, L.nreg, h->d_desc, h->U, L.R,
+                        h->params, l));
   if ((e = fill_ghosts(h, l, h->U1, alpha0 + 0.5)) != cudaSuccess) return e;
   if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;
   h->cur_class = AMR_T_REG;
   if (kids) {
     DevLevel& K = h->dl[l + 1];
-    if (K.nreg) LK(h->ops->reg_coarse(h->stream, K.regs, K.nreg, h->d_desc, h->U1, K.R, h->params, l, 2));
+    if (K.nreg)
+      LK(h->ops->reg_coarse(h->stream, K.regs, K.reg_first, K.reg_chunk, K.nrect, K.nreg, h->d_desc, h->U1, K.R,
+                            h->params, l, 2));
   }
-  if (l > 0 && L.nreg) LK(h->ops->reg_fine(h->stream, L.regs, L.nreg, h->d_desc, h->U1, L.R, h->params, l));
+  if (l > 0 && L.nreg)
+    LK(h->ops->reg_fine(h->stream, L.regs, L.reg_first, L.reg_chunk, L.nrect, L.nreg, h->d_desc, h->U1, L.R,
+                        h->params, l));
   if (kids) {
     if ((e = advance(h, l + 1, 0.0)) != cudaSuccess) return e;
     if ((e = advance(h, l + 1, 0.5)) != cudaSuccess) return e;
@@ -524,8 +535,16 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
     } else {
       LK(h->ops->restrict_(h->stream, K.restrict_segs, K.nrestrict, h->d_desc, h->U));
     }
-    double dxc[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
-    if (K.nuniq) LK(h->ops->reflux(h->stream, K.regs, K.reflux_first, K.nuniq, K.nreg, h->d_desc, K.R, h->U, dxc));
+    // reflux: the cells with one register in one launch; cells with several
+    // registers in (d, side) passes, so each gets its corrections in that order
+    const double dxc[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
+    if (K.nreg)
+      LK(h->ops->reflux(h->stream, K.regs, K.reg_first, K.reg_chunk, K.nrect, 0, K.nreg, K.nreg, h->d_desc, K.R, h->U,
+                        dxc, 0));
+    for (int pass = 0; pass < 6; ++pass)
+      if (K.reg_ordered[pass] && K.reg_pass[pass + 1] > K.reg_pass[pass])
+        LK(h->ops->reflux(h->stream, K.regs, K.reg_first, K.reg_chunk, K.nrect, K.reg_pass[pass],
+                          K.reg_pass[pass + 1], K.nreg, h->d_desc, K.R, h->U, dxc, 1));
   }
   // scheduled regrid: rebuild the levels finer than l now that l has completed a
   // step (its parent has reached fraction alpha0 + 1/2 of its own step)
@@ -747,7 +766,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   size_t nregd = 0;
   for (int l = 1; l < nlev; ++l) {
     reg_off[l] = nregd;
-    nregd += 2 * (size_t)nv * pl.levels[l].regs.size();
+    nregd += 2 * (size_t)nv * pl.levels[l].regs.total;
   }
   TablePack buf;
   size_t o_desc = buf.add(pl.desc);
@@ -759,7 +778,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
   size_t o_lvol = buf.add(lvol);
   struct FlatOffs { size_t boxes, first, chunk; };
-  struct Offs { size_t items, ghost, ghost_stage, prolong, gather_ghost, restr, regs, rf; FlatOffs fg, fa, fp, fr; };
+  struct Offs { size_t items, ghost, ghost_stage, prolong, gather_ghost, restr; FlatOffs fg, fa, fp, fr, rg; };
   std::vector<Offs> lo(nlev);
   auto put_flat = [&](const auto& f) { return FlatOffs{buf.add(f.boxes), buf.add(f.first), buf.add(f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
@@ -773,8 +792,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     lo[l].prolong = buf.add(L.prolong);
     lo[l].gather_ghost = buf.add(L.gather_ghost);
     lo[l].restr = buf.add(L.restrict_segs);
-    lo[l].regs = buf.add(L.regs);
-    lo[l].rf = buf.add(L.reflux_first);
+    lo[l].rg = put_flat(L.regs);
   }
   void* p = nullptr;
   CK(dmalloc(h, &p, buf.size));
@@ -815,15 +833,18 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
     D.nprolong = (int)L.prolong.size();
     D.ngather_ghost = (int)L.gather_ghost.size();
     D.nrestrict = (int)L.restrict_segs.size();
-    D.nreg = (int)L.regs.size();
-    D.nuniq = L.reflux_first.empty() ? 0 : (int)L.reflux_first.size() - 1;
+    D.nreg = L.regs.total;
+    D.nrect = (int)L.regs.boxes.size();
+    for (int p = 0; p < 7; ++p) D.reg_pass[p] = L.reg_pass[p];
+    for (int p = 0; p < 6; ++p) D.reg_ordered[p] = L.reg_ordered[p];
     D.ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost);
     D.ghost_stage = reinterpret_cast<const CopySeg*>(h->tables + lo[l].ghost_stage);
     D.prolong = reinterpret_cast<const ProlongBox*>(h->tables + lo[l].prolong);
     D.gather_ghost = reinterpret_cast<const CopySeg*>(h->tables + lo[l].gather_ghost);
     D.restrict_segs = reinterpret_cast<const RestrictSeg*>(h->tables + lo[l].restr);
-    D.regs = reinterpret_cast<const RegFace*>(h->tables + lo[l].regs);
-    D.reflux_first = reinterpret_cast<const int*>(h->tables + lo[l].rf);
+    D.regs = reinterpret_cast<const RegRect*>(h->tables + lo[l].rg.boxes);
+    D.reg_first = reinterpret_cast<const int*>(h->tables + lo[l].rg.first);
+    D.reg_chunk = reinterpret_cast<const int*>(h->tables + lo[l].rg.chunk);
     D.R = h->regs ? h->regs + reg_off[l] : nullptr;
     auto set_flat = [&](DevLevel::Flat& F, const auto& f, const FlatOffs& o) {
       F.boxes = h->tables + o.boxes;
@@ -1077,9 +1098,9 @@ amr_status regrid_impl(amr_handle* h, const RegridParams& rp_in, int mid_level, 
   size_t keep_regs = 0;
   if (mid) {
     for (int l = 1; l <= rp.min_level && l < (int)op.levels.size(); ++l) {
-      if (l >= (int)np.levels.size() || np.levels[l].regs.size() != op.levels[l].regs.size())
+      if (l >= (int)np.levels.size() || np.levels[l].regs.total != op.levels[l].regs.total)
         return fail(h, AMR_ERR_STATE, "regrid: the kept levels changed");
-      keep_regs += 2 * (size_t)nv * op.levels[l].regs.size();
+      keep_regs += 2 * (size_t)nv * op.levels[l].regs.total;
     }
   }
   DeviceBufs old = detach(h);

@@ -131,15 +131,21 @@ struct RestrictSeg {
   int16_t cn[3];     // box extent
 };
 
-// One coarse-fine face: fine patch `fpatch` face plane on side `side` along
-// axis `d`, against the uncovered coarse cell C of patch `cpatch`.
-struct RegFace {
+// Coarse-fine faces of one fine-patch face against one coarse patch: a
+// rectangle of uncovered coarse cells C with a fixed coordinate along the face
+// normal d and na x nb cells along t1 = (d+1)%3, t2 = (d+2)%3.  Its flux
+// registers are na * nb consecutive entries, the in-plane x axis fastest (b,
+// along t2 = x, for d = 1; a, along t1, otherwise); the face of entry (a, b)
+// sits between C = clo + a e_t1 + b e_t2 and the covered cell on C's side
+// cside, and its four fine sub-faces start at flo + 2a e_t1 + 2b e_t2.
+struct RegRect {
   int fpatch, cpatch;
-  int16_t fface[3];  // fine local face index of the (0,0) sub-face (face i sits at the low side of cell i)
-  int16_t cidx[3];   // coarse local cell index of C
+  int16_t clo[3];    // coarse local index of the first cell C
+  int16_t flo[3];    // fine local face index of the first (0,0) sub-face (face i sits at the low side of cell i)
+  int16_t na, nb;
   int8_t d, side;    // axis, side of the fine patch (0 lo, 1 hi)
-  int8_t cside;      // +1: face is C's high face, -1: C's low face
-  int8_t pad;
+  int8_t cside;      // +1: the face is C's high face, -1: C's low face
+  int8_t ordered;    // 1: some cell C also has a register of another rectangle (reflux in (d, side) order)
 };
 
 // Regrid block tagging on the device: levels [l0, L) of a hierarchy with at

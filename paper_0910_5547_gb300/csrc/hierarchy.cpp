@@ -590,6 +590,8 @@ void finish_flat(FlatList<B>& f, const std::vector<int>& cells, int chunk) {
 void flatten_copies(const Plan& plan, const std::vector<CopySeg>& segs, bool gather, FlatList<FlatCopy>& f) {
   f = FlatList<FlatCopy>();
   std::vector<int> cells;
+  f.boxes.reserve(segs.size());
+  cells.reserve(segs.size());
   for (const CopySeg& g : segs) {
     const PatchDesc& D = plan.desc[g.dst_patch];
     const PatchDesc& S = plan.desc[g.src_patch];
@@ -932,12 +934,16 @@ void classify_faces(Plan& plan, int i, const std::vector<CopySeg>& segs, std::ar
 }
 
 void build_flat(Plan& plan) {
-  for (LevelPlan& L : plan.levels) {
-    flatten_copies(plan, L.ghost_stage, false, L.fghost);
-    flatten_copies(plan, L.gather_ghost, true, L.fgather);
-    flatten_prolong(plan, L.prolong, L.fprolong);
-    flatten_restrict(plan, L.restrict_segs, L.frestrict);
-  }
+  // four independent lists per level, flattened in parallel
+  parallel_for(4 * (int)plan.levels.size(), [&](int t) {
+    LevelPlan& L = plan.levels[t / 4];
+    switch (t % 4) {
+      case 0: flatten_copies(plan, L.ghost_stage, false, L.fghost); break;
+      case 1: flatten_copies(plan, L.gather_ghost, true, L.fgather); break;
+      case 2: flatten_prolong(plan, L.prolong, L.fprolong); break;
+      default: flatten_restrict(plan, L.restrict_segs, L.frestrict); break;
+    }
+  });
 }
 
 amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan& plan, std::string& msg,
@@ -1203,11 +1209,11 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     PatchIndex fix(P, L.first, L.count), cix(P, C.first, C.count);
     // tasks in (d, side, patch) order; concatenated in that order below
     const int ntask = 6 * L.count;
-    std::vector<std::vector<RegFace>> rs(ntask);
+    std::vector<std::vector<RegRect>> rs(ntask);
     std::vector<std::string> err(ntask);
     parallel_for(ntask, [&](int task) {
       const int d = task / (2 * L.count), side = (task / L.count) % 2, i = L.first + task % L.count;
-      std::vector<RegFace>& Rv = rs[task];
+      std::vector<RegRect>& Rv = rs[task];
       std::vector<int> cand;
           const HPatch& p = P[i];
           int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -1252,109 +1258,116 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             for (int y = y0; y < y1; ++y)
               for (int x = x0; x < x1; ++x) owner[(size_t)(y - b0) * A + (x - a0)] = q;
           }
-          Rv.reserve((size_t)A * B);
-          for (int b = 0; b < B; ++b)
-            for (int a = 0; a < A; ++a) {
-              if (cov2[(size_t)b * A + a]) continue;
-              int q = owner[(size_t)b * A + a];
-              if (q < 0) { err[task] = fmt("patch %d: coarse neighbour cell outside level %d", i, l - 1); return; }
-              const HPatch& o = P[q];
-              RegFace r{};
+          // one rectangle per run of uncovered cells with the same coarse owner
+          std::vector<int> qs;
+          for (size_t e = 0; e < owner.size(); ++e)
+            if (!cov2[e]) {
+              if (owner[e] < 0) { err[task] = fmt("patch %d: coarse neighbour cell outside level %d", i, l - 1); return; }
+              if (std::find(qs.begin(), qs.end(), owner[e]) == qs.end()) qs.push_back(owner[e]);
+            }
+          std::sort(qs.begin(), qs.end());
+          // does a level-l patch cover any coarse cell of [lo, hi) (level l-1 indices; a
+          // cell beyond an outflow face is not covered, periodic axes wrap)
+          auto covered_any = [&](int lo[3], int hi[3]) {
+            for (int k = 0; k < 3; ++k) {
+              const int Nk = level_n(cfg, l - 1, k);
+              if (lo[k] < 0 || hi[k] > Nk) {
+                if (!periodic(cfg, k) || hi[k] - lo[k] != 1) return false;   // only single-cell strips leave the box
+                lo[k] = ((lo[k] % Nk) + Nk) % Nk;
+                hi[k] = lo[k] + 1;
+              }
+            }
+            int qlo[3], qhi[3];
+            for (int k = 0; k < 3; ++k) { qlo[k] = 2 * lo[k]; qhi[k] = 2 * hi[k]; }
+            std::vector<int> cc;
+            fix.query(qlo, qhi, cc);
+            for (int q2 : cc) {
+              const HPatch& o = P[q2];
+              bool hit = true;
+              for (int k = 0; k < 3 && hit; ++k)
+                hit = std::max(lo[k], o.lo[k] / 2) < std::min(hi[k], (o.lo[k] + o.n[k]) / 2);
+              if (hit) return true;
+            }
+            return false;
+          };
+          std::vector<unsigned char> other((size_t)A * B);
+          for (int q : qs) {
+            for (size_t e = 0; e < other.size(); ++e) other[e] = (cov2[e] || owner[e] != q) ? 1 : 0;
+            const HPatch& o = P[q];
+            for (const Rect& rc : mask_rects(other, A, B)) {
+              RegRect r{};
               r.fpatch = i; r.cpatch = q;
               r.d = (int8_t)d; r.side = (int8_t)side; r.cside = (int8_t)(side ? -1 : 1);
               int Cc[3];
-              Cc[d] = Cd; Cc[t1] = a0 + a; Cc[t2] = b0 + b;
-              for (int k = 0; k < 3; ++k) r.cidx[k] = (int16_t)(Cc[k] - o.lo[k]);
-              r.fface[d] = (int16_t)(side ? p.n[d] : 0);
-              r.fface[t1] = (int16_t)(2 * (a0 + a) - p.lo[t1]);
-              r.fface[t2] = (int16_t)(2 * (b0 + b) - p.lo[t2]);
+              Cc[d] = Cd; Cc[t1] = a0 + rc.a0; Cc[t2] = b0 + rc.b0;
+              for (int kk = 0; kk < 3; ++kk) r.clo[kk] = (int16_t)(Cc[kk] - o.lo[kk]);
+              r.flo[d] = (int16_t)(side ? p.n[d] : 0);
+              r.flo[t1] = (int16_t)(2 * (a0 + rc.a0) - p.lo[t1]);
+              r.flo[t2] = (int16_t)(2 * (b0 + rc.b0) - p.lo[t2]);
+              r.na = (int16_t)rc.na;
+              r.nb = (int16_t)rc.nb;
+              // another register on one of these coarse cells (a one-cell gap along d, or a
+              // covered in-plane neighbour of a boundary cell): its reflux is ordered
+              {
+                const int cl[3] = {Cd, a0 + rc.a0, b0 + rc.b0};
+                const int ch[3] = {Cd + 1, a0 + rc.a0 + rc.na, b0 + rc.b0 + rc.nb};
+                int lo[3], hi[3];
+                auto box = [&](int dd, int v) {   // the rectangle's cells shifted to coordinate v on axis dd
+                  for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; }
+                  int m[3];
+                  m[d] = 0; m[t1] = 1; m[t2] = 2;
+                  for (int k = 0; k < 3; ++k) { lo[k] = cl[m[k]]; hi[k] = ch[m[k]]; }
+                  lo[dd] = v;
+                  hi[dd] = v + 1;
+                };
+                bool conflict = false;
+                box(d, Cd - r.cside);
+                conflict = conflict || covered_any(lo, hi);
+                box(t1, a0 + rc.a0 - 1);
+                conflict = conflict || covered_any(lo, hi);
+                box(t1, a0 + rc.a0 + rc.na);
+                conflict = conflict || covered_any(lo, hi);
+                box(t2, b0 + rc.b0 - 1);
+                conflict = conflict || covered_any(lo, hi);
+                box(t2, b0 + rc.b0 + rc.nb);
+                conflict = conflict || covered_any(lo, hi);
+                r.ordered = conflict ? 1 : 0;
+              }
               Rv.push_back(r);
             }
+          }
             });
     for (int task = 0; task < ntask; ++task)
       if (!err[task].empty()) {
         msg = err[task];
         return AMR_ERR_NESTING;
       }
-    // group by coarse cell, keeping the task order ((d, side, patch)) inside a
-    // cell: a stable counting sort by coarse patch (all of level l-1) over chunks
-    // of tasks (per-chunk histograms, parallel scatter), then a stable sort by cell
-    // inside each coarse patch
-    const int c0 = C.first, nc = C.count;
-    const int nchunk = std::max(1, std::min(64, ntask / 64));
-    auto chunk_lo = [&](int k) { return (int)((int64_t)ntask * k / nchunk); };
-    std::vector<std::vector<int>> hist(nchunk, std::vector<int>(nc, 0));
-    parallel_for(nchunk, [&](int k) {
-      for (int task = chunk_lo(k); task < chunk_lo(k + 1); ++task)
-        for (const RegFace& r : rs[task]) hist[k][r.cpatch - c0]++;
-    });
-    std::vector<int> start(nc + 1, 0);
-    {
-      size_t run = 0;
-      for (int c = 0; c < nc; ++c) {
-        start[c] = (int)run;
-        for (int k = 0; k < nchunk; ++k) {
-          const int n = hist[k][c];
-          hist[k][c] = (int)run;   // first slot of chunk k's registers of coarse patch c0 + c
-          run += n;
-        }
+    // rectangles in task order, (d, side, fine patch): the reflux passes go over
+    // (d, side) = 0 .. 5 in turn, and in one pass every coarse cell has at most
+    // one register (a coarse face borders one fine patch)
+    L.regs = FlatList<RegRect>();
+    std::vector<int> cells;
+    int64_t run = 0;
+    for (int task = 0; task < ntask; ++task) {
+      for (const RegRect& r : rs[task]) {
+        L.regs.boxes.push_back(r);
+        cells.push_back((int)r.na * r.nb);
+        run += (int64_t)r.na * r.nb;
+        if (r.ordered) L.reg_ordered[task / L.count] = 1;
       }
-      start[nc] = (int)run;
+      L.reg_pass[task / L.count + 1] = (int)run;   // pass = task / count = 2 d + side
     }
-    RegVec regs(start[nc]);   // not zero-filled: the scatter threads touch the pages first
-    parallel_for(nchunk, [&](int k) {
-      std::vector<int>& pos = hist[k];
-      for (int task = chunk_lo(k); task < chunk_lo(k + 1); ++task)
-        for (const RegFace& r : rs[task]) regs[pos[r.cpatch - c0]++] = r;
-    });
-    std::vector<std::vector<int>>().swap(hist);
-    std::vector<std::vector<RegFace>>().swap(rs);
-    auto same_cell = [](const RegFace& a, const RegFace& b) {
-      return a.cpatch == b.cpatch && a.cidx[0] == b.cidx[0] && a.cidx[1] == b.cidx[1] && a.cidx[2] == b.cidx[2];
-    };
-    // per coarse patch: sort by cell, count the unique cells (CSR built below)
-    std::vector<int> nuniq(nc + 1, 0);
-    parallel_for(nc, [&](int c) {
-      // (z, y, x) order of the coarse cell as one key (cell indices are >= 0)
-      auto key = [](const RegFace& r) {
-        return ((uint64_t)(uint16_t)r.cidx[2] << 32) | ((uint64_t)(uint16_t)r.cidx[1] << 16) | (uint16_t)r.cidx[0];
-      };
-      std::stable_sort(regs.begin() + start[c], regs.begin() + start[c + 1],
-                       [&](const RegFace& x, const RegFace& y) { return key(x) < key(y); });
-      int u = 0;
-      for (int e = start[c]; e < start[c + 1]; ++e)
-        if (e == start[c] || !same_cell(regs[e], regs[e - 1])) ++u;
-      nuniq[c + 1] = u;
-    });
-    for (int c = 0; c < nc; ++c) nuniq[c + 1] += nuniq[c];
-    L.reflux_first.assign(nuniq[nc] + 1, 0);
-    parallel_for(nc, [&](int c) {
-      int u = nuniq[c];
-      for (int e = start[c]; e < start[c + 1]; ++e)
-        if (e == start[c] || !same_cell(regs[e], regs[e - 1])) L.reflux_first[u++] = e;
-    });
-    L.reflux_first[nuniq[nc]] = (int)regs.size();
-    L.regs.swap(regs);
+    finish_flat(L.regs, cells, kBoxThreads);
   }
   // the coarse-side register flux reads two cells on either side of a coarse-fine
   // face: where that stencil leaves the coarse patch, its ghost cells are read,
   // so that face of the coarse patch keeps copied ghost cells
-  for (int l = 1; l < nlev && direct_ok; ++l) {
-    // the registers are sorted by coarse patch: one task per coarse patch over its range
-    const LevelPlan& L = plan.levels[l];
-    const int c0 = plan.levels[l - 1].first;
-    parallel_for(plan.levels[l - 1].count, [&](int c) {
-      const int cp = c0 + c;
-      auto lo = std::lower_bound(L.regs.begin(), L.regs.end(), cp,
-                                 [](const RegFace& r, int v) { return r.cpatch < v; });
-      for (auto it = lo; it != L.regs.end() && it->cpatch == cp; ++it) {
-        const RegFace& r = *it;
-        const int f = r.cidx[r.d] + (r.cside > 0 ? 1 : 0);   // face index between cells f-1 and f
-        if (f - 2 < 0) direct[cp][2 * r.d] = 0;
-        if (f + 1 >= P[cp].n[r.d]) direct[cp][2 * r.d + 1] = 0;
-      }
-    });
-  }
+  for (int l = 1; l < nlev && direct_ok; ++l)
+    for (const RegRect& r : plan.levels[l].regs.boxes) {
+      const int f = r.clo[r.d] + (r.cside > 0 ? 1 : 0);   // face index between cells f-1 and f
+      if (f - 2 < 0) direct[r.cpatch][2 * r.d] = 0;
+      if (f + 1 >= P[r.cpatch].n[r.d]) direct[r.cpatch][2 * r.d + 1] = 0;
+    }
   for (int i = 0; i < np; ++i)
     for (int f = 0; f < 6; ++f)
       if (!direct[i][f]) plan.desc[i].face[f] = own_face(plan.desc[i]);

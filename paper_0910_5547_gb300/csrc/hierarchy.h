@@ -46,7 +46,6 @@ struct NoInitAlloc : std::allocator<T> {
     else ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
   }
 };
-using RegVec = std::vector<RegFace, NoInitAlloc<RegFace>>;
 
 struct LevelPlan {
   int first = 0, count = 0;                  // patch range [first, first + count)
@@ -61,8 +60,11 @@ struct LevelPlan {
   std::vector<CopySeg> gather_ghost;         // parent-cell gathers (level >= 1): the tile cells the per-stage
                                              //   prolongation reads, grouped by fine patch
   std::vector<RestrictSeg> restrict_segs;    // this level -> parent (level >= 1)
-  RegVec regs;                               // coarse-fine faces of this level (level >= 1), sorted by coarse cell
-  std::vector<int> reflux_first;             // CSR over unique coarse cells: reg range per unique cell
+  // coarse-fine faces of this level (level >= 1) as rectangles, in (d, side, fine patch) order;
+  // flattened: register e belongs to the rectangle b with first[b] <= e < first[b + 1]
+  FlatList<RegRect> regs;
+  int reg_pass[7] = {0, 0, 0, 0, 0, 0, 0};   // registers of the fine faces (d, side) = p / 2, p % 2: [pass[p], pass[p+1])
+  int reg_ordered[6] = {0, 0, 0, 0, 0, 0};   // pass p holds rectangles whose cells have several registers
   FlatList<FlatCopy> fghost, fgather;        // the ghost and gather boxes, flattened (batched launches)
   FlatList<FlatProlong> fprolong;            // the prolongation boxes, flattened
   FlatList<FlatCopy> frestrict;              // the restriction boxes (this level -> parent), flattened

@@ -1057,19 +1057,56 @@ __device__ __forceinline__ void face_flux_dir(const T* base, const PatchDesc& P,
   else face_flux_from_array<T, NV, 2>(base, P.vstride, c1, (int64_t)P.pitch * P.m1, ph, F);
 }
 
+// Flux registers are stored per rectangle of coarse-fine faces (RegRect):
+// register e of a level belongs to rectangle b with first[b] <= e < first[b+1];
+// chunk_box[e / kBoxThreads] is the rectangle holding the first register of
+// e's chunk.  Entry (a, b) of a rectangle: coarse cell C = clo + a e_t1 + b e_t2.
+// Threads per CTA of the register kernels: small CTAs spread the few thousand
+// registers of a small level over all SMs (each register is several flux solves).
+constexpr int kRegThreads = 64;
+
+// Entry q of a rectangle as (a, b) along (t1, t2): the in-plane axis that is x
+// (t2 for d = 1) runs fastest, so neighbouring threads touch neighbouring cells.
+__device__ __forceinline__ void reg_entry(const RegRect& r, int q, int& a, int& b) {
+  if (r.d == 1) { a = q / r.nb; b = q - a * r.nb; }
+  else { b = q / r.na; a = q - b * r.na; }
+}
+
+__device__ __forceinline__ int reg_rect_of(const int* first, const int* chunk_box, int nrect, int nreg, int e) {
+  const int k = e / kBoxThreads;
+  int lo = chunk_box[k];                                                 // first[lo] <= e
+  int hi = (k + 1) * kBoxThreads < nreg ? chunk_box[k + 1] : nrect - 1;  // e < first[hi + 1]
+  while (lo < hi) {   // the last rectangle starting at or before e (rectangles are never empty)
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Coarse side: R_c (+)= dt/2 * F_coarse at the face of C (stage 1 also clears R_f).
 template <typename T, int NV>
-__global__ void reg_coarse_kernel(const RegFace* regs, int nreg, const PatchDesc* desc, const T* Uin,
-                                  double* R, StepParams* params, double dt_scale, Phys<T> ph0, int stage) {
+__global__ void __launch_bounds__(kRegThreads) reg_coarse_kernel(const RegRect* rects, const int* first,
+                                                                 const int* chunk_box, int nrect, int nreg,
+                                                                 const PatchDesc* desc, const T* Uin, double* R,
+                                                                 StepParams* params, double dt_scale, Phys<T> ph0,
+                                                                 int stage) {
   const Phys<T> ph = phys_with_ch<T, NV>(ph0, params);
   const double dt = (double)(T)(params->dt0 * dt_scale);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nreg; e += gridDim.x * blockDim.x) {
-    const RegFace r = regs[e];
+    const int b0 = reg_rect_of(first, chunk_box, nrect, nreg, e);
+    const RegRect r = rects[b0];
+    const int q = e - first[b0];
+    const int d = r.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    int a, bb;
+    reg_entry(r, q, a, bb);
     const PatchDesc C = desc[r.cpatch];
-    int f[3] = {r.cidx[0], r.cidx[1], r.cidx[2]};
-    if (r.cside > 0) f[r.d] += 1;
+    int f[3] = {r.clo[0], r.clo[1], r.clo[2]};
+    f[t1] += a;
+    f[t2] += bb;
+    if (r.cside > 0) f[d] += 1;
     T F[NV];
-    face_flux_dir<T, NV>(Uin + C.off, C, f[0], f[1], f[2], r.d, ph, F);
+    face_flux_dir<T, NV>(Uin + C.off, C, f[0], f[1], f[2], d, ph, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       double* Rc = R + (size_t)v * nreg + e;
@@ -1083,53 +1120,75 @@ __global__ void reg_coarse_kernel(const RegFace* regs, int nreg, const PatchDesc
 
 // Fine side: R_f += dt_f/2 * (1/4) * sum of the 4 fine sub-face fluxes.
 template <typename T, int NV>
-__global__ void reg_fine_kernel(const RegFace* regs, int nreg, const PatchDesc* desc, const T* Uin, double* R,
-                                StepParams* params, double dt_scale, Phys<T> ph0) {
+__global__ void __launch_bounds__(kRegThreads) reg_fine_kernel(const RegRect* rects, const int* first,
+                                                               const int* chunk_box, int nrect, int nreg,
+                                                               const PatchDesc* desc,
+                                                               const T* Uin, double* R, StepParams* params,
+                                                               double dt_scale, Phys<T> ph0) {
   const Phys<T> ph = phys_with_ch<T, NV>(ph0, params);
   const double dt = (double)(T)(params->dt0 * dt_scale);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nreg; e += gridDim.x * blockDim.x) {
-    const RegFace r = regs[e];
-    const PatchDesc Pf = desc[r.fpatch];
+    const int b0 = reg_rect_of(first, chunk_box, nrect, nreg, e);
+    const RegRect r = rects[b0];
+    const int q = e - first[b0];
     const int d = r.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    double q[2][2][NV];
+    const PatchDesc Pf = desc[r.fpatch];
+    int ea, eb;
+    reg_entry(r, q, ea, eb);
+    int f0[3] = {r.flo[0], r.flo[1], r.flo[2]};
+    f0[t1] += 2 * ea;
+    f0[t2] += 2 * eb;
+    double qf[2][2][NV];
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        int f[3] = {r.fface[0], r.fface[1], r.fface[2]};
+        int f[3] = {f0[0], f0[1], f0[2]};
         f[t1] += a;
         f[t2] += b;
         T F[NV];
         face_flux_dir<T, NV>(Uin + Pf.off, Pf, f[0], f[1], f[2], d, ph, F);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) q[b][a][v] = (double)F[v];
+        for (int v = 0; v < NV; ++v) qf[b][a][v] = (double)F[v];
       }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double sum = (q[0][0][v] + q[0][1][v]) + (q[1][0][v] + q[1][1][v]);
+      const double sum = (qf[0][0][v] + qf[0][1][v]) + (qf[1][0][v] + qf[1][1][v]);
       R[(size_t)(NV + v) * nreg + e] += 0.5 * dt * (0.25 * sum);
     }
   }
 }
 
-// U_C -= side * (R_f - R_c) / dx_c, every register of one coarse cell in (axis, side) order.
+// Reflux: U_C -= cside (R_f - R_c) / dx_d for the registers [e0, e1), in FP64.
+// ordered = 0: the registers of rectangles whose cells have no other register
+// (any order; one launch over all of them); ordered = 1: one pass over the
+// registers of one fine-face orientation (d, side) that share cells with
+// other rectangles.  The ordered passes run in (d, side) order, and within a
+// pass a coarse cell has at most one register (a coarse face borders one fine
+// patch), so a cell's corrections apply in that order without races.
 template <typename T, int NV>
-__global__ void reflux_kernel(const RegFace* regs, const int* first, int nuniq, int nreg, const PatchDesc* desc,
-                              const double* R, T* U, double dx0, double dx1, double dx2) {
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nuniq; u += gridDim.x * blockDim.x) {
-    const int e0 = first[u], e1 = first[u + 1];
-    const RegFace r0 = regs[e0];
-    const PatchDesc C = desc[r0.cpatch];
-    const int64_t ci = C.off + cell_index(C, r0.cidx[0], r0.cidx[1], r0.cidx[2]);
+__global__ void __launch_bounds__(kRegThreads) reflux_kernel(const RegRect* rects, const int* first,
+                                                             const int* chunk_box, int nrect, int e0, int e1, int nreg,
+                                                             const PatchDesc* desc, const double* R, T* U,
+                                                             double dx0, double dx1, double dx2, int ordered) {
+  for (int e = e0 + blockIdx.x * blockDim.x + threadIdx.x; e < e1; e += gridDim.x * blockDim.x) {
+    const int b0 = reg_rect_of(first, chunk_box, nrect, nreg, e);
+    const RegRect r = rects[b0];
+    if (r.ordered != ordered) continue;
+    const double dxd = r.d == 0 ? dx0 : (r.d == 1 ? dx1 : dx2);
+    const int q = e - first[b0];
+    const int d = r.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    int ea, eb;
+    reg_entry(r, q, ea, eb);
+    int c[3] = {r.clo[0], r.clo[1], r.clo[2]};
+    c[t1] += ea;
+    c[t2] += eb;
+    const PatchDesc C = desc[r.cpatch];
+    const int64_t ci = C.off + cell_index(C, c[0], c[1], c[2]);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double val = (double)U[ci + v * C.vstride];
-      for (int e = e0; e < e1; ++e) {
-        const RegFace r = regs[e];
-        const double dxc = r.d == 0 ? dx0 : (r.d == 1 ? dx1 : dx2);
-        const double delta = R[(size_t)(NV + v) * nreg + e] - R[(size_t)v * nreg + e];
-        val = val - (double)r.cside * delta / dxc;
-      }
+      const double delta = R[(size_t)(NV + v) * nreg + e] - R[(size_t)v * nreg + e];
+      const double val = (double)U[ci + v * C.vstride] - (double)r.cside * delta / dxd;
       U[ci + v * C.vstride] = (T)val;
     }
   }

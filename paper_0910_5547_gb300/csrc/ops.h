@@ -54,12 +54,18 @@ struct OpsBase {
   virtual cudaError_t prolong(cudaStream_t s, const ProlongBox* boxes, int nbox, const PatchDesc* desc,
                               const void* tile, void* arena) = 0;
   virtual cudaError_t restrict_(cudaStream_t s, const RestrictSeg* segs, int nseg, const PatchDesc* desc, void* U) = 0;
-  virtual cudaError_t reg_coarse(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc,
-                                 const void* Uin, double* R, StepParams* prm, int level, int stage) = 0;
-  virtual cudaError_t reg_fine(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc,
-                               const void* Uin, double* R, StepParams* prm, int level) = 0;
-  virtual cudaError_t reflux(cudaStream_t s, const RegFace* regs, const int* first, int nuniq, int nreg,
-                             const PatchDesc* desc, const double* R, void* U, const double dxc[3]) = 0;
+  // flux registers over register rectangles (first / chunk_box: flattened, chunks of kBoxThreads)
+  virtual cudaError_t reg_coarse(cudaStream_t s, const RegRect* rects, const int* first, const int* chunk_box,
+                                 int nrect, int nreg, const PatchDesc* desc, const void* Uin, double* R, StepParams* prm,
+                                 int level, int stage) = 0;
+  virtual cudaError_t reg_fine(cudaStream_t s, const RegRect* rects, const int* first, const int* chunk_box,
+                               int nrect, int nreg, const PatchDesc* desc, const void* Uin, double* R, StepParams* prm,
+                               int level) = 0;
+  // reflux of the registers [e0, e1) of the rectangles whose `ordered` flag equals `ordered`
+  virtual cudaError_t reflux(cudaStream_t s, const RegRect* rects, const int* first, const int* chunk_box, int nrect,
+                             int e0,
+                             int e1, int nreg, const PatchDesc* desc, const double* R, void* U, const double dxc[3],
+                             int ordered) = 0;
   virtual cudaError_t speed(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,
                             const void* U, StepParams* prm, const double dx0[3]) = 0;
   virtual cudaError_t totals(cudaStream_t s, const ChunkDesc* chunks, int nchunk, const PatchDesc* desc,

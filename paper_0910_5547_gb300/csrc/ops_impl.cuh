@@ -198,27 +198,34 @@ struct Ops final : OpsBase {
     return cudaGetLastError();
   }
 
-  cudaError_t reg_coarse(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc, const void* Uin,
-                         double* R, StepParams* prm, int level, int stage) override {
+  cudaError_t reg_coarse(cudaStream_t s, const RegRect* rects, const int* first, const int* chunk_box, int nrect,
+                         int nreg,
+                         const PatchDesc* desc, const void* Uin, double* R, StepParams* prm, int level,
+                         int stage) override {
     if (nreg <= 0) return cudaSuccess;
-    reg_coarse_kernel<T, NV><<<grid_for((nreg + 127) / 128), 128, 0, s>>>(
-        regs, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level), ph, stage);
+    reg_coarse_kernel<T, NV><<<grid_for((nreg + kRegThreads - 1) / kRegThreads), kRegThreads, 0, s>>>(
+        rects, first, chunk_box, nrect, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level), ph,
+        stage);
     return cudaGetLastError();
   }
 
-  cudaError_t reg_fine(cudaStream_t s, const RegFace* regs, int nreg, const PatchDesc* desc, const void* Uin,
-                       double* R, StepParams* prm, int level) override {
+  cudaError_t reg_fine(cudaStream_t s, const RegRect* rects, const int* first, const int* chunk_box, int nrect,
+                       int nreg,
+                       const PatchDesc* desc, const void* Uin, double* R, StepParams* prm, int level) override {
     if (nreg <= 0) return cudaSuccess;
-    reg_fine_kernel<T, NV><<<grid_for((nreg + 127) / 128), 128, 0, s>>>(
-        regs, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level), ph);
+    reg_fine_kernel<T, NV><<<grid_for((nreg + kRegThreads - 1) / kRegThreads), kRegThreads, 0, s>>>(
+        rects, first, chunk_box, nrect, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level),
+        ph);
     return cudaGetLastError();
   }
 
-  cudaError_t reflux(cudaStream_t s, const RegFace* regs, const int* first, int nuniq, int nreg, const PatchDesc* desc,
-                     const double* R, void* U, const double dxc[3]) override {
-    if (nuniq <= 0) return cudaSuccess;
-    reflux_kernel<T, NV><<<grid_for((nuniq + 127) / 128), 128, 0, s>>>(regs, first, nuniq, nreg, desc, R,
-                                                                        static_cast<T*>(U), dxc[0], dxc[1], dxc[2]);
+  cudaError_t reflux(cudaStream_t s, const RegRect* rects, const int* first, const int* chunk_box, int nrect, int e0,
+                     int e1,
+                     int nreg, const PatchDesc* desc, const double* R, void* U, const double dxc[3],
+                     int ordered) override {
+    if (e1 <= e0) return cudaSuccess;
+    reflux_kernel<T, NV><<<grid_for((e1 - e0 + kRegThreads - 1) / kRegThreads), kRegThreads, 0, s>>>(
+        rects, first, chunk_box, nrect, e0, e1, nreg, desc, R, static_cast<T*>(U), dxc[0], dxc[1], dxc[2], ordered);
     return cudaGetLastError();
   }
 

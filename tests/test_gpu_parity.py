@@ -314,3 +314,23 @@ def test_cell_update_counter(graph):
         s.step(0.0, sync=False)
     s.check()
     assert N.amr_cell_updates(s.h) - c0 == 3 * per_step
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_concave_fine_region_and_one_cell_gap(precision):
+    """Coarse cells with several flux registers: an L-shaped fine region (the
+    coarse cells in its inner corner border fine patches along x and along y)
+    and two fine patches one coarse cell apart (that cell borders both along x).
+    Their refluxes apply in (axis, side) order; parity with the oracle and
+    conservation on the periodic box."""
+    patches = ai.uniform_patches((16, 16, 16), (8, 8, 8))
+    patches += [ai.Patch(1, (8, 8, 8), (8, 8, 8)), ai.Patch(1, (16, 8, 8), (8, 8, 8)),
+                ai.Patch(1, (8, 16, 8), (8, 8, 8)),
+                ai.Patch(1, (0, 0, 24), (8, 8, 4)), ai.Patch(1, (10, 0, 24), (8, 8, 4))]
+    pb = ai.random_smooth(patches, (16,) * 3, seed=14, amp=0.25)
+    t0 = Solver.from_problem(pb, precision=precision).totals()
+    o, s = run_pair(pb, precision, steps=3)
+    assert_parity(s.all_cons(), o.all_cons(), pb.patches, precision, "concave+gap")
+    t1 = s.totals()
+    scale = np.abs(t0).max()
+    assert np.all(np.abs(t1 - t0) <= (2e-14 if precision == "fp64" else 2e-6) * scale), (t1 - t0)
