@@ -715,6 +715,11 @@ def main():
             for k, v in NV.amr_get_regrid_timing(so.h).items():
                 phases_s[k] += v
             counts.append([len(so.patches), 1 + max(p.level for p in so.patches)])
+        # kernel classes of one eager coarse step on the final (11k-patch) hierarchy
+        NV.amr_set_timing(so.h, True)
+        so.step(0.0, sync=False)
+        tm_ad = NV.amr_get_timing(so.h)
+        NV.amr_set_timing(so.h, False)
         so.check()
         so.close()
         rg_s = sum(ph_sched.values())
@@ -729,6 +734,7 @@ def main():
                 "value": ws * tot_cu / max_over_ranks(t_steps),
                 "value_with_regrid": ws * tot_cu / max_over_ranks(t_steps + t_regrid), "cell_updates": tot_cu,
                 "regrid_s": t_regrid, "regrid_phases_s": {k: round(v, 4) for k, v in phases_s.items()},
+                "class_ms_one_coarse_step_final_hierarchy": {k: round(v[0], 3) for k, v in tm_ad.items() if v[1]},
                 "patches_levels_after_each_regrid": counts},
             "workload": f"blast in a log-normal clump field (sigma 1), base 64^3 + {lmax} levels, FP32 batched, "
                         f"density-gradient regrid (threshold 0.3) of the levels above l after every step of "

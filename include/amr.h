@@ -59,6 +59,7 @@ enum { AMR_PLM = 0, AMR_WENO3 = 1 };                  /* face states */
 enum { AMR_BC_OUTFLOW = 0, AMR_BC_PERIODIC = 1 };     /* per domain face */
 enum { AMR_STATE_CONSERVED = 0, AMR_STATE_PRIMITIVE = 1 };
 enum { AMR_GHOST_DIRECT = 0, AMR_GHOST_COPY = 1 };    /* how stages read same-level ghost cells */
+enum { AMR_SPAN_LAYERS = 0, AMR_SPAN_PATCH = 1 };     /* batched stage work items */
 
 typedef struct {
   int nvar;              /* 5 (Euler) or 9 (GLM-MHD) */
@@ -101,6 +102,11 @@ typedef struct {
                             are copied or prolonged into ghost cells; AMR_GHOST_COPY: every face is
                             filled into ghost cells before each stage.  Same results bit for bit;
                             AMR_FLUXREC always copies. */
+  int item_span;         /* work items of the batched stage launches: AMR_SPAN_LAYERS (0, default): the
+                            patches of a level that share a z range and tile a rectangle are cut into
+                            column blocks as one region (a block may take cells of several patches, so
+                            small patches fill whole CTAs); AMR_SPAN_PATCH: every block lies in one patch.
+                            Same results bit for bit; AMR_FLUXREC always uses per-patch blocks. */
 } amr_config;
 
 /* One patch: `n` interior cells per axis starting at `lo` in the index space of

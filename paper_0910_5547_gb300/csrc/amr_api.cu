@@ -68,7 +68,10 @@ __global__ void set_dt_kernel(StepParams* params, double dt) { params->dt0 = dt;
 
 struct DevLevel {
   int nitems = 0, nghost = 0, nghost_stage = 0, nprolong = 0, ngather_ghost = 0, nrestrict = 0, nreg = 0, nrect = 0;
-  const StageItem* items = nullptr;
+  const StageItem* items = nullptr;        // per-patch stage items (plain launches)
+  const StageItem* bitems = nullptr;       // stage items of the batched launch
+  int nbitems = 0;
+  bool has_span = false;                   // some batched items span patches
   const CopySeg* ghost = nullptr;          // every face ghost segment (diagnostics, regrid flags)
   const CopySeg* ghost_stage = nullptr;    // the faces a stage does not read directly
   const ProlongBox* prolong = nullptr;
@@ -161,6 +164,7 @@ struct amr_handle {
   long long counting = 0;   // launches counted while enqueueing
   // stage-kernel work items (own buffer: the autotuner swaps the tiling)
   StageItem* items_dev = nullptr;
+  const ItemSpan* d_spans = nullptr;   // inside items_dev: the spanning batched items' patch lists
   TileParams tp;            // tile shape in use (autotuned or default)
   int sms = 0;              // SMs of the device (persistent stage grids)
   int persist_mode = -1;    // -1: the autotuner decides; 0 / 1: one CTA per item / persistent CTAs
@@ -471,12 +475,14 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
   if (h->cfg.batched) {
     // persistent: one wave of resident CTAs takes the level's items from a device counter
     const int grid = h->tp.persistent ? h->sms * h->ops->resident_ctas() : 0;
-    LK(h->ops->stage(s, h->stream, h->d_desc, L.items, L.nitems, in, out, h->params, l, dx, h->dx0, fuse, grid));
+    LK(h->ops->stage(s, h->stream, h->d_desc, L.bitems, L.nbitems, L.has_span ? h->d_spans : nullptr, in, out,
+                     h->params, l, dx, h->dx0, fuse, grid));
   } else {
     for (int p = 0; p < LP.count; ++p) {
       int a = LP.item_first[p], b = LP.item_first[p + 1];
       if (b > a)
-        LK(h->ops->stage(s, h->stream, h->d_desc, L.items + a, b - a, in, out, h->params, l, dx, h->dx0, fuse, 0));
+        LK(h->ops->stage(s, h->stream, h->d_desc, L.items + a, b - a, nullptr, in, out, h->params, l, dx, h->dx0,
+                         fuse, 0));
     }
   }
   return cudaSuccess;
@@ -688,21 +694,34 @@ cudaError_t host_stage(amr_handle* h, size_t bytes) {
 
 // Upload the stage work items of every level into their own device buffer.
 amr_status upload_items(amr_handle* h) {
+  // one buffer: every level's per-patch items, then its batched items, then the spans
   std::vector<StageItem> all;
-  std::vector<size_t> first;
+  std::vector<size_t> first, bfirst;
   for (const LevelPlan& L : h->plan.levels) {
     first.push_back(all.size());
     all.insert(all.end(), L.items.begin(), L.items.end());
+    bfirst.push_back(all.size());
+    all.insert(all.end(), L.bitems.begin(), L.bitems.end());
   }
+  const size_t span_off = (all.size() * sizeof(StageItem) + 255) / 256 * 256;
+  const size_t bytes = span_off + h->plan.spans.size() * sizeof(ItemSpan);
   dfree(h, h->items_dev);
   h->items_dev = nullptr;
   void* p = nullptr;
-  CK(dmalloc(h, &p, std::max<size_t>(all.size(), 1) * sizeof(StageItem)));
+  CK(dmalloc(h, &p, std::max<size_t>(bytes, 256)));
   h->items_dev = static_cast<StageItem*>(p);
   CK(cudaMemcpyAsync(h->items_dev, all.data(), all.size() * sizeof(StageItem), cudaMemcpyHostToDevice, h->stream));
+  h->d_spans = reinterpret_cast<const ItemSpan*>(static_cast<unsigned char*>(p) + span_off);
+  if (!h->plan.spans.empty())
+    CK(cudaMemcpyAsync(static_cast<unsigned char*>(p) + span_off, h->plan.spans.data(),
+                       h->plan.spans.size() * sizeof(ItemSpan), cudaMemcpyHostToDevice, h->stream));
   for (size_t l = 0; l < h->dl.size(); ++l) {
     h->dl[l].items = h->items_dev + first[l];
     h->dl[l].nitems = (int)h->plan.levels[l].items.size();
+    h->dl[l].bitems = h->items_dev + bfirst[l];
+    h->dl[l].nbitems = (int)h->plan.levels[l].bitems.size();
+    h->dl[l].has_span = false;
+    for (const StageItem& it : h->plan.levels[l].bitems) h->dl[l].has_span = h->dl[l].has_span || it.span >= 0;
   }
   return AMR_OK;
 }

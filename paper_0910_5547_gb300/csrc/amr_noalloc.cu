@@ -164,6 +164,7 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   a.idz0 = 1.0 / dx[2];
   a.fuse_rate = 0;
   a.dynamic = 0;
+  a.spans = nullptr;   // one patch: per-patch blocks only
   a.ph = ph;
   const int nseg = (int)L.ghost.size();
   const int gseg = nseg < 65535 ? nseg : 65535;

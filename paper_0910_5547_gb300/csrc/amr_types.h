@@ -59,12 +59,26 @@ AMR_HD inline int64_t cell_index(const PatchDesc& p, int i, int j, int k) {
   return ((int64_t)(k + kGhost) * p.m1 + (j + kGhost)) * p.pitch + (i + kGhost);
 }
 
-// One CTA of the fused stage kernel: a wx * wy column block of one patch,
-// marching through z in [z0, z0 + wz).
+// One CTA of the fused stage kernel: a wx * wy column block marching through
+// wz planes.  span < 0: a block of patch `patch` starting at its local cell
+// (x0, y0, z0).  span >= 0: a block of one z-layer of a level (patches with
+// the same z range that tile a rectangle), described by spans[span]; its
+// columns may lie in different patches of the layer.
 struct StageItem {
   int patch;
   int16_t x0, y0, z0, wx, wy, wz;
-  int16_t pad;
+  int span;
+};
+
+// A stage work item spanning patches: the level index of its first cell
+// (ox, oy, oz) and the patches of its z-layer that meet the block grown by the
+// two halo cells in x and y (each column, and each halo cell inside the layer,
+// lies in one of them).
+constexpr int kSpanMax = 24;
+struct ItemSpan {
+  int ox, oy, oz;
+  int n;
+  int patch[kSpanMax];
 };
 
 // Box copy used by ghost fill and parent-tile gather.  dst cell (a, b, c) of

@@ -378,6 +378,10 @@ amr_status validate_config(const amr_config& c, std::string& msg) {
   }
   if (c.riemann == AMR_FLUXREC && c.nvar != 5) { msg = "AMR_FLUXREC is for the Euler system (nvar 5)"; return AMR_ERR_ARG; }
   if (c.recon != AMR_PLM && c.recon != AMR_WENO3) { msg = "recon must be AMR_PLM or AMR_WENO3"; return AMR_ERR_ARG; }
+  if (c.item_span != AMR_SPAN_LAYERS && c.item_span != AMR_SPAN_PATCH) {
+    msg = "item_span must be AMR_SPAN_LAYERS or AMR_SPAN_PATCH";
+    return AMR_ERR_ARG;
+  }
   if (c.ghost_fill != AMR_GHOST_DIRECT && c.ghost_fill != AMR_GHOST_COPY) {
     msg = "ghost_fill must be AMR_GHOST_DIRECT or AMR_GHOST_COPY";
     return AMR_ERR_ARG;
@@ -535,36 +539,123 @@ void build_items(Plan& plan, const TileParams& tp) {
       s += w;
     }
   };
+  auto zsplit = [&](int nz, std::vector<std::pair<int, int>>& zs) {
+    const int zparts = nz <= zchunk + zchunk / 2 ? 1 : (nz + zchunk - 1) / zchunk;
+    split(nz, zparts, zs);
+  };
+  // one halo cell per thread: 4 (wx + wy) <= threads (= max_cols); plane with halo within
+  // the shared-memory plane of the CTA size that runs the tile
+  auto wy_max = [&](int wx) {
+    const int w = std::min(std::min(max_cols / wx, stage_plane_max(max_cols) / (wx + 4) - 4), max_cols / 4 - wx);
+    return std::max(w, 1);
+  };
+  // tiles of an n0 x n1 rectangle, each with its z chunks, as (x0, wx, y0, wy)
+  auto tiles = [&](int n0, int n1, std::vector<std::array<int, 4>>& out) {
+    out.clear();
+    std::vector<std::pair<int, int>> xs, ys;
+    split(n0, (n0 + max_wx - 1) / max_wx, xs);
+    for (auto& x : xs) {
+      const int wymax = wy_max(x.second);
+      split(n1, (n1 + wymax - 1) / wymax, ys);
+      for (auto& y : ys) out.push_back({x.first, x.second, y.first, y.second});
+    }
+  };
+  plan.spans.clear();
   for (size_t l = 0; l < plan.levels.size(); ++l) {
     LevelPlan& L = plan.levels[l];
     L.items.clear();
     L.item_first.clear();
     L.item_first.push_back(0);
+    std::vector<std::pair<int, int>> zs;
+    std::vector<std::array<int, 4>> ts;
     for (int i = L.first; i < L.first + L.count; ++i) {
       const HPatch& p = P[i];
-      std::vector<std::pair<int, int>> xs, ys, zs;
-      split(p.n[0], (p.n[0] + max_wx - 1) / max_wx, xs);
-      int zparts = p.n[2] <= zchunk + zchunk / 2 ? 1 : (p.n[2] + zchunk - 1) / zchunk;
-      split(p.n[2], zparts, zs);
-      for (auto& z : zs)
-        for (auto& x : xs) {
-          // one halo cell per thread: 4 (wx + wy) <= threads (= max_cols); plane with halo within
-          // the shared-memory plane of the CTA size that runs the tile
-          int wymax = std::min(std::min(max_cols / x.second, stage_plane_max(max_cols) / (x.second + 4) - 4),
-                               max_cols / 4 - x.second);
-          wymax = std::max(wymax, 1);
-          split(p.n[1], (p.n[1] + wymax - 1) / wymax, ys);
-          for (auto& y : ys) {
-            StageItem it{};
-            it.patch = i;
-            it.x0 = (int16_t)x.first; it.wx = (int16_t)x.second;
-            it.y0 = (int16_t)y.first; it.wy = (int16_t)y.second;
-            it.z0 = (int16_t)z.first; it.wz = (int16_t)z.second;
-            L.items.push_back(it);
-          }
+      zsplit(p.n[2], zs);
+      for (auto& z : zs) {
+        tiles(p.n[0], p.n[1], ts);
+        for (auto& tl : ts) {
+          StageItem it{};
+          it.patch = i;
+          it.x0 = (int16_t)tl[0]; it.wx = (int16_t)tl[1];
+          it.y0 = (int16_t)tl[2]; it.wy = (int16_t)tl[3];
+          it.z0 = (int16_t)z.first; it.wz = (int16_t)z.second;
+          it.span = -1;
+          L.items.push_back(it);
         }
+      }
       L.item_first.push_back((int)L.items.size());
     }
+    // batched launches: the z-layers of the level whose patches tile a rectangle
+    // (same z range) are tiled as one region, so a column block may take cells of
+    // several patches and small patches fill whole CTAs; other patches keep
+    // their own blocks
+    L.bitems.clear();
+    if (!tp.span || plan.cfg.item_span != AMR_SPAN_LAYERS || plan.cfg.riemann == AMR_FLUXREC) {
+      L.bitems = L.items;
+      continue;
+    }
+    std::map<std::pair<int, int>, std::vector<int>> layers;   // (lo z, n z) -> patches
+    for (int i = L.first; i < L.first + L.count; ++i) layers[{P[i].lo[2], P[i].n[2]}].push_back(i);
+    std::vector<char> spanned(L.count, 0);
+    for (auto& kv : layers) {
+      const std::vector<int>& ps = kv.second;
+      if (ps.size() < 2) continue;
+      int lo0 = INT32_MAX, lo1 = INT32_MAX, hi0 = INT32_MIN, hi1 = INT32_MIN;
+      int64_t area = 0;
+      for (int i : ps) {
+        lo0 = std::min(lo0, P[i].lo[0]); hi0 = std::max(hi0, P[i].lo[0] + P[i].n[0]);
+        lo1 = std::min(lo1, P[i].lo[1]); hi1 = std::max(hi1, P[i].lo[1] + P[i].n[1]);
+        area += (int64_t)P[i].n[0] * P[i].n[1];
+      }
+      if (area != (int64_t)(hi0 - lo0) * (hi1 - lo1)) continue;   // not a full rectangle (patches never overlap)
+      tiles(hi0 - lo0, hi1 - lo1, ts);
+      zsplit(kv.first.second, zs);
+      // span the layer only where that fills the CTAs markedly better than the
+      // patches' own blocks (a block over several patches pays a patch lookup per
+      // column and halo cell)
+      {
+        int64_t own_blocks = 0;
+        for (int i : ps) own_blocks += L.item_first[i - L.first + 1] - L.item_first[i - L.first];
+        own_blocks /= std::max<int64_t>(1, (int64_t)zs.size());   // per z chunk of the layer's patches
+        const double own_fill = (double)area / ((double)own_blocks * max_cols);
+        const double span_fill = (double)area / ((double)ts.size() * max_cols);
+        if (span_fill < own_fill + 0.05) continue;
+      }
+      std::vector<ItemSpan> sp;
+      bool ok = true;
+      for (auto& tl : ts) {
+        ItemSpan S{};
+        S.ox = lo0 + tl[0];
+        S.oy = lo1 + tl[2];
+        const int gx0 = S.ox - kGhost, gx1 = S.ox + tl[1] + kGhost, gy0 = S.oy - kGhost, gy1 = S.oy + tl[3] + kGhost;
+        for (int i : ps)
+          if (std::max(gx0, P[i].lo[0]) < std::min(gx1, P[i].lo[0] + P[i].n[0]) &&
+              std::max(gy0, P[i].lo[1]) < std::min(gy1, P[i].lo[1] + P[i].n[1])) {
+            if (S.n == kSpanMax) { ok = false; break; }
+            S.patch[S.n++] = i;
+          }
+        if (!ok) break;
+        sp.push_back(S);
+      }
+      if (!ok) continue;
+      for (auto& z : zs)
+        for (size_t k = 0; k < ts.size(); ++k) {
+          ItemSpan S = sp[k];
+          S.oz = kv.first.first + z.first;
+          StageItem it{};
+          it.patch = S.patch[0];
+          it.wx = (int16_t)ts[k][1];
+          it.wy = (int16_t)ts[k][3];
+          it.wz = (int16_t)z.second;
+          it.span = (int)plan.spans.size();
+          plan.spans.push_back(S);
+          L.bitems.push_back(it);
+        }
+      for (int i : ps) spanned[i - L.first] = 1;
+    }
+    for (int ii = 0; ii < L.count; ++ii)
+      if (!spanned[ii])
+        L.bitems.insert(L.bitems.end(), L.items.begin() + L.item_first[ii], L.items.begin() + L.item_first[ii + 1]);
   }
 }
 

@@ -49,8 +49,10 @@ struct NoInitAlloc : std::allocator<T> {
 
 struct LevelPlan {
   int first = 0, count = 0;                  // patch range [first, first + count)
-  std::vector<StageItem> items;              // stage work items, grouped by patch
+  std::vector<StageItem> items;              // stage work items, grouped by patch (plain launches)
   std::vector<int> item_first;               // per patch of the level: first item (size count + 1)
+  std::vector<StageItem> bitems;             // items of the batched launch (blocks may span the patches
+                                             //   of a z-layer that tiles a rectangle)
   std::vector<CopySeg> ghost;                // sibling copies + outflow boundary, grouped by dst patch
   std::vector<int> ghost_first;              // per patch (size count + 1)
   std::vector<CopySeg> ghost_stage;          // the ghost segments of the faces a stage does not read
@@ -77,6 +79,7 @@ struct Plan {
   std::vector<HPatch> patches;
   std::vector<PatchDesc> desc;
   std::vector<LevelPlan> levels;
+  std::vector<ItemSpan> spans;               // the spanning batched items of all levels
   std::vector<CoverBox> cover;               // covered boxes, grouped by patch
   std::vector<int> cover_first;              // size npatch + 1
   int64_t arena_elems = 0;                   // elements of one state array (U, U1, Uold)
@@ -97,6 +100,7 @@ struct TileParams {
   int max_cols = 0;
   int zchunk = 0;
   int persistent = 0;   // batched stages: persistent CTAs taking items from a device counter
+  int span = 1;         // batched stages: blocks over the z-layers of a level that tile a rectangle
 };
 
 // Regridding: cluster cells flagged on levels min_level .. max_level-1 into the

@@ -181,6 +181,7 @@ struct StageArgs {
   double idx0, idy0, idz0;  // 1 / dx of level 0 (CFL rate)
   int fuse_rate;     // stage 2: accumulate the CFL rate of the new state
   int dynamic;       // persistent CTAs take items from params->work_next (stage_kernel)
+  const ItemSpan* spans;   // the spanning blocks' patch lists (items with span >= 0)
   Phys<T> ph;
 };
 
@@ -247,7 +248,7 @@ __device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, 
 // faces.  The work of plane j is skewed against that of plane j-1 so that
 // one plane costs two barriers.
 template <typename T, int NV, int STAGE, int MINB = (sizeof(T) == 4 && NV == 5) ? 2 : 1, int NT = kStageThreads,
-          bool WENO = false>
+          bool WENO = false, bool SPAN = false>
 __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kPlane = StageDims<NT>::plane, kState = StageDims<NT>::state;
@@ -297,27 +298,63 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
   }
   for (; itn < a.nitems;) {
     const StageItem it = a.items[itn];
-    const PatchDesc P = a.desc[it.patch];
     const int wx = it.wx, wy = it.wy, wz = it.wz;
     const int sw = wx + 4;
     const int ncol = wx * wy;
     T* FY = FX + NV * kFaceX;
     const bool active = t < ncol;
     const int tx = active ? t % wx : 0, ty = active ? t / wx : 0;
+    // the patch among the block's patches (its own patch, or the patches of its
+    // z-layer for a spanning block) that holds level cell (gx, gy) of the layer; -1: none
+    auto find = [&](int gx, int gy) -> int {
+      if (!SPAN || it.span < 0) {
+        const PatchDesc& Q = a.desc[it.patch];
+        return (gx >= Q.lo[0] && gx < Q.lo[0] + Q.n[0] && gy >= Q.lo[1] && gy < Q.lo[1] + Q.n[1]) ? it.patch : -1;
+      }
+      const ItemSpan& S = a.spans[it.span];
+      for (int k = 0; k < S.n; ++k) {
+        const int q = S.patch[k];
+        const PatchDesc& Q = a.desc[q];
+        if (gx >= Q.lo[0] && gx < Q.lo[0] + Q.n[0] && gy >= Q.lo[1] && gy < Q.lo[1] + Q.n[1]) return q;
+      }
+      return -1;
+    };
+    // level index of the block's first cell
+    int ox, oy, oz;
+    if (SPAN && it.span >= 0) {
+      const ItemSpan& S = a.spans[it.span];
+      ox = S.ox; oy = S.oy; oz = S.oz;
+    } else {
+      const PatchDesc& Q = a.desc[it.patch];
+      ox = Q.lo[0] + it.x0; oy = Q.lo[1] + it.y0; oz = Q.lo[2] + it.z0;
+    }
+    // this thread's column: its patch qc and local cell (lx, ly, lz0) at the block's first plane
+    // (SPAN = false: a launch whose blocks all lie in one patch each)
+    int qc = it.patch;
+    if constexpr (SPAN) {
+      if (it.span >= 0) qc = find(ox + tx, oy + ty);
+      if (qc < 0) {   // not reached: the planner puts every column of a block in one of its patches
+        qc = it.patch;
+        bad = true;
+      }
+    }
+    const PatchDesc P = a.desc[qc];
+    const int lx = ox + tx - P.lo[0], ly = oy + ty - P.lo[1], lz0 = oz - P.lo[2];
     const T* Ub = a.Uin + P.off;
     T* Ob = a.Uout + P.off;
     const int vs = (int)P.vstride;
     const int plane = P.pitch * P.m1;
-    const int col = ((it.z0 + kGhost) * P.m1 + (it.y0 + ty + kGhost)) * P.pitch + (it.x0 + tx + kGhost);
+    const int col = ((lz0 + kGhost) * P.m1 + (ly + kGhost)) * P.pitch + (lx + kGhost);
     const int me = (ty + 2) * sw + (tx + 2);
     const int xs = ty * (wx + 2) + (tx + 1);     // x-state slot of the own cell
     const int ys = (ty + 1) * wx + tx;           // y-state slot of the own cell
     // this thread's halo cell (one per thread, 4 (wx + wy) <= blockDim)
     const int nhalo = 4 * (wx + wy);
     const bool has_halo = t < nhalo;
-    // this thread's halo cell at plane z0, planes hpl and variables hvs elements apart:
-    // an interior cell of the patch, or a ghost cell of an x/y face read where the
-    // face's source lies (own ghost cells, a neighbour's interior, outflow boundary cells)
+    // this thread's halo cell at the block's first plane, planes hpl and variables
+    // hvs elements apart: an interior cell of one of the block's patches, or a
+    // ghost cell of an x/y face read where the face's source lies (own ghost
+    // cells, a neighbour's interior, outflow boundary cells)
     const T* hsrc = Ub;
     int hpl = plane, hvs = vs, hpos = 0;
     if (has_halo) {
@@ -332,13 +369,25 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
         hx = c;
         hy = r < 2 ? r - 2 : wy + (r - 2);
       }
-      const int lx = it.x0 + hx, ly = it.y0 + hy;
-      const int f = lx < 0 ? 0 : (lx >= P.n[0] ? 1 : (ly < 0 ? 2 : (ly >= P.n[1] ? 3 : -1)));
-      if (f < 0) {
-        hsrc = Ub + ((it.z0 + kGhost) * P.m1 + (ly + kGhost)) * P.pitch + (lx + kGhost);
-      } else {
-        const FaceSrc fs = a.desc[it.patch].face[f];
-        hsrc = a.Uin + (fs.base + (int64_t)lx * fs.sx + (int64_t)ly * fs.sy + (int64_t)it.z0 * fs.sz);
+      const int hgx = ox + hx, hgy = oy + hy;
+      const int qh = find(hgx, hgy);
+      if (qh >= 0) {
+        const PatchDesc& Q = a.desc[qh];
+        hsrc = a.Uin + Q.off + ((oz - Q.lo[2] + kGhost) * Q.m1 + (hgy - Q.lo[1] + kGhost)) * Q.pitch +
+               (hgx - Q.lo[0] + kGhost);
+        hpl = Q.pitch * Q.m1;
+        hvs = (int)Q.vstride;
+      } else {   // beyond the block's patches: a ghost cell of the face of the patch next to it
+        const bool xh = hx < 0 || hx >= wx;
+        int qi = find(xh ? (hx < 0 ? ox : ox + wx - 1) : hgx, xh ? hgy : (hy < 0 ? oy : oy + wy - 1));
+        if (qi < 0) {   // not reached (the block's own cells lie in its patches)
+          qi = qc;
+          bad = true;
+        }
+        const PatchDesc& Q = a.desc[qi];
+        const FaceSrc fs = Q.face[xh ? (hx < 0 ? 0 : 1) : (hy < 0 ? 2 : 3)];
+        hsrc = a.Uin + (fs.base + (int64_t)(hgx - Q.lo[0]) * fs.sx + (int64_t)(hgy - Q.lo[1]) * fs.sy +
+                        (int64_t)(oz - Q.lo[2]) * fs.sz);
         hpl = fs.sz;
         hvs = fs.vs;
       }
@@ -364,14 +413,14 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     // source of this column's plane z0 + p and its variable stride: the patch's own
     // array inside it; below and above it the z faces' sources (warp-uniform branch)
     auto col_src = [&](int p, int& svs) -> const T* {
-      const int lz = it.z0 + p;
+      const int lz = lz0 + p;
       if (lz >= 0 && lz < P.n[2]) {
         svs = vs;
         return Ub + col + p * plane;
       }
-      const FaceSrc fs = a.desc[it.patch].face[lz < 0 ? 4 : 5];
+      const FaceSrc fs = a.desc[qc].face[lz < 0 ? 4 : 5];
       svs = fs.vs;
-      return a.Uin + (fs.base + (int64_t)(it.x0 + tx) * fs.sx + (int64_t)(it.y0 + ty) * fs.sy + (int64_t)lz * fs.sz);
+      return a.Uin + (fs.base + (int64_t)lx * fs.sx + (int64_t)ly * fs.sy + (int64_t)lz * fs.sz);
     };
 
     // z-march registers at the start of iteration j: wA = w(j-1), wB = w(j),

@@ -35,30 +35,36 @@ struct Ops final : OpsBase {
     ph.ch = ph.ch2 = ph.half_inv_ch = T(0);
     ph.efl = (T)(p.p_floor / (p.gamma - 1.0));
     ph.glm_alpha = (T)p.glm_alpha;
-    cudaFuncSetAttribute(stage_kernel<T, NV, 1, kDef>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, kDef>());
-    cudaFuncSetAttribute(stage_kernel<T, NV, 2, kDef>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, kDef>());
-    cudaFuncSetAttribute(stage_kernel<T, NV, 1, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, 2 * kDef, 128>());
-    cudaFuncSetAttribute(stage_kernel<T, NV, 2, 2 * kDef, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, 2 * kDef, 128>());
-    if constexpr (kAlt128 > 0) {
-      cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)stage_smem_bytes<T, NV, kAlt128, 128>());
-      cudaFuncSetAttribute(stage_kernel<T, NV, 2, kAlt128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)stage_smem_bytes<T, NV, kAlt128, 128>());
+    set_smem<kDef, kStageThreads, false>();
+    set_smem<2 * kDef, 128, false>();
+    if constexpr (kAlt128 > 0) set_smem<kAlt128, 128, false>();
+    set_smem<kDef, kStageThreads, true>();
+    if constexpr (kHasAlt) set_smem<kAlt, kStageThreads, false>();
+  }
+
+  // dynamic shared memory limit of one build (both stages, blocks in one patch or spanning)
+  template <int MINB, int NTT, bool WENO>
+  static void set_smem() {
+    const int sm = (int)stage_smem_bytes<T, NV, MINB, NTT>();
+    constexpr auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaFuncSetAttribute(stage_kernel<T, NV, 1, MINB, NTT, WENO, false>, attr, sm);
+    cudaFuncSetAttribute(stage_kernel<T, NV, 2, MINB, NTT, WENO, false>, attr, sm);
+    cudaFuncSetAttribute(stage_kernel<T, NV, 1, MINB, NTT, WENO, true>, attr, sm);
+    cudaFuncSetAttribute(stage_kernel<T, NV, 2, MINB, NTT, WENO, true>, attr, sm);
+  }
+
+  // launch of one build; span: the items include blocks that span patches
+  template <int MINB, int NTT, bool WENO>
+  static cudaError_t launch(int stage, bool span, int g, cudaStream_t s, const StageArgs<T>& a) {
+    const size_t sm = stage_smem_bytes<T, NV, MINB, NTT>();
+    if (span) {
+      if (stage == 1) stage_kernel<T, NV, 1, MINB, NTT, WENO, true><<<g, NTT, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, MINB, NTT, WENO, true><<<g, NTT, sm, s>>>(a);
+    } else {
+      if (stage == 1) stage_kernel<T, NV, 1, MINB, NTT, WENO, false><<<g, NTT, sm, s>>>(a);
+      else stage_kernel<T, NV, 2, MINB, NTT, WENO, false><<<g, NTT, sm, s>>>(a);
     }
-    cudaFuncSetAttribute(stage_kernel<T, NV, 1, kDef, kStageThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, kDef>());
-    cudaFuncSetAttribute(stage_kernel<T, NV, 2, kDef, kStageThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_smem_bytes<T, NV, kDef>());
-    if (kHasAlt) {
-      cudaFuncSetAttribute(stage_kernel<T, NV, 1, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)stage_smem_bytes<T, NV, kAlt>());
-      cudaFuncSetAttribute(stage_kernel<T, NV, 2, kAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)stage_smem_bytes<T, NV, kAlt>());
-    }
+    return cudaGetLastError();
   }
 
   void set_stage_threads(int n) override { nt = n == 128 ? 128 : kStageThreads; }
@@ -74,13 +80,14 @@ struct Ops final : OpsBase {
   size_t elem_size() const override { return sizeof(T); }
 
   cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
-                    const void* Uin, void* Uout, StepParams* prm, int level, const double dx[3],
-                    const double dx0[3], int fuse_rate, int grid) override {
+                    const ItemSpan* spans, const void* Uin, void* Uout, StepParams* prm, int level,
+                    const double dx[3], const double dx0[3], int fuse_rate, int grid) override {
     if (nitems <= 0) return cudaSuccess;
     StageArgs<T> a;
     a.desc = desc;
     a.items = items;
     a.nitems = nitems;
+    a.spans = spans;
     a.Uin = static_cast<const T*>(Uin);
     a.Uout = static_cast<T*>(Uout);
     a.params = prm;
@@ -103,34 +110,16 @@ struct Ops final : OpsBase {
         return cudaGetLastError();
       }
     }
-    if (weno) {   // any tiling's items fit the 256-thread CTA
-      const size_t sm = stage_smem_bytes<T, NV, kDef>();
-      if (stage == 1) stage_kernel<T, NV, 1, kDef, kStageThreads, true><<<g, kStageThreads, sm, s>>>(a);
-      else stage_kernel<T, NV, 2, kDef, kStageThreads, true><<<g, kStageThreads, sm, s>>>(a);
-      return cudaGetLastError();
-    }
+    const bool span = spans != nullptr;
+    if (weno) return launch<kDef, kStageThreads, true>(stage, span, g, s, a);   // any tiling's items fit 256 threads
     if constexpr (kAlt128 > 0) {
-      if (nt == 128 && occ == kAlt) {
-        const size_t sm = stage_smem_bytes<T, NV, kAlt128, 128>();
-        if (stage == 1) stage_kernel<T, NV, 1, kAlt128, 128><<<g, 128, sm, s>>>(a);
-        else stage_kernel<T, NV, 2, kAlt128, 128><<<g, 128, sm, s>>>(a);
-        return cudaGetLastError();
-      }
+      if (nt == 128 && occ == kAlt) return launch<kAlt128, 128, false>(stage, span, g, s, a);
     }
-    if (nt == 128) {
-      const size_t sm = stage_smem_bytes<T, NV, 2 * kDef, 128>();
-      if (stage == 1) stage_kernel<T, NV, 1, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
-      else stage_kernel<T, NV, 2, 2 * kDef, 128><<<g, 128, sm, s>>>(a);
-    } else if (kHasAlt && occ == kAlt) {
-      const size_t sm = stage_smem_bytes<T, NV, kAlt>();
-      if (stage == 1) stage_kernel<T, NV, 1, kAlt><<<g, kStageThreads, sm, s>>>(a);
-      else stage_kernel<T, NV, 2, kAlt><<<g, kStageThreads, sm, s>>>(a);
-    } else {
-      const size_t sm = stage_smem_bytes<T, NV, kDef>();
-      if (stage == 1) stage_kernel<T, NV, 1, kDef><<<g, kStageThreads, sm, s>>>(a);
-      else stage_kernel<T, NV, 2, kDef><<<g, kStageThreads, sm, s>>>(a);
+    if (nt == 128) return launch<2 * kDef, 128, false>(stage, span, g, s, a);
+    if constexpr (kHasAlt) {
+      if (occ == kAlt) return launch<kAlt, kStageThreads, false>(stage, span, g, s, a);
     }
-    return cudaGetLastError();
+    return launch<kDef, kStageThreads, false>(stage, span, g, s, a);
   }
 
   static int grid_for(int n) { return n < 65535 ? n : 65535; }

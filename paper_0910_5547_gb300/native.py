@@ -28,6 +28,7 @@ AMR_PLM, AMR_WENO3 = 0, 1
 AMR_BC_OUTFLOW, AMR_BC_PERIODIC = 0, 1
 AMR_STATE_CONSERVED, AMR_STATE_PRIMITIVE = 0, 1
 AMR_GHOST_DIRECT, AMR_GHOST_COPY = 0, 1
+AMR_SPAN_LAYERS, AMR_SPAN_PATCH = 0, 1
 
 STATUS_NAMES = {0: "AMR_OK", -1: "AMR_ERR_ARG", -2: "AMR_ERR_NESTING", -3: "AMR_ERR_CUDA",
                 -4: "AMR_ERR_NONPHYSICAL", -5: "AMR_ERR_TIMEOUT", -6: "AMR_ERR_STATE"}
@@ -82,6 +83,7 @@ class amr_config(ctypes.Structure):
         ("alloc_ctx", ctypes.c_void_p),
         ("recon", ctypes.c_int),
         ("ghost_fill", ctypes.c_int),
+        ("item_span", ctypes.c_int),
     ]
 
 

@@ -23,7 +23,7 @@ class Solver:
                  gamma=1.4, theta=1.5, cfl=0.4, base_n=(32, 32, 32), bc=(0,) * 6, max_level=None,
                  riemann="hll", ch=0.0, batched=True, use_graph=True, domain_lo=(0.0, 0.0, 0.0),
                  domain_hi=(1.0, 1.0, 1.0), kind=N.AMR_STATE_PRIMITIVE, stream=None, p_floor=0.0,
-                 glm_alpha=0.0, allocator=None, recon="plm", ghost_fill="direct"):
+                 glm_alpha=0.0, allocator=None, recon="plm", ghost_fill="direct", item_span="layers"):
         self.patches = list(patches)
         self.nvar = nvar
         if max_level is None:
@@ -36,6 +36,7 @@ class Solver:
             batched=int(batched), use_graph=int(use_graph),
             recon={"plm": N.AMR_PLM, "weno3": N.AMR_WENO3}[recon],
             ghost_fill={"direct": N.AMR_GHOST_DIRECT, "copy": N.AMR_GHOST_COPY}[ghost_fill],
+            item_span={"layers": N.AMR_SPAN_LAYERS, "patch": N.AMR_SPAN_PATCH}[item_span],
             domain_lo=domain_lo, domain_hi=domain_hi, cuda_stream=stream)
         # allocator="torch": device memory from PyTorch's caching allocator (callbacks kept alive here)
         self._alloc_fns = N.torch_allocator() if allocator == "torch" else None
