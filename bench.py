@@ -655,6 +655,17 @@ def main():
             out["launch_form"] = {"chosen": "persistent" if chosen[4] else "one CTA per item",
                                   "tiling": list(chosen[:4]),
                                   "other_form_value": ws * cu * ka / max_over_ranks(t_other)}
+            # the same step on one stream (no second stream for the stage-2 parent fill and the registers)
+            so = make_solver(pb, "fp32", True, True, stream)
+            so.set_tiling(*chosen[:4])
+            so.set_persistent(chosen[4])
+            so.set_overlap(False)
+            for _ in range(2):
+                so.step(0.0, sync=False)
+            t_one = timed_steps(torch, so, stream, ka)
+            so.check()
+            so.close()
+            out["one_stream_value"] = ws * cu * ka / max_over_ranks(t_one)
         if fp64_plain_steps:
             def one(precision, batched, steps):
                 sp = make_solver(pb, precision, batched, batched, stream)

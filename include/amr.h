@@ -84,7 +84,8 @@ typedef struct {
   void* cuda_stream;     /* cudaStream_t to run on; NULL: the library creates its own */
   /* Device memory: when dev_alloc and dev_free are both set, every device buffer of
    * the handle comes from dev_alloc(bytes, stream, alloc_ctx) (NULL = failure, the call
-   * returns AMR_ERR_CUDA) and goes back through dev_free(ptr, stream, alloc_ctx), both
+   * returns AMR_ERR_CUDA; so does a pointer that is not 256-byte aligned, as cudaMalloc's
+   * are, which is handed back at once) and goes back through dev_free(ptr, stream, alloc_ctx), both
    * ordered on the handle's stream (e.g. a framework's caching allocator); otherwise
    * the library uses cudaMallocAsync / cudaFreeAsync on that stream.  All of it is
    * released by amr_destroy (and old buffers by amr_set_patches / amr_regrid). */
@@ -236,6 +237,18 @@ amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, i
  *      amr_autotune runs, one CTA per item).
  * Same results bit for bit.  AMR_ERR_ARG for another mode. */
 amr_status amr_set_persistent(amr_handle* h, int mode);
+
+/* Second stream of a batched step with more than one level (a scheduling
+ * choice; the paper sends one grid at a time to the GPU, Sec. 3, and has no
+ * counterpart).  on = 1 (default): while a level's stage-1 kernel runs, the
+ * parent-cell gather and prolongation of its stage-2 ghost cells (into a second
+ * parent tile) and its flux-register kernels run on a second stream of the
+ * handle; the stage-2 register kernels run beside the finer levels' steps.
+ * Events order every read after the write it needs, so the results are the
+ * same bit for bit as with on = 0 (one stream, the recursive order of Sec. 3).  With
+ * amr_set_timing on, steps use one stream.  Invalidates the step graphs;
+ * AMR_ERR_ARG for another value. */
+amr_status amr_set_overlap(amr_handle* h, int on);
 
 /* Autotuner: time the stage kernel over the installed hierarchy for each
  * candidate work-item shape (x width, columns per CTA, z chunk) and compiled

@@ -10,6 +10,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -168,6 +169,17 @@ struct amr_handle {
   TileParams tp;            // tile shape in use (autotuned or default)
   int sms = 0;              // SMs of the device (persistent stage grids)
   int persist_mode = -1;    // -1: the autotuner decides; 0 / 1: one CTA per item / persistent CTAs
+  // second stream of a batched multi-level step: the parent-cell gather and
+  // prolongation of a level's stage-2 ghost cells and the flux-register kernels
+  // run on it beside the stage kernels (fork / join through events, captured
+  // into the step graph as parallel branches)
+  bool overlap = true;               // amr_set_overlap
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> side_ev;  // ring of fork / join events
+  size_t side_next = 0;
+  bool side_dirty = false;           // the side stream holds work the main stream has not joined
+  std::vector<cudaEvent_t> u1_ev;    // per level: recorded on the side stream after its last read of U1
+  std::vector<char> u1_pend;         // per level: u1_ev recorded in this step and not yet waited for
   // optional per-class event timing (eager steps only)
   bool timing = false;
   int cur_class = 0;
@@ -226,7 +238,14 @@ cudaError_t dmalloc(amr_handle* h, void** p, size_t bytes) {
   bytes = std::max<size_t>(bytes, 256);
   if (h->cfg.dev_alloc && h->cfg.dev_free) {
     *p = h->cfg.dev_alloc(bytes, h->stream, h->cfg.alloc_ctx);
-    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (!*p) return cudaErrorMemoryAllocation;
+    // the kernels' vector loads and asynchronous copies assume the alignment cudaMalloc gives
+    if (reinterpret_cast<uintptr_t>(*p) % 256 != 0) {
+      h->cfg.dev_free(*p, h->stream, h->cfg.alloc_ctx);
+      *p = nullptr;
+      return cudaErrorMisalignedAddress;
+    }
+    return cudaSuccess;
   }
   if (h->pool) return cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
   return cudaMallocAsync(p, bytes, h->stream);
@@ -430,28 +449,31 @@ double level_dx(const amr_handle* h, int l, int d) { return h->dx0[d] / (double)
 // the faces the stage kernel does not read straight from their source
 // (PatchDesc::face); all = true: every face (for kernels that read ghost cells
 // themselves: regrid flags, div B).
-cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha, bool all = false) {
+cudaError_t fill_parent(amr_handle* h, int l, void* arr, double alpha, cudaStream_t st, void* tile) {
+  const DevLevel& L = h->dl[l];
+  if (l == 0) return cudaSuccess;
+  h->cur_class = AMR_T_PARENT;
+  if (h->cfg.batched) {
+    const DevLevel::Flat& G = L.fgather;
+    const DevLevel::Flat& P = L.fprolong;
+    LK(h->ops->gather_flat(st, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk, G.total, tile,
+                           h->U, h->Uold, alpha));
+    LK(h->ops->prolong_flat(st, static_cast<const FlatProlong*>(P.boxes), P.first, P.chunk_box, P.nchunk, P.total,
+                            tile, arr));
+  } else {
+    LK(h->ops->gather(st, L.gather_ghost, L.ngather_ghost, h->d_desc, tile, h->U, h->Uold, alpha));
+    LK(h->ops->prolong(st, L.prolong, L.nprolong, h->d_desc, tile, arr));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t fill_same(amr_handle* h, int l, void* arr, bool all) {
   const DevLevel& L = h->dl[l];
   const LevelPlan& LP = h->plan.levels[l];
-  const bool batched = h->cfg.batched != 0;
-  if (l > 0) {
-    h->cur_class = AMR_T_PARENT;
-    if (batched) {
-      const DevLevel::Flat& G = L.fgather;
-      const DevLevel::Flat& P = L.fprolong;
-      LK(h->ops->gather_flat(h->stream, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk,
-                             G.total, h->tile, h->U, h->Uold, alpha));
-      LK(h->ops->prolong_flat(h->stream, static_cast<const FlatProlong*>(P.boxes), P.first, P.chunk_box, P.nchunk,
-                              P.total, h->tile, arr));
-    } else {
-      LK(h->ops->gather(h->stream, L.gather_ghost, L.ngather_ghost, h->d_desc, h->tile, h->U, h->Uold, alpha));
-      LK(h->ops->prolong(h->stream, L.prolong, L.nprolong, h->d_desc, h->tile, arr));
-    }
-  }
   h->cur_class = AMR_T_GHOST;
   if (all) {
     LK(h->ops->ghost_copy(h->stream, L.ghost, L.nghost, h->d_desc, arr));
-  } else if (batched) {
+  } else if (h->cfg.batched) {
     const DevLevel::Flat& G = L.fghost;
     LK(h->ops->ghost_copy_flat(h->stream, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk,
                                G.total, arr));
@@ -464,6 +486,52 @@ cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha, bool all 
     }
   }
   return cudaSuccess;
+}
+
+cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha, bool all = false) {
+  cudaError_t e = fill_parent(h, l, arr, alpha, h->stream, h->tile);
+  return e == cudaSuccess ? fill_same(h, l, arr, all) : e;
+}
+
+// ---- the side stream of a step ----
+// Order (main | side), level l, one step:
+//   main: [Uold copy] stage-1 ghosts of U | fork | stage 1 (U -> U1) | join | same-level ghosts of U1 |
+//         stage 2 (U1 -> U) | fork | children | join | restriction, reflux
+//   side: after the first fork: stage-2 parent gather (second tile) and prolongation into U1,
+//         stage-1 registers (read U); after the second fork: stage-2 registers (read U1)
+// Stage 1 of a level waits for the side stream's last read of that level's U1
+// (u1_ev); the joins cover every other hazard (ghost cells of U1 before stage 2;
+// U of the level, which the registers and the children's gathers read, before
+// stage 2 and the restriction write it; the registers before the reflux).
+bool overlap_on(const amr_handle* h) {
+  return h->overlap && h->side && h->cfg.batched && !h->timing && h->dl.size() > 1;
+}
+
+int side_event(amr_handle* h) {
+  if (h->side_ev.empty()) {
+    h->side_ev.resize(64);
+    for (cudaEvent_t& e : h->side_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  }
+  const int k = (int)(h->side_next++ % h->side_ev.size());
+  return k;
+}
+
+// The side stream waits for everything enqueued on the main stream so far.
+cudaError_t fork_side(amr_handle* h) {
+  const int k = side_event(h);
+  cudaError_t e = cudaEventRecord(h->side_ev[k], h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->side_ev[k], 0);
+  return e;
+}
+
+// The main stream waits for everything enqueued on the side stream so far.
+cudaError_t join_side(amr_handle* h) {
+  if (!h->side_dirty) return cudaSuccess;
+  const int k = side_event(h);
+  cudaError_t e = cudaEventRecord(h->side_ev[k], h->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->side_ev[k], 0);
+  if (e == cudaSuccess) h->side_dirty = false;
+  return e;
 }
 
 cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
@@ -490,6 +558,44 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
 
 amr_status regrid_impl(amr_handle* h, const RegridParams& rp, int mid_level, double alpha);
 
+cudaError_t u1_wait(amr_handle* h, int l) {
+  if (l >= (int)h->u1_pend.size() || !h->u1_pend[l]) return cudaSuccess;
+  h->u1_pend[l] = 0;
+  return cudaStreamWaitEvent(h->stream, h->u1_ev[l], 0);
+}
+
+cudaError_t u1_mark(amr_handle* h, int l) {
+  if ((int)h->u1_ev.size() <= l) {
+    const size_t n0 = h->u1_ev.size();
+    h->u1_ev.resize(l + 1, nullptr);
+    h->u1_pend.resize(l + 1, 0);
+    for (size_t k = n0; k < h->u1_ev.size(); ++k) {
+      cudaError_t e = cudaEventCreateWithFlags(&h->u1_ev[k], cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  cudaError_t e = cudaEventRecord(h->u1_ev[l], h->side);
+  if (e == cudaSuccess) h->u1_pend[l] = 1;
+  return e;
+}
+
+// The two flux-register kernels after stage s of level l on stream st: the
+// coarse side of the registers of level l+1 and the fine side of level l's.
+cudaError_t registers(amr_handle* h, int l, int s, const void* in, cudaStream_t st) {
+  const bool kids = l + 1 < (int)h->dl.size();
+  h->cur_class = AMR_T_REG;
+  if (kids) {
+    DevLevel& K = h->dl[l + 1];
+    if (K.nreg)
+      LK(h->ops->reg_coarse(st, K.regs, K.reg_first, K.reg_chunk, K.nrect, K.nreg, h->d_desc, in, K.R, h->params, l,
+                            s));
+  }
+  DevLevel& L = h->dl[l];
+  if (l > 0 && L.nreg)
+    LK(h->ops->reg_fine(st, L.regs, L.reg_first, L.reg_chunk, L.nrect, L.nreg, h->d_desc, in, L.R, h->params, l));
+  return cudaSuccess;
+}
+
 cudaError_t advance(amr_handle* h, int l, double alpha0) {
   static const char* names[] = {"level 0 step", "level 1 step", "level 2 step", "level 3 step", "level 4 step",
                                 "level 5 step", "level 6 step", "level 7+ step"};
@@ -497,6 +603,7 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
   if (!h->capturing) h->cell_updates += h->plan.levels[l].cells;
   const int nlev = (int)h->dl.size();
   const bool kids = l + 1 < nlev;
+  const bool ov = overlap_on(h);
   DevLevel& L = h->dl[l];
   const size_t es = h->ops->elem_size();
   if (kids) {
@@ -506,32 +613,34 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
   }
   cudaError_t e;
   if ((e = fill_ghosts(h, l, h->U, alpha0)) != cudaSuccess) return e;
-  if ((e = stage(h, l, 1, h->U, h->U1)) != cudaSuccess) return e;
-  h->cur_class = AMR_T_REG;
-  if (kids) {
-    DevLevel& K = h->dl[l + 1];
-    if (K.nreg)
-      LK(h->ops->reg_coarse(h->stream, K.regs, K.reg_first, K.reg_chunk, K.nrect, K.nreg, h->d_desc, h->U, K.R,
-                            h->params, l, 1));
+  if (ov) {
+    // stage 2's parent cells into the second tile and prolonged into U1's ghost
+    // cells, and stage 1's registers, beside stage 1
+    if ((e = fork_side(h)) != cudaSuccess) return e;
+    void* tile2 = h->tile ? (char*)h->tile + std::max<int64_t>(h->plan.tile_elems, 1) * es : nullptr;
+    if ((e = fill_parent(h, l, h->U1, alpha0 + 0.5, h->side, tile2)) != cudaSuccess) return e;
+    if ((e = registers(h, l, 1, h->U, h->side)) != cudaSuccess) return e;
+    h->side_dirty = true;
+    if ((e = u1_wait(h, l)) != cudaSuccess) return e;
+    if ((e = stage(h, l, 1, h->U, h->U1)) != cudaSuccess) return e;
+    if ((e = join_side(h)) != cudaSuccess) return e;
+    if ((e = fill_same(h, l, h->U1, false)) != cudaSuccess) return e;
+    if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;
+    if ((e = fork_side(h)) != cudaSuccess) return e;
+    if ((e = registers(h, l, 2, h->U1, h->side)) != cudaSuccess) return e;
+    if ((e = u1_mark(h, l)) != cudaSuccess) return e;
+    h->side_dirty = true;
+  } else {
+    if ((e = stage(h, l, 1, h->U, h->U1)) != cudaSuccess) return e;
+    if ((e = registers(h, l, 1, h->U, h->stream)) != cudaSuccess) return e;
+    if ((e = fill_ghosts(h, l, h->U1, alpha0 + 0.5)) != cudaSuccess) return e;
+    if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;
+    if ((e = registers(h, l, 2, h->U1, h->stream)) != cudaSuccess) return e;
   }
-  if (l > 0 && L.nreg)
-    LK(h->ops->reg_fine(h->stream, L.regs, L.reg_first, L.reg_chunk, L.nrect, L.nreg, h->d_desc, h->U, L.R,
-                        h->params, l));
-  if ((e = fill_ghosts(h, l, h->U1, alpha0 + 0.5)) != cudaSuccess) return e;
-  if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;
-  h->cur_class = AMR_T_REG;
-  if (kids) {
-    DevLevel& K = h->dl[l + 1];
-    if (K.nreg)
-      LK(h->ops->reg_coarse(h->stream, K.regs, K.reg_first, K.reg_chunk, K.nrect, K.nreg, h->d_desc, h->U1, K.R,
-                            h->params, l, 2));
-  }
-  if (l > 0 && L.nreg)
-    LK(h->ops->reg_fine(h->stream, L.regs, L.reg_first, L.reg_chunk, L.nrect, L.nreg, h->d_desc, h->U1, L.R,
-                        h->params, l));
   if (kids) {
     if ((e = advance(h, l + 1, 0.0)) != cudaSuccess) return e;
     if ((e = advance(h, l + 1, 0.5)) != cudaSuccess) return e;
+    if ((e = join_side(h)) != cudaSuccess) return e;
     DevLevel& K = h->dl[l + 1];
     h->cur_class = AMR_T_SYNC;
     if (h->cfg.batched) {
@@ -555,11 +664,17 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
   // scheduled regrid: rebuild the levels finer than l now that l has completed a
   // step (its parent has reached fraction alpha0 + 1/2 of its own step)
   if (h->sched_on && l <= h->sched_level && l < h->cfg.max_level) {
+    if ((e = join_side(h)) != cudaSuccess) return e;
     const amr_status st = regrid_impl(h, h->sched_rp, l, l == 0 ? 1.0 : alpha0 + 0.5);
+    for (char& p : h->u1_pend) p = 0;   // the side stream was joined
     if (st != AMR_OK) {
       h->sched_status = st;
       return cudaErrorUnknown;
     }
+  }
+  if (l == 0) {   // a step ends with nothing left on the side stream
+    if ((e = join_side(h)) != cudaSuccess) return e;
+    for (char& p : h->u1_pend) p = 0;
   }
   return cudaSuccess;
 }
@@ -832,7 +947,8 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   if (nlev > 1) {
     CK(dmalloc(h, &h->Uold, pl.arena_elems * es));
     CK(cudaMemsetAsync(h->Uold, 0, pl.arena_elems * es, h->stream));
-    CK(dmalloc(h, &h->tile, std::max<int64_t>(pl.tile_elems, 1) * es));
+    // two parent tiles: stage 1's and (gathered on the side stream meanwhile) stage 2's
+    CK(dmalloc(h, &h->tile, 2 * std::max<int64_t>(pl.tile_elems, 1) * es));
   }
   CK(dmalloc(h, &p, (size_t)h->nchunk * nv * sizeof(double)));
   h->partial = static_cast<double*>(p);
@@ -1241,6 +1357,12 @@ amr_status amr_create(const amr_config* cfg, amr_handle** out) {
     }
     h->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+    g_global_err = "cudaStreamCreate failed";
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return AMR_ERR_CUDA;
+  }
   h->ops = make_ops(*cfg);
   {
     int dev = 0;
@@ -1454,6 +1576,19 @@ amr_status amr_set_tiling(amr_handle* h, int max_wx, int max_cols, int zchunk, i
   if (!h->ready) return AMR_OK;
   build_items(h->plan, h->tp);
   return upload_items(h);
+}
+
+amr_status amr_set_overlap(amr_handle* h, int on) {
+  if (!h) return AMR_ERR_ARG;
+  if (on != 0 && on != 1) return fail(h, AMR_ERR_ARG, "on must be 0 or 1");
+  if (h->overlap != (on == 1)) {
+    h->overlap = on == 1;
+    for (int g = 0; g < 4; ++g) {
+      if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+      h->graph[g] = nullptr;
+    }
+  }
+  return AMR_OK;
 }
 
 amr_status amr_set_persistent(amr_handle* h, int mode) {
@@ -1806,10 +1941,15 @@ const char* amr_last_error(const amr_handle* h) { return h ? h->err.c_str() : "n
 
 void amr_destroy(amr_handle* h) {
   if (!h) return;
+  if (h->side) cudaStreamSynchronize(h->side);
   if (h->stream) cudaStreamSynchronize(h->stream);
   release_async(h);
   free_device(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->side_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->u1_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   dfree(h, h->params);
   if (h->stream) cudaStreamSynchronize(h->stream);   // stream-ordered frees done
   if (h->pool) cudaMemPoolDestroy(h->pool);

@@ -100,7 +100,7 @@ struct CopySeg {
 constexpr int kBoxThreads = 256;
 constexpr int kCopyPerThread = 4;
 constexpr int kCopyChunk = kBoxThreads * kCopyPerThread;
-constexpr int kProlongPerThread = 2;
+constexpr int kProlongPerThread = 1;   // parent cells (eight fine cells each)
 constexpr int kProlongChunk = kBoxThreads * kProlongPerThread;
 constexpr int kRestrictPerThread = 2;
 constexpr int kRestrictChunk = kBoxThreads * kRestrictPerThread;
@@ -119,16 +119,19 @@ struct alignas(16) FlatCopy {
   int pad;
 };
 
-// Prolongation box: fine cell (a, b, c) at dst0 + a + b dsy + c dsz has the
-// global fine coordinate g = g0 + (a, b, c) and parent tile cell
-// (g >> 1) - cb, i.e. tile0 + cx + cy tsy + cz tsz (variable stride tvol).
+// Prolongation box, walked by parent cell: parent (pa, pb, pc) of the box is
+// the tile cell tp0 + pa + pb tsy + pc tsz (variable stride tvol) and has the
+// children a = 2 pa + i - odd_x, b = 2 pb + j - odd_y, c = 2 pc + k - odd_z
+// (i, j, k in {0, 1}) in the fine box [0, n) at dst0 + a + b dsy + c dsz
+// (variable stride dvs); children outside the box are skipped.  odd_d is the
+// parity of the box's first fine cell along d, np0 x np1 the parents per plane.
 struct alignas(16) FlatProlong {
-  int64_t dst0, tile0;
+  int64_t dst0, tp0;
   int dvs, dsy, dsz;
   int tvol, tsy, tsz;
-  int g0[3];
-  int cb[3];
-  int n0, n1;
+  int n[3];
+  int np0, np1;
+  int odd;   // bit d: odd_d
 };
 
 // Box of fine ghost cells filled by prolongation from the parent tile.

@@ -336,7 +336,7 @@ void split_prolong(std::vector<ProlongBox>& v, size_t from) {
       int k = 0;
       for (int a = 1; a < 3; ++a) if (s.n[a] > s.n[k]) k = a;
       ProlongBox a = s, b = s;
-      a.n[k] = (int16_t)(s.n[k] / 2);
+      a.n[k] = (int16_t)((s.n[k] / 2 + 1) & ~1);   // even: no parent cell split between the halves
       b.n[k] = (int16_t)(s.n[k] - a.n[k]);
       b.lo[k] = (int16_t)(s.lo[k] + a.n[k]);
       work.push_back(b);
@@ -713,6 +713,8 @@ void flatten_copies(const Plan& plan, const std::vector<CopySeg>& segs, bool gat
   finish_flat(f, cells, kCopyChunk);
 }
 
+int floor_half(int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); }
+
 void flatten_prolong(const Plan& plan, const std::vector<ProlongBox>& boxes, FlatList<FlatProlong>& f) {
   f = FlatList<FlatProlong>();
   std::vector<int> cells;
@@ -720,21 +722,25 @@ void flatten_prolong(const Plan& plan, const std::vector<ProlongBox>& boxes, Fla
     const PatchDesc& D = plan.desc[b.patch];
     FlatProlong c{};
     c.dst0 = D.off + cell_index(D, b.lo[0], b.lo[1], b.lo[2]);
-    c.tile0 = D.tile_off;
     c.dvs = (int)D.vstride;
     c.dsy = D.pitch;
     c.dsz = D.pitch * D.m1;
     c.tvol = D.tn[0] * D.tn[1] * D.tn[2];
     c.tsy = D.tn[0];
     c.tsz = D.tn[0] * D.tn[1];
+    int p0[3], np[3];
     for (int d = 0; d < 3; ++d) {
-      c.g0[d] = D.lo[d] + b.lo[d];
-      c.cb[d] = (D.lo[d] >> 1) - 2;
+      const int g0 = D.lo[d] + b.lo[d];
+      p0[d] = floor_half(g0) - (floor_half(D.lo[d]) - 2);   // tile-local parent of the first fine cell
+      np[d] = floor_half(g0 + b.n[d] - 1) - floor_half(g0) + 1;
+      c.n[d] = b.n[d];
+      if (g0 & 1) c.odd |= 1 << d;
     }
-    c.n0 = b.n[0];
-    c.n1 = b.n[1];
+    c.tp0 = D.tile_off + p0[0] + (int64_t)p0[1] * c.tsy + (int64_t)p0[2] * c.tsz;
+    c.np0 = np[0];
+    c.np1 = np[1];
     f.boxes.push_back(c);
-    cells.push_back(b.n[0] * b.n[1] * b.n[2]);
+    cells.push_back(np[0] * np[1] * np[2]);
   }
   finish_flat(f, cells, kProlongChunk);
 }
@@ -1110,7 +1116,10 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
         for (int d = 0; d < 3; ++d) {
           int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
           int Nl = level_n(cfg, l, d);
-          for (int side = 0; side < 2; ++side)
+          for (int side = 0; side < 2; ++side) {
+            // one neighbour query for both ghost layers of the face when they are
+            // adjacent level cells (the loop below keeps the patches of each layer)
+            int qd_lo = 0, qd_hi = 0;   // layer range along d the current cand covers
             for (int gg = 0; gg < kGhost; ++gg) {
               int loc = side ? p.n[d] + gg : -1 - gg;
               int G = p.lo[d] + loc;
@@ -1128,12 +1137,21 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 G = ((G % Nl) + Nl) % Nl;
               }
               int A = p.n[t1], B = p.n[t2];
-              {
+              if (!(G >= qd_lo && G < qd_hi)) {
                 int qlo[3], qhi[3];
                 qlo[d] = G; qhi[d] = G + 1;
+                if (gg + 1 < kGhost) {   // the next layer, if it lies next to this one in the level
+                  const int Gn = p.lo[d] + (side ? p.n[d] + gg + 1 : -2 - gg);
+                  if (Gn >= 0 && Gn < Nl && (Gn == G + 1 || Gn == G - 1)) {
+                    qlo[d] = std::min(G, Gn);
+                    qhi[d] = std::max(G, Gn) + 1;
+                  }
+                }
                 qlo[t1] = p.lo[t1]; qhi[t1] = p.lo[t1] + p.n[t1];
                 qlo[t2] = p.lo[t2]; qhi[t2] = p.lo[t2] + p.n[t2];
                 six.query(qlo, qhi, cand);
+                qd_lo = qlo[d];
+                qd_hi = qhi[d];
               }
               const size_t g0 = Gv.size();
               int64_t area = 0;      // same-level patches do not overlap: the covered area sums
@@ -1175,6 +1193,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 Pv.push_back(pb);
               }
             }
+          }
         }
         // merge the two ghost layers of a face into one two-deep segment where
         // both layers copy from the same source with the same mapping
@@ -1251,15 +1270,17 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   }
 
   // ---- restriction segments and coverage boxes ----
-  std::vector<int> cand;
   plan.cover_first.assign(np + 1, 0);
   std::vector<std::vector<CoverBox>> cov(np);
   for (int l = 1; l < nlev; ++l) {
     LevelPlan& L = plan.levels[l];
     const LevelPlan& C = plan.levels[l - 1];
     PatchIndex cix(P, C.first, C.count);
-    for (int i = L.first; i < L.first + L.count; ++i) {
+    std::vector<std::vector<RestrictSeg>> rsegs(L.count);   // per fine patch, concatenated in patch order
+    parallel_for(L.count, [&](int ii) {
+      const int i = L.first + ii;
       const HPatch& f = P[i];
+      std::vector<int> cand;
       {
         int qlo[3], qhi[3];
         for (int d = 0; d < 3; ++d) { qlo[d] = f.lo[d] / 2; qhi[d] = (f.lo[d] + f.n[d]) / 2; }
@@ -1277,15 +1298,20 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
         if (!ok) continue;
         RestrictSeg r{};
         r.fine = i; r.coarse = q;
-        CoverBox cb{};
         for (int d = 0; d < 3; ++d) {
-          r.clo[d] = (int16_t)(lo[d] - o.lo[d]); r.cn[d] = (int16_t)(hi[d] - lo[d]);
-          cb.lo[d] = r.clo[d]; cb.n[d] = r.cn[d];
+          r.clo[d] = (int16_t)(lo[d] - o.lo[d]);
+          r.cn[d] = (int16_t)(hi[d] - lo[d]);
         }
-        L.restrict_segs.push_back(r);
-        cov[q].push_back(cb);
+        rsegs[ii].push_back(r);
       }
-    }
+    });
+    for (int ii = 0; ii < L.count; ++ii)
+      for (const RestrictSeg& r : rsegs[ii]) {
+        L.restrict_segs.push_back(r);
+        CoverBox cb{};
+        for (int d = 0; d < 3; ++d) { cb.lo[d] = r.clo[d]; cb.n[d] = r.cn[d]; }
+        cov[r.coarse].push_back(cb);
+      }
   }
   for (int l = 1; l < nlev; ++l) split_restrict(plan.levels[l].restrict_segs);
   for (int i = 0; i < np; ++i) {
@@ -1357,22 +1383,41 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
               if (std::find(qs.begin(), qs.end(), owner[e]) == qs.end()) qs.push_back(owner[e]);
             }
           std::sort(qs.begin(), qs.end());
+          // level-l patches near the face: coarse cells [Cd - 1, Cd + 2) along d and one
+          // cell beyond the face's extent in-plane (every box covered_any asks about
+          // that does not wrap lies inside)
+          std::vector<int> near;
+          int nlo[3], nhi[3];
+          nlo[d] = Cd - 1; nhi[d] = Cd + 2;
+          nlo[t1] = a0 - 1; nhi[t1] = a0 + A + 1;
+          nlo[t2] = b0 - 1; nhi[t2] = b0 + B + 1;
+          {
+            int qlo[3], qhi[3];
+            for (int k = 0; k < 3; ++k) { qlo[k] = 2 * nlo[k]; qhi[k] = 2 * nhi[k]; }
+            fix.query(qlo, qhi, near);
+          }
           // does a level-l patch cover any coarse cell of [lo, hi) (level l-1 indices; a
           // cell beyond an outflow face is not covered, periodic axes wrap)
+          std::vector<int> cc;
           auto covered_any = [&](int lo[3], int hi[3]) {
+            bool wrapped = false;
             for (int k = 0; k < 3; ++k) {
               const int Nk = level_n(cfg, l - 1, k);
               if (lo[k] < 0 || hi[k] > Nk) {
                 if (!periodic(cfg, k) || hi[k] - lo[k] != 1) return false;   // only single-cell strips leave the box
                 lo[k] = ((lo[k] % Nk) + Nk) % Nk;
                 hi[k] = lo[k] + 1;
+                wrapped = true;
               }
             }
-            int qlo[3], qhi[3];
-            for (int k = 0; k < 3; ++k) { qlo[k] = 2 * lo[k]; qhi[k] = 2 * hi[k]; }
-            std::vector<int> cc;
-            fix.query(qlo, qhi, cc);
-            for (int q2 : cc) {
+            const std::vector<int>* cands = &near;
+            if (wrapped) {
+              int qlo[3], qhi[3];
+              for (int k = 0; k < 3; ++k) { qlo[k] = 2 * lo[k]; qhi[k] = 2 * hi[k]; }
+              fix.query(qlo, qhi, cc);
+              cands = &cc;
+            }
+            for (int q2 : *cands) {
               const HPatch& o = P[q2];
               bool hit = true;
               for (int k = 0; k < 3 && hit; ++k)

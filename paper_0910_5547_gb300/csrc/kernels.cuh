@@ -957,55 +957,55 @@ __global__ void __launch_bounds__(kBoxThreads) box_copy_kernel(const FlatCopy* b
   }
 }
 
-// Batched prolongation over flattened boxes (chunks of kProlongChunk cells);
-// same values as prolong_kernel.
+// Batched prolongation over flattened boxes, one parent cell per thread: the
+// three limited slopes of a parent are formed once and its (up to) eight
+// children in the box are written from them, each child by the same
+// operations in the same order as prolong_kernel (same values).
 template <typename T, int NV>
 __global__ void __launch_bounds__(kBoxThreads) box_prolong_kernel(const FlatProlong* boxes, const int* first,
                                                                   const int* chunk_box, int nchunk, int total,
                                                                   const T* tile, T* dst) {
   for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
+    const int e = k * kProlongChunk + (int)threadIdx.x;
+    if (e >= total) continue;
     int b = chunk_box[k];
-    T val[kProlongPerThread][NV];
-    int64_t di[kProlongPerThread];
-    int dvs[kProlongPerThread];
+    while (first[b + 1] <= e) ++b;
+    const FlatProlong g = boxes[b];
+    const int q = e - first[b];
+    const int r = q / g.np0, pa = q - r * g.np0;
+    const int pc = r / g.np1, pb = r - pc * g.np1;
+    const T* tc = tile + g.tp0 + pa + (int64_t)pb * g.tsy + (int64_t)pc * g.tsz;
+    // children's fine coordinates in the box: 2 p + i - odd, i in {0, 1}
+    const int a0 = 2 * pa - (g.odd & 1), b0 = 2 * pb - ((g.odd >> 1) & 1), c0 = 2 * pc - ((g.odd >> 2) & 1);
+    const int64_t d0 = g.dst0 + a0 + (int64_t)b0 * g.dsy + (int64_t)c0 * g.dsz;
+    bool in[3][2];
+    in[0][0] = a0 >= 0; in[0][1] = a0 + 1 < g.n[0];
+    in[1][0] = b0 >= 0; in[1][1] = b0 + 1 < g.n[1];
+    in[2][0] = c0 >= 0; in[2][1] = c0 + 1 < g.n[2];
+    const int st[3] = {1, g.tsy, g.tsz};
 #pragma unroll
-    for (int i = 0; i < kProlongPerThread; ++i) {
-      const int e = k * kProlongChunk + i * kBoxThreads + (int)threadIdx.x;
-      di[i] = -1;
-      if (e < total) {
-        while (first[b + 1] <= e) ++b;
-        const FlatProlong g = boxes[b];
-        const int q = e - first[b];
-        const int r = q / g.n0, a = q - r * g.n0;
-        const int c = r / g.n1, y = r - c * g.n1;
-        const int gx = g.g0[0] + a, gy = g.g0[1] + y, gz = g.g0[2] + c;
-        const int64_t ci = g.tile0 + ((gx >> 1) - g.cb[0]) + (int64_t)((gy >> 1) - g.cb[1]) * g.tsy +
-                           (int64_t)((gz >> 1) - g.cb[2]) * g.tsz;
-        const int st[3] = {1, g.tsy, g.tsz};
-        const T sg[3] = {(gx & 1) ? T(0.25) : T(-0.25), (gy & 1) ? T(0.25) : T(-0.25),
-                         (gz & 1) ? T(0.25) : T(-0.25)};
-        di[i] = g.dst0 + a + (int64_t)y * g.dsy + (int64_t)c * g.dsz;
-        dvs[i] = g.dvs;
+    for (int v = 0; v < NV; ++v) {
+      const T* tv = tc + (int64_t)v * g.tvol;
+      const T uc = tv[0];
+      T sl[3];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const T* tv = tile + ci + (int64_t)v * g.tvol;
-          const T uc = tv[0];
-          T u = uc;
+      for (int d = 0; d < 3; ++d) {
+        const T up = tv[st[d]], um = tv[-st[d]];
+        sl[d] = minmod2(up - uc, uc - um);
+      }
+      T* dv = dst + d0 + (int64_t)v * g.dvs;
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const T up = tv[st[d]], um = tv[-st[d]];
-            u = fma(sg[d], minmod2(up - uc, uc - um), u);
+      for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+        for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+          for (int ix = 0; ix < 2; ++ix) {
+            if (!(in[0][ix] && in[1][jy] && in[2][kz])) continue;
+            T u = fma(ix ? T(0.25) : T(-0.25), sl[0], uc);
+            u = fma(jy ? T(0.25) : T(-0.25), sl[1], u);
+            u = fma(kz ? T(0.25) : T(-0.25), sl[2], u);
+            dv[ix + (int64_t)jy * g.dsy + (int64_t)kz * g.dsz] = u;
           }
-          val[i][v] = u;
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kProlongPerThread; ++i) {
-      if (di[i] >= 0) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dst[di[i] + (int64_t)v * dvs[i]] = val[i][v];
-      }
     }
   }
 }
@@ -1046,6 +1046,11 @@ __global__ void restrict_kernel(const RestrictSeg* segs, int nseg, const PatchDe
   }
 }
 
+template <typename T> struct Pair2Of;
+template <> struct Pair2Of<float> { using type = float2; };
+template <> struct Pair2Of<double> { using type = double2; };
+template <typename T> using Pair2 = typename Pair2Of<T>::type;
+
 // Batched restriction over flattened boxes (chunks of kRestrictChunk coarse
 // cells); same pairwise sums as restrict_kernel.
 template <typename T, int NV>
@@ -1078,8 +1083,10 @@ __global__ void __launch_bounds__(kBoxThreads) box_restrict_kernel(const FlatCop
             T ys[2];
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
-              const T* row = Y + (int64_t)dy * g.ssy + (int64_t)dz * g.ssz;
-              ys[dy] = row[0] + row[1];
+              // the fine pair (2a, 2a+1) starts at an even element of an even-pitched,
+              // 32-element-aligned patch block: one aligned two-element load
+              const Pair2<T> row = *reinterpret_cast<const Pair2<T>*>(Y + (int64_t)dy * g.ssy + (int64_t)dz * g.ssz);
+              ys[dy] = row.x + row.y;
             }
             zs[dz] = ys[0] + ys[1];
           }
@@ -1167,7 +1174,11 @@ __global__ void __launch_bounds__(kRegThreads) reg_coarse_kernel(const RegRect* 
   }
 }
 
-// Fine side: R_f += dt_f/2 * (1/4) * sum of the 4 fine sub-face fluxes.
+// Fine side: R_f += dt_f/2 * (1/4) * sum of the 4 fine sub-face fluxes.  Four
+// neighbouring lanes take the four sub-faces (a, b) of one register, lane
+// a + 2 b of the group, and add them with two butterfly shuffles:
+// (F_00 + F_01) + (F_10 + F_11) (additions commute exactly, so every lane of
+// the group holds the same sum).
 template <typename T, int NV>
 __global__ void __launch_bounds__(kRegThreads) reg_fine_kernel(const RegRect* rects, const int* first,
                                                                const int* chunk_box, int nrect, int nreg,
@@ -1176,7 +1187,15 @@ __global__ void __launch_bounds__(kRegThreads) reg_fine_kernel(const RegRect* re
                                                                double dt_scale, Phys<T> ph0) {
   const Phys<T> ph = phys_with_ch<T, NV>(ph0, params);
   const double dt = (double)(T)(params->dt0 * dt_scale);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nreg; e += gridDim.x * blockDim.x) {
+  const int lane = (int)threadIdx.x & 31;
+  const int64_t nsub = 4 * (int64_t)nreg;
+  // warp-uniform trip count: the shuffles see all 32 lanes
+  for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; t0 < nsub;
+       t0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = t0 + lane;
+    const bool act = t < nsub;
+    const int e = act ? (int)(t >> 2) : nreg - 1;
+    const int sub = (int)(t & 3);
     const int b0 = reg_rect_of(first, chunk_box, nrect, nreg, e);
     const RegRect r = rects[b0];
     const int q = e - first[b0];
@@ -1184,26 +1203,17 @@ __global__ void __launch_bounds__(kRegThreads) reg_fine_kernel(const RegRect* re
     const PatchDesc Pf = desc[r.fpatch];
     int ea, eb;
     reg_entry(r, q, ea, eb);
-    int f0[3] = {r.flo[0], r.flo[1], r.flo[2]};
-    f0[t1] += 2 * ea;
-    f0[t2] += 2 * eb;
-    double qf[2][2][NV];
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        int f[3] = {f0[0], f0[1], f0[2]};
-        f[t1] += a;
-        f[t2] += b;
-        T F[NV];
-        face_flux_dir<T, NV>(Uin + Pf.off, Pf, f[0], f[1], f[2], d, ph, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) qf[b][a][v] = (double)F[v];
-      }
+    int f[3] = {r.flo[0], r.flo[1], r.flo[2]};
+    f[t1] += 2 * ea + (sub & 1);
+    f[t2] += 2 * eb + (sub >> 1);
+    T F[NV];
+    face_flux_dir<T, NV>(Uin + Pf.off, Pf, f[0], f[1], f[2], d, ph, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double sum = (qf[0][0][v] + qf[0][1][v]) + (qf[1][0][v] + qf[1][1][v]);
-      R[(size_t)(NV + v) * nreg + e] += 0.5 * dt * (0.25 * sum);
+      double x = (double)F[v];
+      x = x + __shfl_xor_sync(0xffffffffu, x, 1);
+      x = x + __shfl_xor_sync(0xffffffffu, x, 2);
+      if (act && sub == 0) R[(size_t)(NV + v) * nreg + e] += 0.5 * dt * (0.25 * x);
     }
   }
 }

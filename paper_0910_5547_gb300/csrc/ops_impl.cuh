@@ -202,7 +202,8 @@ struct Ops final : OpsBase {
                        int nreg,
                        const PatchDesc* desc, const void* Uin, double* R, StepParams* prm, int level) override {
     if (nreg <= 0) return cudaSuccess;
-    reg_fine_kernel<T, NV><<<grid_for((nreg + kRegThreads - 1) / kRegThreads), kRegThreads, 0, s>>>(
+    // four lanes per register (one per fine sub-face)
+    reg_fine_kernel<T, NV><<<grid_for((4 * nreg + kRegThreads - 1) / kRegThreads), kRegThreads, 0, s>>>(
         rects, first, chunk_box, nrect, nreg, desc, static_cast<const T*>(Uin), R, prm, 1.0 / (double)(1 << level),
         ph);
     return cudaGetLastError();

@@ -41,7 +41,7 @@ EXPORTS = ["amr_default_config", "amr_create", "amr_validate_patches", "amr_set_
            "amr_get_patches", "amr_autotune", "amr_set_tiling", "amr_get_regrid_timing", "amr_floor_count",
            "amr_set_regrid_schedule", "amr_cell_updates", "amr_divb_norms", "amr_set_state_async",
            "amr_get_state_all_async", "amr_wait_state", "amr_partition_patches", "amr_get_regrid_counts",
-           "amr_peak_fma_rates", "amr_set_persistent"]
+           "amr_peak_fma_rates", "amr_set_persistent", "amr_set_overlap"]
 REGRID_PHASES = ["flag", "cluster", "plan", "fill_tables", "install", "fill"]
 TIMING_CLASSES = ["stage1", "stage2", "ghost", "parent", "registers", "sync", "speed"]
 
@@ -143,6 +143,8 @@ def load():
     L.amr_step_patch_noalloc.restype = ctypes.c_int
     L.amr_set_persistent.argtypes = [H, ctypes.c_int]
     L.amr_set_persistent.restype = ctypes.c_int
+    L.amr_set_overlap.argtypes = [H, ctypes.c_int]
+    L.amr_set_overlap.restype = ctypes.c_int
     L.amr_peak_fma_rates.argtypes = [dp]
     L.amr_peak_fma_rates.restype = ctypes.c_int
     L.amr_regrid.argtypes = [H, ctypes.POINTER(amr_regrid_params), ctypes.POINTER(ctypes.c_int)]
@@ -391,6 +393,11 @@ def amr_step_patch_noalloc(cfg: amr_config, state_in_ptr: int, state_out_ptr: in
 def amr_set_persistent(h, mode: int) -> None:
     """Stage launch form: 0 one CTA per work item, 1 persistent CTAs, -1 the autotuner decides."""
     _check(h, load().amr_set_persistent(h, int(mode)))
+
+
+def amr_set_overlap(h, on: bool) -> None:
+    """Second stream of a multi-level batched step (stage-2 parent fill and registers beside the stages)."""
+    _check(h, load().amr_set_overlap(h, 1 if on else 0))
 
 
 def amr_peak_fma_rates() -> dict:

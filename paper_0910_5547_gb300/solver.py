@@ -121,6 +121,10 @@ class Solver:
         """Stage launch form: 0 one CTA per work item, 1 persistent CTAs, -1 the autotuner decides."""
         N.amr_set_persistent(self.h, mode)
 
+    def set_overlap(self, on: bool) -> None:
+        """Run the stage-2 parent fill and the register kernels on a second stream (default) or not."""
+        N.amr_set_overlap(self.h, on)
+
     def autotune(self) -> str:
         """Time the stage kernel's candidate tilings on this hierarchy and keep the fastest."""
         return N.amr_autotune(self.h)
