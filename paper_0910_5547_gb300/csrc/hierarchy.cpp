@@ -136,7 +136,7 @@ class WorkerPool {
     static WorkerPool pool;
     return pool;
   }
-  bool run(int n, const std::function<void(int)>& f) {
+  bool run(int n, const std::function<void(int)>& f, int grain = 8) {
     if (inside_ || nt_ <= 1 || getpid() != pid_) return false;
     std::unique_lock<std::mutex> busy(busy_, std::try_to_lock);
     if (!busy.owns_lock()) return false;
@@ -144,6 +144,7 @@ class WorkerPool {
       std::lock_guard<std::mutex> lk(m_);
       job_ = &f;
       n_ = n;
+      grain_ = grain;
       next_.store(0);
       pending_ = (int)threads_.size();
       ++gen_;
@@ -173,9 +174,9 @@ class WorkerPool {
   void work() {
     inside_ = true;
     for (;;) {
-      const int i0 = next_.fetch_add(8);
+      const int i0 = next_.fetch_add(grain_);
       if (i0 >= n_) break;
-      const int i1 = std::min(i0 + 8, n_);
+      const int i1 = std::min(i0 + grain_, n_);
       for (int i = i0; i < i1; ++i) (*job_)(i);
     }
     inside_ = false;
@@ -201,6 +202,7 @@ class WorkerPool {
   std::condition_variable cv_, done_;
   const std::function<void(int)>* job_ = nullptr;
   int n_ = 0;
+  int grain_ = 8;
   std::atomic<int> next_{0};
   int pending_ = 0;
   uint64_t gen_ = 0;
@@ -215,6 +217,16 @@ void parallel_for(int n, F&& f) {
   if (n >= 64) {
     const std::function<void(int)> job = [&](int i) { f(i); };
     if (WorkerPool::instance().run(n, job)) return;
+  }
+  for (int i = 0; i < n; ++i) f(i);
+}
+
+// A few large independent tasks, handed out one at a time.
+template <class F>
+void parallel_tasks(int n, F&& f) {
+  if (n >= 2) {
+    const std::function<void(int)> job = [&](int i) { f(i); };
+    if (WorkerPool::instance().run(n, job, 1)) return;
   }
   for (int i = 0; i < n; ++i) f(i);
 }
@@ -1032,7 +1044,7 @@ void classify_faces(Plan& plan, int i, const std::vector<CopySeg>& segs, std::ar
 
 void build_flat(Plan& plan) {
   // four independent lists per level, flattened in parallel
-  parallel_for(4 * (int)plan.levels.size(), [&](int t) {
+  parallel_tasks(4 * (int)plan.levels.size(), [&](int t) {
     LevelPlan& L = plan.levels[t / 4];
     switch (t % 4) {
       case 0: flatten_copies(plan, L.ghost_stage, false, L.fghost); break;
@@ -1351,6 +1363,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             qlo[t2] = 2 * b0; qhi[t2] = 2 * (b0 + B);
             fix.query(qlo, qhi, cand);
           }
+          int64_t covered = 0;   // same-level patches do not overlap: their areas add up
           for (int q : cand) {
             const HPatch& o = P[q];
             if (2 * Cd < o.lo[d] || 2 * Cd >= o.lo[d] + o.n[d]) continue;
@@ -1358,7 +1371,9 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             int y0 = std::max(b0, o.lo[t2] / 2), y1 = std::min(b0 + B, (o.lo[t2] + o.n[t2]) / 2);
             for (int y = y0; y < y1; ++y)
               for (int x = x0; x < x1; ++x) cov2[(size_t)(y - b0) * A + (x - a0)] = 1;
+            if (x1 > x0 && y1 > y0) covered += (int64_t)(x1 - x0) * (y1 - y0);
           }
+          if (covered == (int64_t)A * B) return;   // the face borders level l all over: no register
           std::vector<int> owner((size_t)A * B, -1);
           {
             int qlo[3], qhi[3];
