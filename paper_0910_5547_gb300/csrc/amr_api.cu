@@ -534,7 +534,7 @@ cudaError_t join_side(amr_handle* h) {
   return e;
 }
 
-cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
+cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out, void* uold = nullptr) {
   const DevLevel& L = h->dl[l];
   const LevelPlan& LP = h->plan.levels[l];
   double dx[3] = {level_dx(h, l, 0), level_dx(h, l, 1), level_dx(h, l, 2)};
@@ -544,13 +544,13 @@ cudaError_t stage(amr_handle* h, int l, int s, const void* in, void* out) {
     // persistent: one wave of resident CTAs takes the level's items from a device counter
     const int grid = h->tp.persistent ? h->sms * h->ops->resident_ctas() : 0;
     LK(h->ops->stage(s, h->stream, h->d_desc, L.bitems, L.nbitems, L.has_span ? h->d_spans : nullptr, in, out,
-                     h->params, l, dx, h->dx0, fuse, grid));
+                     h->params, l, dx, h->dx0, fuse, grid, uold));
   } else {
     for (int p = 0; p < LP.count; ++p) {
       int a = LP.item_first[p], b = LP.item_first[p + 1];
       if (b > a)
         LK(h->ops->stage(s, h->stream, h->d_desc, L.items + a, b - a, nullptr, in, out, h->params, l, dx, h->dx0,
-                         fuse, 0));
+                         fuse, 0, uold));
     }
   }
   return cudaSuccess;
@@ -606,7 +606,11 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
   const bool ov = overlap_on(h);
   DevLevel& L = h->dl[l];
   const size_t es = h->ops->elem_size();
-  if (kids) {
+  // the level's state at the start of its step (U^n), which its children
+  // interpolate in time: stored by stage 1 beside its own output (every interior
+  // cell is updated exactly once), or copied
+  void* uold = (kids && h->ops->stage_stores_old()) ? h->Uold : nullptr;
+  if (kids && !uold) {
     cudaError_t e = cudaMemcpyAsync((char*)h->Uold + L.arena_begin * es, (char*)h->U + L.arena_begin * es,
                                     (L.arena_end - L.arena_begin) * es, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return e;
@@ -622,7 +626,7 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
     if ((e = registers(h, l, 1, h->U, h->side)) != cudaSuccess) return e;
     h->side_dirty = true;
     if ((e = u1_wait(h, l)) != cudaSuccess) return e;
-    if ((e = stage(h, l, 1, h->U, h->U1)) != cudaSuccess) return e;
+    if ((e = stage(h, l, 1, h->U, h->U1, uold)) != cudaSuccess) return e;
     if ((e = join_side(h)) != cudaSuccess) return e;
     if ((e = fill_same(h, l, h->U1, false)) != cudaSuccess) return e;
     if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;
@@ -631,7 +635,7 @@ cudaError_t advance(amr_handle* h, int l, double alpha0) {
     if ((e = u1_mark(h, l)) != cudaSuccess) return e;
     h->side_dirty = true;
   } else {
-    if ((e = stage(h, l, 1, h->U, h->U1)) != cudaSuccess) return e;
+    if ((e = stage(h, l, 1, h->U, h->U1, uold)) != cudaSuccess) return e;
     if ((e = registers(h, l, 1, h->U, h->stream)) != cudaSuccess) return e;
     if ((e = fill_ghosts(h, l, h->U1, alpha0 + 0.5)) != cudaSuccess) return e;
     if ((e = stage(h, l, 2, h->U1, h->U)) != cudaSuccess) return e;

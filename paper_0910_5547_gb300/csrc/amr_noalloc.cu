@@ -165,6 +165,7 @@ amr_status run(const amr_config& cfg, const Plan& pl, unsigned char* base, const
   a.fuse_rate = 0;
   a.dynamic = 0;
   a.spans = nullptr;   // one patch: per-patch blocks only
+  a.Uold = nullptr;    // one level: no old-time state
   a.ph = ph;
   const int nseg = (int)L.ghost.size();
   const int gseg = nseg < 65535 ? nseg : 65535;

@@ -182,6 +182,7 @@ struct StageArgs {
   int fuse_rate;     // stage 2: accumulate the CFL rate of the new state
   int dynamic;       // persistent CTAs take items from params->work_next (stage_kernel)
   const ItemSpan* spans;   // the spanning blocks' patch lists (items with span >= 0)
+  T* Uold;           // stage 1: also store the stage input (U^n) of every updated cell here, or nullptr
   Phys<T> ph;
 };
 
@@ -626,6 +627,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           const T u2 = uin[v] - dtx * (fxp[v] - Fx0[v]) - dty * (fyp[v] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
           if (STAGE == 1) {
             if (prev) Ob[v * vs + c] = u2;
+            if (a.Uold != nullptr && prev) a.Uold[P.off + v * vs + c] = uin[v];   // U^n for the finer levels' time interpolation
           } else {
             un[v] = T(0.5) * un[v] + T(0.5) * u2;
             if (NV == 9 && v == 8) un[v] *= damp;

@@ -26,7 +26,10 @@ struct OpsBase {
   // fused RK2 stage over items [0, nitems) of `items` (device pointer)
   virtual cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
                             const ItemSpan* spans, const void* Uin, void* Uout, StepParams* prm, int level,
-                            const double dx[3], const double dx0[3], int fuse_rate, int grid) = 0;
+                            const double dx[3], const double dx0[3], int fuse_rate, int grid,
+                            void* uold = nullptr) = 0;
+  // whether stage 1 stores its input into uold (every build but the flux-reconstruction kernel)
+  virtual bool stage_stores_old() const = 0;
   // resident CTAs per SM the stage kernel is compiled for (register budget);
   // each variant except FP64 MHD has a second build, selected here
   virtual int stage_occupancy() const = 0;

@@ -78,10 +78,12 @@ struct Ops final : OpsBase {
   }
 
   size_t elem_size() const override { return sizeof(T); }
+  bool stage_stores_old() const override { return !(NV == 5 && ph.fluxrec); }
 
   cudaError_t stage(int stage, cudaStream_t s, const PatchDesc* desc, const StageItem* items, int nitems,
                     const ItemSpan* spans, const void* Uin, void* Uout, StepParams* prm, int level,
-                    const double dx[3], const double dx0[3], int fuse_rate, int grid) override {
+                    const double dx[3], const double dx0[3], int fuse_rate, int grid,
+                    void* uold = nullptr) override {
     if (nitems <= 0) return cudaSuccess;
     StageArgs<T> a;
     a.desc = desc;
@@ -99,6 +101,7 @@ struct Ops final : OpsBase {
     a.idy0 = 1.0 / dx0[1];
     a.idz0 = 1.0 / dx0[2];
     a.fuse_rate = fuse_rate;
+    a.Uold = stage == 1 ? static_cast<T*>(uold) : nullptr;
     a.ph = ph;
     // grid > 0: that many persistent CTAs, items handed out by a device counter
     a.dynamic = grid > 0 ? 1 : 0;
