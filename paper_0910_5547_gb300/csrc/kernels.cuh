@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     const int lx = ox + tx - P.lo[0], ly = oy + ty - P.lo[1], lz0 = oz - P.lo[2];
     const T* Ub = a.Uin + P.off;
     T* Ob = a.Uout + P.off;
+    T* Oo = a.Uold == nullptr ? nullptr : a.Uold + P.off;   // stage 1's copy of U^n, if asked
     const int vs = (int)P.vstride;
     const int plane = P.pitch * P.m1;
     const int col = ((lz0 + kGhost) * P.m1 + (ly + kGhost)) * P.pitch + (lx + kGhost);
@@ -490,6 +491,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     T xrOwn[NV], yrOwn[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) xrOwn[v] = yrOwn[v] = T(0);
+    // FP32 Euler blocks of one patch unroll the march by two planes (the other
+    // builds would spill at their register budgets)
+    constexpr int kMarchUnroll = (NV == 5 && sizeof(T) == 4 && !SPAN) ? 2 : 1;
+#pragma unroll kMarchUnroll
     for (int j = 0; j <= wz; ++j) {
       const bool cur = j < wz, prev = j > 0;
       T Fzp[NV], Fx0[NV], Fy0[NV], own[NV], un[NV], uin[NV];
@@ -627,7 +632,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
           const T u2 = uin[v] - dtx * (fxp[v] - Fx0[v]) - dty * (fyp[v] - Fy0[v]) - dtz * (Fzp[v] - Fzm[v]);
           if (STAGE == 1) {
             if (prev) Ob[v * vs + c] = u2;
-            if (a.Uold != nullptr && prev) a.Uold[P.off + v * vs + c] = uin[v];   // U^n for the finer levels' time interpolation
+            if (Oo != nullptr && prev) Oo[v * vs + c] = uin[v];   // U^n for the finer levels' time interpolation
           } else {
             un[v] = T(0.5) * un[v] + T(0.5) * u2;
             if (NV == 9 && v == 8) un[v] *= damp;
