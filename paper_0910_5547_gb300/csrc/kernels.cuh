@@ -491,9 +491,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(StageArgs<T> a) {
     T xrOwn[NV], yrOwn[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) xrOwn[v] = yrOwn[v] = T(0);
-    // FP32 Euler blocks of one patch unroll the march by two planes (the other
-    // builds would spill at their register budgets)
-    constexpr int kMarchUnroll = (NV == 5 && sizeof(T) == 4 && !SPAN) ? 2 : 1;
+    // FP32 Euler blocks of one patch with 128 registers per thread (512 threads
+    // per SM) unroll the march by two planes (measured: three or four planes are
+    // slower; the other builds would spill at their register budgets)
+    constexpr int kMarchUnroll = (NV == 5 && sizeof(T) == 4 && !SPAN && MINB * NT <= 512) ? 2 : 1;
 #pragma unroll kMarchUnroll
     for (int j = 0; j <= wz; ++j) {
       const bool cur = j < wz, prev = j > 0;
