@@ -2094,7 +2094,11 @@ void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch
     std::vector<int> cand;
     std::vector<CopySeg>& Cv = cs[ii];
     std::vector<ProlongBox>& Fv = fs[ii];
-    std::vector<unsigned char> mask((size_t)p.n[0] * p.n[1] * p.n[2], 0);
+    // the new patch's cells outside every old patch of its level, as boxes: the
+    // patch box minus each overlapping old box in turn (a box minus a box is at
+    // most six boxes: below and above in z, then in y, then in x)
+    struct B3 { int lo[3], hi[3]; };
+    std::vector<B3> rest{{{p.lo[0], p.lo[1], p.lo[2]}, {p.lo[0] + p.n[0], p.lo[1] + p.n[1], p.lo[2] + p.n[2]}}}, next;
     if (l < (int)oix.size()) {
       int qlo[3], qhi[3];
       for (int d = 0; d < 3; ++d) { qlo[d] = p.lo[d]; qhi[d] = p.lo[d] + p.n[d]; }
@@ -2121,21 +2125,35 @@ void build_regrid_fill(const std::vector<HPatch>& oldp, const std::vector<HPatch
         sg.mode[d] = 0;
       }
       Cv.push_back(sg);
-      for (int z = lo[2]; z < hi[2]; ++z)
-        for (int y = lo[1]; y < hi[1]; ++y)
-          for (int x = lo[0]; x < hi[0]; ++x)
-            mask[((size_t)(z - p.lo[2]) * p.n[1] + (y - p.lo[1])) * p.n[0] + (x - p.lo[0])] = 1;
+      next.clear();
+      for (const B3& a : rest) {
+        int c0[3], c1[3];
+        bool meet = true;
+        for (int d = 0; d < 3; ++d) {
+          c0[d] = std::max(a.lo[d], lo[d]);
+          c1[d] = std::min(a.hi[d], hi[d]);
+          if (c0[d] >= c1[d]) meet = false;
+        }
+        if (!meet) { next.push_back(a); continue; }
+        B3 core = a;   // shrinks to the overlap axis by axis, z first
+        for (int d = 2; d >= 0; --d) {
+          if (core.lo[d] < c0[d]) { B3 b = core; b.hi[d] = c0[d]; next.push_back(b); }
+          if (c1[d] < core.hi[d]) { B3 b = core; b.lo[d] = c1[d]; next.push_back(b); }
+          core.lo[d] = c0[d];
+          core.hi[d] = c1[d];
+        }
+      }
+      rest.swap(next);
     }
     split_copy(Cv, 0);
-    for (int z = 0; z < p.n[2]; ++z) {
-      for (const Rect& r : mask_rects(mask.data() + (size_t)z * p.n[0] * p.n[1], p.n[0], p.n[1])) {
-        ProlongBox b{};
-        b.patch = (int)i;
-        b.lo[0] = (int16_t)r.a0; b.n[0] = (int16_t)r.na;
-        b.lo[1] = (int16_t)r.b0; b.n[1] = (int16_t)r.nb;
-        b.lo[2] = (int16_t)z; b.n[2] = 1;
-        Fv.push_back(b);
+    for (const B3& a : rest) {
+      ProlongBox b{};
+      b.patch = (int)i;
+      for (int d = 0; d < 3; ++d) {
+        b.lo[d] = (int16_t)(a.lo[d] - p.lo[d]);
+        b.n[d] = (int16_t)(a.hi[d] - a.lo[d]);
       }
+      Fv.push_back(b);
     }
     split_prolong(Fv, 0);
   });
