@@ -1241,35 +1241,6 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
           Gv.insert(Gv.end(), merged.begin(), merged.end());
           split_copy(Gv, g0);
         }
-        // the two ghost layers of a face prolonged over the same rectangle become one
-        // two-deep box: both layers have the same parent cells, whose limited slopes
-        // the prolongation then forms once for both
-        {
-          std::vector<char> used(Pv.size(), 0);
-          std::vector<ProlongBox> merged;
-          for (size_t a = 0; a < Pv.size(); ++a) {
-            if (used[a]) continue;
-            ProlongBox m = Pv[a];
-            for (size_t b = a + 1; b < Pv.size(); ++b) {
-              if (used[b]) continue;
-              const ProlongBox& o = Pv[b];
-              int d = -1;
-              for (int k = 0; k < 3; ++k)
-                if (m.n[k] == 1 && o.n[k] == 1 && (o.lo[k] == m.lo[k] - 1 || o.lo[k] == m.lo[k] + 1)) d = k;
-              if (d < 0) continue;
-              bool same = true;
-              for (int k = 0; k < 3 && same; ++k)
-                if (k != d) same = o.lo[k] == m.lo[k] && o.n[k] == m.n[k];
-              if (!same) continue;
-              m.lo[d] = std::min(m.lo[d], o.lo[d]);
-              m.n[d] = 2;
-              used[b] = 1;
-              break;
-            }
-            merged.push_back(m);
-          }
-          Pv.swap(merged);
-        }
         split_prolong(Pv, 0);
         if (direct_ok) classify_faces(plan, i, Gv, direct[i]);
     });
