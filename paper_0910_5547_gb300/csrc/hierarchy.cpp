@@ -69,10 +69,11 @@ std::vector<std::pair<int, int>> wrap_interval(const amr_config& c, int l, int d
 // Decompose the cells with mask == 0 of an A x B grid into rectangles
 // (row runs merged across consecutive rows with identical extent).
 struct Rect { int a0, na, b0, nb; };
-std::vector<Rect> mask_rects(const unsigned char* m, int A, int B) {
-  std::vector<Rect> done;
+void mask_rects(const unsigned char* m, int A, int B, std::vector<Rect>& done) {
+  done.clear();
   // runs of the previous row that are still open: (a0, na, index into done)
-  std::vector<std::array<int, 3>> open, next;
+  thread_local std::vector<std::array<int, 3>> open, next;
+  open.clear();
   for (int b = 0; b < B; ++b) {
     next.clear();
     size_t oi = 0;   // open runs are in increasing a0 order, like the runs of this row
@@ -92,6 +93,10 @@ std::vector<Rect> mask_rects(const unsigned char* m, int A, int B) {
     }
     open.swap(next);
   }
+}
+std::vector<Rect> mask_rects(const unsigned char* m, int A, int B) {
+  std::vector<Rect> done;
+  mask_rects(m, A, B, done);
   return done;
 }
 std::vector<Rect> mask_rects(const std::vector<unsigned char>& m, int A, int B) { return mask_rects(m.data(), A, B); }
@@ -104,10 +109,12 @@ std::vector<Box3> need_boxes(const std::vector<unsigned char>& need, int n0, int
   std::vector<Box3> done;
   std::vector<std::pair<Rect, int>> open, next;
   std::vector<unsigned char> inv((size_t)n0 * n1);
+  std::vector<Rect> rects;
   for (int z = 0; z < n2; ++z) {
     for (size_t e = 0; e < inv.size(); ++e) inv[e] = need[(size_t)z * n0 * n1 + e] ? 0 : 1;
     next.clear();
-    for (const Rect& r : mask_rects(inv, n0, n1)) {
+    mask_rects(inv.data(), n0, n1, rects);
+    for (const Rect& r : rects) {
       int hit = -1;
       for (const auto& o : open)
         if (o.first.a0 == r.a0 && o.first.na == r.na && o.first.b0 == r.b0 && o.first.nb == r.nb) hit = o.second;
