@@ -90,7 +90,7 @@ struct DevLevel {
     const int* first = nullptr;
     const int* chunk_box = nullptr;
     int nchunk = 0, total = 0;
-  } fghost, fgather, fprolong, frestrict;
+  } fghost, fghost_all, fgather, fprolong, frestrict;
   int64_t arena_begin = 0, arena_end = 0;  // element range of the level's patches
 };
 
@@ -471,7 +471,11 @@ cudaError_t fill_same(amr_handle* h, int l, void* arr, bool all) {
   const DevLevel& L = h->dl[l];
   const LevelPlan& LP = h->plan.levels[l];
   h->cur_class = AMR_T_GHOST;
-  if (all) {
+  if (all && h->cfg.batched) {   // every face, over flattened boxes
+    const DevLevel::Flat& G = L.fghost_all;
+    LK(h->ops->ghost_copy_flat(h->stream, static_cast<const FlatCopy*>(G.boxes), G.first, G.chunk_box, G.nchunk,
+                               G.total, arr));
+  } else if (all) {
     LK(h->ops->ghost_copy(h->stream, L.ghost, L.nghost, h->d_desc, arr));
   } else if (h->cfg.batched) {
     const DevLevel::Flat& G = L.fghost;
@@ -916,12 +920,13 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
   for (int l = 0; l < nlev; ++l) lvol[l] = level_dx(h, l, 0) * level_dx(h, l, 1) * level_dx(h, l, 2);
   size_t o_lvol = buf.add(lvol);
   struct FlatOffs { size_t boxes, first, chunk; };
-  struct Offs { size_t items, ghost, ghost_stage, prolong, gather_ghost, restr; FlatOffs fg, fa, fp, fr, rg; };
+  struct Offs { size_t items, ghost, ghost_stage, prolong, gather_ghost, restr; FlatOffs fg, fga, fa, fp, fr, rg; };
   std::vector<Offs> lo(nlev);
   auto put_flat = [&](const auto& f) { return FlatOffs{buf.add(f.boxes), buf.add(f.first), buf.add(f.chunk_box)}; };
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = pl.levels[l];
     lo[l].fg = put_flat(L.fghost);
+    lo[l].fga = put_flat(L.fghost_all);
     lo[l].fa = put_flat(L.fgather);
     lo[l].fp = put_flat(L.fprolong);
     lo[l].fr = put_flat(L.frestrict);
@@ -993,6 +998,7 @@ amr_status install_plan(amr_handle* h, Plan&& plan) {
       F.total = f.total;
     };
     set_flat(D.fghost, L.fghost, lo[l].fg);
+    set_flat(D.fghost_all, L.fghost_all, lo[l].fga);
     set_flat(D.fgather, L.fgather, lo[l].fa);
     set_flat(D.fprolong, L.fprolong, lo[l].fp);
     set_flat(D.frestrict, L.frestrict, lo[l].fr);

@@ -1050,13 +1050,14 @@ void classify_faces(Plan& plan, int i, const std::vector<CopySeg>& segs, std::ar
 }
 
 void build_flat(Plan& plan) {
-  // four independent lists per level, flattened in parallel
-  parallel_tasks(4 * (int)plan.levels.size(), [&](int t) {
-    LevelPlan& L = plan.levels[t / 4];
-    switch (t % 4) {
+  // five independent lists per level, flattened in parallel
+  parallel_tasks(5 * (int)plan.levels.size(), [&](int t) {
+    LevelPlan& L = plan.levels[t / 5];
+    switch (t % 5) {
       case 0: flatten_copies(plan, L.ghost_stage, false, L.fghost); break;
       case 1: flatten_copies(plan, L.gather_ghost, true, L.fgather); break;
       case 2: flatten_prolong(plan, L.prolong, L.fprolong); break;
+      case 3: flatten_copies(plan, L.ghost, false, L.fghost_all); break;
       default: flatten_restrict(plan, L.restrict_segs, L.frestrict); break;
     }
   });

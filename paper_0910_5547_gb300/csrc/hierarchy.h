@@ -68,6 +68,7 @@ struct LevelPlan {
   int reg_pass[7] = {0, 0, 0, 0, 0, 0, 0};   // registers of the fine faces (d, side) = p / 2, p % 2: [pass[p], pass[p+1])
   int reg_ordered[6] = {0, 0, 0, 0, 0, 0};   // pass p holds rectangles whose cells have several registers
   FlatList<FlatCopy> fghost, fgather;        // the ghost and gather boxes, flattened (batched launches)
+  FlatList<FlatCopy> fghost_all;             // every face's ghost segments, flattened (refills of all faces)
   FlatList<FlatProlong> fprolong;            // the prolongation boxes, flattened
   FlatList<FlatCopy> frestrict;              // the restriction boxes (this level -> parent), flattened
   int64_t cells = 0;
