@@ -323,8 +323,12 @@ class PatchIndex {
 constexpr int kMaxBoxCells = 4096;
 
 void split_copy(std::vector<CopySeg>& v, size_t from) {
+  bool any = false;   // nothing to split (the common case): keep v as it is
+  for (size_t i = from; i < v.size() && !any; ++i) any = v[i].dn[0] * v[i].dn[1] * v[i].dn[2] > kMaxBoxCells;
+  if (!any) return;
   std::vector<CopySeg> out(v.begin(), v.begin() + from);
   for (size_t i = from; i < v.size(); ++i) {
+    if (v[i].dn[0] * v[i].dn[1] * v[i].dn[2] <= kMaxBoxCells) { out.push_back(v[i]); continue; }
     std::vector<CopySeg> work{v[i]};
     while (!work.empty()) {
       CopySeg s = work.back();
@@ -345,8 +349,12 @@ void split_copy(std::vector<CopySeg>& v, size_t from) {
 }
 
 void split_prolong(std::vector<ProlongBox>& v, size_t from) {
+  bool any = false;   // nothing to split (the common case): keep v as it is
+  for (size_t i = from; i < v.size() && !any; ++i) any = v[i].n[0] * v[i].n[1] * v[i].n[2] > kMaxBoxCells;
+  if (!any) return;
   std::vector<ProlongBox> out(v.begin(), v.begin() + from);
   for (size_t i = from; i < v.size(); ++i) {
+    if (v[i].n[0] * v[i].n[1] * v[i].n[2] <= kMaxBoxCells) { out.push_back(v[i]); continue; }
     std::vector<ProlongBox> work{v[i]};
     while (!work.empty()) {
       ProlongBox s = work.back();
@@ -367,7 +375,9 @@ void split_prolong(std::vector<ProlongBox>& v, size_t from) {
 
 void split_restrict(std::vector<RestrictSeg>& v) {
   std::vector<RestrictSeg> out;
+  out.reserve(v.size());
   for (size_t i = 0; i < v.size(); ++i) {
+    if (v[i].cn[0] * v[i].cn[1] * v[i].cn[2] <= kMaxBoxCells / 2) { out.push_back(v[i]); continue; }
     std::vector<RestrictSeg> work{v[i]};
     while (!work.empty()) {
       RestrictSeg s = work.back();
@@ -1198,7 +1208,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                   for (int b = c.dlo[t2]; b < c.dlo[t2] + c.dn[t2]; ++b)
                     for (int a = c.dlo[t1]; a < c.dlo[t1] + c.dn[t1]; ++a) mask[(size_t)b * A + a] = 1;
                 }
-                rects = mask_rects(mask, A, B);
+                mask_rects(mask.data(), A, B, rects);
               }
               if (!rects.empty() && l == 0) {
                 err[ii] = fmt("level-0 patch %d has uncovered ghost cells", i);
@@ -1450,10 +1460,12 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
             return false;
           };
           std::vector<unsigned char> other((size_t)A * B);
+          std::vector<Rect> orects;
           for (int q : qs) {
             for (size_t e = 0; e < other.size(); ++e) other[e] = (cov2[e] || owner[e] != q) ? 1 : 0;
             const HPatch& o = P[q];
-            for (const Rect& rc : mask_rects(other, A, B)) {
+            mask_rects(other.data(), A, B, orects);
+            for (const Rect& rc : orects) {
               RegRect r{};
               r.fpatch = i; r.cpatch = q;
               r.d = (int8_t)d; r.side = (int8_t)side; r.cside = (int8_t)(side ? -1 : 1);
