@@ -872,7 +872,14 @@ void prolong_gathers(const amr_config& cfg, const Plan& plan, const PatchIndex& 
   std::vector<int> cand;
   // gathers of the tile cells [blo, bhi) per axis; returns the cells covered
   auto gather_box = [&](const int* blo, const int* bhi) -> int64_t {
-    std::vector<Piece> pieces[3];
+    // at most three pieces per axis (below the domain, inside, above: the kind only grows along an axis)
+    struct Pieces {
+      Piece v[3];
+      int n = 0;
+      void push_back(const Piece& x) { v[n++] = x; }
+      const Piece* begin() const { return v; }
+      const Piece* end() const { return v + n; }
+    } pieces[3];
     for (int d = 0; d < 3; ++d) {
       const int Nc = level_n(cfg, l - 1, d);
       const int T0 = p.lo[d] / 2 - 2;
@@ -895,9 +902,9 @@ void prolong_gathers(const amr_config& cfg, const Plan& plan, const PatchIndex& 
       }
     }
     int64_t covered = 0;
-    for (auto& p0 : pieces[0])
-      for (auto& p1 : pieces[1])
-        for (auto& p2 : pieces[2]) {
+    for (const Piece& p0 : pieces[0])
+      for (const Piece& p1 : pieces[1])
+        for (const Piece& p2 : pieces[2]) {
           const Piece* pp[3] = {&p0, &p1, &p2};
           int qlo[3], qhi[3];
           for (int d = 0; d < 3; ++d) {
