@@ -499,14 +499,16 @@ cudaError_t fill_ghosts(amr_handle* h, int l, void* arr, double alpha, bool all 
 
 // ---- the side stream of a step ----
 // Order (main | side), level l, one step:
-//   main: [Uold copy] stage-1 ghosts of U | fork | stage 1 (U -> U1) | join | same-level ghosts of U1 |
-//         stage 2 (U1 -> U) | fork | children | join | restriction, reflux
+//   main: stage-1 ghosts of U | fork | stage 1 (U -> U1, and U^n -> Uold for a level with
+//         children) | join | same-level ghosts of U1 | stage 2 (U1 -> U) | fork | children | join |
+//         restriction, reflux
 //   side: after the first fork: stage-2 parent gather (second tile) and prolongation into U1,
 //         stage-1 registers (read U); after the second fork: stage-2 registers (read U1)
 // Stage 1 of a level waits for the side stream's last read of that level's U1
 // (u1_ev); the joins cover every other hazard (ghost cells of U1 before stage 2;
 // U of the level, which the registers and the children's gathers read, before
-// stage 2 and the restriction write it; the registers before the reflux).
+// stage 2 and the restriction write it; its Uold, which the children's gathers
+// read, before the next stage 1 writes it; the registers before the reflux).
 bool overlap_on(const amr_handle* h) {
   return h->overlap && h->side && h->cfg.batched && !h->timing && h->dl.size() > 1;
 }
