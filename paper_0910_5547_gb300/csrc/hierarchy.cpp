@@ -303,6 +303,8 @@ class PatchIndex {
             if (hit) out.push_back(i);
           }
         }
+    // one bucket: its patches are listed once each, in ascending order already
+    if (b0[0] == b1[0] && b0[1] == b1[1] && b0[2] == b1[2]) return;
     std::sort(out.begin(), out.end());
     out.erase(std::unique(out.begin(), out.end()), out.end());
   }
