@@ -1,0 +1,66 @@
+"""Host planner checks that need no GPU: the regrid fill of a new hierarchy
+fills every cell of every rebuilt patch exactly once, from the old patches of
+its level (copy segments that keep each cell in place) or by prolongation
+(fresh boxes).  The planner source is compiled with a small C++ driver
+(`planner_check.cpp`) for the check."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import amr_inputs as ai
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "..", "paper_0910_5547_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not found")
+    out = str(tmp_path_factory.mktemp("planner") / "planner_check")
+    cmd = ["g++", "-O1", "-std=c++17", "-pthread", "-I", CSRC, os.path.join(HERE, "planner_check.cpp"),
+           os.path.join(CSRC, "hierarchy.cpp"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return out
+
+
+def listing(patches):
+    lines = [str(len(patches))]
+    lines += [" ".join(map(str, (p.level, *p.lo, *p.n))) for p in patches]
+    return "\n".join(lines)
+
+
+def run(checker, base, max_level, old, new):
+    text = f"{base} {base} {base} {max_level}\n{listing(old)}\n{listing(new)}\n"
+    r = subprocess.run([checker], input=text, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    return [int(x) for x in r.stdout.split()[1:]]
+
+
+def test_fill_covers_every_rebuilt_cell_once(checker):
+    # the same nested cubes tiled by two seeded partitions: partial overlaps everywhere
+    old = ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16)
+    new = ai.nested_cubes(32, (32, 32), 12, pmin=8, pmax=16)
+    segs, fresh = run(checker, 32, 2, old, new)
+    assert segs > 0 and fresh == 0   # same covered region: everything is copied
+
+
+def test_fill_prolongs_the_cells_no_old_patch_held(checker):
+    # larger refined cubes than before: the new cells outside the old cubes are prolonged
+    old = ai.nested_cubes(32, (24, 24), 21, pmin=8, pmax=16)
+    new = ai.nested_cubes(32, (40, 48), 22, pmin=8, pmax=24)
+    segs, fresh = run(checker, 32, 2, old, new)
+    assert segs > 0 and fresh > 0
+
+
+def test_fill_with_shifted_and_shrunk_levels(checker):
+    rng = np.random.Generator(np.random.PCG64(5))
+    old = ai.nested_cubes(32, (32, 40), 31, pmin=8, pmax=16)
+    new = [p for p in ai.nested_cubes(32, (16, 24), 32, pmin=8, pmax=16)]
+    # drop a few refined patches of the new hierarchy (holes are allowed for the fill)
+    keep = [p for p in new if p.level == 0 or rng.random() > 0.2]
+    run(checker, 32, 2, old, keep)
