@@ -1,12 +1,20 @@
-// Host-side checks of the hierarchy planner's regrid fill (test infrastructure,
-// compiled by tests/test_planner_host.py with the planner source).
+// Host-side checks of the hierarchy planner (test infrastructure, compiled by
+// tests/test_planner_host.py with the planner source).  Prints "ok ..." or the
+// first violation.
 //
-// Input (stdin): base_n0 base_n1 base_n2 max_level, then two patch lists (old,
-// new), each "count" followed by "level lo0 lo1 lo2 n0 n1 n2" lines.  For every
-// kept level k = 0 .. max_level - 1 the fill of each new patch above level k
-// must cover each of its cells exactly once: copy segments from old patches of
-// the same level (whose source cells lie inside the old patch) plus fresh
-// (prolonged) boxes.  Prints "ok" or the first violation.
+// "fill": base_n0 base_n1 base_n2 max_level, then two patch lists (old, new),
+// each "count" followed by "level lo0 lo1 lo2 n0 n1 n2" lines.  For every kept
+// level k = 0 .. max_level - 1 the fill of each new patch above level k must
+// cover each of its cells exactly once: copy segments from old patches of the
+// same level (whose source cells lie inside the old patch) plus fresh
+// (prolonged) boxes.
+//
+// "ghost": base_n0 base_n1 base_n2 max_level bc0 .. bc5, then one patch list.
+// Each of the two ghost layers of every patch face is covered exactly once by
+// the plan's ghost segments and prolongation boxes, and nothing else is; a
+// segment copies, for every ghost cell, the level cell at that cell's position
+// (wrapped on periodic axes) or, across an outflow face, the boundary cell of
+// the patch itself.
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -25,7 +33,102 @@ static bool read_list(std::vector<HPatch>& v) {
   return true;
 }
 
+static int check_ghost() {
+  int bn[3], ml, bc[6];
+  if (scanf("%d %d %d %d %d %d %d %d %d %d", &bn[0], &bn[1], &bn[2], &ml, &bc[0], &bc[1], &bc[2], &bc[3], &bc[4],
+            &bc[5]) != 10)
+    return 2;
+  std::vector<HPatch> P;
+  if (!read_list(P)) return 2;
+  amr_config cfg{};
+  cfg.nvar = 5;
+  cfg.precision = AMR_FP32;
+  cfg.gamma = 1.4;
+  cfg.theta = 1.5;
+  cfg.cfl = 0.4;
+  cfg.ref_ratio = 2;
+  for (int d = 0; d < 3; ++d) {
+    cfg.base_n[d] = bn[d];
+    cfg.domain_lo[d] = 0;
+    cfg.domain_hi[d] = 1;
+  }
+  for (int f = 0; f < 6; ++f) cfg.bc[f] = bc[f];
+  cfg.max_level = ml;
+  cfg.batched = 1;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, TileParams()) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  long long segs = 0, boxes = 0;
+  for (const LevelPlan& L : plan.levels) {
+    for (int ii = 0; ii < L.count; ++ii) {
+      const int i = L.first + ii;
+      const HPatch& p = P[i];
+      const int g0 = kGhost, m[3] = {p.n[0] + 2 * kGhost, p.n[1] + 2 * kGhost, p.n[2] + 2 * kGhost};
+      std::vector<unsigned char> cnt((size_t)m[0] * m[1] * m[2], 0);
+      auto at = [&](int x, int y, int z) -> unsigned char& {
+        return cnt[((size_t)(z + g0) * m[1] + (y + g0)) * m[0] + (x + g0)];
+      };
+      for (int e = L.ghost_first[ii]; e < L.ghost_first[ii + 1]; ++e) {
+        const CopySeg& s = L.ghost[e];
+        const HPatch& o = P[s.src_patch];
+        if (s.dst_patch != i || o.level != p.level) { printf("ghost segment of a wrong patch or level\n"); return 1; }
+        for (int z = s.dlo[2]; z < s.dlo[2] + s.dn[2]; ++z)
+          for (int y = s.dlo[1]; y < s.dlo[1] + s.dn[1]; ++y)
+            for (int x = s.dlo[0]; x < s.dlo[0] + s.dn[0]; ++x) {
+              const int c[3] = {x, y, z};
+              for (int d = 0; d < 3; ++d) {
+                const int src = s.mode[d] ? s.sh[d] : c[d] + s.sh[d];   // source-local coordinate
+                if (src < 0 || src >= o.n[d]) { printf("ghost source outside its patch\n"); return 1; }
+                const int N = p.level == 0 ? bn[d] : bn[d] << p.level;
+                const int G = p.lo[d] + c[d];
+                if (s.mode[d]) {   // outflow: the patch's own boundary cell
+                  if (s.src_patch != i || (G >= 0 && G < N) || src != (G < 0 ? 0 : p.n[d] - 1)) {
+                    printf("outflow ghost not the boundary cell\n");
+                    return 1;
+                  }
+                } else if (((G % N) + N) % N != o.lo[d] + src) {
+                  printf("ghost copies a cell from another position\n");
+                  return 1;
+                }
+              }
+              ++at(x, y, z);
+            }
+        ++segs;
+      }
+      if (p.level > 0)
+        for (int e = L.prolong_first[ii]; e < L.prolong_first[ii + 1]; ++e) {
+          const ProlongBox& b = L.prolong[e];
+          if (b.patch != i) { printf("prolongation box of a wrong patch\n"); return 1; }
+          for (int z = b.lo[2]; z < b.lo[2] + b.n[2]; ++z)
+            for (int y = b.lo[1]; y < b.lo[1] + b.n[1]; ++y)
+              for (int x = b.lo[0]; x < b.lo[0] + b.n[0]; ++x) ++at(x, y, z);
+          ++boxes;
+        }
+      for (int z = -g0; z < p.n[2] + g0; ++z)
+        for (int y = -g0; y < p.n[1] + g0; ++y)
+          for (int x = -g0; x < p.n[0] + g0; ++x) {
+            const int c[3] = {x, y, z};
+            int out = 0;
+            for (int d = 0; d < 3; ++d) out += (c[d] < 0 || c[d] >= p.n[d]) ? 1 : 0;
+            const int want = out == 1 ? 1 : 0;   // face layers only (no edges, corners or interior)
+            if (at(x, y, z) != want) {
+              printf("patch %d cell (%d, %d, %d): covered %d times, want %d\n", i, x, y, z, (int)at(x, y, z), want);
+              return 1;
+            }
+          }
+    }
+  }
+  printf("ok %lld %lld\n", segs, boxes);
+  return 0;
+}
+
 int main() {
+  char mode[16] = {0};
+  if (scanf("%15s", mode) != 1) return 2;
+  if (std::string(mode) == "ghost") return check_ghost();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

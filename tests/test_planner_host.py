@@ -1,8 +1,11 @@
-"""Host planner checks that need no GPU: the regrid fill of a new hierarchy
-fills every cell of every rebuilt patch exactly once, from the old patches of
-its level (copy segments that keep each cell in place) or by prolongation
-(fresh boxes).  The planner source is compiled with a small C++ driver
-(`planner_check.cpp`) for the check."""
+"""Host planner checks that need no GPU, with the planner source compiled with a
+small C++ driver (`planner_check.cpp`):
+* the regrid fill of a new hierarchy fills every cell of every rebuilt patch
+  exactly once, from the old patches of its level (copy segments that keep each
+  cell in place) or by prolongation (fresh boxes);
+* the ghost tables cover each of the two ghost layers of every patch face
+  exactly once (same-level copies of the right level cell, periodic images,
+  outflow boundary cells, or prolongation boxes) and nothing else."""
 import os
 import shutil
 import subprocess
@@ -35,7 +38,7 @@ def listing(patches):
 
 
 def run(checker, base, max_level, old, new):
-    text = f"{base} {base} {base} {max_level}\n{listing(old)}\n{listing(new)}\n"
+    text = f"fill {base} {base} {base} {max_level}\n{listing(old)}\n{listing(new)}\n"
     r = subprocess.run([checker], input=text, capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
     return [int(x) for x in r.stdout.split()[1:]]
@@ -64,3 +67,23 @@ def test_fill_with_shifted_and_shrunk_levels(checker):
     # drop a few refined patches of the new hierarchy (holes are allowed for the fill)
     keep = [p for p in new if p.level == 0 or rng.random() > 0.2]
     run(checker, 32, 2, old, keep)
+
+
+def ghost(checker, base, max_level, bc, patches):
+    text = f"ghost {base} {base} {base} {max_level} {' '.join(map(str, bc))}\n{listing(patches)}\n"
+    r = subprocess.run([checker], input=text, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    return [int(x) for x in r.stdout.split()[1:]]
+
+
+@pytest.mark.parametrize("bc", [(ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6,
+                                (ai.PERIODIC, ai.PERIODIC, ai.OUTFLOW, ai.OUTFLOW, ai.PERIODIC, ai.PERIODIC)])
+def test_ghost_layers_covered_once(checker, bc):
+    segs, boxes = ghost(checker, 32, 2, bc, ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16))
+    assert segs > 0 and boxes > 0
+
+
+def test_ghost_layers_of_the_sedov_hierarchy(checker):
+    pb = ai.sedov_amr()
+    segs, boxes = ghost(checker, pb.base_n[0], pb.max_level, pb.bc, pb.patches)
+    assert segs > 0 and boxes > 0
