@@ -15,7 +15,16 @@
 // segment copies, for every ghost cell, the level cell at that cell's position
 // (wrapped on periodic axes) or, across an outflow face, the boundary cell of
 // the patch itself.
+//
+// "registers": same input as "ghost".  The flux-register rectangles of each
+// fine patch face hold exactly the coarse cells next to that face that no
+// patch of the fine level covers (wrapped on periodic axes, none beyond an
+// outflow face), each once, each in the coarse patch that holds it, with the
+// coarse cell on the right side of the face; a rectangle marked unordered has
+// no cell that another rectangle also holds.
+#include <array>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -125,10 +134,134 @@ static int check_ghost() {
   return 0;
 }
 
+static bool read_config(amr_config& cfg, int bn[3], int& ml, std::vector<HPatch>& P) {
+  int bc[6];
+  if (scanf("%d %d %d %d %d %d %d %d %d %d", &bn[0], &bn[1], &bn[2], &ml, &bc[0], &bc[1], &bc[2], &bc[3], &bc[4],
+            &bc[5]) != 10)
+    return false;
+  if (!read_list(P)) return false;
+  cfg = amr_config{};
+  cfg.nvar = 5;
+  cfg.precision = AMR_FP32;
+  cfg.gamma = 1.4;
+  cfg.theta = 1.5;
+  cfg.cfl = 0.4;
+  cfg.ref_ratio = 2;
+  for (int d = 0; d < 3; ++d) {
+    cfg.base_n[d] = bn[d];
+    cfg.domain_lo[d] = 0;
+    cfg.domain_hi[d] = 1;
+  }
+  for (int f = 0; f < 6; ++f) cfg.bc[f] = bc[f];
+  cfg.max_level = ml;
+  cfg.batched = 1;
+  return true;
+}
+
+static int check_registers() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  if (!read_config(cfg, bn, ml, P)) return 2;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, TileParams()) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  auto level_n = [&](int l, int d) { return bn[d] << l; };
+  auto periodic = [&](int d) { return cfg.bc[2 * d] == AMR_BC_PERIODIC; };
+  long long nreg = 0;
+  for (int l = 1; l < (int)plan.levels.size(); ++l) {
+    const LevelPlan& L = plan.levels[l];
+    const LevelPlan& C = plan.levels[l - 1];
+    // coarse cell (global, level l-1) -> (coarse patch, count) of the registers on each fine face
+    std::map<std::array<int, 6>, int> got;   // (fpatch, 2d+side, cx, cy, cz, 0) -> count
+    std::map<std::array<int, 6>, int> all_cells;   // (cx, cy, cz, 0, 0, 0) -> registers on the cell
+    for (const RegRect& r : L.regs.boxes) {
+      const HPatch& cp = P[r.cpatch];
+      if (cp.level != l - 1 || P[r.fpatch].level != l) { printf("register on a wrong level\n"); return 1; }
+      const int d = r.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      for (int a = 0; a < r.na; ++a)
+        for (int b = 0; b < r.nb; ++b) {
+          int c[3] = {r.clo[0], r.clo[1], r.clo[2]};
+          c[t1] += a;
+          c[t2] += b;
+          for (int k = 0; k < 3; ++k)
+            if (c[k] < 0 || c[k] >= cp.n[k]) { printf("register cell outside its coarse patch\n"); return 1; }
+          if (r.cside != (r.side ? -1 : 1)) { printf("register on the wrong side of its coarse cell\n"); return 1; }
+          std::array<int, 6> key{r.fpatch, 2 * d + r.side, cp.lo[0] + c[0], cp.lo[1] + c[1], cp.lo[2] + c[2], 0};
+          got[key] += 1;
+          all_cells[{cp.lo[0] + c[0], cp.lo[1] + c[1], cp.lo[2] + c[2], 0, 0, 0}] += 1;
+          ++nreg;
+        }
+    }
+    for (const RegRect& r : L.regs.boxes) {
+      if (r.ordered) continue;
+      const HPatch& cp = P[r.cpatch];
+      const int d = r.d, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      for (int a = 0; a < r.na; ++a)
+        for (int b = 0; b < r.nb; ++b) {
+          int c[3] = {r.clo[0], r.clo[1], r.clo[2]};
+          c[t1] += a;
+          c[t2] += b;
+          if (all_cells[{cp.lo[0] + c[0], cp.lo[1] + c[1], cp.lo[2] + c[2], 0, 0, 0}] != 1) {
+            printf("unordered rectangle shares a cell with another register\n");
+            return 1;
+          }
+        }
+    }
+    // expected: every coarse cell next to a fine face that no level-l patch covers
+    std::map<std::array<int, 6>, int> want;
+    for (int i = L.first; i < L.first + L.count; ++i) {
+      const HPatch& p = P[i];
+      for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side) {
+          const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          int Cd = side ? (p.lo[d] + p.n[d]) / 2 : p.lo[d] / 2 - 1;
+          const int Nc = level_n(l - 1, d);
+          if (Cd < 0 || Cd >= Nc) {
+            if (!periodic(d)) continue;
+            Cd = ((Cd % Nc) + Nc) % Nc;
+          }
+          for (int u = p.lo[t1] / 2; u < (p.lo[t1] + p.n[t1]) / 2; ++u)
+            for (int v = p.lo[t2] / 2; v < (p.lo[t2] + p.n[t2]) / 2; ++v) {
+              int c[3];
+              c[d] = Cd; c[t1] = u; c[t2] = v;
+              bool covered = false;
+              for (int q = L.first; q < L.first + L.count && !covered; ++q) {
+                const HPatch& o = P[q];
+                bool in = true;
+                for (int k = 0; k < 3 && in; ++k) in = 2 * c[k] >= o.lo[k] && 2 * c[k] < o.lo[k] + o.n[k];
+                covered = in;
+              }
+              if (covered) continue;
+              bool held = false;
+              for (int q = C.first; q < C.first + C.count && !held; ++q) {
+                const HPatch& o = P[q];
+                bool in = true;
+                for (int k = 0; k < 3 && in; ++k) in = c[k] >= o.lo[k] && c[k] < o.lo[k] + o.n[k];
+                held = in;
+              }
+              if (!held) { printf("coarse cell next to a fine face outside the coarse level\n"); return 1; }
+              want[{i, 2 * d + side, c[0], c[1], c[2], 0}] = 1;
+            }
+        }
+    }
+    if (got != want) {
+      printf("level %d: registers %zu cells, expected %zu\n", l, got.size(), want.size());
+      return 1;
+    }
+  }
+  printf("ok %lld\n", nreg);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
   if (std::string(mode) == "ghost") return check_ghost();
+  if (std::string(mode) == "registers") return check_registers();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

@@ -5,7 +5,10 @@ small C++ driver (`planner_check.cpp`):
   cell in place) or by prolongation (fresh boxes);
 * the ghost tables cover each of the two ghost layers of every patch face
   exactly once (same-level copies of the right level cell, periodic images,
-  outflow boundary cells, or prolongation boxes) and nothing else."""
+  outflow boundary cells, or prolongation boxes) and nothing else;
+* the flux-register rectangles hold exactly the coarse cells next to each fine
+  patch face that the fine level does not cover (Sec. 3's correction), each
+  once, and a rectangle reflowed in any order shares no cell with another."""
 import os
 import shutil
 import subprocess
@@ -69,8 +72,8 @@ def test_fill_with_shifted_and_shrunk_levels(checker):
     run(checker, 32, 2, old, keep)
 
 
-def ghost(checker, base, max_level, bc, patches):
-    text = f"ghost {base} {base} {base} {max_level} {' '.join(map(str, bc))}\n{listing(patches)}\n"
+def ghost(checker, base, max_level, bc, patches, mode="ghost"):
+    text = f"{mode} {base} {base} {base} {max_level} {' '.join(map(str, bc))}\n{listing(patches)}\n"
     r = subprocess.run([checker], input=text, capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
     return [int(x) for x in r.stdout.split()[1:]]
@@ -87,3 +90,20 @@ def test_ghost_layers_of_the_sedov_hierarchy(checker):
     pb = ai.sedov_amr()
     segs, boxes = ghost(checker, pb.base_n[0], pb.max_level, pb.bc, pb.patches)
     assert segs > 0 and boxes > 0
+
+
+@pytest.mark.parametrize("bc", [(ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6,
+                                (ai.PERIODIC, ai.PERIODIC, ai.OUTFLOW, ai.OUTFLOW, ai.PERIODIC, ai.PERIODIC)])
+def test_register_cells(checker, bc):
+    (n,) = ghost(checker, 32, 2, bc, ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16), mode="registers")
+    assert n > 0
+
+
+def test_register_cells_of_a_refined_region_touching_the_domain_boundary(checker):
+    # the level-1 cube spans the whole domain along x: periodic registers wrap, outflow ones stop
+    base = 16
+    patches = ai.box_patches(0, (0, 0, 0), (base,) * 3, np.random.Generator(np.random.PCG64(3)), 4, 8)
+    patches += ai.box_patches(1, (0, 8, 8), (32, 24, 24), np.random.Generator(np.random.PCG64(4)), 4, 8)
+    for bc in ((ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6):
+        (n,) = ghost(checker, base, 1, bc, patches, mode="registers")
+        assert n > 0
