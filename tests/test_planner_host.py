@@ -107,3 +107,18 @@ def test_register_cells_of_a_refined_region_touching_the_domain_boundary(checker
     for bc in ((ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6):
         (n,) = ghost(checker, base, 1, bc, patches, mode="registers")
         assert n > 0
+
+
+def test_register_cells_on_partly_covered_faces(checker):
+    # a refined slab attached to one face of a refined cube: the cube's patch faces
+    # there border the fine level over most of their area, but not all of it
+    base = 32
+    rng = np.random.Generator(np.random.PCG64(7))
+    patches = ai.box_patches(0, (0, 0, 0), (base,) * 3, rng, 8, 16)
+    patches += ai.box_patches(1, (16, 16, 16), (40, 40, 40), rng, 8, 16)
+    patches += ai.box_patches(1, (40, 16, 16), (48, 40, 36), rng, 8, 12)
+    for bc in ((ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6):
+        (n,) = ghost(checker, base, 1, bc, patches, mode="registers")
+        assert n > 0
+        segs, boxes = ghost(checker, base, 1, bc, patches)
+        assert boxes > 0
