@@ -22,6 +22,12 @@
 // outflow face), each once, each in the coarse patch that holds it, with the
 // coarse cell on the right side of the face; a rectangle marked unordered has
 // no cell that another rectangle also holds.
+//
+// "items": same input as "ghost" plus the tile shape (max_wx max_cols zchunk).
+// The stage work items of every level, the per-patch ones and the batched ones
+// (blocks over the z-layers of patches that tile a rectangle included), cover
+// every interior cell of the level exactly once, each block column inside one
+// patch of the block over the block's whole z range.
 #include <array>
 #include <cstdio>
 #include <map>
@@ -257,11 +263,77 @@ static int check_registers() {
   return 0;
 }
 
+static int check_items() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  if (!read_config(cfg, bn, ml, P)) return 2;
+  TileParams tp;
+  if (scanf("%d %d %d", &tp.max_wx, &tp.max_cols, &tp.zchunk) != 3) return 2;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, tp) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  long long nitems = 0, nspan = 0;
+  for (const LevelPlan& L : plan.levels) {
+    for (int pass = 0; pass < 2; ++pass) {   // 0: per-patch items, 1: batched items
+      std::vector<std::vector<unsigned char>> cnt(L.count);
+      for (int ii = 0; ii < L.count; ++ii) {
+        const HPatch& p = P[L.first + ii];
+        cnt[ii].assign((size_t)p.n[0] * p.n[1] * p.n[2], 0);
+      }
+      const std::vector<StageItem>& items = pass ? L.bitems : L.items;
+      for (const StageItem& it : items) {
+        if (it.wx <= 0 || it.wy <= 0 || it.wz <= 0 || it.wx * it.wy > 256) { printf("bad block shape\n"); return 1; }
+        int ox, oy, oz;
+        std::vector<int> cand;
+        if (it.span >= 0) {
+          if (!pass) { printf("spanning block among the per-patch items\n"); return 1; }
+          const ItemSpan& S = plan.spans[it.span];
+          ox = S.ox; oy = S.oy; oz = S.oz;
+          cand.assign(S.patch, S.patch + S.n);
+          ++nspan;
+        } else {
+          const HPatch& q = P[it.patch];
+          ox = q.lo[0] + it.x0; oy = q.lo[1] + it.y0; oz = q.lo[2] + it.z0;
+          cand.push_back(it.patch);
+        }
+        for (int ty = 0; ty < it.wy; ++ty)
+          for (int tx = 0; tx < it.wx; ++tx) {
+            const int gx = ox + tx, gy = oy + ty;
+            int qc = -1;
+            for (int q : cand) {
+              const HPatch& o = P[q];
+              if (gx >= o.lo[0] && gx < o.lo[0] + o.n[0] && gy >= o.lo[1] && gy < o.lo[1] + o.n[1]) { qc = q; break; }
+            }
+            if (qc < 0 || qc < L.first || qc >= L.first + L.count) { printf("block column outside its patches\n"); return 1; }
+            const HPatch& o = P[qc];
+            if (oz < o.lo[2] || oz + it.wz > o.lo[2] + o.n[2]) { printf("block z range leaves its patch\n"); return 1; }
+            for (int z = oz; z < oz + it.wz; ++z)
+              cnt[qc - L.first][((size_t)(z - o.lo[2]) * o.n[1] + (gy - o.lo[1])) * o.n[0] + (gx - o.lo[0])] += 1;
+          }
+        ++nitems;
+      }
+      for (int ii = 0; ii < L.count; ++ii)
+        for (unsigned char c : cnt[ii])
+          if (c != 1) {
+            printf("%s items: a cell of patch %d covered %d times\n", pass ? "batched" : "per-patch", L.first + ii, c);
+            return 1;
+          }
+    }
+  }
+  printf("ok %lld %lld\n", nitems, nspan);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
   if (std::string(mode) == "ghost") return check_ghost();
   if (std::string(mode) == "registers") return check_registers();
+  if (std::string(mode) == "items") return check_items();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

@@ -8,7 +8,9 @@ small C++ driver (`planner_check.cpp`):
   outflow boundary cells, or prolongation boxes) and nothing else;
 * the flux-register rectangles hold exactly the coarse cells next to each fine
   patch face that the fine level does not cover (Sec. 3's correction), each
-  once, and a rectangle reflowed in any order shares no cell with another."""
+  once, and a rectangle reflowed in any order shares no cell with another;
+* the stage work items, per patch and batched (blocks over z-layers of patches
+  that tile a rectangle included), cover every interior cell exactly once."""
 import os
 import shutil
 import subprocess
@@ -122,3 +124,14 @@ def test_register_cells_on_partly_covered_faces(checker):
         assert n > 0
         segs, boxes = ghost(checker, base, 1, bc, patches)
         assert boxes > 0
+
+
+@pytest.mark.parametrize("tiling", [(32, 256, 32), (16, 256, 16), (16, 128, 8), (32, 256, 64)])
+def test_stage_items_cover_every_cell_once(checker, tiling):
+    pb = ai.sedov_amr()
+    text = (f"items {pb.base_n[0]} {pb.base_n[1]} {pb.base_n[2]} {pb.max_level} {' '.join(map(str, pb.bc))}\n"
+            f"{listing(pb.patches)}\n{' '.join(map(str, tiling))}\n")
+    r = subprocess.run([checker], input=text, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    nitems, nspan = [int(x) for x in r.stdout.split()[1:]]
+    assert nspan > 0   # the nested cubes' z-layers tile rectangles: blocks span patches
