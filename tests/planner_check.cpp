@@ -28,6 +28,11 @@
 // (blocks over the z-layers of patches that tile a rectangle included), cover
 // every interior cell of the level exactly once, each block column inside one
 // patch of the block over the block's whole z range.
+//
+// "gathers": same input as "ghost".  For every refined patch, each parent-tile
+// cell that its prolongation reads (the parents of its prolongation boxes and
+// their face neighbours) is gathered exactly once, from the coarse cell at that
+// position (wrapped on periodic axes, the boundary cell beyond an outflow face).
 #include <array>
 #include <cstdio>
 #include <map>
@@ -328,12 +333,90 @@ static int check_items() {
   return 0;
 }
 
+static int check_gathers() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  if (!read_config(cfg, bn, ml, P)) return 2;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, TileParams()) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  auto fdiv = [](int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); };
+  long long ncell = 0;
+  for (int l = 1; l < (int)plan.levels.size(); ++l) {
+    const LevelPlan& L = plan.levels[l];
+    std::vector<std::vector<unsigned char>> need(L.count), got(L.count);
+    for (int ii = 0; ii < L.count; ++ii) {
+      const HPatch& p = P[L.first + ii];
+      const size_t tv = (size_t)(p.n[0] / 2 + 4) * (p.n[1] / 2 + 4) * (p.n[2] / 2 + 4);
+      need[ii].assign(tv, 0);
+      got[ii].assign(tv, 0);
+    }
+    for (const ProlongBox& b : L.prolong) {
+      const HPatch& p = P[b.patch];
+      const int ii = b.patch - L.first;
+      const int tn[3] = {p.n[0] / 2 + 4, p.n[1] / 2 + 4, p.n[2] / 2 + 4};
+      for (int z = b.lo[2]; z < b.lo[2] + b.n[2]; ++z)
+        for (int y = b.lo[1]; y < b.lo[1] + b.n[1]; ++y)
+          for (int x = b.lo[0]; x < b.lo[0] + b.n[0]; ++x) {
+            const int f[3] = {x, y, z};
+            int t[3];
+            for (int d = 0; d < 3; ++d) t[d] = fdiv(p.lo[d] + f[d]) - (fdiv(p.lo[d]) - 2);
+            for (int k = -1; k < 6; ++k) {   // the parent and its six face neighbours
+              int u[3] = {t[0], t[1], t[2]};
+              if (k >= 0) u[k / 2] += (k & 1) ? 1 : -1;
+              for (int d = 0; d < 3; ++d)
+                if (u[d] < 0 || u[d] >= tn[d]) { printf("stencil outside the parent tile\n"); return 1; }
+              need[ii][((size_t)u[2] * tn[1] + u[1]) * tn[0] + u[0]] = 1;
+            }
+          }
+    }
+    for (const CopySeg& s : L.gather_ghost) {
+      const HPatch& p = P[s.dst_patch];
+      const HPatch& o = P[s.src_patch];
+      if (p.level != l || o.level != l - 1) { printf("gather segment on a wrong level\n"); return 1; }
+      const int ii = s.dst_patch - L.first;
+      const int tn[3] = {p.n[0] / 2 + 4, p.n[1] / 2 + 4, p.n[2] / 2 + 4};
+      for (int z = s.dlo[2]; z < s.dlo[2] + s.dn[2]; ++z)
+        for (int y = s.dlo[1]; y < s.dlo[1] + s.dn[1]; ++y)
+          for (int x = s.dlo[0]; x < s.dlo[0] + s.dn[0]; ++x) {
+            const int t[3] = {x, y, z};
+            for (int d = 0; d < 3; ++d) {
+              if (t[d] < 0 || t[d] >= tn[d]) { printf("gather outside the parent tile\n"); return 1; }
+              const int src = s.mode[d] ? s.sh[d] : t[d] + s.sh[d];   // coarse-patch local
+              if (src < 0 || src >= o.n[d]) { printf("gather source outside its coarse patch\n"); return 1; }
+              const int Nc = bn[d] << (l - 1);
+              int G = fdiv(p.lo[d]) - 2 + t[d];   // the coarse cell under tile cell t
+              if (G < 0 || G >= Nc) {
+                if (cfg.bc[2 * d] == AMR_BC_PERIODIC) G = ((G % Nc) + Nc) % Nc;
+                else G = G < 0 ? 0 : Nc - 1;
+              }
+              if (o.lo[d] + src != G) { printf("gather reads another coarse cell\n"); return 1; }
+            }
+            got[ii][((size_t)z * tn[1] + y) * tn[0] + x] += 1;
+          }
+    }
+    for (int ii = 0; ii < L.count; ++ii)
+      for (size_t c = 0; c < need[ii].size(); ++c) {
+        if (got[ii][c] > 1) { printf("a tile cell gathered twice\n"); return 1; }
+        if (need[ii][c] && !got[ii][c]) { printf("a needed tile cell not gathered\n"); return 1; }
+        ncell += got[ii][c];
+      }
+  }
+  printf("ok %lld\n", ncell);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
   if (std::string(mode) == "ghost") return check_ghost();
   if (std::string(mode) == "registers") return check_registers();
   if (std::string(mode) == "items") return check_items();
+  if (std::string(mode) == "gathers") return check_gathers();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

@@ -10,7 +10,9 @@ small C++ driver (`planner_check.cpp`):
   patch face that the fine level does not cover (Sec. 3's correction), each
   once, and a rectangle reflowed in any order shares no cell with another;
 * the stage work items, per patch and batched (blocks over z-layers of patches
-  that tile a rectangle included), cover every interior cell exactly once."""
+  that tile a rectangle included), cover every interior cell exactly once;
+* the parent-tile gathers hold, once each, every parent cell the prolongation
+  reads, taken from the right coarse cell."""
 import os
 import shutil
 import subprocess
@@ -135,3 +137,14 @@ def test_stage_items_cover_every_cell_once(checker, tiling):
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
     nitems, nspan = [int(x) for x in r.stdout.split()[1:]]
     assert nspan > 0   # the nested cubes' z-layers tile rectangles: blocks span patches
+
+
+@pytest.mark.parametrize("bc", [(ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6])
+def test_gathers_hold_every_parent_cell_the_prolongation_reads(checker, bc):
+    (n,) = ghost(checker, 32, 2, bc, ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16), mode="gathers")
+    assert n > 0
+    base = 16   # a refined region across the whole domain along x: wrapped or clamped parents
+    patches = ai.box_patches(0, (0, 0, 0), (base,) * 3, np.random.Generator(np.random.PCG64(3)), 4, 8)
+    patches += ai.box_patches(1, (0, 8, 8), (32, 24, 24), np.random.Generator(np.random.PCG64(4)), 4, 8)
+    (n,) = ghost(checker, base, 1, bc, patches, mode="gathers")
+    assert n > 0
