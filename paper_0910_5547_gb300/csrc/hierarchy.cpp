@@ -1137,6 +1137,10 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
   // faces whose ghost layers a stage reads straight from a neighbour (or outflow boundary cells)
   const bool direct_ok = cfg.ghost_fill == AMR_GHOST_DIRECT && cfg.riemann != AMR_FLUXREC;
   std::vector<std::array<uint8_t, 6>> direct(np);
+  // bit 2d+side: the ghost layer of that face two cells out on the low side (one on
+  // the high side) -- the fine cells of the coarse cells next to the face -- lies
+  // in same-level patches all over, so the face has no flux register
+  std::vector<uint8_t> face_full(np, 0);
   for (auto& a : direct) a.fill(0);
 
   // ---- ghost fill: sibling copies (incl. periodic images), outflow, prolongation boxes ----
@@ -1209,6 +1213,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
                 Gv.push_back(s);
                 area += (int64_t)(a1 - a0) * (b1 - b0);
               }
+              if (area == (int64_t)A * B && gg == (side ? 0 : 1)) face_full[i] |= (uint8_t)(1u << (2 * d + side));
               std::vector<Rect> rects;
               if (area < (int64_t)A * B) {   // uncovered parts of the face layer: prolongation boxes
                 std::vector<unsigned char> mask((size_t)A * B, 0);
@@ -1369,6 +1374,7 @@ amr_status build_plan(const amr_config& cfg, const std::vector<HPatch>& P, Plan&
     std::vector<std::string> err(ntask);
     parallel_for(ntask, [&](int task) {
       const int d = task / (2 * L.count), side = (task / L.count) % 2, i = L.first + task % L.count;
+      if (face_full[i] & (1u << (2 * d + side))) return;   // the fine level covers the cells next to the face
       std::vector<RegRect>& Rv = rs[task];
       std::vector<int> cand;
           const HPatch& p = P[i];
