@@ -33,6 +33,11 @@
 // cell that its prolongation reads (the parents of its prolongation boxes and
 // their face neighbours) is gathered exactly once, from the coarse cell at that
 // position (wrapped on periodic axes, the boundary cell beyond an outflow face).
+//
+// "restrict": same input as "ghost".  Every coarse cell under a finer patch is
+// restricted exactly once, from the fine patch that holds its eight children,
+// and the coverage boxes (which exclude covered cells from the leaf totals)
+// mark exactly those coarse cells.
 #include <array>
 #include <cstdio>
 #include <map>
@@ -410,6 +415,74 @@ static int check_gathers() {
   return 0;
 }
 
+static int check_restrict() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  if (!read_config(cfg, bn, ml, P)) return 2;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, TileParams()) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  long long ncell = 0;
+  const int np = (int)P.size();
+  std::vector<std::vector<unsigned char>> rcnt(np), ccnt(np);
+  for (int i = 0; i < np; ++i) {
+    rcnt[i].assign((size_t)P[i].n[0] * P[i].n[1] * P[i].n[2], 0);
+    ccnt[i].assign(rcnt[i].size(), 0);
+  }
+  for (int l = 1; l < (int)plan.levels.size(); ++l)
+    for (const RestrictSeg& r : plan.levels[l].restrict_segs) {
+      const HPatch& f = P[r.fine];
+      const HPatch& c = P[r.coarse];
+      if (f.level != l || c.level != l - 1) { printf("restriction on a wrong level\n"); return 1; }
+      for (int z = r.clo[2]; z < r.clo[2] + r.cn[2]; ++z)
+        for (int y = r.clo[1]; y < r.clo[1] + r.cn[1]; ++y)
+          for (int x = r.clo[0]; x < r.clo[0] + r.cn[0]; ++x) {
+            const int cc[3] = {x, y, z};
+            for (int d = 0; d < 3; ++d) {
+              if (cc[d] < 0 || cc[d] >= c.n[d]) { printf("restricted cell outside its coarse patch\n"); return 1; }
+              const int g = 2 * (c.lo[d] + cc[d]);   // first child, level l
+              if (g < f.lo[d] || g + 2 > f.lo[d] + f.n[d]) { printf("children outside the fine patch\n"); return 1; }
+            }
+            rcnt[r.coarse][((size_t)z * c.n[1] + y) * c.n[0] + x] += 1;
+          }
+    }
+  for (int i = 0; i < np; ++i)
+    for (int e = plan.cover_first[i]; e < plan.cover_first[i + 1]; ++e) {
+      const CoverBox& b = plan.cover[e];
+      const HPatch& c = P[i];
+      for (int z = b.lo[2]; z < b.lo[2] + b.n[2]; ++z)
+        for (int y = b.lo[1]; y < b.lo[1] + b.n[1]; ++y)
+          for (int x = b.lo[0]; x < b.lo[0] + b.n[0]; ++x) ccnt[i][((size_t)z * c.n[1] + y) * c.n[0] + x] += 1;
+    }
+  for (int i = 0; i < np; ++i) {
+    const HPatch& c = P[i];
+    for (int z = 0; z < c.n[2]; ++z)
+      for (int y = 0; y < c.n[1]; ++y)
+        for (int x = 0; x < c.n[0]; ++x) {
+          // covered: some patch one level finer holds the cell's first child
+          bool covered = false;
+          for (int q = 0; q < np && !covered; ++q) {
+            const HPatch& f = P[q];
+            if (f.level != c.level + 1) continue;
+            const int g[3] = {2 * (c.lo[0] + x), 2 * (c.lo[1] + y), 2 * (c.lo[2] + z)};
+            bool in = true;
+            for (int d = 0; d < 3 && in; ++d) in = g[d] >= f.lo[d] && g[d] < f.lo[d] + f.n[d];
+            covered = in;
+          }
+          const size_t k = ((size_t)z * c.n[1] + y) * c.n[0] + x;
+          if (rcnt[i][k] != (covered ? 1 : 0)) { printf("patch %d: a coarse cell restricted %d times\n", i, rcnt[i][k]); return 1; }
+          if (ccnt[i][k] != (covered ? 1 : 0)) { printf("patch %d: a coverage box count %d\n", i, ccnt[i][k]); return 1; }
+          ncell += covered ? 1 : 0;
+        }
+  }
+  printf("ok %lld\n", ncell);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
@@ -417,6 +490,7 @@ int main() {
   if (std::string(mode) == "registers") return check_registers();
   if (std::string(mode) == "items") return check_items();
   if (std::string(mode) == "gathers") return check_gathers();
+  if (std::string(mode) == "restrict") return check_restrict();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

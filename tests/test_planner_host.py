@@ -12,7 +12,9 @@ small C++ driver (`planner_check.cpp`):
 * the stage work items, per patch and batched (blocks over z-layers of patches
   that tile a rectangle included), cover every interior cell exactly once;
 * the parent-tile gathers hold, once each, every parent cell the prolongation
-  reads, taken from the right coarse cell."""
+  reads, taken from the right coarse cell;
+* every coarse cell under a finer patch is restricted once, from the patch that
+  holds its children, and the leaf-coverage boxes mark exactly those cells."""
 import os
 import shutil
 import subprocess
@@ -148,3 +150,16 @@ def test_gathers_hold_every_parent_cell_the_prolongation_reads(checker, bc):
     patches += ai.box_patches(1, (0, 8, 8), (32, 24, 24), np.random.Generator(np.random.PCG64(4)), 4, 8)
     (n,) = ghost(checker, base, 1, bc, patches, mode="gathers")
     assert n > 0
+
+
+def test_restriction_and_coverage(checker):
+    (n,) = ghost(checker, 32, 2, (ai.PERIODIC,) * 6, ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16),
+                 mode="restrict")
+    assert n == 16 ** 3 + 16 ** 3   # the two refined cubes of 32^3 fine cells cover 16^3 cells each below
+    base = 32
+    rng = np.random.Generator(np.random.PCG64(7))
+    patches = ai.box_patches(0, (0, 0, 0), (base,) * 3, rng, 8, 16)
+    patches += ai.box_patches(1, (16, 16, 16), (40, 40, 40), rng, 8, 16)
+    patches += ai.box_patches(1, (40, 16, 16), (48, 40, 36), rng, 8, 12)
+    (n,) = ghost(checker, base, 1, (ai.OUTFLOW,) * 6, patches, mode="restrict")
+    assert n == 12 ** 3 + 4 * 12 * 10
