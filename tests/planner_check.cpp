@@ -38,6 +38,14 @@
 // restricted exactly once, from the fine patch that holds its eight children,
 // and the coverage boxes (which exclude covered cells from the leaf totals)
 // mark exactly those coarse cells.
+//
+// "faces": same input as "ghost".  Where a patch face is read in place (its
+// face-table entry is not the patch's own ghost cells), the entry maps each
+// cell of the face's two ghost layers to the interior cell that holds that
+// level position (wrapped on periodic axes) in a patch of the same level, or,
+// across an outflow face, to the patch's own boundary cell; the entry's
+// variable stride is that patch's.
+#include <algorithm>
 #include <array>
 #include <cstdio>
 #include <map>
@@ -483,6 +491,68 @@ static int check_restrict() {
   return 0;
 }
 
+static int check_faces() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  if (!read_config(cfg, bn, ml, P)) return 2;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, TileParams()) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  const int np = (int)P.size();
+  std::vector<std::pair<int64_t, int>> starts(np);   // (arena offset, patch), ascending
+  for (int i = 0; i < np; ++i) starts[i] = {plan.desc[i].off, i};
+  std::sort(starts.begin(), starts.end());
+  long long ndirect = 0;
+  for (int i = 0; i < np; ++i) {
+    const PatchDesc& D = plan.desc[i];
+    const HPatch& p = P[i];
+    const int64_t own = D.off + ((int64_t)kGhost * D.m1 + kGhost) * D.pitch + kGhost;
+    for (int f = 0; f < 6; ++f) {
+      const FaceSrc& fs = D.face[f];
+      if (fs.base == own && fs.sx == 1 && fs.sy == D.pitch && fs.sz == D.pitch * D.m1) continue;   // own ghosts
+      ++ndirect;
+      const int d = f / 2, side = f % 2, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      for (int g = 0; g < kGhost; ++g)
+        for (int b = 0; b < p.n[t2]; ++b)
+          for (int a = 0; a < p.n[t1]; ++a) {
+            int c[3];
+            c[d] = side ? p.n[d] + g : -1 - g;
+            c[t1] = a;
+            c[t2] = b;
+            const int64_t o = fs.base + (int64_t)c[0] * fs.sx + (int64_t)c[1] * fs.sy + (int64_t)c[2] * fs.sz;
+            auto it = std::upper_bound(starts.begin(), starts.end(), std::make_pair(o, np));
+            if (it == starts.begin()) { printf("face entry points before the arena\n"); return 1; }
+            const int q = std::prev(it)->second;
+            const PatchDesc& Q = plan.desc[q];
+            const int64_t idx = o - Q.off;
+            if (idx >= Q.vstride) { printf("face entry points past a patch\n"); return 1; }
+            const int lz = (int)(idx / ((int64_t)Q.pitch * Q.m1)) - kGhost;
+            const int ly = (int)((idx / Q.pitch) % Q.m1) - kGhost;
+            const int lx = (int)(idx % Q.pitch) - kGhost;
+            const int l[3] = {lx, ly, lz};
+            for (int k = 0; k < 3; ++k)
+              if (l[k] < 0 || l[k] >= P[q].n[k]) { printf("face entry reads a ghost cell\n"); return 1; }
+            if (P[q].level != p.level || fs.vs != (int)Q.vstride) { printf("face source of another level\n"); return 1; }
+            for (int k = 0; k < 3; ++k) {
+              const int N = bn[k] << p.level;
+              int G = p.lo[k] + c[k];
+              if (G < 0 || G >= N) {
+                if (cfg.bc[2 * k] == AMR_BC_PERIODIC) G = ((G % N) + N) % N;
+                else G = G < 0 ? 0 : N - 1;   // outflow: the boundary cell of the patch itself
+              }
+              if (P[q].lo[k] + l[k] != G) { printf("patch %d face %d reads another position\n", i, f); return 1; }
+            }
+          }
+    }
+  }
+  printf("ok %lld\n", ndirect);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
@@ -491,6 +561,7 @@ int main() {
   if (std::string(mode) == "items") return check_items();
   if (std::string(mode) == "gathers") return check_gathers();
   if (std::string(mode) == "restrict") return check_restrict();
+  if (std::string(mode) == "faces") return check_faces();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

@@ -14,7 +14,10 @@ small C++ driver (`planner_check.cpp`):
 * the parent-tile gathers hold, once each, every parent cell the prolongation
   reads, taken from the right coarse cell;
 * every coarse cell under a finer patch is restricted once, from the patch that
-  holds its children, and the leaf-coverage boxes mark exactly those cells."""
+  holds its children, and the leaf-coverage boxes mark exactly those cells;
+* a face whose ghost layers the stage kernel reads in place maps each ghost
+  cell to the interior cell at that level position (periodic image) or to the
+  patch's own boundary cell (outflow)."""
 import os
 import shutil
 import subprocess
@@ -163,3 +166,13 @@ def test_restriction_and_coverage(checker):
     patches += ai.box_patches(1, (40, 16, 16), (48, 40, 36), rng, 8, 12)
     (n,) = ghost(checker, base, 1, (ai.OUTFLOW,) * 6, patches, mode="restrict")
     assert n == 12 ** 3 + 4 * 12 * 10
+
+
+@pytest.mark.parametrize("bc", [(ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6,
+                                (ai.PERIODIC, ai.PERIODIC, ai.OUTFLOW, ai.OUTFLOW, ai.PERIODIC, ai.PERIODIC)])
+def test_faces_read_in_place_map_to_the_right_cells(checker, bc):
+    (n,) = ghost(checker, 32, 2, bc, ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16), mode="faces")
+    assert n > 0
+    pb = ai.sedov_amr()
+    (n,) = ghost(checker, pb.base_n[0], pb.max_level, bc, pb.patches, mode="faces")
+    assert n > 0
