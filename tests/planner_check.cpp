@@ -45,6 +45,13 @@
 // level position (wrapped on periodic axes) in a patch of the same level, or,
 // across an outflow face, to the patch's own boundary cell; the entry's
 // variable stride is that patch's.
+//
+// "flat": same input as "ghost".  The flattened lists the batched kernels walk
+// address the same cells as the boxes they come from: each prolongation box,
+// walked by parent cell as box_prolong_kernel does (children 2p + i - odd in
+// the box), writes each of its fine cells once, at that cell's arena index,
+// from the parent-tile cell above it; each ghost copy box reads and writes the
+// cells of its segment.
 #include <algorithm>
 #include <array>
 #include <cstdio>
@@ -553,6 +560,80 @@ static int check_faces() {
   return 0;
 }
 
+static int check_flat() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  if (!read_config(cfg, bn, ml, P)) return 2;
+  Plan plan;
+  std::string msg;
+  if (build_plan(cfg, P, plan, msg, TileParams()) != AMR_OK) {
+    printf("plan failed: %s\n", msg.c_str());
+    return 1;
+  }
+  auto fdiv = [](int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); };
+  long long nb = 0;
+  for (const LevelPlan& L : plan.levels) {
+    if (L.fprolong.boxes.size() != L.prolong.size()) { printf("flattened prolongation list length\n"); return 1; }
+    for (size_t k = 0; k < L.prolong.size(); ++k) {
+      const ProlongBox& b = L.prolong[k];
+      const FlatProlong& g = L.fprolong.boxes[k];
+      const PatchDesc& D = plan.desc[b.patch];
+      const int np2 = L.fprolong.first[k + 1] - L.fprolong.first[k];
+      if (np2 % (g.np0 * g.np1) != 0) { printf("parent count not a whole number of planes\n"); return 1; }
+      std::map<int64_t, int> written;   // arena index -> times
+      for (int q = 0; q < np2; ++q) {   // as box_prolong_kernel: q -> (pa, pb, pc)
+        const int r = q / g.np0, pa = q - r * g.np0, pc = r / g.np1, pb = r - pc * g.np1;
+        const int a0 = 2 * pa - (g.odd & 1), b0 = 2 * pb - ((g.odd >> 1) & 1), c0 = 2 * pc - ((g.odd >> 2) & 1);
+        const int64_t tile = g.tp0 + pa + (int64_t)pb * g.tsy + (int64_t)pc * g.tsz;
+        for (int kz = 0; kz < 2; ++kz)
+          for (int jy = 0; jy < 2; ++jy)
+            for (int ix = 0; ix < 2; ++ix) {
+              const int a = a0 + ix, bb = b0 + jy, c = c0 + kz;
+              if (a < 0 || a >= g.n[0] || bb < 0 || bb >= g.n[1] || c < 0 || c >= g.n[2]) continue;
+              const int f[3] = {b.lo[0] + a, b.lo[1] + bb, b.lo[2] + c};   // fine cell, patch local
+              const int64_t di = g.dst0 + a + (int64_t)bb * g.dsy + (int64_t)c * g.dsz;
+              if (di != D.off + cell_index(D, f[0], f[1], f[2])) { printf("prolongation writes another cell\n"); return 1; }
+              int t[3];
+              for (int d = 0; d < 3; ++d) t[d] = fdiv(D.lo[d] + f[d]) - (fdiv(D.lo[d]) - 2);
+              const int64_t want = D.tile_off + t[0] + (int64_t)t[1] * D.tn[0] + (int64_t)t[2] * D.tn[0] * D.tn[1];
+              if (tile != want) { printf("prolongation reads another parent\n"); return 1; }
+              written[di] += 1;
+            }
+      }
+      if ((int64_t)written.size() != (int64_t)b.n[0] * b.n[1] * b.n[2]) { printf("prolongation box cells missed\n"); return 1; }
+      for (auto& w : written)
+        if (w.second != 1) { printf("prolongation writes a cell twice\n"); return 1; }
+      ++nb;
+    }
+    // ghost copies: the flattened box's source and destination of every cell
+    if (L.fghost_all.boxes.size() != L.ghost.size()) { printf("flattened ghost list length\n"); return 1; }
+    for (size_t k = 0; k < L.ghost.size(); ++k) {
+      const CopySeg& sgm = L.ghost[k];
+      const FlatCopy& c = L.fghost_all.boxes[k];
+      const PatchDesc& D = plan.desc[sgm.dst_patch];
+      const PatchDesc& S = plan.desc[sgm.src_patch];
+      for (int z = 0; z < sgm.dn[2]; ++z)
+        for (int y = 0; y < sgm.dn[1]; ++y)
+          for (int x = 0; x < sgm.dn[0]; ++x) {
+            const int dl[3] = {sgm.dlo[0] + x, sgm.dlo[1] + y, sgm.dlo[2] + z};
+            int sl[3];
+            for (int d = 0; d < 3; ++d) sl[d] = sgm.mode[d] ? sgm.sh[d] : dl[d] + sgm.sh[d];
+            const int64_t di = c.dst0 + x + (int64_t)y * c.dsy + (int64_t)z * c.dsz;
+            const int64_t si = c.src0 + (int64_t)x * c.ssx + (int64_t)y * c.ssy + (int64_t)z * c.ssz;
+            if (di != D.off + cell_index(D, dl[0], dl[1], dl[2]) || si != S.off + cell_index(S, sl[0], sl[1], sl[2])) {
+              printf("flattened ghost copy moves another cell\n");
+              return 1;
+            }
+          }
+      if (c.dvs != (int)D.vstride || c.svs != (int)S.vstride) { printf("flattened ghost copy variable stride\n"); return 1; }
+      ++nb;
+    }
+  }
+  printf("ok %lld\n", nb);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
@@ -562,6 +643,7 @@ int main() {
   if (std::string(mode) == "gathers") return check_gathers();
   if (std::string(mode) == "restrict") return check_restrict();
   if (std::string(mode) == "faces") return check_faces();
+  if (std::string(mode) == "flat") return check_flat();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

@@ -17,7 +17,9 @@ small C++ driver (`planner_check.cpp`):
   holds its children, and the leaf-coverage boxes mark exactly those cells;
 * a face whose ghost layers the stage kernel reads in place maps each ghost
   cell to the interior cell at that level position (periodic image) or to the
-  patch's own boundary cell (outflow)."""
+  patch's own boundary cell (outflow);
+* the flattened lists the batched kernels walk address the same cells as the
+  boxes they come from (prolongation by parent cell, ghost copies)."""
 import os
 import shutil
 import subprocess
@@ -175,4 +177,17 @@ def test_faces_read_in_place_map_to_the_right_cells(checker, bc):
     assert n > 0
     pb = ai.sedov_amr()
     (n,) = ghost(checker, pb.base_n[0], pb.max_level, bc, pb.patches, mode="faces")
+    assert n > 0
+
+
+@pytest.mark.parametrize("bc", [(ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6])
+def test_flattened_lists_address_the_same_cells(checker, bc):
+    (n,) = ghost(checker, 32, 2, bc, ai.nested_cubes(32, (32, 32), 11, pmin=8, pmax=16), mode="flat")
+    assert n > 0
+    base = 32   # prolongation boxes on odd rectangles of a partly covered face
+    rng = np.random.Generator(np.random.PCG64(7))
+    patches = ai.box_patches(0, (0, 0, 0), (base,) * 3, rng, 8, 16)
+    patches += ai.box_patches(1, (16, 16, 16), (40, 40, 40), rng, 8, 16)
+    patches += ai.box_patches(1, (40, 16, 16), (48, 40, 36), rng, 8, 12)
+    (n,) = ghost(checker, base, 1, bc, patches, mode="flat")
     assert n > 0
