@@ -52,6 +52,12 @@
 // the box), writes each of its fine cells once, at that cell's arena index,
 // from the parent-tile cell above it; each ghost copy box reads and writes the
 // cells of its segment.
+//
+// "cluster": base_n0 base_n1 base_n2 max_level bc0 .. bc5 buffer block
+// max_patch min_level, one patch list, then per patch "0" (not flagged) or "1"
+// and its n0 n1 n2 flags (z, y, x order).  Prints "ok", the number of new
+// patches and one "level lo0 lo1 lo2 n0 n1 n2" line each: the host clustering
+// from byte flags, for comparison with the oracle's.
 #include <algorithm>
 #include <array>
 #include <cstdio>
@@ -634,6 +640,54 @@ static int check_flat() {
   return 0;
 }
 
+static int run_cluster() {
+  int bn[3], ml;
+  amr_config cfg;
+  std::vector<HPatch> P;
+  int bc[6];
+  RegridParams rp;
+  if (scanf("%d %d %d %d %d %d %d %d %d %d", &bn[0], &bn[1], &bn[2], &ml, &bc[0], &bc[1], &bc[2], &bc[3], &bc[4],
+            &bc[5]) != 10)
+    return 2;
+  if (scanf("%d %d %d %d", &rp.buffer, &rp.block, &rp.max_patch, &rp.min_level) != 4) return 2;
+  if (!read_list(P)) return 2;
+  cfg = amr_config{};
+  cfg.nvar = 5;
+  cfg.precision = AMR_FP32;
+  cfg.gamma = 1.4;
+  cfg.theta = 1.5;
+  cfg.cfl = 0.4;
+  cfg.ref_ratio = 2;
+  for (int d = 0; d < 3; ++d) {
+    cfg.base_n[d] = bn[d];
+    cfg.domain_lo[d] = 0;
+    cfg.domain_hi[d] = 1;
+  }
+  for (int f = 0; f < 6; ++f) cfg.bc[f] = bc[f];
+  cfg.max_level = ml;
+  std::vector<std::vector<uint8_t>> flags(P.size());
+  for (size_t i = 0; i < P.size(); ++i) {
+    int has = 0;
+    if (scanf("%d", &has) != 1) return 2;
+    if (!has) continue;
+    flags[i].resize((size_t)P[i].n[0] * P[i].n[1] * P[i].n[2]);
+    for (auto& f : flags[i]) {
+      int v;
+      if (scanf("%d", &v) != 1) return 2;
+      f = (uint8_t)v;
+    }
+  }
+  std::vector<HPatch> out;
+  std::string msg;
+  if (cluster_patches(cfg, P, flags, rp, out, msg) != AMR_OK) {
+    printf("cluster failed: %s\n", msg.c_str());
+    return 1;
+  }
+  printf("ok %zu\n", out.size());
+  for (const HPatch& p : out) printf("%d %d %d %d %d %d %d\n", p.level, p.lo[0], p.lo[1], p.lo[2], p.n[0], p.n[1], p.n[2]);
+  return 0;
+}
+
 int main() {
   char mode[16] = {0};
   if (scanf("%15s", mode) != 1) return 2;
@@ -644,6 +698,7 @@ int main() {
   if (std::string(mode) == "restrict") return check_restrict();
   if (std::string(mode) == "faces") return check_faces();
   if (std::string(mode) == "flat") return check_flat();
+  if (std::string(mode) == "cluster") return run_cluster();
   int bn[3], ml;
   if (scanf("%d %d %d %d", &bn[0], &bn[1], &bn[2], &ml) != 4) return 2;
   std::vector<HPatch> oldp, newp;

@@ -19,7 +19,9 @@ small C++ driver (`planner_check.cpp`):
   cell to the interior cell at that level position (periodic image) or to the
   patch's own boundary cell (outflow);
 * the flattened lists the batched kernels walk address the same cells as the
-  boxes they come from (prolongation by parent cell, ghost copies)."""
+  boxes they come from (prolongation by parent cell, ghost copies);
+* the host clustering of flagged cells into new patches gives the oracle's
+  hierarchy (oracle.regrid.cluster, an independent implementation)."""
 import os
 import shutil
 import subprocess
@@ -191,3 +193,39 @@ def test_flattened_lists_address_the_same_cells(checker, bc):
     patches += ai.box_patches(1, (40, 16, 16), (48, 40, 36), rng, 8, 12)
     (n,) = ghost(checker, base, 1, bc, patches, mode="flat")
     assert n > 0
+
+
+def host_cluster(checker, base, max_level, bc, patches, flags, buffer, block, max_patch, min_level):
+    lines = [f"cluster {base} {base} {base} {max_level} {' '.join(map(str, bc))} {buffer} {block} {max_patch} "
+             f"{min_level}", listing(patches)]
+    for f in flags:
+        lines.append("0" if f is None else "1 " + " ".join(map(str, f.astype(np.uint8).ravel())))
+    r = subprocess.run([checker], input="\n".join(lines) + "\n", capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    rows = r.stdout.split("\n")[1:]
+    return [tuple(map(int, x.split())) for x in rows if x.strip()]
+
+
+@pytest.mark.parametrize("bc", [(ai.PERIODIC,) * 6, (ai.OUTFLOW,) * 6])
+@pytest.mark.parametrize("buffer,block,max_patch,min_level", [(2, 4, 32, 0), (1, 2, 16, 0), (4, 8, 32, 1)])
+def test_host_clustering_matches_the_oracle(checker, bc, buffer, block, max_patch, min_level):
+    from oracle import regrid as rg
+    patches = ai.nested_cubes(16, (16, 16), 41, pmin=8, pmax=16)
+    rng = np.random.Generator(np.random.PCG64(97 + buffer + block))
+    flags = []
+    for p in patches:
+        if p.level < min_level or p.level >= 2:
+            flags.append(None)
+            continue
+        f = np.zeros((p.n[2], p.n[1], p.n[0]), dtype=bool)
+        # a few seeded blobs of flagged cells
+        for _ in range(2):
+            c = [int(rng.integers(0, p.n[d])) for d in range(3)]
+            r = int(rng.integers(1, 4))
+            f[max(0, c[2] - r):c[2] + r, max(0, c[1] - r):c[1] + r, max(0, c[0] - r):c[0] + r] = True
+        flags.append(f)
+    ours = host_cluster(checker, 16, 2, bc, patches, flags, buffer, block, max_patch, min_level)
+    ref = rg.cluster(patches, flags, (16,) * 3, bc, 2, buffer=buffer, block=block, max_patch=max_patch,
+                     min_level=min_level)
+    assert ours == [(q.level, *q.lo, *q.n) for q in ref]
+    assert any(q[0] >= 1 for q in ours)
